@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark: partial plans evaluated per second by PUMP's exploration on one GB300.
+
+A step is one planning query on a device-resident graph, through the C ABI (pump_plan): particle
+edge masks for the query's obstacles, Explore (Algorithm 4) and PlanSelection with Monte Carlo
+certification (Algorithm 5).  `value` = partial plans evaluated (candidates of Algorithm 4) per
+second over the timed steps, summed over ranks.  `e2e` measures the same through the public API
+from pinned host buffers: graph build from host arrays + plan + result readback, per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload indoor_4k]
+
+Under torchrun each rank plans its own query (seed = rank): weak scaling, no collective on the
+data path; the timed region is bracketed by a barrier and the maximum over ranks is reported.
+`--impl reference` times the CPU oracle (plain single-threaded C restatement of the method) on the
+same workload, rank 0 only.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def plan_params(pump, wl):
+    return pump.default_plan_params(alpha=wl.alpha, eta=wl.eta, lam=wl.lam, n_mc=wl.n_mc, mc_substeps=wl.mc_substeps,
+                                    mc_seed=wl.mc_seed)
+
+
+def time_cpu_oracle(wl, budget_s=30.0, max_steps=1):
+    """Oracle step on the host: masks + Explore + PlanSelection on the oracle's own graph (graph
+    build untimed, as for the GPU step).  Returns (seconds per step, candidates per step, steps)."""
+    from oracle import cpu
+    g = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
+    kmin, kmax = cpu.cp_thresholds(wl.alpha, wl.eta, wl.n_particles)
+    times, cands = [], 0
+    t_start = time.perf_counter()
+    for _ in range(max_steps):
+        t0 = time.perf_counter()
+        masks = cpu.edge_masks(g, wl.xi, wl.boxes, wl.n_particles)
+        ex = cpu.explore(g["n"], g["row_ptr"], g["col"], g["ecost"], masks, 0, wl.goal_idx, kmin, kmax, wl.lam,
+                         wl.radius)
+        cpu.plan_select(g, ex, wl.alpha, wl.states, wl.boxes, wl.sigma, wl.n_mc, wl.mc_substeps, wl.mc_seed)
+        times.append(time.perf_counter() - t0)
+        cands = ex["n_candidates"]
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return float(np.mean(times)), cands, len(times)
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle as it stands, on this arm's workload and metric."""
+    from paper_1607_06886_gb300 import inputs
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import cpu
+    cpu.build()
+    wl = inputs.make_workload(args.workload, seed=0)
+    # bounded sample per step: the oracle graph and masks are built once (untimed); each step runs
+    # Explore and PlanSelection of the query on them
+    g = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
+    masks = cpu.edge_masks(g, wl.xi, wl.boxes, wl.n_particles)
+    kmin, kmax = cpu.cp_thresholds(wl.alpha, wl.eta, wl.n_particles)
+
+    def step():
+        ex = cpu.explore(g["n"], g["row_ptr"], g["col"], g["ecost"], masks, 0, wl.goal_idx, kmin, kmax, wl.lam,
+                         wl.radius)
+        cpu.plan_select(g, ex, wl.alpha, wl.states, wl.boxes, wl.sigma, wl.n_mc, wl.mc_substeps, wl.mc_seed)
+        return ex["n_candidates"]
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    cands = 0
+    for _ in range(args.steps):
+        cands += step()
+    dt = time.perf_counter() - t0
+    value = cands / dt
+    line = {"impl": "reference", "metric": "partial plans evaluated per second", "value": value,
+            "unit": "partial_plans/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "samples": wl.n - 2, "particles": wl.n_particles,
+                       "waypoints": wl.n_waypoints, "boxes": int(wl.boxes.shape[0]), "cp_target": wl.alpha,
+                       "seed": 0},
+            "cpu_baseline": {"value": value, "unit": "partial_plans/s", "cores": 1, "kind": "oracle",
+                             "sample": "Explore + PlanSelection per step on the oracle's graph and masks "
+                                       "(built once, untimed), single thread"},
+            "e2e": {"value": value, "unit": "partial_plans/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="indoor_4k")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1607_06886_gb300 import inputs, pump
+
+    ws, rank, local = dist_setup()
+    pump.load()
+    pump.use_torch_allocator()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = inputs.make_workload(args.workload, seed=rank)
+    prm = plan_params(pump, wl)
+    todev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    G = pump.Graph.build(todev(wl.states), todev(wl.goal_idx), todev(wl.boxes), todev(wl.xi), wl.radius,
+                         wl.n_particles, wl.n_waypoints, wl.sigma)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # warm-up
+    for _ in range(max(args.warmup, 3)):
+        res = G.plan(prm)
+        assert res["rc"] in (pump.OK, pump.ERR_INFEASIBLE), res
+    torch.cuda.synchronize()
+
+    # timed region: K plan steps, device time by CUDA events; L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = pump.kernel_launches()
+    cands = 0
+    parts = {"ms_masks": 0.0, "ms_explore": 0.0, "ms_select": 0.0}
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            res = G.plan(prm)
+            ev[k][1].record(stream)
+            cands += res["n_candidates"]
+            for key in parts:
+                parts[key] += res[key]
+        torch.cuda.synchronize()
+        barrier(ws)
+    launches = pump.kernel_launches() - launches0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_max = max_over_ranks(ms, ws)
+    cands_all = sum_over_ranks(cands, ws)
+    value = cands_all / (ms_max / 1000.0)
+    ms_per_step = ms_max / args.steps
+
+    # dominant kernels timed alone with CUDA events on the launching stream
+    roof, kernel_detail = roofline_measure(pump, G, prm, wl, dev, flush, args.steps)
+
+    # end to end through the public API from pinned host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_states, h_goal, h_boxes, h_xi = pin(wl.states), pin(wl.goal_idx), pin(wl.boxes), pin(wl.xi)
+    h2d = sum(int(t.numel() * t.element_size()) for t in (h_states, h_goal, h_boxes, h_xi))
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        G2 = pump.Graph.build(h_states, h_goal, h_boxes, h_xi, wl.radius, wl.n_particles, wl.n_waypoints, wl.sigma)
+        G2.plan(prm)
+        G2.close()
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_cands = 0
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        G2 = pump.Graph.build(h_states, h_goal, h_boxes, h_xi, wl.radius, wl.n_particles, wl.n_waypoints, wl.sigma)
+        r2 = G2.plan(prm)
+        e_cands += r2["n_candidates"]
+        G2.close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    e_value = sum_over_ranks(e_cands, ws) / (e_ms / 1000.0)
+    d2h = 4 * int(res["path_len"]) + 128  # result record and path
+
+    line = {
+        "metric": "partial plans evaluated per second", "value": value, "unit": "partial_plans/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "samples": wl.n - 2, "particles": wl.n_particles,
+                   "waypoints": wl.n_waypoints, "boxes": int(wl.boxes.shape[0]), "cp_target": wl.alpha,
+                   "edges": int(G.counts()[1]), "partial_plans_per_step": res["n_candidates"],
+                   "plans_per_step": res["n_plans"], "groups": res["n_groups"], "seed_per_rank": "rank",
+                   "l2": "flushed between steps (2x L2 buffer write)", "parallelism": f"replicas{ws}"},
+        "step_ms": {k: v / args.steps for k, v in parts.items()},
+        "result": {"cost": res["cost"], "cp_hat": res["cp_hat"], "cp_mc": res["cp_mc"], "status": res["status"]},
+        "clocks": clk.summary(),
+        "e2e": {"value": e_value, "unit": "partial_plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e_ms / e2e_steps, "includes": "graph build from pinned host arrays + plan + readback"},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernels": kernel_detail,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import cpu
+        cpu.build()
+        sec, oc, nst = time_cpu_oracle(wl)
+        line["cpu_baseline"] = {"value": oc / sec, "unit": "partial_plans/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{nst} full step(s) of the same query (masks + Explore + PlanSelection, "
+                                          f"graph built untimed), single thread, {sec:.1f} s per step"}
+    if rank == 0:
+        print(json.dumps(line))
+    G.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline_measure(pump, G, prm, wl, dev, flush, steps):
+    """Average device time of the edge-mask launch and of Explore, each run alone (CUDA events on
+    the launching stream, L2 flushed before each launch), with their algorithmic work."""
+    import torch
+    peaks = load_peaks()
+    stream = torch.cuda.current_stream()
+    reps = max(5, min(steps, 20))
+    # edge masks
+    t = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.edge_masks()
+        b.record(stream)
+        t.append((a, b))
+    torch.cuda.synchronize()
+    ms_mask = float(np.mean([a.elapsed_time(b) for a, b in t]))
+    # explore alone (persistent kernel + its init/finalize launches)
+    t = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = G.explore(prm)
+        b.record(stream)
+        t.append((a, b))
+    torch.cuda.synchronize()
+    ms_expl = float(np.mean([a.elapsed_time(b) for a, b in t]))
+    cnt = G.counts()
+    E, N, W = int(cnt[1]), int(cnt[4]), int(cnt[5])
+    # edge masks: ALU-bound; algorithmic lane-ops = 24 per particle-waypoint (3 axes x 8 float ops of
+    # the deviation recurrence and position) + 6 comparisons per particle-waypoint-box over all boxes
+    O = int(wl.boxes.shape[0])
+    ops_mask = float(E) * N * W * (24 + 6 * O)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    alu_peak = props.multi_processor_count * 128 * sm_mhz * 1e6  # lane-ops/s
+    mask_frac = (ops_mask / (ms_mask / 1e3)) / alu_peak
+    # explore: algorithmic bytes per candidate (edge id, cost, mask words, dominance slot) and per
+    # surviving plan (record), see the design doc
+    w = N // 32
+    bytes_expl = float(st["n_candidates"]) * (4 + 4 + 4 * w + 4) + float(st["n_plans"]) * (28 + 4 * w)
+    hbm = float(peaks["hbm_gbs"])
+    expl_gbs = bytes_expl / (ms_expl / 1e3) / 1e9
+    detail = {
+        "edge_mask": {"ms": ms_mask, "bound": "alu", "ops": ops_mask, "achieved_tops": ops_mask / (ms_mask / 1e3) / 1e12,
+                      "peak_tops": alu_peak / 1e12, "frac": mask_frac},
+        "explore": {"ms": ms_expl, "bound": "hbm", "bytes": bytes_expl, "achieved_gbs": expl_gbs, "peak_gbs": hbm,
+                    "frac": expl_gbs / hbm, "iterations": st["n_iterations"]},
+    }
+    if ms_expl >= ms_mask:
+        roof = {"kernel": "k_explore_persistent", "bound": "hbm", "achieved": expl_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": expl_gbs / hbm, "traffic": None, "peak_source": peaks["_source"]}
+    else:
+        roof = {"kernel": "k_edge_mask", "bound": "alu", "achieved": ops_mask / (ms_mask / 1e3) / 1e12,
+                "peak": alu_peak / 1e12, "unit": "Tops/s", "frac": mask_frac, "traffic": None,
+                "peak_source": "152 SMs x 128 lanes x sm_max_mhz (derived)"}
+    return roof, detail
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,260 @@
+/*
+ * pump.h - C interface of libpump, a GB300 (sm_103a) implementation of the
+ * multiobjective exploration of PUMP (Parallel Uncertainty-aware
+ * Multiobjective Planning; Ichter, Schmerling, Agha-mohammadi, Pavone,
+ * "Real-Time Stochastic Kinodynamic Motion Planning via Multiobjective Search
+ * on GPUs").
+ *
+ * Conventions for every entry point:
+ *  - Returns a pump_status code; no exception or device trap crosses this
+ *    interface.  Output arguments are written only when PUMP_OK is returned,
+ *    except where stated.
+ *  - Array arguments may be host or device pointers (the library inspects
+ *    each one); host arrays are copied to the device on the given stream.
+ *    The caller keeps ownership of everything it passes in.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; calls that return results on the host synchronise it.
+ *  - A pump_graph is used by one stream at a time.
+ *  - Device memory comes from the allocator installed with
+ *    pump_set_allocator (default: cudaMallocAsync on the call's stream).
+ *
+ * Problem model (Section II, Eq. (1)-(3); Section V-A): 6D double integrator
+ * (3D position, velocity), state x = (p, v).  Obstacles are closed
+ * axis-aligned boxes (Section V-C).  A plan's approximate collision
+ * probability is popcount(mask) / N where mask ORs, over the plan's
+ * connections, which of N particles collide (Section III-B).
+ */
+#ifndef PUMP_H_
+#define PUMP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PUMP_OK = 0,
+  PUMP_ERR_INVALID_ARG = 1, /* bad size, pointer or parameter                    */
+  PUMP_ERR_OOM = 2,         /* the allocator returned NULL                         */
+  PUMP_ERR_CUDA = 3,        /* a CUDA runtime call failed                          */
+  PUMP_ERR_CAPACITY = 4,    /* plan arena full: raise pump_plan_params.max_plans   */
+  PUMP_ERR_TIMEOUT = 5,     /* iteration cap reached, or a device wait gave up     */
+  PUMP_ERR_INFEASIBLE = 6   /* Algorithm 5 found no plan with MC CP <= alpha       */
+} pump_status;
+
+/* pump_plan_params.flags */
+#define PUMP_NO_EARLY_STOP 1 /* Explore runs until P_open is empty (testing)        */
+#define PUMP_EXPLORE_ONLY 2  /* pump_plan stops after Explore (no PlanSelection)    */
+#define PUMP_STEPWISE 4      /* run Explore's phases as separate launches           */
+
+typedef struct pump_graph pump_graph;
+
+/* Closed box lo <= p <= hi on all three axes. */
+typedef struct {
+  float lo[3];
+  float hi[3];
+} pump_aabb;
+
+typedef struct {
+  float radius;        /* r_n: edge v->u iff float(Cost(v,u)) < radius (Section IV, Near) */
+  int32_t n_particles; /* N, a multiple of 32 in [32, 1024]; masks have N/32 words       */
+  int32_t n_waypoints; /* W >= 1 waypoints per connection                                */
+  float sigma;         /* process-noise standard deviation, V_c = sigma^2 I (Eq. (1))    */
+  int32_t flags;       /* reserved, 0                                                    */
+} pump_graph_params;
+
+typedef struct {
+  float alpha;            /* CP target (Eq. (3))                                          */
+  float eta;              /* CP approximation factor: alpha_min = alpha/eta, alpha_max = eta*alpha (Algorithm 2) */
+  float lambda;           /* group cost factor in (0, 1] (Algorithm 2, Algorithm 4)        */
+  int32_t n_mc;           /* Monte Carlo rollouts per certification (Section III-A)       */
+  int32_t mc_substeps;    /* rollout sub-steps per waypoint interval (>= 1)                */
+  uint64_t mc_seed;       /* Philox4x64-10 key of the rollout normals                      */
+  int64_t max_plans;      /* plan arena capacity; more survivors -> PUMP_ERR_CAPACITY      */
+  int32_t max_iterations; /* cap on Explore's group index; exceeded -> PUMP_ERR_TIMEOUT    */
+  int32_t flags;          /* PUMP_NO_EARLY_STOP | PUMP_EXPLORE_ONLY | PUMP_STEPWISE       */
+} pump_plan_params;
+
+typedef struct {
+  int32_t status;         /* pump_status of the plan (PUMP_ERR_INFEASIBLE possible)        */
+  int32_t chosen_plan;    /* arena id of the selected plan, -1 if none                     */
+  float cost;             /* its cost                                                      */
+  int32_t popc;           /* its particle-collision count; CP-hat = popc / N               */
+  float cp_hat;           /* popc / N                                                      */
+  double cp_mc;           /* Monte Carlo CP of the selected plan                           */
+  int64_t mc_collisions;  /* colliding rollouts of the selected plan                       */
+  int64_t n_candidates;   /* partial plans evaluated (Algorithm 4, candidate creation)     */
+  int64_t n_kept;         /* candidates under the CP cutoff                                */
+  int64_t n_plans;        /* plans in the arena (root + surviving candidates)              */
+  int32_t n_iterations;   /* final group index i of Algorithm 4                            */
+  int32_t n_groups;       /* non-empty groups expanded                                     */
+  int32_t n_goal;         /* |P_goal|                                                      */
+  int32_t n_certified;    /* plans certified by Monte Carlo                                */
+  int32_t path_len;       /* node ids of the selected plan written to `path`               */
+  int32_t path_truncated; /* 1 if path_len exceeded path_cap (path holds the first path_cap) */
+  float ms_masks;         /* device time of the edge-mask step                             */
+  float ms_explore;       /* device time of Explore                                        */
+  float ms_select;        /* device time of PlanSelection                                  */
+} pump_plan_result;
+
+/* --------------------------------------------------------------------------
+ * pump_set_allocator: install device-memory callbacks used for every later
+ * allocation (graph buffers and plan scratch).  alloc(bytes, stream, ctx)
+ * returns a device pointer or NULL; free_(ptr, stream, ctx) releases it.
+ * Passing alloc == NULL restores the default (cudaMallocAsync/cudaFreeAsync).
+ * Not thread-safe with concurrent library calls.  Returns PUMP_OK.
+ * No counterpart in the paper (runtime plumbing).
+ */
+int pump_set_allocator(void* (*alloc)(size_t bytes, void* stream, void* ctx),
+                       void (*free_)(void* ptr, void* stream, void* ctx), void* ctx);
+
+/* --------------------------------------------------------------------------
+ * pump_graph_build: BuildGraph (Algorithm 3) plus the obstacle-dependent
+ * edge geometry the exploration needs.
+ *  states  : n x 6 float (p, v) row-major; x_init = states[start_idx].
+ *  goal_idx: n_goal node ids forming X_goal (at least one; Algorithm 3 keeps
+ *            one sample of X_goal in V).
+ *  boxes   : n_boxes closed AABBs (0 <= n_boxes <= 1024).
+ *  xi      : N x (W+1) x 3 x 2 float standard normals (common random numbers
+ *            of the particles: xi[i][0] draws the initial deviation from the
+ *            stationary covariance, xi[i][k] drives step k).
+ * Computes: node validity (outside every box), directed edges v->u for
+ * valid v != u with float(Cost(v,u)) < radius whose nominal connection,
+ * sampled at 4W uniform times in (0, tau], stays outside the boxes; edges of
+ * each source sorted by target id; per edge the float cost, duration tau,
+ * waypoint step h = tau/W, the closed-loop transition Phi(h) and noise
+ * factor L(h), and the W nominal waypoints at t = k h.  Cost is the optimal
+ * cost of the connection under c = integral (1 + u^T u) dt (Section II).
+ * Errors: INVALID_ARG (n < 2, start/goal ids out of range or start inside
+ * a box, N not a multiple of 32 or > 1024, W < 1 or > 64, radius <= 0,
+ * sigma < 0), OOM, CUDA.  On success *out owns device memory; release with
+ * pump_graph_destroy.  Synchronises `stream`.
+ */
+int pump_graph_build(const float* states, int32_t n, int32_t start_idx, const int32_t* goal_idx,
+                     int32_t n_goal, const pump_aabb* boxes, int32_t n_boxes, const float* xi,
+                     const pump_graph_params* params, void* stream, pump_graph** out);
+
+/* --------------------------------------------------------------------------
+ * pump_graph_from_csr: import a precomputed graph with its edge masks (the
+ * paper caches neighbours and edge controls offline, Section V-A).
+ *  row_ptr : n+1 int32, col: E int32 targets (ascending within a row, no self
+ *            loops), ecost: E float edge costs (>= 0), emask: E x (N/32) uint32.
+ *  start_idx, goal_idx: as in pump_graph_build.
+ * The graph has no geometry: pump_edge_masks and pump_certify return
+ * INVALID_ARG on it.  Errors: INVALID_ARG, OOM, CUDA.  Synchronises.
+ */
+int pump_graph_from_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, const float* ecost,
+                        const uint32_t* emask, int32_t n_particles, int32_t start_idx,
+                        const int32_t* goal_idx, int32_t n_goal, void* stream, pump_graph** out);
+
+/* --------------------------------------------------------------------------
+ * pump_edge_masks: particle collision mask of every edge (Section III-B with
+ * a direct particle-in-box test).  Particle i of edge e starts at deviation
+ * Linf xi[i][0] (Linf the Cholesky factor of the stationary covariance) and
+ * steps d <- Phi(h) d + L(h) xi[i][k], k = 1..W, per axis in float with the
+ * fixed fused-multiply-add order
+ *   n0 = L00 xi0;  n1 = fma(L10, xi0, L11 xi1);
+ *   d0 = fma(Phi00, d0, fma(Phi01, d1, n0));  d1 = fma(Phi10, d0_old, fma(Phi11, d1, n1));
+ * its position at waypoint k is nominal_k + d0 (float add).  Bit i of the
+ * mask is set iff some waypoint position lies in some box.  Masks are kept
+ * in the graph (E x N/32 words, bit i%32 of word i/32).  Enqueued on
+ * `stream`, no synchronisation.  Errors: INVALID_ARG (NULL graph, imported
+ * graph), CUDA.
+ */
+int pump_edge_masks(pump_graph* g, void* stream);
+
+/* --------------------------------------------------------------------------
+ * pump_explore: Explore (Algorithm 4) on the graph's current edge masks.
+ * Starts from the root plan (x_init, {}, 0, 0); groups G_i = open plans with
+ * cost <= float(i * (lambda * r)) (product in double; r = the graph's radius,
+ * or the `radius` argument for imported graphs); each group plan is extended
+ * along every out-edge (cost = float sum, mask = OR); candidates with
+ * popc >= K_max are cut (K_max = #{k >= 0 : k < (eta*alpha) N}); every open
+ * plan dominated at its node (another plan there with strictly lower cost
+ * and no larger popc) is removed; the search stops when a group holds a goal
+ * plan with popc < K_min (K_min = #{k >= 0 : k < (alpha/eta) N}) or no open
+ * plan remains.  Surviving candidates get consecutive arena ids in candidate
+ * order (group plans by ascending id, then out-edges by target id).
+ * `radius` is used only for graphs from pump_graph_from_csr (pass 0 for
+ * built graphs).  Results stay in the graph (pump_export); counters in
+ * `stats` (only the Explore fields are written).  Synchronises.
+ * Errors: INVALID_ARG, OOM, CUDA, CAPACITY (arena full), TIMEOUT.
+ */
+int pump_explore(pump_graph* g, const pump_plan_params* params, float radius, pump_plan_result* stats,
+                 void* stream);
+
+/* --------------------------------------------------------------------------
+ * pump_plan: PUMP (Algorithm 2) on a built graph: edge masks, Explore, and
+ * PlanSelection (Algorithm 5): P_goal sorted by ascending CP-hat, ties by
+ * descending cost then ascending id; 1-based bisection with MC(P_m) > alpha
+ * moving u = m - 1, else l = m; failure if the final MC(P_m) > alpha.
+ * Smoothing is not applied.  `path` (host, capacity path_cap) receives the
+ * node ids of the selected plan from x_init.  `out` is written on PUMP_OK
+ * and on PUMP_ERR_INFEASIBLE (out->status tells which).  Synchronises.
+ * Errors: those of pump_explore, plus INFEASIBLE (no certified plan).
+ */
+int pump_plan(pump_graph* g, const pump_plan_params* params, int32_t* path, int32_t path_cap,
+              pump_plan_result* out, void* stream);
+
+/* --------------------------------------------------------------------------
+ * pump_certify: MC(p) (Section III-A) for the plan visiting `path`
+ * (path_len >= 1 node ids, consecutive ones joined by graph edges).  n_mc
+ * rollouts of the closed loop: deviation drawn from the stationary
+ * covariance at x_init and carried across connections; each waypoint
+ * interval split into `substeps` steps of h/substeps; a rollout collides
+ * iff a sub-step position lies in a box.  Rollout m, step s, axis j draws
+ * its two normals by Box-Muller from Philox4x64-10 with counter (m, s, j, 0)
+ * and key (seed, 0).  Writes the colliding count and count / n_mc.
+ * Errors: INVALID_ARG (imported graph, path not along edges), OOM, CUDA.
+ * Synchronises.
+ */
+int pump_certify(pump_graph* g, const int32_t* path, int32_t path_len, int32_t n_mc, int32_t substeps,
+                 uint64_t seed, int64_t* n_collide, double* cp, void* stream);
+
+/* --------------------------------------------------------------------------
+ * pump_export: copy one array of the graph or of the last Explore into host
+ * memory `host_buf` of `cap` bytes; *needed receives the byte size (always
+ * written).  Returns INVALID_ARG if cap < needed or `what` is unknown.
+ * Synchronises.  No counterpart in the paper (inspection and testing).
+ */
+enum {
+  PUMP_EXPORT_COUNTS = 0,     /* int64[8]: n, E, n_plans, n_goal, N, W, n_words, valid nodes */
+  PUMP_EXPORT_NODE_VALID = 1, /* uint8[n]                        */
+  PUMP_EXPORT_ROW_PTR = 2,    /* int32[n+1]                      */
+  PUMP_EXPORT_COL = 3,        /* int32[E]                        */
+  PUMP_EXPORT_ECOST = 4,      /* float[E]                        */
+  PUMP_EXPORT_TAU = 5,        /* float[E]                        */
+  PUMP_EXPORT_H = 6,          /* float[E]                        */
+  PUMP_EXPORT_PHI = 7,        /* float[E][4]                     */
+  PUMP_EXPORT_L = 8,          /* float[E][3]                     */
+  PUMP_EXPORT_NOMINAL = 9,    /* float[E][W][3]                  */
+  PUMP_EXPORT_LINF = 10,      /* float[3]                        */
+  PUMP_EXPORT_MASKS = 11,     /* uint32[E][N/32]                 */
+  PUMP_EXPORT_PLAN_HEAD = 12, /* int32[n_plans]                  */
+  PUMP_EXPORT_PLAN_PARENT = 13,
+  PUMP_EXPORT_PLAN_COST = 14,    /* float[n_plans]                  */
+  PUMP_EXPORT_PLAN_MASK = 15,    /* uint32[n_plans][N/32]           */
+  PUMP_EXPORT_PLAN_POPC = 16,    /* int32[n_plans]                  */
+  PUMP_EXPORT_PLAN_CREATED = 17, /* int32[n_plans] group index that created the plan (-1 root) */
+  PUMP_EXPORT_PLAN_EXPANDED = 18, /* int32[n_plans] group index that expanded it, -1 if never */
+  PUMP_EXPORT_GOAL_PLANS = 19     /* int32[n_goal] P_goal ids in PlanSelection order */
+};
+int pump_export(pump_graph* g, int32_t what, void* host_buf, size_t cap, size_t* needed);
+
+/* pump_kernel_launches: number of kernels this library has launched in the
+ * process so far (host-side counter, all devices; for launch accounting).
+ * No counterpart in the paper. */
+uint64_t pump_kernel_launches(void);
+
+/* pump_graph_destroy: release a graph and its scratch (NULL is a no-op). */
+void pump_graph_destroy(pump_graph* g);
+
+/* pump_status_str: static description of a status code. */
+const char* pump_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PUMP_H_ */

@@ -784,17 +784,15 @@ static void box_muller(uint64_t w1, uint64_t w2, float* z0, float* z1) {
   *z1 = (float)(rad * sin(ang));
 }
 
-/* Normals (xi0, xi1) for rollout m, step s, all three axes: counter          */
-/* (m, s, 0, 0) gives axes 0 and 1, counter (m, s, 1, 0) gives axis 2; key     */
-/* (seed, 0).                                                                    */
+/* Normals (xi0, xi1) of rollout m, step s, axis j: Philox4x64-10 with        */
+/* counter (m, s, j, 0) and key (seed, 0); words 0 and 1 feed Box-Muller.      */
 void orc_mc_normals(uint64_t seed, uint64_t m, uint64_t s, float* xi /* 3 x 2 */) {
-  uint64_t key[2] = {seed, 0}, c[4] = {m, s, 0, 0}, o[4];
-  orc_philox4x64(c, key, o);
-  box_muller(o[0], o[1], &xi[0], &xi[1]);
-  box_muller(o[2], o[3], &xi[2], &xi[3]);
-  c[2] = 1;
-  orc_philox4x64(c, key, o);
-  box_muller(o[0], o[1], &xi[4], &xi[5]);
+  uint64_t key[2] = {seed, 0}, o[4];
+  for (uint64_t j = 0; j < 3; ++j) {
+    uint64_t c[4] = {m, s, j, 0};
+    orc_philox4x64(c, key, o);
+    box_muller(o[0], o[1], &xi[2 * j], &xi[2 * j + 1]);
+  }
 }
 
 /* ========================================================================== */

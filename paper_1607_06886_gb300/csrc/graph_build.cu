@@ -1,0 +1,326 @@
+// BuildGraph (Algorithm 3) on the device: SampleFree validity, Near with the
+// optimal steering cost, Collision on the nominal connection, and the per-edge
+// values the exploration uses (cost, duration, waypoint step, closed-loop
+// Phi(h), noise factor L(h), nominal waypoints).  Compiled without FMA
+// contraction so double-precision expressions round as written.
+#include <cuda_runtime.h>
+
+#include "pump_internal.cuh"
+
+namespace pump {
+namespace {
+
+constexpr int kBlock = 256;
+
+__global__ void k_node_flags(const float* __restrict__ states, int n, const float* __restrict__ boxes, int nb,
+                             const int32_t* __restrict__ goal_idx, int n_goal, uint8_t* valid, uint8_t* is_goal) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) {
+    float x = states[6 * v], y = states[6 * v + 1], z = states[6 * v + 2];
+    bool in = false;
+    for (int o = 0; o < nb && !in; ++o) in = in_box_dev(x, y, z, boxes + 6 * o);
+    valid[v] = in ? 0 : 1;
+    is_goal[v] = 0;
+  }
+}
+
+__global__ void k_goal_flags(const int32_t* __restrict__ goal_idx, int n_goal, uint8_t* is_goal) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n_goal) is_goal[goal_idx[k]] = 1;
+}
+
+// Exact necessary conditions for float(Cost(v,u)) < r, evaluated in float with
+// a 1e-4 relative margin (float rounding here is below 1e-6 relative):
+//   Cost >= 2 |dv|                       (time term + velocity-change energy)
+//   |dp| < |vbar| r + (3/32) r^2         (position energy 12|dp - vbar t|^2/t^3 < r - t, t < r)
+__device__ inline bool prefilter(const float* sv, const float* su, float r) {
+  float dv2 = 0.f, dp2 = 0.f, vb2 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float dv = su[3 + j] - sv[3 + j], dp = su[j] - sv[j], vb = 0.5f * (su[3 + j] + sv[3 + j]);
+    dv2 += dv * dv;
+    dp2 += dp * dp;
+    vb2 += vb * vb;
+  }
+  const float m = 1.0001f;
+  if (2.f * sqrtf(dv2) >= r * m) return false;
+  if (sqrtf(dp2) >= (sqrtf(vb2) * r + 0.09375f * r * r) * m + 1e-6f) return false;
+  return true;
+}
+
+// Pass 1 counts and pass 2 lists the pairs (v, u), v != u, both valid, that
+// pass the prefilter.  One warp covers 32 targets u of one source v.
+template <bool kWrite>
+__global__ void k_prefilter(const float* __restrict__ states, const uint8_t* __restrict__ valid, int n, float r,
+                            unsigned long long* count, int2* list) {
+  const int nw = (n + 31) / 32;
+  const long long total = (long long)n * nw;
+  const int lane = threadIdx.x & 31;
+  long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (; wid < total; wid += nwarps) {
+    int v = (int)(wid / nw);
+    int u = (int)(wid % nw) * 32 + lane;
+    bool ok = false;
+    if (u < n && u != v && valid[v] && valid[u]) ok = prefilter(states + 6 * v, states + 6 * u, r);
+    unsigned b = __ballot_sync(0xffffffffu, ok);
+    if (b == 0) continue;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(b));
+    if (kWrite) {
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (ok) list[base + __popc(b & ((1u << lane) - 1u))] = make_int2(v, u);
+    }
+  }
+}
+
+// Collision(v, u): the nominal connection of duration tau (float) sampled at
+// t_m = tau (m / 4W), m = 1..4W, positions rounded to float, closed boxes.
+__device__ inline bool connection_hits(const double* xv, const double* xu, double tau, int W, const float* boxes,
+                                       int nb) {
+  for (int m = 1; m <= 4 * W; ++m) {
+    double t = tau * ((double)m / (double)(4 * W));
+    float p0 = (float)nominal_dev(xv, xu, tau, 0, t);
+    float p1 = (float)nominal_dev(xv, xu, tau, 1, t);
+    float p2 = (float)nominal_dev(xv, xu, tau, 2, t);
+    for (int o = 0; o < nb; ++o)
+      if (in_box_dev(p0, p1, p2, boxes + 6 * o)) return true;
+  }
+  return false;
+}
+
+__global__ void k_steer_pairs(const float* __restrict__ states, const int2* __restrict__ list, long long n_list,
+                              int n, float r, int W, const float* __restrict__ boxes_g, int nb, uint32_t* keep) {
+  extern __shared__ float boxes[];
+  for (int k = threadIdx.x; k < 6 * nb; k += blockDim.x) boxes[k] = boxes_g[k];
+  __syncthreads();
+  const int nw = (n + 31) / 32;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n_list;
+       q += (long long)gridDim.x * blockDim.x) {
+    int2 vu = list[q];
+    double xv[6], xu[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      xv[j] = (double)states[6 * vu.x + j];
+      xu[j] = (double)states[6 * vu.y + j];
+    }
+    double tau, J;
+    if (!steer_dev(xv, xu, &tau, &J)) continue;
+    if (!(__double2float_rn(J) < r)) continue;
+    double td = (double)__double2float_rn(tau);
+    if (connection_hits(xv, xu, td, W, boxes, nb)) continue;
+    atomicOr(keep + (size_t)vu.x * nw + (vu.y >> 5), 1u << (vu.y & 31));
+  }
+}
+
+__global__ void k_row_counts(const uint32_t* __restrict__ keep, int n, int32_t* deg) {
+  const int nw = (n + 31) / 32;
+  int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (v >= n) return;
+  int c = 0;
+  for (int k = lane; k < nw; k += 32) c += __popc(keep[(size_t)v * nw + k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) deg[v] = c;
+}
+
+// Exclusive scan of n int32 into out[0..n], out[n] = total; one block.
+__global__ void k_scan_single(const int32_t* __restrict__ in, int n, int32_t* out) {
+  __shared__ int64_t part[1024];
+  int T = blockDim.x, t = threadIdx.x;
+  int per = (n + T - 1) / T;
+  int lo = min(n, t * per), hi = min(n, lo + per);
+  int64_t s = 0;
+  for (int k = lo; k < hi; ++k) s += in[k];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < T; off <<= 1) {
+    int64_t v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int64_t run = part[t] - s;
+  for (int k = lo; k < hi; ++k) {
+    out[k] = (int32_t)run;
+    run += in[k];
+  }
+  if (t == T - 1) out[n] = (int32_t)part[T - 1];
+}
+
+// One warp per source row: edges in ascending target order, values recomputed.
+__global__ void k_fill(const float* __restrict__ states, const uint32_t* __restrict__ keep, int n, int W, float sigma,
+                       const int32_t* __restrict__ row_ptr, int32_t* col, float* ecost, float* tau_o, float* h_o,
+                       float* phi_o, float* L_o, float* nom_o) {
+  const int nw = (n + 31) / 32;
+  int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (v >= n) return;
+  double xv[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) xv[j] = (double)states[6 * v + j];
+  int pos = row_ptr[v];
+  for (int k = 0; k < nw; ++k) {
+    uint32_t word = keep[(size_t)v * nw + k];
+    if (!word) continue;
+    if ((word >> lane) & 1u) {
+      int u = k * 32 + lane;
+      int e = pos + __popc(word & ((1u << lane) - 1u));
+      double xu[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) xu[j] = (double)states[6 * u + j];
+      double tau = 0.0, J = 0.0;
+      steer_dev(xv, xu, &tau, &J);
+      float t32 = __double2float_rn(tau);
+      float h = __fdiv_rn(t32, (float)W);
+      col[e] = u;
+      ecost[e] = __double2float_rn(J);
+      tau_o[e] = t32;
+      h_o[e] = h;
+      double Phi[4], L[3], Linf[3];
+      model_dev((double)sigma, (double)h, Phi, L, Linf);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) phi_o[4 * (size_t)e + q] = __double2float_rn(Phi[q]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) L_o[3 * (size_t)e + q] = __double2float_rn(L[q]);
+      double td = (double)t32;
+      for (int kk = 1; kk <= W; ++kk) {
+        double t = (double)kk * (double)h;
+        for (int j = 0; j < 3; ++j)
+          nom_o[((size_t)e * W + (kk - 1)) * 3 + j] = __double2float_rn(nominal_dev(xv, xu, td, j, t));
+      }
+    }
+    pos += __popc(word);
+  }
+}
+
+// xi[i][k][axis][c] -> xi_t[k][axis][i] as float2 (lane-contiguous particles).
+__global__ void k_transpose_xi(const float* __restrict__ xi, int N, int W, float2* xi_t) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  int total = N * (W + 1) * 3;
+  if (q >= total) return;
+  int i = q / ((W + 1) * 3);
+  int rem = q % ((W + 1) * 3);
+  int k = rem / 3, a = rem % 3;
+  xi_t[((size_t)k * 3 + a) * N + i] = make_float2(xi[2 * (size_t)q], xi[2 * (size_t)q + 1]);
+}
+
+__global__ void k_linf(float sigma, float* out) {
+  double Phi[4], L[3], Linf[3];
+  model_dev((double)sigma, 1.0, Phi, L, Linf);
+  out[0] = __double2float_rn(Linf[0]);
+  out[1] = __double2float_rn(Linf[1]);
+  out[2] = __double2float_rn(Linf[2]);
+}
+
+__global__ void k_count_valid(const uint8_t* __restrict__ valid, int n, int32_t* out) {
+  int c = 0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) c += valid[v];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
+}
+
+}  // namespace
+
+// Expects g->states, g->boxes, g->valid, g->is_goal, xi (raw, device) staged.
+int build_graph_device(pump_graph* g, cudaStream_t s) {
+  const int n = g->n;
+  const int nw = (n + 31) / 32;
+  const int sms = num_sms();
+  // node flags (validity) and goal flags were filled by the caller's kernels
+  // prefilter: count, allocate, list
+  unsigned long long* d_count = (unsigned long long*)dev_alloc(sizeof(unsigned long long) * 2, s);
+  if (!d_count) return PUMP_ERR_OOM;
+  PUMP_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * 2, s));
+  int grid = sms * 8;
+  k_prefilter<false><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, d_count, nullptr);
+  note_launch();
+  unsigned long long n_list = 0;
+  PUMP_CUDA_TRY(cudaMemcpyAsync(&n_list, d_count, sizeof(n_list), cudaMemcpyDeviceToHost, s));
+  PUMP_CUDA_TRY(cudaStreamSynchronize(s));
+  int2* list = nullptr;
+  if (n_list) {
+    list = (int2*)dev_alloc(sizeof(int2) * n_list, s);
+    if (!list) { dev_free(d_count, s); return PUMP_ERR_OOM; }
+    PUMP_CUDA_TRY(cudaMemsetAsync(d_count + 1, 0, sizeof(unsigned long long), s));
+    k_prefilter<true><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, d_count + 1, list);
+    note_launch();
+  }
+  uint32_t* keep = (uint32_t*)dev_alloc(sizeof(uint32_t) * (size_t)n * nw, s);
+  int32_t* deg = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)(n + 1), s);
+  if (!keep || !deg) return PUMP_ERR_OOM;
+  PUMP_CUDA_TRY(cudaMemsetAsync(keep, 0, sizeof(uint32_t) * (size_t)n * nw, s));
+  if (n_list) {
+    long long blocks = ((long long)n_list + kBlock - 1) / kBlock;
+    int gsteer = (int)(blocks < (long long)sms * 16 ? blocks : (long long)sms * 16);
+    k_steer_pairs<<<gsteer, kBlock, sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1), s>>>(
+        g->states, list, (long long)n_list, n, g->radius, g->W, g->boxes, g->n_boxes, keep);
+    note_launch();
+  }
+  k_row_counts<<<(n + 7) / 8, kBlock, 0, s>>>(keep, n, deg);
+  note_launch();
+  g->row_ptr = (int32_t*)graph_alloc(g, sizeof(int32_t) * (size_t)(n + 1), s);
+  if (!g->row_ptr) return PUMP_ERR_OOM;
+  k_scan_single<<<1, 1024, 0, s>>>(deg, n, g->row_ptr);
+  note_launch();
+  int32_t E = 0;
+  PUMP_CUDA_TRY(cudaMemcpyAsync(&E, g->row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  PUMP_CUDA_TRY(cudaStreamSynchronize(s));
+  g->E = E;
+  size_t Es = E > 0 ? (size_t)E : 1;
+  g->col = (int32_t*)graph_alloc(g, sizeof(int32_t) * Es, s);
+  g->ecost = (float*)graph_alloc(g, sizeof(float) * Es, s);
+  g->tau = (float*)graph_alloc(g, sizeof(float) * Es, s);
+  g->h = (float*)graph_alloc(g, sizeof(float) * Es, s);
+  g->phi = (float*)graph_alloc(g, sizeof(float) * 4 * Es, s);
+  g->L = (float*)graph_alloc(g, sizeof(float) * 3 * Es, s);
+  g->nom = (float*)graph_alloc(g, sizeof(float) * 3 * (size_t)g->W * Es, s);
+  g->emask = (uint32_t*)graph_alloc(g, sizeof(uint32_t) * (size_t)g->n_words * Es, s);
+  if (!g->col || !g->ecost || !g->tau || !g->h || !g->phi || !g->L || !g->nom || !g->emask) return PUMP_ERR_OOM;
+  if (E > 0) {
+    k_fill<<<(n + 7) / 8, kBlock, 0, s>>>(g->states, keep, n, g->W, g->sigma, g->row_ptr, g->col, g->ecost, g->tau,
+                                          g->h, g->phi, g->L, g->nom);
+    note_launch();
+  }
+  // valid node count (for export)
+  PUMP_CUDA_TRY(cudaMemsetAsync(deg, 0, sizeof(int32_t), s));
+  k_count_valid<<<32, kBlock, 0, s>>>(g->valid, n, deg);
+  note_launch();
+  PUMP_CUDA_TRY(cudaMemcpyAsync(&g->n_valid, deg, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  PUMP_CUDA_TRY(cudaGetLastError());
+  PUMP_CUDA_TRY(cudaStreamSynchronize(s));
+  dev_free(d_count, s);
+  if (list) dev_free(list, s);
+  dev_free(keep, s);
+  dev_free(deg, s);
+  return PUMP_OK;
+}
+
+int launch_node_flags(pump_graph* g, const int32_t* goal_dev, cudaStream_t s) {
+  k_node_flags<<<(g->n + kBlock - 1) / kBlock, kBlock, 0, s>>>(g->states, g->n, g->boxes, g->n_boxes, goal_dev,
+                                                              g->n_goal, g->valid, g->is_goal);
+  note_launch();
+  k_goal_flags<<<(g->n_goal + kBlock - 1) / kBlock, kBlock, 0, s>>>(goal_dev, g->n_goal, g->is_goal);
+  note_launch();
+  PUMP_CUDA_TRY(cudaGetLastError());
+  return PUMP_OK;
+}
+
+int launch_transpose_xi(pump_graph* g, const float* xi_dev, cudaStream_t s) {
+  int total = g->N * (g->W + 1) * 3;
+  k_transpose_xi<<<(total + kBlock - 1) / kBlock, kBlock, 0, s>>>(xi_dev, g->N, g->W, g->xi_t);
+  note_launch();
+  PUMP_CUDA_TRY(cudaGetLastError());
+  return PUMP_OK;
+}
+
+int launch_linf(pump_graph* g, float* out_dev, cudaStream_t s) {
+  k_linf<<<1, 1, 0, s>>>(g->sigma, out_dev);
+  note_launch();
+  PUMP_CUDA_TRY(cudaGetLastError());
+  return PUMP_OK;
+}
+
+}  // namespace pump

@@ -1,0 +1,182 @@
+"""BuildGraph, edge masks, Explore and PlanSelection on the GPU vs the CPU oracle, each side on its
+own graph built from the same seeded samples, obstacles and particle normals.
+
+Graph tier (tolerance): same node flags and edge sets (an edge may differ only where the oracle's
+cost is within 2 float ulps of r), edge values within a few float ulps (double arithmetic in a
+different order, transcendental functions of different libraries).  Masks, Explore and the chosen
+plan are then compared exactly: masks bit for bit on every edge whose float descriptors agree bit
+for bit, the arena record by record, and the Monte Carlo count within the tolerance derived in
+test_gpu_certify.py."""
+import numpy as np
+import pytest
+
+from oracle import cpu
+from paper_1607_06886_gb300 import inputs, pump
+
+from _util import assert_arena_equal, compare_graphs, export_arena, export_graph, gpu_graph, plan_params, ulp_diff
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    pump.load()
+    pump.use_torch_allocator()
+    yield
+
+
+def mc_tolerance(count):
+    return 3 + int(0.002 * count)
+
+
+WORKLOADS = [("three_box_1k", 0, 300), ("three_box_1k", 1, 300), ("indoor_4k", 0, 400), ("indoor_4k", 2, 600),
+             ("three_box_1k", 0, None)]
+
+
+@pytest.mark.parametrize("name,seed,ns", WORKLOADS)
+def test_graph_and_masks(name, seed, ns):
+    wl = inputs.make_workload(name, seed, ns)
+    G = gpu_graph(wl)
+    gg = export_graph(G)
+    og = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
+    E = og["n_edges"]
+    assert E > 0
+    ndiff, diff = compare_graphs(gg, og, wl.radius)
+    assert ndiff <= max(2, int(1e-4 * E)), ndiff
+    G.edge_masks()
+    gm = G.export("masks")
+    om = cpu.edge_masks(og, wl.xi, wl.boxes, wl.n_particles)
+    same = ~diff
+    np.testing.assert_array_equal(gm[same], om[same])
+    assert (gm != om).any(axis=1).sum() <= ndiff
+    assert (om != 0).any()
+
+
+@pytest.mark.parametrize("name,seed,ns", WORKLOADS)
+def test_plan_matches_oracle(name, seed, ns):
+    wl = inputs.make_workload(name, seed, ns)
+    G = gpu_graph(wl)
+    res = G.plan(plan_params(wl))
+    o = cpu.plan(wl)
+    og, ex, sel = o["graph"], o["explore"], o["select"]
+    ndiff, _ = compare_graphs(export_graph(G), og, wl.radius)
+    assert ndiff == 0, "graphs differ in float values; explore comparison needs identical inputs"
+    np.testing.assert_array_equal(G.export("masks"), o["masks"])
+    assert res["n_candidates"] == ex["n_candidates"]
+    assert res["n_kept"] == ex["n_kept"]
+    assert res["n_plans"] == ex["n_plans"]
+    assert res["n_iterations"] == ex["n_iterations"]
+    assert_arena_equal(export_arena(G), ex, wl.n_particles // 32)
+    # PlanSelection: same plan unless an MC count sits within tolerance of the threshold
+    if sel["chosen"] == res["chosen_plan"]:
+        assert abs(res["mc_collisions"] - sel["collisions"]) <= mc_tolerance(sel["collisions"])
+        assert (res["rc"] == pump.OK) == (sel["status"] == cpu.OK)
+    else:
+        thr = wl.alpha * wl.n_mc
+        assert abs(sel["collisions"] - thr) <= mc_tolerance(sel["collisions"]), (sel, res)
+    if res["chosen_plan"] >= 0:
+        path = cpu.backtrack(ex["parent"], ex["head"], res["chosen_plan"])
+        np.testing.assert_array_equal(res["path"], path)
+        assert res["cost"] == ex["cost"][res["chosen_plan"]]
+        assert res["popc"] == ex["popc"][res["chosen_plan"]]
+
+
+def test_plan_full_indoor_workload():
+    """The benchmark's workload: indoor scene, 4000 samples, N = 128, W = 10, CP target 1 %."""
+    test_plan_matches_oracle("indoor_4k", 0, None)
+
+
+def test_plan_invariants_at_full_size():
+    """Properties that hold at any size: each plan's cost is the float left-fold of its edge costs,
+    its mask the OR of its edges' masks, every popc below K_max, no group plan dominated when it
+    was expanded, and the chosen plan certified under the target."""
+    wl = inputs.make_workload("indoor_4k", 0)
+    G = gpu_graph(wl)
+    res = G.plan(plan_params(wl))
+    assert res["rc"] == pump.OK
+    col, rp, ec, masks = G.export("col"), G.export("row_ptr"), G.export("ecost"), G.export("masks")
+    a = export_arena(G)
+    kmin, kmax = cpu.cp_thresholds(wl.alpha, wl.eta, wl.n_particles)
+    P = len(a["plan_head"])
+    rng = np.random.default_rng(0)
+    for p in rng.choice(P, size=min(P, 400), replace=False):
+        q = int(p)
+        par = int(a["plan_parent"][q])
+        if par < 0:
+            continue
+        v, u = int(a["plan_head"][par]), int(a["plan_head"][q])
+        seg = col[rp[v]:rp[v + 1]]
+        e = rp[v] + int(np.searchsorted(seg, u))
+        assert col[e] == u
+        assert a["plan_cost"][q] == np.float32(a["plan_cost"][par] + ec[e])
+        np.testing.assert_array_equal(a["plan_mask"][q], a["plan_mask"][par] | masks[e])
+        assert a["plan_popc"][q] < kmax
+    assert res["cp_mc"] <= wl.alpha
+    assert res["popc"] < kmax
+
+
+def test_plan_is_repeatable():
+    wl = inputs.make_workload("indoor_4k", 3, 500)
+    G = gpu_graph(wl)
+    r1 = G.plan(plan_params(wl))
+    a1 = export_arena(G)
+    r2 = G.plan(plan_params(wl))
+    a2 = export_arena(G)
+    for k in a1:
+        np.testing.assert_array_equal(a1[k], a2[k])
+    for k in ("chosen_plan", "mc_collisions", "n_candidates", "cost"):
+        assert r1[k] == r2[k]
+
+
+def test_zero_noise_masks_equal_nominal_collisions():
+    wl = inputs.make_workload("three_box_1k", 4, 200)
+    wl.sigma = 0.0
+    G = gpu_graph(wl)
+    G.edge_masks()
+    gm = G.export("masks")
+    # every particle sits on the nominal waypoint: a word is all ones or all zeros
+    assert np.all((gm == 0) | (gm == 0xFFFFFFFF))
+    og = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, 0.0)
+    np.testing.assert_array_equal(gm, cpu.edge_masks(og, wl.xi, wl.boxes, wl.n_particles))
+
+
+def test_no_boxes_gives_zero_masks():
+    wl = inputs.make_workload("three_box_1k", 5, 150)
+    wl.boxes = np.zeros((0, 6), np.float32)
+    G = gpu_graph(wl)
+    G.edge_masks()
+    assert not G.export("masks").any()
+
+
+def test_start_inside_a_box_is_rejected():
+    wl = inputs.make_workload("three_box_1k", 6, 50)
+    wl.boxes = np.array([[0.0, 0.0, 0.0, 0.2, 0.2, 0.2]], np.float32)
+    with pytest.raises(pump.PumpError) as e:
+        gpu_graph(wl)
+    assert e.value.status == pump.ERR_INVALID_ARG
+
+
+def test_bad_build_parameters_are_rejected():
+    wl = inputs.make_workload("three_box_1k", 0, 20)
+    for N, W, r, s in ((48, 8, 1.0, 0.01), (32, 0, 1.0, 0.01), (32, 8, -1.0, 0.01), (32, 8, 1.0, -0.1),
+                       (2048, 8, 1.0, 0.01)):
+        with pytest.raises(pump.PumpError):
+            pump.Graph.build(wl.states, wl.goal_idx, wl.boxes, np.zeros((max(N, 32), W + 1, 3, 2), np.float32), r,
+                             N, W, s)
+    with pytest.raises(pump.PumpError):
+        pump.Graph.build(wl.states, [len(wl.states)], wl.boxes, wl.xi, 1.0, 32, 8, 0.01)
+
+
+def test_device_resident_inputs_match_host_inputs():
+    import torch
+    wl = inputs.make_workload("indoor_4k", 4, 300)
+    Gh = gpu_graph(wl)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    Gd = pump.Graph.build(dev(wl.states), dev(wl.goal_idx), dev(wl.boxes), dev(wl.xi), wl.radius, wl.n_particles,
+                          wl.n_waypoints, wl.sigma)
+    for k in ("col", "ecost", "nominal"):
+        np.testing.assert_array_equal(Gh.export(k), Gd.export(k))
+    rh, rd = Gh.plan(plan_params(wl)), Gd.plan(plan_params(wl))
+    assert rh["chosen_plan"] == rd["chosen_plan"] and rh["mc_collisions"] == rd["mc_collisions"]
