@@ -54,7 +54,7 @@ def lib():
             L.orc_steer.restype = C.c_int
             L.orc_model.argtypes = [C.c_double, C.c_double, P, P, P, P, P]
             L.orc_model.restype = None
-            L.orc_graph_build.argtypes = [P, C.c_int, P, C.c_int, C.c_float, C.c_int, C.c_double, C.c_int]
+            L.orc_graph_build.argtypes = [P, C.c_int, P, C.c_int, C.c_float, C.c_int, C.c_float, C.c_int]
             L.orc_graph_build.restype = P
             L.orc_graph_counts.argtypes = [P, P]
             L.orc_graph_export.argtypes = [P] * 11
@@ -69,7 +69,7 @@ def lib():
             L.orc_pair_costs.argtypes = [P, C.c_int, P]
             L.orc_philox4x64.argtypes = [P, P, P]
             L.orc_mc_normals.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, P]
-            L.orc_mc_certify.argtypes = [P, P, C.c_int, P, C.c_int, C.c_double, P, C.c_int, C.c_int64,
+            L.orc_mc_certify.argtypes = [P, P, C.c_int, P, C.c_int, C.c_float, P, C.c_int, C.c_int64,
                                          C.c_int, C.c_uint64]
             L.orc_mc_certify.restype = C.c_int64
             _lib = L
@@ -109,7 +109,7 @@ def graph_build(states, boxes, radius: float, W: int, sigma: float, exhaustive: 
     st = _c(states, np.float32)
     bx = _c(boxes, np.float32).reshape(-1, 6)
     n = st.shape[0]
-    g = lib().orc_graph_build(_p(st), n, _p(bx), bx.shape[0], C.c_float(radius), int(W), float(sigma),
+    g = lib().orc_graph_build(_p(st), n, _p(bx), bx.shape[0], C.c_float(radius), int(W), C.c_float(sigma),
                               int(bool(exhaustive)))
     if not g:
         raise RuntimeError("oracle graph build failed")
@@ -233,7 +233,7 @@ def mc_certify(states, path, edge_tau, W: int, sigma: float, boxes, n_mc: int, s
     bx = _c(boxes, np.float32).reshape(-1, 6)
     if len(et) == 0:
         et = np.zeros(1, np.float32)
-    return int(lib().orc_mc_certify(_p(st), _p(pa), len(pa), _p(et), int(W), float(sigma), _p(bx),
+    return int(lib().orc_mc_certify(_p(st), _p(pa), len(pa), _p(et), int(W), C.c_float(sigma), _p(bx),
                                     bx.shape[0], int(n_mc), int(substeps), C.c_uint64(seed)))
 
 

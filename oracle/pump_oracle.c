@@ -298,12 +298,13 @@ void orc_graph_free(orc_graph* g) {
   free(g->phi); free(g->L); free(g->nom); free(g);
 }
 
+/* sigma is the problem's float noise level (as at the library boundary); it is widened to double. */
 orc_graph* orc_graph_build(const float* states, int n, const float* boxes, int n_boxes, float r,
-                           int W, double sigma, int exhaustive) {
+                           int W, float sigma, int exhaustive) {
   if (n <= 0 || W <= 0 || !(r > 0.0f)) return NULL;
   orc_graph* g = (orc_graph*)calloc(1, sizeof(orc_graph));
   if (!g) return NULL;
-  g->n = n; g->W = W; g->sigma = sigma;
+  g->n = n; g->W = W; g->sigma = (double)sigma;
   g->valid = (uint8_t*)malloc((size_t)n);
   g->row_ptr = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
   size_t cap = 1024, E = 0;
@@ -373,7 +374,7 @@ orc_graph* orc_graph_build(const float* states, int n, const float* boxes, int n
   if (!g->h || !g->phi || !g->L || !g->nom) goto oom;
   {
     float phi_dummy[4], l_dummy[3];
-    model_f32(sigma, 1.0f, phi_dummy, l_dummy, g->linf);
+    model_f32(g->sigma, 1.0f, phi_dummy, l_dummy, g->linf);
   }
   for (int v = 0; v < n; ++v) {
     double xv[6];
@@ -384,7 +385,7 @@ orc_graph* orc_graph_build(const float* states, int n, const float* boxes, int n
       float h = g->tau[e] / (float)W;
       float lin[3];
       g->h[e] = h;
-      model_f32(sigma, h, g->phi + 4 * (size_t)e, g->L + 3 * (size_t)e, lin);
+      model_f32(g->sigma, h, g->phi + 4 * (size_t)e, g->L + 3 * (size_t)e, lin);
       double td = (double)g->tau[e];
       for (int k = 1; k <= W; ++k) {
         double tk = (double)k * (double)h;
@@ -811,8 +812,9 @@ void orc_mc_normals(uint64_t seed, uint64_t m, uint64_t s, float* xi /* 3 x 2 */
 /* connection (len - 1 values).                                                  */
 /* ========================================================================== */
 int64_t orc_mc_certify(const float* states, const int32_t* path, int len, const float* edge_tau, int W,
-                       double sigma, const float* boxes, int n_boxes, int64_t n_mc, int substeps,
+                       float sigma_f, const float* boxes, int n_boxes, int64_t n_mc, int substeps,
                        uint64_t seed) {
+  const double sigma = (double)sigma_f;
   if (len < 1 || W < 1 || substeps < 1 || n_mc < 0) return -1;
   int n_edges = len - 1;
   float lin[3], phi_d[4], l_d[3];

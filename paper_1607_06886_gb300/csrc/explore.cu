@@ -37,6 +37,8 @@
 // bounded: on expiry the kernel records PUMP_ERR_TIMEOUT and returns.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include "pump_internal.cuh"
 
 namespace pump {
@@ -369,7 +371,6 @@ __device__ bool grid_sync(ExploreCtl* ctl, int nb, long long limit) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
@@ -465,6 +466,16 @@ __global__ void k_explore_commit(ExploreCtl* c) {
 
 }  // namespace
 
+// Blocks of the persistent Explore kernel (PUMP_EXPLORE_BLOCKS overrides; default one per SM).
+int explore_blocks() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("PUMP_EXPLORE_BLOCKS");
+    v = e ? atoi(e) : 0;
+  }
+  return v;
+}
+
 int run_explore_kernels(pump_graph* g, const ExploreArgs& A, bool stepwise, cudaStream_t s) {
   const int64_t mb = (int64_t)g->n * A.kstride;
   k_fill_u32<<<256, 256, 0, s>>>(A.mbest, mb, 0x7f800000u);
@@ -480,7 +491,10 @@ int run_explore_kernels(pump_graph* g, const ExploreArgs& A, bool stepwise, cuda
   if (!stepwise && coop) {
     int per_sm = 0;
     PUMP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_explore_persistent, kT, 0));
-    int nb = sms * (per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm));
+    const int max_nb = sms * (per_sm < 1 ? 1 : per_sm);
+    int nb = explore_blocks();
+    if (nb <= 0) nb = sms;
+    if (nb > max_nb) nb = max_nb;
     ExploreArgs a = A;
     void* args[] = {&a};
     PUMP_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_explore_persistent, dim3(nb), dim3(kT), args, 0, s));

@@ -45,7 +45,7 @@ CASES = [
     (500, 20, 128, 0.01, 2.0, 0.5, 0, 3),
     (500, 20, 128, 0.01, 2.0, 0.5, pump.NO_EARLY_STOP, 4),
     (400, 16, 256, 0.01, 2.0, 0.25, 0, 5),
-    (250, 10, 1024, 0.004, 2.0, 1.0, pump.NO_EARLY_STOP, 6),
+    (250, 10, 1024, 0.02, 2.0, 1.0, pump.NO_EARLY_STOP, 6),
     (800, 30, 128, 0.05, 2.0, 0.5, pump.NO_EARLY_STOP, 7),
     (300, 12, 32, 0.5, 2.0, 0.5, pump.NO_EARLY_STOP, 8),
 ]

@@ -62,7 +62,11 @@ def test_plan_matches_oracle(name, seed, ns):
     o = cpu.plan(wl)
     og, ex, sel = o["graph"], o["explore"], o["select"]
     ndiff, _ = compare_graphs(export_graph(G), og, wl.radius)
-    assert ndiff == 0, "graphs differ in float values; explore comparison needs identical inputs"
+    assert ndiff <= max(2, int(1e-4 * og["n_edges"])), ndiff
+    # Explore's inputs are the adjacency, the float edge costs and the edge masks: identical on
+    # both sides, so Explore must agree bit for bit
+    np.testing.assert_array_equal(G.export("col"), og["col"])
+    np.testing.assert_array_equal(G.export("ecost").view(np.uint32), og["ecost"].view(np.uint32))
     np.testing.assert_array_equal(G.export("masks"), o["masks"])
     assert res["n_candidates"] == ex["n_candidates"]
     assert res["n_kept"] == ex["n_kept"]
