@@ -243,6 +243,38 @@ enum {
 };
 int pump_export(pump_graph* g, int32_t what, void* host_buf, size_t cap, size_t* needed);
 
+/* --------------------------------------------------------------------------
+ * pump_explore_noalloc: pump_explore for callers that cannot allocate device
+ * memory (code inside a captured CUDA graph or another library's
+ * stream-ordered region, runtimes whose device memory is fixed up front, or
+ * processes whose allocator belongs to a host framework that must not be
+ * re-entered).  No counterpart in the paper: it is the same Explore run as
+ * pump_explore on an imported graph, with the same results, but it calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *  Inputs (device pointers): row_ptr n+1, col E, ecost E, emask E x N/32
+ *  (as for pump_graph_from_csr, which the caller must already satisfy: no
+ *  checks are made on their contents), is_goal n bytes (nonzero = in X_goal).
+ *  Outputs (device pointers, `capacity` entries each; plan_mask capacity x
+ *  N/32 words): the plan arena as pump_export would return it, and goal_plans
+ *  (P_goal in PlanSelection order, stats->n_goal entries).  stats receives
+ *  the Explore counters.
+ *  The kernels' scratch lives in a file-scope device array of 32 MiB that
+ *  every GPU loading the library holds until the process exits.  A call
+ *  needs 48 KiB + 4 n max(K_max, 1) + 20 capacity bytes (rounded up per
+ *  buffer to 256 B); larger problems return PUMP_ERR_INVALID_ARG, as do host
+ *  pointers.  The first call on a device looks up the array's device address
+ *  (cudaGetSymbolAddress) with that device current; make that first call
+ *  before any stream capture.  All calls on a device share the array: calls
+ *  whose work overlaps on the GPU race and must be serialised by the caller.
+ *  Synchronises `stream`.  Errors: INVALID_ARG, CUDA, CAPACITY, TIMEOUT.
+ */
+int pump_explore_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col, const float* ecost,
+                         const uint32_t* emask, int32_t n_particles, int32_t start_idx, const uint8_t* is_goal,
+                         float radius, const pump_plan_params* params, int64_t capacity, int32_t* plan_head,
+                         int32_t* plan_parent, float* plan_cost, uint32_t* plan_mask, int32_t* plan_popc,
+                         int32_t* plan_created, int32_t* plan_expanded, int32_t* goal_plans,
+                         pump_plan_result* stats, void* stream);
+
 /* pump_kernel_launches: number of kernels this library has launched in the
  * process so far (host-side counter, all devices; for launch accounting).
  * No counterpart in the paper. */

@@ -26,6 +26,7 @@ UNITS = {
     "edge_mask.cu": [],
     "explore.cu": [],
     "select.cu": [],
+    "noalloc.cu": [],
 }
 
 

@@ -92,6 +92,8 @@ def load(build_if_missing: bool = False):
     L.pump_export.argtypes = [P, i32, P, C.c_size_t, C.POINTER(C.c_size_t)]
     L.pump_graph_destroy.argtypes = [P]
     L.pump_graph_destroy.restype = None
+    L.pump_explore_noalloc.argtypes = [i32, P, P, P, P, i32, i32, P, f32, C.POINTER(PlanParams), i64,
+                                       P, P, P, P, P, P, P, P, C.POINTER(PlanResult), P]
     L.pump_kernel_launches.argtypes = []
     L.pump_kernel_launches.restype = C.c_uint64
     L.pump_status_str.argtypes = [C.c_int]
@@ -149,6 +151,22 @@ def _np(a, dtype):
     if hasattr(a, "data_ptr"):
         return a
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def explore_noalloc(n: int, row_ptr, col, ecost, emask, n_particles: int, start_idx: int, is_goal, radius: float,
+                    params: PlanParams, capacity: int, out: Dict, stream: Optional[int] = None) -> Dict:
+    """pump_explore_noalloc on caller-owned device tensors (inputs and the `out` arena buffers:
+    plan_head, plan_parent, plan_cost, plan_mask, plan_popc, plan_created, plan_expanded, goal_plans)."""
+    res = PlanResult()
+    rc = load().pump_explore_noalloc(int(n), _ptr(row_ptr), _ptr(col), _ptr(ecost), _ptr(emask), int(n_particles),
+                                     int(start_idx), _ptr(is_goal), float(radius), C.byref(params), int(capacity),
+                                     _ptr(out["plan_head"]), _ptr(out["plan_parent"]), _ptr(out["plan_cost"]),
+                                     _ptr(out["plan_mask"]), _ptr(out["plan_popc"]), _ptr(out["plan_created"]),
+                                     _ptr(out["plan_expanded"]), _ptr(out["goal_plans"]), C.byref(res),
+                                     current_stream() if stream is None else stream)
+    d = res.as_dict()
+    d["rc"] = rc
+    return d
 
 
 def default_plan_params(alpha=0.01, eta=2.0, lam=0.5, n_mc=10000, mc_substeps=4, mc_seed=0,
