@@ -1,11 +1,12 @@
 #!/usr/bin/env python3
 """Benchmark: partial plans evaluated per second by PUMP's exploration on one GB300.
 
-A step is one planning query on a device-resident graph, through the C ABI (pump_plan): particle
-edge masks for the query's obstacles, Explore (Algorithm 4) and PlanSelection with Monte Carlo
-certification (Algorithm 5).  `value` = partial plans evaluated (candidates of Algorithm 4) per
-second over the timed steps, summed over ranks.  `e2e` measures the same through the public API
-from pinned host buffers: graph build from host arrays + plan + result readback, per step.
+A step is one pass of the exploration hot path on a device-resident graph, through the C ABI
+(pump_plan with PUMP_EXPLORE_ONLY): the particle edge masks for the query's obstacles and Explore
+(Algorithm 4).  `value` = partial plans evaluated (candidates of Algorithm 4) per second over the
+timed steps, summed over ranks.  `full_query` times the whole query on the resident graph (with
+PlanSelection and Monte Carlo certification, Algorithm 5), and `e2e` the whole query through the
+public API from pinned host buffers: graph build from host arrays + plan + result readback.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload indoor_4k]
 
@@ -139,25 +140,40 @@ def plan_params(pump, wl):
                                     mc_seed=wl.mc_seed)
 
 
-def time_cpu_oracle(wl, budget_s=30.0, max_steps=1):
-    """Oracle step on the host: masks + Explore + PlanSelection on the oracle's own graph (graph
-    build untimed, as for the GPU step).  Returns (seconds per step, candidates per step, steps)."""
+def oracle_step(g, wl, kmin, kmax, mask_stride=1, offset=0):
+    """One oracle step of the same hot path: edge masks + Explore on the oracle's own graph.
+    With mask_stride > 1 only every mask_stride-th edge's mask is computed and its time is scaled
+    by the sampled fraction (Explore then runs on the full masks computed once).  Returns
+    (seconds, candidates)."""
+    from oracle import cpu
+    E = g["n_edges"]
+    if mask_stride == 1:
+        t0 = time.perf_counter()
+        masks = cpu.edge_masks(g, wl.xi, wl.boxes, wl.n_particles)
+        t_mask = time.perf_counter() - t0
+    else:
+        idx = np.arange(offset % mask_stride, E, mask_stride)
+        sub = {"n_edges": len(idx), "W": g["W"], "phi": g["phi"][idx], "L": g["L"][idx], "nom": g["nom"][idx],
+               "linf": g["linf"]}
+        t0 = time.perf_counter()
+        cpu.edge_masks(sub, wl.xi, wl.boxes, wl.n_particles)
+        t_mask = (time.perf_counter() - t0) * E / max(len(idx), 1)
+        masks = g["_masks"]
+    t0 = time.perf_counter()
+    ex = cpu.explore(g["n"], g["row_ptr"], g["col"], g["ecost"], masks, 0, wl.goal_idx, kmin, kmax, wl.lam,
+                     wl.radius)
+    t_ex = time.perf_counter() - t0
+    return t_mask + t_ex, ex["n_candidates"]
+
+
+def time_cpu_oracle(wl):
+    """cpu_baseline: one full oracle step (all edge masks + Explore, single thread; graph built
+    untimed, as for the GPU step)."""
     from oracle import cpu
     g = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
     kmin, kmax = cpu.cp_thresholds(wl.alpha, wl.eta, wl.n_particles)
-    times, cands = [], 0
-    t_start = time.perf_counter()
-    for _ in range(max_steps):
-        t0 = time.perf_counter()
-        masks = cpu.edge_masks(g, wl.xi, wl.boxes, wl.n_particles)
-        ex = cpu.explore(g["n"], g["row_ptr"], g["col"], g["ecost"], masks, 0, wl.goal_idx, kmin, kmax, wl.lam,
-                         wl.radius)
-        cpu.plan_select(g, ex, wl.alpha, wl.states, wl.boxes, wl.sigma, wl.n_mc, wl.mc_substeps, wl.mc_seed)
-        times.append(time.perf_counter() - t0)
-        cands = ex["n_candidates"]
-        if time.perf_counter() - t_start > budget_s:
-            break
-    return float(np.mean(times)), cands, len(times)
+    sec, cands = oracle_step(g, wl, kmin, kmax)
+    return sec, cands, 1
 
 
 def run_reference(args):
@@ -170,36 +186,30 @@ def run_reference(args):
     from oracle import cpu
     cpu.build()
     wl = inputs.make_workload(args.workload, seed=0)
-    # bounded sample per step: the oracle graph and masks are built once (untimed); each step runs
-    # Explore and PlanSelection of the query on them
+    # bounded sample per step: the oracle graph is built once (untimed); each step times Explore on
+    # the full masks and the mask pass on a rotating 1/16 sample of the edges, scaled to all edges
     g = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
-    masks = cpu.edge_masks(g, wl.xi, wl.boxes, wl.n_particles)
+    g["_masks"] = cpu.edge_masks(g, wl.xi, wl.boxes, wl.n_particles)
     kmin, kmax = cpu.cp_thresholds(wl.alpha, wl.eta, wl.n_particles)
-
-    def step():
-        ex = cpu.explore(g["n"], g["row_ptr"], g["col"], g["ecost"], masks, 0, wl.goal_idx, kmin, kmax, wl.lam,
-                         wl.radius)
-        cpu.plan_select(g, ex, wl.alpha, wl.states, wl.boxes, wl.sigma, wl.n_mc, wl.mc_substeps, wl.mc_seed)
-        return ex["n_candidates"]
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    cands = 0
-    for _ in range(args.steps):
-        cands += step()
-    dt = time.perf_counter() - t0
-    value = cands / dt
+    stride = 16
+    for k in range(args.warmup):
+        oracle_step(g, wl, kmin, kmax, stride, k)
+    tot, cands = 0.0, 0
+    for k in range(args.steps):
+        sec, c = oracle_step(g, wl, kmin, kmax, stride, k)
+        tot += sec
+        cands += c
+    value = cands / tot
     line = {"impl": "reference", "metric": "partial plans evaluated per second", "value": value,
             "unit": "partial_plans/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1000.0 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "samples": wl.n - 2, "particles": wl.n_particles,
                        "waypoints": wl.n_waypoints, "boxes": int(wl.boxes.shape[0]), "cp_target": wl.alpha,
                        "seed": 0},
             "cpu_baseline": {"value": value, "unit": "partial_plans/s", "cores": 1, "kind": "oracle",
-                             "sample": "Explore + PlanSelection per step on the oracle's graph and masks "
-                                       "(built once, untimed), single thread"},
+                             "sample": "per step: Explore on the full masks + the mask pass over a rotating 1/16 of "
+                                       "the edges scaled to all edges; graph built once untimed; single thread"},
             "e2e": {"value": value, "unit": "partial_plans/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -229,6 +239,8 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     wl = inputs.make_workload(args.workload, seed=rank)
     prm = plan_params(pump, wl)
+    prm_step = plan_params(pump, wl)
+    prm_step.flags = pump.EXPLORE_ONLY
     todev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     G = pump.Graph.build(todev(wl.states), todev(wl.goal_idx), todev(wl.boxes), todev(wl.xi), wl.radius,
                          wl.n_particles, wl.n_waypoints, wl.sigma)
@@ -237,8 +249,8 @@ def main():
 
     # warm-up
     for _ in range(max(args.warmup, 3)):
-        res = G.plan(prm)
-        assert res["rc"] in (pump.OK, pump.ERR_INFEASIBLE), res
+        res = G.plan(prm_step)
+        assert res["rc"] == pump.OK, res
     torch.cuda.synchronize()
 
     # timed region: K plan steps, device time by CUDA events; L2 flushed between steps
@@ -252,10 +264,10 @@ def main():
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
-            res = G.plan(prm)
+            res = G.plan(prm_step)
             ev[k][1].record(stream)
             cands += res["n_candidates"]
-            for key in parts:
+            for key in ("ms_masks", "ms_explore"):
                 parts[key] += res[key]
         torch.cuda.synchronize()
         barrier(ws)
@@ -265,6 +277,20 @@ def main():
     cands_all = sum_over_ranks(cands, ws)
     value = cands_all / (ms_max / 1000.0)
     ms_per_step = ms_max / args.steps
+
+    # the whole query on the resident graph (with PlanSelection and Monte Carlo certification)
+    fq = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        full = G.plan(prm)
+        b.record(stream)
+        fq.append((a, b, full))
+    torch.cuda.synchronize()
+    fq_ms = float(np.median([a.elapsed_time(b) for a, b, _ in fq]))
+    full = fq[-1][2]
+    assert full["rc"] in (pump.OK, pump.ERR_INFEASIBLE), full
 
     # dominant kernels timed alone with CUDA events on the launching stream
     roof, kernel_detail = roofline_measure(pump, G, prm, wl, dev, flush, args.steps)
@@ -292,7 +318,7 @@ def main():
     torch.cuda.synchronize()
     e_ms = max_over_ranks(e0.elapsed_time(e1), ws)
     e_value = sum_over_ranks(e_cands, ws) / (e_ms / 1000.0)
-    d2h = 4 * int(res["path_len"]) + 128  # result record and path
+    d2h = 4 * int(r2["path_len"]) + 128  # result record and path
 
     line = {
         "metric": "partial plans evaluated per second", "value": value, "unit": "partial_plans/s",
@@ -303,8 +329,13 @@ def main():
                    "edges": int(G.counts()[1]), "partial_plans_per_step": res["n_candidates"],
                    "plans_per_step": res["n_plans"], "groups": res["n_groups"], "seed_per_rank": "rank",
                    "l2": "flushed between steps (2x L2 buffer write)", "parallelism": f"replicas{ws}"},
-        "step_ms": {k: v / args.steps for k, v in parts.items()},
-        "result": {"cost": res["cost"], "cp_hat": res["cp_hat"], "cp_mc": res["cp_mc"], "status": res["status"]},
+        "step": "edge masks + Explore (Algorithm 4), graph resident",
+        "step_ms": {k: v / args.steps for k, v in parts.items() if k != "ms_select"},
+        "full_query": {"ms": fq_ms, "value": full["n_candidates"] / (fq_ms / 1000.0), "unit": "partial_plans/s",
+                       "ms_masks": full["ms_masks"], "ms_explore": full["ms_explore"], "ms_select": full["ms_select"],
+                       "includes": "edge masks + Explore + PlanSelection with Monte Carlo certification"},
+        "result": {"cost": full["cost"], "cp_hat": full["cp_hat"], "cp_mc": full["cp_mc"], "status": full["status"],
+                   "goal_plans": full["n_goal"], "certified": full["n_certified"]},
         "clocks": clk.summary(),
         "e2e": {"value": e_value, "unit": "partial_plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e_ms / e2e_steps, "includes": "graph build from pinned host arrays + plan + readback"},
@@ -317,8 +348,8 @@ def main():
         cpu.build()
         sec, oc, nst = time_cpu_oracle(wl)
         line["cpu_baseline"] = {"value": oc / sec, "unit": "partial_plans/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{nst} full step(s) of the same query (masks + Explore + PlanSelection, "
-                                          f"graph built untimed), single thread, {sec:.1f} s per step"}
+                                "sample": f"{nst} full step of the same query (all edge masks + Explore, graph "
+                                          f"built untimed), single thread, {sec:.1f} s"}
     if rank == 0:
         print(json.dumps(line))
     G.close()

@@ -772,28 +772,26 @@ void orc_philox4x64(const uint64_t* ctr_in, const uint64_t* key_in, uint64_t* ou
   for (int q = 0; q < 4; ++q) out[q] = c[q];
 }
 
-/* Standard normal pair from two 64-bit words (Box and Muller, 1958): the top  */
-/* 24 bits of each word give u = (bits + 1/2) 2^-24 in (0, 1); then            */
-/* z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = sqrt(-2 ln u1) sin(2 pi u2),          */
-/* evaluated in double and rounded to float.                                     */
-static void box_muller(uint64_t w1, uint64_t w2, float* z0, float* z1) {
-  double u1 = ((double)(w1 >> 40) + 0.5) * (1.0 / 16777216.0);
-  double u2 = ((double)(w2 >> 40) + 0.5) * (1.0 / 16777216.0);
+/* Standard normal pair from two 24-bit integers (Box and Muller, 1958):      */
+/* u = (bits + 1/2) 2^-24 in (0, 1), z0 = sqrt(-2 ln u1) cos(2 pi u2),          */
+/* z1 = sqrt(-2 ln u1) sin(2 pi u2), evaluated in double and rounded to float.  */
+static void box_muller(uint64_t b1, uint64_t b2, float* z0, float* z1) {
+  double u1 = ((double)b1 + 0.5) * (1.0 / 16777216.0);
+  double u2 = ((double)b2 + 0.5) * (1.0 / 16777216.0);
   double rad = sqrt(-2.0 * log(u1));
   double ang = 6.283185307179586476925286766559 * u2;
   *z0 = (float)(rad * cos(ang));
   *z1 = (float)(rad * sin(ang));
 }
 
-/* Normals (xi0, xi1) of rollout m, step s, axis j: Philox4x64-10 with        */
-/* counter (m, s, j, 0) and key (seed, 0); words 0 and 1 feed Box-Muller.      */
+/* Normals (xi0, xi1) of rollout m, step s, for the three axes: one Philox4x64-10 */
+/* call with counter (m, s, 0, 0) and key (seed, 0); axis j takes word j, whose  */
+/* bits 63..40 give u1 and bits 39..16 give u2.                                   */
 void orc_mc_normals(uint64_t seed, uint64_t m, uint64_t s, float* xi /* 3 x 2 */) {
-  uint64_t key[2] = {seed, 0}, o[4];
-  for (uint64_t j = 0; j < 3; ++j) {
-    uint64_t c[4] = {m, s, j, 0};
-    orc_philox4x64(c, key, o);
-    box_muller(o[0], o[1], &xi[2 * j], &xi[2 * j + 1]);
-  }
+  uint64_t key[2] = {seed, 0}, c[4] = {m, s, 0, 0}, o[4];
+  orc_philox4x64(c, key, o);
+  for (int j = 0; j < 3; ++j)
+    box_muller(o[j] >> 40, (o[j] >> 16) & 0xFFFFFFull, &xi[2 * j], &xi[2 * j + 1]);
 }
 
 /* ========================================================================== */

@@ -23,15 +23,16 @@
 // undominated plans; empty group indices in between expand nothing and are
 // skipped, which leaves every plan, id and stamp unchanged.
 //
-// Schedule.  One iteration is five phases separated by grid barriers:
-//   P1 expand: candidates of the group (plans by id, then out-edges), CP cutoff,
-//      atomicMin into mbest; stamp e = i on group plans.
-//   P2 count survivors per block (candidate ranges are contiguous per block).
-//   P3 write survivors at arena offsets from the block counts (stable order);
-//      minimum bucket over new and older open undominated plans.
-//   P4 count plans of the next group per block, with their out-degree sums;
-//      raise the stop flag on a goal plan with popc < K_min.
-//   P5 write the group (ascending id) and its candidate offsets.
+// Schedule.  One iteration is four phases separated by grid barriers:
+//   P1 expand: candidates of the group (plans by id, then out-edges; a warp per
+//      group plan, lanes over its edges), CP cutoff, atomicMin into mbest;
+//      stamp e = i on group plans.
+//   P2 survivors per block (candidate ranges are contiguous per block) and the
+//      least group index over open undominated plans, new and older.
+//   P3 survivors written at arena ids from the block counts (stable order);
+//      next-group members counted per block, older plans and survivors apart,
+//      with out-degree sums; stop flag on a goal plan with popc < K_min.
+//   P4 the group written in ascending id with its candidate offsets.
 // The persistent kernel runs all iterations in one cooperative launch; the
 // stepwise driver launches each phase separately.  Every barrier wait is
 // bounded: on expiry the kernel records PUMP_ERR_TIMEOUT and returns.
@@ -161,11 +162,53 @@ __device__ __forceinline__ Cand cand_at(const ExploreArgs& A, int64_t c, int32_t
 }
 
 // ---------------------------------------------------------------- phases
-__device__ void phase_expand(const ExploreArgs& A, int b, int nb) {
+//
+// Shared memory of the persistent kernel: a block keeps the candidates of its chunk (and
+// bucket flags of its chunk of older plans) from P1 to P4, so each is computed once.  The
+// stepwise driver (separate launches) and chunks that do not fit recompute instead; both
+// paths produce the same values.
+constexpr int kCandCap = 1536;
+constexpr int kOldCap = 2048;
+constexpr int kMaxBlocks = 1024;
+
+struct ExploreSmem {
+  int32_t cx[kCandCap];     // candidate target node
+  int32_t cpar[kCandCap];   // parent plan
+  int32_t cedge[kCandCap];  // edge; after P3 the survivor's id
+  float ccost[kCandCap];
+  int32_t ceff[kCandCap];   // group of a kept candidate (-1 = not kept), from P2
+  int16_t cpc[kCandCap];
+  int32_t oeff[kOldCap];    // group of an open undominated older plan (-1 otherwise), from P2
+  int32_t slot0;
+};
+
+__device__ __forceinline__ int32_t deg_of(const ExploreArgs& A, int32_t x) { return A.row_ptr[x + 1] - A.row_ptr[x]; }
+
+// Largest slot s < g with goff[s] <= c.
+__device__ __forceinline__ int32_t slot_of(const ExploreArgs& A, int64_t c, int32_t g) {
+  int lo = 0, hi = g;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (ld64(A.goff + mid) <= c) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int32_t old_eff(const ExploreArgs& A, int64_t p) {
+  if (ld32(A.eexp + p) != -1) return -1;
+  const float c = ldf(A.cost + p);
+  if (dominated(A, ld32(A.head + p), ld32(A.popc + p), c)) return -1;
+  return eff_bucket(A, c, ld32(A.tcre + p));
+}
+
+// P1: candidates of the group, CP cutoff, dominance table; group plans stamped expanded.
+template <bool kC>
+__device__ void phase_expand(const ExploreArgs& A, int b, int nb, ExploreSmem* sm, int k) {
   ExploreCtl* ctl = A.ctl;
-  const int64_t C = ld64(&ctl->group_cands);
-  const int32_t g = ld32(&ctl->group_size);
-  const int32_t i = ld32(&ctl->iter);
+  const IterState* cur = &ctl->st[k & 1];
+  const int64_t C = ld64(&cur->group_cands);
+  const int32_t g = ld32(&cur->group_size);
+  const int32_t i = ld32(&cur->iter);
   if (b == 0 && threadIdx.x == 0) {
     ctl->n_plans = ld64(&ctl->n_plans) + ld32(&ctl->survivors);
     ctl->survivors = 0;
@@ -176,37 +219,122 @@ __device__ void phase_expand(const ExploreArgs& A, int b, int nb) {
   int64_t c0, c1;
   chunk(C, b, nb, &c0, &c1);
   int64_t kept = 0;
-  for (int64_t c = c0 + threadIdx.x; c < c1; c += kT) {
-    Cand q = cand_at(A, c, g);
-    if (q.pc < A.kmax) {
-      atomicMin(A.mbest + (size_t)q.x * A.kstride + q.pc, __float_as_uint(q.cost));
-      ++kept;
+  if (kC && c1 - c0 <= kCandCap) {
+    if (c0 < c1) {
+      if (threadIdx.x == 0) sm->slot0 = slot_of(A, c0, g);
+      __syncthreads();
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int32_t s = sm->slot0 + warp; s < g; s += kWarpsT) {
+        const int64_t lo_s = ld64(A.goff + s);
+        if (lo_s >= c1) break;
+        const int64_t hi_s = ld64(A.goff + s + 1);
+        const int64_t lo = max(lo_s, c0), hi = min(hi_s, c1);
+        if (lo >= hi) continue;
+        const int32_t p = ld32(A.group + s);
+        const int32_t v = ld32(A.head + p);
+        const int32_t rp = A.row_ptr[v];
+        const float pcost = ldf(A.cost + p);
+        const uint32_t* pm = A.mask + (size_t)p * A.w;
+        for (int64_t c = lo + lane; c < hi; c += 32) {
+          const int32_t e = rp + (int32_t)(c - lo_s);
+          const int32_t x = A.col[e];
+          const float cost = __fadd_rn(pcost, A.ecost[e]);
+          const uint32_t* em = A.emask + (size_t)e * A.w;
+          int pc = 0;
+          for (int j = 0; j < A.w; ++j) pc += __popc(ldu(pm + j) | em[j]);
+          const int jl = (int)(c - c0);
+          sm->cx[jl] = x;
+          sm->cpar[jl] = p;
+          sm->cedge[jl] = e;
+          sm->ccost[jl] = cost;
+          sm->cpc[jl] = (int16_t)pc;
+          if (pc < A.kmax) {
+            atomicMin(A.mbest + (size_t)x * A.kstride + pc, __float_as_uint(cost));
+            ++kept;
+          }
+        }
+      }
+    }
+  } else {
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += kT) {
+      Cand q = cand_at(A, c, g);
+      if (q.pc < A.kmax) {
+        atomicMin(A.mbest + (size_t)q.x * A.kstride + q.pc, __float_as_uint(q.cost));
+        ++kept;
+      }
     }
   }
   kept = block_sum<int64_t>(kept);
   if (threadIdx.x == 0 && kept) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->n_kept), (unsigned long long)kept);
 }
 
-__device__ void phase_count(const ExploreArgs& A, int b, int nb) {
-  const int64_t C = ld64(&A.ctl->group_cands);
-  const int32_t g = ld32(&A.ctl->group_size);
-  int64_t c0, c1;
-  chunk(C, b, nb, &c0, &c1);
-  int32_t cnt = 0;
-  for (int64_t c = c0 + threadIdx.x; c < c1; c += kT) {
-    Cand q = cand_at(A, c, g);
-    if (q.pc < A.kmax && !dominated(A, q.x, q.pc, q.cost)) ++cnt;
+// Candidate jl of the block's chunk (from shared memory or recomputed).
+template <bool kC>
+__device__ __forceinline__ Cand local_cand(const ExploreArgs& A, const ExploreSmem* sm, bool fits, int64_t c0, int jl,
+                                           int32_t g) {
+  if (kC && fits) {
+    Cand q;
+    q.x = sm->cx[jl];
+    q.parent = sm->cpar[jl];
+    q.edge = sm->cedge[jl];
+    q.cost = sm->ccost[jl];
+    q.pc = sm->cpc[jl];
+    return q;
   }
-  cnt = block_sum<int32_t>(cnt);
-  if (threadIdx.x == 0) A.bcnt[b] = cnt;
+  return cand_at(A, c0 + jl, g);
 }
 
-__device__ void phase_write(const ExploreArgs& A, int b, int nb) {
+// P2: survivors per block (kept and undominated after all of the group's candidates), and the
+// least group index among open undominated plans, new and older.
+template <bool kC>
+__device__ void phase_count(const ExploreArgs& A, int b, int nb, ExploreSmem* sm, int k) {
   ExploreCtl* ctl = A.ctl;
-  const int64_t C = ld64(&ctl->group_cands);
-  const int32_t g = ld32(&ctl->group_size);
-  const int32_t i = ld32(&ctl->iter);
-  const int32_t parity = ld32(&ctl->it_count) & 1;
+  const IterState* cur = &ctl->st[k & 1];
+  const int64_t C = ld64(&cur->group_cands);
+  const int32_t g = ld32(&cur->group_size);
+  const int32_t i = ld32(&cur->iter);
+  const int32_t parity = k & 1;
+  const int64_t base = ld64(&ctl->n_plans);
+  int64_t c0, c1;
+  chunk(C, b, nb, &c0, &c1);
+  const bool fits = c1 - c0 <= kCandCap;
+  int32_t cnt = 0, bmin = kNoBucket;
+  for (int jl = threadIdx.x; jl < (int)(c1 - c0); jl += kT) {
+    const Cand q = local_cand<kC>(A, sm, fits, c0, jl, g);
+    const bool keep = q.pc < A.kmax && !dominated(A, q.x, q.pc, q.cost);
+    const int32_t eff = keep ? eff_bucket(A, q.cost, i) : -1;
+    if (kC && fits) sm->ceff[jl] = eff;
+    if (keep) {
+      ++cnt;
+      bmin = min(bmin, eff);
+    }
+  }
+  int64_t a0, a1;
+  chunk(base, b, nb, &a0, &a1);
+  const bool ofits = a1 - a0 <= kOldCap;
+  for (int64_t p = a0 + threadIdx.x; p < a1; p += kT) {
+    const int32_t eff = old_eff(A, p);
+    if (kC && ofits) sm->oeff[p - a0] = eff;
+    if (eff >= 0) bmin = min(bmin, eff);
+  }
+  cnt = block_sum<int32_t>(cnt);
+  bmin = block_min(bmin);
+  if (threadIdx.x == 0) {
+    A.bcnt[b] = cnt;
+    if (bmin != kNoBucket) atomicMin(&ctl->next_bucket[parity], bmin);
+  }
+}
+
+// P3: survivors written at arena ids in candidate order; members of the next group counted
+// (older plans first, then this iteration's survivors) with their out-degree sums.
+template <bool kC>
+__device__ void phase_write(const ExploreArgs& A, int b, int nb, ExploreSmem* sm, int k) {
+  ExploreCtl* ctl = A.ctl;
+  const IterState* cur = &ctl->st[k & 1];
+  const int64_t C = ld64(&cur->group_cands);
+  const int32_t g = ld32(&cur->group_size);
+  const int32_t i = ld32(&cur->iter);
+  const int32_t nbk = ld32(&ctl->next_bucket[k & 1]);
   const int64_t base = ld64(&ctl->n_plans);
   int32_t before, total;
   block_prefix_of<int32_t>(A.bcnt, b, nb, &before, &total);
@@ -216,15 +344,24 @@ __device__ void phase_write(const ExploreArgs& A, int b, int nb) {
   }
   int64_t c0, c1;
   chunk(C, b, nb, &c0, &c1);
-  int32_t bmin = kNoBucket;
+  const bool fits = c1 - c0 <= kCandCap;
+  int32_t cnt_n = 0, stop = 0;
+  int64_t deg_n = 0;
   int64_t run = base + before;
-  for (int64_t t0 = c0; t0 < c1; t0 += kT) {
-    const int64_t c = t0 + threadIdx.x;
+  for (int t0 = 0; t0 < (int)(c1 - c0); t0 += kT) {
+    const int jl = t0 + threadIdx.x;
     bool keep = false;
+    int32_t eff = -1;
     Cand q;
-    if (c < c1) {
-      q = cand_at(A, c, g);
-      keep = q.pc < A.kmax && !dominated(A, q.x, q.pc, q.cost);
+    if (jl < (int)(c1 - c0)) {
+      q = local_cand<kC>(A, sm, fits, c0, jl, g);
+      if (kC && fits) {
+        eff = sm->ceff[jl];
+        keep = eff >= 0;
+      } else {
+        keep = q.pc < A.kmax && !dominated(A, q.x, q.pc, q.cost);
+        eff = keep ? eff_bucket(A, q.cost, i) : -1;
+      }
     }
     int32_t tile_total;
     const int32_t rank = block_scan<int32_t>(keep ? 1 : 0, &tile_total);
@@ -241,89 +378,82 @@ __device__ void phase_write(const ExploreArgs& A, int b, int nb) {
       const uint32_t* em = A.emask + (size_t)q.edge * A.w;
       uint32_t* om = A.mask + (size_t)id * A.w;
       for (int j = 0; j < A.w; ++j) om[j] = ldu(pm + j) | em[j];
-      bmin = min(bmin, eff_bucket(A, q.cost, i));
       if (A.is_goal[q.x]) {
-        int slot = atomicAdd(&ctl->n_goal_all, 1);
+        const int slot = atomicAdd(&ctl->n_goal_all, 1);
         A.goal_all[slot] = (int32_t)id;
+      }
+      if (kC && fits) sm->cedge[jl] = (int32_t)id;
+      if (eff == nbk) {
+        ++cnt_n;
+        deg_n += deg_of(A, q.x);
+        if (A.is_goal[q.x] && q.pc < A.kmin) stop = 1;
       }
     }
     run += tile_total;
   }
-  // older open plans
-  for (int64_t p = (int64_t)b * kT + threadIdx.x; p < base; p += (int64_t)nb * kT) {
-    if (ld32(A.eexp + p) != -1) continue;
-    const float c = ldf(A.cost + p);
-    const int32_t pc = ld32(A.popc + p);
-    if (dominated(A, ld32(A.head + p), pc, c)) continue;
-    bmin = min(bmin, eff_bucket(A, c, ld32(A.tcre + p)));
+  int32_t cnt_o = 0;
+  int64_t deg_o = 0;
+  int64_t a0, a1;
+  chunk(base, b, nb, &a0, &a1);
+  const bool ofits = a1 - a0 <= kOldCap;
+  if (nbk != kNoBucket) {
+    for (int64_t p = a0 + threadIdx.x; p < a1; p += kT) {
+      const int32_t eff = (kC && ofits) ? sm->oeff[p - a0] : old_eff(A, p);
+      if (eff != nbk) continue;
+      const int32_t x = ld32(A.head + p);
+      ++cnt_o;
+      deg_o += deg_of(A, x);
+      if (A.is_goal[x] && ld32(A.popc + p) < A.kmin) stop = 1;
+    }
   }
-  bmin = block_min(bmin);
-  if (threadIdx.x == 0 && bmin != kNoBucket) atomicMin(&ctl->next_bucket[parity], bmin);
+  cnt_n = block_sum<int32_t>(cnt_n);
+  cnt_o = block_sum<int32_t>(cnt_o);
+  deg_n = block_sum<int64_t>(deg_n);
+  deg_o = block_sum<int64_t>(deg_o);
+  stop = block_sum<int32_t>(stop);
+  if (threadIdx.x == 0) {
+    A.bcnt[kMaxBlocks + b] = cnt_o;
+    A.bcnt[2 * kMaxBlocks + b] = cnt_n;
+    A.bdeg[b] = deg_o;
+    A.bdeg[kMaxBlocks + b] = deg_n;
+    if (stop) atomicOr(&ctl->stop_next, 1);
+  }
   if (b == 0 && threadIdx.x == 0) ctl->survivors = total;
 }
 
-__device__ __forceinline__ bool selected(const ExploreArgs& A, int64_t p, int32_t nbk, int32_t* deg, bool* goal_stop) {
-  if (ld32(A.eexp + p) != -1) return false;
-  const float c = ldf(A.cost + p);
-  const int32_t pc = ld32(A.popc + p);
-  const int32_t x = ld32(A.head + p);
-  if (eff_bucket(A, c, ld32(A.tcre + p)) != nbk) return false;
-  if (dominated(A, x, pc, c)) return false;
-  *deg = A.row_ptr[x + 1] - A.row_ptr[x];
-  *goal_stop = A.is_goal[x] && pc < A.kmin;
-  return true;
-}
-
-__device__ void phase_select_count(const ExploreArgs& A, int b, int nb) {
+// P4: the next group in ascending id (older plans, then new survivors) and its candidate
+// offsets; block 0 advances the control block.
+template <bool kC>
+__device__ void phase_select_write(const ExploreArgs& A, int b, int nb, ExploreSmem* sm, int k) {
   ExploreCtl* ctl = A.ctl;
-  const int32_t parity = ld32(&ctl->it_count) & 1;
-  const int32_t nbk = ld32(&ctl->next_bucket[parity]);
-  const int64_t n_all = ld64(&ctl->n_plans) + ld32(&ctl->survivors);
-  int32_t cnt = 0;
-  int64_t dsum = 0;
-  int32_t stop = 0;
+  const IterState* cur = &ctl->st[k & 1];
+  const int64_t C = ld64(&cur->group_cands);
+  const int32_t i = ld32(&cur->iter);
+  const int32_t nbk = ld32(&ctl->next_bucket[k & 1]);
+  const int64_t base = ld64(&ctl->n_plans);
+  int32_t before_o, total_o, before_n, total_n, before_s, total_s;
+  int64_t dbefore_o, dtotal_o, dbefore_n, dtotal_n;
+  block_prefix_of<int32_t>(A.bcnt + kMaxBlocks, b, nb, &before_o, &total_o);
+  block_prefix_of<int32_t>(A.bcnt + 2 * kMaxBlocks, b, nb, &before_n, &total_n);
+  block_prefix_of<int64_t>(A.bdeg, b, nb, &dbefore_o, &dtotal_o);
+  block_prefix_of<int64_t>(A.bdeg + kMaxBlocks, b, nb, &dbefore_n, &dtotal_n);
+  block_prefix_of<int32_t>(A.bcnt, b, nb, &before_s, &total_s);
   if (nbk != kNoBucket) {
+    // older plans
     int64_t a0, a1;
-    chunk(n_all, b, nb, &a0, &a1);
-    for (int64_t p = a0 + threadIdx.x; p < a1; p += kT) {
-      int32_t d;
-      bool gs;
-      if (selected(A, p, nbk, &d, &gs)) {
-        ++cnt;
-        dsum += d;
-        stop |= gs ? 1 : 0;
-      }
-    }
-  }
-  cnt = block_sum<int32_t>(cnt);
-  dsum = block_sum<int64_t>(dsum);
-  stop = block_sum<int32_t>(stop);
-  if (threadIdx.x == 0) {
-    A.bcnt[b] = cnt;
-    A.bdeg[b] = dsum;
-    if (stop) atomicOr(&ctl->stop_next, 1);
-  }
-}
-
-__device__ void phase_select_write(const ExploreArgs& A, int b, int nb) {
-  ExploreCtl* ctl = A.ctl;
-  const int32_t parity = ld32(&ctl->it_count) & 1;
-  const int32_t nbk = ld32(&ctl->next_bucket[parity]);
-  const int64_t n_all = ld64(&ctl->n_plans) + ld32(&ctl->survivors);
-  int32_t before, total;
-  int64_t dbefore, dtotal;
-  block_prefix_of<int32_t>(A.bcnt, b, nb, &before, &total);
-  block_prefix_of<int64_t>(A.bdeg, b, nb, &dbefore, &dtotal);
-  if (nbk != kNoBucket) {
-    int64_t a0, a1;
-    chunk(n_all, b, nb, &a0, &a1);
-    int32_t run = before;
-    int64_t drun = dbefore;
+    chunk(base, b, nb, &a0, &a1);
+    const bool ofits = a1 - a0 <= kOldCap;
+    int32_t run = before_o;
+    int64_t drun = dbefore_o;
     for (int64_t t0 = a0; t0 < a1; t0 += kT) {
       const int64_t p = t0 + threadIdx.x;
+      bool sel = false;
       int32_t d = 0;
-      bool gs = false;
-      const bool sel = p < a1 && selected(A, p, nbk, &d, &gs);
+      if (p < a1) {
+        const int32_t eff = (kC && ofits) ? sm->oeff[p - a0] : old_eff(A, p);
+        sel = eff == nbk;
+        if (sel) d = deg_of(A, ld32(A.head + p));
+      }
       int32_t tt;
       int64_t dt;
       const int32_t r = block_scan<int32_t>(sel ? 1 : 0, &tt);
@@ -335,17 +465,73 @@ __device__ void phase_select_write(const ExploreArgs& A, int b, int nb) {
       run += tt;
       drun += dt;
     }
+    // this iteration's survivors: this block's are arena ids [base + before_s, + its count); the
+    // group list being written here must not be read, so they are taken from shared memory or
+    // from the arena records P3 wrote
+    int64_t c0, c1;
+    chunk(C, b, nb, &c0, &c1);
+    const bool fits = c1 - c0 <= kCandCap;
+    run = total_o + before_n;
+    drun = dtotal_o + dbefore_n;
+    if (kC && fits) {
+      for (int t0 = 0; t0 < (int)(c1 - c0); t0 += kT) {
+        const int jl = t0 + threadIdx.x;
+        bool sel = false;
+        int32_t d = 0, id = -1;
+        if (jl < (int)(c1 - c0)) {
+          const int32_t eff = sm->ceff[jl];
+          sel = eff >= 0 && eff == nbk;
+          if (sel) {
+            id = sm->cedge[jl];
+            d = deg_of(A, sm->cx[jl]);
+          }
+        }
+        int32_t tt;
+        int64_t dt;
+        const int32_t r = block_scan<int32_t>(sel ? 1 : 0, &tt);
+        const int64_t dr = block_scan<int64_t>(sel ? (int64_t)d : 0, &dt);
+        if (sel) {
+          A.group[run + r] = id;
+          A.goff[run + r] = drun + dr;
+        }
+        run += tt;
+        drun += dt;
+      }
+    } else {
+      const int32_t mine = ld32(A.bcnt + b);
+      const int64_t id0 = base + before_s;
+      for (int t0 = 0; t0 < mine; t0 += kT) {
+        const int k = t0 + threadIdx.x;
+        bool sel = false;
+        int32_t d = 0;
+        if (k < mine) {
+          sel = eff_bucket(A, ldf(A.cost + id0 + k), i) == nbk;
+          if (sel) d = deg_of(A, ld32(A.head + id0 + k));
+        }
+        int32_t tt;
+        int64_t dt;
+        const int32_t r = block_scan<int32_t>(sel ? 1 : 0, &tt);
+        const int64_t dr = block_scan<int64_t>(sel ? (int64_t)d : 0, &dt);
+        if (sel) {
+          A.group[run + r] = (int32_t)(id0 + k);
+          A.goff[run + r] = drun + dr;
+        }
+        run += tt;
+        drun += dt;
+      }
+    }
   }
   if (b == 0 && threadIdx.x == 0) {
-    const int32_t it = ld32(&ctl->iter);
-    ctl->group_size = total;
-    ctl->group_cands = dtotal;
-    A.goff[total] = dtotal;
-    ctl->iter = nbk != kNoBucket ? nbk : it + 1;
-    ctl->stop = A.early_stop ? ld32(&ctl->stop_next) : 0;
+    IterState* nxt = &ctl->st[(k + 1) & 1];
+    const int32_t gsize = nbk != kNoBucket ? total_o + total_n : 0;
+    const int64_t gc = nbk != kNoBucket ? dtotal_o + dtotal_n : 0;
+    nxt->group_size = gsize;
+    nxt->group_cands = gc;
+    A.goff[gsize] = gc;
+    nxt->iter = nbk != kNoBucket ? nbk : i + 1;
+    nxt->stop = A.early_stop ? ld32(&ctl->stop_next) : 0;
     ctl->stop_next = 0;
-    ctl->next_bucket[parity ^ 1] = kNoBucket;
-    ctl->it_count = ld32(&ctl->it_count) + 1;
+    ctl->next_bucket[(k + 1) & 1] = kNoBucket;
   }
 }
 
@@ -380,39 +566,41 @@ __device__ bool grid_sync(ExploreCtl* ctl, int nb, long long limit) {
 }
 
 __global__ void __launch_bounds__(kT) k_explore_persistent(ExploreArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ExploreSmem* sm = reinterpret_cast<ExploreSmem*>(smem_raw);
   const int b = blockIdx.x, nb = gridDim.x;
   ExploreCtl* ctl = A.ctl;
-  for (;;) {
-    const int32_t g = ld32(&ctl->group_size);
+  int k = 0;
+  for (;; ++k) {
+    const IterState* cur = &ctl->st[k & 1];
+    const int32_t g = ld32(&cur->group_size);
+    const int32_t stop = ld32(&cur->stop);
+    const int32_t it = ld32(&cur->iter);
     const int32_t st = ld32(&ctl->status);
-    const int32_t stop = ld32(&ctl->stop);
-    const int32_t it = ld32(&ctl->iter);
     if (st || stop || g == 0) break;
     if (it >= A.max_iter) {
       if (b == 0 && threadIdx.x == 0) atomicExch(&ctl->status, (int)PUMP_ERR_TIMEOUT);
       break;
     }
-    phase_expand(A, b, nb);
+    phase_expand<true>(A, b, nb, sm, k);
     if (!grid_sync(ctl, nb, A.spin_limit)) return;
-    phase_count(A, b, nb);
+    phase_count<true>(A, b, nb, sm, k);
     if (!grid_sync(ctl, nb, A.spin_limit)) return;
-    phase_write(A, b, nb);
+    phase_write<true>(A, b, nb, sm, k);
     if (!grid_sync(ctl, nb, A.spin_limit)) return;
     if (ld32(&ctl->status)) break;
-    phase_select_count(A, b, nb);
-    if (!grid_sync(ctl, nb, A.spin_limit)) return;
-    phase_select_write(A, b, nb);
+    phase_select_write<true>(A, b, nb, sm, k);
     if (!grid_sync(ctl, nb, A.spin_limit)) return;
   }
+  if (b == 0 && threadIdx.x == 0) ctl->k_exit = k;
 }
 
-__global__ void __launch_bounds__(kT) k_phase(ExploreArgs A, int which) {
+__global__ void __launch_bounds__(kT) k_phase(ExploreArgs A, int which, int k) {
   switch (which) {
-    case 1: phase_expand(A, blockIdx.x, gridDim.x); break;
-    case 2: phase_count(A, blockIdx.x, gridDim.x); break;
-    case 3: phase_write(A, blockIdx.x, gridDim.x); break;
-    case 4: phase_select_count(A, blockIdx.x, gridDim.x); break;
-    case 5: phase_select_write(A, blockIdx.x, gridDim.x); break;
+    case 1: phase_expand<false>(A, blockIdx.x, gridDim.x, nullptr, k); break;
+    case 2: phase_count<false>(A, blockIdx.x, gridDim.x, nullptr, k); break;
+    case 3: phase_write<false>(A, blockIdx.x, gridDim.x, nullptr, k); break;
+    case 4: phase_select_write<false>(A, blockIdx.x, gridDim.x, nullptr, k); break;
   }
 }
 
@@ -438,19 +626,24 @@ __global__ void k_explore_init(ExploreArgs A, int32_t start) {
   c->n_plans = 1;
   c->n_candidates = 0;
   c->n_kept = 0;
-  c->group_cands = d0;
-  c->group_size = 1;
-  c->iter = 0;
-  c->it_count = 0;
+  c->st[0].group_cands = d0;
+  c->st[0].group_size = 1;
+  c->st[0].iter = 0;
+  c->st[0].stop = (A.early_stop && A.is_goal[start] && 0 < A.kmin) ? 1 : 0;
+  c->st[1].group_cands = 0;
+  c->st[1].group_size = 0;
+  c->st[1].iter = 0;
+  c->st[1].stop = 0;
   c->next_bucket[0] = kNoBucket;
   c->next_bucket[1] = kNoBucket;
-  c->stop = (A.early_stop && A.is_goal[start] && 0 < A.kmin) ? 1 : 0;
   c->stop_next = 0;
   c->status = 0;
   c->n_groups = 0;
   c->survivors = 0;
   c->n_goal_all = 0;
   c->n_goal = 0;
+  c->k_exit = 0;
+  c->iter = 0;
   c->bar_count = 0;
   c->bar_gen = 0;
   if (A.is_goal[start]) {
@@ -459,9 +652,13 @@ __global__ void k_explore_init(ExploreArgs A, int32_t start) {
   }
 }
 
-__global__ void k_explore_commit(ExploreCtl* c) {
+// End of a run: commit the last survivors and record the final group index.  k < 0 takes the
+// iteration count the persistent kernel stored.
+__global__ void k_explore_commit(ExploreCtl* c, int k) {
+  if (k < 0) k = c->k_exit;
   c->n_plans += c->survivors;
   c->survivors = 0;
+  c->iter = c->st[k & 1].iter;
 }
 
 }  // namespace
@@ -489,35 +686,40 @@ int run_explore_kernels(pump_graph* g, const ExploreArgs& A, bool stepwise, cuda
   PUMP_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   const int sms = num_sms();
   if (!stepwise && coop) {
+    const size_t smem = sizeof(ExploreSmem);
+    PUMP_CUDA_TRY(cudaFuncSetAttribute(k_explore_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    PUMP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_explore_persistent, kT, 0));
+    PUMP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_explore_persistent, kT, smem));
     const int max_nb = sms * (per_sm < 1 ? 1 : per_sm);
     int nb = explore_blocks();
     if (nb <= 0) nb = sms;
     if (nb > max_nb) nb = max_nb;
+    if (nb > kMaxBlocks) nb = kMaxBlocks;
     ExploreArgs a = A;
     void* args[] = {&a};
-    PUMP_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_explore_persistent, dim3(nb), dim3(kT), args, 0, s));
+    PUMP_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_explore_persistent, dim3(nb), dim3(kT), args, smem, s));
     note_launch();
-    k_explore_commit<<<1, 1, 0, s>>>(A.ctl);
+    k_explore_commit<<<1, 1, 0, s>>>(A.ctl, -1);
     note_launch();
     PUMP_CUDA_TRY(cudaGetLastError());
     return PUMP_OK;
   }
   // stepwise: phases as separate launches, host reads the control block
-  const int nb = sms;
+  const int nb = sms < kMaxBlocks ? sms : kMaxBlocks;
   ExploreCtl h;
-  for (;;) {
+  int k = 0;
+  for (;; ++k) {
     PUMP_CUDA_TRY(cudaMemcpyAsync(&h, A.ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
     PUMP_CUDA_TRY(cudaStreamSynchronize(s));
-    if (h.status || h.stop || h.group_size == 0) break;
-    if (h.iter >= A.max_iter) {
+    const IterState& cur = h.st[k & 1];
+    if (h.status || cur.stop || cur.group_size == 0) break;
+    if (cur.iter >= A.max_iter) {
       int st = PUMP_ERR_TIMEOUT;
       PUMP_CUDA_TRY(cudaMemcpyAsync(&A.ctl->status, &st, sizeof(int), cudaMemcpyHostToDevice, s));
       break;
     }
-    for (int ph = 1; ph <= 5; ++ph) {
-      k_phase<<<nb, kT, 0, s>>>(A, ph);
+    for (int ph = 1; ph <= 4; ++ph) {
+      k_phase<<<nb, kT, 0, s>>>(A, ph, k);
       note_launch();
       if (ph == 3) {
         // a full arena stops the run before the group is formed
@@ -529,7 +731,7 @@ int run_explore_kernels(pump_graph* g, const ExploreArgs& A, bool stepwise, cuda
     PUMP_CUDA_TRY(cudaGetLastError());
     if (h.status) break;
   }
-  k_explore_commit<<<1, 1, 0, s>>>(A.ctl);
+  k_explore_commit<<<1, 1, 0, s>>>(A.ctl, k);
   note_launch();
   PUMP_CUDA_TRY(cudaGetLastError());
   return PUMP_OK;

@@ -130,7 +130,21 @@ static int32_t popc_bound(double a, int N) {
   return (int32_t)std::min<double>(k, (double)N + 1.0);
 }
 
-int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* st, cudaStream_t s) {
+void fill_explore_stats(pump_graph* g, const ExploreCtl& h, pump_plan_result* st) {
+  g->explored = true;
+  g->last_plans = h.n_plans;
+  g->last_goal = h.status ? 0 : h.n_goal;
+  st->n_candidates = h.n_candidates;
+  st->n_kept = h.n_kept;
+  st->n_plans = h.n_plans;
+  st->n_iterations = h.iter;
+  st->n_groups = h.n_groups;
+  st->n_goal = g->last_goal;
+}
+
+// Enqueue Explore; with `collect` read its control block back and fill `st`.
+int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* st, cudaStream_t s,
+                bool collect) {
   const double alpha = (double)p->alpha, eta = (double)p->eta;
   const int32_t kmax = popc_bound((eta * alpha) * (double)g->N, g->N);
   const int32_t kmin = popc_bound((alpha / eta) * (double)g->N, g->N);
@@ -172,23 +186,13 @@ int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_pla
   if (rc) return rc;
   rc = run_goal_finalize(g, A, s);
   if (rc) return rc;
+  g->explored = false;
+  if (!collect) return PUMP_OK;
   ExploreCtl h;
   PUMP_CUDA_TRY(cudaMemcpyAsync(&h, X.ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
   PUMP_CUDA_TRY(cudaStreamSynchronize(s));
-  g->explored = true;
-  g->last_plans = h.n_plans;
-  g->last_goal = h.n_goal;
-  st->n_candidates = h.n_candidates;
-  st->n_kept = h.n_kept;
-  st->n_plans = h.n_plans;
-  st->n_iterations = h.iter;
-  st->n_groups = h.n_groups;
-  st->n_goal = h.n_goal;
-  if (h.status) {
-    g->last_goal = 0;
-    return h.status;
-  }
-  return PUMP_OK;
+  fill_explore_stats(g, h, st);
+  return h.status ? h.status : PUMP_OK;
 }
 
 static bool is_device_ptr(const void* p) {
@@ -421,7 +425,7 @@ int pump_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_pl
   if (!(r > 0.f) || !std::isfinite(r)) return PUMP_ERR_INVALID_ARG;
   std::memset(stats, 0, sizeof(*stats));
   stats->chosen_plan = -1;
-  int rc = run_explore(g, p, r, stats, (cudaStream_t)stream);
+  int rc = run_explore(g, p, r, stats, (cudaStream_t)stream, true);
   stats->status = rc;
   return rc;
 }
@@ -440,11 +444,14 @@ int pump_plan(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t p
   rc = compute_edge_masks(g, s);
   if (rc) return rc;
   PUMP_CUDA_TRY(cudaEventRecord(g->ev[1], s));
-  rc = run_explore(g, p, g->radius, &r, s);
+  const bool explore_only = (p->flags & PUMP_EXPLORE_ONLY) != 0;
+  rc = run_explore(g, p, g->radius, &r, s, explore_only);
   PUMP_CUDA_TRY(cudaEventRecord(g->ev[2], s));
   if (rc) return rc;
-  if (!(p->flags & PUMP_EXPLORE_ONLY)) {
-    rc = run_select(g, p, path, path_cap, &r, s);
+  if (!explore_only) {
+    ExploreCtl h;
+    rc = run_select(g, p, path, path_cap, &r, &h, s);
+    fill_explore_stats(g, h, &r);
     if (rc) return rc;
   } else {
     r.status = PUMP_OK;

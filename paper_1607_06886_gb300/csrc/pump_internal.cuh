@@ -32,26 +32,34 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Per-iteration state of Explore, double-buffered by iteration parity: iteration k
+// reads slot k & 1 and its last phase writes slot (k + 1) & 1, so no block reads a
+// field another block of the same phase is changing.
+struct IterState {
+  int64_t group_cands;  // candidates of the group
+  int32_t group_size;   // |G|
+  int32_t iter;         // group index i
+  int32_t stop;         // the group holds a goal plan with popc < K_min
+  int32_t pad;
+};
+
 // Control block of one Explore run (device resident).
 struct ExploreCtl {
+  IterState st[2];
   int64_t n_plans;        // committed arena size
   int64_t n_candidates;   // partial plans evaluated so far
   int64_t n_kept;         // candidates under the CP cutoff
-  int64_t group_cands;    // candidates of the current group
-  int32_t group_size;     // |G|
-  int32_t iter;           // group index i of the current group
-  int32_t it_count;       // expansions so far (parity selects next_bucket slot)
-  int32_t next_bucket[2]; // minimum bucket of open, undominated plans
-  int32_t stop;           // goal plan with popc < K_min in G
+  int32_t next_bucket[2]; // least group index among open undominated plans, by parity
   int32_t stop_next;
   int32_t status;         // pump_status of the run (CAPACITY, TIMEOUT)
   int32_t n_groups;       // non-empty groups expanded
-  int32_t survivors;      // survivors of the last expansion (committed at next P1)
+  int32_t survivors;      // survivors of the last expansion (committed at the next P1)
   int32_t n_goal_all;     // arena plans at goal nodes (unfiltered)
   int32_t n_goal;         // |P_goal|
+  int32_t k_exit;         // iteration count when the loop ended
+  int32_t iter;           // final group index (set when the run ends)
   uint32_t bar_count;     // grid barrier arrivals
   uint32_t bar_gen;       // grid barrier generation
-  int32_t pad;
 };
 
 struct ExploreArgs {
@@ -177,9 +185,10 @@ void* graph_realloc(pump_graph* g, void* old, size_t bytes, cudaStream_t s);
 int build_graph_device(pump_graph* g, cudaStream_t s);
 int compute_edge_masks(pump_graph* g, cudaStream_t s);
 int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* stats,
-                cudaStream_t s);
+                cudaStream_t s, bool collect);
+void fill_explore_stats(pump_graph* g, const ExploreCtl& h, pump_plan_result* st);
 int run_select(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t path_cap,
-               pump_plan_result* out, cudaStream_t s);
+               pump_plan_result* out, ExploreCtl* ctl_host, cudaStream_t s);
 int run_certify_path(pump_graph* g, const int32_t* path_host, int32_t path_len, int32_t n_mc,
                      int32_t substeps, uint64_t seed, int64_t* n_collide, cudaStream_t s);
 int ensure_explore_bufs(pump_graph* g, int64_t cap, int32_t kmax, cudaStream_t s);
