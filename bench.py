@@ -97,9 +97,8 @@ class ClockSampler:
 
 def dist_setup():
     import torch
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1607_06886_gb300 import dist as pd
+    ws, rank, local = pd.world()
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -110,29 +109,18 @@ def dist_setup():
 
 
 def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_1607_06886_gb300 import dist as pd
+    pd.barrier()
 
 
 def max_over_ranks(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1607_06886_gb300 import dist as pd
+    return pd.reduce_max(x, device="cuda")
 
 
 def sum_over_ranks(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    from paper_1607_06886_gb300 import dist as pd
+    return pd.reduce_sum(x, device="cuda")
 
 
 def plan_params(pump, wl):
@@ -237,7 +225,8 @@ def main():
     pump.load()
     pump.use_torch_allocator()
     dev = torch.device("cuda", torch.cuda.current_device())
-    wl = inputs.make_workload(args.workload, seed=rank)
+    from paper_1607_06886_gb300 import dist as pd
+    wl = inputs.make_workload(args.workload, seed=pd.query_seed(rank))
     prm = plan_params(pump, wl)
     prm_step = plan_params(pump, wl)
     prm_step.flags = pump.EXPLORE_ONLY

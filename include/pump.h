@@ -260,7 +260,7 @@ int pump_export(pump_graph* g, int32_t what, void* host_buf, size_t cap, size_t*
  *  the Explore counters.
  *  The kernels' scratch lives in a file-scope device array of 32 MiB that
  *  every GPU loading the library holds until the process exits.  A call
- *  needs 48 KiB + 4 n max(K_max, 1) + 20 capacity bytes (rounded up per
+ *  needs 48 KiB + 4 n max(K_max, 1) + 36 capacity bytes (rounded up per
  *  buffer to 256 B); larger problems return PUMP_ERR_INVALID_ARG, as do host
  *  pointers.  The first call on a device looks up the array's device address
  *  (cudaGetSymbolAddress) with that device current; make that first call

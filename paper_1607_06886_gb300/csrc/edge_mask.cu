@@ -1,14 +1,16 @@
 // Edge particle collision masks (Section III-B, with a direct particle-in-box
 // test in place of the half-space test).
 //
-// One warp handles one (edge, 32-particle word): lane l is particle
-// 32*word + l.  The common normals xi_t[k][axis][i] and the boxes are staged
-// in shared memory once per block; the grid is persistent over the
-// (edge, word) items.  Pass 1 runs the particle recurrence and reduces the
-// warp's exact position bounding box; boxes that miss it cannot hold any of
-// the warp's positions and are culled.  Pass 2 re-runs the (deterministic)
-// recurrence only when some box survives and tests the survivors; the mask
-// word is the warp ballot of the per-particle OR over waypoints and boxes.
+// The particle deviations of an edge depend on its step h and the common
+// normals, not on the obstacles.  Graph build therefore records, per edge, a
+// box holding every particle position (nominal waypoints widened by the
+// largest |d0| of any particle).  Per query, a warp takes one edge: lanes test
+// the obstacle boxes against that box, and an edge with no box left gets zero
+// mask words without running its particles.  Otherwise lane l runs particle
+// 32*word + l through the recurrence once per word and tests the left boxes;
+// the mask word is the warp ballot of the per-particle OR over waypoints and
+// boxes.  The normals xi_t[k][axis][i] and the boxes sit in shared memory; the
+// grid is persistent over the edges.
 #include <cuda_runtime.h>
 
 #include "pump_internal.cuh"
@@ -33,10 +35,72 @@ __device__ __forceinline__ void dev_step(const float* P, const float* L, float2 
   d1 = e1;
 }
 
+// Graph-build pass (obstacle independent): per edge the largest |d0| over all particles,
+// waypoints and axes, as float bits (atomicMax over the edge's words).
+template <bool kSmemXi>
+__global__ void __launch_bounds__(kWarps * 32) k_edge_bound(const float2* __restrict__ xi_g, int N, int W,
+                                                            const float* __restrict__ phi,
+                                                            const float* __restrict__ Lg,
+                                                            const float* __restrict__ linf_g, int E, int w,
+                                                            unsigned int* __restrict__ dbound) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* xi_s = reinterpret_cast<float2*>(smem);
+  const int xi_n = (W + 1) * 3 * N;
+  if (kSmemXi)
+    for (int k = threadIdx.x; k < xi_n; k += blockDim.x) xi_s[k] = xi_g[k];
+  __syncthreads();
+  const float2* xi = kSmemXi ? xi_s : xi_g;
+  const float linf[3] = {linf_g[0], linf_g[1], linf_g[2]};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long items = (long long)E * w;
+  for (long long it = (long long)blockIdx.x * kWarps + warp; it < items; it += (long long)gridDim.x * kWarps) {
+    const int e = (int)(it / w), word = (int)(it % w);
+    const int i = word * 32 + lane;
+    const float P[4] = {phi[4 * (size_t)e], phi[4 * (size_t)e + 1], phi[4 * (size_t)e + 2], phi[4 * (size_t)e + 3]};
+    const float L[3] = {Lg[3 * (size_t)e], Lg[3 * (size_t)e + 1], Lg[3 * (size_t)e + 2]};
+    float m = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float d0, d1;
+      dev_init(linf, xi[(size_t)a * N + i], d0, d1);
+      for (int k = 1; k <= W; ++k) {
+        dev_step(P, L, xi[((size_t)k * 3 + a) * N + i], d0, d1);
+        m = fmaxf(m, fabsf(d0));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) atomicMax(dbound + e, __float_as_uint(m));
+  }
+}
+
+// Per edge: box holding every particle position, [min nominal - M, max nominal + M] per axis,
+// rounded to nearest (float rounding is monotone, so fl(nominal + d0) stays inside).
+__global__ void k_edge_ibox(const float* __restrict__ nom, const unsigned int* __restrict__ dbound, int E, int W,
+                            float* __restrict__ ibox) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const float M = __uint_as_float(dbound[e]);
+  const float* nm = nom + (size_t)e * W * 3;
+  for (int a = 0; a < 3; ++a) {
+    float lo = nm[a], hi = nm[a];
+    for (int k = 1; k < W; ++k) {
+      lo = fminf(lo, nm[k * 3 + a]);
+      hi = fmaxf(hi, nm[k * 3 + a]);
+    }
+    ibox[6 * (size_t)e + a] = __fsub_rn(lo, M);
+    ibox[6 * (size_t)e + 3 + a] = __fadd_rn(hi, M);
+  }
+}
+
+// Query pass: a warp per edge.  Boxes that miss the edge's position box cannot hold any of its
+// particle positions; an edge with none left gets zero mask words without running the
+// particles.  Otherwise each 32-particle word runs the recurrence once and tests the left boxes.
 template <bool kSmemXi>
 __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restrict__ xi_g, int N, int W,
                                                            const float* __restrict__ phi, const float* __restrict__ Lg,
                                                            const float* __restrict__ nom, const float* __restrict__ linf_g,
+                                                           const float* __restrict__ ibox_g,
                                                            const float* __restrict__ boxes_g, int nb, int E, int w,
                                                            uint32_t* __restrict__ mask) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -52,60 +116,38 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restr
   const float linf[3] = {linf_g[0], linf_g[1], linf_g[2]};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int* my_cand = cand + warp * kCandCap;
-  const long long items = (long long)E * w;
-  for (long long it = (long long)blockIdx.x * kWarps + warp; it < items; it += (long long)gridDim.x * kWarps) {
-    const int e = (int)(it / w), word = (int)(it % w);
-    const int i = word * 32 + lane;
-    const float P[4] = {phi[4 * (size_t)e], phi[4 * (size_t)e + 1], phi[4 * (size_t)e + 2], phi[4 * (size_t)e + 3]};
-    const float L[3] = {Lg[3 * (size_t)e], Lg[3 * (size_t)e + 1], Lg[3 * (size_t)e + 2]};
-    const float* nm = nom + (size_t)e * W * 3;
-    // pass 1: bounding box of the warp's positions
-    float d0[3], d1[3], lo[3], hi[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      dev_init(linf, xi[(size_t)a * N + i], d0[a], d1[a]);
-      lo[a] = __int_as_float(0x7f800000);
-      hi[a] = -lo[a];
-    }
-    for (int k = 1; k <= W; ++k) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        dev_step(P, L, xi[((size_t)k * 3 + a) * N + i], d0[a], d1[a]);
-        float p = __fadd_rn(nm[(k - 1) * 3 + a], d0[a]);
-        lo[a] = fminf(lo[a], p);
-        hi[a] = fmaxf(hi[a], p);
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
-        hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
-      }
-    }
-    // cull: boxes overlapping the bounding box (closed intervals)
+  for (long long e = (long long)blockIdx.x * kWarps + warp; e < E; e += (long long)gridDim.x * kWarps) {
+    const float* ib = ibox_g + 6 * e;
+    const float lo0 = ib[0], lo1 = ib[1], lo2 = ib[2], hi0 = ib[3], hi1 = ib[4], hi2 = ib[5];
     int n_cand = 0;
     for (int base = 0; base < nb; base += 32) {
-      int o = base + lane;
+      const int o = base + lane;
       bool ov = false;
       if (o < nb) {
         const float* b = boxes + 6 * o;
-        ov = b[0] <= hi[0] && lo[0] <= b[3] && b[1] <= hi[1] && lo[1] <= b[4] && b[2] <= hi[2] && lo[2] <= b[5];
+        ov = b[0] <= hi0 && lo0 <= b[3] && b[1] <= hi1 && lo1 <= b[4] && b[2] <= hi2 && lo2 <= b[5];
       }
-      unsigned bal = __ballot_sync(0xffffffffu, ov);
-      int pos = n_cand + __popc(bal & ((1u << lane) - 1u));
+      const unsigned bal = __ballot_sync(0xffffffffu, ov);
+      const int pos = n_cand + __popc(bal & ((1u << lane) - 1u));
       if (ov && pos < kCandCap) my_cand[pos] = o;
       n_cand += __popc(bal);
     }
     __syncwarp();
-    uint32_t word_bits = 0;
-    if (n_cand > 0) {
-      const bool all = n_cand > kCandCap;
-      const int nc = all ? nb : n_cand;
-      bool hit = false;
+    if (n_cand == 0) {
+      for (int word = lane; word < w; word += 32) mask[(size_t)e * w + word] = 0u;
+      continue;
+    }
+    const bool all = n_cand > kCandCap;
+    const int nc = all ? nb : n_cand;
+    const float P[4] = {phi[4 * e], phi[4 * e + 1], phi[4 * e + 2], phi[4 * e + 3]};
+    const float L[3] = {Lg[3 * e], Lg[3 * e + 1], Lg[3 * e + 2]};
+    const float* nm = nom + (size_t)e * W * 3;
+    for (int word = 0; word < w; ++word) {
+      const int i = word * 32 + lane;
+      float d0[3], d1[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) dev_init(linf, xi[(size_t)a * N + i], d0[a], d1[a]);
+      bool hit = false;
       for (int k = 1; k <= W; ++k) {
         float p[3];
 #pragma unroll
@@ -118,9 +160,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restr
           hit = in_box_dev(p[0], p[1], p[2], boxes + 6 * o);
         }
       }
-      word_bits = __ballot_sync(0xffffffffu, hit);
+      const unsigned bits = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) mask[(size_t)e * w + word] = bits;
     }
-    if (lane == 0) mask[(size_t)e * w + word] = word_bits;
     __syncwarp();
   }
 }
@@ -134,6 +176,54 @@ size_t edge_mask_smem(int N, int W, int nb, bool xi_in_smem) {
   return b;
 }
 
+template <typename K>
+static int occupancy_grid(K kernel, size_t smem, long long items_per_block, long long items, int* grid) {
+  PUMP_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  PUMP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, smem));
+  if (per_sm < 1) per_sm = 1;
+  long long want = (items + items_per_block - 1) / items_per_block;
+  long long gsz = (long long)num_sms() * per_sm;
+  if (gsz > want) gsz = want;
+  if (gsz < 1) gsz = 1;
+  *grid = (int)gsz;
+  return PUMP_OK;
+}
+
+// Obstacle-independent per-edge position boxes (graph build).
+int compute_edge_bounds(pump_graph* g, cudaStream_t s) {
+  if (g->E == 0) return PUMP_OK;
+  unsigned int* dbound = (unsigned int*)dev_alloc(sizeof(unsigned int) * (size_t)g->E, s);
+  if (!dbound) return PUMP_ERR_OOM;
+  PUMP_CUDA_TRY(cudaMemsetAsync(dbound, 0, sizeof(unsigned int) * (size_t)g->E, s));
+  const size_t smem_xi = sizeof(float2) * (size_t)(g->W + 1) * 3 * g->N;
+  const bool use_smem = smem_xi <= 160 * 1024;
+  const long long items = (long long)g->E * g->n_words;
+  int grid = 1;
+  if (use_smem) {
+    {
+      const int rco = occupancy_grid(k_edge_bound<true>, smem_xi, kWarps, items, &grid);
+      if (rco) return rco;
+    }
+    k_edge_bound<true><<<grid, kWarps * 32, smem_xi, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->linf_dev, g->E,
+                                                          g->n_words, dbound);
+    note_launch();
+  } else {
+    {
+      const int rco = occupancy_grid(k_edge_bound<false>, 16, kWarps, items, &grid);
+      if (rco) return rco;
+    }
+    k_edge_bound<false><<<grid, kWarps * 32, 16, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->linf_dev, g->E,
+                                                      g->n_words, dbound);
+    note_launch();
+  }
+  k_edge_ibox<<<(g->E + 255) / 256, 256, 0, s>>>(g->nom, dbound, g->E, g->W, g->ibox);
+  note_launch();
+  PUMP_CUDA_TRY(cudaGetLastError());
+  dev_free(dbound, s);
+  return PUMP_OK;
+}
+
 int compute_edge_masks(pump_graph* g, cudaStream_t s) {
   if (g->E == 0) {
     g->masks_ready = true;
@@ -142,26 +232,22 @@ int compute_edge_masks(pump_graph* g, cudaStream_t s) {
   const size_t smem_xi = edge_mask_smem(g->N, g->W, g->n_boxes, true);
   const bool use_smem = smem_xi <= 160 * 1024;
   const size_t smem = use_smem ? smem_xi : edge_mask_smem(g->N, g->W, g->n_boxes, false);
-  int blocks_per_sm = 0;
+  int grid = 1;
   if (use_smem) {
-    PUMP_CUDA_TRY(cudaFuncSetAttribute(k_edge_mask<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PUMP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_edge_mask<true>, kWarps * 32, smem));
-  } else {
-    PUMP_CUDA_TRY(cudaFuncSetAttribute(k_edge_mask<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PUMP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_edge_mask<false>, kWarps * 32, smem));
-  }
-  if (blocks_per_sm < 1) blocks_per_sm = 1;
-  long long items = (long long)g->E * g->n_words;
-  long long want = (items + kWarps - 1) / kWarps;
-  long long grid = (long long)num_sms() * blocks_per_sm;
-  if (grid > want) grid = want;
-  if (use_smem) {
-    k_edge_mask<true><<<(int)grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
-                                                           g->boxes, g->n_boxes, g->E, g->n_words, g->emask);
+    {
+      const int rco = occupancy_grid(k_edge_mask<true>, smem, kWarps, g->E, &grid);
+      if (rco) return rco;
+    }
+    k_edge_mask<true><<<grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
+                                                      g->ibox, g->boxes, g->n_boxes, g->E, g->n_words, g->emask);
     note_launch();
   } else {
-    k_edge_mask<false><<<(int)grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
-                                                            g->boxes, g->n_boxes, g->E, g->n_words, g->emask);
+    {
+      const int rco = occupancy_grid(k_edge_mask<false>, smem, kWarps, g->E, &grid);
+      if (rco) return rco;
+    }
+    k_edge_mask<false><<<grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
+                                                       g->ibox, g->boxes, g->n_boxes, g->E, g->n_words, g->emask);
     note_launch();
   }
   PUMP_CUDA_TRY(cudaGetLastError());

@@ -108,6 +108,34 @@ __device__ int32_t block_min(int32_t v) {
   return r;
 }
 
+// Sums of K int64 values over the block in one pass (one shared-memory round).
+template <int K>
+__device__ void block_sums(int64_t (&v)[K]) {
+  __shared__ int64_t wsum[K][kWarpsT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0) wsum[q][warp] = v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    int64_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kWarpsT; ++w) t += wsum[q][w];
+    v[q] = t;
+  }
+  __syncthreads();
+}
+
+// Packed (count, degree sum): count in bits 40.., sum in bits 0..39.
+constexpr int kPackShift = 40;
+__device__ __forceinline__ int64_t pack_cd(int64_t c, int64_t d) { return (c << kPackShift) | d; }
+__device__ __forceinline__ int32_t pack_c(int64_t x) { return (int32_t)(x >> kPackShift); }
+__device__ __forceinline__ int64_t pack_d(int64_t x) { return x & ((int64_t(1) << kPackShift) - 1); }
+
 // Sum over blocks b' < b of cnt[b'] (and over all blocks), read by the whole block.
 template <typename T>
 __device__ void block_prefix_of(const T* cnt, int b, int nb, T* before, T* all) {
@@ -146,13 +174,13 @@ __device__ __forceinline__ Cand cand_at(const ExploreArgs& A, int64_t c, int32_t
     if (ld64(A.goff + mid) <= c) lo = mid; else hi = mid;
   }
   Cand q;
-  const int32_t p = ld32(A.group + lo);
-  const int32_t v = ld32(A.head + p);
-  const int32_t e = A.row_ptr[v] + (int32_t)(c - ld64(A.goff + lo));
+  const int4 gi = __ldcg(A.ginfo + lo);
+  const int32_t p = gi.x;
+  const int32_t e = gi.z + (int32_t)(c - ld64(A.goff + lo));
   q.x = A.col[e];
   q.parent = p;
   q.edge = e;
-  q.cost = __fadd_rn(ldf(A.cost + p), A.ecost[e]);
+  q.cost = __fadd_rn(__int_as_float(gi.w), A.ecost[e]);
   int pc = 0;
   const uint32_t* pm = A.mask + (size_t)p * A.w;
   const uint32_t* em = A.emask + (size_t)e * A.w;
@@ -230,10 +258,10 @@ __device__ void phase_expand(const ExploreArgs& A, int b, int nb, ExploreSmem* s
         const int64_t hi_s = ld64(A.goff + s + 1);
         const int64_t lo = max(lo_s, c0), hi = min(hi_s, c1);
         if (lo >= hi) continue;
-        const int32_t p = ld32(A.group + s);
-        const int32_t v = ld32(A.head + p);
-        const int32_t rp = A.row_ptr[v];
-        const float pcost = ldf(A.cost + p);
+        const int4 gi = __ldcg(A.ginfo + s);
+        const int32_t p = gi.x;
+        const int32_t rp = gi.z;
+        const float pcost = __int_as_float(gi.w);
         const uint32_t* pm = A.mask + (size_t)p * A.w;
         for (int64_t c = lo + lane; c < hi; c += 32) {
           const int32_t e = rp + (int32_t)(c - lo_s);
@@ -317,12 +345,12 @@ __device__ void phase_count(const ExploreArgs& A, int b, int nb, ExploreSmem* sm
     if (kC && ofits) sm->oeff[p - a0] = eff;
     if (eff >= 0) bmin = min(bmin, eff);
   }
+  // count by a block sum; group index by warp minima and one atomic per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+  if ((threadIdx.x & 31) == 0 && bmin != kNoBucket) atomicMin(&ctl->next_bucket[parity], bmin);
   cnt = block_sum<int32_t>(cnt);
-  bmin = block_min(bmin);
-  if (threadIdx.x == 0) {
-    A.bcnt[b] = cnt;
-    if (bmin != kNoBucket) atomicMin(&ctl->next_bucket[parity], bmin);
-  }
+  if (threadIdx.x == 0) A.bcnt[b] = cnt;
 }
 
 // P3: survivors written at arena ids in candidate order; members of the next group counted
@@ -406,17 +434,12 @@ __device__ void phase_write(const ExploreArgs& A, int b, int nb, ExploreSmem* sm
       if (A.is_goal[x] && ld32(A.popc + p) < A.kmin) stop = 1;
     }
   }
-  cnt_n = block_sum<int32_t>(cnt_n);
-  cnt_o = block_sum<int32_t>(cnt_o);
-  deg_n = block_sum<int64_t>(deg_n);
-  deg_o = block_sum<int64_t>(deg_o);
-  stop = block_sum<int32_t>(stop);
+  int64_t red[3] = {pack_cd(cnt_o, deg_o), pack_cd(cnt_n, deg_n), stop};
+  block_sums<3>(red);
   if (threadIdx.x == 0) {
-    A.bcnt[kMaxBlocks + b] = cnt_o;
-    A.bcnt[2 * kMaxBlocks + b] = cnt_n;
-    A.bdeg[b] = deg_o;
-    A.bdeg[kMaxBlocks + b] = deg_n;
-    if (stop) atomicOr(&ctl->stop_next, 1);
+    A.bdeg[b] = red[0];
+    A.bdeg[kMaxBlocks + b] = red[1];
+    if (red[2]) atomicOr(&ctl->stop_next, 1);
   }
   if (b == 0 && threadIdx.x == 0) ctl->survivors = total;
 }
@@ -431,13 +454,25 @@ __device__ void phase_select_write(const ExploreArgs& A, int b, int nb, ExploreS
   const int32_t i = ld32(&cur->iter);
   const int32_t nbk = ld32(&ctl->next_bucket[k & 1]);
   const int64_t base = ld64(&ctl->n_plans);
-  int32_t before_o, total_o, before_n, total_n, before_s, total_s;
-  int64_t dbefore_o, dtotal_o, dbefore_n, dtotal_n;
-  block_prefix_of<int32_t>(A.bcnt + kMaxBlocks, b, nb, &before_o, &total_o);
-  block_prefix_of<int32_t>(A.bcnt + 2 * kMaxBlocks, b, nb, &before_n, &total_n);
-  block_prefix_of<int64_t>(A.bdeg, b, nb, &dbefore_o, &dtotal_o);
-  block_prefix_of<int64_t>(A.bdeg + kMaxBlocks, b, nb, &dbefore_n, &dtotal_n);
-  block_prefix_of<int32_t>(A.bcnt, b, nb, &before_s, &total_s);
+  // prefixes over blocks of: old-plan (count, degree), survivor (count, degree), survivor count
+  int64_t red[6] = {0, 0, 0, 0, 0, 0};
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+    const int64_t po = ld64(A.bdeg + q), pn = ld64(A.bdeg + kMaxBlocks + q), sc = ld32(A.bcnt + q);
+    red[1] += po;
+    red[3] += pn;
+    red[5] += sc;
+    if (q < b) {
+      red[0] += po;
+      red[2] += pn;
+      red[4] += sc;
+    }
+  }
+  block_sums<6>(red);
+  const int32_t before_o = pack_c(red[0]), total_o = pack_c(red[1]);
+  const int64_t dbefore_o = pack_d(red[0]), dtotal_o = pack_d(red[1]);
+  const int32_t before_n = pack_c(red[2]), total_n = pack_c(red[3]);
+  const int64_t dbefore_n = pack_d(red[2]), dtotal_n = pack_d(red[3]);
+  const int32_t before_s = (int32_t)red[4];
   if (nbk != kNoBucket) {
     // older plans
     int64_t a0, a1;
@@ -449,21 +484,26 @@ __device__ void phase_select_write(const ExploreArgs& A, int b, int nb, ExploreS
       const int64_t p = t0 + threadIdx.x;
       bool sel = false;
       int32_t d = 0;
+      int4 gi = make_int4(0, 0, 0, 0);
       if (p < a1) {
         const int32_t eff = (kC && ofits) ? sm->oeff[p - a0] : old_eff(A, p);
         sel = eff == nbk;
-        if (sel) d = deg_of(A, ld32(A.head + p));
+        if (sel) {
+          const int32_t x = ld32(A.head + p);
+          const int32_t r0 = A.row_ptr[x];
+          d = A.row_ptr[x + 1] - r0;
+          gi = make_int4((int32_t)p, x, r0, __float_as_int(ldf(A.cost + p)));
+        }
       }
-      int32_t tt;
-      int64_t dt;
-      const int32_t r = block_scan<int32_t>(sel ? 1 : 0, &tt);
-      const int64_t dr = block_scan<int64_t>(sel ? (int64_t)d : 0, &dt);
+      int64_t tpk;
+      const int64_t rpk = block_scan<int64_t>(sel ? pack_cd(1, d) : 0, &tpk);
       if (sel) {
-        A.group[run + r] = (int32_t)p;
-        A.goff[run + r] = drun + dr;
+        A.group[run + pack_c(rpk)] = (int32_t)p;
+        A.ginfo[run + pack_c(rpk)] = gi;
+        A.goff[run + pack_c(rpk)] = drun + pack_d(rpk);
       }
-      run += tt;
-      drun += dt;
+      run += pack_c(tpk);
+      drun += pack_d(tpk);
     }
     // this iteration's survivors: this block's are arena ids [base + before_s, + its count); the
     // group list being written here must not be read, so they are taken from shared memory or
@@ -478,24 +518,27 @@ __device__ void phase_select_write(const ExploreArgs& A, int b, int nb, ExploreS
         const int jl = t0 + threadIdx.x;
         bool sel = false;
         int32_t d = 0, id = -1;
+        int4 gi = make_int4(0, 0, 0, 0);
         if (jl < (int)(c1 - c0)) {
           const int32_t eff = sm->ceff[jl];
           sel = eff >= 0 && eff == nbk;
           if (sel) {
             id = sm->cedge[jl];
-            d = deg_of(A, sm->cx[jl]);
+            const int32_t x = sm->cx[jl];
+            const int32_t r0 = A.row_ptr[x];
+            d = A.row_ptr[x + 1] - r0;
+            gi = make_int4(id, x, r0, __float_as_int(sm->ccost[jl]));
           }
         }
-        int32_t tt;
-        int64_t dt;
-        const int32_t r = block_scan<int32_t>(sel ? 1 : 0, &tt);
-        const int64_t dr = block_scan<int64_t>(sel ? (int64_t)d : 0, &dt);
+        int64_t tpk;
+        const int64_t rpk = block_scan<int64_t>(sel ? pack_cd(1, d) : 0, &tpk);
         if (sel) {
-          A.group[run + r] = id;
-          A.goff[run + r] = drun + dr;
+          A.group[run + pack_c(rpk)] = id;
+          A.ginfo[run + pack_c(rpk)] = gi;
+          A.goff[run + pack_c(rpk)] = drun + pack_d(rpk);
         }
-        run += tt;
-        drun += dt;
+        run += pack_c(tpk);
+        drun += pack_d(tpk);
       }
     } else {
       const int32_t mine = ld32(A.bcnt + b);
@@ -504,20 +547,26 @@ __device__ void phase_select_write(const ExploreArgs& A, int b, int nb, ExploreS
         const int k = t0 + threadIdx.x;
         bool sel = false;
         int32_t d = 0;
+        int4 gi = make_int4(0, 0, 0, 0);
         if (k < mine) {
-          sel = eff_bucket(A, ldf(A.cost + id0 + k), i) == nbk;
-          if (sel) d = deg_of(A, ld32(A.head + id0 + k));
+          const float c = ldf(A.cost + id0 + k);
+          sel = eff_bucket(A, c, i) == nbk;
+          if (sel) {
+            const int32_t x = ld32(A.head + id0 + k);
+            const int32_t r0 = A.row_ptr[x];
+            d = A.row_ptr[x + 1] - r0;
+            gi = make_int4((int32_t)(id0 + k), x, r0, __float_as_int(c));
+          }
         }
-        int32_t tt;
-        int64_t dt;
-        const int32_t r = block_scan<int32_t>(sel ? 1 : 0, &tt);
-        const int64_t dr = block_scan<int64_t>(sel ? (int64_t)d : 0, &dt);
+        int64_t tpk;
+        const int64_t rpk = block_scan<int64_t>(sel ? pack_cd(1, d) : 0, &tpk);
         if (sel) {
-          A.group[run + r] = (int32_t)(id0 + k);
-          A.goff[run + r] = drun + dr;
+          A.group[run + pack_c(rpk)] = (int32_t)(id0 + k);
+          A.ginfo[run + pack_c(rpk)] = gi;
+          A.goff[run + pack_c(rpk)] = drun + pack_d(rpk);
         }
-        run += tt;
-        drun += dt;
+        run += pack_c(tpk);
+        drun += pack_d(tpk);
       }
     }
   }
@@ -620,6 +669,7 @@ __global__ void k_explore_init(ExploreArgs A, int32_t start) {
   for (int j = 0; j < A.w; ++j) A.mask[j] = 0u;
   A.mbest[(size_t)start * A.kstride] = 0u;  // float 0
   A.group[0] = 0;
+  A.ginfo[0] = make_int4(0, start, A.row_ptr[start], __float_as_int(0.f));
   const int64_t d0 = A.row_ptr[start + 1] - A.row_ptr[start];
   A.goff[0] = 0;
   A.goff[1] = d0;

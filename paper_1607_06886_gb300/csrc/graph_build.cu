@@ -78,11 +78,12 @@ __global__ void k_prefilter(const float* __restrict__ states, const uint8_t* __r
 // t_m = tau (m / 4W), m = 1..4W, positions rounded to float, closed boxes.
 __device__ inline bool connection_hits(const double* xv, const double* xu, double tau, int W, const float* boxes,
                                        int nb) {
+  const Cubic cx = cubic_dev(xv, xu, tau, 0), cy = cubic_dev(xv, xu, tau, 1), cz = cubic_dev(xv, xu, tau, 2);
   for (int m = 1; m <= 4 * W; ++m) {
     double t = tau * ((double)m / (double)(4 * W));
-    float p0 = (float)nominal_dev(xv, xu, tau, 0, t);
-    float p1 = (float)nominal_dev(xv, xu, tau, 1, t);
-    float p2 = (float)nominal_dev(xv, xu, tau, 2, t);
+    float p0 = (float)cubic_at(cx, t);
+    float p1 = (float)cubic_at(cy, t);
+    float p2 = (float)cubic_at(cz, t);
     for (int o = 0; o < nb; ++o)
       if (in_box_dev(p0, p1, p2, boxes + 6 * o)) return true;
   }
@@ -90,7 +91,8 @@ __device__ inline bool connection_hits(const double* xv, const double* xu, doubl
 }
 
 __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __restrict__ list, long long n_list,
-                              int n, float r, int W, const float* __restrict__ boxes_g, int nb, uint32_t* keep) {
+                              int n, float r, int W, const float* __restrict__ boxes_g, int nb, uint32_t* keep,
+                              double* __restrict__ res_tau, float* __restrict__ res_cost) {
   extern __shared__ float boxes[];
   for (int k = threadIdx.x; k < 6 * nb; k += blockDim.x) boxes[k] = boxes_g[k];
   __syncthreads();
@@ -109,6 +111,8 @@ __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __re
     if (!(__double2float_rn(J) < r)) continue;
     double td = (double)__double2float_rn(tau);
     if (connection_hits(xv, xu, td, W, boxes, nb)) continue;
+    res_tau[q] = tau;
+    res_cost[q] = __double2float_rn(J);
     atomicOr(keep + (size_t)vu.x * nw + (vu.y >> 5), 1u << (vu.y & 31));
   }
 }
@@ -149,49 +153,80 @@ __global__ void k_scan_single(const int32_t* __restrict__ in, int n, int32_t* ou
   if (t == T - 1) out[n] = (int32_t)part[T - 1];
 }
 
-// One warp per source row: edges in ascending target order, values recomputed.
-__global__ void k_fill(const float* __restrict__ states, const uint32_t* __restrict__ keep, int n, int W, float sigma,
-                       const int32_t* __restrict__ row_ptr, int32_t* col, float* ecost, float* tau_o, float* h_o,
-                       float* phi_o, float* L_o, float* nom_o) {
+// Edge index of the first kept pair of each keep word: row start + kept pairs before it in the
+// row (a warp per row, 32 words at a time).
+__global__ void k_word_prefix(const uint32_t* __restrict__ keep, int n, const int32_t* __restrict__ row_ptr,
+                              int32_t* __restrict__ wpre) {
   const int nw = (n + 31) / 32;
-  int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  int lane = threadIdx.x & 31;
+  const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (v >= n) return;
-  double xv[6];
+  int run = row_ptr[v];
+  for (int k0 = 0; k0 < nw; k0 += 32) {
+    const int k = k0 + lane;
+    const int c = k < nw ? __popc(keep[(size_t)v * nw + k]) : 0;
+    int x = c;
 #pragma unroll
-  for (int j = 0; j < 6; ++j) xv[j] = (double)states[6 * v + j];
-  int pos = row_ptr[v];
-  for (int k = 0; k < nw; ++k) {
-    uint32_t word = keep[(size_t)v * nw + k];
-    if (!word) continue;
-    if ((word >> lane) & 1u) {
-      int u = k * 32 + lane;
-      int e = pos + __popc(word & ((1u << lane) - 1u));
-      double xu[6];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) xu[j] = (double)states[6 * u + j];
-      double tau = 0.0, J = 0.0;
-      steer_dev(xv, xu, &tau, &J);
-      float t32 = __double2float_rn(tau);
-      float h = __fdiv_rn(t32, (float)W);
-      col[e] = u;
-      ecost[e] = __double2float_rn(J);
-      tau_o[e] = t32;
-      h_o[e] = h;
-      double Phi[4], L[3], Linf[3];
-      model_dev((double)sigma, (double)h, Phi, L, Linf);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) phi_o[4 * (size_t)e + q] = __double2float_rn(Phi[q]);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) L_o[3 * (size_t)e + q] = __double2float_rn(L[q]);
-      double td = (double)t32;
-      for (int kk = 1; kk <= W; ++kk) {
-        double t = (double)kk * (double)h;
-        for (int j = 0; j < 3; ++j)
-          nom_o[((size_t)e * W + (kk - 1)) * 3 + j] = __double2float_rn(nominal_dev(xv, xu, td, j, t));
-      }
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    pos += __popc(word);
+    if (k < nw) wpre[(size_t)v * nw + k] = run + x - c;
+    run += __shfl_sync(0xffffffffu, x, 31);
+  }
+}
+
+// Kept pairs to their CSR slots (targets ascending within a row).
+__global__ void k_scatter_edges(const int2* __restrict__ list, long long n_list, int n,
+                                const uint32_t* __restrict__ keep, const int32_t* __restrict__ wpre,
+                                const double* __restrict__ res_tau, const float* __restrict__ res_cost,
+                                int32_t* __restrict__ src, int32_t* __restrict__ col, double* __restrict__ etau,
+                                float* __restrict__ ecost) {
+  const int nw = (n + 31) / 32;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n_list;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int2 vu = list[q];
+    const size_t wi = (size_t)vu.x * nw + (vu.y >> 5);
+    const uint32_t word = keep[wi];
+    const uint32_t bit = 1u << (vu.y & 31);
+    if (!(word & bit)) continue;
+    const int e = wpre[wi] + __popc(word & (bit - 1u));
+    src[e] = vu.x;
+    col[e] = vu.y;
+    etau[e] = res_tau[q];
+    ecost[e] = res_cost[q];
+  }
+}
+
+// Per edge: float duration, waypoint step h = tau/W, Phi(h), L(h), nominal waypoints at t = k h.
+__global__ void k_fill_edges(const float* __restrict__ states, int E, int W, float sigma,
+                             const int32_t* __restrict__ src, const int32_t* __restrict__ col,
+                             const double* __restrict__ etau, float* tau_o, float* h_o, float* phi_o, float* L_o,
+                             float* nom_o) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int v = src[e], u = col[e];
+  double xv[6], xu[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    xv[j] = (double)states[6 * v + j];
+    xu[j] = (double)states[6 * u + j];
+  }
+  const float t32 = __double2float_rn(etau[e]);
+  const float h = __fdiv_rn(t32, (float)W);
+  tau_o[e] = t32;
+  h_o[e] = h;
+  double Phi[4], L[3], Linf[3];
+  model_dev((double)sigma, (double)h, Phi, L, Linf);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) phi_o[4 * (size_t)e + q] = __double2float_rn(Phi[q]);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) L_o[3 * (size_t)e + q] = __double2float_rn(L[q]);
+  const double td = (double)t32;
+  for (int j = 0; j < 3; ++j) {
+    const Cubic c = cubic_dev(xv, xu, td, j);
+    for (int kk = 1; kk <= W; ++kk)
+      nom_o[((size_t)e * W + (kk - 1)) * 3 + j] = __double2float_rn(cubic_at(c, (double)kk * (double)h));
   }
 }
 
@@ -250,13 +285,16 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   }
   uint32_t* keep = (uint32_t*)dev_alloc(sizeof(uint32_t) * (size_t)n * nw, s);
   int32_t* deg = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)(n + 1), s);
-  if (!keep || !deg) return PUMP_ERR_OOM;
+  int32_t* wpre = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)n * nw, s);
+  double* res_tau = (double*)dev_alloc(sizeof(double) * (n_list ? n_list : 1), s);
+  float* res_cost = (float*)dev_alloc(sizeof(float) * (n_list ? n_list : 1), s);
+  if (!keep || !deg || !wpre || !res_tau || !res_cost) return PUMP_ERR_OOM;
   PUMP_CUDA_TRY(cudaMemsetAsync(keep, 0, sizeof(uint32_t) * (size_t)n * nw, s));
+  long long list_blocks = ((long long)n_list + kBlock - 1) / kBlock;
+  const int glist = (int)(list_blocks < (long long)sms * 16 ? (list_blocks > 0 ? list_blocks : 1) : (long long)sms * 16);
   if (n_list) {
-    long long blocks = ((long long)n_list + kBlock - 1) / kBlock;
-    int gsteer = (int)(blocks < (long long)sms * 16 ? blocks : (long long)sms * 16);
-    k_steer_pairs<<<gsteer, kBlock, sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1), s>>>(
-        g->states, list, (long long)n_list, n, g->radius, g->W, g->boxes, g->n_boxes, keep);
+    k_steer_pairs<<<glist, kBlock, sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1), s>>>(
+        g->states, list, (long long)n_list, n, g->radius, g->W, g->boxes, g->n_boxes, keep, res_tau, res_cost);
     note_launch();
   }
   k_row_counts<<<(n + 7) / 8, kBlock, 0, s>>>(keep, n, deg);
@@ -278,11 +316,27 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   g->L = (float*)graph_alloc(g, sizeof(float) * 3 * Es, s);
   g->nom = (float*)graph_alloc(g, sizeof(float) * 3 * (size_t)g->W * Es, s);
   g->emask = (uint32_t*)graph_alloc(g, sizeof(uint32_t) * (size_t)g->n_words * Es, s);
-  if (!g->col || !g->ecost || !g->tau || !g->h || !g->phi || !g->L || !g->nom || !g->emask) return PUMP_ERR_OOM;
+  g->ibox = (float*)graph_alloc(g, sizeof(float) * 6 * Es, s);
+  if (!g->col || !g->ecost || !g->tau || !g->h || !g->phi || !g->L || !g->nom || !g->emask || !g->ibox)
+    return PUMP_ERR_OOM;
   if (E > 0) {
-    k_fill<<<(n + 7) / 8, kBlock, 0, s>>>(g->states, keep, n, g->W, g->sigma, g->row_ptr, g->col, g->ecost, g->tau,
-                                          g->h, g->phi, g->L, g->nom);
+    int32_t* src = (int32_t*)dev_alloc(sizeof(int32_t) * Es, s);
+    double* etau = (double*)dev_alloc(sizeof(double) * Es, s);
+    if (!src || !etau) return PUMP_ERR_OOM;
+    k_word_prefix<<<(n + 7) / 8, kBlock, 0, s>>>(keep, n, g->row_ptr, wpre);
     note_launch();
+    k_scatter_edges<<<glist, kBlock, 0, s>>>(list, (long long)n_list, n, keep, wpre, res_tau, res_cost, src, g->col,
+                                             etau, g->ecost);
+    note_launch();
+    k_fill_edges<<<(E + 127) / 128, 128, 0, s>>>(g->states, E, g->W, g->sigma, src, g->col, etau, g->tau, g->h,
+                                                 g->phi, g->L, g->nom);
+    note_launch();
+    dev_free(src, s);
+    dev_free(etau, s);
+  }
+  {
+    const int rcb = compute_edge_bounds(g, s);
+    if (rcb) return rcb;
   }
   // valid node count (for export)
   PUMP_CUDA_TRY(cudaMemsetAsync(deg, 0, sizeof(int32_t), s));
@@ -295,6 +349,9 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   if (list) dev_free(list, s);
   dev_free(keep, s);
   dev_free(deg, s);
+  dev_free(wpre, s);
+  dev_free(res_tau, s);
+  dev_free(res_cost, s);
   return PUMP_OK;
 }
 

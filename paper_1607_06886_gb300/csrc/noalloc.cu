@@ -76,7 +76,8 @@ int scratch_bytes(int32_t n, int32_t n_particles, const pump_plan_params* p, int
   const int32_t kstride = kmax > 1 ? kmax : 1;
   *bytes = align256(sizeof(pump::ExploreCtl)) + align256(sizeof(int32_t) * kBlockSlots) +
            align256(sizeof(int64_t) * kBlockSlots) + align256(sizeof(uint32_t) * (size_t)n * kstride) +
-           3 * align256(sizeof(int32_t) * (size_t)capacity) + align256(sizeof(int64_t) * ((size_t)capacity + 1));
+           3 * align256(sizeof(int32_t) * (size_t)capacity) + align256(sizeof(int4) * (size_t)capacity) +
+           align256(sizeof(int64_t) * ((size_t)capacity + 1));
   return PUMP_OK;
 }
 
@@ -126,6 +127,7 @@ extern "C" int pump_explore_noalloc(int32_t n, const int32_t* row_ptr, const int
   A.bdeg = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * kBlockSlots));
   A.mbest = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * (size_t)n * kstride));
   A.group = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)capacity));
+  A.ginfo = reinterpret_cast<int4*>(carve(sizeof(int4) * (size_t)capacity));
   A.pedge = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)capacity));
   A.goal_all = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)capacity));
   A.goff = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * ((size_t)capacity + 1)));

@@ -95,11 +95,12 @@ int ensure_explore_bufs(pump_graph* g, int64_t cap, int32_t kmax, cudaStream_t s
     X.popc = (int32_t*)graph_realloc(g, X.popc, sizeof(int32_t) * cap, s);
     X.mask = (uint32_t*)graph_realloc(g, X.mask, sizeof(uint32_t) * cap * w, s);
     X.group = (int32_t*)graph_realloc(g, X.group, sizeof(int32_t) * cap, s);
+    X.ginfo = (int4*)graph_realloc(g, X.ginfo, sizeof(int4) * cap, s);
     X.goff = (int64_t*)graph_realloc(g, X.goff, sizeof(int64_t) * (cap + 1), s);
     X.goal_all = (int32_t*)graph_realloc(g, X.goal_all, sizeof(int32_t) * cap, s);
     X.goal_sorted = (int32_t*)graph_realloc(g, X.goal_sorted, sizeof(int32_t) * cap, s);
     if (!X.head || !X.parent || !X.pedge || !X.tcre || !X.eexp || !X.cost || !X.popc || !X.mask || !X.group ||
-        !X.goff || !X.goal_all || !X.goal_sorted) {
+        !X.ginfo || !X.goff || !X.goal_all || !X.goal_sorted) {
       X.cap = 0;
       return PUMP_ERR_OOM;
     }
@@ -174,6 +175,7 @@ int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_pla
   A.cap = p->max_plans;
   A.mbest = X.mbest;
   A.group = X.group;
+  A.ginfo = X.ginfo;
   A.goff = X.goff;
   A.bcnt = X.bcnt;
   A.bdeg = X.bdeg;

@@ -90,6 +90,7 @@ struct ExploreArgs {
   // search state
   uint32_t* mbest;  // n x kmax float bits: least cost of any plan inserted at (node, popc)
   int32_t* group;
+  int4* ginfo;      // per group slot: plan id, head node, row start, cost bits
   int64_t* goff;    // group_size + 1 candidate offsets
   int32_t* bcnt;    // per-block survivor / selection counts
   int64_t* bdeg;    // per-block degree sums
@@ -112,6 +113,7 @@ struct ExploreBufs {
   uint32_t* mask = nullptr;
   uint32_t* mbest = nullptr;
   int32_t* group = nullptr;
+  int4* ginfo = nullptr;
   int64_t* goff = nullptr;
   int32_t* bcnt = nullptr;
   int64_t* bdeg = nullptr;
@@ -161,6 +163,7 @@ struct pump_graph {
   float* L = nullptr;        // E x 3
   float* nom = nullptr;      // E x W x 3
   uint32_t* emask = nullptr; // E x n_words
+  float* ibox = nullptr;     // E x 6: box holding every particle position of the edge
   std::vector<pump::DevBuf> bufs;
   pump::ExploreBufs ex;
   // last explore
@@ -184,6 +187,7 @@ void* graph_realloc(pump_graph* g, void* old, size_t bytes, cudaStream_t s);
 
 int build_graph_device(pump_graph* g, cudaStream_t s);
 int compute_edge_masks(pump_graph* g, cudaStream_t s);
+int compute_edge_bounds(pump_graph* g, cudaStream_t s);
 int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* stats,
                 cudaStream_t s, bool collect);
 void fill_explore_stats(pump_graph* g, const ExploreCtl& h, pump_plan_result* st);
@@ -312,13 +316,23 @@ __device__ inline bool steer_dev(const double* x0, const double* x1, double* tau
   return true;
 }
 
-// Position of the optimal connection of duration tau at time t, one axis.
+// Position of the optimal connection of duration tau at time t, one axis: the cubic
+// p0 + v0 t + c2 t^2 + c3 t^3 matching both end states.
+struct Cubic {
+  double p0, v0, c2, c3;
+};
+__device__ inline Cubic cubic_dev(const double* x0, const double* x1, double tau, int j) {
+  Cubic q;
+  q.p0 = x0[j];
+  q.v0 = x0[3 + j];
+  double dp = x1[j] - q.p0 - q.v0 * tau, dv = x1[3 + j] - q.v0;
+  q.c2 = (3.0 * dp - dv * tau) / (tau * tau);
+  q.c3 = (dv * tau - 2.0 * dp) / (tau * tau * tau);
+  return q;
+}
+__device__ inline double cubic_at(const Cubic& q, double t) { return q.p0 + q.v0 * t + q.c2 * t * t + q.c3 * t * t * t; }
 __device__ inline double nominal_dev(const double* x0, const double* x1, double tau, int j, double t) {
-  double p0 = x0[j], v0 = x0[3 + j];
-  double dp = x1[j] - p0 - v0 * tau, dv = x1[3 + j] - v0;
-  double c2 = (3.0 * dp - dv * tau) / (tau * tau);
-  double c3 = (dv * tau - 2.0 * dp) / (tau * tau * tau);
-  return p0 + v0 * t + c2 * t * t + c3 * t * t * t;
+  return cubic_at(cubic_dev(x0, x1, tau, j), t);
 }
 
 __device__ inline bool in_box_dev(float x, float y, float z, const float* b) {
