@@ -74,6 +74,77 @@ __global__ void k_prefilter(const float* __restrict__ states, const uint8_t* __r
   }
 }
 
+// Float estimate of Cost(v,u), used only to skip pairs far above the radius.  Same monotone
+// pieces as steer_dev; J is evaluated as tau + |dv|^2/tau + 12|dp - vbar tau|^2/tau^3, a sum
+// of non-negative terms (no cancellation), at the float roots.  J(tau) >= Cost for every tau,
+// and a minimum float cannot resolve is no deeper than float rounding, so a pair whose
+// estimate exceeds r by 0.1 % is not a neighbour.  Returns false when undecided.
+__device__ inline float st32_f(float a, float b, float c, float t) { return ((t * t - 4.f * a) * t + 24.f * b) * t - 36.f * c; }
+__device__ inline float st32_fp(float a, float b, float t) { return (4.f * t * t - 8.f * a) * t + 24.f * b; }
+__device__ inline float st32_root(float a, float b, float c, int which, float lo, float hi, bool inc) {
+  float x = 0.5f * (lo + hi);
+  for (int it = 0; it < 80; ++it) {
+    const float gx = which == 0 ? st32_f(a, b, c, x) : st32_fp(a, b, x);
+    if (gx == 0.f) return x;
+    const bool right = inc ? (gx < 0.f) : (gx > 0.f);
+    if (right) lo = x; else hi = x;
+    const float dg = which == 0 ? st32_fp(a, b, x) : (12.f * x * x - 8.f * a);
+    float xn = x - gx / dg;
+    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+    const float step = fabsf(xn - x);
+    x = xn;
+    if (step <= 2.4e-7f * fabsf(x) || !(hi - lo > 1.2e-7f * fabsf(hi))) break;
+  }
+  return x;
+}
+__device__ inline bool steer_estimate(const float* xv, const float* xu, float* J_out) {
+  float a = 0.f, b = 0.f, c = 0.f, dv2 = 0.f;
+  float dp[3], vb[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    dp[j] = xu[j] - xv[j];
+    const float v0 = xv[3 + j], v1 = xu[3 + j];
+    vb[j] = 0.5f * (v0 + v1);
+    a += v0 * v0 + v0 * v1 + v1 * v1;
+    b += dp[j] * (v0 + v1);
+    c += dp[j] * dp[j];
+    dv2 += (v1 - v0) * (v1 - v0);
+  }
+  if (!(c > 0.f)) return false;
+  const float tc = sqrtf(2.f * a / 3.f);
+  const float hi_f = 1.f + fmaxf(4.f * a, fmaxf(24.f * fabsf(b), 36.f * c));
+  float lo_s[2], hi_s[2];
+  int ns = 0;
+  if (st32_fp(a, b, tc) >= 0.f) {
+    lo_s[ns] = 0.f; hi_s[ns++] = hi_f;
+  } else {
+    const float hi_fp = fmaxf(1.f + fmaxf(2.f * a, 6.f * fabsf(b)), tc * 2.f + 1.f);
+    const float tb = st32_root(a, b, c, 1, tc, hi_fp, true);
+    if (b > 0.f) {
+      lo_s[ns] = 0.f; hi_s[ns++] = st32_root(a, b, c, 1, 0.f, tc, false);
+    }
+    lo_s[ns] = tb; hi_s[ns++] = fmaxf(hi_f, tb * 2.f + 1.f);
+  }
+  float best = __int_as_float(0x7f800000);
+  bool any = false;
+  for (int q = 0; q < ns; ++q) {
+    if (!(st32_f(a, b, c, lo_s[q]) < 0.f && st32_f(a, b, c, hi_s[q]) > 0.f)) continue;
+    const float t = st32_root(a, b, c, 0, lo_s[q], hi_s[q], true);
+    if (!(t > 0.f)) continue;
+    float r2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float d = dp[j] - vb[j] * t;
+      r2 += d * d;
+    }
+    const float J = t + dv2 / t + 12.f * r2 / (t * t * t);
+    best = fminf(best, J);
+    any = true;
+  }
+  *J_out = best;
+  return any;
+}
+
 // Collision(v, u): the nominal connection of duration tau (float) sampled at
 // t_m = tau (m / 4W), m = 1..4W, positions rounded to float, closed boxes.
 __device__ inline bool connection_hits(const double* xv, const double* xu, double tau, int W, const float* boxes,
@@ -100,11 +171,19 @@ __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __re
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n_list;
        q += (long long)gridDim.x * blockDim.x) {
     int2 vu = list[q];
+    float fv[6], fu[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      fv[j] = states[6 * vu.x + j];
+      fu[j] = states[6 * vu.y + j];
+    }
+    float J32;
+    if (steer_estimate(fv, fu, &J32) && J32 > r * 1.001f) continue;
     double xv[6], xu[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      xv[j] = (double)states[6 * vu.x + j];
-      xu[j] = (double)states[6 * vu.y + j];
+      xv[j] = (double)fv[j];
+      xu[j] = (double)fu[j];
     }
     double tau, J;
     if (!steer_dev(xv, xu, &tau, &J)) continue;

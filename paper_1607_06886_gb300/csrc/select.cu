@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -170,7 +171,7 @@ __global__ void k_path_edges(const int32_t* __restrict__ nodes, int len, const i
 __global__ void k_mc_prep(const int32_t* __restrict__ n_cert_p, const int32_t* __restrict__ plen,
                           const int32_t* __restrict__ pedges, const int32_t* __restrict__ pnodes,
                           const float* __restrict__ states, const float* __restrict__ tau, int W, int S, float sigma,
-                          float* table) {
+                          const float* __restrict__ boxes, int nb, float B, float* table) {
   const int k = blockIdx.y;
   if (k >= *n_cert_p) return;
   const int L = plen[k];
@@ -193,12 +194,30 @@ __global__ void k_mc_prep(const int32_t* __restrict__ n_cert_p, const int32_t* _
       xu[q] = (double)states[6 * u + q];
     }
     const double td = (double)t32;
-    for (int kk = 1; kk <= W; ++kk)
-      for (int s = 1; s <= S; ++s) {
-        const double t = (double)((kk - 1) * S + s) * (double)hs;
-        for (int a = 0; a < 3; ++a)
-          T[8 + (((kk - 1) * S + (s - 1)) * 3) + a] = __double2float_rn(nominal_dev(xv, xu, td, a, t));
-      }
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+      const Cubic c = cubic_dev(xv, xu, td, a);
+      lo[a] = __int_as_float(0x7f800000);
+      hi[a] = -lo[a];
+      for (int kk = 1; kk <= W; ++kk)
+        for (int s = 1; s <= S; ++s) {
+          const double t = (double)((kk - 1) * S + s) * (double)hs;
+          const float pv = __double2float_rn(cubic_at(c, t));
+          T[8 + (((kk - 1) * S + (s - 1)) * 3) + a] = pv;
+          lo[a] = fminf(lo[a], pv);
+          hi[a] = fmaxf(hi[a], pv);
+        }
+      lo[a] = __fsub_rn(lo[a], B);
+      hi[a] = __fadd_rn(hi[a], B);
+    }
+    // boxes that can hold a position nominal + d0 with |d0| <= B on every axis
+    uint32_t bits = 0u;
+    for (int o = 0; o < nb && o < 32; ++o) {
+      const float* b = boxes + 6 * o;
+      if (b[0] <= hi[0] && lo[0] <= b[3] && b[1] <= hi[1] && lo[1] <= b[4] && b[2] <= hi[2] && lo[2] <= b[5])
+        bits |= 1u << o;
+    }
+    T[7] = __uint_as_float(bits);
   }
 }
 
@@ -222,13 +241,45 @@ __device__ __forceinline__ void mc_normals(uint64_t seed, uint64_t m, uint64_t s
 constexpr int kMcThreads = 128;
 constexpr int kMcTableSmem = 24 * 1024;  // floats of a plan's table staged in shared memory
 
-// One thread per rollout; plan k = blockIdx.x / bpp.
+// Box test of a position: with nb <= 32 and every |d0| <= B only the path edge's candidate
+// boxes (bits) can hold it; otherwise all boxes are tested.
+__device__ __forceinline__ bool mc_hit(const float* p, const float* d0, float B, uint32_t bits, const float* boxes,
+                                       int nb) {
+  if (nb <= 32 && fabsf(d0[0]) <= B && fabsf(d0[1]) <= B && fabsf(d0[2]) <= B) {
+    while (bits) {
+      const int o = __ffs(bits) - 1;
+      bits &= bits - 1u;
+      if (in_box_dev(p[0], p[1], p[2], boxes + 6 * o)) return true;
+    }
+    return false;
+  }
+  for (int o = 0; o < nb; ++o)
+    if (in_box_dev(p[0], p[1], p[2], boxes + 6 * o)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void mc_update(const float* z, float P0, float P1, float P2, float P3, float L0, float L1,
+                                          float L2, const float* nomq, float* d0, float* d1, float* p) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float n0 = __fmul_rn(L0, z[2 * a]);
+    const float n1 = fmaf(L1, z[2 * a], __fmul_rn(L2, z[2 * a + 1]));
+    const float e0 = fmaf(P0, d0[a], fmaf(P1, d1[a], n0));
+    const float e1 = fmaf(P2, d0[a], fmaf(P3, d1[a], n1));
+    d0[a] = e0;
+    d1[a] = e1;
+    p[a] = __fadd_rn(nomq[a], e0);
+  }
+}
+
+// One thread per rollout; plan k = blockIdx.x / bpp.  Normals of two consecutive steps are drawn
+// before either update (independent Philox chains overlap).
 __global__ void __launch_bounds__(kMcThreads) k_mc_rollout(const int32_t* __restrict__ n_cert_p, int bpp,
                                                             const int32_t* __restrict__ plen,
                                                             const float* __restrict__ table, int W, int S,
                                                             const float* __restrict__ linf_g,
                                                             const float* __restrict__ boxes_g, int nb, int n_mc,
-                                                            uint64_t seed, unsigned long long* counts) {
+                                                            uint64_t seed, float B, unsigned long long* counts) {
   extern __shared__ float sm[];
   const int k = blockIdx.x / bpp;
   if (k >= *n_cert_p) return;
@@ -247,7 +298,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_rollout(const int32_t* __rest
   const int m = (blockIdx.x % bpp) * kMcThreads + threadIdx.x;
   bool hit = false;
   if (m < n_mc) {
-    float z[6], d0[3], d1[3];
+    float z[6], zb[6], d0[3], d1[3], p[3];
     mc_normals(seed, (uint64_t)m, 0ull, z);
     const float l0 = linf_g[0], l1 = linf_g[1], l2 = linf_g[2];
 #pragma unroll
@@ -255,28 +306,23 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_rollout(const int32_t* __rest
       d0[a] = __fmul_rn(l0, z[2 * a]);
       d1[a] = fmaf(l1, z[2 * a], __fmul_rn(l2, z[2 * a + 1]));
     }
+    const int WS = W * S;
     uint64_t step = 0;
     for (int e = 0; e < L && !hit; ++e) {
       const float* Te = T + (size_t)e * stride;
       const float P0 = Te[0], P1 = Te[1], P2 = Te[2], P3 = Te[3], L0 = Te[4], L1 = Te[5], L2 = Te[6];
-      for (int q = 0; q < W * S && !hit; ++q) {
-        mc_normals(seed, (uint64_t)m, ++step, z);
-        float p[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float n0 = __fmul_rn(L0, z[2 * a]);
-          const float n1 = fmaf(L1, z[2 * a], __fmul_rn(L2, z[2 * a + 1]));
-          const float e0 = fmaf(P0, d0[a], fmaf(P1, d1[a], n0));
-          const float e1 = fmaf(P2, d0[a], fmaf(P3, d1[a], n1));
-          d0[a] = e0;
-          d1[a] = e1;
-          p[a] = __fadd_rn(Te[8 + q * 3 + a], e0);
+      const uint32_t bits = __float_as_uint(Te[7]);
+      for (int q = 0; q < WS && !hit; q += 2) {
+        const bool two = q + 1 < WS;
+        mc_normals(seed, (uint64_t)m, step + 1, z);
+        if (two) mc_normals(seed, (uint64_t)m, step + 2, zb);
+        mc_update(z, P0, P1, P2, P3, L0, L1, L2, Te + 8 + q * 3, d0, d1, p);
+        hit = mc_hit(p, d0, B, bits, boxes, nb);
+        if (two && !hit) {
+          mc_update(zb, P0, P1, P2, P3, L0, L1, L2, Te + 8 + (q + 1) * 3, d0, d1, p);
+          hit = mc_hit(p, d0, B, bits, boxes, nb);
         }
-        for (int o = 0; o < nb; ++o)
-          if (in_box_dev(p[0], p[1], p[2], boxes + 6 * o)) {
-            hit = true;
-            break;
-          }
+        step += two ? 2 : 1;
       }
     }
   }
@@ -393,8 +439,11 @@ int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert_max, int n_mc,
              cudaStream_t s) {
   ExploreBufs& X = g->ex;
   dim3 grid(kMaxPathEdges / 64, n_cert_max);
+  // deviation bound for the box cull: 12 stationary position standard deviations (any B is exact)
+  const double sq3 = 1.7320508075688772935;
+  const float B = (float)(12.0 * (double)g->sigma * sqrt(1.0 / sq3 + 0.5 * sq3)) + 1e-6f;
   k_mc_prep<<<grid, 64, 0, s>>>(n_cert_dev, X.mc_plen, X.mc_pedges, X.path_buf, g->states, g->tau, g->W, S,
-                                g->sigma, X.mc_table);
+                                g->sigma, g->boxes, g->n_boxes, B, X.mc_table);
   note_launch();
   PUMP_CUDA_TRY(cudaMemsetAsync(X.mc_count, 0, sizeof(int64_t) * n_cert_max, s));
   const int bpp = (n_mc + kMcThreads - 1) / kMcThreads;
@@ -402,7 +451,7 @@ int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert_max, int n_mc,
     const size_t smem = sizeof(float) * (6 * (size_t)std::max(g->n_boxes, 1) + kMcTableSmem);
     PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_mc_rollout<<<n_cert_max * bpp, kMcThreads, smem, s>>>(n_cert_dev, bpp, X.mc_plen, X.mc_table, g->W, S,
-                                                            g->linf_dev, g->boxes, g->n_boxes, n_mc, seed,
+                                                            g->linf_dev, g->boxes, g->n_boxes, n_mc, seed, B,
                                                             reinterpret_cast<unsigned long long*>(X.mc_count));
     note_launch();
   }
