@@ -97,7 +97,8 @@ __device__ inline float st32_root(float a, float b, float c, int which, float lo
   }
   return x;
 }
-__device__ inline bool steer_estimate(const float* xv, const float* xu, float* J_out) {
+__device__ inline bool steer_estimate(const float* xv, const float* xu, float* J_out, float* tmin = nullptr,
+                                      int* n_min = nullptr, float* Jmin = nullptr) {
   float a = 0.f, b = 0.f, c = 0.f, dv2 = 0.f;
   float dp[3], vb[3];
 #pragma unroll
@@ -138,6 +139,11 @@ __device__ inline bool steer_estimate(const float* xv, const float* xu, float* J
       r2 += d * d;
     }
     const float J = t + dv2 / t + 12.f * r2 / (t * t * t);
+    if (tmin) {
+      tmin[*n_min] = t;
+      Jmin[*n_min] = J;
+      ++*n_min;
+    }
     best = fminf(best, J);
     any = true;
   }
@@ -145,16 +151,63 @@ __device__ inline bool steer_estimate(const float* xv, const float* xu, float* J
   return any;
 }
 
+// Cost(v,u) in double from the float minimisers: Newton from each inside a bracket of +-1e-5
+// (relative) whose end signs are checked in double.  Falls back to the full analysis
+// (steer_dev) when a bracket fails or two minima lie within 1e-4 of each other, so the chosen
+// root is the one the full analysis picks.
+__device__ inline bool steer_refined(const double* xv, const double* xu, const float* tmin, const float* Jmin, int nm,
+                                     double* tau_out, double* J_out) {
+  if (nm < 1 || (nm == 2 && fabsf(Jmin[0] - Jmin[1]) <= 1e-4f * fmaxf(Jmin[0], Jmin[1])))
+    return steer_dev(xv, xu, tau_out, J_out);
+  SteerCoef k{0.0, 0.0, 0.0};
+  for (int j = 0; j < 3; ++j) {
+    const double dp = xu[j] - xv[j], v0 = xv[3 + j], v1 = xu[3 + j];
+    k.a += v0 * v0 + v0 * v1 + v1 * v1;
+    k.b += dp * (v0 + v1);
+    k.c += dp * dp;
+  }
+  double best_t = -1.0, best_J = 0.0;
+  for (int q = 0; q < nm; ++q) {
+    const double t0 = (double)tmin[q];
+    const double lo = t0 * (1.0 - 1e-5), hi = t0 * (1.0 + 1e-5);
+    if (!(st_f(k, lo) < 0.0 && st_f(k, hi) > 0.0)) return steer_dev(xv, xu, tau_out, J_out);
+    const double t = st_root(k, 0, lo, hi, true);
+    const double J = st_J(k, t);
+    if (best_t < 0.0 || J < best_J || (J == best_J && t < best_t)) {
+      best_t = t;
+      best_J = J;
+    }
+  }
+  *tau_out = best_t;
+  *J_out = best_J;
+  return true;
+}
+
 // Collision(v, u): the nominal connection of duration tau (float) sampled at
 // t_m = tau (m / 4W), m = 1..4W, positions rounded to float, closed boxes.
+// frac[m-1] = m / (4W) in double, shared by the block.  Before sampling, a box holding the whole
+// cubic on [0, tau] (p0 +- (|v0| tau + |c2| tau^2 + |c3| tau^3), widened by 1e-6 against
+// rounding) is tested; no obstacle in it means no sample can hit.
 __device__ inline bool connection_hits(const double* xv, const double* xu, double tau, int W, const float* boxes,
-                                       int nb) {
-  const Cubic cx = cubic_dev(xv, xu, tau, 0), cy = cubic_dev(xv, xu, tau, 1), cz = cubic_dev(xv, xu, tau, 2);
+                                       int nb, const double* frac) {
+  const Cubic c[3] = {cubic_dev(xv, xu, tau, 0), cubic_dev(xv, xu, tau, 1), cubic_dev(xv, xu, tau, 2)};
+  float lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    const double R = fabs(c[a].v0) * tau + fabs(c[a].c2) * tau * tau + fabs(c[a].c3) * tau * tau * tau;
+    lo[a] = (float)(c[a].p0 - R) - 1e-6f;
+    hi[a] = (float)(c[a].p0 + R) + 1e-6f;
+  }
+  bool near = false;
+  for (int o = 0; o < nb && !near; ++o) {
+    const float* b = boxes + 6 * o;
+    near = b[0] <= hi[0] && lo[0] <= b[3] && b[1] <= hi[1] && lo[1] <= b[4] && b[2] <= hi[2] && lo[2] <= b[5];
+  }
+  if (!near) return false;
   for (int m = 1; m <= 4 * W; ++m) {
-    double t = tau * ((double)m / (double)(4 * W));
-    float p0 = (float)cubic_at(cx, t);
-    float p1 = (float)cubic_at(cy, t);
-    float p2 = (float)cubic_at(cz, t);
+    const double t = tau * frac[m - 1];
+    const float p0 = (float)cubic_at(c[0], t);
+    const float p1 = (float)cubic_at(c[1], t);
+    const float p2 = (float)cubic_at(c[2], t);
     for (int o = 0; o < nb; ++o)
       if (in_box_dev(p0, p1, p2, boxes + 6 * o)) return true;
   }
@@ -164,8 +217,10 @@ __device__ inline bool connection_hits(const double* xv, const double* xu, doubl
 __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __restrict__ list, long long n_list,
                               int n, float r, int W, const float* __restrict__ boxes_g, int nb, uint32_t* keep,
                               double* __restrict__ res_tau, float* __restrict__ res_cost) {
-  extern __shared__ float boxes[];
+  extern __shared__ double frac[];
+  float* boxes = reinterpret_cast<float*>(frac + 4 * W);
   for (int k = threadIdx.x; k < 6 * nb; k += blockDim.x) boxes[k] = boxes_g[k];
+  for (int m = threadIdx.x; m < 4 * W; m += blockDim.x) frac[m] = (double)(m + 1) / (double)(4 * W);
   __syncthreads();
   const int nw = (n + 31) / 32;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n_list;
@@ -177,8 +232,10 @@ __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __re
       fv[j] = states[6 * vu.x + j];
       fu[j] = states[6 * vu.y + j];
     }
-    float J32;
-    if (steer_estimate(fv, fu, &J32) && J32 > r * 1.001f) continue;
+    float J32, tmin[2], Jmin[2];
+    int nm = 0;
+    const bool est = steer_estimate(fv, fu, &J32, tmin, &nm, Jmin);
+    if (est && J32 > r * 1.001f) continue;
     double xv[6], xu[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -186,10 +243,10 @@ __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __re
       xu[j] = (double)fu[j];
     }
     double tau, J;
-    if (!steer_dev(xv, xu, &tau, &J)) continue;
+    if (!(est ? steer_refined(xv, xu, tmin, Jmin, nm, &tau, &J) : steer_dev(xv, xu, &tau, &J))) continue;
     if (!(__double2float_rn(J) < r)) continue;
     double td = (double)__double2float_rn(tau);
-    if (connection_hits(xv, xu, td, W, boxes, nb)) continue;
+    if (connection_hits(xv, xu, td, W, boxes, nb, frac)) continue;
     res_tau[q] = tau;
     res_cost[q] = __double2float_rn(J);
     atomicOr(keep + (size_t)vu.x * nw + (vu.y >> 5), 1u << (vu.y & 31));
@@ -372,7 +429,7 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   long long list_blocks = ((long long)n_list + kBlock - 1) / kBlock;
   const int glist = (int)(list_blocks < (long long)sms * 16 ? (list_blocks > 0 ? list_blocks : 1) : (long long)sms * 16);
   if (n_list) {
-    k_steer_pairs<<<glist, kBlock, sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1), s>>>(
+    k_steer_pairs<<<glist, kBlock, sizeof(double) * 4 * g->W + sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1), s>>>(
         g->states, list, (long long)n_list, n, g->radius, g->W, g->boxes, g->n_boxes, keep, res_tau, res_cost);
     note_launch();
   }
