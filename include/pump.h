@@ -239,7 +239,10 @@ enum {
   PUMP_EXPORT_PLAN_POPC = 16,    /* int32[n_plans]                  */
   PUMP_EXPORT_PLAN_CREATED = 17, /* int32[n_plans] group index that created the plan (-1 root) */
   PUMP_EXPORT_PLAN_EXPANDED = 18, /* int32[n_plans] group index that expanded it, -1 if never */
-  PUMP_EXPORT_GOAL_PLANS = 19     /* int32[n_goal] P_goal ids in PlanSelection order */
+  PUMP_EXPORT_GOAL_PLANS = 19,    /* int32[n_goal] P_goal ids in PlanSelection order */
+  PUMP_EXPORT_EDGE_BOX = 20       /* float[E][6] lo xyz, hi xyz: box holding every particle
+                                     position of the edge (graph build; pump_edge_masks skips
+                                     the obstacles it misses) */
 };
 int pump_export(pump_graph* g, int32_t what, void* host_buf, size_t cap, size_t* needed);
 

@@ -519,6 +519,7 @@ int pump_export(pump_graph* g, int32_t what, void* host_buf, size_t cap, size_t*
     case PUMP_EXPORT_PLAN_CREATED: if (!ex) return PUMP_ERR_INVALID_ARG; src = g->ex.tcre; bytes = 4 * P; break;
     case PUMP_EXPORT_PLAN_EXPANDED: if (!ex) return PUMP_ERR_INVALID_ARG; src = g->ex.eexp; bytes = 4 * P; break;
     case PUMP_EXPORT_GOAL_PLANS: if (!ex) return PUMP_ERR_INVALID_ARG; src = g->ex.goal_sorted; bytes = 4 * (size_t)g->last_goal; break;
+    case PUMP_EXPORT_EDGE_BOX: if (!geo) return PUMP_ERR_INVALID_ARG; src = g->ibox; bytes = 24 * E; break;
     default: return PUMP_ERR_INVALID_ARG;
   }
   *needed = bytes;

@@ -23,7 +23,7 @@ NO_EARLY_STOP, EXPLORE_ONLY, STEPWISE = 1, 2, 4
 EXPORT = {
     "counts": 0, "node_valid": 1, "row_ptr": 2, "col": 3, "ecost": 4, "tau": 5, "h": 6, "phi": 7, "L": 8,
     "nominal": 9, "linf": 10, "masks": 11, "plan_head": 12, "plan_parent": 13, "plan_cost": 14, "plan_mask": 15,
-    "plan_popc": 16, "plan_created": 17, "plan_expanded": 18, "goal_plans": 19,
+    "plan_popc": 16, "plan_created": 17, "plan_expanded": 18, "goal_plans": 19, "edge_box": 20,
 }
 
 
@@ -280,7 +280,8 @@ class Graph:
                   "linf": (np.float32, (3,)), "masks": (np.uint32, (E, w)), "plan_head": (np.int32, (P,)),
                   "plan_parent": (np.int32, (P,)), "plan_cost": (np.float32, (P,)), "plan_mask": (np.uint32, (P, w)),
                   "plan_popc": (np.int32, (P,)), "plan_created": (np.int32, (P,)),
-                  "plan_expanded": (np.int32, (P,)), "goal_plans": (np.int32, (G,))}
+                  "plan_expanded": (np.int32, (P,)), "goal_plans": (np.int32, (G,)),
+                  "edge_box": (np.float32, (E, 6))}
         dt, shp = shapes[what]
         return raw.view(dt).reshape(shp).copy()
 

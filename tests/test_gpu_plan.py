@@ -184,3 +184,38 @@ def test_device_resident_inputs_match_host_inputs():
         np.testing.assert_array_equal(Gh.export(k), Gd.export(k))
     rh, rd = Gh.plan(plan_params(wl)), Gd.plan(plan_params(wl))
     assert rh["chosen_plan"] == rd["chosen_plan"] and rh["mc_collisions"] == rd["mc_collisions"]
+
+
+def test_edge_boxes_hold_every_particle_position():
+    """The per-edge position box that lets the mask query skip obstacles must hold every particle
+    position of the edge.  Six slabs just outside the box (each a box starting one float ulp past a
+    face) are handed to the oracle's mask computation for the edge: no particle may touch any."""
+    wl = inputs.make_workload("indoor_4k", 3, 300)
+    G = gpu_graph(wl)
+    gg = export_graph(G)
+    og = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
+    _, diff = compare_graphs(gg, og, wl.radius)
+    ib = G.export("edge_box")
+    E = len(og["col"])
+    assert ib.shape == (E, 6) and np.all(ib[:, :3] <= ib[:, 3:])
+    nom = og["nom"].reshape(E, wl.n_waypoints, 3)
+    assert np.all(nom >= ib[:, None, :3]) and np.all(nom <= ib[:, None, 3:])
+    rng = np.random.default_rng(7)
+    big = np.float32(1e3)
+    for e in rng.choice(np.flatnonzero(~diff), size=min(120, int((~diff).sum())), replace=False):
+        lo, hi = ib[e, :3], ib[e, 3:]
+        slabs = []
+        for a in range(3):
+            s = np.array([-big, -big, -big, big, big, big], np.float32)
+            s[a] = np.nextafter(hi[a], np.float32(np.inf))
+            slabs.append(s.copy())
+            s = np.array([-big, -big, -big, big, big, big], np.float32)
+            s[3 + a] = np.nextafter(lo[a], np.float32(-np.inf))
+            slabs.append(s)
+        one = {"n_edges": 1, "W": og["W"], "phi": og["phi"][e:e + 1].copy(), "L": og["L"][e:e + 1].copy(),
+               "nom": og["nom"][e:e + 1].copy(), "linf": og["linf"]}
+        m = cpu.edge_masks(one, wl.xi, np.stack(slabs), wl.n_particles)
+        assert not m.any(), e
+        # control: a slab from the first nominal waypoint's x upward catches particles
+        s = np.array([nom[e, 0, 0], -big, -big, big, big, big], np.float32)
+        assert cpu.edge_masks(one, wl.xi, s[None], wl.n_particles).any(), e
