@@ -432,11 +432,11 @@ def roofline_measure(pump, G, prm, wl, dev, flush, steps):
                       "frac": mask_frac, "traffic": measured_traffic("k_edge_mask")},
         "explore": {"ms": ms_expl, "bound": "hbm", "bytes": bytes_expl, "achieved_gbs": expl_gbs, "peak_gbs": hbm,
                     "frac": expl_gbs / hbm, "iterations": st["n_iterations"],
-                    "traffic": measured_traffic("k_explore_persistent")},
+                    "traffic": measured_traffic("k_explore_cluster")},
     }
     if ms_expl >= ms_mask:
-        roof = {"kernel": "k_explore_persistent", "bound": "hbm", "achieved": expl_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": expl_gbs / hbm, "traffic": measured_traffic("k_explore_persistent"),
+        roof = {"kernel": "k_explore_cluster", "bound": "hbm", "achieved": expl_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": expl_gbs / hbm, "traffic": measured_traffic("k_explore_cluster"),
                 "peak_source": peaks["_source"]}
     else:
         roof = {"kernel": "k_edge_mask", "bound": "alu", "achieved": ops_mask / (ms_mask / 1e3) / 1e12,

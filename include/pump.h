@@ -48,6 +48,8 @@ typedef enum {
 #define PUMP_NO_EARLY_STOP 1 /* Explore runs until P_open is empty (testing)        */
 #define PUMP_EXPLORE_ONLY 2  /* pump_plan stops after Explore (no PlanSelection)    */
 #define PUMP_STEPWISE 4      /* run Explore's phases as separate launches           */
+#define PUMP_EXPLORE_GRID 8  /* run Explore as one grid-wide cooperative kernel
+                                instead of one thread-block cluster                 */
 
 typedef struct pump_graph pump_graph;
 
@@ -74,7 +76,8 @@ typedef struct {
   uint64_t mc_seed;       /* Philox4x64-10 key of the rollout normals                      */
   int64_t max_plans;      /* plan arena capacity; more survivors -> PUMP_ERR_CAPACITY      */
   int32_t max_iterations; /* cap on Explore's group index; exceeded -> PUMP_ERR_TIMEOUT    */
-  int32_t flags;          /* PUMP_NO_EARLY_STOP | PUMP_EXPLORE_ONLY | PUMP_STEPWISE       */
+  int32_t flags;          /* PUMP_NO_EARLY_STOP | PUMP_EXPLORE_ONLY | PUMP_STEPWISE |
+                             PUMP_EXPLORE_GRID                                        */
 } pump_plan_params;
 
 typedef struct {

@@ -25,6 +25,7 @@ UNITS = {
     "graph_build.cu": ["-fmad=false"],
     "edge_mask.cu": [],
     "explore.cu": [],
+    "explore_cluster.cu": [],
     "select.cu": [],
     "noalloc.cu": [],
 }

@@ -723,10 +723,25 @@ int explore_blocks() {
   return v;
 }
 
-int run_explore_kernels(pump_graph* g, const ExploreArgs& A, bool stepwise, cudaStream_t s) {
-  const int64_t mb = (int64_t)g->n * A.kstride;
-  k_fill_u32<<<256, 256, 0, s>>>(A.mbest, mb, 0x7f800000u);
-  note_launch();
+int plan_explore_cluster(const ExploreArgs& A, int* nr, bool* dsm);
+int run_explore_cluster(pump_graph* g, const ExploreArgs& A, int nr, bool dsm, cudaStream_t s);
+
+// Explore kernels for one run.  mode 0: the thread-block cluster kernel (explore_cluster.cu)
+// where the device can co-schedule one, else the grid kernel; 1: the grid kernel; 2: the
+// phases as separate launches.
+int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStream_t s) {
+  const bool stepwise = mode == 2;
+  int cl_nr = 0;
+  bool cl_dsm = false;
+  if (mode == 0) {
+    const int rc = plan_explore_cluster(A, &cl_nr, &cl_dsm);
+    if (rc) return rc;
+  }
+  if (!(cl_nr > 0 && cl_dsm)) {  // the cluster kernel keeps mbest on chip and fills it itself
+    const int64_t mb = (int64_t)g->n * A.kstride;
+    k_fill_u32<<<256, 256, 0, s>>>(A.mbest, mb, 0x7f800000u);
+    note_launch();
+  }
   k_explore_init<<<1, 1, 0, s>>>(A, g->start);
   note_launch();
   PUMP_CUDA_TRY(cudaGetLastError());
@@ -735,6 +750,12 @@ int run_explore_kernels(pump_graph* g, const ExploreArgs& A, bool stepwise, cuda
   int coop = 0;
   PUMP_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   const int sms = num_sms();
+  if (cl_nr > 0) {
+    const int rc = run_explore_cluster(g, A, cl_nr, cl_dsm, s);
+    if (rc) return rc;
+    PUMP_CUDA_TRY(cudaGetLastError());
+    return PUMP_OK;
+  }
   if (!stepwise && coop) {
     const size_t smem = sizeof(ExploreSmem);
     PUMP_CUDA_TRY(cudaFuncSetAttribute(k_explore_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -1,0 +1,1186 @@
+// Explore (Algorithm 4) inside one thread-block cluster.
+//
+// Why a cluster.  The search is a chain of dependent groups, and one group is
+// small (hundreds of plans, thousands of candidates), so its cost is latency:
+// the barriers between the steps of an iteration and the dependent loads
+// inside them.  A grid-wide barrier built on global-memory atomics costs
+// microseconds; the hardware barrier of a thread-block cluster costs well
+// under one, and distributed shared memory lets the CTAs hand each other
+// counts and the next group's members without a round trip through L2.  One
+// cluster of CL CTAs (16 where the device can co-schedule them, else 8 or 4)
+// runs the whole search.
+//
+// State.  The plan arena, the group list (ginfo, goff) and the goal list are
+// in global memory as for the grid kernel (explore.cu).  The table mbest[x][k]
+// (least cost ever inserted at node x with popcount k, float bits) is
+// partitioned over the CTAs' shared memory by node (x mod CL) when it fits,
+// else it stays in global memory.  The argument that "dominated by a plan ever
+// inserted at x" equals "dominated by a plan in P(x)" is in explore.cu.
+//
+// One iteration (group i) is three phases, each closed by a cluster barrier:
+//   A expand.  CTA r takes candidates [r per, (r+1) per) of the group (members
+//     in ascending id, out-edges in ascending target; per = ceil(C / CL)), a
+//     warp per member: cost, mask OR, popcount, CP cutoff, atomicMin into
+//     mbest.  Members are stamped expanded (e = i).  The members of the chunk
+//     were placed in the CTA's shared memory by their writers (phase C).
+//   B filter.  Each cached candidate is tested against mbest (strict cost,
+//     non-strict popcount) and gets its group index max(bucket, i + 1).
+//     Recent plans that may still be open are re-tested the same way.  The
+//     CTA counts survivors; for each group index i+1 .. i+kWin, members from
+//     older plans and from survivors with their out-degree sums; goal-stop
+//     bits; the least group index; the least id of an older open plan.  It
+//     copies these counts into every CTA's shared memory.
+//   C write.  Every CTA derives from the same counts the next group index,
+//     arena ids (survivors numbered in candidate order: CTA by CTA, then by
+//     position) and next-group positions (older plans first, then survivors,
+//     each in id order).  It writes its survivors to the arena and its members
+//     to the group list with candidate offsets, and copies each member into
+//     the shared memory of every CTA whose next chunk holds its candidates.  A
+//     next group index beyond the window takes one more counting round.
+//
+// Older plans.  A plan whose group index is at most i was expanded (it was a
+// member of that group) or was dominated when that group was formed or
+// skipped, and removal is permanent because mbest only decreases; a plan with
+// a larger group index has not been expanded.  So an older plan is open and
+// undominated iff its group index exceeds i and mbest does not dominate it,
+// and only ids from the least id of an older open plan upward are re-tested.
+//
+// Every value that decides control flow (group size, candidate count, group
+// index, stop, status) is computed identically by every CTA from the same
+// counts, so all CTAs take the same number of barriers.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <mutex>
+#include <vector>
+
+#include "pump_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pump {
+namespace {
+
+#ifndef PUMP_CLUSTER_THREADS
+#define PUMP_CLUSTER_THREADS 1024
+#endif
+constexpr int kCT = PUMP_CLUSTER_THREADS;  // threads per CTA
+constexpr int kCW = kCT / 32;              // warps per CTA (at most 32: one warp scans the warp totals)
+static_assert(kCT % 32 == 0 && kCW <= 32 && kCT >= 64, "CTA size");
+constexpr int kCCap = 2048;       // candidates a CTA keeps in shared memory
+constexpr int kOCap = 1024;       // older plans a CTA keeps in shared memory
+constexpr int kMemCap = 512;      // next-chunk members a CTA receives in shared memory
+constexpr int kWin = 32;          // group indices ahead counted in phase B
+constexpr int kThr = 64;          // group thresholds thr_i .. thr_{i+63} kept per iteration
+constexpr int kMaxCluster = 16;
+constexpr uint32_t kGoalBit = 0x80000000u;
+constexpr size_t kSmemLimit = 227 * 1024;
+constexpr size_t kDynSmemMax = kSmemLimit - 2048;  // dynamic part (the kernel's static part is < 1 KiB)
+
+__device__ __forceinline__ int32_t ld32(const int32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ int64_t ld64(const int64_t* p) { return __ldcg(reinterpret_cast<const long long*>(p)); }
+__device__ __forceinline__ float ldf(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ uint32_t ldu(const uint32_t* p) { return __ldcg(p); }
+
+// Counts one CTA publishes after phase B (every CTA reads them in phase C).
+struct Pub {
+  int32_t surv;      // survivors of the CTA's chunk
+  int32_t minb;      // least group index of an open undominated plan seen by the CTA
+  int32_t min_open;  // least id of an older open undominated plan (INT_MAX if none)
+  uint32_t stop;     // bit q: a member of group i+1+q is a goal plan with popc < K_min
+  int32_t ocnt[kWin], ncnt[kWin];
+  unsigned long long odeg[kWin], ndeg[kWin];
+};
+// Counts for one group index beyond the window (extra round).
+struct PubS {
+  int32_t ocnt, ncnt;
+  unsigned long long odeg, ndeg;
+  uint32_t stop, pad;
+};
+
+// Loop state, the same in every CTA of the cluster (kept in shared memory; thread 0 writes it
+// between barriers).
+struct St {
+  int64_t C;      // candidates of the group
+  int64_t base;   // arena size before the group's survivors
+  int64_t lo;     // least id that may still be an open plan
+  int64_t ncand;  // candidates over the run
+  int32_t g;      // group size
+  int32_t i;      // group index
+  int32_t stop;
+  int32_t status;
+  int32_t n_groups;
+  int32_t k;      // iteration (loop count)
+  // this CTA's share of the iteration (set with the state; per-CTA values)
+  int64_t c0, c1; // candidates [c0, c1) of the group
+  int64_t a0, a1; // older plans [a0, a1) re-tested
+  int32_t big;    // the group's chunks exceed the candidate cache
+};
+
+struct CSmem {
+  St st;
+  float thr[kThr];  // thr[q] = float((i + q) lambda r), the same rounding as bucket_of
+  uint4 cmask[kCCap];   // OR'd mask words of a candidate (w <= 4)
+  uint4 omask[kOCap];   // mask words of an older open plan (w <= 4)
+  uint4 mt_mask[kMemCap];
+  int4 mt_info[kMemCap];       // member: plan id, head node, row start, cost bits
+  long long mt_off[kMemCap];   // member: first candidate offset
+  int32_t mt_deg[kMemCap];     // member: out-degree
+  int32_t mt_tag[kMemCap];     // member: group position
+  int32_t mt_gen[kMemCap];     // member: iteration it belongs to (entry valid iff tag and gen match)
+  int32_t cx[kCCap], cpar[kCCap], cedge[kCCap], ceff[kCCap], cr0[kCCap];
+  uint32_t cdg[kCCap];  // target out-degree | goal bit
+  float ccost[kCCap];
+  int16_t cpc[kCCap];
+  int32_t oeff[kOCap], ox[kOCap], or0[kOCap];
+  uint32_t odg[kOCap];
+  float ocost[kOCap];
+  int16_t opc[kOCap];
+  Pub pub;     // this CTA's counts (accumulated in phase B, read by every CTA in phase C)
+  PubS pubs_s; // the same for a group index beyond the window
+  // cluster-wide values of phase C, derived by warp 0 and read by the whole CTA
+  int32_t b_nbk, b_min_open, b_before_s, b_total_s, b_before_o, b_total_o, b_before_n, b_total_n, b_stop, b_fast;
+  long long b_dbefore_o, b_dtotal_o, b_dbefore_n, b_dtotal_n, b_per_n;
+  int32_t slot0;     // member holding the first candidate of this CTA's chunk (set by its writer)
+  int32_t slot_end;  // member holding the last candidate of this CTA's chunk (set by its writer)
+  long long kept; // candidates under the CP cutoff, this CTA, whole run
+};
+
+__device__ __forceinline__ void chunk(int64_t total, int r, int nr, int64_t* lo, int64_t* hi) {
+  const int64_t per = (total + nr - 1) / nr;
+  *lo = min(total, (int64_t)r * per);
+  *hi = min(total, *lo + per);
+}
+
+// Exclusive block scan over kCT threads; returns the prefix and writes the total.
+template <typename T>
+__device__ T cscan(T v, T* total) {
+  __shared__ T ws[kCW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    T s = lane < kCW ? ws[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kCW) ws[lane] = s;
+  }
+  __syncthreads();
+  const T pre = (warp > 0 ? ws[warp - 1] : T(0)) + x - v;
+  *total = ws[kCW - 1];
+  __syncthreads();
+  return pre;
+}
+
+// Block sum and two minima in one shared-memory round.
+__device__ void creduce(int32_t& sum, int32_t& mn, int32_t& mn2) {
+  __shared__ int32_t s_sum[kCW], s_mn[kCW], s_mn2[kCW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mn2 = min(mn2, __shfl_xor_sync(0xffffffffu, mn2, o));
+  }
+  if (lane == 0) {
+    s_sum[warp] = sum;
+    s_mn[warp] = mn;
+    s_mn2[warp] = mn2;
+  }
+  __syncthreads();
+  sum = lane < kCW ? s_sum[lane] : 0;
+  mn = lane < kCW ? s_mn[lane] : INT_MAX;
+  mn2 = lane < kCW ? s_mn2[lane] : INT_MAX;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mn2 = min(mn2, __shfl_xor_sync(0xffffffffu, mn2, o));
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ long long csum_ll(long long v) {
+  __shared__ long long s[kCW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) s[warp] = v;
+  __syncthreads();
+  v = lane < kCW ? s[lane] : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;
+}
+
+// Packed scan fields: survivor count in bits 52..63, member count in bits 40..51, member
+// out-degree sum in bits 0..39 (a tile holds at most kCT items of each).
+constexpr int kPackShift = 40;
+__device__ __forceinline__ int64_t pack_cd(int64_t c, int64_t d) { return (c << kPackShift) | d; }
+__device__ __forceinline__ int32_t pack_c(int64_t x) { return (int32_t)((x >> kPackShift) & 0xFFF); }
+__device__ __forceinline__ int32_t pack_k(int64_t x) { return (int32_t)(x >> 52); }
+__device__ __forceinline__ int64_t pack_d(int64_t x) { return x & ((int64_t(1) << kPackShift) - 1); }
+
+// mbest row of node x: in the owning CTA's shared memory, or in global memory.
+template <bool kDsm>
+__device__ __forceinline__ uint32_t* mb_row(const ExploreArgs& A, cg::cluster_group& cl, uint32_t* mbl, int32_t x) {
+  if (kDsm) {
+    const unsigned nr = cl.num_blocks();
+    return cl.map_shared_rank(mbl + (size_t)(x / (int)nr) * A.kstride, (unsigned)(x % (int)nr));
+  }
+  return A.mbest + (size_t)x * A.kstride;
+}
+
+template <bool kDsm>
+__device__ __forceinline__ uint32_t mb_ld(const uint32_t* p) {
+  if (kDsm) return *reinterpret_cast<const volatile uint32_t*>(p);
+  return __ldcg(p);
+}
+
+// Dominated: some entry k <= pc of x's row holds a cost strictly below c.  Up to four entries
+// are loaded at once.
+template <bool kDsm>
+__device__ __forceinline__ bool dominated_c(const ExploreArgs& A, cg::cluster_group& cl, uint32_t* mbl, int32_t x,
+                                            int pc, float c) {
+  const uint32_t* row = mb_row<kDsm>(A, cl, mbl, x);
+  for (int k0 = 0; k0 <= pc; k0 += 4) {
+    uint32_t v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = k0 + j <= pc ? mb_ld<kDsm>(row + k0 + j) : 0x7f800000u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (__uint_as_float(v[j]) < c) return true;
+  }
+  return false;
+}
+
+struct CCand {
+  int32_t x, parent, edge, pc, r0;
+  uint32_t dg;
+  float cost;
+};
+
+// Target of edge e: node, cost bits, row start, out-degree | goal bit.
+__device__ __forceinline__ int4 edge_target(const ExploreArgs& A, int32_t e) {
+  if (A.etgt) return __ldg(A.etgt + e);
+  const int32_t x = A.col[e];
+  const int32_t r0 = A.row_ptr[x];
+  const uint32_t dg = (uint32_t)(A.row_ptr[x + 1] - r0) | (A.is_goal[x] ? kGoalBit : 0u);
+  return make_int4(x, __float_as_int(A.ecost[e]), r0, (int32_t)dg);
+}
+
+// Candidate c of the current group, recomputed from the group list (chunks that do not fit).
+__device__ __noinline__ CCand cand_at_c(const ExploreArgs& A, int64_t c, int32_t g) {
+  int lo = 0, hi = g;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (ld64(A.goff + mid) <= c) lo = mid; else hi = mid;
+  }
+  CCand q;
+  const int4 gi = __ldcg(A.ginfo + lo);
+  const int32_t e = gi.z + (int32_t)(c - ld64(A.goff + lo));
+  const int4 t = edge_target(A, e);
+  q.x = t.x;
+  q.parent = gi.x;
+  q.edge = e;
+  q.cost = __fadd_rn(__int_as_float(gi.w), __int_as_float(t.y));
+  q.r0 = t.z;
+  q.dg = (uint32_t)t.w;
+  int pc = 0;
+  const uint32_t* pm = A.mask + (size_t)gi.x * A.w;
+  const uint32_t* em = A.emask + (size_t)e * A.w;
+  for (int j = 0; j < A.w; ++j) pc += __popc(ldu(pm + j) | em[j]);
+  q.pc = pc;
+  return q;
+}
+
+__device__ __forceinline__ uint4 load_mask4(const uint32_t* p, int w) {
+  return make_uint4(ldu(p), w > 1 ? ldu(p + 1) : 0u, w > 2 ? ldu(p + 2) : 0u, w > 3 ? ldu(p + 3) : 0u);
+}
+
+// Warp-aggregated count of a plan toward group index i+1+q (q in [0, kWin)).
+__device__ __forceinline__ void bucket_add(bool on, int q, int deg, bool goal_stop, int32_t* cnt,
+                                           unsigned long long* dsum, uint32_t* stop_bits) {
+  const bool in = on && q >= 0 && q < kWin;
+  const unsigned act = __ballot_sync(0xffffffffu, in);
+  if (!in) return;
+  const unsigned peers = __match_any_sync(act, q);
+  const unsigned ds = __reduce_add_sync(peers, (unsigned)deg);
+  const bool st = __any_sync(peers, goal_stop);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+    atomicAdd(cnt + q, __popc(peers));
+    atomicAdd(dsum + q, (unsigned long long)ds);
+    if (st) atomicOr(stop_bits, 1u << q);
+  }
+}
+
+// Group index past the threshold table (rare; kept out of line).
+__device__ __noinline__ int32_t bucket_far(float c, double lr) { return bucket_of(c, lr); }
+
+// Group index from the iteration's threshold table (float compares; bucket_of's double
+// arithmetic is far slower on this part).  bucket_gt(c, a): least j > i + a with
+// c <= thr_j, given c > thr_{i+a}; past the table it falls back to bucket_of (same result).
+__device__ __forceinline__ int32_t bucket_gt(const CSmem* sm, const ExploreArgs& A, int32_t i, float c, int a) {
+  int b = kThr - 1;
+  if (!(c <= sm->thr[b])) return bucket_far(c, A.lr);
+  while (b - a > 1) {
+    const int m = (a + b) >> 1;
+    if (c <= sm->thr[m]) b = m; else a = m;
+  }
+  return i + b;
+}
+
+// Group index of a survivor of group i: max(bucket(c), i + 1).
+__device__ __forceinline__ int32_t eff_new(const CSmem* sm, const ExploreArgs& A, int32_t i, float c) {
+  return c <= sm->thr[1] ? i + 1 : bucket_gt(sm, A, i, c, 1);
+}
+
+// ---------------------------------------------------------------- phase A
+template <bool kDsm>
+__device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl, const St& S) {
+  const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // this CTA's counts for phase B (the copies other CTAs hold are separate)
+  if (threadIdx.x < kWin) {
+    sm->pub.ocnt[threadIdx.x] = 0;
+    sm->pub.ncnt[threadIdx.x] = 0;
+    sm->pub.odeg[threadIdx.x] = 0;
+    sm->pub.ndeg[threadIdx.x] = 0;
+  }
+  if (threadIdx.x == 0) sm->pub.stop = 0;
+  if (threadIdx.x < kThr) sm->thr[threadIdx.x] = group_thr(S.i + (int32_t)threadIdx.x, A.lr);
+  for (int64_t s = (int64_t)r * kCT + threadIdx.x; s < S.g; s += (int64_t)nr * kCT)
+    A.eexp[ld32(&A.ginfo[s].x)] = S.i;
+  const int64_t c0 = S.c0, c1 = S.c1;
+  const int64_t n = c1 - c0;
+  long long kept = 0;
+  if (n > 0 && n <= kCCap) {
+    const int w = A.w;
+    const int32_t s_end = min(sm->slot_end, S.g - 1);
+    for (int32_t s = sm->slot0 + warp; s <= s_end; s += kCW) {
+      const int slot = s % kMemCap;
+      int64_t lo_s, hi_s;
+      int4 gi;
+      uint4 pmv = make_uint4(0u, 0u, 0u, 0u);
+      const bool local = sm->mt_tag[slot] == s && sm->mt_gen[slot] == S.k;
+      if (local) {
+        lo_s = sm->mt_off[slot];
+        hi_s = lo_s + sm->mt_deg[slot];
+        gi = sm->mt_info[slot];
+        pmv = sm->mt_mask[slot];
+      } else {
+        lo_s = ld64(A.goff + s);
+        hi_s = ld64(A.goff + s + 1);
+        gi = __ldcg(A.ginfo + s);
+      }
+      if (lo_s >= c1) break;
+      const int64_t lo = max(lo_s, c0), hi = min(hi_s, c1);
+      if (lo >= hi) continue;
+      const int32_t p = gi.x, r0 = gi.z;
+      const float pcost = __int_as_float(gi.w);
+      const uint32_t* pm = A.mask + (size_t)p * w;
+      if (!local && w <= 4) {
+        const uint32_t pmw = lane < w ? ldu(pm + lane) : 0u;
+        pmv.x = __shfl_sync(0xffffffffu, pmw, 0);
+        pmv.y = __shfl_sync(0xffffffffu, pmw, 1);
+        pmv.z = __shfl_sync(0xffffffffu, pmw, 2);
+        pmv.w = __shfl_sync(0xffffffffu, pmw, 3);
+      }
+      for (int64_t c = lo + lane; c < hi; c += 32) {
+        const int32_t e = r0 + (int32_t)(c - lo_s);
+        const int4 t = edge_target(A, e);
+        const float cost = __fadd_rn(pcost, __int_as_float(t.y));
+        const int jl = (int)(c - c0);
+        int pc = 0;
+        if (w <= 4) {
+          uint4 em;
+          if (w == 4) {
+            em = __ldg(reinterpret_cast<const uint4*>(A.emask) + e);
+          } else {
+            const uint32_t* ep = A.emask + (size_t)e * w;
+            em.x = ep[0];
+            em.y = w > 1 ? ep[1] : 0u;
+            em.z = w > 2 ? ep[2] : 0u;
+            em.w = 0u;
+          }
+          const uint4 m = make_uint4(pmv.x | em.x, pmv.y | em.y, pmv.z | em.z, pmv.w | em.w);
+          pc = __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
+          sm->cmask[jl] = m;
+        } else {
+          const uint32_t* em = A.emask + (size_t)e * w;
+          for (int j = 0; j < w; ++j) pc += __popc(ldu(pm + j) | em[j]);
+        }
+        sm->cx[jl] = t.x;
+        sm->cpar[jl] = p;
+        sm->cedge[jl] = e;
+        sm->ccost[jl] = cost;
+        sm->cpc[jl] = (int16_t)pc;
+        sm->cr0[jl] = t.z;
+        sm->cdg[jl] = (uint32_t)t.w;
+        if (pc < A.kmax) {
+          atomicMin(mb_row<kDsm>(A, cl, mbl, t.x) + pc, __float_as_uint(cost));
+          ++kept;
+        }
+      }
+    }
+  } else if (n > 0) {
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += kCT) {
+      const CCand q = cand_at_c(A, c, S.g);
+      if (q.pc < A.kmax) {
+        atomicMin(mb_row<kDsm>(A, cl, mbl, q.x) + q.pc, __float_as_uint(q.cost));
+        ++kept;
+      }
+    }
+  }
+  kept = csum_ll(kept);
+  if (threadIdx.x == 0) sm->kept += kept;
+}
+
+// Older plan p: its group index if open and undominated, else -1 (see the header on older plans).
+template <bool kDsm>
+__device__ __forceinline__ int32_t old_eff_c(const ExploreArgs& A, const CSmem* sm, cg::cluster_group& cl,
+                                             uint32_t* mbl, int64_t p, int32_t i, int32_t* x_out, float* c_out,
+                                             int32_t* pc_out) {
+  const int32_t x = ld32(A.head + p);
+  const float c = ldf(A.cost + p);
+  const int32_t pc = ld32(A.popc + p);
+  const int32_t t = ld32(A.tcre + p);
+  *x_out = x;
+  *c_out = c;
+  *pc_out = pc;
+  // bucket(c) <= i iff c <= thr_i; above it the table gives the bucket
+  const int32_t b = c <= sm->thr[0] ? (t + 1 <= i ? -1 : bucket_far(c, A.lr)) : bucket_gt(sm, A, i, c, 0);
+  if (b < 0) return -1;
+  const int32_t eff = max(b, t + 1);
+  if (eff <= i) return -1;
+  if (dominated_c<kDsm>(A, cl, mbl, x, pc, c)) return -1;
+  return eff;
+}
+
+// ---------------------------------------------------------------- phase B
+template <bool kDsm>
+__device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl, const St& S) {
+  const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
+  const int64_t c0 = S.c0, c1 = S.c1;
+  const int n = (int)(c1 - c0);
+  const bool fits = n <= kCCap;
+  int32_t surv = 0, minb = kNoBucket, min_open = INT_MAX;
+  for (int t0 = 0; t0 < n; t0 += kCT) {
+    const int jl = t0 + threadIdx.x;
+    bool keep = false;
+    int32_t eff = -1, deg = 0;
+    bool gstop = false;
+    if (jl < n) {
+      CCand q;
+      if (fits) {
+        q.x = sm->cx[jl];
+        q.pc = sm->cpc[jl];
+        q.cost = sm->ccost[jl];
+        q.dg = sm->cdg[jl];
+      } else {
+        q = cand_at_c(A, c0 + jl, S.g);
+      }
+      keep = q.pc < A.kmax && !dominated_c<kDsm>(A, cl, mbl, q.x, q.pc, q.cost);
+      if (keep) {
+        eff = eff_new(sm, A, S.i, q.cost);
+        deg = (int32_t)(q.dg & ~kGoalBit);
+        ++surv;
+        minb = min(minb, eff);
+        gstop = (q.dg & kGoalBit) && q.pc < A.kmin;
+      }
+      if (fits) sm->ceff[jl] = eff;
+    }
+    bucket_add(keep, eff - S.i - 1, deg, gstop, sm->pub.ncnt, sm->pub.ndeg, &sm->pub.stop);
+  }
+  const int64_t a0 = S.a0, a1 = S.a1;
+  const bool ofits = a1 - a0 <= kOCap;
+  for (int64_t t0 = a0; t0 < a1; t0 += kCT) {
+    const int64_t p = t0 + threadIdx.x;
+    int32_t eff = -1, x = 0, pc = 0, deg = 0, r0 = 0;
+    bool goal = false;
+    float c = 0.f;
+    if (p < a1) {
+      eff = old_eff_c<kDsm>(A, sm, cl, mbl, p, S.i, &x, &c, &pc);
+      if (eff >= 0) {
+        r0 = A.row_ptr[x];
+        deg = A.row_ptr[x + 1] - r0;
+        goal = A.is_goal[x] != 0;
+        minb = min(minb, eff);
+        min_open = min(min_open, (int32_t)p);
+      }
+      if (ofits) {
+        const int o = (int)(p - a0);
+        sm->oeff[o] = eff;
+        if (eff >= 0) {
+          sm->ox[o] = x;
+          sm->ocost[o] = c;
+          sm->or0[o] = r0;
+          sm->odg[o] = (uint32_t)deg | (goal ? kGoalBit : 0u);
+          sm->opc[o] = (int16_t)pc;
+          if (A.w <= 4) sm->omask[o] = load_mask4(A.mask + (size_t)p * A.w, A.w);
+        }
+      }
+    }
+    bucket_add(eff >= 0, eff - S.i - 1, deg, goal && pc < A.kmin, sm->pub.ocnt, sm->pub.odeg, &sm->pub.stop);
+  }
+  creduce(surv, minb, min_open);
+  if (threadIdx.x == 0) {
+    sm->pub.surv = surv;
+    sm->pub.minb = minb;
+    sm->pub.min_open = min_open;
+  }
+}
+
+// Warp 0: exclusive prefix over CTAs (lanes) of v for this CTA, and the total.
+template <typename T>
+__device__ __forceinline__ void lane_prefix(T v, int r, T* before, T* total) {
+  const int lane = threadIdx.x & 31;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  *total = __shfl_sync(0xffffffffu, x, 31);
+  const T incl = __shfl_sync(0xffffffffu, x, r);
+  const T mine = __shfl_sync(0xffffffffu, v, r);
+  *before = incl - mine;
+}
+
+// Recount for a next group index beyond the window (uniform decision; one extra barrier).
+template <bool kDsm>
+__device__ __noinline__ void c_recount(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl, const St& S,
+                          int32_t nbk) {
+  const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
+  const int64_t c0 = S.c0, c1 = S.c1;
+  const int n = (int)(c1 - c0);
+  const bool fits = n <= kCCap;
+  long long nc = 0, nd = 0, oc = 0, od = 0;
+  int32_t stop = 0;
+  for (int jl = threadIdx.x; jl < n; jl += kCT) {
+    int32_t eff, pc;
+    uint32_t dg;
+    if (fits) {
+      eff = sm->ceff[jl];
+      dg = sm->cdg[jl];
+      pc = sm->cpc[jl];
+    } else {
+      const CCand q = cand_at_c(A, c0 + jl, S.g);
+      const bool keep = q.pc < A.kmax && !dominated_c<kDsm>(A, cl, mbl, q.x, q.pc, q.cost);
+      eff = keep ? eff_new(sm, A, S.i, q.cost) : -1;
+      dg = q.dg;
+      pc = q.pc;
+    }
+    if (eff == nbk) {
+      ++nc;
+      nd += dg & ~kGoalBit;
+      if ((dg & kGoalBit) && pc < A.kmin) stop = 1;
+    }
+  }
+  const int64_t a0 = S.a0, a1 = S.a1;
+  const bool ofits = a1 - a0 <= kOCap;
+  for (int64_t p = a0 + threadIdx.x; p < a1; p += kCT) {
+    int32_t eff, x = 0, pc = 0;
+    uint32_t dg = 0;
+    float c = 0.f;
+    if (ofits) {
+      eff = sm->oeff[p - a0];
+      if (eff == nbk) {
+        dg = sm->odg[p - a0];
+        pc = sm->opc[p - a0];
+      }
+    } else {
+      eff = old_eff_c<kDsm>(A, sm, cl, mbl, p, S.i, &x, &c, &pc);
+      if (eff == nbk) dg = (uint32_t)(A.row_ptr[x + 1] - A.row_ptr[x]) | (A.is_goal[x] ? kGoalBit : 0u);
+    }
+    if (eff == nbk) {
+      ++oc;
+      od += dg & ~kGoalBit;
+      if ((dg & kGoalBit) && pc < A.kmin) stop = 1;
+    }
+  }
+  nc = csum_ll(nc);
+  nd = csum_ll(nd);
+  oc = csum_ll(oc);
+  od = csum_ll(od);
+  stop = __syncthreads_or(stop);
+  if (threadIdx.x == 0) {
+    sm->pubs_s.ncnt = (int32_t)nc;
+    sm->pubs_s.ndeg = (unsigned long long)nd;
+    sm->pubs_s.ocnt = (int32_t)oc;
+    sm->pubs_s.odeg = (unsigned long long)od;
+    sm->pubs_s.stop = stop ? 1u : 0u;
+    sm->pubs_s.pad = 0u;
+  }
+}
+
+// Copies a next-group member (iteration gen) into the shared memory of every CTA whose next
+// chunk [rr per, min((rr+1) per, Cn)) holds some of its candidates [off, off + deg), and tells
+// the CTAs whose chunk starts or ends inside it.  A member without edges goes to the CTA whose
+// range holds its offset.
+__device__ __forceinline__ void send_member(CSmem* sm, cg::cluster_group& cl, int64_t Cn, int64_t per, int32_t gen,
+                                            int32_t pos, int4 info, int64_t off, int32_t deg, uint4 mask) {
+  if (per <= 0) return;
+  const int nr = (int)cl.num_blocks();
+  const int slot = pos % kMemCap;
+  int64_t first, last;
+  const int64_t end = deg > 0 ? off + deg - 1 : off;
+  if (end < (int64_t)INT_MAX && per < (int64_t)INT_MAX) {
+    first = (uint32_t)off / (uint32_t)per;
+    last = (uint32_t)end / (uint32_t)per;
+  } else {
+    first = off / per;
+    last = end / per;
+  }
+  for (int64_t rr = first; rr <= last && rr < nr; ++rr) {
+    CSmem* d = cl.map_shared_rank(sm, (unsigned)rr);
+    d->mt_info[slot] = info;
+    d->mt_off[slot] = off;
+    d->mt_deg[slot] = deg;
+    d->mt_mask[slot] = mask;
+    d->mt_tag[slot] = pos;
+    d->mt_gen[slot] = gen;
+    if (deg > 0) {
+      const int64_t lo = rr * per, hi = min((rr + 1) * per, Cn);
+      if (lo >= off) d->slot0 = pos;                      // the chunk starts inside this member
+      if (hi - 1 < off + deg && hi > lo) d->slot_end = pos;  // and ends inside it
+    }
+  }
+}
+
+// ---------------------------------------------------------------- phase C
+template <bool kDsm>
+__device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl, St& S) {
+  const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // Warp 0 reads every CTA's counts (lane l from CTA l) and derives the cluster-wide values.
+  if (warp == 0) {
+    const bool on = lane < nr;
+    const Pub* rp = cl.map_shared_rank(&sm->pub, (unsigned)(on ? lane : 0));
+    int32_t minb = on ? rp->minb : kNoBucket;
+    int32_t mo = on ? rp->min_open : INT_MAX;
+    const int32_t sv = on ? rp->surv : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
+      mo = min(mo, __shfl_xor_sync(0xffffffffu, mo, o));
+    }
+    int32_t bs, ts;
+    lane_prefix<int32_t>(sv, r, &bs, &ts);
+    const int32_t q = minb == kNoBucket ? -1 : minb - S.i - 1;
+    const bool fast = minb == kNoBucket || (q >= 0 && q < kWin);
+    int32_t bo = 0, to = 0, bn = 0, tn = 0;
+    long long dbo = 0, dto = 0, dbn = 0, dtn = 0;
+    bool stp = false;
+    if (minb != kNoBucket && fast) {
+      const int32_t oc = on ? rp->ocnt[q] : 0, nc = on ? rp->ncnt[q] : 0;
+      const long long od = on ? (long long)rp->odeg[q] : 0, nd = on ? (long long)rp->ndeg[q] : 0;
+      const bool sb = on && ((rp->stop >> q) & 1u);
+      lane_prefix<int32_t>(oc, r, &bo, &to);
+      lane_prefix<int32_t>(nc, r, &bn, &tn);
+      lane_prefix<long long>(od, r, &dbo, &dto);
+      lane_prefix<long long>(nd, r, &dbn, &dtn);
+      stp = __any_sync(0xffffffffu, sb);
+    }
+    if (lane == 0) {
+      sm->b_nbk = minb;
+      sm->b_min_open = mo;
+      sm->b_before_s = bs;
+      sm->b_total_s = ts;
+      sm->b_fast = fast ? 1 : 0;
+      sm->b_before_o = bo;
+      sm->b_total_o = to;
+      sm->b_before_n = bn;
+      sm->b_total_n = tn;
+      sm->b_dbefore_o = dbo;
+      sm->b_dtotal_o = dto;
+      sm->b_dbefore_n = dbn;
+      sm->b_dtotal_n = dtn;
+      sm->b_stop = stp ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  const int32_t nbk = sm->b_nbk;
+  if (!sm->b_fast) {
+    // every CTA takes this branch together: nbk is the same everywhere
+    c_recount<kDsm>(A, sm, mbl, cl, S, nbk);
+    cl.sync();
+    if (warp == 0) {
+      const bool on = lane < nr;
+      const PubS* rs = cl.map_shared_rank(&sm->pubs_s, (unsigned)(on ? lane : 0));
+      const int32_t oc = on ? rs->ocnt : 0, nc = on ? rs->ncnt : 0;
+      const long long od = on ? (long long)rs->odeg : 0, nd = on ? (long long)rs->ndeg : 0;
+      const bool sb = on && rs->stop;
+      int32_t bo, to, bn, tn;
+      long long dbo, dto, dbn, dtn;
+      lane_prefix<int32_t>(oc, r, &bo, &to);
+      lane_prefix<int32_t>(nc, r, &bn, &tn);
+      lane_prefix<long long>(od, r, &dbo, &dto);
+      lane_prefix<long long>(nd, r, &dbn, &dtn);
+      const bool stp = __any_sync(0xffffffffu, sb);
+      if (lane == 0) {
+        sm->b_before_o = bo;
+        sm->b_total_o = to;
+        sm->b_before_n = bn;
+        sm->b_total_n = tn;
+        sm->b_dbefore_o = dbo;
+        sm->b_dtotal_o = dto;
+        sm->b_dbefore_n = dbn;
+        sm->b_dtotal_n = dtn;
+        sm->b_stop = stp ? 1 : 0;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const long long Cn = nbk != kNoBucket ? sm->b_dtotal_o + sm->b_dtotal_n : 0;
+    sm->b_per_n = (Cn + nr - 1) / nr;
+  }
+  __syncthreads();
+  const int32_t total_s = sm->b_total_s, before_s = sm->b_before_s;
+  const int32_t total_o = sm->b_total_o, before_o = sm->b_before_o;
+  const int32_t total_n = sm->b_total_n, before_n = sm->b_before_n;
+  const long long dtotal_o = sm->b_dtotal_o, dbefore_o = sm->b_dbefore_o;
+  const long long dtotal_n = sm->b_dtotal_n, dbefore_n = sm->b_dbefore_n;
+  const bool stop_any = sm->b_stop != 0;
+  const int32_t min_open = sm->b_min_open;
+  if (S.base + total_s > A.cap) {
+    __syncthreads();
+    if (threadIdx.x == 0) S.status = PUMP_ERR_CAPACITY;
+    __syncthreads();
+    return;
+  }
+  const bool has_next = nbk != kNoBucket;
+  const int64_t Cn = has_next ? dtotal_o + dtotal_n : 0;
+  const int64_t per_n = sm->b_per_n;
+  const bool small_w = A.w <= 4;
+  // survivors to the arena, members among them to the group list
+  const int64_t c0 = S.c0, c1 = S.c1;
+  const int n = (int)(c1 - c0);
+  const bool fits = n <= kCCap;
+  // Chunks larger than the cache recompute their candidates from the group list, which this
+  // phase overwrites with the next group: then survivors are written first, and after a barrier
+  // (taken by every CTA: `big` is the same everywhere) the members are read back from the arena.
+  const bool big = S.big != 0;
+  int64_t run = S.base + before_s;
+  int64_t mrun = total_o + before_n;
+  int64_t drun = dtotal_o + dbefore_n;
+  for (int t0 = 0; t0 < n; t0 += kCT) {
+    const int jl = t0 + threadIdx.x;
+    bool keep = false;
+    int32_t eff = -1;
+    CCand q;
+    q.x = q.parent = q.edge = q.pc = q.r0 = 0;
+    q.dg = 0u;
+    q.cost = 0.f;
+    if (jl < n) {
+      if (fits) {
+        eff = sm->ceff[jl];
+        keep = eff >= 0;
+        if (keep) {
+          q.x = sm->cx[jl];
+          q.parent = sm->cpar[jl];
+          q.edge = sm->cedge[jl];
+          q.cost = sm->ccost[jl];
+          q.pc = sm->cpc[jl];
+          q.r0 = sm->cr0[jl];
+          q.dg = sm->cdg[jl];
+        }
+      } else {
+        q = cand_at_c(A, c0 + jl, S.g);
+        keep = q.pc < A.kmax && !dominated_c<kDsm>(A, cl, mbl, q.x, q.pc, q.cost);
+        if (keep) eff = eff_new(sm, A, S.i, q.cost);
+      }
+    }
+    const int32_t deg = (int32_t)(q.dg & ~kGoalBit);
+    const bool member = !big && keep && eff == nbk;
+    int64_t tk;
+    const int64_t rk = cscan<int64_t>((keep ? (int64_t(1) << 52) : 0) | (member ? pack_cd(1, deg) : 0), &tk);
+    if (keep) {
+      const int64_t id = run + pack_k(rk);
+      A.head[id] = q.x;
+      A.parent[id] = q.parent;
+      A.pedge[id] = q.edge;
+      A.cost[id] = q.cost;
+      A.popc[id] = q.pc;
+      A.tcre[id] = S.i;
+      A.eexp[id] = -1;
+      uint32_t* om = A.mask + (size_t)id * A.w;
+      uint4 m = make_uint4(0u, 0u, 0u, 0u);
+      if (fits && small_w) {
+        m = sm->cmask[jl];
+        if (A.w == 4) {
+          *reinterpret_cast<uint4*>(om) = m;
+        } else {
+          om[0] = m.x;
+          if (A.w > 1) om[1] = m.y;
+          if (A.w > 2) om[2] = m.z;
+        }
+      } else {
+        const uint32_t* pm = A.mask + (size_t)q.parent * A.w;
+        const uint32_t* em = A.emask + (size_t)q.edge * A.w;
+        for (int j = 0; j < A.w; ++j) om[j] = ldu(pm + j) | em[j];
+      }
+      if (q.dg & kGoalBit) {
+        const int slot = atomicAdd(&A.ctl->n_goal_all, 1);
+        A.goal_all[slot] = (int32_t)id;
+      }
+      if (member) {
+        const int64_t pos = mrun + pack_c(rk);
+        const int64_t off = drun + pack_d(rk);
+        const int4 info = make_int4((int32_t)id, q.x, q.r0, __float_as_int(q.cost));
+        A.ginfo[pos] = info;
+        A.goff[pos] = off;
+        send_member(sm, cl, Cn, per_n, S.k + 1, (int32_t)pos, info, off, deg, m);
+      }
+    }
+    run += pack_k(tk);
+    mrun += pack_c(tk);
+    drun += pack_d(tk);
+  }
+  if (big) {
+    cl.sync();
+    const int32_t mine = sm->pub.surv;
+    const int64_t id0 = S.base + before_s;
+    for (int t0 = 0; t0 < mine; t0 += kCT) {
+      const int k = t0 + threadIdx.x;
+      bool sel = false;
+      int32_t x = 0, r0 = 0, deg = 0;
+      float c = 0.f;
+      if (k < mine) {
+        c = ldf(A.cost + id0 + k);
+        sel = has_next && eff_new(sm, A, S.i, c) == nbk;
+        if (sel) {
+          x = ld32(A.head + id0 + k);
+          r0 = A.row_ptr[x];
+          deg = A.row_ptr[x + 1] - r0;
+        }
+      }
+      int64_t tm;
+      const int64_t mr = cscan<int64_t>(sel ? pack_cd(1, deg) : 0, &tm);
+      if (sel) {
+        const int64_t pos = mrun + pack_c(mr);
+        const int64_t off = drun + pack_d(mr);
+        const int4 info = make_int4((int32_t)(id0 + k), x, r0, __float_as_int(c));
+        A.ginfo[pos] = info;
+        A.goff[pos] = off;
+        const uint4 m = small_w ? load_mask4(A.mask + (size_t)(id0 + k) * A.w, A.w) : make_uint4(0u, 0u, 0u, 0u);
+        send_member(sm, cl, Cn, per_n, S.k + 1, (int32_t)pos, info, off, deg, m);
+      }
+      mrun += pack_c(tm);
+      drun += pack_d(tm);
+    }
+  }
+  // older members (ids below every survivor's) come first in the next group
+  if (has_next) {
+    const int64_t a0 = S.a0, a1 = S.a1;
+    const bool ofits = a1 - a0 <= kOCap;
+    int64_t orun = before_o, odrun = dbefore_o;
+    for (int64_t t0 = a0; t0 < a1; t0 += kCT) {
+      const int64_t p = t0 + threadIdx.x;
+      bool sel = false;
+      int32_t x = 0, r0 = 0, deg = 0;
+      float c = 0.f;
+      uint4 m = make_uint4(0u, 0u, 0u, 0u);
+      if (p < a1) {
+        int32_t eff;
+        if (ofits) {
+          const int o = (int)(p - a0);
+          eff = sm->oeff[o];
+          if (eff == nbk) {
+            x = sm->ox[o];
+            c = sm->ocost[o];
+            r0 = sm->or0[o];
+            deg = (int32_t)(sm->odg[o] & ~kGoalBit);
+            if (small_w) m = sm->omask[o];
+          }
+        } else {
+          int32_t pc;
+          eff = old_eff_c<kDsm>(A, sm, cl, mbl, p, S.i, &x, &c, &pc);
+          if (eff == nbk) {
+            r0 = A.row_ptr[x];
+            deg = A.row_ptr[x + 1] - r0;
+            if (small_w) m = load_mask4(A.mask + (size_t)p * A.w, A.w);
+          }
+        }
+        sel = eff == nbk;
+      }
+      int64_t tpk;
+      const int64_t rpk = cscan<int64_t>(sel ? pack_cd(1, deg) : 0, &tpk);
+      if (sel) {
+        const int64_t pos = orun + pack_c(rpk);
+        const int64_t off = odrun + pack_d(rpk);
+        const int4 info = make_int4((int32_t)p, x, r0, __float_as_int(c));
+        A.ginfo[pos] = info;
+        A.goff[pos] = off;
+        send_member(sm, cl, Cn, per_n, S.k + 1, (int32_t)pos, info, off, deg, m);
+      }
+      orun += pack_c(tpk);
+      odrun += pack_d(tpk);
+    }
+  }
+  const int32_t gn = has_next ? total_o + total_n : 0;
+  if (r == 0 && threadIdx.x == 0) A.goff[gn] = Cn;
+  // next state (the same in every CTA of the cluster)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S.lo = min((int64_t)min_open, S.base);
+    S.base += total_s;
+    S.g = gn;
+    S.C = Cn;
+    S.i = has_next ? nbk : S.i + 1;
+    S.stop = A.early_stop && stop_any ? 1 : 0;
+  }
+  __syncthreads();
+}
+
+template <bool kDsm>
+__global__ void __launch_bounds__(kCT, 1) k_explore_cluster(ExploreArgs A, int32_t start) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
+  uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
+  ExploreCtl* ctl = A.ctl;
+  if (kDsm) {
+    const int rows = (A.n + nr - 1) / nr;
+    for (int k = threadIdx.x; k < rows * A.kstride; k += kCT) mbl[k] = 0x7f800000u;  // +inf
+  }
+  for (int k = threadIdx.x; k < kMemCap; k += kCT) {
+    sm->mt_tag[k] = -1;
+    sm->mt_gen[k] = -1;
+  }
+  if (threadIdx.x == 0) {
+    sm->slot0 = 0;  // group 0 is the root alone
+    sm->slot_end = 0;
+    sm->kept = 0;
+  }
+  __syncthreads();
+  if (kDsm && start % nr == r && threadIdx.x == 0) mbl[(size_t)(start / nr) * A.kstride] = 0u;  // root: cost 0
+  St& S = sm->st;
+  if (threadIdx.x == 0) {
+    S.C = ld64(&ctl->st[0].group_cands);
+    S.g = ld32(&ctl->st[0].group_size);
+    S.i = ld32(&ctl->st[0].iter);
+    S.stop = ld32(&ctl->st[0].stop);
+    S.base = ld64(&ctl->n_plans);
+    S.lo = 0;
+    S.ncand = 0;
+    S.status = 0;
+    S.n_groups = 0;
+    S.k = 0;
+  }
+  cl.sync();
+  int k = 0;
+  for (;; ++k) {
+    if (S.status || S.stop || S.g == 0) break;
+    // every iteration expands at least one plan that no later group holds, so k is also
+    // bounded by the arena; both caps end the run with the same status
+    if (S.i >= A.max_iter || k >= A.max_iter) {
+      __syncthreads();
+      if (threadIdx.x == 0) S.status = PUMP_ERR_TIMEOUT;
+      __syncthreads();
+      break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      S.k = k;
+      S.ncand += S.C;
+      ++S.n_groups;
+      chunk(S.C, r, nr, &S.c0, &S.c1);
+      chunk(S.base - S.lo, r, nr, &S.a0, &S.a1);
+      S.a0 += S.lo;
+      S.a1 += S.lo;
+      S.big = (S.C + nr - 1) / nr > kCCap ? 1 : 0;
+    }
+    __syncthreads();
+    c_expand<kDsm>(A, sm, mbl, cl, S);
+    cl.sync();
+    c_filter<kDsm>(A, sm, mbl, cl, S);
+    cl.sync();
+    c_write<kDsm>(A, sm, mbl, cl, S);
+    cl.sync();
+  }
+  if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->n_kept), (unsigned long long)sm->kept);
+  if (r == 0 && threadIdx.x == 0) {
+    ctl->n_plans = S.base;
+    ctl->n_candidates = S.ncand;
+    ctl->n_groups = S.n_groups;
+    ctl->status = S.status;
+    ctl->iter = S.i;
+    ctl->survivors = 0;
+    ctl->k_exit = k;
+  }
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
+}
+
+// Per edge: target node, edge cost bits, target row start, target out-degree | goal bit.
+__global__ void k_edge_targets(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                               const float* __restrict__ ecost, const uint8_t* __restrict__ is_goal, int32_t E,
+                               int4* __restrict__ out) {
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const int32_t x = col[e];
+    const int32_t r0 = row_ptr[x];
+    const uint32_t dg = (uint32_t)(row_ptr[x + 1] - r0) | (is_goal[x] ? kGoalBit : 0u);
+    out[e] = make_int4(x, __float_as_int(ecost[e]), r0, (int32_t)dg);
+  }
+}
+
+size_t cluster_smem_bytes(int n, int kstride, int nr, bool dsm) {
+  size_t b = (sizeof(CSmem) + 15) & ~size_t(15);
+  if (dsm) b += sizeof(uint32_t) * (size_t)((n + nr - 1) / nr) * kstride;
+  return b;
+}
+
+template <bool kDsm>
+int try_cluster_size(int nr, size_t smem, cudaStream_t s, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+  auto kern = k_explore_cluster<kDsm>;
+  // one ceiling for every configuration (the attribute belongs to the kernel, not to a launch)
+  if (smem > kDynSmemMax ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmemMax) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (nr > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cfg->gridDim = dim3(nr);
+  cfg->blockDim = dim3(kCT);
+  cfg->dynamicSmemBytes = smem;
+  cfg->stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nr;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, kern, cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nclusters;
+}
+
+// Cluster size: PUMP_EXPLORE_CLUSTER overrides (0 disables the cluster kernel), and
+// PUMP_EXPLORE_MBEST_GLOBAL=1 keeps the dominance table in global memory.  Both are read on
+// every call (tuning and tests).
+int cluster_env() {
+  const char* e = getenv("PUMP_EXPLORE_CLUSTER");
+  return e ? atoi(e) : -1;
+}
+
+bool mbest_global_env() {
+  const char* e = getenv("PUMP_EXPLORE_MBEST_GLOBAL");
+  return e && atoi(e) != 0;
+}
+
+// Cluster form for a run: size and where mbest lives.  The device check (attributes and the
+// occupancy query) is done once per device and configuration and remembered.
+struct ClusterChoice {
+  int dev, nr, kstride_rows;  // key: device, cluster size, mbest words per CTA (0: global)
+  size_t smem;
+  int ok;
+};
+
+std::mutex g_choice_mu;
+std::vector<ClusterChoice> g_choices;
+
+int cluster_ok(int dev, int nr, bool dsm, size_t smem, int words) {
+  {
+    std::lock_guard<std::mutex> lk(g_choice_mu);
+    for (const auto& c : g_choices)
+      if (c.dev == dev && c.nr == nr && c.kstride_rows == (dsm ? words : 0) && c.smem == smem) return c.ok;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  const int ok = (dsm ? try_cluster_size<true>(nr, smem, 0, &cfg, attr) : try_cluster_size<false>(nr, smem, 0, &cfg, attr)) >= 1;
+  std::lock_guard<std::mutex> lk(g_choice_mu);
+  g_choices.push_back({dev, nr, dsm ? words : 0, smem, ok ? 1 : 0});
+  return ok;
+}
+
+}  // namespace
+
+// Edge targets of a graph (computed once; the graph's arrays do not change afterwards).
+int ensure_edge_targets(pump_graph* g, cudaStream_t s) {
+  if (g->etgt || g->E == 0) return PUMP_OK;
+  g->etgt = (int4*)graph_alloc(g, sizeof(int4) * (size_t)g->E, s);
+  if (!g->etgt) return PUMP_ERR_OOM;
+  const int blocks = (int)std::min<int64_t>(((int64_t)g->E + 255) / 256, 4096);
+  k_edge_targets<<<blocks, 256, 0, s>>>(g->row_ptr, g->col, g->ecost, g->is_goal, g->E, g->etgt);
+  note_launch();
+  PUMP_CUDA_TRY(cudaGetLastError());
+  return PUMP_OK;
+}
+
+// Picks the cluster form for a run: *nr = cluster size (0 when no cluster form fits the device)
+// and *dsm = mbest in distributed shared memory.
+int plan_explore_cluster(const ExploreArgs& A, int* nr_out, bool* dsm_out) {
+  *nr_out = 0;
+  *dsm_out = false;
+  const int env = cluster_env();
+  if (env == 0) return PUMP_OK;
+  int sizes[3] = {16, 8, 4};
+  int n_sizes = 3;
+  if (env > 0) {
+    if (env > kMaxCluster) return PUMP_OK;
+    sizes[0] = env;
+    n_sizes = 1;
+  }
+  int dev = 0;
+  PUMP_CUDA_TRY(cudaGetDevice(&dev));
+  const size_t fixed = cluster_smem_bytes(A.n, A.kstride, 1, false);
+  for (int t = 0; t < n_sizes; ++t) {
+    const int nr = sizes[t];
+    const int words = ((A.n + nr - 1) / nr) * A.kstride;
+    const bool dsm = !mbest_global_env() && fixed + sizeof(uint32_t) * (size_t)words + 4096 <= kSmemLimit;
+    const size_t smem = cluster_smem_bytes(A.n, A.kstride, nr, dsm);
+    if (cluster_ok(dev, nr, dsm, smem, words)) {
+      *nr_out = nr;
+      *dsm_out = dsm;
+      return PUMP_OK;
+    }
+  }
+  return PUMP_OK;
+}
+
+// Launches the cluster kernel in the form plan_explore_cluster chose.
+int run_explore_cluster(pump_graph* g, const ExploreArgs& A, int nr, bool dsm, cudaStream_t s) {
+  const size_t smem = cluster_smem_bytes(A.n, A.kstride, nr, dsm);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nr);
+  cfg.blockDim = dim3(kCT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nr;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int32_t start = g->start;
+  cudaError_t e;
+  if (dsm)
+    e = cudaLaunchKernelEx(&cfg, k_explore_cluster<true>, A, start);
+  else
+    e = cudaLaunchKernelEx(&cfg, k_explore_cluster<false>, A, start);
+  note_launch();
+  return e == cudaSuccess ? PUMP_OK : PUMP_ERR_CUDA;
+}
+
+}  // namespace pump

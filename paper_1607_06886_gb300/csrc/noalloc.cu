@@ -23,7 +23,6 @@
 #include "pump_internal.cuh"
 
 namespace pump {
-int run_explore_kernels(pump_graph* g, const ExploreArgs& A, bool stepwise, cudaStream_t s);
 int run_goal_finalize(pump_graph* g, const ExploreArgs& A, cudaStream_t s);
 }  // namespace pump
 
@@ -130,6 +129,7 @@ extern "C" int pump_explore_noalloc(int32_t n, const int32_t* row_ptr, const int
   A.ginfo = reinterpret_cast<int4*>(carve(sizeof(int4) * (size_t)capacity));
   A.pedge = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)capacity));
   A.goal_all = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)capacity));
+  A.etgt = nullptr;  // edge targets are read from the graph arrays
   A.goff = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * ((size_t)capacity + 1)));
   A.row_ptr = row_ptr;
   A.col = col;
@@ -159,7 +159,7 @@ extern "C" int pump_explore_noalloc(int32_t n, const int32_t* row_ptr, const int
   shell.n = n;
   shell.start = start_idx;
   shell.ex.goal_sorted = goal_plans;
-  rc = run_explore_kernels(&shell, A, (p->flags & PUMP_STEPWISE) != 0, s);
+  rc = run_explore_kernels(&shell, A, explore_mode(p->flags), s);
   if (!rc) rc = run_goal_finalize(&shell, A, s);
   if (rc) return rc;
   ExploreCtl h;

@@ -15,7 +15,6 @@
 
 namespace pump {
 
-int run_explore_kernels(pump_graph* g, const ExploreArgs& A, bool stepwise, cudaStream_t s);
 int run_goal_finalize(pump_graph* g, const ExploreArgs& A, cudaStream_t s);
 int launch_node_flags(pump_graph* g, const int32_t* goal_dev, cudaStream_t s);
 int launch_transpose_xi(pump_graph* g, const float* xi_dev, cudaStream_t s);
@@ -184,7 +183,10 @@ int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_pla
   A.spin_limit = 20000000ll;
   A.kstride = std::max(kmax, 1);
   A.kmax = kmax;
-  rc = run_explore_kernels(g, A, (p->flags & PUMP_STEPWISE) != 0, s);
+  rc = ensure_edge_targets(g, s);
+  if (rc) return rc;
+  A.etgt = g->etgt;
+  rc = run_explore_kernels(g, A, explore_mode(p->flags), s);
   if (rc) return rc;
   rc = run_goal_finalize(g, A, s);
   if (rc) return rc;

@@ -92,6 +92,7 @@ struct ExploreArgs {
   int32_t* group;
   int4* ginfo;      // per group slot: plan id, head node, row start, cost bits
   int64_t* goff;    // group_size + 1 candidate offsets
+  const int4* etgt; // per edge: target node, cost bits, target row start, degree | goal bit (or null)
   int32_t* bcnt;    // per-block survivor / selection counts
   int64_t* bdeg;    // per-block degree sums
   int32_t* goal_all;
@@ -164,6 +165,7 @@ struct pump_graph {
   float* nom = nullptr;      // E x W x 3
   uint32_t* emask = nullptr; // E x n_words
   float* ibox = nullptr;     // E x 6: box holding every particle position of the edge
+  int4* etgt = nullptr;      // E: target node, cost bits, target row start, degree | goal bit
   std::vector<pump::DevBuf> bufs;
   pump::ExploreBufs ex;
   // last explore
@@ -196,6 +198,12 @@ int run_select(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t 
 int run_certify_path(pump_graph* g, const int32_t* path_host, int32_t path_len, int32_t n_mc,
                      int32_t substeps, uint64_t seed, int64_t* n_collide, cudaStream_t s);
 int ensure_explore_bufs(pump_graph* g, int64_t cap, int32_t kmax, cudaStream_t s);
+int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStream_t s);
+int ensure_edge_targets(pump_graph* g, cudaStream_t s);
+// Explore kernel form from pump_plan_params.flags (see run_explore_kernels).
+inline int explore_mode(int32_t flags) {
+  return (flags & PUMP_STEPWISE) ? 2 : ((flags & PUMP_EXPLORE_GRID) ? 1 : 0);
+}
 int num_sms();
 
 // ---------------------------------------------------------------------------

@@ -18,7 +18,7 @@ from . import build as _build
 
 # status codes
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_INFEASIBLE = range(7)
-NO_EARLY_STOP, EXPLORE_ONLY, STEPWISE = 1, 2, 4
+NO_EARLY_STOP, EXPLORE_ONLY, STEPWISE, EXPLORE_GRID = 1, 2, 4, 8
 
 EXPORT = {
     "counts": 0, "node_valid": 1, "row_ptr": 2, "col": 3, "ecost": 4, "tau": 5, "h": 6, "phi": 7, "L": 8,

@@ -2,9 +2,11 @@
 
 Both sides receive the same seeded random graph (CSR, edge costs, edge masks) and must produce
 the same arena: plan ids, heads, parents, cost bits, masks, creation and expansion group indices,
-the same P_goal in PlanSelection order, and the same counters.  Covers the persistent cooperative
-kernel and the stepwise launches, several particle counts, CP cutoffs, early stop on and off, and
-the degenerate cases."""
+the same P_goal in PlanSelection order, and the same counters.  Covers the thread-block cluster
+kernel (cluster sizes 16, 8 and 4; dominance table on chip and in global memory; groups larger than
+the on-chip candidate cache; next group indices beyond the counted window), the grid-wide
+cooperative kernel and the stepwise launches, several particle counts, CP cutoffs, early stop on
+and off, and the degenerate cases."""
 import numpy as np
 import pytest
 
@@ -48,17 +50,17 @@ CASES = [
     (250, 10, 1024, 0.02, 2.0, 1.0, pump.NO_EARLY_STOP, 6),
     (800, 30, 128, 0.05, 2.0, 0.5, pump.NO_EARLY_STOP, 7),
     (300, 12, 32, 0.5, 2.0, 0.5, pump.NO_EARLY_STOP, 8),
+    (300, 12, 32, 0.05, 2.0, 0.004, pump.NO_EARLY_STOP, 12),
 ]
 
+MODES = {"cluster": 0, "grid": pump.EXPLORE_GRID, "stepwise": pump.STEPWISE}
 
-@pytest.mark.parametrize("stepwise", [False, True])
-@pytest.mark.parametrize("n,deg,N,alpha,eta,lam,flags,seed", CASES)
-def test_explore_bit_exact(n, deg, N, alpha, eta, lam, flags, seed, stepwise):
+
+def check_explore(n, deg, N, alpha, eta, lam, flags, seed):
     g = inputs.random_explore_graph(n, deg, N, seed, radius=1.3, bit_prob=0.01, hot_edge_frac=0.08,
                                     hot_bit_prob=0.15)
     goal = [n - 1, n - 2, n // 2]
-    f = flags | (pump.STEPWISE if stepwise else 0)
-    G, st, ex = run_both(g, 0, goal, alpha, eta, lam, flags=f)
+    G, st, ex = run_both(g, 0, goal, alpha, eta, lam, flags=flags)
     assert st["rc"] == pump.OK and ex["status"] == cpu.OK
     assert ex["n_plans"] > 1
     assert st["n_plans"] == ex["n_plans"]
@@ -67,6 +69,37 @@ def test_explore_bit_exact(n, deg, N, alpha, eta, lam, flags, seed, stepwise):
     assert st["n_iterations"] == ex["n_iterations"]
     assert st["n_groups"] == ex["n_groups_expanded"]
     assert st["n_goal"] == ex["n_goal"]
+    assert_arena_equal({k: G.export(k) for k in ("plan_head", "plan_parent", "plan_cost", "plan_mask", "plan_popc",
+                                                 "plan_created", "plan_expanded", "goal_plans")}, ex, g.n_words)
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("n,deg,N,alpha,eta,lam,flags,seed", CASES)
+def test_explore_bit_exact(n, deg, N, alpha, eta, lam, flags, seed, mode):
+    check_explore(n, deg, N, alpha, eta, lam, flags | MODES[mode], seed)
+
+
+@pytest.mark.parametrize("cluster,mbest_global", [(8, False), (4, False), (16, True), (4, True)])
+@pytest.mark.parametrize("case", [1, 4, 6, 7, 9])
+def test_explore_cluster_forms(monkeypatch, cluster, mbest_global, case):
+    """The cluster kernel at other cluster sizes and with the dominance table in global memory."""
+    monkeypatch.setenv("PUMP_EXPLORE_CLUSTER", str(cluster))
+    monkeypatch.setenv("PUMP_EXPLORE_MBEST_GLOBAL", "1" if mbest_global else "0")
+    check_explore(*CASES[case])
+
+
+def test_explore_cluster_large_groups(monkeypatch):
+    """Groups with more candidates than four CTAs cache on chip: candidates are recomputed from the
+    group list and members read back from the arena after an extra barrier."""
+    monkeypatch.setenv("PUMP_EXPLORE_CLUSTER", "4")
+    g = inputs.random_explore_graph(4002, 33, 128, 11, radius=1.25, bit_prob=0.003, hot_edge_frac=0.05,
+                                    hot_bit_prob=0.1)
+    G, st, ex = run_both(g, 0, [1, 2, 3], 0.01, 2.0, 0.5, flags=pump.NO_EARLY_STOP)
+    assert st["rc"] == pump.OK and st["n_candidates"] == ex["n_candidates"]
+    cre, exp_ = ex["t_created"], ex["e_expanded"]
+    deg = np.diff(g.row_ptr)
+    per_group = np.bincount(exp_[exp_ >= 0], weights=deg[ex["head"][exp_ >= 0]])
+    assert per_group.max() > 4 * 2048
     assert_arena_equal({k: G.export(k) for k in ("plan_head", "plan_parent", "plan_cost", "plan_mask", "plan_popc",
                                                  "plan_created", "plan_expanded", "goal_plans")}, ex, g.n_words)
 
