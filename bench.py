@@ -211,6 +211,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="indoor_4k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-queries", type=int, default=256,
+                    help="queries of the batched leg (uneven sizes, one persistent Explore launch); 0 skips it")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -341,6 +343,8 @@ def main():
         "roofline": roof,
         "kernels": kernel_detail,
     }
+    if args.batch_queries > 0:
+        line["batched"] = batched_measure(pump, args, dev, flush, rank, ws)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import cpu
         cpu.build()
@@ -369,6 +373,66 @@ def measured_traffic(kernel):
     if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
         return None
     return float(rec["dram_bytes_per_launch"])
+
+
+def batched_measure(pump, args, dev, flush, rank, ws):
+    """The batched form: args.batch_queries independent queries of uneven size (samples
+    U{1000..8000}, boxes U{5..50}, N in {64, 128, 256}, W = 10, CP target 1 %), graphs resident,
+    each step = edge masks of every query + all Explore runs in one persistent launch
+    (pump_plan_batch, Explore only).  The launch form comes from the autotuner.  Also times the
+    same queries one after another through the single-query call."""
+    import torch
+    from paper_1607_06886_gb300 import autotune, inputs
+    nq = args.batch_queries
+    wls = inputs.batch_workloads(nq, seed=1000 * (rank + 1))
+    todev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    Gs = [pump.Graph.build(todev(w.states), todev(w.goal_idx), todev(w.boxes), todev(w.xi), w.radius, w.n_particles,
+                           w.n_waypoints, w.sigma) for w in wls]
+    prms = [pump.default_plan_params(alpha=w.alpha, eta=w.eta, lam=w.lam, n_mc=w.n_mc, mc_substeps=w.mc_substeps,
+                                     mc_seed=w.mc_seed, flags=pump.EXPLORE_ONLY) for w in wls]
+    cfg, rec = autotune.tune_batch(Gs, prms)
+    stream = torch.cuda.current_stream()
+    # the same queries one at a time through pump_plan (reference for the batched launch)
+    flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    single = [G.plan(p) for G, p in zip(Gs, prms)]
+    b.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b)
+    reps, times, res = max(3, min(args.steps, 5)), [], None
+    for k in range(reps + 1):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(ws)
+        a.record(stream)
+        rc, res = pump.plan_batch(Gs, prms, cfg)
+        b.record(stream)
+        torch.cuda.synchronize()
+        assert rc == pump.OK, rc
+        if k:
+            times.append(a.elapsed_time(b))
+    same = all(r["n_candidates"] == q["n_candidates"] and r["n_plans"] == q["n_plans"] for r, q in zip(res, single))
+    ms = max_over_ranks(float(np.median(times)), ws)
+    cands = sum(r["n_candidates"] for r in res)
+    plans = sum(r["n_plans"] for r in res)
+    ms_expl, ms_mask = res[0]["ms_explore"], res[0]["ms_masks"]
+    # expansion proper against HBM: algorithmic bytes per candidate and per kept plan (as for the
+    # single query), over all queries, divided by the batched Explore launch's time
+    nbytes = sum(r["n_candidates"] * (12 + 4 * (G.counts()[4] // 32)) + r["n_plans"] * (28 + 4 * (G.counts()[4] // 32))
+                 for r, G in zip(res, Gs))
+    hbm = float(load_peaks()["hbm_gbs"])
+    out = {"workload": f"batch_{nq}", "queries": nq, "value": sum_over_ranks(cands, ws) / (ms / 1e3),
+           "unit": "partial_plans/s", "ms_per_batch": ms, "ms_masks": ms_mask, "ms_explore": ms_expl,
+           "partial_plans": cands, "plans": plans, "edges": int(sum(int(G.counts()[1]) for G in Gs)),
+           "single_queries_ms": seq_ms, "speedup_vs_single_queries": seq_ms / ms, "results_equal_single": bool(same),
+           "launch": {"cluster_size": cfg.cluster_size, "mbest_global": cfg.mbest_global, "tuned_ms": rec.get("explore_ms")},
+           "explore_roofline": {"bound": "hbm", "achieved": nbytes / (ms_expl / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                "frac": nbytes / (ms_expl / 1e3) / 1e9 / hbm},
+           "inputs": "seeded synthetic: samples U{1000..8000}, boxes U{5..50}, N in {64,128,256}, W=10, CP 1%"}
+    for G in Gs:
+        G.close()
+    return out
 
 
 def roofline_measure(pump, G, prm, wl, dev, flush, steps):

@@ -202,6 +202,33 @@ int pump_plan(pump_graph* g, const pump_plan_params* params, int32_t* path, int3
               pump_plan_result* out, void* stream);
 
 /* --------------------------------------------------------------------------
+ * pump_plan_batch: pump_plan for n_queries independent queries, one per
+ * built graph, with the Explore runs of all queries in one persistent launch
+ * (no counterpart in the paper: a throughput form of Algorithm 2 for many
+ * problems at once).  graphs[q] (distinct, built by pump_graph_build) is
+ * planned with params[q]; results[q] receives what pump_plan would write for
+ * it (the selected path is left in the graph: pump_export of the plan arrays
+ * and goal plans), except that ms_masks / ms_explore / ms_select are the
+ * whole batch's phase times.  Each result equals the single-query result:
+ * every query runs exactly the single-query algorithm, only concurrently.
+ * `config` (may be NULL) chooses the form of the Explore launch:
+ */
+typedef struct {
+  int32_t cluster_size; /* CTAs per query: 16, 8 or 4; 0 = the largest the device co-schedules */
+  int32_t mbest_global; /* 1: dominance tables in global memory instead of on chip             */
+  int32_t max_clusters; /* queries in flight at once; 0 = as many as fit on the device          */
+  int32_t reserved;     /* 0                                                                    */
+} pump_batch_config;
+/* Queries whose params set PUMP_EXPLORE_ONLY stop after Explore; the others
+ * run PlanSelection one after another.  Synchronises.
+ * Errors: INVALID_ARG (null or repeated graph, imported graph, bad params or
+ * config), OOM, CUDA; a query's own Explore or selection error is returned in
+ * results[q].status (and the call returns the first such error).
+ */
+int pump_plan_batch(pump_graph* const* graphs, int32_t n_queries, const pump_plan_params* params,
+                    const pump_batch_config* config, pump_plan_result* results, void* stream);
+
+/* --------------------------------------------------------------------------
  * pump_certify: MC(p) (Section III-A) for the plan visiting `path`
  * (path_len >= 1 node ids, consecutive ones joined by graph edges).  n_mc
  * rollouts of the closed loop: deviation drawn from the stationary

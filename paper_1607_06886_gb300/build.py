@@ -26,6 +26,7 @@ UNITS = {
     "edge_mask.cu": [],
     "explore.cu": [],
     "explore_cluster.cu": [],
+    "batch.cu": [],
     "select.cu": [],
     "noalloc.cu": [],
 }

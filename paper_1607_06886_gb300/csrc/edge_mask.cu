@@ -13,6 +13,9 @@
 // grid is persistent over the edges.
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <vector>
+
 #include "pump_internal.cuh"
 
 namespace pump {
@@ -20,6 +23,14 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kCandCap = 64;
+constexpr int kPW = 4;  // mask words (32-particle groups) a lane advances together
+
+// Shared memory of the query pass before the normals: boxes, per-warp candidate lists and
+// per-warp waypoint box masks (16-byte aligned end).
+__host__ __device__ constexpr size_t edge_mask_fixed_smem(int nb) {
+  return (sizeof(float) * 6 * (size_t)nb + sizeof(int) * kWarps * kCandCap + sizeof(uint32_t) * kWarps * kMaxWaypoints +
+          15) & ~(size_t)15;
+}
 
 __device__ __forceinline__ void dev_init(const float* linf, float2 x, float& d0, float& d1) {
   d0 = __fmul_rn(linf[0], x.x);
@@ -95,18 +106,24 @@ __global__ void k_edge_ibox(const float* __restrict__ nom, const unsigned int* _
 
 // Query pass: a warp per edge.  Boxes that miss the edge's position box cannot hold any of its
 // particle positions; an edge with none left gets zero mask words without running the
-// particles.  Otherwise each 32-particle word runs the recurrence once and tests the left boxes.
+// particles.  With at most 32 boxes left, the warp narrows them per waypoint: at waypoint k every
+// particle position lies in [nominal_k - M, nominal_k + M] (M = the edge's largest |d0|, rounded
+// the way the positions are), so only boxes meeting that box are tested there, and the particles
+// run only up to the last waypoint that has one.  Each 32-particle word then runs the
+// recurrence once and its lanes stop testing when all of them have hit.
 template <bool kSmemXi>
 __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restrict__ xi_g, int N, int W,
                                                            const float* __restrict__ phi, const float* __restrict__ Lg,
                                                            const float* __restrict__ nom, const float* __restrict__ linf_g,
                                                            const float* __restrict__ ibox_g,
+                                                           const unsigned int* __restrict__ dmax,
                                                            const float* __restrict__ boxes_g, int nb, int E, int w,
                                                            uint32_t* __restrict__ mask) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* boxes = reinterpret_cast<float*>(smem);
   int* cand = reinterpret_cast<int*>(boxes + 6 * nb);
-  float2* xi_s = reinterpret_cast<float2*>(cand + kWarps * kCandCap);
+  uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kWarps * kCandCap);
+  float2* xi_s = reinterpret_cast<float2*>(smem + edge_mask_fixed_smem(nb));
   for (int k = threadIdx.x; k < 6 * nb; k += blockDim.x) boxes[k] = boxes_g[k];
   const int xi_n = (W + 1) * 3 * N;
   if (kSmemXi)
@@ -116,6 +133,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restr
   const float linf[3] = {linf_g[0], linf_g[1], linf_g[2]};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int* my_cand = cand + warp * kCandCap;
+  uint32_t* wm = wmask_all + warp * kMaxWaypoints;
   for (long long e = (long long)blockIdx.x * kWarps + warp; e < E; e += (long long)gridDim.x * kWarps) {
     const float* ib = ibox_g + 6 * e;
     const float lo0 = ib[0], lo1 = ib[1], lo2 = ib[2], hi0 = ib[3], hi1 = ib[4], hi2 = ib[5];
@@ -133,7 +151,26 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restr
       n_cand += __popc(bal);
     }
     __syncwarp();
-    if (n_cand == 0) {
+    const float* nm = nom + (size_t)e * W * 3;
+    int k_last = W;
+    const bool narrow = n_cand > 0 && n_cand <= 32;
+    if (narrow) {
+      // boxes per waypoint: lane c tests candidate c against waypoint k's position box
+      const float M = __uint_as_float(dmax[e]);
+      const float* bc = boxes + 6 * my_cand[lane < n_cand ? lane : 0];
+      k_last = 0;
+      for (int k = 1; k <= W; ++k) {
+        const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
+        const bool ov = lane < n_cand && bc[0] <= __fadd_rn(n0, M) && __fsub_rn(n0, M) <= bc[3] &&
+                        bc[1] <= __fadd_rn(n1, M) && __fsub_rn(n1, M) <= bc[4] &&
+                        bc[2] <= __fadd_rn(n2, M) && __fsub_rn(n2, M) <= bc[5];
+        const unsigned m = __ballot_sync(0xffffffffu, ov);
+        if (lane == 0) wm[k - 1] = m;
+        if (m) k_last = k;
+      }
+      __syncwarp();
+    }
+    if (n_cand == 0 || k_last == 0) {
       for (int word = lane; word < w; word += 32) mask[(size_t)e * w + word] = 0u;
       continue;
     }
@@ -141,27 +178,62 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restr
     const int nc = all ? nb : n_cand;
     const float P[4] = {phi[4 * e], phi[4 * e + 1], phi[4 * e + 2], phi[4 * e + 3]};
     const float L[3] = {Lg[3 * e], Lg[3 * e + 1], Lg[3 * e + 2]};
-    const float* nm = nom + (size_t)e * W * 3;
-    for (int word = 0; word < w; ++word) {
-      const int i = word * 32 + lane;
-      float d0[3], d1[3];
+    // up to kPW words per pass: lane l runs particles 32 (w0 + j) + l, j < kPW, side by side
+    for (int w0 = 0; w0 < w; w0 += kPW) {
+      const int nw = min(kPW, w - w0);
+      float d0[kPW][3], d1[kPW][3];
+      bool hit[kPW];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) dev_init(linf, xi[(size_t)a * N + i], d0[a], d1[a]);
-      bool hit = false;
-      for (int k = 1; k <= W; ++k) {
-        float p[3];
+      for (int j = 0; j < kPW; ++j) {
+        hit[j] = j >= nw;  // absent words count as hit (they never block the early exit)
+        if (j < nw) {
+          const int i = (w0 + j) * 32 + lane;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          dev_step(P, L, xi[((size_t)k * 3 + a) * N + i], d0[a], d1[a]);
-          p[a] = __fadd_rn(nm[(k - 1) * 3 + a], d0[a]);
-        }
-        for (int c = 0; c < nc && !hit; ++c) {
-          const int o = all ? c : my_cand[c];
-          hit = in_box_dev(p[0], p[1], p[2], boxes + 6 * o);
+          for (int a = 0; a < 3; ++a) dev_init(linf, xi[(size_t)a * N + i], d0[j][a], d1[j][a]);
         }
       }
-      const unsigned bits = __ballot_sync(0xffffffffu, hit);
-      if (lane == 0) mask[(size_t)e * w + word] = bits;
+      for (int k = 1; k <= k_last; ++k) {
+        const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
+        float p[kPW][3];
+#pragma unroll
+        for (int j = 0; j < kPW; ++j) {
+          if (j < nw) {
+            const int i = (w0 + j) * 32 + lane;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dev_step(P, L, xi[((size_t)k * 3 + a) * N + i], d0[j][a], d1[j][a]);
+            p[j][0] = __fadd_rn(n0, d0[j][0]);
+            p[j][1] = __fadd_rn(n1, d0[j][1]);
+            p[j][2] = __fadd_rn(n2, d0[j][2]);
+          }
+        }
+        if (narrow) {
+          unsigned bits = wm[k - 1];
+          while (bits) {
+            const int c = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const float* b = boxes + 6 * my_cand[c];
+#pragma unroll
+            for (int j = 0; j < kPW; ++j)
+              if (j < nw && !hit[j]) hit[j] = in_box_dev(p[j][0], p[j][1], p[j][2], b);
+          }
+        } else {
+          for (int c = 0; c < nc; ++c) {
+            const float* b = boxes + 6 * (all ? c : my_cand[c]);
+#pragma unroll
+            for (int j = 0; j < kPW; ++j)
+              if (j < nw && !hit[j]) hit[j] = in_box_dev(p[j][0], p[j][1], p[j][2], b);
+          }
+        }
+        bool done = true;
+#pragma unroll
+        for (int j = 0; j < kPW; ++j) done = done && hit[j];
+        if (__all_sync(0xffffffffu, done)) break;
+      }
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) {
+        const unsigned bits = __ballot_sync(0xffffffffu, hit[j]);
+        if (j < nw && lane == 0) mask[(size_t)e * w + w0 + j] = bits;
+      }
     }
     __syncwarp();
   }
@@ -170,17 +242,40 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restr
 }  // namespace
 
 size_t edge_mask_smem(int N, int W, int nb, bool xi_in_smem) {
-  size_t b = sizeof(float) * 6 * (size_t)nb + sizeof(int) * kWarps * kCandCap;
-  b = (b + 15) & ~(size_t)15;
+  size_t b = edge_mask_fixed_smem(nb);
   if (xi_in_smem) b += sizeof(float2) * (size_t)(W + 1) * 3 * N;
   return b;
 }
 
+struct OccEntry {
+  const void* kernel;
+  size_t smem;
+  int dev, per_sm;
+};
+static std::mutex g_occ_mu;
+static std::vector<OccEntry> g_occ;
+constexpr size_t kMaskSmemMax = 200 * 1024;
+
+// Blocks for `items` work items: resident blocks per SM (queried once per kernel, size and
+// device) times the SMs, at most one block per items_per_block items.
 template <typename K>
 static int occupancy_grid(K kernel, size_t smem, long long items_per_block, long long items, int* grid) {
-  PUMP_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  PUMP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, smem));
+  if (smem > kMaskSmemMax) return PUMP_ERR_INVALID_ARG;
+  int dev = 0;
+  PUMP_CUDA_TRY(cudaGetDevice(&dev));
+  int per_sm = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    for (const auto& o : g_occ)
+      if (o.kernel == (const void*)kernel && o.smem == smem && o.dev == dev) per_sm = o.per_sm;
+  }
+  if (per_sm < 0) {
+    // one ceiling for every size (the attribute belongs to the kernel)
+    PUMP_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaskSmemMax));
+    PUMP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, smem));
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    g_occ.push_back({(const void*)kernel, smem, dev, per_sm});
+  }
   if (per_sm < 1) per_sm = 1;
   long long want = (items + items_per_block - 1) / items_per_block;
   long long gsz = (long long)num_sms() * per_sm;
@@ -193,7 +288,8 @@ static int occupancy_grid(K kernel, size_t smem, long long items_per_block, long
 // Obstacle-independent per-edge position boxes (graph build).
 int compute_edge_bounds(pump_graph* g, cudaStream_t s) {
   if (g->E == 0) return PUMP_OK;
-  unsigned int* dbound = (unsigned int*)dev_alloc(sizeof(unsigned int) * (size_t)g->E, s);
+  g->dmax = (unsigned int*)graph_alloc(g, sizeof(unsigned int) * (size_t)g->E, s);
+  unsigned int* dbound = g->dmax;
   if (!dbound) return PUMP_ERR_OOM;
   PUMP_CUDA_TRY(cudaMemsetAsync(dbound, 0, sizeof(unsigned int) * (size_t)g->E, s));
   const size_t smem_xi = sizeof(float2) * (size_t)(g->W + 1) * 3 * g->N;
@@ -220,7 +316,6 @@ int compute_edge_bounds(pump_graph* g, cudaStream_t s) {
   k_edge_ibox<<<(g->E + 255) / 256, 256, 0, s>>>(g->nom, dbound, g->E, g->W, g->ibox);
   note_launch();
   PUMP_CUDA_TRY(cudaGetLastError());
-  dev_free(dbound, s);
   return PUMP_OK;
 }
 
@@ -239,7 +334,7 @@ int compute_edge_masks(pump_graph* g, cudaStream_t s) {
       if (rco) return rco;
     }
     k_edge_mask<true><<<grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
-                                                      g->ibox, g->boxes, g->n_boxes, g->E, g->n_words, g->emask);
+                                                      g->ibox, g->dmax, g->boxes, g->n_boxes, g->E, g->n_words, g->emask);
     note_launch();
   } else {
     {
@@ -247,7 +342,7 @@ int compute_edge_masks(pump_graph* g, cudaStream_t s) {
       if (rco) return rco;
     }
     k_edge_mask<false><<<grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
-                                                       g->ibox, g->boxes, g->n_boxes, g->E, g->n_words, g->emask);
+                                                       g->ibox, g->dmax, g->boxes, g->n_boxes, g->E, g->n_words, g->emask);
     note_launch();
   }
   PUMP_CUDA_TRY(cudaGetLastError());

@@ -657,50 +657,7 @@ __global__ void k_fill_u32(uint32_t* p, int64_t n, uint32_t v) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) p[k] = v;
 }
 
-__global__ void k_explore_init(ExploreArgs A, int32_t start) {
-  ExploreCtl* c = A.ctl;
-  A.head[0] = start;
-  A.parent[0] = -1;
-  A.pedge[0] = -1;
-  A.cost[0] = 0.f;
-  A.popc[0] = 0;
-  A.tcre[0] = -1;
-  A.eexp[0] = -1;
-  for (int j = 0; j < A.w; ++j) A.mask[j] = 0u;
-  A.mbest[(size_t)start * A.kstride] = 0u;  // float 0
-  A.group[0] = 0;
-  A.ginfo[0] = make_int4(0, start, A.row_ptr[start], __float_as_int(0.f));
-  const int64_t d0 = A.row_ptr[start + 1] - A.row_ptr[start];
-  A.goff[0] = 0;
-  A.goff[1] = d0;
-  c->n_plans = 1;
-  c->n_candidates = 0;
-  c->n_kept = 0;
-  c->st[0].group_cands = d0;
-  c->st[0].group_size = 1;
-  c->st[0].iter = 0;
-  c->st[0].stop = (A.early_stop && A.is_goal[start] && 0 < A.kmin) ? 1 : 0;
-  c->st[1].group_cands = 0;
-  c->st[1].group_size = 0;
-  c->st[1].iter = 0;
-  c->st[1].stop = 0;
-  c->next_bucket[0] = kNoBucket;
-  c->next_bucket[1] = kNoBucket;
-  c->stop_next = 0;
-  c->status = 0;
-  c->n_groups = 0;
-  c->survivors = 0;
-  c->n_goal_all = 0;
-  c->n_goal = 0;
-  c->k_exit = 0;
-  c->iter = 0;
-  c->bar_count = 0;
-  c->bar_gen = 0;
-  if (A.is_goal[start]) {
-    A.goal_all[0] = 0;
-    c->n_goal_all = 1;
-  }
-}
+__global__ void k_explore_init(ExploreArgs A, int32_t start) { explore_init_thread(A, start); }
 
 // End of a run: commit the last survivors and record the final group index.  k < 0 takes the
 // iteration count the persistent kernel stored.

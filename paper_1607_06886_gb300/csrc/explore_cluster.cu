@@ -143,6 +143,8 @@ struct CSmem {
   // cluster-wide values of phase C, derived by warp 0 and read by the whole CTA
   int32_t b_nbk, b_min_open, b_before_s, b_total_s, b_before_o, b_total_o, b_before_n, b_total_n, b_stop, b_fast;
   long long b_dbefore_o, b_dtotal_o, b_dbefore_n, b_dtotal_n, b_per_n;
+  ExploreArgs args;  // the query's arguments (batched form)
+  int32_t qnext;     // query index taken by the cluster (batched form; written by CTA 0)
   int32_t slot0;     // member holding the first candidate of this CTA's chunk (set by its writer)
   int32_t slot_end;  // member holding the last candidate of this CTA's chunk (set by its writer)
   long long kept; // candidates under the CP cutoff, this CTA, whole run
@@ -946,12 +948,10 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
   __syncthreads();
 }
 
+// One Explore run by the whole cluster.  Starts and ends with a cluster barrier, so a cluster
+// can run several in a row (batched form).
 template <bool kDsm>
-__global__ void __launch_bounds__(kCT, 1) k_explore_cluster(ExploreArgs A, int32_t start) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
-  uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
-  cg::cluster_group cl = cg::this_cluster();
+__device__ void explore_one(const ExploreArgs& A, int32_t start, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl) {
   const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
   ExploreCtl* ctl = A.ctl;
   if (kDsm) {
@@ -1023,7 +1023,45 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_cluster(ExploreArgs A, int32
     ctl->survivors = 0;
     ctl->k_exit = k;
   }
-  cl.sync();  // no CTA leaves while another may still write into its shared memory
+  cl.sync();  // no CTA leaves (or starts another run) while another may still touch its shared memory
+}
+
+template <bool kDsm>
+__global__ void __launch_bounds__(kCT, 1) k_explore_cluster(ExploreArgs A, int32_t start) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
+  uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
+  cg::cluster_group cl = cg::this_cluster();
+  explore_one<kDsm>(A, start, sm, mbl, cl);
+}
+
+// Batched form: every cluster takes the next query from *next (a device counter starting at 0)
+// until none is left; query q runs with As[q] and starts[q], exactly as the single-query kernel.
+template <bool kDsm>
+__global__ void __launch_bounds__(kCT, 1) k_explore_cluster_batch(const ExploreArgs* __restrict__ As,
+                                                                  const int32_t* __restrict__ starts, int32_t nq,
+                                                                  int32_t* next) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
+  uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
+  constexpr int kArgWords = sizeof(ExploreArgs) / 4;
+  static_assert(sizeof(ExploreArgs) % 4 == 0, "argument copy");
+  for (;;) {
+    if (r == 0 && threadIdx.x == 0) {
+      const int32_t q = atomicAdd(next, 1);
+      for (int rr = 0; rr < nr; ++rr) *cl.map_shared_rank(&sm->qnext, (unsigned)rr) = q;
+    }
+    cl.sync();
+    const int32_t q = sm->qnext;
+    if (q >= nq) break;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(As + q);
+    for (int t = threadIdx.x; t < kArgWords; t += kCT) reinterpret_cast<uint32_t*>(&sm->args)[t] = src[t];
+    __syncthreads();
+    explore_one<kDsm>(sm->args, starts[q], sm, mbl, cl);
+  }
+  cl.sync();  // the last query index was read everywhere before any CTA leaves
 }
 
 // Per edge: target node, edge cost bits, target row start, target out-degree | goal bit.
@@ -1047,6 +1085,12 @@ size_t cluster_smem_bytes(int n, int kstride, int nr, bool dsm) {
 template <bool kDsm>
 int try_cluster_size(int nr, size_t smem, cudaStream_t s, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
   auto kern = k_explore_cluster<kDsm>;
+  auto bkern = k_explore_cluster_batch<kDsm>;
+  if (cudaFuncSetAttribute(bkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmemMax) != cudaSuccess ||
+      cudaFuncSetAttribute(bkern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   // one ceiling for every configuration (the attribute belongs to the kernel, not to a launch)
   if (smem > kDynSmemMax ||
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmemMax) != cudaSuccess) {
@@ -1127,58 +1171,97 @@ int ensure_edge_targets(pump_graph* g, cudaStream_t s) {
   return PUMP_OK;
 }
 
-// Picks the cluster form for a run: *nr = cluster size (0 when no cluster form fits the device)
-// and *dsm = mbest in distributed shared memory.
-int plan_explore_cluster(const ExploreArgs& A, int* nr_out, bool* dsm_out) {
+// Picks the cluster form: *nr = cluster size (0 when no cluster form fits the device) and *dsm =
+// mbest in distributed shared memory, for tables of n nodes x kstride.  want_nr > 0 asks for one
+// size (0: 16, else 8, else 4; the PUMP_EXPLORE_CLUSTER environment variable overrides it) and
+// want_global keeps mbest in global memory.
+int plan_cluster_form(int32_t n, int32_t kstride, int want_nr, bool want_global, int* nr_out, bool* dsm_out,
+                      size_t* smem_out) {
   *nr_out = 0;
   *dsm_out = false;
   const int env = cluster_env();
   if (env == 0) return PUMP_OK;
   int sizes[3] = {16, 8, 4};
   int n_sizes = 3;
-  if (env > 0) {
-    if (env > kMaxCluster) return PUMP_OK;
-    sizes[0] = env;
+  const int want = env > 0 ? env : want_nr;
+  if (want > 0) {
+    if (want > kMaxCluster) return PUMP_OK;
+    sizes[0] = want;
     n_sizes = 1;
   }
   int dev = 0;
   PUMP_CUDA_TRY(cudaGetDevice(&dev));
-  const size_t fixed = cluster_smem_bytes(A.n, A.kstride, 1, false);
+  const size_t fixed = cluster_smem_bytes(n, kstride, 1, false);
   for (int t = 0; t < n_sizes; ++t) {
     const int nr = sizes[t];
-    const int words = ((A.n + nr - 1) / nr) * A.kstride;
-    const bool dsm = !mbest_global_env() && fixed + sizeof(uint32_t) * (size_t)words + 4096 <= kSmemLimit;
-    const size_t smem = cluster_smem_bytes(A.n, A.kstride, nr, dsm);
+    const int words = ((n + nr - 1) / nr) * kstride;
+    const bool dsm = !want_global && !mbest_global_env() && fixed + sizeof(uint32_t) * (size_t)words + 4096 <= kSmemLimit;
+    const size_t smem = cluster_smem_bytes(n, kstride, nr, dsm);
     if (cluster_ok(dev, nr, dsm, smem, words)) {
       *nr_out = nr;
       *dsm_out = dsm;
+      if (smem_out) *smem_out = smem;
       return PUMP_OK;
     }
   }
   return PUMP_OK;
 }
 
-// Launches the cluster kernel in the form plan_explore_cluster chose.
-int run_explore_cluster(pump_graph* g, const ExploreArgs& A, int nr, bool dsm, cudaStream_t s) {
-  const size_t smem = cluster_smem_bytes(A.n, A.kstride, nr, dsm);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nr);
-  cfg.blockDim = dim3(kCT);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+int plan_explore_cluster(const ExploreArgs& A, int* nr_out, bool* dsm_out) {
+  return plan_cluster_form(A.n, A.kstride, 0, false, nr_out, dsm_out, nullptr);
+}
+
+static void cluster_config(cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr, int nr, int n_clusters, size_t smem,
+                           cudaStream_t s) {
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = dim3(nr * n_clusters);
+  cfg->blockDim = dim3(kCT);
+  cfg->dynamicSmemBytes = smem;
+  cfg->stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = nr;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+}
+
+// Launches the cluster kernel in the form plan_explore_cluster chose.
+int run_explore_cluster(pump_graph* g, const ExploreArgs& A, int nr, bool dsm, cudaStream_t s) {
+  const size_t smem = cluster_smem_bytes(A.n, A.kstride, nr, dsm);
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cluster_config(&cfg, attr, nr, 1, smem, s);
   const int32_t start = g->start;
   cudaError_t e;
   if (dsm)
     e = cudaLaunchKernelEx(&cfg, k_explore_cluster<true>, A, start);
   else
     e = cudaLaunchKernelEx(&cfg, k_explore_cluster<false>, A, start);
+  note_launch();
+  return e == cudaSuccess ? PUMP_OK : PUMP_ERR_CUDA;
+}
+
+// Clusters of the batched kernel that fit on the device at once for this form.
+int cluster_capacity(int nr, bool dsm, size_t smem, int* out) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  *out = dsm ? try_cluster_size<true>(nr, smem, 0, &cfg, attr) : try_cluster_size<false>(nr, smem, 0, &cfg, attr);
+  return PUMP_OK;
+}
+
+// Batched launch: n_clusters clusters of nr CTAs take queries from *next until nq are done.
+int run_explore_cluster_batch(const ExploreArgs* As_dev, const int32_t* starts_dev, int32_t nq, int nr, bool dsm,
+                              size_t smem, int n_clusters, int32_t* next_dev, cudaStream_t s) {
+  PUMP_CUDA_TRY(cudaMemsetAsync(next_dev, 0, sizeof(int32_t), s));
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cluster_config(&cfg, attr, nr, n_clusters, smem, s);
+  cudaError_t e;
+  if (dsm)
+    e = cudaLaunchKernelEx(&cfg, k_explore_cluster_batch<true>, As_dev, starts_dev, nq, next_dev);
+  else
+    e = cudaLaunchKernelEx(&cfg, k_explore_cluster_batch<false>, As_dev, starts_dev, nq, next_dev);
   note_launch();
   return e == cudaSuccess ? PUMP_OK : PUMP_ERR_CUDA;
 }

@@ -142,9 +142,8 @@ void fill_explore_stats(pump_graph* g, const ExploreCtl& h, pump_plan_result* st
   st->n_goal = g->last_goal;
 }
 
-// Enqueue Explore; with `collect` read its control block back and fill `st`.
-int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* st, cudaStream_t s,
-                bool collect) {
+// Explore's arguments for graph g and plan parameters p (buffers allocated as needed).
+int prepare_explore_args(pump_graph* g, const pump_plan_params* p, float radius, ExploreArgs* out, cudaStream_t s) {
   const double alpha = (double)p->alpha, eta = (double)p->eta;
   const int32_t kmax = popc_bound((eta * alpha) * (double)g->N, g->N);
   const int32_t kmin = popc_bound((alpha / eta) * (double)g->N, g->N);
@@ -186,6 +185,17 @@ int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_pla
   rc = ensure_edge_targets(g, s);
   if (rc) return rc;
   A.etgt = g->etgt;
+  *out = A;
+  return PUMP_OK;
+}
+
+// Enqueue Explore; with `collect` read its control block back and fill `st`.
+int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* st, cudaStream_t s,
+                bool collect) {
+  ExploreArgs A;
+  int rc = prepare_explore_args(g, p, radius, &A, s);
+  if (rc) return rc;
+  ExploreBufs& X = g->ex;
   rc = run_explore_kernels(g, A, explore_mode(p->flags), s);
   if (rc) return rc;
   rc = run_goal_finalize(g, A, s);
@@ -242,7 +252,16 @@ static void destroy(pump_graph* g) {
   delete g;
 }
 
-static int make_events(pump_graph* g) {
+int check_plan_params(const pump_plan_params* p) {
+  if (!p) return PUMP_ERR_INVALID_ARG;
+  if (!(p->alpha >= 0.f) || !(p->alpha <= 1.f) || !(p->eta > 0.f) || !std::isfinite(p->eta)) return PUMP_ERR_INVALID_ARG;
+  if (!(p->lambda > 0.f) || !(p->lambda <= 1.f)) return PUMP_ERR_INVALID_ARG;
+  if (p->max_plans < 1 || p->max_plans > (1ll << 31) - 2 || p->max_iterations < 1) return PUMP_ERR_INVALID_ARG;
+  if (p->n_mc < 0 || p->mc_substeps < 1 || p->mc_substeps > 64) return PUMP_ERR_INVALID_ARG;
+  return PUMP_OK;
+}
+
+int make_events(pump_graph* g) {
   for (auto& e : g->ev)
     if (!e) PUMP_CUDA_TRY(cudaEventCreate(&e));
   return PUMP_OK;
@@ -411,15 +430,6 @@ int pump_graph_from_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, c
 int pump_edge_masks(pump_graph* g, void* stream) {
   if (!g || !g->has_geometry) return PUMP_ERR_INVALID_ARG;
   return compute_edge_masks(g, (cudaStream_t)stream);
-}
-
-static int check_plan_params(const pump_plan_params* p) {
-  if (!p) return PUMP_ERR_INVALID_ARG;
-  if (!(p->alpha >= 0.f) || !(p->alpha <= 1.f) || !(p->eta > 0.f) || !std::isfinite(p->eta)) return PUMP_ERR_INVALID_ARG;
-  if (!(p->lambda > 0.f) || !(p->lambda <= 1.f)) return PUMP_ERR_INVALID_ARG;
-  if (p->max_plans < 1 || p->max_plans > (1ll << 31) - 2 || p->max_iterations < 1) return PUMP_ERR_INVALID_ARG;
-  if (p->n_mc < 0 || p->mc_substeps < 1 || p->mc_substeps > 64) return PUMP_ERR_INVALID_ARG;
-  return PUMP_OK;
 }
 
 int pump_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* stats, void* stream) {

@@ -166,6 +166,7 @@ struct pump_graph {
   uint32_t* emask = nullptr; // E x n_words
   float* ibox = nullptr;     // E x 6: box holding every particle position of the edge
   int4* etgt = nullptr;      // E: target node, cost bits, target row start, degree | goal bit
+  unsigned int* dmax = nullptr;  // E: largest |d0| of the edge's particles (float bits)
   std::vector<pump::DevBuf> bufs;
   pump::ExploreBufs ex;
   // last explore
@@ -200,6 +201,10 @@ int run_certify_path(pump_graph* g, const int32_t* path_host, int32_t path_len, 
 int ensure_explore_bufs(pump_graph* g, int64_t cap, int32_t kmax, cudaStream_t s);
 int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStream_t s);
 int ensure_edge_targets(pump_graph* g, cudaStream_t s);
+int prepare_explore_args(pump_graph* g, const pump_plan_params* p, float radius, ExploreArgs* out, cudaStream_t s);
+int check_plan_params(const pump_plan_params* p);
+int make_events(pump_graph* g);
+int compute_edge_masks(pump_graph* g, cudaStream_t s);
 // Explore kernel form from pump_plan_params.flags (see run_explore_kernels).
 inline int explore_mode(int32_t flags) {
   return (flags & PUMP_STEPWISE) ? 2 : ((flags & PUMP_EXPLORE_GRID) ? 1 : 0);
@@ -355,6 +360,96 @@ __device__ inline int32_t bucket_of(float cost, double lr) {
   while (i > 0 && cost <= group_thr(i - 1, lr)) --i;
   while (cost > group_thr(i, lr)) ++i;
   return i;
+}
+
+// Explore's starting state, one thread: the root plan (id 0) at the start node, mbest entry
+// (start, 0) = 0, group 0 = {root} with its candidate offsets, and the control block.
+__device__ __forceinline__ void explore_init_thread(const ExploreArgs& A, int32_t start) {
+  ExploreCtl* c = A.ctl;
+  A.head[0] = start;
+  A.parent[0] = -1;
+  A.pedge[0] = -1;
+  A.cost[0] = 0.f;
+  A.popc[0] = 0;
+  A.tcre[0] = -1;
+  A.eexp[0] = -1;
+  for (int j = 0; j < A.w; ++j) A.mask[j] = 0u;
+  A.mbest[(size_t)start * A.kstride] = 0u;  // float 0
+  A.group[0] = 0;
+  A.ginfo[0] = make_int4(0, start, A.row_ptr[start], __float_as_int(0.f));
+  const int64_t d0 = A.row_ptr[start + 1] - A.row_ptr[start];
+  A.goff[0] = 0;
+  A.goff[1] = d0;
+  c->n_plans = 1;
+  c->n_candidates = 0;
+  c->n_kept = 0;
+  c->st[0].group_cands = d0;
+  c->st[0].group_size = 1;
+  c->st[0].iter = 0;
+  c->st[0].stop = (A.early_stop && A.is_goal[start] && 0 < A.kmin) ? 1 : 0;
+  c->st[1].group_cands = 0;
+  c->st[1].group_size = 0;
+  c->st[1].iter = 0;
+  c->st[1].stop = 0;
+  c->next_bucket[0] = kNoBucket;
+  c->next_bucket[1] = kNoBucket;
+  c->stop_next = 0;
+  c->status = 0;
+  c->n_groups = 0;
+  c->survivors = 0;
+  c->n_goal_all = 0;
+  c->n_goal = 0;
+  c->k_exit = 0;
+  c->iter = 0;
+  c->bar_count = 0;
+  c->bar_gen = 0;
+  if (A.is_goal[start]) {
+    A.goal_all[0] = 0;
+    c->n_goal_all = 1;
+  }
+}
+
+// P_goal order: popc ascending, then cost descending, then id ascending.
+__device__ __forceinline__ bool key_less(const ExploreArgs& A, int32_t a, int32_t b) {
+  const int32_t pa = A.popc[a], pb = A.popc[b];
+  if (pa != pb) return pa < pb;
+  const float ca = A.cost[a], cb = A.cost[b];
+  if (ca != cb) return ca > cb;
+  return a < b;
+}
+
+// P_goal from the goal plans Explore recorded (one block): drops the plans RemoveDominated removed
+// (settled from creation / expansion stamps) and sorts the rest in PlanSelection order.
+__device__ __forceinline__ void goal_finalize_block(const ExploreArgs& A, int32_t* removed, int32_t* sorted) {
+  ExploreCtl* ctl = A.ctl;
+  const int G = ctl->n_goal_all;
+  for (int k = threadIdx.x; k < G; k += blockDim.x) {
+    const int32_t p = A.goal_all[k];
+    const int32_t ep = A.eexp[p] >= 0 ? A.eexp[p] : INT_MAX;
+    const int32_t x = A.head[p];
+    int rem = 0;
+    for (int j = 0; j < G && !rem; ++j) {
+      const int32_t q = A.goal_all[j];
+      if (q == p || A.head[q] != x) continue;
+      if (A.tcre[q] <= ep && A.cost[q] < A.cost[p] && A.popc[q] <= A.popc[p]) rem = 1;
+    }
+    removed[k] = rem;
+  }
+  __syncthreads();
+  __shared__ int count;
+  if (threadIdx.x == 0) count = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < G; k += blockDim.x) {
+    if (removed[k]) continue;
+    const int32_t p = A.goal_all[k];
+    int rank = 0;
+    for (int j = 0; j < G; ++j)
+      if (!removed[j] && key_less(A, A.goal_all[j], p)) ++rank;
+    sorted[rank] = p;
+    atomicAdd(&count, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ctl->n_goal = count;
 }
 
 // Philox4x64-10 (Salmon et al., SC'11).

@@ -34,45 +34,8 @@
 namespace pump {
 namespace {
 
-__device__ __forceinline__ bool key_less(const ExploreArgs& A, int32_t a, int32_t b) {
-  const int32_t pa = A.popc[a], pb = A.popc[b];
-  if (pa != pb) return pa < pb;
-  const float ca = A.cost[a], cb = A.cost[b];
-  if (ca != cb) return ca > cb;
-  return a < b;
-}
 
-__global__ void k_goal_finalize(ExploreArgs A, int32_t* removed, int32_t* sorted) {
-  ExploreCtl* ctl = A.ctl;
-  const int G = ctl->n_goal_all;
-  for (int k = threadIdx.x; k < G; k += blockDim.x) {
-    const int32_t p = A.goal_all[k];
-    const int32_t ep = A.eexp[p] >= 0 ? A.eexp[p] : INT_MAX;
-    const int32_t x = A.head[p];
-    int rem = 0;
-    for (int j = 0; j < G && !rem; ++j) {
-      const int32_t q = A.goal_all[j];
-      if (q == p || A.head[q] != x) continue;
-      if (A.tcre[q] <= ep && A.cost[q] < A.cost[p] && A.popc[q] <= A.popc[p]) rem = 1;
-    }
-    removed[k] = rem;
-  }
-  __syncthreads();
-  __shared__ int count;
-  if (threadIdx.x == 0) count = 0;
-  __syncthreads();
-  for (int k = threadIdx.x; k < G; k += blockDim.x) {
-    if (removed[k]) continue;
-    const int32_t p = A.goal_all[k];
-    int rank = 0;
-    for (int j = 0; j < G; ++j)
-      if (!removed[j] && key_less(A, A.goal_all[j], p)) ++rank;
-    sorted[rank] = p;
-    atomicAdd(&count, 1);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) ctl->n_goal = count;
-}
+__global__ void k_goal_finalize(ExploreArgs A, int32_t* removed, int32_t* sorted) { goal_finalize_block(A, removed, sorted); }
 
 // Selection state (device): bisection indices and the outcome.
 struct SelState {

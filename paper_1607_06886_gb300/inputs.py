@@ -186,6 +186,30 @@ def make_workload(name: str, seed: int = 0, n_samples: Optional[int] = None) -> 
         sigma=0.01, alpha=alpha, eta=2.0, lam=0.5, mc_seed=seed)
 
 
+def batch_workloads(n_queries: int, seed: int = 0, n_range=(1000, 8000), o_range=(5, 50),
+                    particles=(64, 128, 256)) -> List[Workload]:
+    """Independent queries of uneven size for the batched form: query j (seed + j) draws its
+    sample count U{n_range}, its box count U{o_range} (indoor walls and floor, 5 boxes, plus
+    clutter) and N from `particles`; W = 10, sigma = 0.01, CP target 1 %, eta = 2, lambda = 0.5."""
+    out = []
+    for j in range(n_queries):
+        qs = seed + j
+        g = _rng(qs, 7)
+        ns = int(g.integers(n_range[0], n_range[1] + 1))
+        n_obs = int(g.integers(o_range[0], o_range[1] + 1))
+        N = int(particles[int(g.integers(0, len(particles)))])
+        boxes = indoor_boxes(qs, n_clutter=max(n_obs - 5, 0))
+        states = sample_states(ns, qs)
+        out.append(Workload(
+            name="batch", seed=qs, states=states,
+            boxes=np.asarray(boxes, dtype=np.float32).reshape(-1, 6),
+            goal_idx=goal_members(states),
+            xi=particle_normals(N, 10, qs),
+            radius=radius_for(ns + 2), n_particles=N, n_waypoints=10,
+            sigma=0.01, alpha=0.01, eta=2.0, lam=0.5, mc_seed=qs))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Random explore graphs: CSR adjacency, edge costs and edge masks drawn directly,
 # with the degree, cost and mask-density structure of the dynamics-built graphs.

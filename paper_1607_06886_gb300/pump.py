@@ -42,6 +42,11 @@ class PlanParams(C.Structure):
                 ("max_iterations", C.c_int32), ("flags", C.c_int32)]
 
 
+class BatchConfig(C.Structure):
+    _fields_ = [("cluster_size", C.c_int32), ("mbest_global", C.c_int32), ("max_clusters", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class PlanResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("chosen_plan", C.c_int32), ("cost", C.c_float), ("popc", C.c_int32),
                 ("cp_hat", C.c_float), ("cp_mc", C.c_double), ("mc_collisions", C.c_int64),
@@ -94,12 +99,36 @@ def load(build_if_missing: bool = False):
     L.pump_graph_destroy.restype = None
     L.pump_explore_noalloc.argtypes = [i32, P, P, P, P, i32, i32, P, f32, C.POINTER(PlanParams), i64,
                                        P, P, P, P, P, P, P, P, C.POINTER(PlanResult), P]
+    L.pump_plan_batch.argtypes = [P, i32, P, C.POINTER(BatchConfig), P, P]
     L.pump_kernel_launches.argtypes = []
     L.pump_kernel_launches.restype = C.c_uint64
     L.pump_status_str.argtypes = [C.c_int]
     L.pump_status_str.restype = C.c_char_p
     _lib = L
     return L
+
+
+def plan_batch(graphs, params, config: Optional["BatchConfig"] = None, stream: Optional[int] = None):
+    """pump_plan_batch: one query per graph (params: one PlanParams, or one per graph).  Returns
+    (rc, list of result dicts)."""
+    graphs = list(graphs)
+    nq = len(graphs)
+    if isinstance(params, PlanParams):
+        params = [params] * nq
+    if len(params) != nq:
+        raise ValueError("one PlanParams per graph")
+    handles = (C.c_void_p * nq)(*[g._h for g in graphs])
+    prm = (PlanParams * nq)(*params)
+    res = (PlanResult * nq)()
+    rc = load().pump_plan_batch(C.cast(handles, C.c_void_p), nq, C.cast(prm, C.c_void_p),
+                                C.byref(config) if config is not None else None, C.cast(res, C.c_void_p),
+                                current_stream() if stream is None else stream)
+    out = []
+    for r in res:
+        d = r.as_dict()
+        d["rc"] = r.status
+        out.append(d)
+    return rc, out
 
 
 def kernel_launches() -> int:
