@@ -23,13 +23,13 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kCandCap = 64;
-constexpr int kPW = 4;  // mask words (32-particle groups) a lane advances together
+constexpr int kBoxStride = 8;  // floats per box in shared memory: lo xyz, hi xyz, 2 pad
 
 // Shared memory of the query pass before the normals: boxes, per-warp candidate lists and
 // per-warp waypoint box masks (16-byte aligned end).
 __host__ __device__ constexpr size_t edge_mask_fixed_smem(int nb) {
-  return (sizeof(float) * 6 * (size_t)nb + sizeof(int) * kWarps * kCandCap + sizeof(uint32_t) * kWarps * kMaxWaypoints +
-          15) & ~(size_t)15;
+  return (sizeof(float) * kBoxStride * (size_t)nb + sizeof(int) * kWarps * kCandCap +
+          sizeof(uint32_t) * kWarps * kMaxWaypoints + 15) & ~(size_t)15;
 }
 
 __device__ __forceinline__ void dev_init(const float* linf, float2 x, float& d0, float& d1) {
@@ -104,6 +104,68 @@ __global__ void k_edge_ibox(const float* __restrict__ nom, const unsigned int* _
   }
 }
 
+// NW mask words of one edge: lane l advances particles 32 (w0 + j) + l, j < NW, side by side
+// through waypoints 1..k_last and tests the boxes left at each; the words are the warp ballots.
+// The warp stops early once every lane's particles have hit.
+template <int NW>
+__device__ __forceinline__ void word_pass(const float2* __restrict__ xi, int N, int W, const float (&P)[4],
+                                          const float (&L)[3], const float (&linf)[3], const float* __restrict__ nm,
+                                          int k_last, bool narrow, const uint32_t* wm, const int* my_cand, bool all,
+                                          int nc, const float* boxes, int w0, int lane, uint32_t* out) {
+  float d0[NW][3], d1[NW][3];
+  bool hit[NW];
+  const float2* xq = xi + w0 * 32 + lane;
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    hit[j] = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dev_init(linf, xq[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+  }
+  for (int k = 1; k <= k_last; ++k) {
+    const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
+    const float2* xk = xq + (size_t)k * 3 * N;
+    float p[NW][3];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dev_step(P, L, xk[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+      p[j][0] = __fadd_rn(n0, d0[j][0]);
+      p[j][1] = __fadd_rn(n1, d0[j][1]);
+      p[j][2] = __fadd_rn(n2, d0[j][2]);
+    }
+    unsigned bits = narrow ? wm[k - 1] : 0u;
+    int c = 0;
+    for (;;) {
+      int o;
+      if (narrow) {
+        if (!bits) break;
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        o = my_cand[b];
+      } else {
+        if (c >= nc) break;
+        o = all ? c : my_cand[c];
+        ++c;
+      }
+      const float4 b0 = *reinterpret_cast<const float4*>(boxes + kBoxStride * o);      // lo x, y, z, hi x
+      const float2 b1 = *reinterpret_cast<const float2*>(boxes + kBoxStride * o + 4);  // hi y, z
+#pragma unroll
+      for (int j = 0; j < NW; ++j)
+        hit[j] = hit[j] || (b0.x <= p[j][0] && p[j][0] <= b0.w && b0.y <= p[j][1] && p[j][1] <= b1.x &&
+                            b0.z <= p[j][2] && p[j][2] <= b1.y);
+    }
+    bool done = true;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) done = done && hit[j];
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    const unsigned bits = __ballot_sync(0xffffffffu, hit[j]);
+    if (lane == 0) out[w0 + j] = bits;
+  }
+}
+
 // Query pass: a warp per edge.  Boxes that miss the edge's position box cannot hold any of its
 // particle positions; an edge with none left gets zero mask words without running the
 // particles.  With at most 32 boxes left, the warp narrows them per waypoint: at waypoint k every
@@ -111,8 +173,11 @@ __global__ void k_edge_ibox(const float* __restrict__ nom, const unsigned int* _
 // the way the positions are), so only boxes meeting that box are tested there, and the particles
 // run only up to the last waypoint that has one.  Each 32-particle word then runs the
 // recurrence once and its lanes stop testing when all of them have hit.
+#ifndef PUMP_MASK_MIN_BLOCKS
+#define PUMP_MASK_MIN_BLOCKS 4  // 64 registers: four 256-thread blocks per SM (measured best)
+#endif
 template <bool kSmemXi>
-__global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restrict__ xi_g, int N, int W,
+__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask(const float2* __restrict__ xi_g, int N, int W,
                                                            const float* __restrict__ phi, const float* __restrict__ Lg,
                                                            const float* __restrict__ nom, const float* __restrict__ linf_g,
                                                            const float* __restrict__ ibox_g,
@@ -120,11 +185,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restr
                                                            const float* __restrict__ boxes_g, int nb, int E, int w,
                                                            uint32_t* __restrict__ mask) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* boxes = reinterpret_cast<float*>(smem);
-  int* cand = reinterpret_cast<int*>(boxes + 6 * nb);
+  float* boxes = reinterpret_cast<float*>(smem);  // kBoxStride floats per box (16-byte aligned rows)
+  int* cand = reinterpret_cast<int*>(boxes + kBoxStride * nb);
   uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kWarps * kCandCap);
   float2* xi_s = reinterpret_cast<float2*>(smem + edge_mask_fixed_smem(nb));
-  for (int k = threadIdx.x; k < 6 * nb; k += blockDim.x) boxes[k] = boxes_g[k];
+  for (int k = threadIdx.x; k < kBoxStride * nb; k += blockDim.x) {
+    const int o = k / kBoxStride, c = k - o * kBoxStride;
+    boxes[k] = c < 6 ? boxes_g[6 * o + c] : 0.f;
+  }
   const int xi_n = (W + 1) * 3 * N;
   if (kSmemXi)
     for (int k = threadIdx.x; k < xi_n; k += blockDim.x) xi_s[k] = xi_g[k];
@@ -142,7 +210,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restr
       const int o = base + lane;
       bool ov = false;
       if (o < nb) {
-        const float* b = boxes + 6 * o;
+        const float* b = boxes + kBoxStride * o;
         ov = b[0] <= hi0 && lo0 <= b[3] && b[1] <= hi1 && lo1 <= b[4] && b[2] <= hi2 && lo2 <= b[5];
       }
       const unsigned bal = __ballot_sync(0xffffffffu, ov);
@@ -157,7 +225,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restr
     if (narrow) {
       // boxes per waypoint: lane c tests candidate c against waypoint k's position box
       const float M = __uint_as_float(dmax[e]);
-      const float* bc = boxes + 6 * my_cand[lane < n_cand ? lane : 0];
+      const float* bc = boxes + kBoxStride * my_cand[lane < n_cand ? lane : 0];
       k_last = 0;
       for (int k = 1; k <= W; ++k) {
         const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
@@ -178,63 +246,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_mask(const float2* __restr
     const int nc = all ? nb : n_cand;
     const float P[4] = {phi[4 * e], phi[4 * e + 1], phi[4 * e + 2], phi[4 * e + 3]};
     const float L[3] = {Lg[3 * e], Lg[3 * e + 1], Lg[3 * e + 2]};
-    // up to kPW words per pass: lane l runs particles 32 (w0 + j) + l, j < kPW, side by side
-    for (int w0 = 0; w0 < w; w0 += kPW) {
-      const int nw = min(kPW, w - w0);
-      float d0[kPW][3], d1[kPW][3];
-      bool hit[kPW];
-#pragma unroll
-      for (int j = 0; j < kPW; ++j) {
-        hit[j] = j >= nw;  // absent words count as hit (they never block the early exit)
-        if (j < nw) {
-          const int i = (w0 + j) * 32 + lane;
-#pragma unroll
-          for (int a = 0; a < 3; ++a) dev_init(linf, xi[(size_t)a * N + i], d0[j][a], d1[j][a]);
-        }
-      }
-      for (int k = 1; k <= k_last; ++k) {
-        const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
-        float p[kPW][3];
-#pragma unroll
-        for (int j = 0; j < kPW; ++j) {
-          if (j < nw) {
-            const int i = (w0 + j) * 32 + lane;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) dev_step(P, L, xi[((size_t)k * 3 + a) * N + i], d0[j][a], d1[j][a]);
-            p[j][0] = __fadd_rn(n0, d0[j][0]);
-            p[j][1] = __fadd_rn(n1, d0[j][1]);
-            p[j][2] = __fadd_rn(n2, d0[j][2]);
-          }
-        }
-        if (narrow) {
-          unsigned bits = wm[k - 1];
-          while (bits) {
-            const int c = __ffs(bits) - 1;
-            bits &= bits - 1u;
-            const float* b = boxes + 6 * my_cand[c];
-#pragma unroll
-            for (int j = 0; j < kPW; ++j)
-              if (j < nw && !hit[j]) hit[j] = in_box_dev(p[j][0], p[j][1], p[j][2], b);
-          }
-        } else {
-          for (int c = 0; c < nc; ++c) {
-            const float* b = boxes + 6 * (all ? c : my_cand[c]);
-#pragma unroll
-            for (int j = 0; j < kPW; ++j)
-              if (j < nw && !hit[j]) hit[j] = in_box_dev(p[j][0], p[j][1], p[j][2], b);
-          }
-        }
-        bool done = true;
-#pragma unroll
-        for (int j = 0; j < kPW; ++j) done = done && hit[j];
-        if (__all_sync(0xffffffffu, done)) break;
-      }
-#pragma unroll
-      for (int j = 0; j < kPW; ++j) {
-        const unsigned bits = __ballot_sync(0xffffffffu, hit[j]);
-        if (j < nw && lane == 0) mask[(size_t)e * w + w0 + j] = bits;
-      }
+    uint32_t* out = mask + (size_t)e * w;
+    int w0 = 0;
+    for (; w0 + 4 <= w; w0 += 4) word_pass<4>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
+    if (w0 + 2 <= w) {
+      word_pass<2>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
+      w0 += 2;
     }
+    if (w0 < w) word_pass<1>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
     __syncwarp();
   }
 }
