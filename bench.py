@@ -211,6 +211,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="indoor_4k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=150,
+                    help="requests of the served leg (Poisson arrivals, continuous batching); 0 skips it")
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="arrival rate of the served leg (requests/s)")
     ap.add_argument("--batch-queries", type=int, default=256,
                     help="queries of the batched leg (uneven sizes, one persistent Explore launch); 0 skips it")
     args = ap.parse_args()
@@ -345,6 +348,8 @@ def main():
     }
     if args.batch_queries > 0:
         line["batched"] = batched_measure(pump, args, dev, flush, rank, ws)
+    if args.serve_requests > 0:
+        line["served"] = served_measure(pump, args, rank, ws)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import cpu
         cpu.build()
@@ -373,6 +378,51 @@ def measured_traffic(kernel):
     if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
         return None
     return float(rec["dram_bytes_per_launch"])
+
+
+def served_measure(pump, args, rank, ws):
+    """The served form: args.serve_requests requests with Poisson arrivals at args.serve_rate per
+    second (samples U{1000..16000}, boxes U{5..50}, N in {64, 128, 256}, W = 10, CP 1 %), each a
+    whole query from host arrays (graph build + masks + Explore + PlanSelection with MC).  Latency
+    is arrival to result.  Continuous batching (8 slots, requests admitted as slots and device
+    memory free up) against the plain sequential FIFO (1 slot), same arrivals."""
+    from paper_1607_06886_gb300 import inputs
+    R, rate = args.serve_requests, args.serve_rate
+    wls = inputs.batch_workloads(R, seed=2000 * (rank + 1), n_range=(1000, 16000))
+    gaps = np.random.default_rng(12345 + rank).exponential(1.0 / rate, size=R)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    prms = [pump.default_plan_params(alpha=w.alpha, eta=w.eta, lam=w.lam, n_mc=w.n_mc, mc_substeps=w.mc_substeps,
+                                     mc_seed=w.mc_seed) for w in wls]
+
+    def run(slots):
+        srv = pump.Server(slots, 64 << 30)
+        tickets = []
+        t0 = time.perf_counter()
+        for k, (w, p) in enumerate(zip(wls, prms)):
+            delay = t0 + arrivals[k] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(w.states, w.goal_idx, w.boxes, w.xi, w.radius, w.n_particles, w.n_waypoints,
+                                      w.sigma, p))
+        res = [srv.wait(t) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = np.array([r["latency_ms"] for r in res])
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "throughput_rps": R / wall, "peak_running": st["peak_running"],
+                "ok": int(sum(r["rc"] in (pump.OK, pump.ERR_INFEASIBLE) for r in res))}, res
+
+    cont, rc_ = run(8)
+    seq, rs_ = run(1)
+    keys = ("status", "chosen_plan", "cost", "mc_collisions", "n_candidates", "n_plans")
+    same = all(all(a[k] == b[k] for k in keys) for a, b in zip(rc_, rs_))
+    cands = sum(r["n_candidates"] for r in rc_)
+    return {"workload": f"served_{R}_at_{rate:g}rps", "requests": R, "arrival_rate_rps": rate,
+            "continuous_batching": dict(cont, slots=8), "sequential_fifo": dict(seq, slots=1),
+            "p99_speedup": seq["p99_ms"] / cont["p99_ms"], "results_equal": bool(same), "partial_plans": cands,
+            "includes": "graph build from host arrays + masks + Explore + PlanSelection with MC + readback",
+            "inputs": "seeded synthetic: samples U{1000..16000}, boxes U{5..50}, N in {64,128,256}, W=10, CP 1%"}
 
 
 def batched_measure(pump, args, dev, flush, rank, ws):

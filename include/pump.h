@@ -229,6 +229,60 @@ int pump_plan_batch(pump_graph* const* graphs, int32_t n_queries, const pump_pla
                     const pump_batch_config* config, pump_plan_result* results, void* stream);
 
 /* --------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching (no counterpart in the
+ * paper; a deployment form of Algorithm 2 for a stream of queries).
+ *
+ * A server owns `max_slots` slots, each a CUDA stream with a worker thread on
+ * the device current at creation.  Submitted requests wait in arrival order
+ * and are admitted as soon as a slot is free and their estimated device memory
+ * fits in `device_bytes` next to the admitted ones (a request larger than the
+ * whole budget runs alone).  An admitted request builds its graph from its
+ * arrays (pump_graph_build), plans (pump_plan) and frees the graph; requests in
+ * different slots run concurrently on the device.  Every result equals the
+ * result of the same calls made alone.  Device memory comes from the installed
+ * allocator (pump_set_allocator), called from the worker threads.
+ */
+typedef struct pump_server pump_server;
+typedef struct {
+  const float* states;      /* n x 6, as pump_graph_build (host)            */
+  int32_t n;
+  int32_t start_idx;
+  const int32_t* goal_idx;  /* n_goal node ids (host)                       */
+  int32_t n_goal;
+  const pump_aabb* boxes;   /* n_boxes (host)                               */
+  int32_t n_boxes;
+  const float* xi;          /* N x (W+1) x 3 x 2 (host)                      */
+  pump_graph_params graph;
+  pump_plan_params plan;
+} pump_request;
+
+/* Creates a server.  max_slots in [1, 64]; device_bytes > 0.
+ * Errors: INVALID_ARG, CUDA. */
+int pump_server_create(int32_t max_slots, int64_t device_bytes, pump_server** out);
+
+/* Queues a request (its arrays are copied before the call returns) and
+ * writes its ticket.  Errors: INVALID_ARG (bad arrays or sizes, server
+ * stopping), OOM (host memory). */
+int pump_server_submit(pump_server* s, const pump_request* req, int64_t* ticket);
+
+/* Waits up to timeout_s seconds for a ticket.  On completion writes the
+ * result (as pump_plan writes it), up to path_cap path node ids, the
+ * latency from submission to completion in milliseconds, returns the
+ * request's status, and forgets the ticket.  Returns PUMP_ERR_TIMEOUT if the
+ * request is not done yet (the ticket stays valid), INVALID_ARG for an
+ * unknown ticket. */
+int pump_server_wait(pump_server* s, int64_t ticket, double timeout_s, pump_plan_result* out, int32_t* path,
+                     int32_t path_cap, double* latency_ms);
+
+/* Counters: submitted, admitted, completed, queued, running, peak running,
+ * estimated bytes in use, peak estimated bytes (8 int64). */
+int pump_server_stats(pump_server* s, int64_t* counters);
+
+/* Stops the server: requests not yet admitted are dropped, admitted ones
+ * finish; then the workers exit and the streams are released. */
+void pump_server_destroy(pump_server* s);
+
+/* --------------------------------------------------------------------------
  * pump_certify: MC(p) (Section III-A) for the plan visiting `path`
  * (path_len >= 1 node ids, consecutive ones joined by graph edges).  n_mc
  * rollouts of the closed loop: deviation drawn from the stationary

@@ -27,6 +27,7 @@ UNITS = {
     "explore.cu": [],
     "explore_cluster.cu": [],
     "batch.cu": [],
+    "server.cu": [],
     "select.cu": [],
     "noalloc.cu": [],
 }
@@ -72,7 +73,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if relink:
         objs = [os.path.join(BUILD, u.replace(".cu", ".o")) for u in UNITS]
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode:
             sys.stderr.write(res.stdout + res.stderr)

@@ -252,6 +252,18 @@ static void destroy(pump_graph* g) {
   delete g;
 }
 
+// Frees a graph whose work was all issued on stream s: waits for s only, so other streams keep
+// running (the server's workers).
+void destroy_on_stream(pump_graph* g, cudaStream_t s) {
+  if (!g) return;
+  cudaStreamSynchronize(s);
+  for (auto& b : g->bufs) dev_free(b.ptr, s);
+  for (auto& e : g->ev)
+    if (e) cudaEventDestroy(e);
+  cudaStreamSynchronize(s);
+  delete g;
+}
+
 int check_plan_params(const pump_plan_params* p) {
   if (!p) return PUMP_ERR_INVALID_ARG;
   if (!(p->alpha >= 0.f) || !(p->alpha <= 1.f) || !(p->eta > 0.f) || !std::isfinite(p->eta)) return PUMP_ERR_INVALID_ARG;

@@ -204,6 +204,7 @@ int ensure_edge_targets(pump_graph* g, cudaStream_t s);
 int prepare_explore_args(pump_graph* g, const pump_plan_params* p, float radius, ExploreArgs* out, cudaStream_t s);
 int check_plan_params(const pump_plan_params* p);
 int make_events(pump_graph* g);
+void destroy_on_stream(pump_graph* g, cudaStream_t s);
 int compute_edge_masks(pump_graph* g, cudaStream_t s);
 // Explore kernel form from pump_plan_params.flags (see run_explore_kernels).
 inline int explore_mode(int32_t flags) {

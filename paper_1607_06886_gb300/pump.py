@@ -42,6 +42,12 @@ class PlanParams(C.Structure):
                 ("max_iterations", C.c_int32), ("flags", C.c_int32)]
 
 
+class Request(C.Structure):
+    _fields_ = [("states", C.c_void_p), ("n", C.c_int32), ("start_idx", C.c_int32), ("goal_idx", C.c_void_p),
+                ("n_goal", C.c_int32), ("boxes", C.c_void_p), ("n_boxes", C.c_int32), ("xi", C.c_void_p),
+                ("graph", GraphParams), ("plan", PlanParams)]
+
+
 class BatchConfig(C.Structure):
     _fields_ = [("cluster_size", C.c_int32), ("mbest_global", C.c_int32), ("max_clusters", C.c_int32),
                 ("reserved", C.c_int32)]
@@ -100,6 +106,12 @@ def load(build_if_missing: bool = False):
     L.pump_explore_noalloc.argtypes = [i32, P, P, P, P, i32, i32, P, f32, C.POINTER(PlanParams), i64,
                                        P, P, P, P, P, P, P, P, C.POINTER(PlanResult), P]
     L.pump_plan_batch.argtypes = [P, i32, P, C.POINTER(BatchConfig), P, P]
+    L.pump_server_create.argtypes = [i32, i64, C.POINTER(P)]
+    L.pump_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(i64)]
+    L.pump_server_wait.argtypes = [P, i64, C.c_double, C.POINTER(PlanResult), P, i32, C.POINTER(C.c_double)]
+    L.pump_server_stats.argtypes = [P, P]
+    L.pump_server_destroy.argtypes = [P]
+    L.pump_server_destroy.restype = None
     L.pump_kernel_launches.argtypes = []
     L.pump_kernel_launches.restype = C.c_uint64
     L.pump_status_str.argtypes = [C.c_int]
@@ -131,6 +143,62 @@ def plan_batch(graphs, params, config: Optional["BatchConfig"] = None, stream: O
     return rc, out
 
 
+class Server:
+    """pump_server: continuous batching over `slots` CUDA streams within `device_bytes` (estimated)."""
+
+    def __init__(self, slots: int, device_bytes: int):
+        h = C.c_void_p()
+        rc = load().pump_server_create(int(slots), int(device_bytes), C.byref(h))
+        if rc:
+            raise PumpError(rc, "pump_server_create")
+        self._h = h
+
+    def submit(self, states, goal_idx, boxes, xi, radius: float, n_particles: int, n_waypoints: int, sigma: float,
+               plan: "PlanParams", start_idx: int = 0) -> int:
+        # host arrays (the server copies them before submit returns)
+        st = np.ascontiguousarray(states, dtype=np.float32).reshape(-1, 6)
+        gi = np.ascontiguousarray(goal_idx, dtype=np.int32).ravel()
+        bx = np.ascontiguousarray(boxes, dtype=np.float32).reshape(-1, 6)
+        x = np.ascontiguousarray(xi, dtype=np.float32)
+        req = Request(st.ctypes.data, st.shape[0], int(start_idx), gi.ctypes.data, gi.size,
+                      bx.ctypes.data if bx.size else None, bx.shape[0], x.ctypes.data,
+                      GraphParams(float(radius), int(n_particles), int(n_waypoints), float(sigma), 0), plan)
+        t = C.c_int64()
+        rc = load().pump_server_submit(self._h, C.byref(req), C.byref(t))
+        if rc:
+            raise PumpError(rc, "pump_server_submit")
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout: float = 600.0, path_cap: int = 4097) -> Dict:
+        res = PlanResult()
+        path = np.zeros(max(path_cap, 1), np.int32)
+        lat = C.c_double()
+        rc = load().pump_server_wait(self._h, int(ticket), float(timeout), C.byref(res), _ptr(path), int(path_cap),
+                                     C.byref(lat))
+        d = res.as_dict()
+        d["rc"] = rc
+        d["path"] = path[:max(min(res.path_len, path_cap), 0)].copy()
+        d["latency_ms"] = float(lat.value)
+        return d
+
+    def stats(self) -> Dict:
+        c = np.zeros(8, np.int64)
+        load().pump_server_stats(self._h, _ptr(c))
+        keys = ("submitted", "admitted", "completed", "queued", "running", "peak_running", "bytes_in_use", "peak_bytes")
+        return {k: int(v) for k, v in zip(keys, c)}
+
+    def close(self):
+        if self._h:
+            load().pump_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def kernel_launches() -> int:
     return int(load().pump_kernel_launches())
 
@@ -140,12 +208,16 @@ def status_str(st: int) -> str:
 
 
 def use_torch_allocator() -> None:
-    """Route the library's device allocations to torch's caching allocator."""
+    """Route the library's device allocations to torch's caching allocator.
+
+    Each block is allocated on the stream the library will use it on (the caching allocator then
+    reuses a freed block only in that stream's order), on the calling thread's current device."""
     import torch
 
     def _alloc(nbytes, stream, ctx):
         try:
-            return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                          int(stream) if stream else 0))
         except Exception:  # allocation failure is reported to the library as NULL
             return None
 
