@@ -184,32 +184,77 @@ __device__ inline bool steer_refined(const double* xv, const double* xu, const f
 }
 
 // Collision(v, u): the nominal connection of duration tau (float) sampled at
-// t_m = tau (m / 4W), m = 1..4W, positions rounded to float, closed boxes.
-// frac[m-1] = m / (4W) in double, shared by the block.  Before sampling, a box holding the whole
-// cubic on [0, tau] (p0 +- (|v0| tau + |c2| tau^2 + |c3| tau^3), widened by 1e-6 against
-// rounding) is tested; no obstacle in it means no sample can hit.
-__device__ inline bool connection_hits(const double* xv, const double* xu, double tau, int W, const float* boxes,
-                                       int nb, const double* frac) {
-  const Cubic c[3] = {cubic_dev(xv, xu, tau, 0), cubic_dev(xv, xu, tau, 1), cubic_dev(xv, xu, tau, 2)};
-  float lo[3], hi[3];
+// t_m = tau (m / 4W), m = 1..4W, positions (the double cubic at t_m) rounded to float, closed
+// boxes; frac[m-1] = m / (4W) in double.  Evaluated in float with a rounding margin: the
+// definition's sample position is the double cubic at t_m rounded to float; the float cubic
+// (coefficients and Horner steps in float) is within eps of it, where eps bounds the rounding of
+// every float step by 2^-15 (1 + M), M the largest |p0| + |v0| tau + |c2| tau^2 + |c3| tau^3 of
+// the three axes (the actual error is below 2^-19 (1 + M)).  A sample more than eps outside a box
+// on some axis misses it, one more than eps inside on every axis hits it; only samples within eps
+// of a face are evaluated the definition's way, in double.
+__device__ inline bool connection_hits_fast(const float* fv, const float* fu, const double* xv, const double* xu,
+                                            double td, int W, const float* boxes, int nb, const double* frac,
+                                            const float* fracf) {
+  const float tau = (float)td;  // td holds a float value exactly
+  float p0[3], v0[3], c2[3], c3[3], R[3];
+  float M = 0.f;
   for (int a = 0; a < 3; ++a) {
-    const double R = fabs(c[a].v0) * tau + fabs(c[a].c2) * tau * tau + fabs(c[a].c3) * tau * tau * tau;
-    lo[a] = (float)(c[a].p0 - R) - 1e-6f;
-    hi[a] = (float)(c[a].p0 + R) + 1e-6f;
+    p0[a] = fv[a];
+    v0[a] = fv[3 + a];
+    const float dp = fu[a] - p0[a] - v0[a] * tau, dv = fu[3 + a] - v0[a];
+    c2[a] = (3.f * dp - dv * tau) / (tau * tau);
+    c3[a] = (dv * tau - 2.f * dp) / (tau * tau * tau);
+    R[a] = fabsf(v0[a]) * tau + fabsf(c2[a]) * tau * tau + fabsf(c3[a]) * tau * tau * tau;
+    M = fmaxf(M, fabsf(p0[a]) + R[a]);
   }
-  bool near = false;
-  for (int o = 0; o < nb && !near; ++o) {
+  const float eps = (1.f + M) * 3.0517578125e-5f;  // 2^-15 (1 + M)
+  // boxes the connection can reach: p0 +- (R + eps) per axis (the first 64; beyond that all boxes)
+  unsigned long long cand = 0ull;
+  const int nc = nb < 64 ? nb : 64;
+  for (int o = 0; o < nc; ++o) {
     const float* b = boxes + 6 * o;
-    near = b[0] <= hi[0] && lo[0] <= b[3] && b[1] <= hi[1] && lo[1] <= b[4] && b[2] <= hi[2] && lo[2] <= b[5];
+    bool ov = true;
+    for (int a = 0; a < 3; ++a) ov = ov && b[a] <= p0[a] + R[a] + eps && p0[a] - R[a] - eps <= b[3 + a];
+    if (ov) cand |= 1ull << o;
   }
-  if (!near) return false;
+  const bool rest = nb > 64;
+  if (!cand && !rest) return false;
+  bool have_exact = false;
+  Cubic c[3];
   for (int m = 1; m <= 4 * W; ++m) {
-    const double t = tau * frac[m - 1];
-    const float p0 = (float)cubic_at(c[0], t);
-    const float p1 = (float)cubic_at(c[1], t);
-    const float p2 = (float)cubic_at(c[2], t);
-    for (int o = 0; o < nb; ++o)
-      if (in_box_dev(p0, p1, p2, boxes + 6 * o)) return true;
+    const float t = tau * fracf[m - 1];
+    float p[3];
+    for (int a = 0; a < 3; ++a) p[a] = fmaf(fmaf(fmaf(c3[a], t, c2[a]), t, v0[a]), t, p0[a]);
+    unsigned long long bits = cand;
+    int o = -1;
+    for (;;) {
+      if (bits) {
+        o = __ffsll((long long)bits) - 1;
+        bits &= bits - 1ull;
+      } else if (rest && o < 64) {
+        o = 64;
+      } else if (rest && o >= 64 && o + 1 < nb) {
+        ++o;
+      } else {
+        break;
+      }
+      const float* b = boxes + 6 * o;
+      bool out = false, in = true;
+      for (int a = 0; a < 3; ++a) {
+        out = out || p[a] < b[a] - eps || p[a] > b[3 + a] + eps;
+        in = in && p[a] >= b[a] + eps && p[a] <= b[3 + a] - eps;
+      }
+      if (out) continue;
+      if (in) return true;
+      if (!have_exact) {
+        c[0] = cubic_dev(xv, xu, td, 0);
+        c[1] = cubic_dev(xv, xu, td, 1);
+        c[2] = cubic_dev(xv, xu, td, 2);
+        have_exact = true;
+      }
+      const double te = td * frac[m - 1];
+      if (in_box_dev((float)cubic_at(c[0], te), (float)cubic_at(c[1], te), (float)cubic_at(c[2], te), b)) return true;
+    }
   }
   return false;
 }
@@ -218,9 +263,13 @@ __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __re
                               int n, float r, int W, const float* __restrict__ boxes_g, int nb, uint32_t* keep,
                               double* __restrict__ res_tau, float* __restrict__ res_cost) {
   extern __shared__ double frac[];
-  float* boxes = reinterpret_cast<float*>(frac + 4 * W);
+  float* fracf = reinterpret_cast<float*>(frac + 4 * W);
+  float* boxes = fracf + 4 * W;
   for (int k = threadIdx.x; k < 6 * nb; k += blockDim.x) boxes[k] = boxes_g[k];
-  for (int m = threadIdx.x; m < 4 * W; m += blockDim.x) frac[m] = (double)(m + 1) / (double)(4 * W);
+  for (int m = threadIdx.x; m < 4 * W; m += blockDim.x) {
+    frac[m] = (double)(m + 1) / (double)(4 * W);
+    fracf[m] = (float)frac[m];
+  }
   __syncthreads();
   const int nw = (n + 31) / 32;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n_list;
@@ -246,7 +295,7 @@ __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __re
     if (!(est ? steer_refined(xv, xu, tmin, Jmin, nm, &tau, &J) : steer_dev(xv, xu, &tau, &J))) continue;
     if (!(__double2float_rn(J) < r)) continue;
     double td = (double)__double2float_rn(tau);
-    if (connection_hits(xv, xu, td, W, boxes, nb, frac)) continue;
+    if (connection_hits_fast(fv, fu, xv, xu, td, W, boxes, nb, frac, fracf)) continue;
     res_tau[q] = tau;
     res_cost[q] = __double2float_rn(J);
     atomicOr(keep + (size_t)vu.x * nw + (vu.y >> 5), 1u << (vu.y & 31));
@@ -429,7 +478,7 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   long long list_blocks = ((long long)n_list + kBlock - 1) / kBlock;
   const int glist = (int)(list_blocks < (long long)sms * 16 ? (list_blocks > 0 ? list_blocks : 1) : (long long)sms * 16);
   if (n_list) {
-    k_steer_pairs<<<glist, kBlock, sizeof(double) * 4 * g->W + sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1), s>>>(
+    k_steer_pairs<<<glist, kBlock, (sizeof(double) + sizeof(float)) * 4 * g->W + sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1), s>>>(
         g->states, list, (long long)n_list, n, g->radius, g->W, g->boxes, g->n_boxes, keep, res_tau, res_cost);
     note_launch();
   }
