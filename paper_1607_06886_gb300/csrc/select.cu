@@ -202,7 +202,7 @@ __device__ __forceinline__ void mc_normals(uint64_t seed, uint64_t m, uint64_t s
 }
 
 constexpr int kMcThreads = 128;
-constexpr int kMcTableSmem = 24 * 1024;  // floats of a plan's table staged in shared memory
+constexpr int kMcTableSmem = 4096;  // floats of a plan's table staged in shared memory (larger: read from L2)
 
 // Box test of a position: with nb <= 32 and every |d0| <= B only the path edge's candidate
 // boxes (bits) can hold it; otherwise all boxes are tested.
@@ -235,8 +235,16 @@ __device__ __forceinline__ void mc_update(const float* z, float P0, float P1, fl
   }
 }
 
-// One thread per rollout; plan k = blockIdx.x / bpp.  Normals of two consecutive steps are drawn
-// before either update (independent Philox chains overlap).
+// kMcLanes lanes per rollout; plan k = blockIdx.x / bpp.  The normals of a step depend only on
+// (seed, rollout, step), so the lanes of a rollout draw the normals of consecutive steps in
+// parallel (lane j takes steps j, j + kMcLanes, ...; Philox4x64 dominates the work) and pass
+// them round by group shuffles; every lane of the group then applies the same updates in step
+// order, so all of them hold the same deviation and the same hit flag.
+#ifndef PUMP_MC_LANES
+#define PUMP_MC_LANES 2  // measured best of 1, 2, 4, 8
+#endif
+constexpr int kMcLanes = PUMP_MC_LANES;
+
 __global__ void __launch_bounds__(kMcThreads) k_mc_rollout(const int32_t* __restrict__ n_cert_p, int bpp,
                                                             const int32_t* __restrict__ plen,
                                                             const float* __restrict__ table, int W, int S,
@@ -258,10 +266,14 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_rollout(const int32_t* __rest
     for (int q = threadIdx.x; q < tfl; q += blockDim.x) tab[q] = T0[q];
   __syncthreads();
   const float* T = tab_smem ? tab : T0;
-  const int m = (blockIdx.x % bpp) * kMcThreads + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int j = lane % kMcLanes;                        // lane within the rollout's group
+  const int g0 = lane - j;                              // first lane of the group
+  const unsigned gmask = ((1u << kMcLanes) - 1u) << g0;
+  const int m = (blockIdx.x % bpp) * (kMcThreads / kMcLanes) + threadIdx.x / kMcLanes;
   bool hit = false;
   if (m < n_mc) {
-    float z[6], zb[6], d0[3], d1[3], p[3];
+    float z[6], d0[3], d1[3], p[3];
     mc_normals(seed, (uint64_t)m, 0ull, z);
     const float l0 = linf_g[0], l1 = linf_g[1], l2 = linf_g[2];
 #pragma unroll
@@ -270,27 +282,34 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_rollout(const int32_t* __rest
       d1[a] = fmaf(l1, z[2 * a], __fmul_rn(l2, z[2 * a + 1]));
     }
     const int WS = W * S;
-    uint64_t step = 0;
+    uint64_t step = 0;  // steps taken before this edge
     for (int e = 0; e < L && !hit; ++e) {
       const float* Te = T + (size_t)e * stride;
       const float P0 = Te[0], P1 = Te[1], P2 = Te[2], P3 = Te[3], L0 = Te[4], L1 = Te[5], L2 = Te[6];
       const uint32_t bits = __float_as_uint(Te[7]);
-      for (int q = 0; q < WS && !hit; q += 2) {
-        const bool two = q + 1 < WS;
-        mc_normals(seed, (uint64_t)m, step + 1, z);
-        if (two) mc_normals(seed, (uint64_t)m, step + 2, zb);
-        mc_update(z, P0, P1, P2, P3, L0, L1, L2, Te + 8 + q * 3, d0, d1, p);
-        hit = mc_hit(p, d0, B, bits, boxes, nb);
-        if (two && !hit) {
-          mc_update(zb, P0, P1, P2, P3, L0, L1, L2, Te + 8 + (q + 1) * 3, d0, d1, p);
+      for (int q0 = 0; q0 < WS && !hit; q0 += kMcLanes) {
+        float zj[6];
+        if (q0 + j < WS) {
+          mc_normals(seed, (uint64_t)m, step + (uint64_t)(q0 + j) + 1ull, zj);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) zj[c] = 0.f;
+        }
+        const int nq = min(kMcLanes, WS - q0);
+#pragma unroll
+        for (int t = 0; t < kMcLanes; ++t) {
+          if (t >= nq || hit) break;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) z[c] = __shfl_sync(gmask, zj[c], g0 + t);
+          mc_update(z, P0, P1, P2, P3, L0, L1, L2, Te + 8 + (q0 + t) * 3, d0, d1, p);
           hit = mc_hit(p, d0, B, bits, boxes, nb);
         }
-        step += two ? 2 : 1;
       }
+      step += (uint64_t)WS;
     }
   }
-  const unsigned bal = __ballot_sync(0xffffffffu, hit);
-  if ((threadIdx.x & 31) == 0 && bal) atomicAdd(counts + k, (unsigned long long)__popc(bal));
+  const unsigned bal = __ballot_sync(0xffffffffu, hit && j == 0);
+  if (lane == 0 && bal) atomicAdd(counts + k, (unsigned long long)__popc(bal));
 }
 
 __global__ void k_counts_store(const SelState* __restrict__ st, const unsigned long long* __restrict__ counts,
@@ -409,7 +428,8 @@ int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert_max, int n_mc,
                                 g->sigma, g->boxes, g->n_boxes, B, X.mc_table);
   note_launch();
   PUMP_CUDA_TRY(cudaMemsetAsync(X.mc_count, 0, sizeof(int64_t) * n_cert_max, s));
-  const int bpp = (n_mc + kMcThreads - 1) / kMcThreads;
+  const int per_block = kMcThreads / kMcLanes;
+  const int bpp = (n_mc + per_block - 1) / per_block;
   if (n_mc > 0 && bpp > 0) {
     const size_t smem = sizeof(float) * (6 * (size_t)std::max(g->n_boxes, 1) + kMcTableSmem);
     PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
