@@ -211,6 +211,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="indoor_4k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hsmc-seeds", type=int, default=8,
+                    help="queries of the HSMC leg (CP-hat vs Monte Carlo for box and half-space masks); 0 skips it")
     ap.add_argument("--serve-requests", type=int, default=150,
                     help="requests of the served leg (Poisson arrivals, continuous batching); 0 skips it")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="arrival rate of the served leg (requests/s)")
@@ -350,6 +352,8 @@ def main():
         line["batched"] = batched_measure(pump, args, dev, flush, rank, ws)
     if args.serve_requests > 0:
         line["served"] = served_measure(pump, args, rank, ws)
+    if args.hsmc_seeds > 0:
+        line["hsmc"] = hsmc_measure(pump, args, dev, flush)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import cpu
         cpu.build()
@@ -378,6 +382,67 @@ def measured_traffic(kernel):
     if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
         return None
     return float(rec["dram_bytes_per_launch"])
+
+
+def hsmc_measure(pump, args, dev, flush):
+    """Half-Space Monte Carlo masks (the paper's CP approximation) beside the particle-in-box masks
+    on the indoor workload: graph build and mask-pass times, and over args.hsmc_seeds queries the
+    selected plan's CP-hat against its Monte Carlo CP for each mask kind."""
+    import torch
+    from paper_1607_06886_gb300 import inputs
+    todev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=5):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts)), out
+
+    wl = inputs.make_workload(args.workload, 0)
+    build = lambda f: pump.Graph.build(todev(wl.states), todev(wl.goal_idx), todev(wl.boxes), todev(wl.xi), wl.radius,
+                                       wl.n_particles, wl.n_waypoints, wl.sigma, flags=f)
+    t_build_box, Gb = timed(lambda: build(0), reps=3)
+    t_build_hs, Gh = timed(lambda: build(pump.GRAPH_HSMC), reps=3)
+    t_mask_box, _ = timed(Gb.edge_masks)
+    t_mask_hs, _ = timed(Gh.edge_masks)
+    Gb.close()
+    Gh.close()
+    rows = []
+    for seed in range(args.hsmc_seeds):
+        w = inputs.make_workload(args.workload, seed)
+        prm = pump.default_plan_params(alpha=w.alpha, eta=w.eta, lam=w.lam, n_mc=w.n_mc, mc_substeps=w.mc_substeps,
+                                       mc_seed=w.mc_seed)
+        row = {"seed": seed}
+        for kind, f in (("box", 0), ("hsmc", pump.GRAPH_HSMC)):
+            G = pump.Graph.build(todev(w.states), todev(w.goal_idx), todev(w.boxes), todev(w.xi), w.radius,
+                                 w.n_particles, w.n_waypoints, w.sigma, flags=f)
+            r = G.plan(prm)
+            G.close()
+            row[kind] = {"status": r["status"], "cp_hat": r["cp_hat"], "cp_mc": r["cp_mc"], "cost": r["cost"],
+                         "partial_plans": r["n_candidates"]}
+        rows.append(row)
+
+    def summary(kind):
+        ok = [r[kind] for r in rows if r[kind]["status"] == pump.OK]
+        if not ok:
+            return {"queries_solved": 0}
+        err = np.array([x["cp_hat"] - x["cp_mc"] for x in ok])
+        return {"queries_solved": len(ok), "mean_cp_hat": float(np.mean([x["cp_hat"] for x in ok])),
+                "mean_cp_mc": float(np.mean([x["cp_mc"] for x in ok])), "mean_abs_err": float(np.mean(np.abs(err))),
+                "mean_cost": float(np.mean([x["cost"] for x in ok]))}
+
+    return {"workload": args.workload, "build_ms": {"box": t_build_box, "hsmc": t_build_hs},
+            "mask_ms": {"box": t_mask_box, "hsmc": t_mask_hs}, "cp_target": wl.alpha,
+            "selected_plan_cp": {"box": summary("box"), "hsmc": summary("hsmc")}, "queries": rows,
+            "note": "cp_hat = particle estimate used by Explore (N particles); cp_mc = 10^4-rollout Monte Carlo of the same plan"}
 
 
 def served_measure(pump, args, rank, ws):

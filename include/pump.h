@@ -64,8 +64,20 @@ typedef struct {
   int32_t n_particles; /* N, a multiple of 32 in [32, 1024]; masks have N/32 words       */
   int32_t n_waypoints; /* W >= 1 waypoints per connection                                */
   float sigma;         /* process-noise standard deviation, V_c = sigma^2 I (Eq. (1))    */
-  int32_t flags;       /* reserved, 0                                                    */
+  int32_t flags;       /* 0, or PUMP_GRAPH_HSMC                                          */
 } pump_graph_params;
+
+/* Particle collision masks by Half-Space Monte Carlo (the paper's CP approximation, section
+ * "Half-Space Monte Carlo", Eq. (eq:hs)) instead of the particle-in-box test.  Per waypoint the
+ * graph build forms the local convex region of the nominal position y with nominal velocity v:
+ * repeatedly the remaining box closest to y (closest point c, ties to the lower box index),
+ * d = c - y, a half-space recorded and every remaining box lying in {z : d.(z - y) >= d.d}
+ * pruned (the closest box always), at most 8 half-spaces; each half-space is turned away from
+ * the direction of travel, a = d - ((d.v)/(v.v)) v (a = d if v = 0), b = a.a.  A particle with
+ * position deviation dy fires it iff fma(a2, dy2, fma(a1, dy1, a0 dy0)) > b; its mask bit is the
+ * OR over waypoints 1..W and half-spaces.  All of it in float, each operation rounded as
+ * written, left to right (a waypoint on or inside a box ends its region). */
+#define PUMP_GRAPH_HSMC 1
 
 typedef struct {
   float alpha;            /* CP target (Eq. (3))                                          */
@@ -324,9 +336,10 @@ enum {
   PUMP_EXPORT_PLAN_CREATED = 17, /* int32[n_plans] group index that created the plan (-1 root) */
   PUMP_EXPORT_PLAN_EXPANDED = 18, /* int32[n_plans] group index that expanded it, -1 if never */
   PUMP_EXPORT_GOAL_PLANS = 19,    /* int32[n_goal] P_goal ids in PlanSelection order */
-  PUMP_EXPORT_EDGE_BOX = 20       /* float[E][6] lo xyz, hi xyz: box holding every particle
+  PUMP_EXPORT_EDGE_BOX = 20,      /* float[E][6] lo xyz, hi xyz: box holding every particle
                                      position of the edge (graph build; pump_edge_masks skips
                                      the obstacles it misses) */
+  PUMP_EXPORT_NOMINAL_VEL = 21    /* float[E][W][3] nominal velocity at the waypoints */
 };
 int pump_export(pump_graph* g, int32_t what, void* host_buf, size_t cap, size_t* needed);
 

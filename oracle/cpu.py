@@ -60,6 +60,11 @@ def lib():
             L.orc_graph_export.argtypes = [P] * 11
             L.orc_graph_free.argtypes = [P]
             L.orc_edge_masks.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, C.c_int, P]
+            L.orc_graph_nvel.argtypes = [P, P]
+            L.orc_halfspaces.argtypes = [P, P, P, C.c_int, C.c_int, P, P]
+            L.orc_halfspaces.restype = C.c_int
+            L.orc_edge_masks_hs.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, P, C.c_int, C.c_int, P]
+            L.orc_edge_masks_hs.restype = C.c_int
             L.orc_explore.argtypes = [C.c_int, P, P, P, P, C.c_int, C.c_int, P, C.c_int, C.c_int,
                                       C.c_float, C.c_float, C.c_int64, C.c_int, C.c_int]
             L.orc_explore.restype = P
@@ -124,6 +129,8 @@ def graph_build(states, boxes, radius: float, W: int, sigma: float, exhaustive: 
                "nom": np.zeros((E, W, 3), np.float32), "linf": np.zeros(3, np.float32)}
         lib().orc_graph_export(g, *[_p(out[k]) for k in ("valid", "row_ptr", "col", "ecost", "tau", "h",
                                                           "phi", "L", "nom", "linf")])
+        out["nvel"] = np.zeros((E, W, 3), np.float32)
+        lib().orc_graph_nvel(g, _p(out["nvel"]))
         out.update(n=n, n_edges=E, W=W, pairs_costed=int(cnt[2]), n_near=int(cnt[3]),
                    n_collide_removed=int(cnt[4]))
         return out
@@ -149,6 +156,32 @@ def edge_masks(graph: Dict, xi, boxes, n_particles: int) -> np.ndarray:
     bx = _c(boxes, np.float32).reshape(-1, 6)
     lib().orc_edge_masks(E, W, n_particles, _p(graph["phi"]), _p(graph["L"]), _p(graph["nom"]),
                          _p(graph["linf"]), _p(x), _p(bx), bx.shape[0], _p(out))
+    return out
+
+
+def halfspaces(y, v, boxes, hmax: int = 8):
+    """HSMC local convex region of one waypoint (section 'Half-Space Monte Carlo', Eq. (eq:hs)):
+    (a (h, 3), b (h,)) in construction order."""
+    yy = _c(y, np.float32); vv = _c(v, np.float32)
+    bx = _c(boxes, np.float32).reshape(-1, 6)
+    a = np.zeros((max(hmax, 1), 3), np.float32); b = np.zeros(max(hmax, 1), np.float32)
+    k = lib().orc_halfspaces(_p(yy), _p(vv), _p(bx), bx.shape[0], int(hmax), _p(a), _p(b))
+    if k < 0:
+        raise MemoryError("oracle halfspaces failed")
+    return a[:k].copy(), b[:k].copy()
+
+
+def edge_masks_hs(graph: Dict, xi, boxes, n_particles: int, hmax: int = 8) -> np.ndarray:
+    """HSMC particle masks per edge (E, N/32) uint32."""
+    E, W = graph["n_edges"], graph["W"]
+    w = n_particles // 32
+    out = np.zeros((E, w), np.uint32)
+    x = _c(xi, np.float32)
+    bx = _c(boxes, np.float32).reshape(-1, 6)
+    rc = lib().orc_edge_masks_hs(E, W, n_particles, _p(graph["phi"]), _p(graph["L"]), _p(graph["nom"]),
+                                 _p(graph["nvel"]), _p(graph["linf"]), _p(x), _p(bx), bx.shape[0], int(hmax), _p(out))
+    if rc:
+        raise MemoryError("oracle HSMC masks failed")
     return out
 
 

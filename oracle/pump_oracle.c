@@ -122,6 +122,15 @@ int orc_steer(const double* x0, const double* x1, double* tau_out, double* cost_
   return 0;
 }
 
+/* Velocity of the optimal connection at time t (derivative of the cubic below). */
+static double nominal_vel(const double* x0, const double* x1, double tau, int j, double t) {
+  double p0 = x0[j], v0 = x0[3 + j], p1 = x1[j], v1 = x1[3 + j];
+  double dp = p1 - p0 - v0 * tau, dv = v1 - v0;
+  double c2 = (3.0 * dp - dv * tau) / (tau * tau);
+  double c3 = (dv * tau - 2.0 * dp) / (tau * tau * tau);
+  return v0 + 2.0 * c2 * t + 3.0 * c3 * t * t;
+}
+
 /* Position of the optimal connection at time t (per axis cubic), duration tau. */
 static double nominal_pos(const double* x0, const double* x1, double tau, int j, double t) {
   double p0 = x0[j], v0 = x0[3 + j], p1 = x1[j], v1 = x1[3 + j];
@@ -288,6 +297,7 @@ typedef struct {
   float* phi;   /* E x 4 */
   float* L;     /* E x 3 */
   float* nom;   /* E x W x 3 */
+  float* nvel;  /* E x W x 3: nominal velocity at the waypoints */
   float linf[3];
   int64_t n_pairs_costed, n_near, n_collide_removed;
 } orc_graph;
@@ -295,7 +305,7 @@ typedef struct {
 void orc_graph_free(orc_graph* g) {
   if (!g) return;
   free(g->valid); free(g->row_ptr); free(g->col); free(g->ecost); free(g->tau); free(g->h);
-  free(g->phi); free(g->L); free(g->nom); free(g);
+  free(g->phi); free(g->L); free(g->nom); free(g->nvel); free(g);
 }
 
 /* sigma is the problem's float noise level (as at the library boundary); it is widened to double. */
@@ -371,7 +381,8 @@ orc_graph* orc_graph_build(const float* states, int n, const float* boxes, int n
   g->phi = (float*)malloc(sizeof(float) * 4 * (E ? E : 1));
   g->L = (float*)malloc(sizeof(float) * 3 * (E ? E : 1));
   g->nom = (float*)malloc(sizeof(float) * 3 * (size_t)W * (E ? E : 1));
-  if (!g->h || !g->phi || !g->L || !g->nom) goto oom;
+  g->nvel = (float*)malloc(sizeof(float) * 3 * (size_t)W * (E ? E : 1));
+  if (!g->h || !g->phi || !g->L || !g->nom || !g->nvel) goto oom;
   {
     float phi_dummy[4], l_dummy[3];
     model_f32(g->sigma, 1.0f, phi_dummy, l_dummy, g->linf);
@@ -389,8 +400,10 @@ orc_graph* orc_graph_build(const float* states, int n, const float* boxes, int n
       double td = (double)g->tau[e];
       for (int k = 1; k <= W; ++k) {
         double tk = (double)k * (double)h;
-        for (int j = 0; j < 3; ++j)
+        for (int j = 0; j < 3; ++j) {
           g->nom[((size_t)e * W + (k - 1)) * 3 + j] = (float)nominal_pos(xv, xu, td, j, tk);
+          g->nvel[((size_t)e * W + (k - 1)) * 3 + j] = (float)nominal_vel(xv, xu, td, j, tk);
+        }
       }
     }
   }
@@ -404,6 +417,10 @@ oom:
 void orc_graph_counts(const orc_graph* g, int64_t* out /* n, E, pairs_costed, near, collide_removed */) {
   out[0] = g->n; out[1] = g->n_edges; out[2] = g->n_pairs_costed; out[3] = g->n_near;
   out[4] = g->n_collide_removed;
+}
+
+void orc_graph_nvel(const orc_graph* g, float* nvel) {
+  if (nvel) memcpy(nvel, g->nvel, sizeof(float) * 3 * (size_t)g->W * (size_t)g->n_edges);
 }
 
 void orc_graph_export(const orc_graph* g, uint8_t* valid, int32_t* row_ptr, int32_t* col, float* ecost,
@@ -455,6 +472,108 @@ void orc_edge_masks(int n_edges, int W, int N, const float* phi, const float* L,
       if (collisions > 0) mask[(size_t)e * w + i / 32] |= 1u << (i % 32);
     }
   }
+}
+
+/* ========================================================================== */
+/* O4h  HSMC edge masks (Section III-B, Half-Space Monte Carlo; Eq. (eq:hs)).   */
+/* Local convex region around a waypoint y (nominal position, float) with       */
+/* nominal velocity v: repeatedly take the remaining box closest to y (least    */
+/* squared distance from y to its closest point c, ties to the lower index),   */
+/* d = c - y; record the half-space and prune every remaining box lying in     */
+/* {z : d.(z - y) >= d.d} (the closest box always).  At most hmax half-spaces   */
+/* per waypoint.  Each half-space is turned away from the direction of travel: */
+/* a = d - ((d.v) / (v.v)) v (a = d if v = 0), b = a.a, and a particle with    */
+/* position deviation dy fires it iff a.dy > b.  Our reading fixes the          */
+/* arithmetic: float, every operation rounded as written (left to right), the  */
+/* test dot product as fma(a2, dy2, fma(a1, dy1, a0 * dy0)).  A waypoint on or  */
+/* inside a box (d = 0) ends its region.  The particle mask bit is the OR over  */
+/* waypoints 1..W and half-spaces.                                               */
+/* ========================================================================== */
+int orc_halfspaces(const float* y, const float* v, const float* boxes, int n_boxes, int hmax, float* a_out,
+                   float* b_out) {
+  unsigned char* alive = (unsigned char*)malloc((size_t)(n_boxes > 0 ? n_boxes : 1));
+  if (!alive) return -1;
+  for (int o = 0; o < n_boxes; ++o) alive[o] = 1;
+  int count = 0;
+  const float vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  while (count < hmax) {
+    int best = -1;
+    float bestd = INFINITY, d[3] = {0.f, 0.f, 0.f};
+    for (int o = 0; o < n_boxes; ++o) {
+      if (!alive[o]) continue;
+      const float* b = boxes + 6 * o;
+      float e[3];
+      for (int j = 0; j < 3; ++j) e[j] = fminf(fmaxf(y[j], b[j]), b[3 + j]) - y[j];
+      const float d2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+      if (d2 < bestd) {
+        best = o; bestd = d2;
+        d[0] = e[0]; d[1] = e[1]; d[2] = e[2];
+      }
+    }
+    if (best < 0 || !(bestd > 0.f)) break;
+    float a[3];
+    if (vv > 0.f) {
+      const float f = (d[0] * v[0] + d[1] * v[1] + d[2] * v[2]) / vv;
+      for (int j = 0; j < 3; ++j) a[j] = d[j] - f * v[j];
+    } else {
+      for (int j = 0; j < 3; ++j) a[j] = d[j];
+    }
+    for (int j = 0; j < 3; ++j) a_out[3 * count + j] = a[j];
+    b_out[count] = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+    ++count;
+    alive[best] = 0;
+    for (int o = 0; o < n_boxes; ++o) {
+      if (!alive[o]) continue;
+      const float* b = boxes + 6 * o;
+      float m = 0.f;
+      for (int j = 0; j < 3; ++j) m = m + fminf(d[j] * (b[j] - y[j]), d[j] * (b[3 + j] - y[j]));
+      if (m >= bestd) alive[o] = 0;
+    }
+  }
+  free(alive);
+  return count;
+}
+
+static int hs_fires(const float* a, float b, const float* dy) {
+  return fmaf(a[2], dy[2], fmaf(a[1], dy[1], a[0] * dy[0])) > b;
+}
+
+int orc_edge_masks_hs(int n_edges, int W, int N, const float* phi, const float* L, const float* nom,
+                      const float* nvel, const float* linf, const float* xi, const float* boxes, int n_boxes,
+                      int hmax, uint32_t* mask) {
+  int w = N / 32;
+  float* ha = (float*)malloc(sizeof(float) * 3 * (size_t)W * (size_t)(hmax > 0 ? hmax : 1));
+  float* hb = (float*)malloc(sizeof(float) * (size_t)W * (size_t)(hmax > 0 ? hmax : 1));
+  int* hc = (int*)malloc(sizeof(int) * (size_t)W);
+  if (!ha || !hb || !hc) { free(ha); free(hb); free(hc); return -1; }
+  for (int e = 0; e < n_edges; ++e) {
+    for (int k = 1; k <= W; ++k) {
+      const size_t q = (size_t)e * W + (k - 1);
+      hc[k - 1] = orc_halfspaces(nom + 3 * q, nvel + 3 * q, boxes, n_boxes, hmax, ha + 3 * (size_t)(k - 1) * hmax,
+                                 hb + (size_t)(k - 1) * hmax);
+      if (hc[k - 1] < 0) { free(ha); free(hb); free(hc); return -1; }
+    }
+    for (int qw = 0; qw < w; ++qw) mask[(size_t)e * w + qw] = 0u;
+    for (int i = 0; i < N; ++i) {
+      int fired = 0;
+      float d0[3], d1[3];
+      for (int j = 0; j < 3; ++j) {
+        const float* x = xi + (((size_t)i * (W + 1) + 0) * 3 + j) * 2;
+        dev_init(linf, x[0], x[1], &d0[j], &d1[j]);
+      }
+      for (int k = 1; k <= W; ++k) {
+        for (int j = 0; j < 3; ++j) {
+          const float* x = xi + (((size_t)i * (W + 1) + k) * 3 + j) * 2;
+          dev_step(phi + 4 * (size_t)e, L + 3 * (size_t)e, x[0], x[1], &d0[j], &d1[j]);
+        }
+        for (int h = 0; h < hc[k - 1]; ++h)
+          if (hs_fires(ha + 3 * ((size_t)(k - 1) * hmax + h), hb[(size_t)(k - 1) * hmax + h], d0)) ++fired;
+      }
+      if (fired > 0) mask[(size_t)e * w + i / 32] |= 1u << (i % 32);
+    }
+  }
+  free(ha); free(hb); free(hc);
+  return 0;
 }
 
 /* ========================================================================== */

@@ -13,6 +13,8 @@
 // grid is persistent over the edges.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
 #include <mutex>
 #include <vector>
 
@@ -24,6 +26,12 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kCandCap = 64;
 constexpr int kBoxStride = 8;  // floats per box in shared memory: lo xyz, hi xyz, 2 pad
+constexpr int kHsStage = 128;  // HSMC: half-spaces of one edge staged in shared memory per warp
+
+// Shared memory of the HSMC query pass before the normals: staged half-spaces and waypoint offsets.
+__host__ __device__ constexpr size_t edge_mask_hs_fixed_smem() {
+  return (sizeof(float4) * kWarps * kHsStage + sizeof(int32_t) * kWarps * (kMaxWaypoints + 1) + 15) & ~(size_t)15;
+}
 
 // Shared memory of the query pass before the normals: boxes, per-warp candidate lists and
 // per-warp waypoint box masks (16-byte aligned end).
@@ -258,6 +266,188 @@ __global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask
   }
 }
 
+// ---------------------------------------------------------------- Half-Space Monte Carlo
+//
+// Local convex region of waypoint y (nominal position) with nominal velocity v, in the arithmetic
+// the header states (float, each operation rounded as written, left to right).  Writes to `out`
+// (when given) the half-spaces (a, b) a particle of the edge can fire: a.dy <= (|a0| + |a1| +
+// |a2|) max |dy_j| <= (|a0| + |a1| + |a2|) M, so a half-space with (|a0| + |a1| + |a2|) M (1 +
+// 2^-10) < b can never fire (the margin covers the test's rounding) and is left out.  Returns
+// how many are kept.
+__device__ int hs_region(const float* y, const float* v, const float* boxes, int nb, float M, float4* out) {
+  uint32_t alive[kMaxBoxes / 32];
+  const int nwords = (nb + 31) / 32;
+  for (int q = 0; q < nwords; ++q) alive[q] = (q + 1) * 32 <= nb ? 0xffffffffu : ((1u << (nb - q * 32)) - 1u);
+  const float vv = __fadd_rn(__fadd_rn(__fmul_rn(v[0], v[0]), __fmul_rn(v[1], v[1])), __fmul_rn(v[2], v[2]));
+  int kept = 0;
+  for (int count = 0; count < kHsMax; ++count) {
+    int best = -1;
+    float bestd = __int_as_float(0x7f800000), d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    for (int q = 0; q < nwords; ++q) {
+      uint32_t bits = alive[q];
+      while (bits) {
+        const int o = q * 32 + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const float* b = boxes + 6 * o;
+        const float e0 = __fsub_rn(fminf(fmaxf(y[0], b[0]), b[3]), y[0]);
+        const float e1 = __fsub_rn(fminf(fmaxf(y[1], b[1]), b[4]), y[1]);
+        const float e2 = __fsub_rn(fminf(fmaxf(y[2], b[2]), b[5]), y[2]);
+        const float dd = __fadd_rn(__fadd_rn(__fmul_rn(e0, e0), __fmul_rn(e1, e1)), __fmul_rn(e2, e2));
+        if (dd < bestd) {
+          best = o;
+          bestd = dd;
+          d0 = e0;
+          d1 = e1;
+          d2 = e2;
+        }
+      }
+    }
+    if (best < 0 || !(bestd > 0.f)) break;
+    float a0 = d0, a1 = d1, a2 = d2;
+    if (vv > 0.f) {
+      const float dv = __fadd_rn(__fadd_rn(__fmul_rn(d0, v[0]), __fmul_rn(d1, v[1])), __fmul_rn(d2, v[2]));
+      const float f = __fdiv_rn(dv, vv);
+      a0 = __fsub_rn(d0, __fmul_rn(f, v[0]));
+      a1 = __fsub_rn(d1, __fmul_rn(f, v[1]));
+      a2 = __fsub_rn(d2, __fmul_rn(f, v[2]));
+    }
+    const float bb = __fadd_rn(__fadd_rn(__fmul_rn(a0, a0), __fmul_rn(a1, a1)), __fmul_rn(a2, a2));
+    if ((fabsf(a0) + fabsf(a1) + fabsf(a2)) * M * 1.0009765625f >= bb) {
+      if (out) out[kept] = make_float4(a0, a1, a2, bb);
+      ++kept;
+    }
+    alive[best >> 5] &= ~(1u << (best & 31));
+    for (int q = 0; q < nwords; ++q) {
+      uint32_t bits = alive[q];
+      while (bits) {
+        const int o = q * 32 + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const float* b = boxes + 6 * o;
+        float m = 0.f;
+        m = __fadd_rn(m, fminf(__fmul_rn(d0, __fsub_rn(b[0], y[0])), __fmul_rn(d0, __fsub_rn(b[3], y[0]))));
+        m = __fadd_rn(m, fminf(__fmul_rn(d1, __fsub_rn(b[1], y[1])), __fmul_rn(d1, __fsub_rn(b[4], y[1]))));
+        m = __fadd_rn(m, fminf(__fmul_rn(d2, __fsub_rn(b[2], y[2])), __fmul_rn(d2, __fsub_rn(b[5], y[2]))));
+        if (m >= bestd) alive[q] &= ~(1u << (o & 31));
+      }
+    }
+  }
+  return kept;
+}
+
+// Graph build (HSMC): per waypoint (thread), the number of kept half-spaces, then their values.
+template <bool kFill>
+__global__ void k_hs_build(const float* __restrict__ nom, const float* __restrict__ nvel,
+                           const unsigned int* __restrict__ dmax, const float* __restrict__ boxes_g, int nb, int E,
+                           int W, int32_t* __restrict__ cnt, const int32_t* __restrict__ off, float4* __restrict__ ab) {
+  extern __shared__ float hs_boxes[];
+  for (int k = threadIdx.x; k < 6 * nb; k += blockDim.x) hs_boxes[k] = boxes_g[k];
+  __syncthreads();
+  const long long EW = (long long)E * W;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < EW; q += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(q / W);
+    const float M = __uint_as_float(dmax[e]);
+    const float y[3] = {nom[3 * q], nom[3 * q + 1], nom[3 * q + 2]};
+    const float v[3] = {nvel[3 * q], nvel[3 * q + 1], nvel[3 * q + 2]};
+    if (kFill)
+      hs_region(y, v, hs_boxes, nb, M, ab + off[q]);
+    else
+      cnt[q] = hs_region(y, v, hs_boxes, nb, M, nullptr);
+  }
+}
+
+// Query pass (HSMC): a warp per edge, NW mask words per lane pass as in word_pass; at waypoint k
+// the particles test the edge's kept half-spaces hs[off_k .. off_{k+1}).
+template <int NW>
+__device__ __forceinline__ void word_pass_hs(const float2* __restrict__ xi, int N, const float (&P)[4],
+                                             const float (&L)[3], const float (&linf)[3], const int32_t* woff,
+                                             const float4* hs, int k_last, int w0, int lane, uint32_t* out) {
+  float d0[NW][3], d1[NW][3];
+  bool hit[NW];
+  const float2* xq = xi + w0 * 32 + lane;
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    hit[j] = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dev_init(linf, xq[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+  }
+  for (int k = 1; k <= k_last; ++k) {
+    const float2* xk = xq + (size_t)k * 3 * N;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dev_step(P, L, xk[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+    }
+    for (int h = woff[k - 1]; h < woff[k]; ++h) {
+      const float4 q = hs[h];
+#pragma unroll
+      for (int j = 0; j < NW; ++j)
+        hit[j] = hit[j] || fmaf(q.z, d0[j][2], fmaf(q.y, d0[j][1], __fmul_rn(q.x, d0[j][0]))) > q.w;
+    }
+    bool done = true;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) done = done && hit[j];
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    const unsigned bits = __ballot_sync(0xffffffffu, hit[j]);
+    if (lane == 0) out[w0 + j] = bits;
+  }
+}
+
+template <bool kSmemXi>
+__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask_hs(
+    const float2* __restrict__ xi_g, int N, int W, const float* __restrict__ phi, const float* __restrict__ Lg,
+    const float* __restrict__ linf_g, const int32_t* __restrict__ hs_off, const float4* __restrict__ hs_ab, int E,
+    int w, uint32_t* __restrict__ mask) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* stage_all = reinterpret_cast<float4*>(smem);
+  int32_t* woff_all = reinterpret_cast<int32_t*>(stage_all + kWarps * kHsStage);
+  float2* xi_s = reinterpret_cast<float2*>(smem + edge_mask_hs_fixed_smem());
+  const int xi_n = (W + 1) * 3 * N;
+  if (kSmemXi)
+    for (int k = threadIdx.x; k < xi_n; k += blockDim.x) xi_s[k] = xi_g[k];
+  __syncthreads();
+  const float2* xi = kSmemXi ? xi_s : xi_g;
+  const float linf[3] = {linf_g[0], linf_g[1], linf_g[2]};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4* stage = stage_all + warp * kHsStage;
+  int32_t* woff = woff_all + warp * (kMaxWaypoints + 1);
+  for (long long e = (long long)blockIdx.x * kWarps + warp; e < E; e += (long long)gridDim.x * kWarps) {
+    const int32_t* off = hs_off + (size_t)e * W;
+    const int32_t o0 = off[0], o1 = off[W];
+    uint32_t* out = mask + (size_t)e * w;
+    if (o0 == o1) {
+      for (int word = lane; word < w; word += 32) out[word] = 0u;
+      continue;
+    }
+    // waypoint offsets relative to the edge's first half-space, and the last waypoint with one
+    int k_last = 0;
+    for (int k = lane; k <= W; k += 32) {
+      woff[k] = off[k] - o0;
+      if (k > 0 && off[k] > off[k - 1]) k_last = max(k_last, k);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) k_last = max(k_last, __shfl_xor_sync(0xffffffffu, k_last, o));
+    const int nh = o1 - o0;
+    const bool staged = nh <= kHsStage;
+    if (staged)
+      for (int h = lane; h < nh; h += 32) stage[h] = hs_ab[o0 + h];
+    __syncwarp();
+    const float4* hs = staged ? stage : hs_ab + o0;
+    const float P[4] = {phi[4 * e], phi[4 * e + 1], phi[4 * e + 2], phi[4 * e + 3]};
+    const float L[3] = {Lg[3 * e], Lg[3 * e + 1], Lg[3 * e + 2]};
+    int w0 = 0;
+    for (; w0 + 4 <= w; w0 += 4) word_pass_hs<4>(xi, N, P, L, linf, woff, hs, k_last, w0, lane, out);
+    if (w0 + 2 <= w) {
+      word_pass_hs<2>(xi, N, P, L, linf, woff, hs, k_last, w0, lane, out);
+      w0 += 2;
+    }
+    if (w0 < w) word_pass_hs<1>(xi, N, P, L, linf, woff, hs, k_last, w0, lane, out);
+    __syncwarp();
+  }
+}
+
 }  // namespace
 
 size_t edge_mask_smem(int N, int W, int nb, bool xi_in_smem) {
@@ -338,11 +528,68 @@ int compute_edge_bounds(pump_graph* g, cudaStream_t s) {
   return PUMP_OK;
 }
 
+int scan_counts(const int32_t* in, int n, int32_t* out, cudaStream_t s);
+
+// HSMC half-spaces of every waypoint (graph build, after the deviation bounds).
+int build_halfspaces(pump_graph* g, cudaStream_t s) {
+  const long long EW = (long long)g->E * g->W;
+  if (EW > (long long)INT32_MAX - 1) return PUMP_ERR_INVALID_ARG;
+  g->hs_off = (int32_t*)graph_alloc(g, sizeof(int32_t) * (size_t)(EW + 1), s);
+  int32_t* cnt = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)(EW + 1), s);
+  if (!g->hs_off || !cnt) return PUMP_ERR_OOM;
+  const size_t smem = sizeof(float) * 6 * (size_t)std::max(g->n_boxes, 1);
+  const int grid = (int)std::min<long long>((EW + 255) / 256, (long long)num_sms() * 8);
+  if (EW > 0) {
+    k_hs_build<false><<<grid, 256, smem, s>>>(g->nom, g->nvel, g->dmax, g->boxes, g->n_boxes, g->E, g->W, cnt,
+                                              nullptr, nullptr);
+    note_launch();
+  }
+  int rc = scan_counts(cnt, (int)EW, g->hs_off, s);
+  int32_t total = 0;
+  if (!rc && cudaMemcpyAsync(&total, g->hs_off + EW, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    rc = PUMP_ERR_CUDA;
+  if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = PUMP_ERR_CUDA;
+  dev_free(cnt, s);
+  if (rc) return rc;
+  g->hs_ab = (float4*)graph_alloc(g, sizeof(float4) * (size_t)std::max(total, 1), s);
+  if (!g->hs_ab) return PUMP_ERR_OOM;
+  if (EW > 0 && total > 0) {
+    k_hs_build<true><<<grid, 256, smem, s>>>(g->nom, g->nvel, g->dmax, g->boxes, g->n_boxes, g->E, g->W, nullptr,
+                                             g->hs_off, g->hs_ab);
+    note_launch();
+  }
+  PUMP_CUDA_TRY(cudaGetLastError());
+  return PUMP_OK;
+}
+
+static int compute_edge_masks_hs(pump_graph* g, cudaStream_t s) {
+  const size_t smem_xi = edge_mask_hs_fixed_smem() + sizeof(float2) * (size_t)(g->W + 1) * 3 * g->N;
+  const bool use_smem = smem_xi <= 160 * 1024;
+  const size_t smem = use_smem ? smem_xi : edge_mask_hs_fixed_smem();
+  int grid = 1;
+  if (use_smem) {
+    const int rco = occupancy_grid(k_edge_mask_hs<true>, smem, kWarps, g->E, &grid);
+    if (rco) return rco;
+    k_edge_mask_hs<true><<<grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->linf_dev, g->hs_off,
+                                                         g->hs_ab, g->E, g->n_words, g->emask);
+  } else {
+    const int rco = occupancy_grid(k_edge_mask_hs<false>, smem, kWarps, g->E, &grid);
+    if (rco) return rco;
+    k_edge_mask_hs<false><<<grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->linf_dev, g->hs_off,
+                                                          g->hs_ab, g->E, g->n_words, g->emask);
+  }
+  note_launch();
+  PUMP_CUDA_TRY(cudaGetLastError());
+  g->masks_ready = true;
+  return PUMP_OK;
+}
+
 int compute_edge_masks(pump_graph* g, cudaStream_t s) {
   if (g->E == 0) {
     g->masks_ready = true;
     return PUMP_OK;
   }
+  if (g->hsmc) return compute_edge_masks_hs(g, s);
   const size_t smem_xi = edge_mask_smem(g->N, g->W, g->n_boxes, true);
   const bool use_smem = smem_xi <= 160 * 1024;
   const size_t smem = use_smem ? smem_xi : edge_mask_smem(g->N, g->W, g->n_boxes, false);

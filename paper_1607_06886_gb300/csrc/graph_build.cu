@@ -387,7 +387,7 @@ __global__ void k_scatter_edges(const int2* __restrict__ list, long long n_list,
 __global__ void k_fill_edges(const float* __restrict__ states, int E, int W, float sigma,
                              const int32_t* __restrict__ src, const int32_t* __restrict__ col,
                              const double* __restrict__ etau, float* tau_o, float* h_o, float* phi_o, float* L_o,
-                             float* nom_o) {
+                             float* nom_o, float* nvel_o) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int v = src[e], u = col[e];
@@ -410,8 +410,11 @@ __global__ void k_fill_edges(const float* __restrict__ states, int E, int W, flo
   const double td = (double)t32;
   for (int j = 0; j < 3; ++j) {
     const Cubic c = cubic_dev(xv, xu, td, j);
-    for (int kk = 1; kk <= W; ++kk)
-      nom_o[((size_t)e * W + (kk - 1)) * 3 + j] = __double2float_rn(cubic_at(c, (double)kk * (double)h));
+    for (int kk = 1; kk <= W; ++kk) {
+      const double tk = (double)kk * (double)h;
+      nom_o[((size_t)e * W + (kk - 1)) * 3 + j] = __double2float_rn(cubic_at(c, tk));
+      nvel_o[((size_t)e * W + (kk - 1)) * 3 + j] = __double2float_rn(c.v0 + 2.0 * c.c2 * tk + 3.0 * c.c3 * tk * tk);
+    }
   }
 }
 
@@ -502,7 +505,8 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   g->nom = (float*)graph_alloc(g, sizeof(float) * 3 * (size_t)g->W * Es, s);
   g->emask = (uint32_t*)graph_alloc(g, sizeof(uint32_t) * (size_t)g->n_words * Es, s);
   g->ibox = (float*)graph_alloc(g, sizeof(float) * 6 * Es, s);
-  if (!g->col || !g->ecost || !g->tau || !g->h || !g->phi || !g->L || !g->nom || !g->emask || !g->ibox)
+  g->nvel = (float*)graph_alloc(g, sizeof(float) * 3 * (size_t)g->W * Es, s);
+  if (!g->col || !g->ecost || !g->tau || !g->h || !g->phi || !g->L || !g->nom || !g->emask || !g->ibox || !g->nvel)
     return PUMP_ERR_OOM;
   if (E > 0) {
     int32_t* src = (int32_t*)dev_alloc(sizeof(int32_t) * Es, s);
@@ -514,7 +518,7 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
                                              etau, g->ecost);
     note_launch();
     k_fill_edges<<<(E + 127) / 128, 128, 0, s>>>(g->states, E, g->W, g->sigma, src, g->col, etau, g->tau, g->h,
-                                                 g->phi, g->L, g->nom);
+                                                 g->phi, g->L, g->nom, g->nvel);
     note_launch();
     dev_free(src, s);
     dev_free(etau, s);
@@ -522,6 +526,10 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   {
     const int rcb = compute_edge_bounds(g, s);
     if (rcb) return rcb;
+  }
+  if (g->hsmc) {
+    const int rch = build_halfspaces(g, s);
+    if (rch) return rch;
   }
   // valid node count (for export)
   PUMP_CUDA_TRY(cudaMemsetAsync(deg, 0, sizeof(int32_t), s));
@@ -537,6 +545,14 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   dev_free(wpre, s);
   dev_free(res_tau, s);
   dev_free(res_cost, s);
+  return PUMP_OK;
+}
+
+// Exclusive scan of n counts into out[0..n] (out[n] = total).
+int scan_counts(const int32_t* in, int n, int32_t* out, cudaStream_t s) {
+  k_scan_single<<<1, 1024, 0, s>>>(in, n, out);
+  note_launch();
+  PUMP_CUDA_TRY(cudaGetLastError());
   return PUMP_OK;
 }
 

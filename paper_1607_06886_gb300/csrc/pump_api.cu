@@ -334,6 +334,7 @@ int pump_graph_build(const float* states, int32_t n, int32_t start_idx, const in
   g->radius = prm->radius;
   g->sigma = prm->sigma;
   g->has_geometry = true;
+  g->hsmc = (prm->flags & PUMP_GRAPH_HSMC) != 0;
   g->states = (float*)graph_alloc(g, sizeof(float) * 6 * (size_t)n, s);
   g->boxes = (float*)graph_alloc(g, sizeof(float) * 6 * (size_t)std::max(n_boxes, 1), s);
   g->valid = (uint8_t*)graph_alloc(g, (size_t)n, s);
@@ -544,6 +545,7 @@ int pump_export(pump_graph* g, int32_t what, void* host_buf, size_t cap, size_t*
     case PUMP_EXPORT_PLAN_EXPANDED: if (!ex) return PUMP_ERR_INVALID_ARG; src = g->ex.eexp; bytes = 4 * P; break;
     case PUMP_EXPORT_GOAL_PLANS: if (!ex) return PUMP_ERR_INVALID_ARG; src = g->ex.goal_sorted; bytes = 4 * (size_t)g->last_goal; break;
     case PUMP_EXPORT_EDGE_BOX: if (!geo) return PUMP_ERR_INVALID_ARG; src = g->ibox; bytes = 24 * E; break;
+    case PUMP_EXPORT_NOMINAL_VEL: if (!geo) return PUMP_ERR_INVALID_ARG; src = g->nvel; bytes = 12 * (size_t)g->W * E; break;
     default: return PUMP_ERR_INVALID_ARG;
   }
   *needed = bytes;

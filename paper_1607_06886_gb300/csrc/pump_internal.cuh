@@ -167,6 +167,10 @@ struct pump_graph {
   float* ibox = nullptr;     // E x 6: box holding every particle position of the edge
   int4* etgt = nullptr;      // E: target node, cost bits, target row start, degree | goal bit
   unsigned int* dmax = nullptr;  // E: largest |d0| of the edge's particles (float bits)
+  float* nvel = nullptr;     // E x W x 3: nominal velocity at the waypoints
+  bool hsmc = false;         // masks by Half-Space Monte Carlo
+  int32_t* hs_off = nullptr; // E*W + 1: first half-space of waypoint (e, k) (HSMC)
+  float4* hs_ab = nullptr;   // half-spaces (a xyz, b) that a particle of the edge can fire (HSMC)
   std::vector<pump::DevBuf> bufs;
   pump::ExploreBufs ex;
   // last explore
@@ -189,6 +193,8 @@ void* graph_realloc(pump_graph* g, void* old, size_t bytes, cudaStream_t s);
   } while (0)
 
 int build_graph_device(pump_graph* g, cudaStream_t s);
+int build_halfspaces(pump_graph* g, cudaStream_t s);
+constexpr int kHsMax = 8;  // half-spaces per waypoint (HSMC)
 int compute_edge_masks(pump_graph* g, cudaStream_t s);
 int compute_edge_bounds(pump_graph* g, cudaStream_t s);
 int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* stats,

@@ -19,11 +19,12 @@ from . import build as _build
 # status codes
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_INFEASIBLE = range(7)
 NO_EARLY_STOP, EXPLORE_ONLY, STEPWISE, EXPLORE_GRID = 1, 2, 4, 8
+GRAPH_HSMC = 1
 
 EXPORT = {
     "counts": 0, "node_valid": 1, "row_ptr": 2, "col": 3, "ecost": 4, "tau": 5, "h": 6, "phi": 7, "L": 8,
     "nominal": 9, "linf": 10, "masks": 11, "plan_head": 12, "plan_parent": 13, "plan_cost": 14, "plan_mask": 15,
-    "plan_popc": 16, "plan_created": 17, "plan_expanded": 18, "goal_plans": 19, "edge_box": 20,
+    "plan_popc": 16, "plan_created": 17, "plan_expanded": 18, "goal_plans": 19, "edge_box": 20, "nominal_vel": 21,
 }
 
 
@@ -284,7 +285,8 @@ class Graph:
 
     @classmethod
     def build(cls, states, goal_idx, boxes, xi, radius: float, n_particles: int, n_waypoints: int,
-              sigma: float, start_idx: int = 0, stream: Optional[int] = None) -> "Graph":
+              sigma: float, start_idx: int = 0, stream: Optional[int] = None, flags: int = 0) -> "Graph":
+        """pump_graph_build; flags = GRAPH_HSMC for Half-Space Monte Carlo masks."""
         L = load()
         st = _np(states, np.float32)
         gi = _np(goal_idx, np.int32)
@@ -292,7 +294,7 @@ class Graph:
         x = _np(xi, np.float32)
         n = int(st.shape[0])
         nb = int(bx.shape[0]) if bx is not None else 0
-        prm = GraphParams(float(radius), int(n_particles), int(n_waypoints), float(sigma), 0)
+        prm = GraphParams(float(radius), int(n_particles), int(n_waypoints), float(sigma), int(flags))
         out = C.c_void_p()
         s = current_stream() if stream is None else stream
         rc = L.pump_graph_build(_ptr(st), n, int(start_idx), _ptr(gi), int(len(gi)), _ptr(bx) if nb else None, nb,
@@ -382,7 +384,7 @@ class Graph:
                   "plan_parent": (np.int32, (P,)), "plan_cost": (np.float32, (P,)), "plan_mask": (np.uint32, (P, w)),
                   "plan_popc": (np.int32, (P,)), "plan_created": (np.int32, (P,)),
                   "plan_expanded": (np.int32, (P,)), "goal_plans": (np.int32, (G,)),
-                  "edge_box": (np.float32, (E, 6))}
+                  "edge_box": (np.float32, (E, 6)), "nominal_vel": (np.float32, (E, W, 3))}
         dt, shp = shapes[what]
         return raw.view(dt).reshape(shp).copy()
 
