@@ -74,6 +74,7 @@ def lib():
             L.orc_pair_costs.argtypes = [P, C.c_int, P]
             L.orc_philox4x64.argtypes = [P, P, P]
             L.orc_mc_normals.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, P]
+            L.orc_mlp_draws.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int32, P, P]
             L.orc_mc_certify.argtypes = [P, P, C.c_int, P, C.c_int, C.c_float, P, C.c_int, C.c_int64,
                                          C.c_int, C.c_uint64]
             L.orc_mc_certify.restype = C.c_int64
@@ -241,6 +242,15 @@ def mc_normals(seed: int, m: int, s: int) -> np.ndarray:
     o = np.zeros(6, np.float32)
     lib().orc_mc_normals(C.c_uint64(seed), C.c_uint64(m), C.c_uint64(s), _p(o))
     return o.reshape(3, 2)
+
+
+def mlp_draws(seed: int, t: int, stream: int, rows: int, n_env: int = 0):
+    """Latents (rows x 8 float32) and, with n_env > 0, environment indices of draw set (t, stream)."""
+    z = np.zeros((rows, 8), np.float32)
+    env = np.zeros(rows, np.int32)
+    lib().orc_mlp_draws(C.c_uint64(seed), C.c_uint64(t), C.c_uint64(stream), C.c_int64(rows), C.c_int32(n_env),
+                        _p(z), _p(env))
+    return z, (env if n_env > 0 else None)
 
 
 def backtrack(parent, head, p: int) -> np.ndarray:

@@ -20,6 +20,8 @@
  *   O5 Explore                             Algorithm 4 and RemoveDominated, Section IV
  *   O6 PlanSelection and MC(p)             Algorithm 5, Section III-A
  *   Philox4x64-10 counter-based generator  Salmon et al., SC'11
+ *   O7 draws of the learned sampling proposal (latents, batch rows); the
+ *      proposal network itself is restated in oracle/mlp.py
  *
  * Readings of points the paper leaves open (cost weights, controller gains,
  * tie rules, thresholds) are stated beside the code that takes them.
@@ -981,6 +983,30 @@ void orc_pair_costs(const float* states, int n, float* out) {
       double xu[6], t, J;
       for (int q = 0; q < 6; ++q) xu[q] = (double)states[6 * u + q];
       out[(size_t)v * n + u] = (u != v && orc_steer(xv, xu, &t, &J) == 0) ? (float)J : INFINITY;
+    }
+  }
+}
+
+/* ========================================================================== */
+/* O7  Draws of the learned sampling proposal (not part of the paper, which   */
+/* has no learning).  Row r of draw set (t, stream) takes one Philox4x64-10    */
+/* call with counter (t, r, stream, 0) and key (seed, 1); its four words give   */
+/* eight standard normals through box_muller (word j: bits 63..40 -> u1, bits   */
+/* 39..16 -> u2; z[2j], z[2j+1]).  With n_env > 0 the call with counter         */
+/* (t, r, stream + 1, 0) picks the row's environment from its word 0:           */
+/* env = floor((word0 >> 32) * n_env / 2^32).                                   */
+/* ========================================================================== */
+void orc_mlp_draws(uint64_t seed, uint64_t t, uint64_t stream, int64_t rows, int32_t n_env, float* z,
+                   int32_t* env) {
+  const uint64_t key[2] = {seed, 1};
+  for (int64_t r = 0; r < rows; ++r) {
+    uint64_t c[4] = {t, (uint64_t)r, stream, 0}, o[4];
+    orc_philox4x64(c, key, o);
+    for (int j = 0; j < 4; ++j) box_muller(o[j] >> 40, (o[j] >> 16) & 0xFFFFFFull, &z[8 * r + 2 * j], &z[8 * r + 2 * j + 1]);
+    if (n_env > 0 && env) {
+      uint64_t c2[4] = {t, (uint64_t)r, stream + 1, 0};
+      orc_philox4x64(c2, key, o);
+      env[r] = (int32_t)(((o[0] >> 32) * (uint64_t)n_env) >> 32);
     }
   }
 }
