@@ -375,6 +375,101 @@ int pump_explore_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col, 
                          int32_t* plan_created, int32_t* plan_expanded, int32_t* goal_plans,
                          pump_plan_result* stats, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Learned sampling proposal.  Not in the paper, which draws SampleFree      */
+/* uniformly (Algorithm 3); an extension that learns where solution paths    */
+/* run and proposes part of the samples there.                               */
+/*                                                                          */
+/* Network: dims[0] -> ... -> dims[L] (every width a multiple of 16, at most  */
+/* 4096), ReLU after every layer but the last.  Products take BF16 operands  */
+/* (inputs, weights, hidden activations rounded to nearest even) on the      */
+/* tensor cores with FP32 sums; weights, biases and Adam's moments are FP32. */
+/* An input row is [features (F floats), eight standard normals, zeros].     */
+/* The first six outputs o are squashed into the state box: position         */
+/* 0.5 + 0.5 tanh(o_j), velocity vmax tanh(o_j).  Loss (pump_mlp_set_loss):  */
+/* winner takes all over the row's targets, or path-indexed; batch mean.     */
+/* Optimiser: Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).       */
+/* Parameter vector layout (FP32): per layer W (out x in, row-major) then b. */
+/*                                                                          */
+/* Draws: row r of draw set (t, stream) takes its normals from Philox4x64-10 */
+/* (Salmon et al., SC'11) with counter (t, r, stream, 0) and key (seed, 1):  */
+/* word j gives normals 2j, 2j+1 by Box-Muller on bits 63..40 and 39..16.    */
+/* A training row's environment comes from counter (t, r, stream + 1, 0):    */
+/* floor((word0 >> 32) n_env / 2^32).  Training step t (t = steps taken so   */
+/* far) uses stream 0; proposals use t = 0, stream 2.                        */
+/*                                                                          */
+/* Every call below runs on the model's own stream, ordered after `stream`   */
+/* (NULL: the legacy default stream), and returns when its work is done.     */
+/* Pointer arguments may be host or device memory unless stated.  A model    */
+/* is not thread-safe.  Errors: INVALID_ARG for bad sizes or NULL pointers,  */
+/* OOM, CUDA.                                                               */
+/* ------------------------------------------------------------------------ */
+typedef struct pump_mlp pump_mlp;
+
+/* pump_mlp_create: a model with n_layers layers of widths dims[0..n_layers],
+ * He-uniform weights drawn from `seed`, zero biases, Adam state cleared. */
+int pump_mlp_create(int32_t n_layers, const int32_t* dims, uint64_t seed, pump_mlp** out);
+
+/* pump_mlp_param_count: length of the parameter vector (-1 for NULL). */
+int64_t pump_mlp_param_count(const pump_mlp* m);
+
+/* pump_mlp_set_params / pump_mlp_get_params: copy the FP32 parameter vector
+ * in or out (count must equal pump_mlp_param_count).  Setting clears Adam's
+ * moments and step count; getting also returns the step count (may be NULL). */
+int pump_mlp_set_params(pump_mlp* m, const float* params, int64_t count);
+int pump_mlp_get_params(pump_mlp* m, float* params, int64_t count, int64_t* steps);
+
+/* pump_mlp_forward: outputs y (B x dims[L], FP32) of inputs x (B x dims[0],
+ * FP32, rounded to BF16 on entry). */
+int pump_mlp_forward(pump_mlp* m, const float* x, int32_t B, float* y, void* stream);
+
+/* pump_mlp_gradients: gradient of sum(dy * y) with respect to every
+ * parameter (vector layout; dy B x dims[L] FP32, rounded to BF16 like the
+ * loss gradient) at inputs x.  Leaves the parameters unchanged. */
+int pump_mlp_gradients(pump_mlp* m, const float* x, int32_t B, const float* dy, float* grads, int64_t count,
+                       void* stream);
+
+/* pump_mlp_train_step: one Adam step on explicit rows: inputs x (B x dims[0])
+ * and per-row targets (B x T x 6, row r using its first n_targets[r]; a row
+ * with none adds nothing).  Writes the batch's mean loss before the step. */
+int pump_mlp_train_step(pump_mlp* m, const float* x, int32_t B, const float* targets, const int32_t* n_targets,
+                        int32_t T, float lr, float vmax, float* mean_loss, void* stream);
+
+/* pump_mlp_set_loss: the training loss.  kind 0 (default): winner takes all,
+ * min over the row's targets of |s - y_p|^2.  kind 1: path-indexed, the
+ * targets read as a polyline in path order and the target taken at fraction
+ * u = Phi(x[latent_col]) of it by node index (Phi the standard normal CDF, x
+ * the row's BF16 input): a = u (n - 1), i = min(floor(a), n - 2),
+ * y = y_i + (a - i)(y_{i+1} - y_i), or y_0 when n = 1.  Errors: INVALID_ARG
+ * for another kind or a column outside [0, dims[0]). */
+int pump_mlp_set_loss(pump_mlp* m, int32_t kind, int32_t latent_col);
+
+/* pump_mlp_set_data: copy a training set into the model: per environment e,
+ * features feat[e] (F floats, F + 8 <= dims[0]) and targets (n_env x T x 6)
+ * of which the first n_targets[e] are used. */
+int pump_mlp_set_data(pump_mlp* m, const float* feat, int32_t F, int32_t n_env, const float* targets,
+                      const int32_t* n_targets, int32_t T);
+
+/* pump_mlp_train: `steps` Adam steps of B rows each on the stored training
+ * set, every row drawing its environment and normals (draw set (t, 0)).  One
+ * step is captured as a CUDA graph on first use and replayed.  Writes the
+ * mean loss of each step to loss_trace[0 .. steps) (may be NULL). */
+int pump_mlp_train(pump_mlp* m, int32_t B, int32_t steps, float lr, float vmax, uint64_t seed, float* loss_trace,
+                   void* stream);
+
+/* pump_mlp_assemble: the inputs x (B x dims[0], FP32 values of the BF16
+ * rows) and environments env (B, may be NULL) that training step t with
+ * `seed` would use on the stored training set; no training happens. */
+int pump_mlp_assemble(pump_mlp* m, int32_t B, int64_t t, uint64_t seed, float* x, int32_t* env);
+
+/* pump_mlp_propose: `count` proposal states (count x 6) for one environment
+ * with features feat (F floats), latent draws (0, r, 2) for rows r. */
+int pump_mlp_propose(pump_mlp* m, const float* feat, int32_t F, int32_t count, uint64_t seed, float vmax,
+                     float* states, void* stream);
+
+/* pump_mlp_destroy: release a model (NULL is a no-op). */
+void pump_mlp_destroy(pump_mlp* m);
+
 /* pump_kernel_launches: number of kernels this library has launched in the
  * process so far (host-side counter, all devices; for launch accounting).
  * No counterpart in the paper. */

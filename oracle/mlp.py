@@ -15,8 +15,12 @@ Definitions (the method's, stated here once):
              bf16(W_l); sums are FP32 on the device, exact here.
   Squash     s_j = 0.5 + 0.5 tanh(o_j) for j < 3 (position in the unit cube),
              s_j = vmax tanh(o_j) for 3 <= j < 6 (velocity); outputs past 6 are unused.
-  Loss       winner takes all over a row's targets y_p (the states along a solution path):
-             loss_r = min_p |s - y_p|^2 (first minimiser on ties); the batch loss is the mean.
+  Loss       kind 0, winner takes all over a row's targets y_0 .. y_{n-1} (the states along a
+             solution path, in path order): loss_r = min_p |s - y_p|^2 (first minimiser on
+             ties).  Kind 1, path-indexed: u = Phi(z_0) (standard normal CDF of the row's first
+             latent as the network sees it, i.e. after BF16 rounding), a = u (n - 1),
+             i = min(floor(a), n - 2), f = a - i, target y(u) = y_i + f (y_{i+1} - y_i)
+             (y_0 when n = 1); loss_r = |s - y(u)|^2.  The batch loss is the mean.
   Backward   g = bf16(d mean loss / d o); dW_l = g_l^T h_l, db_l = sum over rows of g_l,
              g_{l-1} = bf16((g_l bf16(W_l)) * [h_l > 0]).
   Adam       Kingma and Ba (2015) with bias correction: beta1 0.9, beta2 0.999, eps 1e-8.
@@ -27,6 +31,7 @@ Definitions (the method's, stated here once):
 """
 from __future__ import annotations
 
+import math
 from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
@@ -102,26 +107,47 @@ def squash(o, vmax: float) -> np.ndarray:
     return s
 
 
-def wta_loss(o, targets, n_targets, vmax: float) -> Tuple[np.ndarray, np.ndarray]:
-    """Per-row loss min_p |s - y_p|^2 and d(mean loss)/d o (B x o.shape[1], zero past column 6).
+def path_point(tg, n: int, u: float) -> np.ndarray:
+    """The state at fraction u of the polyline y_0 .. y_{n-1} by node index (kind-1 target)."""
+    tg = np.asarray(tg, np.float64)
+    if n == 1:
+        return tg[0].copy()
+    a = u * (n - 1)
+    i = min(int(math.floor(a)), n - 2)
+    f = a - i
+    return tg[i] + f * (tg[i + 1] - tg[i])
+
+
+def normal_cdf(z) -> np.ndarray:
+    return 0.5 * np.vectorize(math.erfc)(-np.asarray(z, np.float64) / math.sqrt(2.0))
+
+
+def wta_loss(o, targets, n_targets, vmax: float, kind: int = 0, z0=None) -> Tuple[np.ndarray, np.ndarray]:
+    """Per-row loss and d(mean loss)/d o (B x o.shape[1], zero past column 6).
 
     targets: (B, T, 6); row r uses its first n_targets[r] targets; a row without targets has
-    loss 0 and no gradient."""
+    loss 0 and no gradient.  kind 0: min_p |s - y_p|^2; kind 1: |s - y(Phi(z0[r]))|^2."""
     o = np.asarray(o, np.float64)
     B = o.shape[0]
     s = squash(o, vmax)
     loss = np.zeros(B)
     g = np.zeros_like(o)
+    u = normal_cdf(z0) if kind == 1 else None
     for r in range(B):
         k = int(n_targets[r])
         if k <= 0:
             continue
-        d = ((s[r][None, :] - np.asarray(targets[r][:k], np.float64)) ** 2).sum(axis=1)
-        p = int(np.argmin(d))  # first minimiser
-        loss[r] = d[p]
+        if kind == 0:
+            d = ((s[r][None, :] - np.asarray(targets[r][:k], np.float64)) ** 2).sum(axis=1)
+            p = int(np.argmin(d))  # first minimiser
+            y = np.asarray(targets[r][p], np.float64)
+            loss[r] = d[p]
+        else:
+            y = path_point(targets[r], k, float(u[r]))
+            loss[r] = ((s[r] - y) ** 2).sum()
         th = np.tanh(o[r, :OUT_USED])
         ds = np.where(np.arange(OUT_USED) < 3, 0.5, vmax) * (1.0 - th * th)
-        g[r, :OUT_USED] = 2.0 * (s[r] - targets[r][p]) * ds / B
+        g[r, :OUT_USED] = 2.0 * (s[r] - y) * ds / B
     return loss, g
 
 
@@ -190,14 +216,15 @@ def propose(flat, dims, env_feat_row, count: int, seed: int, vmax: float) -> np.
 
 
 def train_step(state: Dict, dims, env_feat, targets, n_targets, batch: int, seed: int, lr: float,
-               vmax: float) -> float:
+               vmax: float, kind: int = 0) -> float:
     """One training step in place on state = {w, m, v, t}: draws of step t (the count of steps
     taken before), forward, loss, backward, Adam.  Returns the mean loss."""
     t = int(state["t"])
     z, env = train_draws(seed, t, batch, len(env_feat))
     x = assemble(env_feat, env, z, dims[0])
     o, hs = forward(state["w"], dims, x)
-    loss, g = wta_loss(o, np.asarray(targets)[env], np.asarray(n_targets)[env], vmax)
+    F = np.asarray(env_feat).shape[1]
+    loss, g = wta_loss(o, np.asarray(targets)[env], np.asarray(n_targets)[env], vmax, kind, hs[0][:, F])
     grad = backward(state["w"], dims, hs, g)
     state["w"], state["m"], state["v"] = adam(state["w"], grad, state["m"], state["v"], t + 1, lr)
     state["t"] = t + 1

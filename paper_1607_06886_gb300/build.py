@@ -30,6 +30,7 @@ UNITS = {
     "server.cu": [],
     "select.cu": [],
     "noalloc.cu": [],
+    "mlp.cu": [],
 }
 
 

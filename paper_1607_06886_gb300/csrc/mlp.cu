@@ -1,0 +1,977 @@
+// Learned sampling proposal (an extension of the method; the paper has no learning): a small MLP
+// whose products run on the tensor cores in BF16 with FP32 accumulation, FP32 master weights and
+// Adam state, and a training loop that stays on the device.
+//
+// Network.  dims[0] -> dims[1] -> ... -> dims[L]; ReLU after every layer but the last.  Inputs:
+// the environment's features (obstacle boxes, start, goal), eight standard normals z, zeros.  The
+// first six outputs o are squashed into the state box: position 0.5 + 0.5 tanh(o), velocity
+// vmax tanh(o).  Loss over the row's targets y_0 .. y_{n-1} (the states along a solution path, in
+// path order), averaged over the batch: winner takes all, min_p |s - y_p|^2, or path-indexed,
+// |s - y(u)|^2 with u = Phi(z_0) and y(u) the point at fraction u of the polyline by node index.
+//
+// Parameters live in one flat FP32 vector (per layer W (out x in, row-major) then b), with Adam's
+// moments and a BF16 copy beside it, so one launch updates every layer.
+//
+// GEMM.  C[M x N] = A[M x K] B[K x N] with BF16 operands given either K-major (a row of the
+// operand holds consecutive k) or M/N-major (consecutive m or n):
+//   forward   pre_l  = h_l W_l^T     A = h_l (K-major), B = W_l (K-major)
+//   backward  dh_l   = g_l W_l       A = g_l (K-major), B = W_l (N-major)
+//             dW_l   = g_l^T h_l     A = g_l (M-major), B = h_l (N-major), split over K (the batch)
+// so no operand is ever transposed in memory.  A 64 x 64 block tile, four warps of 32 x 32, K
+// steps of 32 staged by cp.async in two buffers; fragments come from ldmatrix (.trans for the
+// M/N-major tiles) and feed mma.sync m16n8k16 (BF16 in, FP32 accumulate).  Tile rows are padded
+// (K-major 40 elements, M/N-major 72) so that every ldmatrix phase hits 32 distinct banks.  The
+// epilogue is fused: bias + ReLU to BF16, bias to FP32, ReLU-mask of the layer below to BF16, or
+// plain FP32 partial sums (split K).  The weight-gradient partials of the S splits stay separate
+// and the Adam launch adds them in a fixed order, so a training step is deterministic.
+//
+// Device-side step counter.  ctl[0] counts the Adam steps taken; the batch assembly of step t
+// draws with t, the loss kernel advances the counter, and Adam corrects its moments with the new
+// count.  Nothing in a step depends on a host value that changes between steps, so one step is
+// captured once as a CUDA graph and replayed.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pump_internal.cuh"
+
+namespace pump {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kBM = 64, kBN = 64, kBK = 32;
+constexpr int kKPad = kBK + 8;  // row length of a K-major tile (elements)
+constexpr int kMPad = kBM + 8;  // row length of an M- or N-major tile (elements)
+constexpr int kTileElems = kBM * kKPad;  // >= kBK * kMPad
+constexpr int kGemmThreads = 128;
+constexpr int kLatent = 8;
+constexpr int kOutUsed = 6;
+constexpr int kMaxSplit = 8;
+constexpr int kLossThreads = 1024;
+
+static_assert(kBK * kMPad <= kTileElems, "tile buffer too small");
+
+enum Epi : int {
+  kEpiBiasRelu = 0,  // out_bf16 = bf16(relu(acc + bias))
+  kEpiBias = 1,      // out_f32 = acc + bias
+  kEpiMask = 2,      // out_bf16 = bf16(acc * (mask > 0))
+  kEpiPartial = 3,   // out_f32[split] = acc
+};
+
+struct GemmArgs {
+  const bf16* A;  // K-major: M x K (lda = row stride); M-major: K x M (lda = row stride)
+  const bf16* B;  // K-major: N x K;                    N-major: K x N
+  int lda, ldb;
+  int M, N, K;
+  int kchunk;     // split z covers k in [z kchunk, min(K, (z + 1) kchunk))
+  const float* bias;
+  const bf16* mask;
+  bf16* out_bf16;
+  float* out_f32;
+  int ldo;               // output row stride (elements)
+  int64_t split_stride;  // offset between the splits' outputs (kEpiPartial)
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(pred ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+__device__ __forceinline__ void ldsm4(uint32_t* r, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t* r, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(p)));
+}
+
+// Stage one K step of an operand into `t`: rows r0 .. r0+63 of R (M or N), k in [k0, k0+32)
+// clipped to [.., ke).  Out-of-range vectors are zero-filled (cp.async with source size 0 reads
+// nothing; the source address is then the operand's base).
+template <bool kKMajor>
+__device__ __forceinline__ void stage_tile(bf16* t, const bf16* X, int ld, int R, int r0, int k0, int ke, int tid) {
+#pragma unroll
+  for (int q = tid; q < kBM * kBK / 8; q += kGemmThreads) {
+    if (kKMajor) {
+      const int r = q >> 2, c = (q & 3) * 8;
+      const bool ok = r0 + r < R && k0 + c < ke;
+      cp_async16(t + r * kKPad + c, ok ? X + (size_t)(r0 + r) * ld + k0 + c : X, ok);
+    } else {
+      const int kr = q >> 3, c = (q & 7) * 8;
+      const bool ok = k0 + kr < ke && r0 + c < R;
+      cp_async16(t + kr * kMPad + c, ok ? X + (size_t)(k0 + kr) * ld + r0 + c : X, ok);
+    }
+  }
+}
+
+template <int kEpi, bool kAK, bool kBK_>
+__global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
+  __shared__ __align__(128) bf16 sA[2][kTileElems];
+  __shared__ __align__(128) bf16 sB[2][kTileElems];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int kb = blockIdx.z * g.kchunk, ke = min(g.K, kb + g.kchunk);
+  const int nk = ke > kb ? (ke - kb + kBK - 1) / kBK : 0;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+
+  if (nk > 0) {
+    stage_tile<kAK>(sA[0], g.A, g.lda, g.M, m0, kb, ke, tid);
+    stage_tile<kBK_>(sB[0], g.B, g.ldb, g.N, n0, kb, ke, tid);
+  }
+  cp_async_commit();
+  const int mi = lane >> 3, i8 = lane & 7;
+  for (int it = 0; it < nk; ++it) {
+    if (it + 1 < nk) {
+      const int k1 = kb + (it + 1) * kBK;
+      stage_tile<kAK>(sA[(it + 1) & 1], g.A, g.lda, g.M, m0, k1, ke, tid);
+      stage_tile<kBK_>(sB[(it + 1) & 1], g.B, g.ldb, g.N, n0, k1, ke, tid);
+    }
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const bf16* tA = sA[it & 1];
+    const bf16* tB = sB[it & 1];
+#pragma unroll
+    for (int kk = 0; kk < kBK; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int mb = wm * 32 + i * 16;
+        if (kAK)
+          ldsm4(a[i], tA + (mb + (mi & 1) * 8 + i8) * kKPad + kk + (mi >> 1) * 8);
+        else
+          ldsm4t(a[i], tA + (kk + (mi >> 1) * 8 + i8) * kMPad + mb + (mi & 1) * 8);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; j += 2) {
+        const int nb = wn * 32 + j * 8;
+        uint32_t r[4];
+        if (kBK_)
+          ldsm4(r, tB + (nb + (mi >> 1) * 8 + i8) * kKPad + kk + (mi & 1) * 8);
+        else
+          ldsm4t(r, tB + (kk + (mi & 1) * 8 + i8) * kMPad + nb + (mi >> 1) * 8);
+        b[j][0] = r[0];
+        b[j][1] = r[1];
+        b[j + 1][0] = r[2];
+        b[j + 1][1] = r[3];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};\n"
+              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+    }
+    __syncthreads();
+  }
+
+  // accumulator (i, j): [0..1] row g, columns 2t, 2t+1; [2..3] row g + 8
+  const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = m0 + wm * 32 + i * 16 + gq + 8 * h;
+        const int c = n0 + wn * 32 + j * 8 + 2 * tq;
+        if (r >= g.M || c >= g.N) continue;
+        float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
+        const size_t o = (size_t)r * g.ldo + c;
+        if (kEpi == kEpiBiasRelu) {
+          v0 = fmaxf(v0 + g.bias[c], 0.f);
+          v1 = fmaxf(v1 + g.bias[c + 1], 0.f);
+          *reinterpret_cast<__nv_bfloat162*>(g.out_bf16 + o) = __floats2bfloat162_rn(v0, v1);
+        } else if (kEpi == kEpiBias) {
+          g.out_f32[o] = v0 + g.bias[c];
+          g.out_f32[o + 1] = v1 + g.bias[c + 1];
+        } else if (kEpi == kEpiMask) {
+          const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(g.mask + o);
+          v0 = __low2float(mk) > 0.f ? v0 : 0.f;
+          v1 = __high2float(mk) > 0.f ? v1 : 0.f;
+          *reinterpret_cast<__nv_bfloat162*>(g.out_bf16 + o) = __floats2bfloat162_rn(v0, v1);
+        } else {
+          float* out = g.out_f32 + blockIdx.z * g.split_stride;
+          out[o] = v0;
+          out[o + 1] = v1;
+        }
+      }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ in, int64_t n, bf16* __restrict__ out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = __float2bfloat16_rn(in[k]);
+}
+
+__global__ void k_bf16_to_f32(const bf16* __restrict__ in, int64_t n, float* __restrict__ out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = __bfloat162float(in[k]);
+}
+
+// Bias-gradient partials: out[s * stride + c] = sum of g[r][c] over rows r of split s
+// (rows [s chunk, min(B, (s + 1) chunk))).  Block (32, 8): 32 columns, 8 row phases added in a
+// fixed order.
+__global__ void k_colsum_part(const bf16* __restrict__ g, int B, int C, int chunk, float* __restrict__ out,
+                              int64_t stride) {
+  __shared__ float red[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x, s = blockIdx.y;
+  const int r0 = s * chunk, r1 = min(B, r0 + chunk);
+  float acc = 0.f;
+  if (c < C)
+    for (int r = r0 + threadIdx.y; r < r1; r += 8) acc += __bfloat162float(g[(size_t)r * C + c]);
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < C) {
+    float t = 0.f;
+    for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
+    out[(int64_t)s * stride + c] = t;
+  }
+}
+
+// Sum of the S gradient partials (for reading the gradient out).
+__global__ void k_sum_parts(const float* __restrict__ part, int S, int64_t P, float* __restrict__ out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    float t = 0.f;
+    for (int s = 0; s < S; ++s) t += part[(int64_t)s * P + k];
+    out[k] = t;
+  }
+}
+
+// Box-Muller on the two 24-bit fields of a 64-bit word (bits 63..40 -> u1, 39..16 -> u2).
+__device__ __forceinline__ void normal_pair(uint64_t w, float* z0, float* z1) {
+  const float u1 = ((float)(uint32_t)(w >> 40) + 0.5f) * 5.9604644775390625e-08f;
+  const float u2 = ((float)(uint32_t)((w >> 16) & 0xFFFFFFull) + 0.5f) * 5.9604644775390625e-08f;
+  const float r = sqrtf(-2.0f * logf(u1));
+  float sn, cs;
+  sincospif(2.0f * u2, &sn, &cs);
+  *z0 = r * cs;
+  *z1 = r * sn;
+}
+
+// Network inputs of B rows: row r = [feat[env_r] (F), z_r (8), zeros] as BF16 (width d0).  Draw
+// set (t, stream): z_r from Philox4x64-10 counter (t, r, stream, 0), key (seed, 1); with
+// n_env > 0, env_r from counter (t, r, stream + 1, 0): floor((word0 >> 32) n_env / 2^32), else 0.
+// t = ctl[0] when ctl is given, else 0.  Block: 16 rows.
+__global__ void k_assemble(const float* __restrict__ feat, int F, int n_env, int d0, int B, uint64_t seed,
+                           uint64_t stream_id, const int64_t* __restrict__ ctl, bf16* __restrict__ x,
+                           int32_t* __restrict__ env_out) {
+  __shared__ float z[16][kLatent];
+  __shared__ int e[16];
+  const int row0 = blockIdx.x * 16;
+  if (threadIdx.x < 16) {
+    const int r = row0 + threadIdx.x;
+    const uint64_t t = ctl ? (uint64_t)ctl[0] : 0ull;
+    uint64_t o[4];
+    philox4x64(t, (uint64_t)r, stream_id, 0ull, seed, 1ull, o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) normal_pair(o[j], &z[threadIdx.x][2 * j], &z[threadIdx.x][2 * j + 1]);
+    int env = 0;
+    if (n_env > 0) {
+      philox4x64(t, (uint64_t)r, stream_id + 1, 0ull, seed, 1ull, o);
+      env = (int)(((o[0] >> 32) * (uint64_t)n_env) >> 32);
+    }
+    e[threadIdx.x] = env;
+    if (env_out && r < B) env_out[r] = env;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 16 * d0; q += blockDim.x) {
+    const int rr = q / d0, c = q - rr * d0, r = row0 + rr;
+    if (r >= B) break;
+    float v = 0.f;
+    if (c < F)
+      v = feat[(size_t)e[rr] * F + c];
+    else if (c < F + kLatent)
+      v = z[rr][c - F];
+    x[(size_t)r * d0 + c] = __float2bfloat16_rn(v);
+  }
+}
+
+__device__ __forceinline__ float squash(float o, int j, float vmax) {
+  return j < 3 ? 0.5f + 0.5f * tanhf(o) : vmax * tanhf(o);
+}
+
+__global__ void k_squash(const float* __restrict__ o, int B, int ld, float vmax, float* __restrict__ states) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= B * kOutUsed) return;
+  const int r = q / kOutUsed, j = q % kOutUsed;
+  states[q] = squash(o[(size_t)r * ld + j], j, vmax);
+}
+
+struct LossArgs {
+  int kind;          // 0 winner takes all, 1 path-indexed
+  const bf16* x;     // network inputs (kind 1 reads the first latent at column latent_col)
+  int d0, latent_col;
+};
+
+// Loss and its gradient.  Row r uses target set env[r] (r without env): targets
+// tg[set][0 .. ntg[set]) of 6 floats.  Kind 0 takes the nearest target (first on ties); kind 1
+// the point at fraction u = Phi(z_0) of the targets' polyline: a = u (n - 1),
+// i = min(floor(a), n - 2), y = y_i + (a - i)(y_{i+1} - y_i).  Writes g = bf16(d mean loss / d o)
+// (B x ld, zero past column 6) and, from thread 0 after a fixed-order block reduction,
+// trace[ctl[0] - ctl[1]] = mean loss; then advances ctl[0].  One block.
+__global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__ o, int B, int ld, float vmax,
+                                                       const float* __restrict__ tg, const int32_t* __restrict__ ntg,
+                                                       int T, const int32_t* __restrict__ env, const LossArgs la,
+                                                       bf16* __restrict__ gout, int64_t* __restrict__ ctl,
+                                                       float* __restrict__ trace, int trace_cap) {
+  __shared__ float red[kLossThreads];
+  float local = 0.f;
+  for (int r = threadIdx.x; r < B; r += kLossThreads) {
+    const int set = env ? env[r] : r;
+    const float* q0 = tg + (size_t)set * T * kOutUsed;
+    const int n = min(ntg[set], T);
+    float s[kOutUsed], y[kOutUsed];
+    for (int j = 0; j < kOutUsed; ++j) s[j] = squash(o[(size_t)r * ld + j], j, vmax);
+    bool has = n > 0;
+    float loss = 0.f;
+    if (has && la.kind == 0) {
+      int best = 0;
+      float bd = 0.f;
+      for (int p = 0; p < n; ++p) {
+        float d = 0.f;
+        for (int j = 0; j < kOutUsed; ++j) {
+          const float u = s[j] - q0[p * kOutUsed + j];
+          d += u * u;
+        }
+        if (p == 0 || d < bd) {
+          best = p;
+          bd = d;
+        }
+      }
+      for (int j = 0; j < kOutUsed; ++j) y[j] = q0[best * kOutUsed + j];
+      loss = bd;
+    } else if (has) {
+      const float z0 = __bfloat162float(la.x[(size_t)r * la.d0 + la.latent_col]);
+      const float u = normcdff(z0);
+      int i = 0;
+      float f = 0.f;
+      if (n > 1) {
+        const float a = u * (float)(n - 1);
+        i = min((int)floorf(a), n - 2);
+        f = a - (float)i;
+      }
+      for (int j = 0; j < kOutUsed; ++j) {
+        const float y0 = q0[i * kOutUsed + j];
+        y[j] = n > 1 ? y0 + f * (q0[(i + 1) * kOutUsed + j] - y0) : y0;
+        const float d = s[j] - y[j];
+        loss += d * d;
+      }
+    }
+    local += loss;
+    for (int j = 0; j < ld; ++j) {
+      float gj = 0.f;
+      if (has && j < kOutUsed) {
+        const float th = tanhf(o[(size_t)r * ld + j]);
+        const float ds = (j < 3 ? 0.5f : vmax) * (1.f - th * th);
+        gj = 2.f * (s[j] - y[j]) * ds / (float)B;
+      }
+      gout[(size_t)r * ld + j] = __float2bfloat16_rn(gj);
+    }
+  }
+  red[threadIdx.x] = local;
+  __syncthreads();
+  for (int w = kLossThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int64_t idx = ctl[0] - ctl[1];
+    if (trace && idx >= 0 && idx < trace_cap) trace[idx] = red[0] / (float)B;
+    ctl[0] += 1;
+  }
+}
+
+// Adam over the flat parameter vector (Kingma and Ba, 2015): gradient = sum of the S partials,
+// step count t = ctl[0] (already advanced by the loss), then the BF16 copy.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ part, int S, int64_t P, float* __restrict__ m,
+                       float* __restrict__ v, const int64_t* __restrict__ ctl, float lr, bf16* __restrict__ wb) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float t = (float)ctl[0];
+  const float c1 = 1.f - powf(b1, t), c2 = 1.f - powf(b2, t);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    float gk = 0.f;
+    for (int s = 0; s < S; ++s) gk += part[(int64_t)s * P + k];
+    const float mk = b1 * m[k] + (1.f - b1) * gk;
+    const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    const float wk = w[k] - lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+    w[k] = wk;
+    wb[k] = __float2bfloat16_rn(wk);
+  }
+}
+
+int grid_for(int64_t n, int threads, int cap = 1184) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, cap));
+}
+
+}  // namespace
+}  // namespace pump
+
+using pump::bf16;
+
+struct pump_mlp {
+  int L = 0;
+  std::vector<int> dims;
+  std::vector<int64_t> offW, offb;  // offsets of W_l and b_l in the flat vector
+  int64_t P = 0;
+  float* w = nullptr;      // FP32 master parameters (flat)
+  float* m1 = nullptr;     // Adam first moments
+  float* m2 = nullptr;     // Adam second moments
+  bf16* wb = nullptr;      // BF16 copy of w
+  int64_t* ctl = nullptr;  // [0] Adam steps taken, [1] trace base
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  // scratch for up to `cap` rows
+  int cap = 0;
+  std::vector<bf16*> act;  // act[l]: layer l input (B x dims[l]), l < L
+  bf16* gA = nullptr;      // gradients w.r.t. pre-activations (B x maxd), two buffers
+  bf16* gB = nullptr;
+  float* out = nullptr;    // last layer's outputs (B x dims[L])
+  float* xf = nullptr;     // FP32 staging (B x max(dims[0], dims[L]))
+  float* part = nullptr;   // gradient partials (kMaxSplit x P)
+  float* gsum = nullptr;   // summed gradient (P)
+  int32_t* env = nullptr;  // row -> target set (B)
+  float* tg_rows = nullptr;  // per-row targets for pump_mlp_train_step (cap x T x 6)
+  int32_t* ntg_rows = nullptr;
+  int tg_rows_T = 0;
+  std::vector<void*> scratch;
+  // training set
+  float* feat = nullptr;
+  float* tg = nullptr;
+  int32_t* ntg = nullptr;
+  int F = 0, n_env = 0, T = 0;
+  // mean losses of the steps of one call
+  float* trace = nullptr;
+  int trace_cap = 0;
+  // captured training step
+  cudaGraphExec_t step_exec = nullptr;
+  int step_batch = 0;
+  uint64_t step_seed = 0;
+  float step_lr = 0.f, step_vmax = 0.f;
+  int step_launches = 0;
+  // loss
+  int loss_kind = 0, latent_col = 0;
+};
+
+namespace {
+
+using namespace pump;
+
+template <typename T>
+T* dmalloc(size_t n) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, sizeof(T) * std::max<size_t>(n, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (T*)p;
+}
+
+void drop_graph(pump_mlp* m) {
+  if (m->step_exec) cudaGraphExecDestroy(m->step_exec);
+  m->step_exec = nullptr;
+  m->step_batch = 0;
+}
+
+void free_scratch(pump_mlp* m) {
+  for (void* p : m->scratch) cudaFree(p);
+  m->scratch.clear();
+  m->act.clear();
+  m->gA = m->gB = nullptr;
+  m->out = m->xf = m->part = m->gsum = m->tg_rows = nullptr;
+  m->env = m->ntg_rows = nullptr;
+  m->tg_rows_T = 0;
+  m->cap = 0;
+}
+
+int ensure_batch(pump_mlp* m, int B) {
+  if (B <= m->cap) return PUMP_OK;
+  cudaStreamSynchronize(m->s);
+  drop_graph(m);
+  free_scratch(m);
+  int maxd = 0;
+  for (int d : m->dims) maxd = std::max(maxd, d);
+  auto take = [&](void* p) {
+    if (p) m->scratch.push_back(p);
+    return p != nullptr;
+  };
+  bool ok = true;
+  for (int l = 0; l < m->L; ++l) {
+    m->act.push_back(dmalloc<bf16>((size_t)B * m->dims[l]));
+    ok &= take(m->act.back());
+  }
+  ok &= take(m->gA = dmalloc<bf16>((size_t)B * maxd));
+  ok &= take(m->gB = dmalloc<bf16>((size_t)B * maxd));
+  ok &= take(m->out = dmalloc<float>((size_t)B * m->dims[m->L]));
+  ok &= take(m->xf = dmalloc<float>((size_t)B * std::max(m->dims[0], m->dims[m->L])));
+  ok &= take(m->part = dmalloc<float>((size_t)kMaxSplit * m->P));
+  ok &= take(m->gsum = dmalloc<float>((size_t)m->P));
+  ok &= take(m->env = dmalloc<int32_t>((size_t)B));
+  if (!ok) {
+    free_scratch(m);
+    return PUMP_ERR_OOM;
+  }
+  m->cap = B;
+  return PUMP_OK;
+}
+
+int ensure_trace(pump_mlp* m, int n) {
+  if (m->trace_cap >= n && m->trace) return PUMP_OK;
+  PUMP_CUDA_TRY(cudaStreamSynchronize(m->s));
+  drop_graph(m);
+  if (m->trace) cudaFree(m->trace);
+  m->trace_cap = std::max(n, 1024);
+  m->trace = dmalloc<float>((size_t)m->trace_cap);
+  if (!m->trace) {
+    m->trace_cap = 0;
+    return PUMP_ERR_OOM;
+  }
+  return PUMP_OK;
+}
+
+// Splits of the weight-gradient products over the batch.
+int n_splits(int B) { return std::max(1, std::min(kMaxSplit, B / 512)); }
+int split_chunk(int B, int S) { return ((B + S - 1) / S + kBK - 1) / kBK * kBK; }
+
+template <int kEpi, bool kAK, bool kBK_>
+void gemm(const GemmArgs& a, int splits, cudaStream_t s, int* launches) {
+  dim3 grid((a.N + kBN - 1) / kBN, (a.M + kBM - 1) / kBM, splits);
+  k_gemm<kEpi, kAK, kBK_><<<grid, kGemmThreads, 0, s>>>(a);
+  ++*launches;
+}
+
+// Forward pass over B rows of act[0]; outputs (FP32) in m->out.
+void forward(pump_mlp* m, int B, cudaStream_t s, int* launches) {
+  for (int l = 0; l < m->L; ++l) {
+    GemmArgs a{};
+    a.A = m->act[l];
+    a.lda = m->dims[l];
+    a.B = m->wb + m->offW[l];
+    a.ldb = m->dims[l];
+    a.M = B;
+    a.N = m->dims[l + 1];
+    a.K = m->dims[l];
+    a.kchunk = a.K;
+    a.bias = m->w + m->offb[l];
+    a.ldo = a.N;
+    if (l + 1 < m->L) {
+      a.out_bf16 = m->act[l + 1];
+      gemm<kEpiBiasRelu, true, true>(a, 1, s, launches);
+    } else {
+      a.out_f32 = m->out;
+      gemm<kEpiBias, true, true>(a, 1, s, launches);
+    }
+  }
+}
+
+// Backward pass from g = m->gA (B x dims[L], BF16); gradient partials into m->part.
+void backward(pump_mlp* m, int B, cudaStream_t s, int* launches) {
+  const int S = n_splits(B), chunk = split_chunk(B, S);
+  bf16* g = m->gA;
+  bf16* gn = m->gB;
+  for (int l = m->L - 1; l >= 0; --l) {
+    const int in = m->dims[l], out = m->dims[l + 1];
+    k_colsum_part<<<dim3((out + 31) / 32, S), dim3(32, 8), 0, s>>>(g, B, out, chunk, m->part + m->offb[l], m->P);
+    ++*launches;
+    GemmArgs w{};  // dW_l = g^T h_l
+    w.A = g;
+    w.lda = out;
+    w.B = m->act[l];
+    w.ldb = in;
+    w.M = out;
+    w.N = in;
+    w.K = B;
+    w.kchunk = chunk;
+    w.out_f32 = m->part + m->offW[l];
+    w.ldo = in;
+    w.split_stride = m->P;
+    gemm<kEpiPartial, false, false>(w, S, s, launches);
+    if (l > 0) {
+      GemmArgs d{};  // g_{l-1} = (g W_l) * [h_l > 0]
+      d.A = g;
+      d.lda = out;
+      d.B = m->wb + m->offW[l];
+      d.ldb = in;
+      d.M = B;
+      d.N = in;
+      d.K = out;
+      d.kchunk = out;
+      d.mask = m->act[l];
+      d.out_bf16 = gn;
+      d.ldo = in;
+      gemm<kEpiMask, true, false>(d, 1, s, launches);
+      std::swap(g, gn);
+    }
+  }
+}
+
+void adam(pump_mlp* m, int B, float lr, cudaStream_t s, int* launches) {
+  k_adam<<<grid_for(m->P, 256), 256, 0, s>>>(m->w, m->part, n_splits(B), m->P, m->m1, m->m2, m->ctl, lr, m->wb);
+  ++*launches;
+}
+
+// Inputs (FP32, host or device, B x dims[0]) -> act[0].
+int stage_input(pump_mlp* m, const float* x, int B, int* launches) {
+  const size_t n = (size_t)B * m->dims[0];
+  PUMP_CUDA_TRY(cudaMemcpyAsync(m->xf, x, sizeof(float) * n, cudaMemcpyDefault, m->s));
+  k_to_bf16<<<grid_for((int64_t)n, 256), 256, 0, m->s>>>(m->xf, (int64_t)n, m->act[0]);
+  ++*launches;
+  return PUMP_OK;
+}
+
+LossArgs loss_args(const pump_mlp* m) {
+  LossArgs a{};
+  a.kind = m->loss_kind;
+  a.x = m->act[0];
+  a.d0 = m->dims[0];
+  a.latent_col = m->latent_col;
+  return a;
+}
+
+// One training step on the stored training set (graph-capturable): draws, forward, loss,
+// backward, Adam.
+void train_step_kernels(pump_mlp* m, int B, uint64_t seed, float lr, float vmax, cudaStream_t s, int* launches) {
+  k_assemble<<<(B + 15) / 16, 128, 0, s>>>(m->feat, m->F, m->n_env, m->dims[0], B, seed, 0ull, m->ctl, m->act[0],
+                                           m->env);
+  ++*launches;
+  forward(m, B, s, launches);
+  k_loss<<<1, kLossThreads, 0, s>>>(m->out, B, m->dims[m->L], vmax, m->tg, m->ntg, m->T, m->env, loss_args(m), m->gA,
+                                    m->ctl, m->trace, m->trace_cap);
+  ++*launches;
+  backward(m, B, s, launches);
+  adam(m, B, lr, s, launches);
+}
+
+void count_launches(int64_t n) {
+  for (int64_t k = 0; k < n; ++k) note_launch();
+}
+
+// Order the library's stream after the caller's.
+int enter(pump_mlp* m, void* stream) {
+  PUMP_CUDA_TRY(cudaEventRecord(m->ev, (cudaStream_t)stream));
+  PUMP_CUDA_TRY(cudaStreamWaitEvent(m->s, m->ev, 0));
+  return PUMP_OK;
+}
+
+int finish(pump_mlp* m) {
+  PUMP_CUDA_TRY(cudaStreamSynchronize(m->s));
+  PUMP_CUDA_TRY(cudaGetLastError());
+  return PUMP_OK;
+}
+
+uint64_t splitmix(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pump_mlp_create(int32_t n_layers, const int32_t* dims, uint64_t seed, pump_mlp** out) {
+  if (!out || !dims || n_layers < 1 || n_layers > 16) return PUMP_ERR_INVALID_ARG;
+  for (int l = 0; l <= n_layers; ++l)
+    if (dims[l] < 16 || dims[l] > 4096 || dims[l] % 16) return PUMP_ERR_INVALID_ARG;
+  pump_mlp* m = new (std::nothrow) pump_mlp();
+  if (!m) return PUMP_ERR_OOM;
+  m->L = n_layers;
+  m->dims.assign(dims, dims + n_layers + 1);
+  for (int l = 0; l < n_layers; ++l) {
+    m->offW.push_back(m->P);
+    m->P += (int64_t)dims[l] * dims[l + 1];
+    m->offb.push_back(m->P);
+    m->P += dims[l + 1];
+  }
+  m->w = dmalloc<float>(m->P);
+  m->m1 = dmalloc<float>(m->P);
+  m->m2 = dmalloc<float>(m->P);
+  m->wb = dmalloc<bf16>(m->P);
+  m->ctl = dmalloc<int64_t>(2);
+  if (!m->w || !m->m1 || !m->m2 || !m->wb || !m->ctl ||
+      cudaStreamCreateWithFlags(&m->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) != cudaSuccess) {
+    pump_mlp_destroy(m);
+    return PUMP_ERR_OOM;
+  }
+  // He-uniform weights from a seeded splitmix64 stream, zero biases
+  std::vector<float> h((size_t)m->P, 0.f);
+  uint64_t st = seed;
+  for (int l = 0; l < n_layers; ++l) {
+    const double lim = std::sqrt(6.0 / (double)dims[l]);
+    for (int64_t k = 0; k < (int64_t)dims[l] * dims[l + 1]; ++k)
+      h[m->offW[l] + k] = (float)((((double)(splitmix(st) >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0) * lim);
+  }
+  const int rc = pump_mlp_set_params(m, h.data(), m->P);
+  if (rc) {
+    pump_mlp_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return PUMP_OK;
+}
+
+int64_t pump_mlp_param_count(const pump_mlp* m) { return m ? m->P : -1; }
+
+int pump_mlp_set_params(pump_mlp* m, const float* params, int64_t count) {
+  if (!m || !params || count != m->P) return PUMP_ERR_INVALID_ARG;
+  PUMP_CUDA_TRY(cudaMemcpyAsync(m->w, params, sizeof(float) * m->P, cudaMemcpyDefault, m->s));
+  PUMP_CUDA_TRY(cudaMemsetAsync(m->m1, 0, sizeof(float) * m->P, m->s));
+  PUMP_CUDA_TRY(cudaMemsetAsync(m->m2, 0, sizeof(float) * m->P, m->s));
+  PUMP_CUDA_TRY(cudaMemsetAsync(m->ctl, 0, sizeof(int64_t) * 2, m->s));
+  k_to_bf16<<<grid_for(m->P, 256), 256, 0, m->s>>>(m->w, m->P, m->wb);
+  count_launches(1);
+  return finish(m);
+}
+
+int pump_mlp_get_params(pump_mlp* m, float* params, int64_t count, int64_t* steps) {
+  if (!m || !params || count != m->P) return PUMP_ERR_INVALID_ARG;
+  PUMP_CUDA_TRY(cudaMemcpyAsync(params, m->w, sizeof(float) * m->P, cudaMemcpyDefault, m->s));
+  int64_t ctl[2] = {0, 0};
+  PUMP_CUDA_TRY(cudaMemcpyAsync(ctl, m->ctl, sizeof(ctl), cudaMemcpyDeviceToHost, m->s));
+  const int rc = finish(m);
+  if (!rc && steps) *steps = ctl[0];
+  return rc;
+}
+
+int pump_mlp_forward(pump_mlp* m, const float* x, int32_t B, float* y, void* stream) {
+  if (!m || !x || !y || B < 1) return PUMP_ERR_INVALID_ARG;
+  int rc = ensure_batch(m, B);
+  if (!rc) rc = enter(m, stream);
+  int n = 0;
+  if (!rc) rc = stage_input(m, x, B, &n);
+  if (rc) return rc;
+  forward(m, B, m->s, &n);
+  count_launches(n);
+  PUMP_CUDA_TRY(cudaMemcpyAsync(y, m->out, sizeof(float) * (size_t)B * m->dims[m->L], cudaMemcpyDefault, m->s));
+  return finish(m);
+}
+
+int pump_mlp_gradients(pump_mlp* m, const float* x, int32_t B, const float* dy, float* grads, int64_t count,
+                       void* stream) {
+  if (!m || !x || !dy || !grads || B < 1 || count != m->P) return PUMP_ERR_INVALID_ARG;
+  int rc = ensure_batch(m, B);
+  if (!rc) rc = enter(m, stream);
+  int n = 0;
+  if (!rc) rc = stage_input(m, x, B, &n);
+  if (rc) return rc;
+  forward(m, B, m->s, &n);
+  const size_t no = (size_t)B * m->dims[m->L];
+  PUMP_CUDA_TRY(cudaMemcpyAsync(m->xf, dy, sizeof(float) * no, cudaMemcpyDefault, m->s));
+  k_to_bf16<<<grid_for((int64_t)no, 256), 256, 0, m->s>>>(m->xf, (int64_t)no, m->gA);
+  ++n;
+  backward(m, B, m->s, &n);
+  k_sum_parts<<<grid_for(m->P, 256), 256, 0, m->s>>>(m->part, n_splits(B), m->P, m->gsum);
+  ++n;
+  count_launches(n);
+  PUMP_CUDA_TRY(cudaMemcpyAsync(grads, m->gsum, sizeof(float) * m->P, cudaMemcpyDefault, m->s));
+  return finish(m);
+}
+
+int pump_mlp_train_step(pump_mlp* m, const float* x, int32_t B, const float* targets, const int32_t* n_targets,
+                        int32_t T, float lr, float vmax, float* mean_loss, void* stream) {
+  if (!m || !x || !targets || !n_targets || B < 1 || T < 1 || !(lr > 0.f) || !(vmax > 0.f))
+    return PUMP_ERR_INVALID_ARG;
+  int rc = ensure_batch(m, B);
+  if (!rc) rc = ensure_trace(m, 1);
+  if (rc) return rc;
+  if (m->tg_rows_T != T || !m->tg_rows) {
+    PUMP_CUDA_TRY(cudaStreamSynchronize(m->s));
+    for (void* p : {(void*)m->tg_rows, (void*)m->ntg_rows}) {
+      auto it = std::find(m->scratch.begin(), m->scratch.end(), p);
+      if (p && it != m->scratch.end()) {
+        cudaFree(p);
+        m->scratch.erase(it);
+      }
+    }
+    m->tg_rows = dmalloc<float>((size_t)m->cap * T * kOutUsed);
+    m->ntg_rows = dmalloc<int32_t>((size_t)m->cap);
+    if (m->tg_rows) m->scratch.push_back(m->tg_rows);
+    if (m->ntg_rows) m->scratch.push_back(m->ntg_rows);
+    if (!m->tg_rows || !m->ntg_rows) {
+      m->tg_rows_T = 0;
+      return PUMP_ERR_OOM;
+    }
+    m->tg_rows_T = T;
+  }
+  rc = enter(m, stream);
+  int n = 0;
+  if (!rc) rc = stage_input(m, x, B, &n);
+  if (rc) return rc;
+  PUMP_CUDA_TRY(
+      cudaMemcpyAsync(m->tg_rows, targets, sizeof(float) * (size_t)B * T * kOutUsed, cudaMemcpyDefault, m->s));
+  PUMP_CUDA_TRY(cudaMemcpyAsync(m->ntg_rows, n_targets, sizeof(int32_t) * B, cudaMemcpyDefault, m->s));
+  // the step's mean loss goes to trace[0]: base = the current step count
+  PUMP_CUDA_TRY(cudaMemcpyAsync(m->ctl + 1, m->ctl, sizeof(int64_t), cudaMemcpyDeviceToDevice, m->s));
+  forward(m, B, m->s, &n);
+  k_loss<<<1, kLossThreads, 0, m->s>>>(m->out, B, m->dims[m->L], vmax, m->tg_rows, m->ntg_rows, T, nullptr,
+                                       loss_args(m), m->gA, m->ctl, m->trace, m->trace_cap);
+  ++n;
+  backward(m, B, m->s, &n);
+  adam(m, B, lr, m->s, &n);
+  count_launches(n);
+  float l = 0.f;
+  PUMP_CUDA_TRY(cudaMemcpyAsync(&l, m->trace, sizeof(float), cudaMemcpyDeviceToHost, m->s));
+  rc = finish(m);
+  if (!rc && mean_loss) *mean_loss = l;
+  return rc;
+}
+
+int pump_mlp_set_loss(pump_mlp* m, int32_t kind, int32_t latent_col) {
+  if (!m || kind < 0 || kind > 1 || latent_col < 0 || latent_col >= m->dims[0]) return PUMP_ERR_INVALID_ARG;
+  PUMP_CUDA_TRY(cudaStreamSynchronize(m->s));
+  drop_graph(m);
+  m->loss_kind = kind;
+  m->latent_col = latent_col;
+  return PUMP_OK;
+}
+
+int pump_mlp_set_data(pump_mlp* m, const float* feat, int32_t F, int32_t n_env, const float* targets,
+                      const int32_t* n_targets, int32_t T) {
+  if (!m || (!feat && F > 0) || !targets || !n_targets || n_env < 1 || T < 1 || F < 0 || F + kLatent > m->dims[0])
+    return PUMP_ERR_INVALID_ARG;
+  PUMP_CUDA_TRY(cudaStreamSynchronize(m->s));
+  drop_graph(m);
+  for (void* p : {(void*)m->feat, (void*)m->tg, (void*)m->ntg})
+    if (p) cudaFree(p);
+  m->feat = dmalloc<float>((size_t)n_env * std::max(F, 1));
+  m->tg = dmalloc<float>((size_t)n_env * T * kOutUsed);
+  m->ntg = dmalloc<int32_t>((size_t)n_env);
+  if (!m->feat || !m->tg || !m->ntg) {
+    for (void* p : {(void*)m->feat, (void*)m->tg, (void*)m->ntg})
+      if (p) cudaFree(p);
+    m->feat = m->tg = nullptr;
+    m->ntg = nullptr;
+    m->n_env = 0;
+    return PUMP_ERR_OOM;
+  }
+  m->F = F;
+  m->n_env = n_env;
+  m->T = T;
+  if (F > 0)
+    PUMP_CUDA_TRY(cudaMemcpyAsync(m->feat, feat, sizeof(float) * (size_t)n_env * F, cudaMemcpyDefault, m->s));
+  PUMP_CUDA_TRY(
+      cudaMemcpyAsync(m->tg, targets, sizeof(float) * (size_t)n_env * T * kOutUsed, cudaMemcpyDefault, m->s));
+  PUMP_CUDA_TRY(cudaMemcpyAsync(m->ntg, n_targets, sizeof(int32_t) * n_env, cudaMemcpyDefault, m->s));
+  return finish(m);
+}
+
+int pump_mlp_assemble(pump_mlp* m, int32_t B, int64_t t, uint64_t seed, float* x, int32_t* env) {
+  if (!m || !x || B < 1 || t < 0 || !m->feat) return PUMP_ERR_INVALID_ARG;
+  int rc = ensure_batch(m, B);
+  if (rc) return rc;
+  int64_t saved[2] = {0, 0};
+  PUMP_CUDA_TRY(cudaMemcpyAsync(saved, m->ctl, sizeof(saved), cudaMemcpyDeviceToHost, m->s));
+  PUMP_CUDA_TRY(cudaStreamSynchronize(m->s));
+  const int64_t tmp[2] = {t, saved[1]};
+  PUMP_CUDA_TRY(cudaMemcpyAsync(m->ctl, tmp, sizeof(tmp), cudaMemcpyHostToDevice, m->s));
+  k_assemble<<<(B + 15) / 16, 128, 0, m->s>>>(m->feat, m->F, m->n_env, m->dims[0], B, seed, 0ull, m->ctl, m->act[0],
+                                              m->env);
+  const size_t n = (size_t)B * m->dims[0];
+  k_bf16_to_f32<<<grid_for((int64_t)n, 256), 256, 0, m->s>>>(m->act[0], (int64_t)n, m->xf);
+  count_launches(2);
+  PUMP_CUDA_TRY(cudaMemcpyAsync(x, m->xf, sizeof(float) * n, cudaMemcpyDefault, m->s));
+  if (env) PUMP_CUDA_TRY(cudaMemcpyAsync(env, m->env, sizeof(int32_t) * B, cudaMemcpyDefault, m->s));
+  PUMP_CUDA_TRY(cudaMemcpyAsync(m->ctl, saved, sizeof(saved), cudaMemcpyHostToDevice, m->s));
+  return finish(m);
+}
+
+int pump_mlp_train(pump_mlp* m, int32_t B, int32_t steps, float lr, float vmax, uint64_t seed, float* loss_trace,
+                   void* stream) {
+  if (!m || B < 1 || steps < 0 || !(lr > 0.f) || !(vmax > 0.f) || !m->feat) return PUMP_ERR_INVALID_ARG;
+  int rc = ensure_batch(m, B);
+  if (!rc) rc = ensure_trace(m, steps);
+  if (!rc) rc = enter(m, stream);
+  if (rc) return rc;
+  // losses of this call go to trace[0 .. steps): base = the current step count
+  PUMP_CUDA_TRY(cudaMemcpyAsync(m->ctl + 1, m->ctl, sizeof(int64_t), cudaMemcpyDeviceToDevice, m->s));
+  if (m->step_exec && (m->step_batch != B || m->step_seed != seed || m->step_lr != lr || m->step_vmax != vmax))
+    drop_graph(m);
+  if (!m->step_exec && steps > 0) {
+    cudaGraph_t graph = nullptr;
+    int n = 0;
+    PUMP_CUDA_TRY(cudaStreamBeginCapture(m->s, cudaStreamCaptureModeThreadLocal));
+    train_step_kernels(m, B, seed, lr, vmax, m->s, &n);
+    const cudaError_t ce = cudaStreamEndCapture(m->s, &graph);
+    if (ce != cudaSuccess || !graph) {
+      cudaGetLastError();
+      return PUMP_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&m->step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      m->step_exec = nullptr;
+      return PUMP_ERR_CUDA;
+    }
+    m->step_batch = B;
+    m->step_seed = seed;
+    m->step_lr = lr;
+    m->step_vmax = vmax;
+    m->step_launches = n;
+  }
+  for (int k = 0; k < steps; ++k) PUMP_CUDA_TRY(cudaGraphLaunch(m->step_exec, m->s));
+  count_launches((int64_t)m->step_launches * steps);
+  if (loss_trace && steps > 0)
+    PUMP_CUDA_TRY(cudaMemcpyAsync(loss_trace, m->trace, sizeof(float) * steps, cudaMemcpyDefault, m->s));
+  return finish(m);
+}
+
+int pump_mlp_propose(pump_mlp* m, const float* feat, int32_t F, int32_t count, uint64_t seed, float vmax,
+                     float* states, void* stream) {
+  if (!m || (!feat && F > 0) || !states || count < 1 || F < 0 || F + kLatent > m->dims[0] || !(vmax > 0.f))
+    return PUMP_ERR_INVALID_ARG;
+  const int B = (count + 15) / 16 * 16;
+  int rc = ensure_batch(m, B);
+  if (!rc) rc = enter(m, stream);
+  if (rc) return rc;
+  if (F > 0) PUMP_CUDA_TRY(cudaMemcpyAsync(m->xf, feat, sizeof(float) * F, cudaMemcpyDefault, m->s));
+  int n = 0;
+  k_assemble<<<B / 16, 128, 0, m->s>>>(m->xf, F, 0, m->dims[0], B, seed, 2ull, nullptr, m->act[0], nullptr);
+  ++n;
+  forward(m, B, m->s, &n);
+  k_squash<<<(count * kOutUsed + 255) / 256, 256, 0, m->s>>>(m->out, count, m->dims[m->L], vmax, m->xf);
+  ++n;
+  count_launches(n);
+  PUMP_CUDA_TRY(cudaMemcpyAsync(states, m->xf, sizeof(float) * (size_t)count * kOutUsed, cudaMemcpyDefault, m->s));
+  return finish(m);
+}
+
+void pump_mlp_destroy(pump_mlp* m) {
+  if (!m) return;
+  if (m->s) cudaStreamSynchronize(m->s);
+  drop_graph(m);
+  free_scratch(m);
+  for (void* p : {(void*)m->w, (void*)m->m1, (void*)m->m2, (void*)m->wb, (void*)m->ctl, (void*)m->feat, (void*)m->tg,
+                  (void*)m->ntg, (void*)m->trace})
+    if (p) cudaFree(p);
+  if (m->ev) cudaEventDestroy(m->ev);
+  if (m->s) cudaStreamDestroy(m->s);
+  delete m;
+}
+
+}  // extern "C"

@@ -252,3 +252,34 @@ def random_explore_graph(n: int, mean_degree: float, n_particles: int, seed: int
         emask[:, j] = (blk << np.arange(32, dtype=np.uint64)).sum(axis=1).astype(np.uint32)
     return ExploreGraph(n=n, row_ptr=row_ptr.astype(np.int32), col=col, ecost=ecost,
                         emask=emask, radius=float(radius), n_words=w)
+
+
+# ---------------------------------------------------------------------------
+# Environments of the learned sampling proposal (an extension; the paper draws samples
+# uniformly).  Indoor-like scenes whose box count is drawn per seed so that every scene fits the
+# proposal's 32 box slots.
+PROPOSAL_BOX_RANGE = (10, 32)
+
+
+def proposal_workload(seed: int, n_samples: int = 4000) -> Workload:
+    """Environment `seed` of the learned-proposal workloads: indoor walls and floor (5 boxes) plus
+    U{5..27} clutter boxes (U{10..32} in all), n_samples uniform samples, N = 128, W = 10,
+    sigma = 0.01, CP target 1 %, eta = 2, lambda = 0.5."""
+    g = _rng(seed, 8)
+    n_obs = int(g.integers(PROPOSAL_BOX_RANGE[0], PROPOSAL_BOX_RANGE[1] + 1))
+    boxes = indoor_boxes(seed, n_clutter=n_obs - 5)
+    states = sample_states(n_samples, seed)
+    return Workload(
+        name="proposal", seed=seed, states=states,
+        boxes=np.asarray(boxes, dtype=np.float32).reshape(-1, 6),
+        goal_idx=goal_members(states),
+        xi=particle_normals(128, 10, seed),
+        radius=radius_for(n_samples + 2), n_particles=128, n_waypoints=10,
+        sigma=0.01, alpha=0.01, eta=2.0, lam=0.5, mc_seed=seed)
+
+
+def with_samples(wl: Workload, samples: np.ndarray) -> Workload:
+    """The same query with its samples replaced (start and goal kept): goal region and radius
+    follow the new sample set."""
+    states = np.concatenate([wl.states[:2], np.asarray(samples, np.float32).reshape(-1, 6)]).astype(np.float32)
+    return dataclasses.replace(wl, states=states, goal_idx=goal_members(states), radius=radius_for(states.shape[0]))

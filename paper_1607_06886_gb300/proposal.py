@@ -1,0 +1,166 @@
+"""Learned sampling proposal: data collection, training and paired evaluation.
+
+The paper draws SampleFree uniformly (Algorithm 3).  This extension learns where certified plans
+run and proposes part of the samples there:
+
+1. collect  - plain PUMP (uniform samples, the full pipeline of graph build, Explore,
+              PlanSelection and MC certification) on seeded training environments through the
+              request server; every certified plan gives its intermediate states as targets.
+2. train    - the BF16 network (pump_mlp_*) learns, for an environment's features and eight
+              normals, a state near one of those targets (winner takes all), with the training
+              loop on the device.
+3. evaluate - on held-out environments, the same query planned twice: all samples uniform, and
+              half uniform (the same first half) plus half proposed; success and certified cost
+              are compared pair by pair.
+
+Features of an environment (204 floats): its boxes (lo, hi) in scene order, zero rows up to 32
+slots, then the start and goal states.  Network input: the features, the eight normals, zeros
+up to 224.  Hidden widths 3 x 256, output 16 (the first six used).
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import inputs, pump
+
+BOX_SLOTS = 32
+FEAT = BOX_SLOTS * 6 + 12
+DIMS = (224, 256, 256, 256, 16)
+MAX_TARGETS = 16
+
+
+def env_features(boxes, start, goal) -> np.ndarray:
+    bx = np.asarray(boxes, np.float32).reshape(-1, 6)
+    if bx.shape[0] > BOX_SLOTS:
+        raise ValueError(f"at most {BOX_SLOTS} boxes")
+    f = np.zeros(FEAT, np.float32)
+    f[:bx.size] = bx.ravel()
+    f[BOX_SLOTS * 6:BOX_SLOTS * 6 + 6] = start
+    f[BOX_SLOTS * 6 + 6:] = goal
+    return f
+
+
+def workload_features(wl: inputs.Workload) -> np.ndarray:
+    return env_features(wl.boxes, wl.states[wl.start_idx], wl.states[1])
+
+
+def plan_params(wl: inputs.Workload) -> pump.PlanParams:
+    return pump.default_plan_params(alpha=wl.alpha, eta=wl.eta, lam=wl.lam, n_mc=wl.n_mc, mc_substeps=wl.mc_substeps,
+                                    mc_seed=wl.mc_seed)
+
+
+def run_queries(wls: Sequence[inputs.Workload], slots: int = 8, device_bytes: int = 64 << 30) -> List[Dict]:
+    """Plan every workload through the request server (continuous batching over `slots`)."""
+    srv = pump.Server(slots, device_bytes)
+    try:
+        tickets = [srv.submit(w.states, w.goal_idx, w.boxes, w.xi, w.radius, w.n_particles, w.n_waypoints, w.sigma,
+                              plan_params(w)) for w in wls]
+        return [srv.wait(t) for t in tickets]
+    finally:
+        srv.close()
+
+
+def certified(res: Dict) -> bool:
+    return res["rc"] == pump.OK and res["status"] == pump.OK and len(res["path"]) >= 2
+
+
+@dataclasses.dataclass
+class Dataset:
+    seeds: np.ndarray      # (n,) environment seeds
+    feat: np.ndarray       # (n, 204) float32
+    targets: np.ndarray    # (n, MAX_TARGETS, 6) float32
+    n_targets: np.ndarray  # (n,) int32
+    stats: Dict
+
+
+def collect(seeds: Sequence[int], n_samples: int = 4000, slots: int = 8, chunk: int = 512) -> Dataset:
+    """Certified plain-PUMP plans on the environments `seeds`; environments without a certified
+    plan, or whose plan has no intermediate state, are left out."""
+    t0 = time.perf_counter()
+    keep_seed, feats, tgs, nts = [], [], [], []
+    solved = 0
+    for c0 in range(0, len(seeds), chunk):
+        wls = [inputs.proposal_workload(int(s), n_samples) for s in seeds[c0:c0 + chunk]]
+        for w, r in zip(wls, run_queries(wls, slots)):
+            if not certified(r):
+                continue
+            solved += 1
+            mid = w.states[r["path"][1:-1]][:MAX_TARGETS]
+            if len(mid) == 0:
+                continue
+            t = np.zeros((MAX_TARGETS, 6), np.float32)
+            t[:len(mid)] = mid
+            keep_seed.append(w.seed)
+            feats.append(workload_features(w))
+            tgs.append(t)
+            nts.append(len(mid))
+    n = len(keep_seed)
+    return Dataset(seeds=np.asarray(keep_seed, np.int64), feat=np.asarray(feats, np.float32).reshape(n, FEAT),
+                   targets=np.asarray(tgs, np.float32).reshape(n, MAX_TARGETS, 6),
+                   n_targets=np.asarray(nts, np.int32),
+                   stats={"environments": len(seeds), "certified": solved, "kept": n,
+                          "mean_targets": float(np.mean(nts)) if nts else 0.0,
+                          "seconds": time.perf_counter() - t0})
+
+
+WTA, PATH_INDEXED = 0, 1
+
+
+def make_model(seed: int = 0, loss: int = PATH_INDEXED) -> pump.MLP:
+    """The proposal network; `loss` WTA (winner takes all over the path's states) or
+    PATH_INDEXED (the first latent picks the fraction along the path)."""
+    m = pump.MLP(DIMS, seed)
+    m.set_loss(loss, FEAT)
+    return m
+
+
+def train(model: pump.MLP, data: Dataset, steps: int, batch: int = 2048, lr: float = 1e-3, seed: int = 0,
+          vmax: float = inputs.VEL_MAX) -> Dict:
+    model.set_data(data.feat, data.targets, data.n_targets)
+    t0 = time.perf_counter()
+    trace = model.train(batch, steps, lr, vmax, seed)
+    return {"steps": int(steps), "batch": int(batch), "lr": float(lr), "seconds": time.perf_counter() - t0,
+            "loss_first": float(np.mean(trace[:max(1, min(50, len(trace)))])) if len(trace) else None,
+            "loss_last": float(np.mean(trace[-max(1, min(50, len(trace))):])) if len(trace) else None,
+            "trace": trace}
+
+
+def mixed_workload(model: pump.MLP, wl: inputs.Workload, n_learned: int, seed: Optional[int] = None,
+                   vmax: float = inputs.VEL_MAX) -> inputs.Workload:
+    """The query with its last n_learned samples replaced by proposals for its environment."""
+    prop = model.propose(workload_features(wl), n_learned, wl.seed if seed is None else seed, vmax)
+    uni = wl.states[2:wl.states.shape[0] - n_learned]
+    return inputs.with_samples(wl, np.concatenate([uni, prop]))
+
+
+def evaluate(model: pump.MLP, seeds: Sequence[int], n_samples: int = 4000, n_learned: int = 2000,
+             slots: int = 8) -> Dict:
+    """Paired comparison on held-out environments: uniform (n_samples) against uniform
+    (n_samples - n_learned, the same ones) + n_learned proposals."""
+    base = [inputs.proposal_workload(int(s), n_samples) for s in seeds]
+    t0 = time.perf_counter()
+    mixed = [mixed_workload(model, w, n_learned) for w in base]
+    t_prop = time.perf_counter() - t0
+    ru = run_queries(base, slots)
+    rm = run_queries(mixed, slots)
+    ok_u = np.array([certified(r) for r in ru])
+    ok_m = np.array([certified(r) for r in rm])
+    cu = np.array([r["cost"] for r in ru], np.float64)
+    cm = np.array([r["cost"] for r in rm], np.float64)
+    both = ok_u & ok_m
+    ratio = cm[both] / cu[both]
+    return {"environments": len(seeds), "samples": n_samples, "learned": n_learned,
+            "success_uniform": float(ok_u.mean()), "success_mixed": float(ok_m.mean()),
+            "solved_only_uniform": int((ok_u & ~ok_m).sum()), "solved_only_mixed": int((ok_m & ~ok_u).sum()),
+            "paired": int(both.sum()),
+            "mean_cost_uniform": float(cu[both].mean()) if both.any() else None,
+            "mean_cost_mixed": float(cm[both].mean()) if both.any() else None,
+            "median_cost_ratio": float(np.median(ratio)) if both.any() else None,
+            "mixed_cheaper": int((ratio < 1).sum()), "mixed_dearer": int((ratio > 1).sum()),
+            "mean_candidates_uniform": float(np.mean([r["n_candidates"] for r in ru])),
+            "mean_candidates_mixed": float(np.mean([r["n_candidates"] for r in rm])),
+            "propose_ms_per_query": 1e3 * t_prop / max(len(seeds), 1)}

@@ -113,6 +113,21 @@ def load(build_if_missing: bool = False):
     L.pump_server_stats.argtypes = [P, P]
     L.pump_server_destroy.argtypes = [P]
     L.pump_server_destroy.restype = None
+    L.pump_mlp_create.argtypes = [i32, P, C.c_uint64, C.POINTER(P)]
+    L.pump_mlp_param_count.argtypes = [P]
+    L.pump_mlp_param_count.restype = i64
+    L.pump_mlp_set_params.argtypes = [P, P, i64]
+    L.pump_mlp_get_params.argtypes = [P, P, i64, C.POINTER(i64)]
+    L.pump_mlp_forward.argtypes = [P, P, i32, P, P]
+    L.pump_mlp_gradients.argtypes = [P, P, i32, P, P, i64, P]
+    L.pump_mlp_train_step.argtypes = [P, P, i32, P, P, i32, f32, f32, C.POINTER(f32), P]
+    L.pump_mlp_set_data.argtypes = [P, P, i32, i32, P, P, i32]
+    L.pump_mlp_set_loss.argtypes = [P, i32, i32]
+    L.pump_mlp_train.argtypes = [P, i32, i32, f32, f32, C.c_uint64, P, P]
+    L.pump_mlp_assemble.argtypes = [P, i32, i64, C.c_uint64, P, P]
+    L.pump_mlp_propose.argtypes = [P, P, i32, i32, C.c_uint64, f32, P, P]
+    L.pump_mlp_destroy.argtypes = [P]
+    L.pump_mlp_destroy.restype = None
     L.pump_kernel_launches.argtypes = []
     L.pump_kernel_launches.restype = C.c_uint64
     L.pump_status_str.argtypes = [C.c_int]
@@ -191,6 +206,102 @@ class Server:
     def close(self):
         if self._h:
             load().pump_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The learned sampling proposal's network (pump_mlp_*): BF16 tensor-core products, FP32
+    master weights, Adam, and a device-side training loop replayed as a CUDA graph."""
+
+    def __init__(self, dims, seed: int = 0):
+        self.dims = [int(d) for d in dims]
+        d = np.asarray(self.dims, np.int32)
+        h = C.c_void_p()
+        rc = load().pump_mlp_create(len(self.dims) - 1, d.ctypes.data, int(seed), C.byref(h))
+        if rc:
+            raise PumpError(rc, "pump_mlp_create")
+        self._h = h
+        self.n_params = int(load().pump_mlp_param_count(h))
+
+    def _check(self, rc, what):
+        if rc:
+            raise PumpError(rc, what)
+
+    def set_params(self, params) -> None:
+        p = np.ascontiguousarray(params, np.float32)
+        self._check(load().pump_mlp_set_params(self._h, p.ctypes.data, p.size), "pump_mlp_set_params")
+
+    def get_params(self):
+        p = np.zeros(self.n_params, np.float32)
+        steps = C.c_int64()
+        self._check(load().pump_mlp_get_params(self._h, p.ctypes.data, p.size, C.byref(steps)), "pump_mlp_get_params")
+        return p, int(steps.value)
+
+    def forward(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, np.float32)
+        y = np.zeros((x.shape[0], self.dims[-1]), np.float32)
+        self._check(load().pump_mlp_forward(self._h, x.ctypes.data, x.shape[0], y.ctypes.data, current_stream()),
+                    "pump_mlp_forward")
+        return y
+
+    def gradients(self, x, dy) -> np.ndarray:
+        x = np.ascontiguousarray(x, np.float32)
+        dy = np.ascontiguousarray(dy, np.float32)
+        g = np.zeros(self.n_params, np.float32)
+        self._check(load().pump_mlp_gradients(self._h, x.ctypes.data, x.shape[0], dy.ctypes.data, g.ctypes.data,
+                                              g.size, current_stream()), "pump_mlp_gradients")
+        return g
+
+    def train_step(self, x, targets, n_targets, lr: float, vmax: float) -> float:
+        x = np.ascontiguousarray(x, np.float32)
+        t = np.ascontiguousarray(targets, np.float32)
+        n = np.ascontiguousarray(n_targets, np.int32)
+        loss = C.c_float()
+        self._check(load().pump_mlp_train_step(self._h, x.ctypes.data, x.shape[0], t.ctypes.data, n.ctypes.data,
+                                               t.shape[1], float(lr), float(vmax), C.byref(loss), current_stream()),
+                    "pump_mlp_train_step")
+        return float(loss.value)
+
+    def set_loss(self, kind: int, latent_col: int = 0) -> None:
+        """0: winner takes all over the targets; 1: path-indexed by Phi(x[latent_col])."""
+        self._check(load().pump_mlp_set_loss(self._h, int(kind), int(latent_col)), "pump_mlp_set_loss")
+
+    def set_data(self, feat, targets, n_targets) -> None:
+        f = np.ascontiguousarray(feat, np.float32)
+        t = np.ascontiguousarray(targets, np.float32)
+        n = np.ascontiguousarray(n_targets, np.int32)
+        self._check(load().pump_mlp_set_data(self._h, f.ctypes.data, f.shape[1], f.shape[0], t.ctypes.data,
+                                             n.ctypes.data, t.shape[1]), "pump_mlp_set_data")
+
+    def train(self, batch: int, steps: int, lr: float, vmax: float, seed: int) -> np.ndarray:
+        tr = np.zeros(max(int(steps), 1), np.float32)
+        self._check(load().pump_mlp_train(self._h, int(batch), int(steps), float(lr), float(vmax), int(seed),
+                                          tr.ctypes.data, current_stream()), "pump_mlp_train")
+        return tr[:int(steps)]
+
+    def assemble(self, batch: int, t: int, seed: int):
+        x = np.zeros((batch, self.dims[0]), np.float32)
+        env = np.zeros(batch, np.int32)
+        self._check(load().pump_mlp_assemble(self._h, int(batch), int(t), int(seed), x.ctypes.data, env.ctypes.data),
+                    "pump_mlp_assemble")
+        return x, env
+
+    def propose(self, feat, count: int, seed: int, vmax: float) -> np.ndarray:
+        f = np.ascontiguousarray(feat, np.float32).ravel()
+        out = np.zeros((int(count), 6), np.float32)
+        self._check(load().pump_mlp_propose(self._h, f.ctypes.data, f.size, int(count), int(seed), float(vmax),
+                                            out.ctypes.data, current_stream()), "pump_mlp_propose")
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().pump_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):

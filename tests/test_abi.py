@@ -50,3 +50,17 @@ def test_invalid_arguments_rejected_before_any_device_work():
     n = ctypes.c_size_t()
     assert lib.pump_export(None, 0, None, 0, ctypes.byref(n)) == pump.ERR_INVALID_ARG
     lib.pump_graph_destroy(None)
+
+
+def test_mlp_invalid_arguments_rejected_on_the_host():
+    lib = pump.load()
+    out = ctypes.c_void_p()
+    dims = (ctypes.c_int32 * 3)(224, 250, 16)   # a width that is not a multiple of 16
+    assert lib.pump_mlp_create(2, dims, 0, ctypes.byref(out)) == pump.ERR_INVALID_ARG
+    assert lib.pump_mlp_create(0, dims, 0, ctypes.byref(out)) == pump.ERR_INVALID_ARG
+    assert lib.pump_mlp_create(2, None, 0, ctypes.byref(out)) == pump.ERR_INVALID_ARG
+    assert lib.pump_mlp_param_count(None) == -1
+    assert lib.pump_mlp_forward(None, None, 0, None, None) == pump.ERR_INVALID_ARG
+    assert lib.pump_mlp_train(None, 16, 1, 1e-3, 0.1, 0, None, None) == pump.ERR_INVALID_ARG
+    assert lib.pump_mlp_propose(None, None, 0, 1, 0, 0.1, None, None) == pump.ERR_INVALID_ARG
+    lib.pump_mlp_destroy(None)

@@ -227,3 +227,62 @@ def test_training_lowers_the_loss():
     st["v"] = np.zeros_like(st["w"])
     losses = [mlp.train_step(st, dims, feat, tg, np.full(n_env, T), 32, 1, 3e-3, 0.1) for _ in range(150)]
     assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:10])
+
+
+# ---------------------------------------------------------------------------
+def test_path_point_walks_the_polyline():
+    tg = np.array([[0.0] * 6, [1.0] * 6, [1.0, 3.0, 1.0, 1.0, 1.0, 1.0]])
+    assert np.array_equal(mlp.path_point(tg, 3, 0.0), tg[0])
+    assert np.allclose(mlp.path_point(tg, 3, 0.25), 0.5 * tg[1])
+    assert np.allclose(mlp.path_point(tg, 3, 0.5), tg[1])
+    assert np.allclose(mlp.path_point(tg, 3, 0.75), [1, 2, 1, 1, 1, 1])
+    assert np.allclose(mlp.path_point(tg, 3, 1.0), tg[2])
+    assert np.array_equal(mlp.path_point(tg, 1, 0.7), tg[0])
+
+
+def test_normal_cdf_matches_scipy():
+    from scipy import stats
+    z = np.linspace(-6, 6, 101)
+    assert np.allclose(mlp.normal_cdf(z), stats.norm.cdf(z), rtol=1e-12, atol=1e-15)
+
+
+def test_path_indexed_loss_and_gradient():
+    vmax = 0.1
+    g = _rng(12)
+    B, T = 16, 5
+    o = g.standard_normal((B, 16)) * 0.5
+    tg = np.concatenate([g.uniform(0, 1, (B, T, 3)), g.uniform(-vmax, vmax, (B, T, 3))], axis=2)
+    n_t = g.integers(1, T + 1, size=B)
+    n_t[2] = 0
+    z0 = g.standard_normal(B)
+    loss, grad = mlp.wta_loss(o, tg, n_t, vmax, kind=1, z0=z0)
+    s = mlp.squash(o, vmax)
+    from scipy import stats
+    for r in range(B):
+        if n_t[r] == 0:
+            assert loss[r] == 0
+            continue
+        u = stats.norm.cdf(z0[r])
+        y = mlp.path_point(tg[r], n_t[r], u)
+        assert loss[r] == pytest.approx(((s[r] - y) ** 2).sum(), rel=1e-12)
+    num = _fd(lambda v: float(mlp.wta_loss(v.reshape(B, 16), tg, n_t, vmax, 1, z0)[0].mean()), o.ravel())
+    assert np.allclose(grad.ravel(), num, rtol=1e-5, atol=1e-9)
+
+
+def test_path_indexed_training_spreads_outputs_along_the_path():
+    # one environment whose targets are two far-apart states: winner-take-all may settle on one,
+    # the path-indexed loss has to produce both ends as the first latent varies
+    dims = [32, 64, 64, 16]
+    feat = np.zeros((1, 24))
+    tg = np.array([[[0.2, 0.2, 0.2, 0, 0, 0], [0.8, 0.8, 0.8, 0, 0, 0]]])
+    st = {"w": _random_net(dims, 13), "t": 0}
+    st["m"] = np.zeros_like(st["w"])
+    st["v"] = np.zeros_like(st["w"])
+    for _ in range(400):
+        mlp.train_step(st, dims, feat, tg, [2], 64, 5, 3e-3, 0.1, kind=1)
+    z = np.array([-2.5, 0.0, 2.5])
+    x = np.zeros((3, 32))
+    x[:, 24] = z
+    o, _ = mlp.forward(st["w"], dims, x)
+    pos = mlp.squash(o, 0.1)[:, 0]
+    assert pos[0] < 0.3 and abs(pos[1] - 0.5) < 0.1 and pos[2] > 0.7, pos
