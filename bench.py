@@ -216,6 +216,11 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=150,
                     help="requests of the served leg (Poisson arrivals, continuous batching); 0 skips it")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="arrival rate of the served leg (requests/s)")
+    ap.add_argument("--learned-envs", type=int, default=10000,
+                    help="training environments of the learned-proposal leg (plain PUMP solutions, then training "
+                         "and a paired held-out evaluation); 0 skips it")
+    ap.add_argument("--learned-eval", type=int, default=200, help="held-out environments of the learned leg")
+    ap.add_argument("--learned-steps", type=int, default=5000, help="training steps of the learned leg")
     ap.add_argument("--batch-queries", type=int, default=256,
                     help="queries of the batched leg (uneven sizes, one persistent Explore launch); 0 skips it")
     args = ap.parse_args()
@@ -354,6 +359,8 @@ def main():
         line["served"] = served_measure(pump, args, rank, ws)
     if args.hsmc_seeds > 0:
         line["hsmc"] = hsmc_measure(pump, args, dev, flush)
+    if args.learned_envs > 0 and rank == 0:
+        line["learned"] = learned_measure(pump, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import cpu
         cpu.build()
@@ -382,6 +389,57 @@ def measured_traffic(kernel):
     if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
         return None
     return float(rec["dram_bytes_per_launch"])
+
+
+def mlp_flops_per_step(dims, B):
+    """Tensor-core flops of one training step: forward products, the weight-gradient products of
+    every layer and the input-gradient products of every layer but the first (2 flops a MAC)."""
+    macs = sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+    first = dims[0] * dims[1]
+    return 2.0 * B * (3 * macs - first)
+
+
+def learned_measure(pump, args):
+    """The learned sampling proposal: plain PUMP on args.learned_envs seeded training environments
+    (indoor scenes, U{10..32} boxes, 4000 uniform samples, N = 128, W = 10, CP 1 %) through the
+    request server; the BF16 network trained on the certified plans' states with the device loop
+    (batch 2048, Adam 1e-3, args.learned_steps steps) under both losses; then the paired held-out
+    evaluation (seeds 1,000,000 on): 4000 uniform samples against the same first 2000 + 2000
+    proposals.  Also the training step's time and tensor throughput."""
+    from paper_1607_06886_gb300 import proposal
+    peak = float(load_peaks()["bf16_tflops"])
+    data = proposal.collect(list(range(args.learned_envs)))
+    held = list(range(1_000_000, 1_000_000 + args.learned_eval))
+    out = {"workload": f"proposal_indoor_4k_{args.learned_envs}env", "collect": data.stats}
+    for name, kind in (("path_indexed", proposal.PATH_INDEXED), ("wta", proposal.WTA)):
+        m = proposal.make_model(0, kind)
+        tr = proposal.train(m, data, args.learned_steps)
+        tr.pop("trace")
+        out[f"train_{name}"] = tr
+        ev = proposal.evaluate(m, held, raw=True)
+        ru = ev.pop("raw_uniform")
+        ev.pop("raw_mixed")
+        sig = [(r["rc"], r["cost"], r["n_candidates"]) for r in ru]
+        if "uniform_results" in out and out["uniform_results"] != sig:
+            bad = [i for i, (a, b) in enumerate(zip(out["uniform_results"], sig)) if a != b]
+            ev["uniform_arm_differs"] = {"queries": bad[:10], "first": [out["uniform_results"][bad[0]], sig[bad[0]]]}
+        out["uniform_results"] = sig
+        out[f"eval_{name}"] = ev
+        if kind == proposal.PATH_INDEXED:
+            perf = {}
+            for B, steps in ((2048, 500), (32768, 50)):
+                m.train(B, 3, 1e-3, 0.1, 1)
+                t0 = time.perf_counter()
+                m.train(B, steps, 1e-3, 0.1, 1)
+                ms = 1e3 * (time.perf_counter() - t0) / steps
+                tf = mlp_flops_per_step(proposal.DIMS, B) / (ms * 1e-3) / 1e12
+                perf[f"b{B}"] = {"ms_per_step": ms, "tflops": tf, "frac_of_measured_peak": tf / peak}
+            out["train_step"] = dict(perf, peak_tflops=peak, dims=list(proposal.DIMS),
+                                     note="one training step = draws + forward + loss + backward + Adam, replayed as "
+                                          "a CUDA graph; host-timed over the replays (one sync)")
+        m.close()
+    out.pop("uniform_results")
+    return out
 
 
 def hsmc_measure(pump, args, dev, flush):

@@ -137,8 +137,18 @@ def mixed_workload(model: pump.MLP, wl: inputs.Workload, n_learned: int, seed: O
     return inputs.with_samples(wl, np.concatenate([uni, prop]))
 
 
+def _errors(rs) -> Dict[str, int]:
+    """Queries that ended in an error (neither a certified plan nor INFEASIBLE), by status."""
+    out: Dict[str, int] = {}
+    for r in rs:
+        if r["rc"] not in (pump.OK, pump.ERR_INFEASIBLE):
+            k = pump.status_str(r["rc"])
+            out[k] = out.get(k, 0) + 1
+    return out
+
+
 def evaluate(model: pump.MLP, seeds: Sequence[int], n_samples: int = 4000, n_learned: int = 2000,
-             slots: int = 8) -> Dict:
+             slots: int = 8, raw: bool = False) -> Dict:
     """Paired comparison on held-out environments: uniform (n_samples) against uniform
     (n_samples - n_learned, the same ones) + n_learned proposals."""
     base = [inputs.proposal_workload(int(s), n_samples) for s in seeds]
@@ -163,4 +173,35 @@ def evaluate(model: pump.MLP, seeds: Sequence[int], n_samples: int = 4000, n_lea
             "mixed_cheaper": int((ratio < 1).sum()), "mixed_dearer": int((ratio > 1).sum()),
             "mean_candidates_uniform": float(np.mean([r["n_candidates"] for r in ru])),
             "mean_candidates_mixed": float(np.mean([r["n_candidates"] for r in rm])),
-            "propose_ms_per_query": 1e3 * t_prop / max(len(seeds), 1)}
+            "propose_ms_per_query": 1e3 * t_prop / max(len(seeds), 1),
+            "errors_uniform": _errors(ru), "errors_mixed": _errors(rm),
+            **({"raw_uniform": ru, "raw_mixed": rm} if raw else {})}
+
+
+def _main(argv=None) -> int:
+    """Training loop alone on a seeded synthetic training set (no planning), for timing and
+    profiling the network kernels: python -m paper_1607_06886_gb300.proposal --steps 20."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=2048)
+    ap.add_argument("--envs", type=int, default=1000)
+    args = ap.parse_args(argv)
+    g = np.random.default_rng(0)
+    feat = np.zeros((args.envs, FEAT), np.float32)
+    feat[:, :BOX_SLOTS * 6] = g.uniform(0, 1, (args.envs, BOX_SLOTS * 6))
+    tg = np.concatenate([g.uniform(0, 1, (args.envs, MAX_TARGETS, 3)),
+                         g.uniform(-inputs.VEL_MAX, inputs.VEL_MAX, (args.envs, MAX_TARGETS, 3))], axis=2)
+    nt = g.integers(1, MAX_TARGETS + 1, size=args.envs)
+    data = Dataset(np.arange(args.envs), feat, tg.astype(np.float32), nt.astype(np.int32), {})
+    m = make_model(0)
+    tr = train(m, data, args.steps, args.batch)
+    tr.pop("trace")
+    print(json.dumps(tr))
+    m.close()
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(_main())
