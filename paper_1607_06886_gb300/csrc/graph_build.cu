@@ -5,6 +5,8 @@
 // contraction so double-precision expressions round as written.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "pump_internal.cuh"
 
 namespace pump {
@@ -48,30 +50,56 @@ __device__ inline bool prefilter(const float* sv, const float* su, float r) {
   return true;
 }
 
-// Pass 1 counts and pass 2 lists the pairs (v, u), v != u, both valid, that
-// pass the prefilter.  One warp covers 32 targets u of one source v.
+// The pairs (v, u), v != u, both valid, that pass the prefilter, row by row: a warp per source v
+// takes the targets u 32 at a time.  Pass 1 counts each row's pairs, an exclusive scan gives the
+// row offsets, and pass 2 writes each row's pairs in ascending u from its offset: no atomics, and
+// the list order is fixed.
 template <bool kWrite>
 __global__ void k_prefilter(const float* __restrict__ states, const uint8_t* __restrict__ valid, int n, float r,
-                            unsigned long long* count, int2* list) {
-  const int nw = (n + 31) / 32;
-  const long long total = (long long)n * nw;
+                            int32_t* __restrict__ cnt, const long long* __restrict__ off, int2* __restrict__ list) {
   const int lane = threadIdx.x & 31;
-  long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (; wid < total; wid += nwarps) {
-    int v = (int)(wid / nw);
-    int u = (int)(wid % nw) * 32 + lane;
-    bool ok = false;
-    if (u < n && u != v && valid[v] && valid[u]) ok = prefilter(states + 6 * v, states + 6 * u, r);
-    unsigned b = __ballot_sync(0xffffffffu, ok);
-    if (b == 0) continue;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(b));
-    if (kWrite) {
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (ok) list[base + __popc(b & ((1u << lane) - 1u))] = make_int2(v, u);
+  const int warps = (int)(((long long)gridDim.x * blockDim.x) >> 5);
+  for (int v = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); v < n; v += warps) {
+    int c = 0;
+    if (valid[v]) {
+      float sv[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) sv[j] = states[6 * v + j];
+      long long base = kWrite ? off[v] : 0;
+      for (int u0 = 0; u0 < n; u0 += 32) {
+        const int u = u0 + lane;
+        const bool ok = u < n && u != v && valid[u] && prefilter(sv, states + 6 * u, r);
+        const unsigned b = __ballot_sync(0xffffffffu, ok);
+        if (kWrite && ok) list[base + c + __popc(b & ((1u << lane) - 1u))] = make_int2(v, u);
+        c += __popc(b);
+      }
     }
+    if (!kWrite && lane == 0) cnt[v] = c;
   }
+}
+
+// Exclusive scan of n int32 counts into 64-bit offsets out[0..n] (out[n] = total); one block.
+__global__ void k_scan_ll(const int32_t* __restrict__ in, int n, long long* __restrict__ out) {
+  __shared__ long long part[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int per = (n + T - 1) / T;
+  const int b0 = min(n, t * per), b1 = min(n, b0 + per);
+  long long sum = 0;
+  for (int i = b0; i < b1; ++i) sum += in[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int d = 1; d < T; d <<= 1) {
+    const long long add = t >= d ? part[t - d] : 0;
+    __syncthreads();
+    part[t] += add;
+    __syncthreads();
+  }
+  long long run = part[t] - sum;  // exclusive prefix of this thread's chunk
+  for (int i = b0; i < b1; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  if (t == T - 1) out[n] = part[T - 1];
 }
 
 // Float estimate of Cost(v,u), used only to skip pairs far above the radius.  Same monotone
@@ -259,7 +287,42 @@ __device__ inline bool connection_hits_fast(const float* fv, const float* fu, co
   return false;
 }
 
-__global__ void k_steer_pairs(const float* __restrict__ states, const int2* __restrict__ list, long long n_list,
+// Near in two passes.  Pass 1 runs the float estimate over every listed pair with whole warps and
+// appends the pairs it cannot reject (about one in ten) to a survivor list, warp by warp; pass 2
+// runs the double-precision refinement and the collision test over the survivors only, so the
+// FP64 work (slow on this part) runs with full warps instead of the few lanes of each warp whose
+// pair survived.  Outputs are indexed by the pair and the keep bitmap is an OR, so the survivors'
+// order does not matter.
+__global__ void k_steer_filter(const float* __restrict__ states, const int2* __restrict__ list, long long n_list,
+                               float r, uint32_t* __restrict__ surv, unsigned long long* n_surv) {
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); q0 < n_list; q0 += stride) {
+    const long long q = q0 + lane;
+    bool keep = false;
+    if (q < n_list) {
+      const int2 vu = list[q];
+      float fv[6], fu[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        fv[j] = states[6 * vu.x + j];
+        fu[j] = states[6 * vu.y + j];
+      }
+      float J32;
+      const bool est = steer_estimate(fv, fu, &J32);
+      keep = !(est && J32 > r * 1.001f);
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, keep);
+    if (!b) continue;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(n_surv, (unsigned long long)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) surv[base + __popc(b & ((1u << lane) - 1u))] = (uint32_t)q;
+  }
+}
+
+__global__ void k_steer_pairs(const float* __restrict__ states, const int2* __restrict__ list,
+                              const uint32_t* __restrict__ surv, const unsigned long long* __restrict__ n_surv,
                               int n, float r, int W, const float* __restrict__ boxes_g, int nb, uint32_t* keep,
                               double* __restrict__ res_tau, float* __restrict__ res_cost) {
   extern __shared__ double frac[];
@@ -272,8 +335,9 @@ __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __re
   }
   __syncthreads();
   const int nw = (n + 31) / 32;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n_list;
-       q += (long long)gridDim.x * blockDim.x) {
+  const long long ns = (long long)*n_surv;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < ns; k += (long long)gridDim.x * blockDim.x) {
+    const long long q = surv[k];
     int2 vu = list[q];
     float fv[6], fu[6];
 #pragma unroll
@@ -284,7 +348,6 @@ __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __re
     float J32, tmin[2], Jmin[2];
     int nm = 0;
     const bool est = steer_estimate(fv, fu, &J32, tmin, &nm, Jmin);
-    if (est && J32 > r * 1.001f) continue;
     double xv[6], xu[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -453,22 +516,26 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   const int nw = (n + 31) / 32;
   const int sms = num_sms();
   // node flags (validity) and goal flags were filled by the caller's kernels
-  // prefilter: count, allocate, list
+  // prefilter: count per row, scan, allocate, list
   unsigned long long* d_count = (unsigned long long*)dev_alloc(sizeof(unsigned long long) * 2, s);
-  if (!d_count) return PUMP_ERR_OOM;
+  int32_t* rcnt = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)n, s);
+  long long* roff = (long long*)dev_alloc(sizeof(long long) * (size_t)(n + 1), s);
+  if (!d_count || !rcnt || !roff) return PUMP_ERR_OOM;
   PUMP_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * 2, s));
-  int grid = sms * 8;
-  k_prefilter<false><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, d_count, nullptr);
+  const int grid = (int)std::min<long long>(((long long)n * 32 + kBlock - 1) / kBlock, (long long)sms * 16);
+  k_prefilter<false><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, rcnt, nullptr, nullptr);
   note_launch();
-  unsigned long long n_list = 0;
-  PUMP_CUDA_TRY(cudaMemcpyAsync(&n_list, d_count, sizeof(n_list), cudaMemcpyDeviceToHost, s));
+  k_scan_ll<<<1, 1024, 0, s>>>(rcnt, n, roff);
+  note_launch();
+  long long n_list_ll = 0;
+  PUMP_CUDA_TRY(cudaMemcpyAsync(&n_list_ll, roff + n, sizeof(n_list_ll), cudaMemcpyDeviceToHost, s));
   PUMP_CUDA_TRY(cudaStreamSynchronize(s));
+  const unsigned long long n_list = (unsigned long long)n_list_ll;
   int2* list = nullptr;
   if (n_list) {
     list = (int2*)dev_alloc(sizeof(int2) * n_list, s);
     if (!list) { dev_free(d_count, s); return PUMP_ERR_OOM; }
-    PUMP_CUDA_TRY(cudaMemsetAsync(d_count + 1, 0, sizeof(unsigned long long), s));
-    k_prefilter<true><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, d_count + 1, list);
+    k_prefilter<true><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, nullptr, roff, list);
     note_launch();
   }
   uint32_t* keep = (uint32_t*)dev_alloc(sizeof(uint32_t) * (size_t)n * nw, s);
@@ -480,9 +547,16 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   PUMP_CUDA_TRY(cudaMemsetAsync(keep, 0, sizeof(uint32_t) * (size_t)n * nw, s));
   long long list_blocks = ((long long)n_list + kBlock - 1) / kBlock;
   const int glist = (int)(list_blocks < (long long)sms * 16 ? (list_blocks > 0 ? list_blocks : 1) : (long long)sms * 16);
+  uint32_t* surv = nullptr;
   if (n_list) {
-    k_steer_pairs<<<glist, kBlock, (sizeof(double) + sizeof(float)) * 4 * g->W + sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1), s>>>(
-        g->states, list, (long long)n_list, n, g->radius, g->W, g->boxes, g->n_boxes, keep, res_tau, res_cost);
+    if (n_list > 0xFFFFFFFFull) return PUMP_ERR_CAPACITY;
+    surv = (uint32_t*)dev_alloc(sizeof(uint32_t) * n_list, s);
+    if (!surv) return PUMP_ERR_OOM;
+    k_steer_filter<<<glist, kBlock, 0, s>>>(g->states, list, (long long)n_list, g->radius, surv, d_count);
+    note_launch();
+    const size_t smem = (sizeof(double) + sizeof(float)) * 4 * g->W + sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1);
+    k_steer_pairs<<<sms * 4, kBlock, smem, s>>>(g->states, list, surv, d_count, n, g->radius, g->W, g->boxes,
+                                                g->n_boxes, keep, res_tau, res_cost);
     note_launch();
   }
   k_row_counts<<<(n + 7) / 8, kBlock, 0, s>>>(keep, n, deg);
@@ -540,6 +614,9 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   PUMP_CUDA_TRY(cudaStreamSynchronize(s));
   dev_free(d_count, s);
   if (list) dev_free(list, s);
+  if (surv) dev_free(surv, s);
+  dev_free(rcnt, s);
+  dev_free(roff, s);
   dev_free(keep, s);
   dev_free(deg, s);
   dev_free(wpre, s);
