@@ -179,38 +179,6 @@ __device__ inline bool steer_estimate(const float* xv, const float* xu, float* J
   return any;
 }
 
-// Cost(v,u) in double from the float minimisers: Newton from each inside a bracket of +-1e-5
-// (relative) whose end signs are checked in double.  Falls back to the full analysis
-// (steer_dev) when a bracket fails or two minima lie within 1e-4 of each other, so the chosen
-// root is the one the full analysis picks.
-__device__ inline bool steer_refined(const double* xv, const double* xu, const float* tmin, const float* Jmin, int nm,
-                                     double* tau_out, double* J_out) {
-  if (nm < 1 || (nm == 2 && fabsf(Jmin[0] - Jmin[1]) <= 1e-4f * fmaxf(Jmin[0], Jmin[1])))
-    return steer_dev(xv, xu, tau_out, J_out);
-  SteerCoef k{0.0, 0.0, 0.0};
-  for (int j = 0; j < 3; ++j) {
-    const double dp = xu[j] - xv[j], v0 = xv[3 + j], v1 = xu[3 + j];
-    k.a += v0 * v0 + v0 * v1 + v1 * v1;
-    k.b += dp * (v0 + v1);
-    k.c += dp * dp;
-  }
-  double best_t = -1.0, best_J = 0.0;
-  for (int q = 0; q < nm; ++q) {
-    const double t0 = (double)tmin[q];
-    const double lo = t0 * (1.0 - 1e-5), hi = t0 * (1.0 + 1e-5);
-    if (!(st_f(k, lo) < 0.0 && st_f(k, hi) > 0.0)) return steer_dev(xv, xu, tau_out, J_out);
-    const double t = st_root(k, 0, lo, hi, true);
-    const double J = st_J(k, t);
-    if (best_t < 0.0 || J < best_J || (J == best_J && t < best_t)) {
-      best_t = t;
-      best_J = J;
-    }
-  }
-  *tau_out = best_t;
-  *J_out = best_J;
-  return true;
-}
-
 // Collision(v, u): the nominal connection of duration tau (float) sampled at
 // t_m = tau (m / 4W), m = 1..4W, positions (the double cubic at t_m) rounded to float, closed
 // boxes; frac[m-1] = m / (4W) in double.  Evaluated in float with a rounding margin: the
@@ -219,80 +187,15 @@ __device__ inline bool steer_refined(const double* xv, const double* xu, const f
 // every float step by 2^-15 (1 + M), M the largest |p0| + |v0| tau + |c2| tau^2 + |c3| tau^3 of
 // the three axes (the actual error is below 2^-19 (1 + M)).  A sample more than eps outside a box
 // on some axis misses it, one more than eps inside on every axis hits it; only samples within eps
-// of a face are evaluated the definition's way, in double.
-__device__ inline bool connection_hits_fast(const float* fv, const float* fu, const double* xv, const double* xu,
-                                            double td, int W, const float* boxes, int nb, const double* frac,
-                                            const float* fracf) {
-  const float tau = (float)td;  // td holds a float value exactly
-  float p0[3], v0[3], c2[3], c3[3], R[3];
-  float M = 0.f;
-  for (int a = 0; a < 3; ++a) {
-    p0[a] = fv[a];
-    v0[a] = fv[3 + a];
-    const float dp = fu[a] - p0[a] - v0[a] * tau, dv = fu[3 + a] - v0[a];
-    c2[a] = (3.f * dp - dv * tau) / (tau * tau);
-    c3[a] = (dv * tau - 2.f * dp) / (tau * tau * tau);
-    R[a] = fabsf(v0[a]) * tau + fabsf(c2[a]) * tau * tau + fabsf(c3[a]) * tau * tau * tau;
-    M = fmaxf(M, fabsf(p0[a]) + R[a]);
-  }
-  const float eps = (1.f + M) * 3.0517578125e-5f;  // 2^-15 (1 + M)
-  // boxes the connection can reach: p0 +- (R + eps) per axis (the first 64; beyond that all boxes)
-  unsigned long long cand = 0ull;
-  const int nc = nb < 64 ? nb : 64;
-  for (int o = 0; o < nc; ++o) {
-    const float* b = boxes + 6 * o;
-    bool ov = true;
-    for (int a = 0; a < 3; ++a) ov = ov && b[a] <= p0[a] + R[a] + eps && p0[a] - R[a] - eps <= b[3 + a];
-    if (ov) cand |= 1ull << o;
-  }
-  const bool rest = nb > 64;
-  if (!cand && !rest) return false;
-  bool have_exact = false;
-  Cubic c[3];
-  for (int m = 1; m <= 4 * W; ++m) {
-    const float t = tau * fracf[m - 1];
-    float p[3];
-    for (int a = 0; a < 3; ++a) p[a] = fmaf(fmaf(fmaf(c3[a], t, c2[a]), t, v0[a]), t, p0[a]);
-    unsigned long long bits = cand;
-    int o = -1;
-    for (;;) {
-      if (bits) {
-        o = __ffsll((long long)bits) - 1;
-        bits &= bits - 1ull;
-      } else if (rest && o < 64) {
-        o = 64;
-      } else if (rest && o >= 64 && o + 1 < nb) {
-        ++o;
-      } else {
-        break;
-      }
-      const float* b = boxes + 6 * o;
-      bool out = false, in = true;
-      for (int a = 0; a < 3; ++a) {
-        out = out || p[a] < b[a] - eps || p[a] > b[3 + a] + eps;
-        in = in && p[a] >= b[a] + eps && p[a] <= b[3 + a] - eps;
-      }
-      if (out) continue;
-      if (in) return true;
-      if (!have_exact) {
-        c[0] = cubic_dev(xv, xu, td, 0);
-        c[1] = cubic_dev(xv, xu, td, 1);
-        c[2] = cubic_dev(xv, xu, td, 2);
-        have_exact = true;
-      }
-      const double te = td * frac[m - 1];
-      if (in_box_dev((float)cubic_at(c[0], te), (float)cubic_at(c[1], te), (float)cubic_at(c[2], te), b)) return true;
-    }
-  }
-  return false;
-}
-
-// Near in two passes.  Pass 1 runs the float estimate over every listed pair with whole warps and
-// appends the pairs it cannot reject (about one in ten) to a survivor list, warp by warp; pass 2
-// runs the double-precision refinement and the collision test over the survivors only, so the
-// FP64 work (slow on this part) runs with full warps instead of the few lanes of each warp whose
-// pair survived.  Outputs are indexed by the pair and the keep bitmap is an OR, so the survivors'
-// order does not matter.
+// of a face are evaluated the definition's way, in double (k_collide).
+// Near and Collision in passes over shrinking lists, so that each pass runs one uniform piece of
+// work with full warps: k_steer_filter takes the float estimate of every listed pair and keeps the
+// pairs it cannot reject (about one in four); k_steer_pairs refines their cost in double (FP64 is
+// slow on this part, so it must not run on the few lanes of a warp whose pair survived) and
+// passes the rare pairs that need the full analysis to k_steer_slow; k_collide tests the nominal
+// connections of the pairs whose cost is below r in float, a warp per pair, and k_collide_exact
+// settles the few pairs the float test leaves undecided.  Outputs are indexed by the
+// pair and the keep bitmap is an OR, so the order of the lists does not matter.
 __global__ void k_steer_filter(const float* __restrict__ states, const int2* __restrict__ list, long long n_list,
                                float r, uint32_t* __restrict__ surv, unsigned long long* n_surv) {
   const int lane = threadIdx.x & 31;
@@ -321,47 +224,336 @@ __global__ void k_steer_filter(const float* __restrict__ states, const int2* __r
   }
 }
 
+// Root of the increasing piece of f on [lo, hi]: Newton safeguarded by bisection, f evaluated in
+// double, the Newton quotient f / f' taken in float.  The quotient only sets the step; its
+// relative error (~1e-7) leaves the iteration converging to the same double root (each step
+// shrinks the error by that factor on top of the quadratic term), without a double division.
+// f and f' with fused multiply-adds (this unit is compiled without contraction; the root solver
+// only needs f's sign to locate the double root, not the as-written rounding).
+struct SteerFma {
+  double a4, b24, c36, a8;
+};
+__device__ inline double st_f_fma(const SteerFma& k, double t) {
+  return __fma_rn(__fma_rn(__fma_rn(t, t, -k.a4), t, k.b24), t, -k.c36);
+}
+__device__ inline double st_fp_fma(const SteerFma& k, double t) {
+  return __fma_rn(__fma_rn(4.0 * t, t, -k.a8), t, k.b24);
+}
+__device__ inline double st_root_fq(const SteerCoef& c, double lo, double hi) {
+  const SteerFma k{4.0 * c.a, 24.0 * c.b, 36.0 * c.c, 8.0 * c.a};
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < 300; ++it) {
+    const double gx = st_f_fma(k, x);
+    if (gx == 0.0) return x;
+    if (gx < 0.0) lo = x; else hi = x;
+    double xn = x - (double)((float)gx / (float)st_fp_fma(k, x));
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    const double step = fabs(xn - x);
+    x = xn;
+    if (step <= 4.0e-16 * fabs(x) || !(hi - lo > 2.5e-16 * fabs(hi))) break;
+  }
+  return x;
+}
+
+// J(t) as t + |dv|^2 / t + 12 |dp - vbar t|^2 / t^3 (the same function as st_J, written as a sum of
+// non-negative terms, one division).
+__device__ inline double st_J_sum(const double* xv, const double* xu, double t) {
+  const double u = 1.0 / t;
+  double dv2 = 0.0, r2 = 0.0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const double dv = xu[3 + j] - xv[3 + j], vb = 0.5 * (xv[3 + j] + xu[3 + j]);
+    const double d = (xu[j] - xv[j]) - vb * t;
+    dv2 += dv * dv;
+    r2 += d * d;
+  }
+  return t + dv2 * u + 12.0 * r2 * (u * u * u);
+}
+
+// Append q to a list, one atomic per warp (every lane of the warp calls this).
+__device__ inline void warp_append(bool take, uint32_t q, uint32_t* out, unsigned long long* n_out) {
+  const int lane = threadIdx.x & 31;
+  const unsigned b = __ballot_sync(0xffffffffu, take);
+  if (!b) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(n_out, (unsigned long long)__popc(b));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (take) out[base + __popc(b & ((1u << lane) - 1u))] = q;
+}
+
+// Survivors on the common path: the float minimisers bracket the double roots (Newton from each
+// inside +-1e-5 relative, end signs checked in double).  A pair with float(Cost) < r gets its
+// duration and cost written and goes to the collision pass; pairs that need the full analysis (no
+// float estimate, a failed bracket, or two minima within 1e-4 of each other) go to
+// k_steer_slow, so the warps here run one uniform piece of FP64 work.
 __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __restrict__ list,
                               const uint32_t* __restrict__ surv, const unsigned long long* __restrict__ n_surv,
-                              int n, float r, int W, const float* __restrict__ boxes_g, int nb, uint32_t* keep,
-                              double* __restrict__ res_tau, float* __restrict__ res_cost) {
-  extern __shared__ double frac[];
-  float* fracf = reinterpret_cast<float*>(frac + 4 * W);
+                              float r, double* __restrict__ res_tau, float* __restrict__ res_cost,
+                              uint32_t* __restrict__ slow, unsigned long long* n_slow, uint32_t* __restrict__ cand,
+                              unsigned long long* n_cand) {
+  const int lane = threadIdx.x & 31;
+  const long long ns = (long long)*n_surv;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < ns; k0 += stride) {
+    const long long k = k0 + lane;
+    bool to_slow = false, edge = false;
+    uint32_t q = 0;
+    if (k < ns) {
+      q = surv[k];
+      const int2 vu = list[q];
+      float fv[6], fu[6];
+      double xv[6], xu[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        fv[j] = states[6 * vu.x + j];
+        fu[j] = states[6 * vu.y + j];
+        xv[j] = (double)fv[j];
+        xu[j] = (double)fu[j];
+      }
+      float J32, tmin[2], Jmin[2];
+      int nm = 0;
+      const bool est = steer_estimate(fv, fu, &J32, tmin, &nm, Jmin);
+      if (!est || nm < 1 || (nm == 2 && fabsf(Jmin[0] - Jmin[1]) <= 1e-4f * fmaxf(Jmin[0], Jmin[1]))) {
+        to_slow = true;
+      } else {
+        SteerCoef c{0.0, 0.0, 0.0};
+        for (int j = 0; j < 3; ++j) {
+          const double dp = xu[j] - xv[j], v0 = xv[3 + j], v1 = xu[3 + j];
+          c.a += v0 * v0 + v0 * v1 + v1 * v1;
+          c.b += dp * (v0 + v1);
+          c.c += dp * dp;
+        }
+        double best_t = -1.0, best_J = 0.0;
+        for (int m = 0; m < nm; ++m) {
+          const double t0 = (double)tmin[m];
+          const double lo = t0 * (1.0 - 1e-5), hi = t0 * (1.0 + 1e-5);
+          if (!(st_f(c, lo) < 0.0 && st_f(c, hi) > 0.0)) {
+            to_slow = true;
+            break;
+          }
+          const double t = st_root_fq(c, lo, hi);
+          const double Jt = st_J_sum(xv, xu, t);
+          if (best_t < 0.0 || Jt < best_J || (Jt == best_J && t < best_t)) {
+            best_t = t;
+            best_J = Jt;
+          }
+        }
+        if (!to_slow && __double2float_rn(best_J) < r) {
+          res_tau[q] = best_t;
+          res_cost[q] = __double2float_rn(best_J);
+          edge = true;
+        }
+      }
+    }
+    warp_append(to_slow, q, slow, n_slow);
+    warp_append(edge, q, cand, n_cand);
+  }
+}
+
+// Survivors that need the full analysis of Cost(v,u) (steer_dev).
+__global__ void k_steer_slow(const float* __restrict__ states, const int2* __restrict__ list,
+                             const uint32_t* __restrict__ slow, const unsigned long long* __restrict__ n_slow, float r,
+                             double* __restrict__ res_tau, float* __restrict__ res_cost, uint32_t* __restrict__ cand,
+                             unsigned long long* n_cand) {
+  const int lane = threadIdx.x & 31;
+  const long long ns = (long long)*n_slow;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < ns; k0 += stride) {
+    const long long k = k0 + lane;
+    bool edge = false;
+    uint32_t q = 0;
+    if (k < ns) {
+      q = slow[k];
+      const int2 vu = list[q];
+      double xv[6], xu[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        xv[j] = (double)states[6 * vu.x + j];
+        xu[j] = (double)states[6 * vu.y + j];
+      }
+      double tau, J;
+      if (steer_dev(xv, xu, &tau, &J) && __double2float_rn(J) < r) {
+        res_tau[q] = tau;
+        res_cost[q] = __double2float_rn(J);
+        edge = true;
+      }
+    }
+    warp_append(edge, q, cand, n_cand);
+  }
+}
+
+// Nominal-connection coefficients in float for Collision: the cubic per axis, the reach R of each
+// axis (|v0| tau + |c2| tau^2 + |c3| tau^3) and the margin eps = 2^-15 (1 + M).
+struct FloatConn {
+  float p0[3], v0[3], c2[3], c3[3], R[3], eps;
+};
+__device__ inline FloatConn float_conn(const float* fv, const float* fu, float tau) {
+  FloatConn c;
+  float M = 0.f;
+  for (int a = 0; a < 3; ++a) {
+    c.p0[a] = fv[a];
+    c.v0[a] = fv[3 + a];
+    const float dp = fu[a] - c.p0[a] - c.v0[a] * tau, dv = fu[3 + a] - c.v0[a];
+    c.c2[a] = (3.f * dp - dv * tau) / (tau * tau);
+    c.c3[a] = (dv * tau - 2.f * dp) / (tau * tau * tau);
+    c.R[a] = fabsf(c.v0[a]) * tau + fabsf(c.c2[a]) * tau * tau + fabsf(c.c3[a]) * tau * tau * tau;
+    M = fmaxf(M, fabsf(c.p0[a]) + c.R[a]);
+  }
+  c.eps = (1.f + M) * 3.0517578125e-5f;
+  return c;
+}
+
+// Collision(v, u) for the pairs whose cost is below r, a warp per pair, in float only: the lanes
+// take the samples m (32 at a time) and test them against the boxes the connection can reach.  A
+// sample more than eps inside a box on every axis is a hit and ends the pair; one more than eps
+// outside on some axis misses that box.  A pair without a hit but with a sample within eps of a
+// box is undecided in float and goes to k_collide_exact; a pair with neither is kept.
+__global__ void k_collide(const float* __restrict__ states, const int2* __restrict__ list,
+                          const uint32_t* __restrict__ cand, const unsigned long long* __restrict__ n_cand, int n,
+                          int W, const float* __restrict__ boxes_g, int nb, const double* __restrict__ res_tau,
+                          uint32_t* keep, uint32_t* __restrict__ undec, unsigned long long* n_undec) {
+  extern __shared__ float smf[];
+  float* fracf = smf;
   float* boxes = fracf + 4 * W;
   for (int k = threadIdx.x; k < 6 * nb; k += blockDim.x) boxes[k] = boxes_g[k];
-  for (int m = threadIdx.x; m < 4 * W; m += blockDim.x) {
-    frac[m] = (double)(m + 1) / (double)(4 * W);
-    fracf[m] = (float)frac[m];
-  }
+  for (int m = threadIdx.x; m < 4 * W; m += blockDim.x) fracf[m] = __double2float_rn((double)(m + 1) / (double)(4 * W));
   __syncthreads();
+  const int lane = threadIdx.x & 31;
   const int nw = (n + 31) / 32;
-  const long long ns = (long long)*n_surv;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < ns; k += (long long)gridDim.x * blockDim.x) {
-    const long long q = surv[k];
-    int2 vu = list[q];
+  const long long nc = (long long)*n_cand;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int S = 4 * W;
+  for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nc; k += warps) {
+    const uint32_t q = cand[k];
+    const int2 vu = list[q];
     float fv[6], fu[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       fv[j] = states[6 * vu.x + j];
       fu[j] = states[6 * vu.y + j];
     }
-    float J32, tmin[2], Jmin[2];
-    int nm = 0;
-    const bool est = steer_estimate(fv, fu, &J32, tmin, &nm, Jmin);
+    const float tau = __double2float_rn(res_tau[q]);
+    const FloatConn c = float_conn(fv, fu, tau);
+    const float eps = c.eps;
+    // boxes the connection can reach (the first 64; beyond that every box is tested)
+    unsigned long long cb = 0ull;
+    for (int o0 = 0; o0 < 64 && o0 < nb; o0 += 32) {
+      const int o = o0 + lane;
+      bool ov = false;
+      if (o < nb) {
+        const float* b = boxes + 6 * o;
+        ov = true;
+        for (int a = 0; a < 3; ++a) ov = ov && b[a] <= c.p0[a] + c.R[a] + eps && c.p0[a] - c.R[a] - eps <= b[3 + a];
+      }
+      cb |= (unsigned long long)__ballot_sync(0xffffffffu, ov) << o0;
+    }
+    const bool rest = nb > 64;
+    bool hit = false, und = false;
+    if (cb || rest) {
+      for (int m0 = 1; m0 <= S && !hit; m0 += 32) {
+        const int m = m0 + lane;
+        bool h = false, u = false;
+        if (m <= S) {
+          const float t = tau * fracf[m - 1];
+          float p[3];
+          for (int a = 0; a < 3; ++a) p[a] = fmaf(fmaf(fmaf(c.c3[a], t, c.c2[a]), t, c.v0[a]), t, c.p0[a]);
+          unsigned long long bits = cb;
+          int o = -1;
+          for (;;) {
+            if (bits) {
+              o = __ffsll((long long)bits) - 1;
+              bits &= bits - 1ull;
+            } else if (rest && o < 64) {
+              o = 64;
+            } else if (rest && o >= 64 && o + 1 < nb) {
+              ++o;
+            } else {
+              break;
+            }
+            const float* b = boxes + 6 * o;
+            bool out = false, in = true;
+            for (int a = 0; a < 3; ++a) {
+              out = out || p[a] < b[a] - eps || p[a] > b[3 + a] + eps;
+              in = in && p[a] >= b[a] + eps && p[a] <= b[3 + a] - eps;
+            }
+            if (out) continue;
+            if (in) {
+              h = true;
+              break;
+            }
+            u = true;
+          }
+        }
+        hit = __any_sync(0xffffffffu, h);
+        und = __any_sync(0xffffffffu, u) || und;
+      }
+    }
+    if (lane == 0 && !hit) {
+      if (und)
+        undec[atomicAdd(n_undec, 1ull)] = q;
+      else
+        atomicOr(keep + (size_t)vu.x * nw + (vu.y >> 5), 1u << (vu.y & 31));
+    }
+  }
+}
+
+// Pairs k_collide could not decide, a warp per pair: the same float test per sample and box, and
+// for a sample within eps of a box the definition's evaluation (double cubic at t_m, rounded to
+// float, closed box).
+__global__ void k_collide_exact(const float* __restrict__ states, const int2* __restrict__ list,
+                                const uint32_t* __restrict__ undec, const unsigned long long* __restrict__ n_undec,
+                                int n, int W, const float* __restrict__ boxes, int nb, const double* __restrict__ res_tau,
+                                uint32_t* keep) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (n + 31) / 32;
+  const long long nu = (long long)*n_undec;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int S = 4 * W;
+  for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nu; k += warps) {
+    const uint32_t q = undec[k];
+    const int2 vu = list[q];
+    float fv[6], fu[6];
     double xv[6], xu[6];
-#pragma unroll
     for (int j = 0; j < 6; ++j) {
+      fv[j] = states[6 * vu.x + j];
+      fu[j] = states[6 * vu.y + j];
       xv[j] = (double)fv[j];
       xu[j] = (double)fu[j];
     }
-    double tau, J;
-    if (!(est ? steer_refined(xv, xu, tmin, Jmin, nm, &tau, &J) : steer_dev(xv, xu, &tau, &J))) continue;
-    if (!(__double2float_rn(J) < r)) continue;
-    double td = (double)__double2float_rn(tau);
-    if (connection_hits_fast(fv, fu, xv, xu, td, W, boxes, nb, frac, fracf)) continue;
-    res_tau[q] = tau;
-    res_cost[q] = __double2float_rn(J);
-    atomicOr(keep + (size_t)vu.x * nw + (vu.y >> 5), 1u << (vu.y & 31));
+    const float tau = __double2float_rn(res_tau[q]);
+    const double td = (double)tau;
+    const FloatConn c = float_conn(fv, fu, tau);
+    const float eps = c.eps;
+    Cubic cx[3];
+    for (int a = 0; a < 3; ++a) cx[a] = cubic_dev(xv, xu, td, a);
+    bool hit = false;
+    for (int m0 = 1; m0 <= S && !hit; m0 += 32) {
+      const int m = m0 + lane;
+      bool h = false;
+      if (m <= S) {
+        const double fr = (double)m / (double)S;
+        const float t = tau * __double2float_rn(fr);
+        float p[3];
+        for (int a = 0; a < 3; ++a) p[a] = fmaf(fmaf(fmaf(c.c3[a], t, c.c2[a]), t, c.v0[a]), t, c.p0[a]);
+        for (int o = 0; o < nb && !h; ++o) {
+          const float* b = boxes + 6 * o;
+          bool out = false, in = true;
+          for (int a = 0; a < 3; ++a) {
+            out = out || p[a] < b[a] - eps || p[a] > b[3 + a] + eps;
+            in = in && p[a] >= b[a] + eps && p[a] <= b[3 + a] - eps;
+          }
+          if (out) continue;
+          if (in) {
+            h = true;
+            break;
+          }
+          const double te = td * fr;
+          h = in_box_dev((float)cubic_at(cx[0], te), (float)cubic_at(cx[1], te), (float)cubic_at(cx[2], te), b);
+        }
+      }
+      hit = __any_sync(0xffffffffu, h);
+    }
+    if (!hit && lane == 0) atomicOr(keep + (size_t)vu.x * nw + (vu.y >> 5), 1u << (vu.y & 31));
   }
 }
 
@@ -517,11 +709,11 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   const int sms = num_sms();
   // node flags (validity) and goal flags were filled by the caller's kernels
   // prefilter: count per row, scan, allocate, list
-  unsigned long long* d_count = (unsigned long long*)dev_alloc(sizeof(unsigned long long) * 2, s);
+  unsigned long long* d_count = (unsigned long long*)dev_alloc(sizeof(unsigned long long) * 4, s);
   int32_t* rcnt = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)n, s);
   long long* roff = (long long*)dev_alloc(sizeof(long long) * (size_t)(n + 1), s);
   if (!d_count || !rcnt || !roff) return PUMP_ERR_OOM;
-  PUMP_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * 2, s));
+  PUMP_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * 4, s));
   const int grid = (int)std::min<long long>(((long long)n * 32 + kBlock - 1) / kBlock, (long long)sms * 16);
   k_prefilter<false><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, rcnt, nullptr, nullptr);
   note_launch();
@@ -550,13 +742,25 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   uint32_t* surv = nullptr;
   if (n_list) {
     if (n_list > 0xFFFFFFFFull) return PUMP_ERR_CAPACITY;
-    surv = (uint32_t*)dev_alloc(sizeof(uint32_t) * n_list, s);
+    surv = (uint32_t*)dev_alloc(sizeof(uint32_t) * n_list * 3, s);
     if (!surv) return PUMP_ERR_OOM;
+    uint32_t* surv_slow = surv + n_list;
+    uint32_t* cand = surv + 2 * n_list;
     k_steer_filter<<<glist, kBlock, 0, s>>>(g->states, list, (long long)n_list, g->radius, surv, d_count);
     note_launch();
-    const size_t smem = (sizeof(double) + sizeof(float)) * 4 * g->W + sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1);
-    k_steer_pairs<<<sms * 4, kBlock, smem, s>>>(g->states, list, surv, d_count, n, g->radius, g->W, g->boxes,
-                                                g->n_boxes, keep, res_tau, res_cost);
+    k_steer_pairs<<<sms * 4, kBlock, 0, s>>>(g->states, list, surv, d_count, g->radius, res_tau, res_cost, surv_slow,
+                                             d_count + 1, cand, d_count + 2);
+    note_launch();
+    k_steer_slow<<<sms, kBlock, 0, s>>>(g->states, list, surv_slow, d_count + 1, g->radius, res_tau, res_cost, cand,
+                                        d_count + 2);
+    note_launch();
+    const size_t smem = sizeof(float) * 4 * g->W + sizeof(float) * 6 * (g->n_boxes > 0 ? g->n_boxes : 1);
+    uint32_t* undec = surv_slow;  // the slow list is consumed by now
+    k_collide<<<sms * 8, kBlock, smem, s>>>(g->states, list, cand, d_count + 2, n, g->W, g->boxes, g->n_boxes, res_tau,
+                                            keep, undec, d_count + 3);
+    note_launch();
+    k_collide_exact<<<sms, kBlock, 0, s>>>(g->states, list, undec, d_count + 3, n, g->W, g->boxes, g->n_boxes, res_tau,
+                                        keep);
     note_launch();
   }
   k_row_counts<<<(n + 7) / 8, kBlock, 0, s>>>(keep, n, deg);
