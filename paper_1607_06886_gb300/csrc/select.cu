@@ -193,9 +193,11 @@ __device__ __forceinline__ void mc_normals(uint64_t seed, uint64_t m, uint64_t s
   for (int j = 0; j < 3; ++j) {
     const float u1 = ((float)(uint32_t)(o[j] >> 40) + 0.5f) * 5.9604644775390625e-08f;
     const float u2 = ((float)(uint32_t)((o[j] >> 16) & 0xFFFFFFull) + 0.5f) * 5.9604644775390625e-08f;
-    const float r = sqrtf(-2.0f * logf(u1));
+    // hardware log2 and sine/cosine approximations (absolute error ~2^-21); the clamp keeps r
+    // real where the approximate log of a u1 just below 1 comes out positive
+    const float r = sqrtf(fmaxf(-2.0f * __logf(u1), 0.0f));
     float sn, cs;
-    sincospif(2.0f * u2, &sn, &cs);
+    __sincosf(6.28318530717958648f * u2, &sn, &cs);
     z[2 * j] = r * cs;
     z[2 * j + 1] = r * sn;
   }
@@ -235,16 +237,12 @@ __device__ __forceinline__ void mc_update(const float* z, float P0, float P1, fl
   }
 }
 
-// kMcLanes lanes per rollout; plan k = blockIdx.x / bpp.  The normals of a step depend only on
+// kMcLanes lanes per rollout (1 or 2); plan k = blockIdx.x / bpp.  The normals of a step depend only on
 // (seed, rollout, step), so the lanes of a rollout draw the normals of consecutive steps in
 // parallel (lane j takes steps j, j + kMcLanes, ...; Philox4x64 dominates the work) and pass
 // them round by group shuffles; every lane of the group then applies the same updates in step
 // order, so all of them hold the same deviation and the same hit flag.
-#ifndef PUMP_MC_LANES
-#define PUMP_MC_LANES 2  // measured best of 1, 2, 4, 8
-#endif
-constexpr int kMcLanes = PUMP_MC_LANES;
-
+template <int kMcLanes>
 __global__ void __launch_bounds__(kMcThreads) k_mc_rollout(const int32_t* __restrict__ n_cert_p, int bpp,
                                                             const int32_t* __restrict__ plen,
                                                             const float* __restrict__ table, int W, int S,
@@ -310,6 +308,171 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_rollout(const int32_t* __rest
   }
   const unsigned bal = __ballot_sync(0xffffffffu, hit && j == 0);
   if (lane == 0 && bal) atomicAdd(counts + k, (unsigned long long)__popc(bal));
+}
+
+constexpr int kMcScanSteps = 8;  // steps per lane per chunk: a chunk is 32 x 8 steps of one rollout
+constexpr int kMcScanThreads = 256;
+
+// MC(p) with a warp per rollout.  The deviation recurrence d_s = Phi_e d_{s-1} + n_s (per axis,
+// n_s = L_e (z0, z1)_s, e the step's edge) is affine in d, so a chunk of 32 x 8 steps runs in
+// parallel: lane j draws the normals of its 8 steps and composes their maps, an inclusive scan
+// over the lanes gives every lane the deviation at the start of its steps, and each lane walks its
+// steps from there and tests their positions.  A rollout collides when any step's position lies
+// in a box, whatever the order the steps are tested in.  Work items (plan k, rollout m) are spread
+// over the warps of the grid.  Against walking the steps one after another the deviations differ
+// only by the float rounding of the composed maps (relative ~1e-7); lane 0 of the first chunk
+// reproduces the one-after-another values exactly.
+__global__ void __launch_bounds__(kMcScanThreads) k_mc_scan(const int32_t* __restrict__ n_cert_p,
+                                                             const int32_t* __restrict__ plen,
+                                                             const float* __restrict__ table, int W, int S,
+                                                             const float* __restrict__ linf_g,
+                                                             const float* __restrict__ boxes_g, int nb, int n_mc,
+                                                             uint64_t seed, float B, unsigned long long* counts) {
+  extern __shared__ float boxes[];
+  for (int q = threadIdx.x; q < 6 * nb; q += blockDim.x) boxes[q] = boxes_g[q];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long items = (long long)(*n_cert_p) * n_mc;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int stride = 8 + W * S * 3, WS = W * S;
+  const float l0 = linf_g[0], l1 = linf_g[1], l2 = linf_g[2];
+  for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < items; w += nwarps) {
+    const int k = (int)(w / n_mc), m = (int)(w % n_mc);
+    const float* T = table + (size_t)k * kMaxPathEdges * stride;
+    const int Ls = plen[k] * WS;
+    float z[6], d0[3], d1[3];
+    mc_normals(seed, (uint64_t)m, 0ull, z);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      d0[a] = __fmul_rn(l0, z[2 * a]);
+      d1[a] = fmaf(l1, z[2 * a], __fmul_rn(l2, z[2 * a + 1]));
+    }
+    bool hit = false;
+    for (int base = 0; base < Ls && !hit; base += 32 * kMcScanSteps) {
+      const int s0 = base + lane * kMcScanSteps + 1;  // first step of this lane
+      int e = s0 <= Ls ? (s0 - 1) / WS : 0, q = s0 <= Ls ? (s0 - 1) - e * WS : 0;
+      // 1. the lane's steps: normals, noise terms and the composed map (M, v): d -> M d + v
+      float n0[kMcScanSteps][3], n1[kMcScanSteps][3];
+      float M00 = 1.f, M01 = 0.f, M10 = 0.f, M11 = 1.f, v0[3] = {0.f, 0.f, 0.f}, v1[3] = {0.f, 0.f, 0.f};
+      {
+        int ee = e, qq = q;
+#pragma unroll
+        for (int c = 0; c < kMcScanSteps; ++c) {
+          const int s = s0 + c;
+          if (s <= Ls) {
+            const float* Te = T + (size_t)ee * stride;
+            const float P0 = Te[0], P1 = Te[1], P2 = Te[2], P3 = Te[3], L0 = Te[4], L1 = Te[5], L2 = Te[6];
+            mc_normals(seed, (uint64_t)m, (uint64_t)s, z);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              n0[c][a] = __fmul_rn(L0, z[2 * a]);
+              n1[c][a] = fmaf(L1, z[2 * a], __fmul_rn(L2, z[2 * a + 1]));
+              const float t0 = fmaf(P0, v0[a], fmaf(P1, v1[a], n0[c][a]));
+              const float t1 = fmaf(P2, v0[a], fmaf(P3, v1[a], n1[c][a]));
+              v0[a] = t0;
+              v1[a] = t1;
+            }
+            const float a00 = fmaf(P0, M00, __fmul_rn(P1, M10)), a01 = fmaf(P0, M01, __fmul_rn(P1, M11));
+            const float a10 = fmaf(P2, M00, __fmul_rn(P3, M10)), a11 = fmaf(P2, M01, __fmul_rn(P3, M11));
+            M00 = a00;
+            M01 = a01;
+            M10 = a10;
+            M11 = a11;
+            if (++qq == WS) {
+              qq = 0;
+              ++ee;
+            }
+          } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) n0[c][a] = n1[c][a] = 0.f;
+          }
+        }
+      }
+      // 2. inclusive scan over the lanes: (M, v) after the maps of every lower lane, lower first
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float u00 = __shfl_up_sync(0xffffffffu, M00, off), u01 = __shfl_up_sync(0xffffffffu, M01, off);
+        const float u10 = __shfl_up_sync(0xffffffffu, M10, off), u11 = __shfl_up_sync(0xffffffffu, M11, off);
+        float w0[3], w1[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          w0[a] = __shfl_up_sync(0xffffffffu, v0[a], off);
+          w1[a] = __shfl_up_sync(0xffffffffu, v1[a], off);
+        }
+        if (lane >= off) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float t0 = fmaf(M00, w0[a], fmaf(M01, w1[a], v0[a]));
+            const float t1 = fmaf(M10, w0[a], fmaf(M11, w1[a], v1[a]));
+            v0[a] = t0;
+            v1[a] = t1;
+          }
+          const float a00 = fmaf(M00, u00, __fmul_rn(M01, u10)), a01 = fmaf(M00, u01, __fmul_rn(M01, u11));
+          const float a10 = fmaf(M10, u00, __fmul_rn(M11, u10)), a11 = fmaf(M10, u01, __fmul_rn(M11, u11));
+          M00 = a00;
+          M01 = a01;
+          M10 = a10;
+          M11 = a11;
+        }
+      }
+      // 3. the deviation at the start of this lane's steps (exclusive prefix) and at the chunk's end
+      float x0[3], x1[3];
+      {
+        float e00 = __shfl_up_sync(0xffffffffu, M00, 1), e01 = __shfl_up_sync(0xffffffffu, M01, 1);
+        float e10 = __shfl_up_sync(0xffffffffu, M10, 1), e11 = __shfl_up_sync(0xffffffffu, M11, 1);
+        const float f00 = __shfl_sync(0xffffffffu, M00, 31), f01 = __shfl_sync(0xffffffffu, M01, 31);
+        const float f10 = __shfl_sync(0xffffffffu, M10, 31), f11 = __shfl_sync(0xffffffffu, M11, 31);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          float y0 = __shfl_up_sync(0xffffffffu, v0[a], 1), y1 = __shfl_up_sync(0xffffffffu, v1[a], 1);
+          if (lane == 0) {
+            x0[a] = d0[a];
+            x1[a] = d1[a];
+          } else {
+            x0[a] = fmaf(e00, d0[a], fmaf(e01, d1[a], y0));
+            x1[a] = fmaf(e10, d0[a], fmaf(e11, d1[a], y1));
+          }
+          const float g0 = __shfl_sync(0xffffffffu, v0[a], 31), g1 = __shfl_sync(0xffffffffu, v1[a], 31);
+          const float c0 = fmaf(f00, d0[a], fmaf(f01, d1[a], g0));
+          const float c1 = fmaf(f10, d0[a], fmaf(f11, d1[a], g1));
+          d0[a] = c0;
+          d1[a] = c1;
+        }
+        (void)e00;
+        (void)e01;
+        (void)e10;
+        (void)e11;
+      }
+      // 4. walk the lane's steps and test the positions
+      bool h = false;
+#pragma unroll
+      for (int c = 0; c < kMcScanSteps; ++c) {
+        const int s = s0 + c;
+        if (s <= Ls && !h) {
+          const float* Te = T + (size_t)e * stride;
+          const float P0 = Te[0], P1 = Te[1], P2 = Te[2], P3 = Te[3];
+          const uint32_t bits = __float_as_uint(Te[7]);
+          const float* nomq = Te + 8 + q * 3;
+          float p[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float t0 = fmaf(P0, x0[a], fmaf(P1, x1[a], n0[c][a]));
+            const float t1 = fmaf(P2, x0[a], fmaf(P3, x1[a], n1[c][a]));
+            x0[a] = t0;
+            x1[a] = t1;
+            p[a] = __fadd_rn(nomq[a], t0);
+          }
+          h = mc_hit(p, x0, B, bits, boxes, nb);
+          if (++q == WS) {
+            q = 0;
+            ++e;
+          }
+        }
+      }
+      hit = __any_sync(0xffffffffu, h);
+    }
+    if (lane == 0 && hit) atomicAdd(counts + k, 1ull);
+  }
 }
 
 __global__ void k_counts_store(const SelState* __restrict__ st, const unsigned long long* __restrict__ counts,
@@ -417,25 +580,42 @@ int ensure_table(pump_graph* g, int S, cudaStream_t s) {
 }
 
 // Certify the plans of the current batch (n_cert read on the device from the state).
-int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert_max, int n_mc, int S, uint64_t seed,
+// n_cert: the batch's plan count, known on the host (the device copy n_cert_dev holds the same).
+int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert, int n_mc, int S, uint64_t seed,
              cudaStream_t s) {
   ExploreBufs& X = g->ex;
-  dim3 grid(kMaxPathEdges / 64, n_cert_max);
+  dim3 grid(kMaxPathEdges / 64, std::max(n_cert, 1));
   // deviation bound for the box cull: 12 stationary position standard deviations (any B is exact)
   const double sq3 = 1.7320508075688772935;
   const float B = (float)(12.0 * (double)g->sigma * sqrt(1.0 / sq3 + 0.5 * sq3)) + 1e-6f;
   k_mc_prep<<<grid, 64, 0, s>>>(n_cert_dev, X.mc_plen, X.mc_pedges, X.path_buf, g->states, g->tau, g->W, S,
                                 g->sigma, g->boxes, g->n_boxes, B, X.mc_table);
   note_launch();
-  PUMP_CUDA_TRY(cudaMemsetAsync(X.mc_count, 0, sizeof(int64_t) * n_cert_max, s));
-  const int per_block = kMcThreads / kMcLanes;
-  const int bpp = (n_mc + per_block - 1) / per_block;
-  if (n_mc > 0 && bpp > 0) {
-    const size_t smem = sizeof(float) * (6 * (size_t)std::max(g->n_boxes, 1) + kMcTableSmem);
-    PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_mc_rollout<<<n_cert_max * bpp, kMcThreads, smem, s>>>(n_cert_dev, bpp, X.mc_plen, X.mc_table, g->W, S,
-                                                            g->linf_dev, g->boxes, g->n_boxes, n_mc, seed, B,
-                                                            reinterpret_cast<unsigned long long*>(X.mc_count));
+  PUMP_CUDA_TRY(cudaMemsetAsync(X.mc_count, 0, sizeof(int64_t) * std::max(n_cert, 1), s));
+  // the form that measured fastest for this many plans: the warp scan while few rollouts are in
+  // flight (one or two plans), then two and one lanes per rollout
+  if (n_mc > 0 && n_cert > 0) {
+    const size_t smem_boxes = sizeof(float) * 6 * (size_t)std::max(g->n_boxes, 1);
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(X.mc_count);
+    if (n_cert <= 2) {
+      PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_boxes));
+      k_mc_scan<<<num_sms() * 4, kMcScanThreads, smem_boxes, s>>>(n_cert_dev, X.mc_plen, X.mc_table, g->W, S,
+                                                                  g->linf_dev, g->boxes, g->n_boxes, n_mc, seed, B,
+                                                                  counts);
+    } else {
+      const size_t smem = smem_boxes + sizeof(float) * kMcTableSmem;
+      if (n_cert <= 6) {
+        const int bpp = (n_mc + kMcThreads / 2 - 1) / (kMcThreads / 2);
+        PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_rollout<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_mc_rollout<2><<<n_cert * bpp, kMcThreads, smem, s>>>(n_cert_dev, bpp, X.mc_plen, X.mc_table, g->W, S,
+                                                               g->linf_dev, g->boxes, g->n_boxes, n_mc, seed, B, counts);
+      } else {
+        const int bpp = (n_mc + kMcThreads - 1) / kMcThreads;
+        PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_rollout<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_mc_rollout<1><<<n_cert * bpp, kMcThreads, smem, s>>>(n_cert_dev, bpp, X.mc_plen, X.mc_table, g->W, S,
+                                                               g->linf_dev, g->boxes, g->n_boxes, n_mc, seed, B, counts);
+      }
+    }
     note_launch();
   }
   PUMP_CUDA_TRY(cudaGetLastError());
@@ -458,6 +638,10 @@ int run_select(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t 
   SelState* st = (SelState*)X.sel_state;
   const int32_t* n_cert_dev = &st->n_cert;
   PUMP_CUDA_TRY(cudaMemsetAsync(X.sel_err, 0, sizeof(int32_t) * 2, s));
+  // Explore's outcome on the host: the first batch's plan count picks the certification form
+  PUMP_CUDA_TRY(cudaMemcpyAsync(ctl_host, X.ctl, sizeof(ExploreCtl), cudaMemcpyDeviceToHost, s));
+  PUMP_CUDA_TRY(cudaStreamSynchronize(s));
+  const int G0 = ctl_host->status ? 0 : ctl_host->n_goal;
   SelState hs;
   out->n_certified = 0;
   for (int round = 0; round < 256; ++round) {
@@ -468,11 +652,11 @@ int run_select(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t 
       k_clear_index<<<64, 256, 0, s>>>(st, X.sel_by_index);
       note_launch();
     }
-    const int n_cert_max = round == 0 ? kCertMax : 1;
+    const int n_cert = round == 0 ? std::min(G0, kCertMax) : 1;
     k_mc_paths<<<1, kCertMax, 0, s>>>(st, X.mc_plan, X.parent, X.pedge, X.head, X.mc_plen, X.mc_pedges, X.path_buf,
                                       X.sel_err);
     note_launch();
-    rc = mc_batch(g, n_cert_dev, n_cert_max, p->n_mc, S, p->mc_seed, s);
+    rc = mc_batch(g, n_cert_dev, n_cert, p->n_mc, S, p->mc_seed, s);
     if (rc) return rc;
     k_counts_store<<<1, kCertMax, 0, s>>>(st, reinterpret_cast<unsigned long long*>(X.mc_count), X.sel_idx,
                                           X.sel_by_index);
@@ -484,7 +668,6 @@ int run_select(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t 
     PUMP_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
     int32_t err = 0;
     PUMP_CUDA_TRY(cudaMemcpyAsync(&err, X.sel_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    if (round == 0) PUMP_CUDA_TRY(cudaMemcpyAsync(ctl_host, X.ctl, sizeof(ExploreCtl), cudaMemcpyDeviceToHost, s));
     const int ncopy = std::min(path_cap, kMaxPathEdges + 1);
     if (path && ncopy > 0)
       PUMP_CUDA_TRY(cudaMemcpyAsync(path, X.path_buf, sizeof(int32_t) * ncopy, cudaMemcpyDeviceToHost, s));
