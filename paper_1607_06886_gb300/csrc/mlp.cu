@@ -18,7 +18,7 @@
 //   backward  dh_l   = g_l W_l       A = g_l (K-major), B = W_l (N-major)
 //             dW_l   = g_l^T h_l     A = g_l (M-major), B = h_l (N-major), split over K (the batch)
 // so no operand is ever transposed in memory.  A 64 x 64 block tile, four warps of 32 x 32, K
-// steps of 32 staged by cp.async in two buffers; fragments come from ldmatrix (.trans for the
+// steps of 32 staged by cp.async four buffers deep; fragments come from ldmatrix (.trans for the
 // M/N-major tiles) and feed mma.sync m16n8k16 (BF16 in, FP32 accumulate).  Tile rows are padded
 // (K-major 40 elements, M/N-major 72) so that every ldmatrix phase hits 32 distinct banks.  The
 // epilogue is fused: bias + ReLU to BF16, bias to FP32, ReLU-mask of the layer below to BF16, or
@@ -50,10 +50,12 @@ constexpr int kKPad = kBK + 8;  // row length of a K-major tile (elements)
 constexpr int kMPad = kBM + 8;  // row length of an M- or N-major tile (elements)
 constexpr int kTileElems = kBM * kKPad;  // >= kBK * kMPad
 constexpr int kGemmThreads = 128;
+constexpr int kStages = 4;  // K steps of 32 in flight per block (cp.async groups)
 constexpr int kLatent = 8;
 constexpr int kOutUsed = 6;
 constexpr int kMaxSplit = 8;
-constexpr int kLossThreads = 1024;
+constexpr int kLossThreads = 256;
+constexpr int kLossBlocksMax = 64;
 
 static_assert(kBK * kMPad <= kTileElems, "tile buffer too small");
 
@@ -85,7 +87,10 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred
                "r"(pred ? 16 : 0));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+template <int kN>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kN));
+}
 
 __device__ __forceinline__ void ldsm4(uint32_t* r, const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -119,8 +124,8 @@ __device__ __forceinline__ void stage_tile(bf16* t, const bf16* X, int ld, int R
 
 template <int kEpi, bool kAK, bool kBK_>
 __global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
-  __shared__ __align__(128) bf16 sA[2][kTileElems];
-  __shared__ __align__(128) bf16 sB[2][kTileElems];
+  __shared__ __align__(128) bf16 sA[kStages][kTileElems];
+  __shared__ __align__(128) bf16 sB[kStages][kTileElems];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 1, wn = warp & 1;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
@@ -134,23 +139,29 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
 
-  if (nk > 0) {
-    stage_tile<kAK>(sA[0], g.A, g.lda, g.M, m0, kb, ke, tid);
-    stage_tile<kBK_>(sB[0], g.B, g.ldb, g.N, n0, kb, ke, tid);
-  }
-  cp_async_commit();
-  const int mi = lane >> 3, i8 = lane & 7;
-  for (int it = 0; it < nk; ++it) {
-    if (it + 1 < nk) {
-      const int k1 = kb + (it + 1) * kBK;
-      stage_tile<kAK>(sA[(it + 1) & 1], g.A, g.lda, g.M, m0, k1, ke, tid);
-      stage_tile<kBK_>(sB[(it + 1) & 1], g.B, g.ldb, g.N, n0, k1, ke, tid);
+  // prologue: the first kStages - 1 K steps in flight (one commit group each, empty past nk)
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    if (st < nk) {
+      stage_tile<kAK>(sA[st], g.A, g.lda, g.M, m0, kb + st * kBK, ke, tid);
+      stage_tile<kBK_>(sB[st], g.B, g.ldb, g.N, n0, kb + st * kBK, ke, tid);
     }
     cp_async_commit();
-    cp_async_wait1();
-    __syncthreads();
-    const bf16* tA = sA[it & 1];
-    const bf16* tB = sB[it & 1];
+  }
+  const int mi = lane >> 3, i8 = lane & 7;
+  for (int it = 0; it < nk; ++it) {
+    cp_async_wait<kStages - 2>();  // step it has landed
+    __syncthreads();               // ... for every thread; and step it - 1's buffer is free
+    {
+      const int nx = it + kStages - 1;
+      if (nx < nk) {
+        stage_tile<kAK>(sA[nx % kStages], g.A, g.lda, g.M, m0, kb + nx * kBK, ke, tid);
+        stage_tile<kBK_>(sB[nx % kStages], g.B, g.ldb, g.N, n0, kb + nx * kBK, ke, tid);
+      }
+      cp_async_commit();
+    }
+    const bf16* tA = sA[it % kStages];
+    const bf16* tB = sB[it % kStages];
 #pragma unroll
     for (int kk = 0; kk < kBK; kk += 16) {
       uint32_t a[2][4], b[4][2];
@@ -185,7 +196,6 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
               : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
               : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
     }
-    __syncthreads();
   }
 
   // accumulator (i, j): [0..1] row g, columns 2t, 2t+1; [2..3] row g + 8
@@ -297,15 +307,20 @@ __global__ void k_assemble(const float* __restrict__ feat, int F, int n_env, int
     if (env_out && r < B) env_out[r] = env;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < 16 * d0; q += blockDim.x) {
-    const int rr = q / d0, c = q - rr * d0, r = row0 + rr;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int rr = warp; rr < 16; rr += nwarp) {
+    const int r = row0 + rr;
     if (r >= B) break;
-    float v = 0.f;
-    if (c < F)
-      v = feat[(size_t)e[rr] * F + c];
-    else if (c < F + kLatent)
-      v = z[rr][c - F];
-    x[(size_t)r * d0 + c] = __float2bfloat16_rn(v);
+    const float* f = feat + (size_t)e[rr] * F;
+    bf16* xr = x + (size_t)r * d0;
+    for (int c = lane; c < d0; c += 32) {
+      float v = 0.f;
+      if (c < F)
+        v = f[c];
+      else if (c < F + kLatent)
+        v = z[rr][c - F];
+      xr[c] = __float2bfloat16_rn(v);
+    }
   }
 }
 
@@ -330,16 +345,19 @@ struct LossArgs {
 // tg[set][0 .. ntg[set]) of 6 floats.  Kind 0 takes the nearest target (first on ties); kind 1
 // the point at fraction u = Phi(z_0) of the targets' polyline: a = u (n - 1),
 // i = min(floor(a), n - 2), y = y_i + (a - i)(y_{i+1} - y_i).  Writes g = bf16(d mean loss / d o)
-// (B x ld, zero past column 6) and, from thread 0 after a fixed-order block reduction,
-// trace[ctl[0] - ctl[1]] = mean loss; then advances ctl[0].  One block.
+// (B x ld, zero past column 6) and, after a fixed-order reduction,
+// trace[ctl[0] - ctl[1]] = mean loss (the blocks' sums added in block order by the last block to
+// finish); then advances ctl[0].
 __global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__ o, int B, int ld, float vmax,
                                                        const float* __restrict__ tg, const int32_t* __restrict__ ntg,
                                                        int T, const int32_t* __restrict__ env, const LossArgs la,
                                                        bf16* __restrict__ gout, int64_t* __restrict__ ctl,
-                                                       float* __restrict__ trace, int trace_cap) {
+                                                       float* __restrict__ trace, int trace_cap,
+                                                       float* __restrict__ part, unsigned int* __restrict__ ticket) {
   __shared__ float red[kLossThreads];
+  __shared__ bool last;
   float local = 0.f;
-  for (int r = threadIdx.x; r < B; r += kLossThreads) {
+  for (int r = blockIdx.x * kLossThreads + threadIdx.x; r < B; r += gridDim.x * kLossThreads) {
     const int set = env ? env[r] : r;
     const float* q0 = tg + (size_t)set * T * kOutUsed;
     const int n = min(ntg[set], T);
@@ -397,10 +415,21 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
+  // the last block to finish adds the blocks' sums in block order, records and advances
   if (threadIdx.x == 0) {
+    part[blockIdx.x] = red[0];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    float sum = 0.f;
+    for (int b = 0; b < (int)gridDim.x; ++b) sum += ((volatile float*)part)[b];
     const int64_t idx = ctl[0] - ctl[1];
-    if (trace && idx >= 0 && idx < trace_cap) trace[idx] = red[0] / (float)B;
+    if (trace && idx >= 0 && idx < trace_cap) trace[idx] = sum / (float)B;
     ctl[0] += 1;
+    *ticket = 0u;
   }
 }
 
@@ -443,6 +472,8 @@ struct pump_mlp {
   float* m2 = nullptr;     // Adam second moments
   bf16* wb = nullptr;      // BF16 copy of w
   int64_t* ctl = nullptr;  // [0] Adam steps taken, [1] trace base
+  float* lpart = nullptr;          // per-block loss sums
+  unsigned int* lticket = nullptr; // blocks of the loss kernel finished
   cudaStream_t s = nullptr;
   cudaEvent_t ev = nullptr;
   // scratch for up to `cap` rows
@@ -643,6 +674,8 @@ int stage_input(pump_mlp* m, const float* x, int B, int* launches) {
   return PUMP_OK;
 }
 
+int loss_blocks(int B) { return std::max(1, std::min(kLossBlocksMax, (B + kLossThreads - 1) / kLossThreads)); }
+
 LossArgs loss_args(const pump_mlp* m) {
   LossArgs a{};
   a.kind = m->loss_kind;
@@ -659,8 +692,9 @@ void train_step_kernels(pump_mlp* m, int B, uint64_t seed, float lr, float vmax,
                                            m->env);
   ++*launches;
   forward(m, B, s, launches);
-  k_loss<<<1, kLossThreads, 0, s>>>(m->out, B, m->dims[m->L], vmax, m->tg, m->ntg, m->T, m->env, loss_args(m), m->gA,
-                                    m->ctl, m->trace, m->trace_cap);
+  k_loss<<<loss_blocks(B), kLossThreads, 0, s>>>(m->out, B, m->dims[m->L], vmax, m->tg, m->ntg, m->T, m->env,
+                                                  loss_args(m), m->gA, m->ctl, m->trace, m->trace_cap, m->lpart,
+                                                  m->lticket);
   ++*launches;
   backward(m, B, s, launches);
   adam(m, B, lr, s, launches);
@@ -713,7 +747,10 @@ int pump_mlp_create(int32_t n_layers, const int32_t* dims, uint64_t seed, pump_m
   m->m2 = dmalloc<float>(m->P);
   m->wb = dmalloc<bf16>(m->P);
   m->ctl = dmalloc<int64_t>(2);
-  if (!m->w || !m->m1 || !m->m2 || !m->wb || !m->ctl ||
+  m->lpart = dmalloc<float>(kLossBlocksMax);
+  m->lticket = dmalloc<unsigned int>(1);
+  if (m->lticket) cudaMemset(m->lticket, 0, sizeof(unsigned int));
+  if (!m->w || !m->m1 || !m->m2 || !m->wb || !m->ctl || !m->lpart || !m->lticket ||
       cudaStreamCreateWithFlags(&m->s, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) != cudaSuccess) {
     pump_mlp_destroy(m);
@@ -829,8 +866,9 @@ int pump_mlp_train_step(pump_mlp* m, const float* x, int32_t B, const float* tar
   // the step's mean loss goes to trace[0]: base = the current step count
   PUMP_CUDA_TRY(cudaMemcpyAsync(m->ctl + 1, m->ctl, sizeof(int64_t), cudaMemcpyDeviceToDevice, m->s));
   forward(m, B, m->s, &n);
-  k_loss<<<1, kLossThreads, 0, m->s>>>(m->out, B, m->dims[m->L], vmax, m->tg_rows, m->ntg_rows, T, nullptr,
-                                       loss_args(m), m->gA, m->ctl, m->trace, m->trace_cap);
+  k_loss<<<loss_blocks(B), kLossThreads, 0, m->s>>>(m->out, B, m->dims[m->L], vmax, m->tg_rows, m->ntg_rows, T,
+                                                     nullptr, loss_args(m), m->gA, m->ctl, m->trace, m->trace_cap,
+                                                     m->lpart, m->lticket);
   ++n;
   backward(m, B, m->s, &n);
   adam(m, B, lr, m->s, &n);
@@ -967,7 +1005,7 @@ void pump_mlp_destroy(pump_mlp* m) {
   drop_graph(m);
   free_scratch(m);
   for (void* p : {(void*)m->w, (void*)m->m1, (void*)m->m2, (void*)m->wb, (void*)m->ctl, (void*)m->feat, (void*)m->tg,
-                  (void*)m->ntg, (void*)m->trace})
+                  (void*)m->ntg, (void*)m->trace, (void*)m->lpart, (void*)m->lticket})
     if (p) cudaFree(p);
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
