@@ -1,10 +1,12 @@
 """MC(p) certification on the GPU vs the CPU oracle.
 
 Both sides draw the same Philox4x64-10 words for every rollout, step and axis and map them to the
-same uniforms; only Box-Muller differs (float on the GPU, double rounded to float in the oracle), a
-few float ulps per normal.  Deviations therefore differ by ~1e-9 and a rollout's outcome can only
-flip when its path grazes a box face at that scale.  Tolerance: |count_gpu - count_oracle| <=
-3 + 0.002 count.  With independent seeds the two estimates agree within their binomial spread."""
+same uniforms; Box-Muller differs (the GPU's hardware log and sine/cosine approximations, absolute
+error ~2^-21 per normal, against double rounded to float in the oracle), and the GPU's warp-scan
+form (one or two plans) composes the deviation recurrence across lanes (float rounding ~1e-7
+relative).  Deviations therefore differ by ~1e-8 and a rollout's outcome can only flip when its
+path grazes a box face at that scale.  Tolerance: |count_gpu - count_oracle| <= 3 + 0.002 count.
+With independent seeds the two estimates agree within their binomial spread."""
 import math
 
 import numpy as np
@@ -84,3 +86,21 @@ def test_certify_rejects_paths_off_the_graph(planned):
     assert e.value.status == pump.ERR_INVALID_ARG
     with pytest.raises(pump.PumpError):
         G.certify([0, wl.n + 5], 10, 4, 0)
+
+
+@pytest.mark.parametrize("seed,lo,hi", [(2, 1, 2), (0, 3, 6), (1, 7, 32)])
+def test_plan_certification_forms_match_oracle(seed, lo, hi):
+    """PlanSelection certifies its first batch of goal plans with the form that suits their count:
+    the warp scan for one or two plans, two lanes per rollout up to six, one lane beyond.  Full
+    indoor queries whose P_goal sizes fall in each range; the chosen plan's count is checked
+    against the oracle's MC of the same path and stream."""
+    wl = inputs.make_workload("indoor_4k", seed)
+    G = gpu_graph(wl)
+    n_mc = 4000
+    res = G.plan(plan_params(wl, n_mc=n_mc))
+    assert lo <= res["n_goal"] <= hi, res["n_goal"]
+    assert res["chosen_plan"] >= 0
+    og = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
+    c_orc = _oracle_count(wl, og, res["path"], n_mc, wl.mc_substeps, wl.mc_seed)
+    assert abs(res["mc_collisions"] - c_orc) <= 3 + int(0.002 * c_orc), (res["mc_collisions"], c_orc)
+    G.close()
