@@ -22,7 +22,8 @@
 // M/N-major tiles) and feed mma.sync m16n8k16 (BF16 in, FP32 accumulate).  Tile rows are padded
 // (K-major 40 elements, M/N-major 72) so that every ldmatrix phase hits 32 distinct banks.  The
 // epilogue is fused: bias + ReLU to BF16, bias to FP32, ReLU-mask of the layer below to BF16, or
-// plain FP32 partial sums (split K).  The weight-gradient partials of the S splits stay separate
+// plain FP32 partial sums (split K; the blocks of the first N tile also sum the gradient's columns,
+// the bias gradient).  The weight-gradient partials of the S splits stay separate
 // and the Adam launch adds them in a fixed order, so a training step is deterministic.
 //
 // Device-side step counter.  ctl[0] counts the Adam steps taken; the batch assembly of step t
@@ -78,6 +79,7 @@ struct GemmArgs {
   float* out_f32;
   int ldo;               // output row stride (elements)
   int64_t split_stride;  // offset between the splits' outputs (kEpiPartial)
+  float* colsum;         // kEpiPartial with an M-major A: also sum_k A[k][m] per split (bias gradient), or null
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
   const int kb = blockIdx.z * g.kchunk, ke = min(g.K, kb + g.kchunk);
   const int nk = ke > kb ? (ke - kb + kBK - 1) / kBK : 0;
   float acc[2][4][4];
+  float csum = 0.f;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -162,6 +165,12 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
     }
     const bf16* tA = sA[it % kStages];
     const bf16* tB = sB[it % kStages];
+    if (kEpi == kEpiPartial && !kAK && g.colsum && blockIdx.x == 0) {
+      // column sums of the M-major A tile: thread t takes column t % 64, rows (t / 64) * 16 .. + 16
+      const int cm = tid & 63, k0r = (tid >> 6) * 16;
+#pragma unroll
+      for (int kr = 0; kr < 16; ++kr) csum += __bfloat162float(tA[(k0r + kr) * kMPad + cm]);
+    }
 #pragma unroll
     for (int kk = 0; kk < kBK; kk += 16) {
       uint32_t a[2][4], b[4][2];
@@ -198,6 +207,12 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
     }
   }
 
+  if (kEpi == kEpiPartial && !kAK && g.colsum && blockIdx.x == 0) {
+    __shared__ float cs[kGemmThreads];
+    cs[tid] = csum;
+    __syncthreads();
+    if (tid < 64 && m0 + tid < g.M) g.colsum[blockIdx.z * g.split_stride + m0 + tid] = cs[tid] + cs[tid + 64];
+  }
   // accumulator (i, j): [0..1] row g, columns 2t, 2t+1; [2..3] row g + 8
   const int gq = lane >> 2, tq = lane & 3;
 #pragma unroll
@@ -241,26 +256,6 @@ __global__ void k_bf16_to_f32(const bf16* __restrict__ in, int64_t n, float* __r
     out[k] = __bfloat162float(in[k]);
 }
 
-// Bias-gradient partials: out[s * stride + c] = sum of g[r][c] over rows r of split s
-// (rows [s chunk, min(B, (s + 1) chunk))).  Block (32, 8): 32 columns, 8 row phases added in a
-// fixed order.
-__global__ void k_colsum_part(const bf16* __restrict__ g, int B, int C, int chunk, float* __restrict__ out,
-                              int64_t stride) {
-  __shared__ float red[8][33];
-  const int c = blockIdx.x * 32 + threadIdx.x, s = blockIdx.y;
-  const int r0 = s * chunk, r1 = min(B, r0 + chunk);
-  float acc = 0.f;
-  if (c < C)
-    for (int r = r0 + threadIdx.y; r < r1; r += 8) acc += __bfloat162float(g[(size_t)r * C + c]);
-  red[threadIdx.y][threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.y == 0 && c < C) {
-    float t = 0.f;
-    for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
-    out[(int64_t)s * stride + c] = t;
-  }
-}
-
 // Sum of the S gradient partials (for reading the gradient out).
 __global__ void k_sum_parts(const float* __restrict__ part, int S, int64_t P, float* __restrict__ out) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
@@ -291,20 +286,23 @@ __global__ void k_assemble(const float* __restrict__ feat, int F, int n_env, int
   __shared__ float z[16][kLatent];
   __shared__ int e[16];
   const int row0 = blockIdx.x * 16;
-  if (threadIdx.x < 16) {
-    const int r = row0 + threadIdx.x;
+  if (threadIdx.x < 32) {
+    const int rr = threadIdx.x & 15, r = row0 + rr;
     const uint64_t t = ctl ? (uint64_t)ctl[0] : 0ull;
     uint64_t o[4];
-    philox4x64(t, (uint64_t)r, stream_id, 0ull, seed, 1ull, o);
+    if (threadIdx.x < 16) {
+      philox4x64(t, (uint64_t)r, stream_id, 0ull, seed, 1ull, o);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) normal_pair(o[j], &z[threadIdx.x][2 * j], &z[threadIdx.x][2 * j + 1]);
-    int env = 0;
-    if (n_env > 0) {
-      philox4x64(t, (uint64_t)r, stream_id + 1, 0ull, seed, 1ull, o);
-      env = (int)(((o[0] >> 32) * (uint64_t)n_env) >> 32);
+      for (int j = 0; j < 4; ++j) normal_pair(o[j], &z[rr][2 * j], &z[rr][2 * j + 1]);
+    } else {
+      int env = 0;
+      if (n_env > 0) {
+        philox4x64(t, (uint64_t)r, stream_id + 1, 0ull, seed, 1ull, o);
+        env = (int)(((o[0] >> 32) * (uint64_t)n_env) >> 32);
+      }
+      e[rr] = env;
+      if (env_out && r < B) env_out[r] = env;
     }
-    e[threadIdx.x] = env;
-    if (env_out && r < B) env_out[r] = env;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -313,6 +311,7 @@ __global__ void k_assemble(const float* __restrict__ feat, int F, int n_env, int
     if (r >= B) break;
     const float* f = feat + (size_t)e[rr] * F;
     bf16* xr = x + (size_t)r * d0;
+#pragma unroll 4
     for (int c = lane; c < d0; c += 32) {
       float v = 0.f;
       if (c < F)
@@ -626,9 +625,7 @@ void backward(pump_mlp* m, int B, cudaStream_t s, int* launches) {
   bf16* gn = m->gB;
   for (int l = m->L - 1; l >= 0; --l) {
     const int in = m->dims[l], out = m->dims[l + 1];
-    k_colsum_part<<<dim3((out + 31) / 32, S), dim3(32, 8), 0, s>>>(g, B, out, chunk, m->part + m->offb[l], m->P);
-    ++*launches;
-    GemmArgs w{};  // dW_l = g^T h_l
+    GemmArgs w{};  // dW_l = g^T h_l, and db_l = column sums of g
     w.A = g;
     w.lda = out;
     w.B = m->act[l];
@@ -640,6 +637,7 @@ void backward(pump_mlp* m, int B, cudaStream_t s, int* launches) {
     w.out_f32 = m->part + m->offW[l];
     w.ldo = in;
     w.split_stride = m->P;
+    w.colsum = m->part + m->offb[l];
     gemm<kEpiPartial, false, false>(w, S, s, launches);
     if (l > 0) {
       GemmArgs d{};  // g_{l-1} = (g W_l) * [h_l > 0]
