@@ -30,6 +30,8 @@
 // draws with t, the loss kernel advances the counter, and Adam corrects its moments with the new
 // count.  Nothing in a step depends on a host value that changes between steps, so one step is
 // captured once as a CUDA graph and replayed.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -246,6 +248,215 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
       }
 }
 
+// ---------------------------------------------------------------------------------------------
+// GEMM on the 5th-generation tensor cores: C[M x N] = A[M x K] B[N x K]^T, both operands K-major
+// BF16, accumulator FP32 in tensor memory.  A block owns 128 rows (the accumulator's 128 TMEM
+// lanes) and tileN <= 256 columns (TMEM columns); K goes 64 at a time through kTcStages shared
+// buffers.  The tensor memory accelerator copies each operand's 64-wide K step as one box of
+// 128-byte rows in the 128-byte swizzled layout (16-byte chunks of row r XOR-permuted by r mod 8,
+// 8-row groups 1024 B apart), the layout the descriptors name; a K = 16 step of the products starts
+// 32 B further along the rows.  Rows past the end and K past the end arrive as zeros.  One thread drives the loop: it
+// starts the copies (completion counted in bytes on a per-buffer "full" mbarrier), issues the
+// tcgen05.mma instructions (M 128, N tileN, K 16), commits them to the buffer's "empty" mbarrier,
+// and refills the buffer once that one has fired; the last commit tells the epilogue that the
+// accumulator is complete.  Every mbarrier wait is bounded: on expiry the block records an error,
+// skips its epilogue and still frees its tensor memory.  The epilogue reads the accumulator with
+// tcgen05.ld (warp w: lanes 32w .. 32w + 31, 16 columns at a time) and applies the same fused
+// operations as the mma.sync kernel.
+constexpr int kTcM = 128, kTcNMax = 256, kTcK = 64, kTcStages = 4, kTcThreads = 128;
+constexpr int kTcStageBytes = (kTcM + kTcNMax) * kTcK * 2;  // 48 KB
+constexpr int kTcSmem = kTcStages * kTcStageBytes + 1024;   // + alignment
+constexpr long long kTcSpin = 1ll << 26;                    // mbarrier polls before giving up
+
+struct TcArgs {
+  int M, N, K, tileN, cols;  // cols: TMEM columns of a block (power of 2, >= 32, >= tileN)
+  const float* bias;
+  const bf16* mask;
+  bf16* out_bf16;
+  float* out_f32;
+  int ldo;
+  int* err;
+};
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzled layout: start
+// address, leading offset 16 B (not used by this layout), 8-row groups 1024 B apart, version 1,
+// layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < kTcSpin; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// One K step of both operands into a buffer: A rows m0 .. m0+127, B rows n0 .. n0+tileN-1, K groups
+// kc*8 .. kc*8+7; the full mbarrier expects the two boxes' bytes.
+__device__ __forceinline__ void tc_load(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t sa, uint32_t sb,
+                                        uint32_t full, int m0, int n0, int kc, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          sa),
+      "l"((uint64_t)tmA), "r"(kc * kTcK), "r"(m0), "r"(full)
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          sb),
+      "l"((uint64_t)tmB), "r"(kc * kTcK), "r"(n0), "r"(full)
+      : "memory");
+}
+
+template <int kEpi>
+__global__ void __launch_bounds__(kTcThreads) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
+                                                         const __grid_constant__ CUtensorMap tmB, const TcArgs g) {
+  extern __shared__ uint8_t tc_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], done;
+  __shared__ int ok_all;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * g.tileN;
+  const int nt = min(g.tileN, g.N - n0);
+  const int nk = (g.K + kTcK - 1) / kTcK;
+  const uint32_t bytes = (uint32_t)(kTcM + g.tileN) * kTcK * 2;
+  const uint32_t stage = (bytes + 1023) & ~1023u;  // buffer stride
+  if (tid == 0) {
+    for (int b = 0; b < kTcStages; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&empty[b])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&done)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    ok_all = 1;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_base)),
+                 "r"(g.cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    // kind::f16: D F32, A and B BF16, both K-major, N = nt, M = 128
+    const uint32_t idesc =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+    const uint32_t base = smem_addr(smem);
+    bool ok = true;
+    for (int c = 0; c < kTcStages && c < nk; ++c) {
+      const uint32_t sa = base + c * stage;
+      tc_load(&tmA, &tmB, sa, sa + kTcM * kTcK * 2, smem_addr(&full[c]), m0, n0, c, bytes);
+    }
+    for (int c = 0; c < nk && ok; ++c) {
+      const int st = c % kTcStages;
+      const uint32_t ph = (uint32_t)((c / kTcStages) & 1);
+      if (!mbar_wait(smem_addr(&full[st]), ph)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      const uint32_t a0 = base + st * stage, b0 = a0 + kTcM * kTcK * 2;
+#pragma unroll
+      for (int kk = 0; kk < kTcK / 16; ++kk) {
+        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem),
+            "l"(tc_desc(a0 + kk * 32)), "l"(tc_desc(b0 + kk * 32)), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_addr(&empty[st])));
+      if (c + kTcStages < nk) {
+        if (!mbar_wait(smem_addr(&empty[st]), ph)) {
+          ok = false;
+          break;
+        }
+        tc_load(&tmA, &tmB, a0, b0, smem_addr(&full[st]), m0, n0, c + kTcStages, bytes);
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_addr(&done)));
+    if (!ok) ok_all = 0;
+  }
+  __syncthreads();
+  if (!mbar_wait(smem_addr(&done), 0u)) atomicExch(&ok_all, 0);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  if (ok_all) {
+    const int r = m0 + warp * 32 + lane;
+    for (int c00 = 0; c00 < nt; c00 += 32) {
+      uint32_t vv[2][16];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (c00 + 16 * h < nt)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];\n"
+              : "=r"(vv[h][0]), "=r"(vv[h][1]), "=r"(vv[h][2]), "=r"(vv[h][3]), "=r"(vv[h][4]), "=r"(vv[h][5]),
+                "=r"(vv[h][6]), "=r"(vv[h][7]), "=r"(vv[h][8]), "=r"(vv[h][9]), "=r"(vv[h][10]), "=r"(vv[h][11]),
+                "=r"(vv[h][12]), "=r"(vv[h][13]), "=r"(vv[h][14]), "=r"(vv[h][15])
+              : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c00 + 16 * h)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+      if (r >= g.M) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+      if (c00 + 16 * h >= nt) break;
+      const uint32_t* v = vv[h];
+      const int col = n0 + c00 + 16 * h;
+      const size_t o = (size_t)r * g.ldo + col;
+      if (kEpi == kEpiBias) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(g.out_f32 + o + j) =
+              make_float4(__uint_as_float(v[j]) + g.bias[col + j], __uint_as_float(v[j + 1]) + g.bias[col + j + 1],
+                          __uint_as_float(v[j + 2]) + g.bias[col + j + 2], __uint_as_float(v[j + 3]) + g.bias[col + j + 3]);
+      } else {
+        uint32_t pk[8];
+        if (kEpi == kEpiBiasRelu) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(__uint_as_float(v[j]) + g.bias[col + j], 0.f),
+                                                           fmaxf(__uint_as_float(v[j + 1]) + g.bias[col + j + 1], 0.f));
+            pk[j / 2] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+        } else {  // kEpiMask
+          const uint4 m4a = *reinterpret_cast<const uint4*>(g.mask + o);
+          const uint4 m4b = *reinterpret_cast<const uint4*>(g.mask + o + 8);
+          const bf16* mk = reinterpret_cast<const bf16*>(&m4a);
+          const bf16* mk2 = reinterpret_cast<const bf16*>(&m4b);
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const float k0 = __bfloat162float(j < 8 ? mk[j] : mk2[j - 8]);
+            const float k1 = __bfloat162float(j < 8 ? mk[j + 1] : mk2[j - 7]);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(k0 > 0.f ? __uint_as_float(v[j]) : 0.f,
+                                                           k1 > 0.f ? __uint_as_float(v[j + 1]) : 0.f);
+            pk[j / 2] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+        }
+        *reinterpret_cast<uint4*>(g.out_bf16 + o) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4*>(g.out_bf16 + o + 8) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(g.err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(g.cols));
+}
+
 __global__ void k_to_bf16(const float* __restrict__ in, int64_t n, bf16* __restrict__ out) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
     out[k] = __float2bfloat16_rn(in[k]);
@@ -432,10 +643,41 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__
   }
 }
 
+// Where each layer's W lives in the flat vector (for the transposed BF16 copy).
+constexpr int kMaxLayers = 16;
+struct LayerTable {
+  int L;
+  int64_t offW[kMaxLayers];
+  int in[kMaxLayers], out[kMaxLayers];
+};
+
+// BF16 copies of parameter k: wb[k], and for a weight W_l[r][c] also wbt[offW_l + c out_l + r]
+// (W_l^T, K-major for the input-gradient product).
+__device__ __forceinline__ void write_bf16(int64_t k, float wk, bf16* __restrict__ wb, bf16* __restrict__ wbt,
+                                           const LayerTable& T) {
+  const bf16 q = __float2bfloat16_rn(wk);
+  wb[k] = q;
+  for (int l = 0; l < T.L; ++l) {
+    const int64_t d = k - T.offW[l];
+    if (d >= 0 && d < (int64_t)T.in[l] * T.out[l]) {
+      const int r = (int)(d / T.in[l]), c = (int)(d - (int64_t)r * T.in[l]);
+      wbt[T.offW[l] + (int64_t)c * T.out[l] + r] = q;
+      break;
+    }
+  }
+}
+
+__global__ void k_weights_bf16(const float* __restrict__ w, int64_t P, bf16* __restrict__ wb, bf16* __restrict__ wbt,
+                               const LayerTable T) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
+    write_bf16(k, w[k], wb, wbt, T);
+}
+
 // Adam over the flat parameter vector (Kingma and Ba, 2015): gradient = sum of the S partials,
-// step count t = ctl[0] (already advanced by the loss), then the BF16 copy.
+// step count t = ctl[0] (already advanced by the loss), then the BF16 copies.
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ part, int S, int64_t P, float* __restrict__ m,
-                       float* __restrict__ v, const int64_t* __restrict__ ctl, float lr, bf16* __restrict__ wb) {
+                       float* __restrict__ v, const int64_t* __restrict__ ctl, float lr, bf16* __restrict__ wb,
+                       bf16* __restrict__ wbt, const LayerTable T) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float t = (float)ctl[0];
   const float c1 = 1.f - powf(b1, t), c2 = 1.f - powf(b2, t);
@@ -448,7 +690,7 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ part, in
     v[k] = vk;
     const float wk = w[k] - lr * (mk / c1) / (sqrtf(vk / c2) + eps);
     w[k] = wk;
-    wb[k] = __float2bfloat16_rn(wk);
+    write_bf16(k, wk, wb, wbt, T);
   }
 }
 
@@ -460,6 +702,7 @@ int grid_for(int64_t n, int threads, int cap = 1184) {
 }  // namespace pump
 
 using pump::bf16;
+using pump::LayerTable;
 
 struct pump_mlp {
   int L = 0;
@@ -470,6 +713,10 @@ struct pump_mlp {
   float* m1 = nullptr;     // Adam first moments
   float* m2 = nullptr;     // Adam second moments
   bf16* wb = nullptr;      // BF16 copy of w
+  bf16* wbt = nullptr;     // BF16 W_l^T per layer (K-major operand of the input gradient)
+  int* tc_err = nullptr;   // a tensor-core block gave up waiting
+  int host_err = 0;        // a launch could not be prepared (tensor map)
+  LayerTable table{};
   int64_t* ctl = nullptr;  // [0] Adam steps taken, [1] trace base
   float* lpart = nullptr;          // per-block loss sums
   unsigned int* lticket = nullptr; // blocks of the loss kernel finished
@@ -594,6 +841,60 @@ void gemm(const GemmArgs& a, int splits, cudaStream_t s, int* launches) {
   ++*launches;
 }
 
+void note_err(pump_mlp* m, int rc) {
+  if (rc && !m->host_err) m->host_err = rc;
+}
+
+// Tensor map of a K-major BF16 operand (rows x K, row stride K): box of 64 K elements (128 B) x
+// box_rows rows, written to shared memory in the 128-byte swizzled layout.
+int tensor_map(CUtensorMap* map, const bf16* X, int rows, int K, int box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !encode) {
+      encode = nullptr;
+      return PUMP_ERR_CUDA;
+    }
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)X, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? PUMP_OK : PUMP_ERR_CUDA;
+}
+
+// Tensor-core GEMM (K-major A and B): N tile 256, 128 or 64, the widest that still gives about one
+// block per SM.
+template <int kEpi>
+int gemm_tc(pump_mlp* m, const bf16* A, const bf16* B, int M, int N, int K, const float* bias, const bf16* mask,
+            bf16* ob, float* of, int ldo, cudaStream_t s, int* launches) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc<kEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    attr = true;
+  }
+  const int mt = (M + kTcM - 1) / kTcM, sms = num_sms();
+  int tileN = kTcNMax;
+  while (tileN > 64 && (long long)mt * ((N + tileN - 1) / tileN) < sms) tileN >>= 1;
+  tileN = std::min(tileN, N);
+  CUtensorMap ta, tb;
+  int rc = tensor_map(&ta, A, M, K, kTcM);
+  if (!rc) rc = tensor_map(&tb, B, N, K, tileN);
+  if (rc) return rc;
+  int cols = 32;
+  while (cols < tileN) cols <<= 1;
+  const int stage = ((kTcM + tileN) * kTcK * 2 + 1023) & ~1023;
+  TcArgs a{M, N, K, tileN, cols, bias, mask, ob, of, ldo, m->tc_err};
+  k_gemm_tc<kEpi><<<dim3((N + tileN - 1) / tileN, mt), kTcThreads, kTcStages * stage + 1024, s>>>(ta, tb, a);
+  ++*launches;
+  return PUMP_OK;
+}
+
 // Forward pass over B rows of act[0]; outputs (FP32) in m->out.
 void forward(pump_mlp* m, int B, cudaStream_t s, int* launches) {
   for (int l = 0; l < m->L; ++l) {
@@ -608,13 +909,11 @@ void forward(pump_mlp* m, int B, cudaStream_t s, int* launches) {
     a.kchunk = a.K;
     a.bias = m->w + m->offb[l];
     a.ldo = a.N;
-    if (l + 1 < m->L) {
-      a.out_bf16 = m->act[l + 1];
-      gemm<kEpiBiasRelu, true, true>(a, 1, s, launches);
-    } else {
-      a.out_f32 = m->out;
-      gemm<kEpiBias, true, true>(a, 1, s, launches);
-    }
+    if (l + 1 < m->L)
+      note_err(m, gemm_tc<kEpiBiasRelu>(m, a.A, a.B, B, a.N, a.K, a.bias, nullptr, m->act[l + 1], nullptr, a.N, s,
+                                        launches));
+    else
+      note_err(m, gemm_tc<kEpiBias>(m, a.A, a.B, B, a.N, a.K, a.bias, nullptr, nullptr, m->out, a.N, s, launches));
   }
 }
 
@@ -640,26 +939,17 @@ void backward(pump_mlp* m, int B, cudaStream_t s, int* launches) {
     w.colsum = m->part + m->offb[l];
     gemm<kEpiPartial, false, false>(w, S, s, launches);
     if (l > 0) {
-      GemmArgs d{};  // g_{l-1} = (g W_l) * [h_l > 0]
-      d.A = g;
-      d.lda = out;
-      d.B = m->wb + m->offW[l];
-      d.ldb = in;
-      d.M = B;
-      d.N = in;
-      d.K = out;
-      d.kchunk = out;
-      d.mask = m->act[l];
-      d.out_bf16 = gn;
-      d.ldo = in;
-      gemm<kEpiMask, true, false>(d, 1, s, launches);
+      // g_{l-1} = (g W_l) * [h_l > 0]: B operand W_l^T (in x out, K-major)
+      note_err(m, gemm_tc<kEpiMask>(m, g, m->wbt + m->offW[l], B, in, out, nullptr, m->act[l], gn, nullptr, in, s,
+                                    launches));
       std::swap(g, gn);
     }
   }
 }
 
 void adam(pump_mlp* m, int B, float lr, cudaStream_t s, int* launches) {
-  k_adam<<<grid_for(m->P, 256), 256, 0, s>>>(m->w, m->part, n_splits(B), m->P, m->m1, m->m2, m->ctl, lr, m->wb);
+  k_adam<<<grid_for(m->P, 256), 256, 0, s>>>(m->w, m->part, n_splits(B), m->P, m->m1, m->m2, m->ctl, lr, m->wb,
+                                             m->wbt, m->table);
   ++*launches;
 }
 
@@ -712,6 +1002,17 @@ int enter(pump_mlp* m, void* stream) {
 int finish(pump_mlp* m) {
   PUMP_CUDA_TRY(cudaStreamSynchronize(m->s));
   PUMP_CUDA_TRY(cudaGetLastError());
+  if (m->host_err) {
+    const int rc = m->host_err;
+    m->host_err = 0;
+    return rc;
+  }
+  int e = 0;
+  PUMP_CUDA_TRY(cudaMemcpy(&e, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    cudaMemset(m->tc_err, 0, sizeof(int));
+    return PUMP_ERR_TIMEOUT;
+  }
   return PUMP_OK;
 }
 
@@ -745,10 +1046,19 @@ int pump_mlp_create(int32_t n_layers, const int32_t* dims, uint64_t seed, pump_m
   m->m2 = dmalloc<float>(m->P);
   m->wb = dmalloc<bf16>(m->P);
   m->ctl = dmalloc<int64_t>(2);
+  m->wbt = dmalloc<bf16>(m->P);
+  m->tc_err = dmalloc<int>(1);
+  if (m->tc_err) cudaMemset(m->tc_err, 0, sizeof(int));
+  m->table.L = n_layers;
+  for (int l = 0; l < n_layers; ++l) {
+    m->table.offW[l] = m->offW[l];
+    m->table.in[l] = dims[l];
+    m->table.out[l] = dims[l + 1];
+  }
   m->lpart = dmalloc<float>(kLossBlocksMax);
   m->lticket = dmalloc<unsigned int>(1);
   if (m->lticket) cudaMemset(m->lticket, 0, sizeof(unsigned int));
-  if (!m->w || !m->m1 || !m->m2 || !m->wb || !m->ctl || !m->lpart || !m->lticket ||
+  if (!m->w || !m->m1 || !m->m2 || !m->wb || !m->wbt || !m->tc_err || !m->ctl || !m->lpart || !m->lticket ||
       cudaStreamCreateWithFlags(&m->s, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming) != cudaSuccess) {
     pump_mlp_destroy(m);
@@ -779,7 +1089,7 @@ int pump_mlp_set_params(pump_mlp* m, const float* params, int64_t count) {
   PUMP_CUDA_TRY(cudaMemsetAsync(m->m1, 0, sizeof(float) * m->P, m->s));
   PUMP_CUDA_TRY(cudaMemsetAsync(m->m2, 0, sizeof(float) * m->P, m->s));
   PUMP_CUDA_TRY(cudaMemsetAsync(m->ctl, 0, sizeof(int64_t) * 2, m->s));
-  k_to_bf16<<<grid_for(m->P, 256), 256, 0, m->s>>>(m->w, m->P, m->wb);
+  k_weights_bf16<<<grid_for(m->P, 256), 256, 0, m->s>>>(m->w, m->P, m->wb, m->wbt, m->table);
   count_launches(1);
   return finish(m);
 }
@@ -1003,7 +1313,8 @@ void pump_mlp_destroy(pump_mlp* m) {
   drop_graph(m);
   free_scratch(m);
   for (void* p : {(void*)m->w, (void*)m->m1, (void*)m->m2, (void*)m->wb, (void*)m->ctl, (void*)m->feat, (void*)m->tg,
-                  (void*)m->ntg, (void*)m->trace, (void*)m->lpart, (void*)m->lticket})
+                  (void*)m->ntg, (void*)m->trace, (void*)m->lpart, (void*)m->lticket, (void*)m->wbt,
+                  (void*)m->tc_err})
     if (p) cudaFree(p);
   if (m->ev) cudaEventDestroy(m->ev);
   if (m->s) cudaStreamDestroy(m->s);
