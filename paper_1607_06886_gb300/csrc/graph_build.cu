@@ -197,12 +197,14 @@ __device__ inline bool steer_estimate(const float* xv, const float* xu, float* J
 // settles the few pairs the float test leaves undecided.  Outputs are indexed by the
 // pair and the keep bitmap is an OR, so the order of the lists does not matter.
 __global__ void k_steer_filter(const float* __restrict__ states, const int2* __restrict__ list, long long n_list,
-                               float r, uint32_t* __restrict__ surv, unsigned long long* n_surv) {
+                               float r, uint2* __restrict__ one, unsigned long long* n_one, uint4* __restrict__ two,
+                               unsigned long long* n_two, uint32_t* __restrict__ slow, unsigned long long* n_slow) {
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long q0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); q0 < n_list; q0 += stride) {
     const long long q = q0 + lane;
-    bool keep = false;
+    int kind = 0;  // 0 rejected, 1 one minimum, 2 two minima, 3 full analysis
+    float tmin[2] = {0.f, 0.f};
     if (q < n_list) {
       const int2 vu = list[q];
       float fv[6], fu[6];
@@ -211,16 +213,32 @@ __global__ void k_steer_filter(const float* __restrict__ states, const int2* __r
         fv[j] = states[6 * vu.x + j];
         fu[j] = states[6 * vu.y + j];
       }
-      float J32;
-      const bool est = steer_estimate(fv, fu, &J32);
-      keep = !(est && J32 > r * 1.001f);
+      float J32, Jmin[2];
+      int nm = 0;
+      const bool est = steer_estimate(fv, fu, &J32, tmin, &nm, Jmin);
+      if (!(est && J32 > r * 1.001f)) {
+        if (!est || nm < 1 || (nm == 2 && fabsf(Jmin[0] - Jmin[1]) <= 1e-4f * fmaxf(Jmin[0], Jmin[1])))
+          kind = 3;
+        else
+          kind = nm;
+      }
     }
-    const unsigned b = __ballot_sync(0xffffffffu, keep);
-    if (!b) continue;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(n_surv, (unsigned long long)__popc(b));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (keep) surv[base + __popc(b & ((1u << lane) - 1u))] = (uint32_t)q;
+    const unsigned b1 = __ballot_sync(0xffffffffu, kind == 1), b2 = __ballot_sync(0xffffffffu, kind == 2);
+    const unsigned b3 = __ballot_sync(0xffffffffu, kind == 3);
+    unsigned long long base1 = 0, base2 = 0, base3 = 0;
+    if (lane == 0) {
+      if (b1) base1 = atomicAdd(n_one, (unsigned long long)__popc(b1));
+      if (b2) base2 = atomicAdd(n_two, (unsigned long long)__popc(b2));
+      if (b3) base3 = atomicAdd(n_slow, (unsigned long long)__popc(b3));
+    }
+    base1 = __shfl_sync(0xffffffffu, base1, 0);
+    base2 = __shfl_sync(0xffffffffu, base2, 0);
+    base3 = __shfl_sync(0xffffffffu, base3, 0);
+    const unsigned below = (1u << lane) - 1u;
+    if (kind == 1) one[base1 + __popc(b1 & below)] = make_uint2((uint32_t)q, __float_as_uint(tmin[0]));
+    if (kind == 2)
+      two[base2 + __popc(b2 & below)] = make_uint4((uint32_t)q, __float_as_uint(tmin[0]), __float_as_uint(tmin[1]), 0u);
+    if (kind == 3) slow[base3 + __popc(b3 & below)] = (uint32_t)q;
   }
 }
 
@@ -281,68 +299,65 @@ __device__ inline void warp_append(bool take, uint32_t q, uint32_t* out, unsigne
   if (take) out[base + __popc(b & ((1u << lane) - 1u))] = q;
 }
 
-// Survivors on the common path: the float minimisers bracket the double roots (Newton from each
-// inside +-1e-5 relative, end signs checked in double).  A pair with float(Cost) < r gets its
-// duration and cost written and goes to the collision pass; pairs that need the full analysis (no
-// float estimate, a failed bracket, or two minima within 1e-4 of each other) go to
-// k_steer_slow, so the warps here run one uniform piece of FP64 work.
+// Pairs with NM float minimisers (one list per count, so a warp runs one shape of work): each
+// minimiser brackets the double root (+-1e-5 relative, end signs checked in double), and three
+// Newton steps from it (float quotient, f in double) reach the root to the last bit; a pair whose
+// bracket or convergence check fails goes to k_steer_slow.  A pair with float(Cost) < r gets its
+// duration and cost written and goes to the collision pass.
+template <int NM>
 __global__ void k_steer_pairs(const float* __restrict__ states, const int2* __restrict__ list,
-                              const uint32_t* __restrict__ surv, const unsigned long long* __restrict__ n_surv,
+                              const uint32_t* __restrict__ items, const unsigned long long* __restrict__ n_items,
                               float r, double* __restrict__ res_tau, float* __restrict__ res_cost,
                               uint32_t* __restrict__ slow, unsigned long long* n_slow, uint32_t* __restrict__ cand,
                               unsigned long long* n_cand) {
+  constexpr int kW = NM == 1 ? 2 : 4;  // words per item
   const int lane = threadIdx.x & 31;
-  const long long ns = (long long)*n_surv;
+  const long long ns = (long long)*n_items;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < ns; k0 += stride) {
     const long long k = k0 + lane;
     bool to_slow = false, edge = false;
     uint32_t q = 0;
     if (k < ns) {
-      q = surv[k];
+      q = items[k * kW];
       const int2 vu = list[q];
-      float fv[6], fu[6];
       double xv[6], xu[6];
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        fv[j] = states[6 * vu.x + j];
-        fu[j] = states[6 * vu.y + j];
-        xv[j] = (double)fv[j];
-        xu[j] = (double)fu[j];
+        xv[j] = (double)states[6 * vu.x + j];
+        xu[j] = (double)states[6 * vu.y + j];
       }
-      float J32, tmin[2], Jmin[2];
-      int nm = 0;
-      const bool est = steer_estimate(fv, fu, &J32, tmin, &nm, Jmin);
-      if (!est || nm < 1 || (nm == 2 && fabsf(Jmin[0] - Jmin[1]) <= 1e-4f * fmaxf(Jmin[0], Jmin[1]))) {
-        to_slow = true;
-      } else {
-        SteerCoef c{0.0, 0.0, 0.0};
-        for (int j = 0; j < 3; ++j) {
-          const double dp = xu[j] - xv[j], v0 = xv[3 + j], v1 = xu[3 + j];
-          c.a += v0 * v0 + v0 * v1 + v1 * v1;
-          c.b += dp * (v0 + v1);
-          c.c += dp * dp;
+      SteerCoef c{0.0, 0.0, 0.0};
+      for (int j = 0; j < 3; ++j) {
+        const double dp = xu[j] - xv[j], v0 = xv[3 + j], v1 = xu[3 + j];
+        c.a += v0 * v0 + v0 * v1 + v1 * v1;
+        c.b += dp * (v0 + v1);
+        c.c += dp * dp;
+      }
+      const SteerFma kf{4.0 * c.a, 24.0 * c.b, 36.0 * c.c, 8.0 * c.a};
+      double best_t = -1.0, best_J = 0.0;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        const double t0 = (double)__uint_as_float(items[k * kW + 1 + m]);
+        const double lo = t0 * (1.0 - 1e-5), hi = t0 * (1.0 + 1e-5);
+        if (!(st_f(c, lo) < 0.0 && st_f(c, hi) > 0.0)) to_slow = true;
+        double x = t0, step = 0.0;
+#pragma unroll
+        for (int it = 0; it < 3; ++it) {
+          step = (double)((float)st_f_fma(kf, x) / (float)st_fp_fma(kf, x));
+          x -= step;
         }
-        double best_t = -1.0, best_J = 0.0;
-        for (int m = 0; m < nm; ++m) {
-          const double t0 = (double)tmin[m];
-          const double lo = t0 * (1.0 - 1e-5), hi = t0 * (1.0 + 1e-5);
-          if (!(st_f(c, lo) < 0.0 && st_f(c, hi) > 0.0)) {
-            to_slow = true;
-            break;
-          }
-          const double t = st_root_fq(c, lo, hi);
-          const double Jt = st_J_sum(xv, xu, t);
-          if (best_t < 0.0 || Jt < best_J || (Jt == best_J && t < best_t)) {
-            best_t = t;
-            best_J = Jt;
-          }
+        if (!(fabs(step) <= 4.0e-16 * fabs(x) && x > lo && x < hi)) to_slow = true;
+        const double Jt = st_J_sum(xv, xu, x);
+        if (best_t < 0.0 || Jt < best_J || (Jt == best_J && x < best_t)) {
+          best_t = x;
+          best_J = Jt;
         }
-        if (!to_slow && __double2float_rn(best_J) < r) {
-          res_tau[q] = best_t;
-          res_cost[q] = __double2float_rn(best_J);
-          edge = true;
-        }
+      }
+      if (!to_slow && __double2float_rn(best_J) < r) {
+        res_tau[q] = best_t;
+        res_cost[q] = __double2float_rn(best_J);
+        edge = true;
       }
     }
     warp_append(to_slow, q, slow, n_slow);
@@ -709,11 +724,11 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   const int sms = num_sms();
   // node flags (validity) and goal flags were filled by the caller's kernels
   // prefilter: count per row, scan, allocate, list
-  unsigned long long* d_count = (unsigned long long*)dev_alloc(sizeof(unsigned long long) * 4, s);
+  unsigned long long* d_count = (unsigned long long*)dev_alloc(sizeof(unsigned long long) * 5, s);
   int32_t* rcnt = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)n, s);
   long long* roff = (long long*)dev_alloc(sizeof(long long) * (size_t)(n + 1), s);
   if (!d_count || !rcnt || !roff) return PUMP_ERR_OOM;
-  PUMP_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * 4, s));
+  PUMP_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * 5, s));
   const int grid = (int)std::min<long long>(((long long)n * 32 + kBlock - 1) / kBlock, (long long)sms * 16);
   k_prefilter<false><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, rcnt, nullptr, nullptr);
   note_launch();
@@ -742,14 +757,23 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   uint32_t* surv = nullptr;
   if (n_list) {
     if (n_list > 0xFFFFFFFFull) return PUMP_ERR_CAPACITY;
-    surv = (uint32_t*)dev_alloc(sizeof(uint32_t) * n_list * 3, s);
+    // word offsets: slow [0, n), cand [n, 2n), one (uint2, 8-byte aligned), two (uint4, 16-byte aligned)
+    const unsigned long long off_one = (3 * n_list + 1) & ~1ull;
+    const unsigned long long off_two = (off_one + 2 * n_list + 3) & ~3ull;
+    surv = (uint32_t*)dev_alloc(sizeof(uint32_t) * (off_two + 4 * n_list), s);
     if (!surv) return PUMP_ERR_OOM;
     uint32_t* surv_slow = surv + n_list;
     uint32_t* cand = surv + 2 * n_list;
-    k_steer_filter<<<glist, kBlock, 0, s>>>(g->states, list, (long long)n_list, g->radius, surv, d_count);
+    uint2* one = reinterpret_cast<uint2*>(surv + off_one);
+    uint4* two = reinterpret_cast<uint4*>(surv + off_two);
+    k_steer_filter<<<glist, kBlock, 0, s>>>(g->states, list, (long long)n_list, g->radius, one, d_count, two,
+                                            d_count + 4, surv_slow, d_count + 1);
     note_launch();
-    k_steer_pairs<<<sms * 4, kBlock, 0, s>>>(g->states, list, surv, d_count, g->radius, res_tau, res_cost, surv_slow,
-                                             d_count + 1, cand, d_count + 2);
+    k_steer_pairs<1><<<sms * 4, kBlock, 0, s>>>(g->states, list, reinterpret_cast<const uint32_t*>(one), d_count,
+                                                g->radius, res_tau, res_cost, surv_slow, d_count + 1, cand, d_count + 2);
+    note_launch();
+    k_steer_pairs<2><<<sms * 4, kBlock, 0, s>>>(g->states, list, reinterpret_cast<const uint32_t*>(two), d_count + 4,
+                                                g->radius, res_tau, res_cost, surv_slow, d_count + 1, cand, d_count + 2);
     note_launch();
     k_steer_slow<<<sms, kBlock, 0, s>>>(g->states, list, surv_slow, d_count + 1, g->radius, res_tau, res_cost, cand,
                                         d_count + 2);
