@@ -29,9 +29,31 @@ void* g_ctx = nullptr;
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// The stream-ordered pool of each device the library allocates on keeps what it has (release
+// threshold raised once per device): by default it hands memory back at every synchronisation and
+// the next query pays to map it again.
+static void keep_pool_memory() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  const unsigned long long bit = 1ull << dev;
+  if (done.load(std::memory_order_relaxed) & bit) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done.fetch_or(bit, std::memory_order_relaxed);
+}
+
 void* dev_alloc(size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
   if (g_alloc) return g_alloc(bytes, (void*)s, g_ctx);
+  keep_pool_memory();
   void* p = nullptr;
   if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
     cudaGetLastError();
