@@ -215,7 +215,8 @@ def main():
                     help="queries of the HSMC leg (CP-hat vs Monte Carlo for box and half-space masks); 0 skips it")
     ap.add_argument("--serve-requests", type=int, default=150,
                     help="requests of the served leg (Poisson arrivals, continuous batching); 0 skips it")
-    ap.add_argument("--serve-rate", type=float, default=50.0, help="arrival rate of the served leg (requests/s)")
+    ap.add_argument("--serve-rate", default="50,200",
+                    help="arrival rates of the served leg (requests/s, comma-separated)")
     ap.add_argument("--learned-envs", type=int, default=10000,
                     help="training environments of the learned-proposal leg (plain PUMP solutions, then training "
                          "and a paired held-out evaluation); 0 skips it")
@@ -356,7 +357,8 @@ def main():
     if args.batch_queries > 0:
         line["batched"] = batched_measure(pump, args, dev, flush, rank, ws)
     if args.serve_requests > 0:
-        line["served"] = served_measure(pump, args, rank, ws)
+        rates = [float(x) for x in str(args.serve_rate).split(",") if x.strip()]
+        line["served"] = [served_measure(pump, args, rank, ws, r) for r in rates]
     if args.hsmc_seeds > 0:
         line["hsmc"] = hsmc_measure(pump, args, dev, flush)
     if args.learned_envs > 0 and rank == 0:
@@ -503,14 +505,14 @@ def hsmc_measure(pump, args, dev, flush):
             "note": "cp_hat = particle estimate used by Explore (N particles); cp_mc = 10^4-rollout Monte Carlo of the same plan"}
 
 
-def served_measure(pump, args, rank, ws):
-    """The served form: args.serve_requests requests with Poisson arrivals at args.serve_rate per
+def served_measure(pump, args, rank, ws, rate):
+    """The served form: args.serve_requests requests with Poisson arrivals at `rate` per
     second (samples U{1000..16000}, boxes U{5..50}, N in {64, 128, 256}, W = 10, CP 1 %), each a
     whole query from host arrays (graph build + masks + Explore + PlanSelection with MC).  Latency
     is arrival to result.  Continuous batching (8 slots, requests admitted as slots and device
     memory free up) against the plain sequential FIFO (1 slot), same arrivals."""
     from paper_1607_06886_gb300 import inputs
-    R, rate = args.serve_requests, args.serve_rate
+    R = args.serve_requests
     wls = inputs.batch_workloads(R, seed=2000 * (rank + 1), n_range=(1000, 16000))
     gaps = np.random.default_rng(12345 + rank).exponential(1.0 / rate, size=R)
     arrivals = np.cumsum(gaps) - gaps[0]
