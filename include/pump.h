@@ -112,6 +112,8 @@ typedef struct {
   float ms_masks;         /* device time of the edge-mask step                             */
   float ms_explore;       /* device time of Explore                                        */
   float ms_select;        /* device time of PlanSelection                                  */
+  int32_t fused;          /* 1: the edge masks ran inside the Explore launch (ms_masks then
+                             covers only what precedes it, ms_explore both)               */
 } pump_plan_result;
 
 /* --------------------------------------------------------------------------
@@ -206,7 +208,11 @@ int pump_explore(pump_graph* g, const pump_plan_params* params, float radius, pu
  * descending cost then ascending id; 1-based bisection with MC(P_m) > alpha
  * moving u = m - 1, else l = m; failure if the final MC(P_m) > alpha.
  * Smoothing is not applied.  `path` (host, capacity path_cap) receives the
- * node ids of the selected plan from x_init.  `out` is written on PUMP_OK
+ * node ids of the selected plan from x_init.  From a graph's second query on
+ * (its edge order laid out once, then reused), the box masks run inside the
+ * Explore launch where the device allows it (out->fused); the environment
+ * variable PUMP_FUSED_MASKS=0 keeps them separate, =1 fuses from the first
+ * query.  Results are the same either way.  `out` is written on PUMP_OK
  * and on PUMP_ERR_INFEASIBLE (out->status tells which).  Synchronises.
  * Errors: those of pump_explore, plus INFEASIBLE (no certified plan).
  */
@@ -339,7 +345,11 @@ enum {
   PUMP_EXPORT_EDGE_BOX = 20,      /* float[E][6] lo xyz, hi xyz: box holding every particle
                                      position of the edge (graph build; pump_edge_masks skips
                                      the obstacles it misses) */
-  PUMP_EXPORT_NOMINAL_VEL = 21    /* float[E][W][3] nominal velocity at the waypoints */
+  PUMP_EXPORT_NOMINAL_VEL = 21,   /* float[E][W][3] nominal velocity at the waypoints */
+  PUMP_EXPORT_EDGE_ORDER = 22     /* int32[E][2] (edge, source row) in the order the masks of
+                                     the fused launch are computed: rows by increasing
+                                     shortest-path cost from the start, a row's edges in order
+                                     (set by the first pump_plan that fuses; INVALID_ARG before) */
 };
 int pump_export(pump_graph* g, int32_t what, void* host_buf, size_t cap, size_t* needed);
 

@@ -1,16 +1,8 @@
 // Edge particle collision masks (Section III-B, with a direct particle-in-box
-// test in place of the half-space test).
-//
-// The particle deviations of an edge depend on its step h and the common
-// normals, not on the obstacles.  Graph build therefore records, per edge, a
-// box holding every particle position (nominal waypoints widened by the
-// largest |d0| of any particle).  Per query, a warp takes one edge: lanes test
-// the obstacle boxes against that box, and an edge with no box left gets zero
-// mask words without running its particles.  Otherwise lane l runs particle
-// 32*word + l through the recurrence once per word and tests the left boxes;
-// the mask word is the warp ballot of the per-particle OR over waypoints and
-// boxes.  The normals xi_t[k][axis][i] and the boxes sit in shared memory; the
-// grid is persistent over the edges.
+// test in place of the half-space test): the graph-build bound pass, the query
+// pass over every edge (a warp per edge, the per-edge routine in mask_dev.cuh)
+// and the Half-Space Monte Carlo forms.  The normals xi_t[k][axis][i] and the
+// boxes sit in shared memory; the grids are persistent over the edges.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,14 +10,13 @@
 #include <mutex>
 #include <vector>
 
+#include "mask_dev.cuh"
 #include "pump_internal.cuh"
 
 namespace pump {
 namespace {
 
 constexpr int kWarps = 8;
-constexpr int kCandCap = 64;
-constexpr int kBoxStride = 8;  // floats per box in shared memory: lo xyz, hi xyz, 2 pad
 constexpr int kHsStage = 128;  // HSMC: half-spaces of one edge staged in shared memory per warp
 
 // Shared memory of the HSMC query pass before the normals: staged half-spaces and waypoint offsets.
@@ -33,26 +24,11 @@ __host__ __device__ constexpr size_t edge_mask_hs_fixed_smem() {
   return (sizeof(float4) * kWarps * kHsStage + sizeof(int32_t) * kWarps * (kMaxWaypoints + 1) + 15) & ~(size_t)15;
 }
 
-// Shared memory of the query pass before the normals: boxes, per-warp candidate lists and
-// per-warp waypoint box masks (16-byte aligned end).
-__host__ __device__ constexpr size_t edge_mask_fixed_smem(int nb) {
-  return (sizeof(float) * kBoxStride * (size_t)nb + sizeof(int) * kWarps * kCandCap +
-          sizeof(uint32_t) * kWarps * kMaxWaypoints + 15) & ~(size_t)15;
-}
+using maskdev::dev_init;
+using maskdev::dev_step;
+using maskdev::kBoxStride;
 
-__device__ __forceinline__ void dev_init(const float* linf, float2 x, float& d0, float& d1) {
-  d0 = __fmul_rn(linf[0], x.x);
-  d1 = fmaf(linf[1], x.x, __fmul_rn(linf[2], x.y));
-}
-
-__device__ __forceinline__ void dev_step(const float* P, const float* L, float2 x, float& d0, float& d1) {
-  float n0 = __fmul_rn(L[0], x.x);
-  float n1 = fmaf(L[1], x.x, __fmul_rn(L[2], x.y));
-  float e0 = fmaf(P[0], d0, fmaf(P[1], d1, n0));
-  float e1 = fmaf(P[2], d0, fmaf(P[3], d1, n1));
-  d0 = e0;
-  d1 = e1;
-}
+__host__ __device__ constexpr size_t edge_mask_fixed_smem(int nb) { return maskdev::fixed_smem(nb, kWarps); }
 
 // Graph-build pass (obstacle independent): per edge the largest |d0| over all particles,
 // waypoints and axes, as float bits (atomicMax over the edge's words).
@@ -112,75 +88,7 @@ __global__ void k_edge_ibox(const float* __restrict__ nom, const unsigned int* _
   }
 }
 
-// NW mask words of one edge: lane l advances particles 32 (w0 + j) + l, j < NW, side by side
-// through waypoints 1..k_last and tests the boxes left at each; the words are the warp ballots.
-// The warp stops early once every lane's particles have hit.
-template <int NW>
-__device__ __forceinline__ void word_pass(const float2* __restrict__ xi, int N, int W, const float (&P)[4],
-                                          const float (&L)[3], const float (&linf)[3], const float* __restrict__ nm,
-                                          int k_last, bool narrow, const uint32_t* wm, const int* my_cand, bool all,
-                                          int nc, const float* boxes, int w0, int lane, uint32_t* out) {
-  float d0[NW][3], d1[NW][3];
-  bool hit[NW];
-  const float2* xq = xi + w0 * 32 + lane;
-#pragma unroll
-  for (int j = 0; j < NW; ++j) {
-    hit[j] = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dev_init(linf, xq[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
-  }
-  for (int k = 1; k <= k_last; ++k) {
-    const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
-    const float2* xk = xq + (size_t)k * 3 * N;
-    float p[NW][3];
-#pragma unroll
-    for (int j = 0; j < NW; ++j) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) dev_step(P, L, xk[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
-      p[j][0] = __fadd_rn(n0, d0[j][0]);
-      p[j][1] = __fadd_rn(n1, d0[j][1]);
-      p[j][2] = __fadd_rn(n2, d0[j][2]);
-    }
-    unsigned bits = narrow ? wm[k - 1] : 0u;
-    int c = 0;
-    for (;;) {
-      int o;
-      if (narrow) {
-        if (!bits) break;
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        o = my_cand[b];
-      } else {
-        if (c >= nc) break;
-        o = all ? c : my_cand[c];
-        ++c;
-      }
-      const float4 b0 = *reinterpret_cast<const float4*>(boxes + kBoxStride * o);      // lo x, y, z, hi x
-      const float2 b1 = *reinterpret_cast<const float2*>(boxes + kBoxStride * o + 4);  // hi y, z
-#pragma unroll
-      for (int j = 0; j < NW; ++j)
-        hit[j] = hit[j] || (b0.x <= p[j][0] && p[j][0] <= b0.w && b0.y <= p[j][1] && p[j][1] <= b1.x &&
-                            b0.z <= p[j][2] && p[j][2] <= b1.y);
-    }
-    bool done = true;
-#pragma unroll
-    for (int j = 0; j < NW; ++j) done = done && hit[j];
-    if (__all_sync(0xffffffffu, done)) break;
-  }
-#pragma unroll
-  for (int j = 0; j < NW; ++j) {
-    const unsigned bits = __ballot_sync(0xffffffffu, hit[j]);
-    if (lane == 0) out[w0 + j] = bits;
-  }
-}
-
-// Query pass: a warp per edge.  Boxes that miss the edge's position box cannot hold any of its
-// particle positions; an edge with none left gets zero mask words without running the
-// particles.  With at most 32 boxes left, the warp narrows them per waypoint: at waypoint k every
-// particle position lies in [nominal_k - M, nominal_k + M] (M = the edge's largest |d0|, rounded
-// the way the positions are), so only boxes meeting that box are tested there, and the particles
-// run only up to the last waypoint that has one.  Each 32-particle word then runs the
-// recurrence once and its lanes stop testing when all of them have hit.
+// Query pass: a warp per edge (maskdev::edge_mask_one), grid persistent over the edges.
 #ifndef PUMP_MASK_MIN_BLOCKS
 #define PUMP_MASK_MIN_BLOCKS 4  // 64 registers: four 256-thread blocks per SM (measured best)
 #endif
@@ -195,75 +103,18 @@ __global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask
   extern __shared__ __align__(16) unsigned char smem[];
   float* boxes = reinterpret_cast<float*>(smem);  // kBoxStride floats per box (16-byte aligned rows)
   int* cand = reinterpret_cast<int*>(boxes + kBoxStride * nb);
-  uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kWarps * kCandCap);
+  uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kWarps * maskdev::kCandCap);
   float2* xi_s = reinterpret_cast<float2*>(smem + edge_mask_fixed_smem(nb));
-  for (int k = threadIdx.x; k < kBoxStride * nb; k += blockDim.x) {
-    const int o = k / kBoxStride, c = k - o * kBoxStride;
-    boxes[k] = c < 6 ? boxes_g[6 * o + c] : 0.f;
-  }
   const int xi_n = (W + 1) * 3 * N;
-  if (kSmemXi)
-    for (int k = threadIdx.x; k < xi_n; k += blockDim.x) xi_s[k] = xi_g[k];
+  maskdev::stage(boxes_g, nb, boxes, xi_g, kSmemXi ? xi_s : nullptr, xi_n);
   __syncthreads();
   const float2* xi = kSmemXi ? xi_s : xi_g;
   const float linf[3] = {linf_g[0], linf_g[1], linf_g[2]};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int* my_cand = cand + warp * kCandCap;
+  int* my_cand = cand + warp * maskdev::kCandCap;
   uint32_t* wm = wmask_all + warp * kMaxWaypoints;
-  for (long long e = (long long)blockIdx.x * kWarps + warp; e < E; e += (long long)gridDim.x * kWarps) {
-    const float* ib = ibox_g + 6 * e;
-    const float lo0 = ib[0], lo1 = ib[1], lo2 = ib[2], hi0 = ib[3], hi1 = ib[4], hi2 = ib[5];
-    int n_cand = 0;
-    for (int base = 0; base < nb; base += 32) {
-      const int o = base + lane;
-      bool ov = false;
-      if (o < nb) {
-        const float* b = boxes + kBoxStride * o;
-        ov = b[0] <= hi0 && lo0 <= b[3] && b[1] <= hi1 && lo1 <= b[4] && b[2] <= hi2 && lo2 <= b[5];
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, ov);
-      const int pos = n_cand + __popc(bal & ((1u << lane) - 1u));
-      if (ov && pos < kCandCap) my_cand[pos] = o;
-      n_cand += __popc(bal);
-    }
-    __syncwarp();
-    const float* nm = nom + (size_t)e * W * 3;
-    int k_last = W;
-    const bool narrow = n_cand > 0 && n_cand <= 32;
-    if (narrow) {
-      // boxes per waypoint: lane c tests candidate c against waypoint k's position box
-      const float M = __uint_as_float(dmax[e]);
-      const float* bc = boxes + kBoxStride * my_cand[lane < n_cand ? lane : 0];
-      k_last = 0;
-      for (int k = 1; k <= W; ++k) {
-        const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
-        const bool ov = lane < n_cand && bc[0] <= __fadd_rn(n0, M) && __fsub_rn(n0, M) <= bc[3] &&
-                        bc[1] <= __fadd_rn(n1, M) && __fsub_rn(n1, M) <= bc[4] &&
-                        bc[2] <= __fadd_rn(n2, M) && __fsub_rn(n2, M) <= bc[5];
-        const unsigned m = __ballot_sync(0xffffffffu, ov);
-        if (lane == 0) wm[k - 1] = m;
-        if (m) k_last = k;
-      }
-      __syncwarp();
-    }
-    if (n_cand == 0 || k_last == 0) {
-      for (int word = lane; word < w; word += 32) mask[(size_t)e * w + word] = 0u;
-      continue;
-    }
-    const bool all = n_cand > kCandCap;
-    const int nc = all ? nb : n_cand;
-    const float P[4] = {phi[4 * e], phi[4 * e + 1], phi[4 * e + 2], phi[4 * e + 3]};
-    const float L[3] = {Lg[3 * e], Lg[3 * e + 1], Lg[3 * e + 2]};
-    uint32_t* out = mask + (size_t)e * w;
-    int w0 = 0;
-    for (; w0 + 4 <= w; w0 += 4) word_pass<4>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
-    if (w0 + 2 <= w) {
-      word_pass<2>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
-      w0 += 2;
-    }
-    if (w0 < w) word_pass<1>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
-    __syncwarp();
-  }
+  for (long long e = (long long)blockIdx.x * kWarps + warp; e < E; e += (long long)gridDim.x * kWarps)
+    maskdev::edge_mask_one(e, xi, N, W, phi, Lg, nom, linf, ibox_g, dmax, boxes, nb, w, my_cand, wm, lane, mask);
 }
 
 // ---------------------------------------------------------------- Half-Space Monte Carlo

@@ -682,17 +682,24 @@ int explore_blocks() {
 
 int plan_explore_cluster(const ExploreArgs& A, int* nr, bool* dsm);
 int run_explore_cluster(pump_graph* g, const ExploreArgs& A, int nr, bool dsm, cudaStream_t s);
+int run_explore_fused(pump_graph* g, const ExploreArgs& A, int nr, bool dsm, cudaStream_t s, bool* launched);
 
 // Explore kernels for one run.  mode 0: the thread-block cluster kernel (explore_cluster.cu)
 // where the device can co-schedule one, else the grid kernel; 1: the grid kernel; 2: the
 // phases as separate launches.
-int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStream_t s) {
+int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStream_t s, bool masks_pending) {
   const bool stepwise = mode == 2;
   int cl_nr = 0;
   bool cl_dsm = false;
   if (mode == 0) {
     const int rc = plan_explore_cluster(A, &cl_nr, &cl_dsm);
     if (rc) return rc;
+  }
+  g->last_fused = false;
+  if (masks_pending && !(cl_nr > 0 && cl_dsm)) {  // the fused form needs the on-chip cluster form
+    const int rc = compute_edge_masks(g, s);
+    if (rc) return rc;
+    masks_pending = false;
   }
   if (!(cl_nr > 0 && cl_dsm)) {  // the cluster kernel keeps mbest on chip and fills it itself
     const int64_t mb = (int64_t)g->n * A.kstride;
@@ -708,6 +715,17 @@ int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStrea
   PUMP_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   const int sms = num_sms();
   if (cl_nr > 0) {
+    if (masks_pending) {
+      bool launched = false;
+      int rc = run_explore_fused(g, A, cl_nr, cl_dsm, s, &launched);
+      if (rc) return rc;
+      if (launched) {
+        g->last_fused = true;
+        return PUMP_OK;
+      }
+      rc = compute_edge_masks(g, s);  // the device cannot run the fused form
+      if (rc) return rc;
+    }
     const int rc = run_explore_cluster(g, A, cl_nr, cl_dsm, s);
     if (rc) return rc;
     PUMP_CUDA_TRY(cudaGetLastError());

@@ -48,6 +48,23 @@
 // Every value that decides control flow (group size, candidate count, group
 // index, stop, status) is computed identically by every CTA from the same
 // counts, so all CTAs take the same number of barriers.
+//
+// Fused form (k_explore_fused).  The edge masks of a query and Explore share
+// one cooperative launch: cluster 0 runs Explore, the CTAs of every other
+// cluster compute masks (the per-edge routine of mask_dev.cuh) for the edges
+// in a fixed order, rows by increasing shortest-path cost from the start, and
+// count the finished edges of each row.  A plan of group i costs at most
+// thr_{i+1}, so its node lies within that cost of the start, and the rows a
+// group expands come early in the order; phase A waits (bounded) for the row
+// count of each member to reach its degree before reading the row's masks.
+// The Explore cluster computes the first positions of the order itself (one
+// edge per warp) before it starts, so the first groups find their rows done.
+// Masks are read through L2 (the workers write them during the launch).  A
+// wait that runs out sets an error flag that phase B publishes, and every CTA
+// ends the run with PUMP_ERR_TIMEOUT after the same phase C.  Counts are not
+// cleared between runs: run e expects (e - 1) x degree + degree.  Each worker
+// warp also counts itself when done; a CTA that sees every worker warp done
+// (phase B, an unordered read made an acquire by a fence) skips the waits.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -56,6 +73,7 @@
 #include <mutex>
 #include <vector>
 
+#include "mask_dev.cuh"
 #include "pump_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -90,6 +108,7 @@ struct Pub {
   int32_t minb;      // least group index of an open undominated plan seen by the CTA
   int32_t min_open;  // least id of an older open undominated plan (INT_MAX if none)
   uint32_t stop;     // bit q: a member of group i+1+q is a goal plan with popc < K_min
+  int32_t err;       // a wait for a row's masks ran out (fused form)
   int32_t ocnt[kWin], ncnt[kWin];
   unsigned long long odeg[kWin], ndeg[kWin];
 };
@@ -141,7 +160,9 @@ struct CSmem {
   Pub pub;     // this CTA's counts (accumulated in phase B, read by every CTA in phase C)
   PubS pubs_s; // the same for a group index beyond the window
   // cluster-wide values of phase C, derived by warp 0 and read by the whole CTA
-  int32_t b_nbk, b_min_open, b_before_s, b_total_s, b_before_o, b_total_o, b_before_n, b_total_n, b_stop, b_fast;
+  int32_t b_nbk, b_min_open, b_before_s, b_total_s, b_before_o, b_total_o, b_before_n, b_total_n, b_stop, b_fast, b_err;
+  int32_t werr;        // this CTA: a wait for a row's masks ran out (fused form)
+  int32_t rows_ready;  // this CTA saw every worker warp finished: no more waits (fused form)
   long long b_dbefore_o, b_dtotal_o, b_dbefore_n, b_dtotal_n, b_per_n;
   ExploreArgs args;  // the query's arguments (batched form)
   int32_t qnext;     // query index taken by the cluster (batched form; written by CTA 0)
@@ -274,6 +295,36 @@ struct CCand {
   float cost;
 };
 
+// Release add: the warp's mask writes (ordered before it by the warp barrier) are visible to a
+// thread whose acquire observes the new count.
+__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Fused form: waits until the mask workers have finished the deg edges of row x in this run
+// (count - (epoch_m1 x deg) reaches deg, mod 2^32; every calling thread acquires the count
+// itself).  After limit polls it sets *err and returns; once *err is set (a wait of this CTA ran
+// out) it returns at once, so one lost row costs one limit.
+__device__ __noinline__ void row_wait(const uint32_t* rowcnt, int32_t x, uint32_t deg, uint32_t epoch_m1,
+                                      long long limit, int32_t* err) {
+  volatile int32_t* verr = err;
+  const uint32_t base = epoch_m1 * deg;
+  long long it = 0;
+  while (ld_acquire_u32(rowcnt + x) - base < deg) {
+    if (*verr || ++it > limit) {
+      *verr = 1;
+      return;
+    }
+    __nanosleep(128);
+  }
+}
+
 // Target of edge e: node, cost bits, row start, out-degree | goal bit.
 __device__ __forceinline__ int4 edge_target(const ExploreArgs& A, int32_t e) {
   if (A.etgt) return __ldg(A.etgt + e);
@@ -284,7 +335,7 @@ __device__ __forceinline__ int4 edge_target(const ExploreArgs& A, int32_t e) {
 }
 
 // Candidate c of the current group, recomputed from the group list (chunks that do not fit).
-__device__ __noinline__ CCand cand_at_c(const ExploreArgs& A, int64_t c, int32_t g) {
+__device__ __noinline__ CCand cand_at_c(const ExploreArgs& A, int64_t c, int32_t g, int32_t* err) {
   int lo = 0, hi = g;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -292,7 +343,9 @@ __device__ __noinline__ CCand cand_at_c(const ExploreArgs& A, int64_t c, int32_t
   }
   CCand q;
   const int4 gi = __ldcg(A.ginfo + lo);
-  const int32_t e = gi.z + (int32_t)(c - ld64(A.goff + lo));
+  const int64_t off = ld64(A.goff + lo);
+  if (A.rowcnt) row_wait(A.rowcnt, gi.y, (uint32_t)(ld64(A.goff + lo + 1) - off), A.epoch_m1, A.spin_limit, err);
+  const int32_t e = gi.z + (int32_t)(c - off);
   const int4 t = edge_target(A, e);
   q.x = t.x;
   q.parent = gi.x;
@@ -303,7 +356,7 @@ __device__ __noinline__ CCand cand_at_c(const ExploreArgs& A, int64_t c, int32_t
   int pc = 0;
   const uint32_t* pm = A.mask + (size_t)gi.x * A.w;
   const uint32_t* em = A.emask + (size_t)e * A.w;
-  for (int j = 0; j < A.w; ++j) pc += __popc(ldu(pm + j) | em[j]);
+  for (int j = 0; j < A.w; ++j) pc += __popc(ldu(pm + j) | ldu(em + j));
   q.pc = pc;
   return q;
 }
@@ -391,6 +444,8 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
       const int64_t lo = max(lo_s, c0), hi = min(hi_s, c1);
       if (lo >= hi) continue;
       const int32_t p = gi.x, r0 = gi.z;
+      if (A.rowcnt && !sm->rows_ready)
+        row_wait(A.rowcnt, gi.y, (uint32_t)(hi_s - lo_s), A.epoch_m1, A.spin_limit, &sm->werr);
       const float pcost = __int_as_float(gi.w);
       const uint32_t* pm = A.mask + (size_t)p * w;
       if (!local && w <= 4) {
@@ -409,12 +464,12 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
         if (w <= 4) {
           uint4 em;
           if (w == 4) {
-            em = __ldg(reinterpret_cast<const uint4*>(A.emask) + e);
+            em = __ldcg(reinterpret_cast<const uint4*>(A.emask) + e);
           } else {
             const uint32_t* ep = A.emask + (size_t)e * w;
-            em.x = ep[0];
-            em.y = w > 1 ? ep[1] : 0u;
-            em.z = w > 2 ? ep[2] : 0u;
+            em.x = ldu(ep);
+            em.y = w > 1 ? ldu(ep + 1) : 0u;
+            em.z = w > 2 ? ldu(ep + 2) : 0u;
             em.w = 0u;
           }
           const uint4 m = make_uint4(pmv.x | em.x, pmv.y | em.y, pmv.z | em.z, pmv.w | em.w);
@@ -422,7 +477,7 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
           sm->cmask[jl] = m;
         } else {
           const uint32_t* em = A.emask + (size_t)e * w;
-          for (int j = 0; j < w; ++j) pc += __popc(ldu(pm + j) | em[j]);
+          for (int j = 0; j < w; ++j) pc += __popc(ldu(pm + j) | ldu(em + j));
         }
         sm->cx[jl] = t.x;
         sm->cpar[jl] = p;
@@ -439,7 +494,7 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
     }
   } else if (n > 0) {
     for (int64_t c = c0 + threadIdx.x; c < c1; c += kCT) {
-      const CCand q = cand_at_c(A, c, S.g);
+      const CCand q = cand_at_c(A, c, S.g, &sm->werr);
       if (q.pc < A.kmax) {
         atomicMin(mb_row<kDsm>(A, cl, mbl, q.x) + q.pc, __float_as_uint(q.cost));
         ++kept;
@@ -479,6 +534,11 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
   const int n = (int)(c1 - c0);
   const bool fits = n <= kCCap;
   int32_t surv = 0, minb = kNoBucket, min_open = INT_MAX;
+  // fused form: whether every worker warp has finished, read without ordering now (its latency
+  // hides behind this phase) and made an acquire by a fence below if so
+  uint32_t done_seen = 0;
+  const bool poll_done = A.done && threadIdx.x == 0 && !sm->rows_ready;
+  if (poll_done) done_seen = *reinterpret_cast<const volatile uint32_t*>(A.done);
   for (int t0 = 0; t0 < n; t0 += kCT) {
     const int jl = t0 + threadIdx.x;
     bool keep = false;
@@ -492,7 +552,7 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
         q.cost = sm->ccost[jl];
         q.dg = sm->cdg[jl];
       } else {
-        q = cand_at_c(A, c0 + jl, S.g);
+        q = cand_at_c(A, c0 + jl, S.g, &sm->werr);
       }
       keep = q.pc < A.kmax && !dominated_c<kDsm>(A, cl, mbl, q.x, q.pc, q.cost);
       if (keep) {
@@ -537,8 +597,13 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
     }
     bucket_add(eff >= 0, eff - S.i - 1, deg, goal && pc < A.kmin, sm->pub.ocnt, sm->pub.odeg, &sm->pub.stop);
   }
+  if (poll_done && done_seen == A.done_target) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    sm->rows_ready = 1;  // read by phase A after this phase's barriers
+  }
   creduce(surv, minb, min_open);
   if (threadIdx.x == 0) {
+    sm->pub.err = sm->werr;
     sm->pub.surv = surv;
     sm->pub.minb = minb;
     sm->pub.min_open = min_open;
@@ -579,7 +644,7 @@ __device__ __noinline__ void c_recount(const ExploreArgs& A, CSmem* sm, uint32_t
       dg = sm->cdg[jl];
       pc = sm->cpc[jl];
     } else {
-      const CCand q = cand_at_c(A, c0 + jl, S.g);
+      const CCand q = cand_at_c(A, c0 + jl, S.g, &sm->werr);
       const bool keep = q.pc < A.kmax && !dominated_c<kDsm>(A, cl, mbl, q.x, q.pc, q.cost);
       eff = keep ? eff_new(sm, A, S.i, q.cost) : -1;
       dg = q.dg;
@@ -674,6 +739,7 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
     int32_t minb = on ? rp->minb : kNoBucket;
     int32_t mo = on ? rp->min_open : INT_MAX;
     const int32_t sv = on ? rp->surv : 0;
+    const bool werr = __any_sync(0xffffffffu, on && rp->err != 0);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
@@ -711,6 +777,7 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
       sm->b_dbefore_n = dbn;
       sm->b_dtotal_n = dtn;
       sm->b_stop = stp ? 1 : 0;
+      sm->b_err = werr ? 1 : 0;
     }
   }
   __syncthreads();
@@ -801,7 +868,7 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
           q.dg = sm->cdg[jl];
         }
       } else {
-        q = cand_at_c(A, c0 + jl, S.g);
+        q = cand_at_c(A, c0 + jl, S.g, &sm->werr);
         keep = q.pc < A.kmax && !dominated_c<kDsm>(A, cl, mbl, q.x, q.pc, q.cost);
         if (keep) eff = eff_new(sm, A, S.i, q.cost);
       }
@@ -833,7 +900,7 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
       } else {
         const uint32_t* pm = A.mask + (size_t)q.parent * A.w;
         const uint32_t* em = A.emask + (size_t)q.edge * A.w;
-        for (int j = 0; j < A.w; ++j) om[j] = ldu(pm + j) | em[j];
+        for (int j = 0; j < A.w; ++j) om[j] = ldu(pm + j) | ldu(em + j);
       }
       if (q.dg & kGoalBit) {
         const int slot = atomicAdd(&A.ctl->n_goal_all, 1);
@@ -944,6 +1011,7 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
     S.C = Cn;
     S.i = has_next ? nbk : S.i + 1;
     S.stop = A.early_stop && stop_any ? 1 : 0;
+    if (sm->b_err) S.status = PUMP_ERR_TIMEOUT;
   }
   __syncthreads();
 }
@@ -966,6 +1034,8 @@ __device__ void explore_one(const ExploreArgs& A, int32_t start, CSmem* sm, uint
     sm->slot0 = 0;  // group 0 is the root alone
     sm->slot_end = 0;
     sm->kept = 0;
+    sm->werr = 0;
+    sm->rows_ready = A.rowcnt ? 0 : 1;
   }
   __syncthreads();
   if (kDsm && start % nr == r && threadIdx.x == 0) mbl[(size_t)(start / nr) * A.kstride] = 0u;  // root: cost 0
@@ -1062,6 +1132,235 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_cluster_batch(const ExploreA
     explore_one<kDsm>(sm->args, starts[q], sm, mbl, cl);
   }
   cl.sync();  // the last query index was read everywhere before any CTA leaves
+}
+
+// ---------------------------------------------------------------- fused form
+// Mask workers' arguments: the query pass's inputs and the order they take the edges in.
+struct FuseArgs {
+  const float2* xi;          // [(W+1)][3][N] normals
+  const float* phi;          // E x 4
+  const float* L;            // E x 3
+  const float* nom;          // E x W x 3
+  const float* linf;         // 3
+  const float* ibox;         // E x 6
+  const unsigned int* dmax;  // E
+  const float* boxes;        // nb x 6
+  const int2* eorder;        // E: (edge, source row) in the order the workers take them
+  uint32_t* emask;           // E x w (written)
+  uint32_t* rowcnt;          // n + 1: finished edges per row, then worker warps finished (both
+                             // accumulated over runs)
+  int32_t N, W, nb, E, w, n;
+  int32_t xi_smem;           // the normals fit in shared memory next to the boxes
+  int32_t hold_row;          // test hook: this row is never counted (-1: none)
+  int32_t head;              // positions [0, head) are computed by the Explore cluster first
+};
+
+// Shared memory a worker CTA uses (boxes, per-warp scratch, normals when they fit).
+__host__ __device__ constexpr size_t worker_smem(int nb, int N, int W, bool xi_smem) {
+  return maskdev::fixed_smem(nb, kCW) + (xi_smem ? sizeof(float2) * (size_t)(W + 1) * 3 * N : 0);
+}
+
+#ifndef PUMP_FUSED_MASK_NW
+#define PUMP_FUSED_MASK_NW 2  // mask words side by side per pass in the fused kernel (2: no spills beside Explore)
+#endif
+// Positions q0 + v, q0 + v + V, ... below q1 of the edge order, warp v of V: the edge's mask
+// words, then its count toward its row by a release add after the warp barrier.  The caller's
+// block stages the boxes (and the normals) first.
+__device__ __forceinline__ void mask_positions(const FuseArgs& F, unsigned char* smem, long long q0, long long q1,
+                                               long long v, long long V, bool count_done) {
+  float* boxes = reinterpret_cast<float*>(smem);
+  int* cand = reinterpret_cast<int*>(boxes + maskdev::kBoxStride * F.nb);
+  uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kCW * maskdev::kCandCap);
+  float2* xi_s = reinterpret_cast<float2*>(smem + maskdev::fixed_smem(F.nb, kCW));
+  const int xi_n = (F.W + 1) * 3 * F.N;
+  maskdev::stage(F.boxes, F.nb, boxes, F.xi, F.xi_smem ? xi_s : nullptr, xi_n);
+  __syncthreads();
+  const float2* xi = F.xi_smem ? xi_s : F.xi;
+  const float linf[3] = {F.linf[0], F.linf[1], F.linf[2]};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* my_cand = cand + warp * maskdev::kCandCap;
+  uint32_t* wm = wmask_all + warp * kMaxWaypoints;
+  for (long long q = q0 + v; q < q1; q += V) {
+    const int2 ex = __ldg(F.eorder + q);
+    maskdev::edge_mask_one<PUMP_FUSED_MASK_NW>(ex.x, xi, F.N, F.W, F.phi, F.L, F.nom, linf, F.ibox, F.dmax, boxes, F.nb, F.w, my_cand, wm,
+                           lane, F.emask);
+    __syncwarp();
+    if (lane == 0 && ex.y != F.hold_row) red_release_add(F.rowcnt + ex.y, 1u);
+  }
+  if (count_done && lane == 0) red_release_add(F.rowcnt + F.n, 1u);  // this warp's edges are counted
+}
+
+// Masks and Explore in one cooperative launch: cluster 0 runs Explore (A.rowcnt set), the
+// other clusters are mask workers.  The first positions of the order (the start row and its
+// neighbourhood, one edge per warp) are computed by the Explore cluster itself before it starts,
+// so the first groups do not wait for the workers' first edges; the workers take the rest.
+template <bool kDsm>
+__global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t start, FuseArgs F) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int nr = (int)cl.num_blocks();
+  const long long warp = threadIdx.x >> 5;
+  if ((int)blockIdx.x < nr) {
+    // shared memory serves as the mask scratch first; explore_one initialises what it uses
+    mask_positions(F, smem_raw, 0, F.head, (long long)blockIdx.x * kCW + warp, (long long)nr * kCW, false);
+    __syncthreads();
+    CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
+    uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
+    explore_one<kDsm>(A, start, sm, mbl, cl);
+    return;
+  }
+  const long long wb = (long long)blockIdx.x - nr, nwb = (long long)gridDim.x - nr;
+  mask_positions(F, smem_raw, F.head, F.E, wb * kCW + warp, nwb * kCW, true);
+}
+
+// Row order of the fused form.  Shortest-path cost from the start over the graph's edges
+// (float sums; an ordering key only), by label-correcting rounds in one cooperative launch: a
+// warp per node whose cost fell in the previous round relaxes its out-edges (atomicMin on the
+// float bits, which order like the non-negative costs).  changed[r mod 3] says whether round r
+// has work; every thread reads it after the same grid barrier, so all leave together.
+__global__ void k_sssp(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                       const float* __restrict__ ecost, int32_t n, int32_t start, uint32_t* dist, uint8_t* fa,
+                       uint8_t* fb, int32_t* changed, int32_t max_rounds) {
+  cg::grid_group grid = cg::this_grid();
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nt = (long long)gridDim.x * blockDim.x;
+  for (long long x = tid; x < n; x += nt) {
+    dist[x] = x == start ? 0u : 0x7f800000u;
+    fa[x] = x == start ? 1 : 0;
+    fb[x] = 0;
+  }
+  if (tid < 3) changed[tid] = tid == 0 ? 1 : 0;
+  grid.sync();
+  const int lane = threadIdx.x & 31;
+  const long long gw = tid >> 5, nw = nt >> 5;
+  for (int r = 0; r < max_rounds; ++r) {
+    if (__ldcg(changed + r % 3) == 0) break;
+    uint8_t* cur = (r & 1) ? fb : fa;
+    uint8_t* nxt = (r & 1) ? fa : fb;
+    bool any = false;
+    for (long long x = gw; x < n; x += nw) {
+      if (!__ldcg(cur + x)) continue;
+      const float dx = __uint_as_float(__ldcg(dist + x));
+      const int32_t e1 = row_ptr[x + 1];
+      for (int32_t e = row_ptr[x] + lane; e < e1; e += 32) {
+        const int32_t y = col[e];
+        const uint32_t nd = __float_as_uint(__fadd_rn(dx, ecost[e]));
+        if (nd < atomicMin(dist + y, nd)) {
+          nxt[y] = 1;
+          any = true;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) cur[x] = 0;
+    }
+    if (__any_sync(0xffffffffu, any) && lane == 0) changed[(r + 1) % 3] = 1;
+    if (tid == 0) changed[(r + 2) % 3] = 0;
+    grid.sync();
+  }
+}
+
+constexpr int kOrderBuckets = 4096;
+constexpr int kOrderThreads = 1024;
+
+// Exclusive prefix of one value per thread over a kOrderThreads block; *tot gets the sum.
+__device__ int32_t order_scan(int32_t v, int32_t* wsum, int32_t* tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  const int32_t pre = (warp > 0 ? wsum[warp - 1] : 0) + x - v;
+  *tot = wsum[31];
+  __syncthreads();
+  return pre;
+}
+
+// Rows by increasing cost (counting sort on the cost quantised to kOrderBuckets - 1 levels over
+// [0, largest finite cost]; unreachable rows last; order inside a level unspecified), and the
+// exclusive prefix of their out-degrees (n + 1 entries).  One block of kOrderThreads threads.
+__global__ void __launch_bounds__(kOrderThreads) k_row_order(const uint32_t* __restrict__ dist,
+                                                             const int32_t* __restrict__ row_ptr, int32_t n,
+                                                             int32_t* __restrict__ order, int32_t* __restrict__ epos) {
+  __shared__ int32_t hist[kOrderBuckets];
+  __shared__ float s_max[32];
+  __shared__ int32_t wsum[32];
+  constexpr int kPer = kOrderBuckets / kOrderThreads;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  float m = 0.f;
+  for (int32_t x = t; x < n; x += kOrderThreads) {
+    const float d = __uint_as_float(dist[x]);
+    if (d < __int_as_float(0x7f800000)) m = fmaxf(m, d);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) s_max[warp] = m;
+  for (int b = t; b < kOrderBuckets; b += kOrderThreads) hist[b] = 0;
+  __syncthreads();
+  m = 0.f;
+  for (int k = 0; k < 32; ++k) m = fmaxf(m, s_max[k]);
+  const float scale = m > 0.f ? (float)(kOrderBuckets - 2) / m : 0.f;
+  auto level = [&](int32_t x) {
+    const float d = __uint_as_float(dist[x]);
+    if (!(d < __int_as_float(0x7f800000))) return kOrderBuckets - 1;
+    return min(kOrderBuckets - 2, (int)(d * scale));
+  };
+  for (int32_t x = t; x < n; x += kOrderThreads) atomicAdd(&hist[level(x)], 1);
+  __syncthreads();
+  {  // exclusive prefix over the levels, kPer consecutive levels per thread
+    int32_t c[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      c[k] = hist[t * kPer + k];
+      sum += c[k];
+    }
+    int32_t tot;
+    int32_t run = order_scan(sum, wsum, &tot);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      hist[t * kPer + k] = run;
+      run += c[k];
+    }
+  }
+  __syncthreads();
+  for (int32_t x = t; x < n; x += kOrderThreads) order[atomicAdd(&hist[level(x)], 1)] = x;
+  __syncthreads();
+  // exclusive prefix of the out-degrees in that order, kOrderThreads rows at a time
+  int32_t carry = 0;
+  for (int32_t j0 = 0; j0 < n; j0 += kOrderThreads) {
+    const int32_t j = j0 + t;
+    const int32_t deg = j < n ? row_ptr[order[j] + 1] - row_ptr[order[j]] : 0;
+    int32_t tot;
+    const int32_t pre = order_scan(deg, wsum, &tot);
+    if (j < n) epos[j] = carry + pre;
+    carry += tot;
+  }
+  if (t == 0) epos[n] = carry;
+}
+
+// Edge order: row order[j]'s edges at positions epos[j] .. epos[j+1] - 1, a warp per row.
+__global__ void k_edge_order(const int32_t* __restrict__ order, const int32_t* __restrict__ epos,
+                             const int32_t* __restrict__ row_ptr, int32_t n, int2* __restrict__ eorder) {
+  const int lane = threadIdx.x & 31;
+  for (long long j = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n;
+       j += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int32_t x = order[j];
+    const int32_t r0 = row_ptr[x], deg = row_ptr[x + 1] - r0, base = epos[j];
+    for (int32_t k = lane; k < deg; k += 32) eorder[base + k] = make_int2(r0 + k, x);
+  }
 }
 
 // Per edge: target node, edge cost bits, target row start, target out-degree | goal bit.
@@ -1264,6 +1563,185 @@ int run_explore_cluster_batch(const ExploreArgs* As_dev, const int32_t* starts_d
     e = cudaLaunchKernelEx(&cfg, k_explore_cluster_batch<false>, As_dev, starts_dev, nq, next_dev);
   note_launch();
   return e == cudaSuccess ? PUMP_OK : PUMP_ERR_CUDA;
+}
+
+int fused_masks_env() {
+  const char* e = getenv("PUMP_FUSED_MASKS");
+  return e ? (atoi(e) != 0 ? 1 : 0) : -1;
+}
+
+// Row order of the fused form, once per graph (its arrays do not change afterwards): costs from
+// the start (k_sssp, cooperative), rows sorted by them, edges in that row order.  *ok = false
+// when the device cannot launch the cooperative pass (nothing is kept then).
+static int ensure_row_order(pump_graph* g, cudaStream_t s, bool* ok) {
+  *ok = g->eorder != nullptr;
+  if (*ok) return PUMP_OK;
+  int dev = 0, coop = 0;
+  PUMP_CUDA_TRY(cudaGetDevice(&dev));
+  PUMP_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return PUMP_OK;
+  const int32_t n = g->n;
+  const int threads = 1024;  // few blocks: the grid barrier of every round is cheaper
+  int per_sm = 0;
+  PUMP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sssp, threads, 0));
+  if (per_sm < 1) return PUMP_OK;
+  const int64_t want = ((int64_t)n + threads / 32 - 1) / (threads / 32);  // a warp per node
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * num_sms()));
+  uint32_t* dist = (uint32_t*)dev_alloc(sizeof(uint32_t) * (size_t)n, s);
+  uint8_t* fa = (uint8_t*)dev_alloc(2 * (size_t)n + 16, s);
+  int32_t* changed = (int32_t*)dev_alloc(sizeof(int32_t) * 4, s);
+  int32_t* order = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)n, s);
+  int32_t* epos = (int32_t*)dev_alloc(sizeof(int32_t) * ((size_t)n + 1), s);
+  int2* eo = (int2*)graph_alloc(g, sizeof(int2) * (size_t)g->E, s);
+  uint32_t* rowcnt = (uint32_t*)graph_alloc(g, sizeof(uint32_t) * ((size_t)n + 1), s);
+  int rc = (dist && fa && changed && order && epos && eo && rowcnt) ? PUMP_OK : PUMP_ERR_OOM;
+  if (!rc) {
+    const int32_t* row_ptr = g->row_ptr;
+    const int32_t* col = g->col;
+    const float* ecost = g->ecost;
+    int32_t nn = n, start = g->start, max_rounds = n + 1;
+    uint8_t* fb = fa + n;
+    void* args[] = {(void*)&row_ptr, (void*)&col, (void*)&ecost, &nn, &start, &dist, &fa, &fb, &changed, &max_rounds};
+    if (cudaLaunchCooperativeKernel((void*)k_sssp, dim3(blocks), dim3(threads), args, 0, s) != cudaSuccess) {
+      cudaGetLastError();
+      rc = -1;  // not available: the caller keeps the separate launches
+    } else {
+      note_launch();
+      k_row_order<<<1, kOrderThreads, 0, s>>>(dist, g->row_ptr, n, order, epos);
+      note_launch();
+      const int eb = (int)std::min<int64_t>(((int64_t)n * 32 + 255) / 256, 4096);
+      k_edge_order<<<eb, 256, 0, s>>>(order, epos, g->row_ptr, n, eo);
+      note_launch();
+      if (cudaGetLastError() != cudaSuccess) rc = PUMP_ERR_CUDA;
+    }
+  }
+  dev_free(epos, s);
+  dev_free(order, s);
+  dev_free(changed, s);
+  dev_free(fa, s);
+  dev_free(dist, s);
+  if (rc == -1) return PUMP_OK;
+  if (rc) return rc;
+  g->eorder = eo;
+  g->rowcnt = rowcnt;
+  *ok = true;
+  return PUMP_OK;
+}
+
+// Fused form per device and shared-memory size: clusters the kernel can keep resident at once
+// (0: the form does not apply), found once.
+struct FusedChoice {
+  int dev;
+  size_t smem;
+  int clusters;
+};
+std::mutex g_fused_mu;
+std::vector<FusedChoice> g_fused;
+
+static int fused_clusters(int dev, int nr, size_t smem) {
+  {
+    std::lock_guard<std::mutex> lk(g_fused_mu);
+    for (const auto& c : g_fused)
+      if (c.dev == dev && c.smem == smem) return c.clusters;
+  }
+  int ncl = 0;
+  auto kern = k_explore_fused<true>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmemMax) == cudaSuccess &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cluster_config(&cfg, attr, nr, 1, smem, 0);
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess) ncl = 0;
+  }
+  cudaGetLastError();
+  if (ncl < 2) ncl = 0;
+  std::lock_guard<std::mutex> lk(g_fused_mu);
+  g_fused.push_back({dev, smem, ncl});
+  return ncl;
+}
+
+static void fused_disable(int dev, size_t smem) {
+  std::lock_guard<std::mutex> lk(g_fused_mu);
+  for (auto& c : g_fused)
+    if (c.dev == dev && c.smem == smem) c.clusters = 0;
+}
+
+// Masks and Explore in one cooperative launch (k_explore_fused): cluster 0 explores, every other
+// co-resident cluster computes masks.  *launched = false, with nothing of the run enqueued,
+// where the form does not apply (box masks, mbest on chip, a second cluster resident, the
+// cooperative passes available); the caller then runs the separate launches.
+int run_explore_fused(pump_graph* g, const ExploreArgs& A0, int nr, bool dsm, cudaStream_t s, bool* launched) {
+  *launched = false;
+  if (!dsm || g->hsmc || g->E == 0 || !g->has_geometry) return PUMP_OK;
+  const bool xi_smem = worker_smem(g->n_boxes, g->N, g->W, true) <= kDynSmemMax;
+  const size_t smem = std::max(cluster_smem_bytes(A0.n, A0.kstride, nr, dsm),
+                               worker_smem(g->n_boxes, g->N, g->W, xi_smem));
+  if (smem > kDynSmemMax) return PUMP_OK;
+  int dev = 0;
+  PUMP_CUDA_TRY(cudaGetDevice(&dev));
+  const int ncl = fused_clusters(dev, nr, smem);
+  if (ncl < 2) return PUMP_OK;
+  bool ok = false;
+  int rc = ensure_row_order(g, s, &ok);
+  if (rc || !ok) return rc;
+  // counts accumulate over runs (no clearing per run); zeroed after a run that may have left
+  // them short
+  if (g->rowcnt_dirty) {
+    PUMP_CUDA_TRY(cudaMemsetAsync(g->rowcnt, 0, sizeof(uint32_t) * ((size_t)g->n + 1), s));
+    g->fuse_epoch = 0;
+    g->rowcnt_dirty = false;
+  }
+  const uint32_t epoch = ++g->fuse_epoch;
+  const uint32_t worker_warps = (uint32_t)((ncl - 1) * nr * kCW);
+  ExploreArgs A = A0;
+  A.rowcnt = g->rowcnt;
+  A.epoch_m1 = epoch - 1;
+  A.done = g->rowcnt + g->n;
+  A.done_target = epoch * worker_warps;
+  // test hooks (bounded-wait path): PUMP_TEST_FUSED_HOLD_ROW names a row whose count never
+  // completes, PUMP_TEST_SPIN_LIMIT shortens the waits
+  const char* hold = getenv("PUMP_TEST_FUSED_HOLD_ROW");
+  const char* lim = getenv("PUMP_TEST_SPIN_LIMIT");
+  if (lim && atoll(lim) > 0) A.spin_limit = atoll(lim);
+  FuseArgs F;
+  F.xi = g->xi_t;
+  F.phi = g->phi;
+  F.L = g->L;
+  F.nom = g->nom;
+  F.linf = g->linf_dev;
+  F.ibox = g->ibox;
+  F.dmax = g->dmax;
+  F.boxes = g->boxes;
+  F.eorder = g->eorder;
+  F.emask = g->emask;
+  F.rowcnt = g->rowcnt;
+  F.N = g->N;
+  F.W = g->W;
+  F.nb = g->n_boxes;
+  F.E = g->E;
+  F.w = g->n_words;
+  F.n = g->n;
+  F.xi_smem = xi_smem ? 1 : 0;
+  F.hold_row = hold ? atoi(hold) : -1;
+  if (F.hold_row >= 0) g->rowcnt_dirty = true;  // that row's count stays short
+  F.head = (int32_t)std::min<int64_t>(g->E, (int64_t)nr * kCW);
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[2];
+  cluster_config(&cfg, attr, nr, ncl, smem, s);
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
+  cfg.numAttrs = 2;
+  const int32_t start = g->start;
+  if (cudaLaunchKernelEx(&cfg, k_explore_fused<true>, A, start, F) != cudaSuccess) {
+    cudaGetLastError();
+    fused_disable(dev, smem);
+    g->rowcnt_dirty = true;
+    return PUMP_OK;
+  }
+  note_launch();
+  g->masks_ready = true;
+  *launched = true;
+  return PUMP_OK;
 }
 
 }  // namespace pump

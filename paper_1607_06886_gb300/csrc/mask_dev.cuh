@@ -1,0 +1,193 @@
+// Particle collision mask of one edge (Section III-B, with a direct particle-in-box test in
+// place of the half-space test): the per-edge work of the query pass, shared by the stand-alone
+// mask kernel (edge_mask.cu) and the mask workers of the fused Explore launch
+// (explore_cluster.cu).
+//
+// The particle deviations of an edge depend on its step h and the common normals, not on the
+// obstacles.  Graph build records, per edge, a box holding every particle position (nominal
+// waypoints widened by the largest |d0| of any particle).  A warp takes one edge: lanes test the
+// obstacle boxes against that box, and an edge with no box left gets zero mask words without
+// running its particles.  Otherwise lane l runs particle 32*word + l through the recurrence once
+// per word and tests the left boxes; the mask word is the warp ballot of the per-particle OR over
+// waypoints and boxes.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pump_internal.cuh"
+
+namespace pump {
+namespace maskdev {
+
+constexpr int kCandCap = 64;
+constexpr int kBoxStride = 8;  // floats per box in shared memory: lo xyz, hi xyz, 2 pad
+
+// Shared memory of one block of the query pass before the normals: boxes, per-warp candidate
+// lists and per-warp waypoint box masks (16-byte aligned end).
+__host__ __device__ constexpr size_t fixed_smem(int nb, int warps) {
+  return (sizeof(float) * kBoxStride * (size_t)nb + sizeof(int) * warps * kCandCap +
+          sizeof(uint32_t) * warps * kMaxWaypoints + 15) & ~(size_t)15;
+}
+
+__device__ __forceinline__ void dev_init(const float* linf, float2 x, float& d0, float& d1) {
+  d0 = __fmul_rn(linf[0], x.x);
+  d1 = fmaf(linf[1], x.x, __fmul_rn(linf[2], x.y));
+}
+
+__device__ __forceinline__ void dev_step(const float* P, const float* L, float2 x, float& d0, float& d1) {
+  float n0 = __fmul_rn(L[0], x.x);
+  float n1 = fmaf(L[1], x.x, __fmul_rn(L[2], x.y));
+  float e0 = fmaf(P[0], d0, fmaf(P[1], d1, n0));
+  float e1 = fmaf(P[2], d0, fmaf(P[3], d1, n1));
+  d0 = e0;
+  d1 = e1;
+}
+
+// NW mask words of one edge: lane l advances particles 32 (w0 + j) + l, j < NW, side by side
+// through waypoints 1..k_last and tests the boxes left at each; the words are the warp ballots.
+// The warp stops early once every lane's particles have hit.
+template <int NW>
+__device__ __forceinline__ void word_pass(const float2* __restrict__ xi, int N, int W, const float (&P)[4],
+                                          const float (&L)[3], const float (&linf)[3], const float* __restrict__ nm,
+                                          int k_last, bool narrow, const uint32_t* wm, const int* my_cand, bool all,
+                                          int nc, const float* boxes, int w0, int lane, uint32_t* out) {
+  float d0[NW][3], d1[NW][3];
+  bool hit[NW];
+  const float2* xq = xi + w0 * 32 + lane;
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    hit[j] = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dev_init(linf, xq[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+  }
+  for (int k = 1; k <= k_last; ++k) {
+    const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
+    const float2* xk = xq + (size_t)k * 3 * N;
+    float p[NW][3];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dev_step(P, L, xk[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+      p[j][0] = __fadd_rn(n0, d0[j][0]);
+      p[j][1] = __fadd_rn(n1, d0[j][1]);
+      p[j][2] = __fadd_rn(n2, d0[j][2]);
+    }
+    unsigned bits = narrow ? wm[k - 1] : 0u;
+    int c = 0;
+    for (;;) {
+      int o;
+      if (narrow) {
+        if (!bits) break;
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        o = my_cand[b];
+      } else {
+        if (c >= nc) break;
+        o = all ? c : my_cand[c];
+        ++c;
+      }
+      const float4 b0 = *reinterpret_cast<const float4*>(boxes + kBoxStride * o);      // lo x, y, z, hi x
+      const float2 b1 = *reinterpret_cast<const float2*>(boxes + kBoxStride * o + 4);  // hi y, z
+#pragma unroll
+      for (int j = 0; j < NW; ++j)
+        hit[j] = hit[j] || (b0.x <= p[j][0] && p[j][0] <= b0.w && b0.y <= p[j][1] && p[j][1] <= b1.x &&
+                            b0.z <= p[j][2] && p[j][2] <= b1.y);
+    }
+    bool done = true;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) done = done && hit[j];
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    const unsigned bits = __ballot_sync(0xffffffffu, hit[j]);
+    if (lane == 0) out[w0 + j] = bits;
+  }
+}
+
+// Stages the boxes in shared memory (kBoxStride floats per box) and, when given, the normals.
+__device__ __forceinline__ void stage(const float* __restrict__ boxes_g, int nb, float* boxes,
+                                      const float2* __restrict__ xi_g, float2* xi_s, int xi_n) {
+  for (int k = threadIdx.x; k < kBoxStride * nb; k += blockDim.x) {
+    const int o = k / kBoxStride, c = k - o * kBoxStride;
+    boxes[k] = c < 6 ? boxes_g[6 * o + c] : 0.f;
+  }
+  if (xi_s)
+    for (int k = threadIdx.x; k < xi_n; k += blockDim.x) xi_s[k] = xi_g[k];
+}
+
+// The w mask words of edge e, written by the calling warp.  Boxes that miss the edge's position
+// box cannot hold any of its particle positions; an edge with none left gets zero mask words
+// without running the particles.  With at most 32 boxes left, the warp narrows them per waypoint:
+// at waypoint k every particle position lies in [nominal_k - M, nominal_k + M] (M = the edge's
+// largest |d0|, rounded the way the positions are), so only boxes meeting that box are tested
+// there, and the particles run only up to the last waypoint that has one.  Each 32-particle word
+// then runs the recurrence once and its lanes stop testing when all of them have hit (up to
+// kMaxNW words side by side per pass: fewer live registers with 2).  my_cand (kCandCap ints) and
+// wm (kMaxWaypoints words) are the warp's shared-memory scratch.
+template <int kMaxNW = 4>
+__device__ __forceinline__ void edge_mask_one(long long e, const float2* __restrict__ xi, int N, int W,
+                                              const float* __restrict__ phi, const float* __restrict__ Lg,
+                                              const float* __restrict__ nom, const float (&linf)[3],
+                                              const float* __restrict__ ibox_g, const unsigned int* __restrict__ dmax,
+                                              const float* boxes, int nb, int w, int* my_cand, uint32_t* wm, int lane,
+                                              uint32_t* __restrict__ mask) {
+  const float* ib = ibox_g + 6 * e;
+  const float lo0 = ib[0], lo1 = ib[1], lo2 = ib[2], hi0 = ib[3], hi1 = ib[4], hi2 = ib[5];
+  int n_cand = 0;
+  for (int base = 0; base < nb; base += 32) {
+    const int o = base + lane;
+    bool ov = false;
+    if (o < nb) {
+      const float* b = boxes + kBoxStride * o;
+      ov = b[0] <= hi0 && lo0 <= b[3] && b[1] <= hi1 && lo1 <= b[4] && b[2] <= hi2 && lo2 <= b[5];
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, ov);
+    const int pos = n_cand + __popc(bal & ((1u << lane) - 1u));
+    if (ov && pos < kCandCap) my_cand[pos] = o;
+    n_cand += __popc(bal);
+  }
+  __syncwarp();
+  const float* nm = nom + (size_t)e * W * 3;
+  int k_last = W;
+  const bool narrow = n_cand > 0 && n_cand <= 32;
+  if (narrow) {
+    // boxes per waypoint: lane c tests candidate c against waypoint k's position box
+    const float M = __uint_as_float(dmax[e]);
+    const float* bc = boxes + kBoxStride * my_cand[lane < n_cand ? lane : 0];
+    k_last = 0;
+    for (int k = 1; k <= W; ++k) {
+      const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
+      const bool ov = lane < n_cand && bc[0] <= __fadd_rn(n0, M) && __fsub_rn(n0, M) <= bc[3] &&
+                      bc[1] <= __fadd_rn(n1, M) && __fsub_rn(n1, M) <= bc[4] &&
+                      bc[2] <= __fadd_rn(n2, M) && __fsub_rn(n2, M) <= bc[5];
+      const unsigned m = __ballot_sync(0xffffffffu, ov);
+      if (lane == 0) wm[k - 1] = m;
+      if (m) k_last = k;
+    }
+    __syncwarp();
+  }
+  if (n_cand == 0 || k_last == 0) {
+    for (int word = lane; word < w; word += 32) mask[(size_t)e * w + word] = 0u;
+    __syncwarp();
+    return;
+  }
+  const bool all = n_cand > kCandCap;
+  const int nc = all ? nb : n_cand;
+  const float P[4] = {phi[4 * e], phi[4 * e + 1], phi[4 * e + 2], phi[4 * e + 3]};
+  const float L[3] = {Lg[3 * e], Lg[3 * e + 1], Lg[3 * e + 2]};
+  uint32_t* out = mask + (size_t)e * w;
+  int w0 = 0;
+  if (kMaxNW >= 4)
+    for (; w0 + 4 <= w; w0 += 4)
+      word_pass<4>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
+  for (; w0 + 2 <= w; w0 += 2)
+    word_pass<2>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
+  if (w0 < w) word_pass<1>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
+  __syncwarp();
+}
+
+}  // namespace maskdev
+}  // namespace pump

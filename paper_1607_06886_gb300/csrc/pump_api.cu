@@ -213,12 +213,12 @@ int prepare_explore_args(pump_graph* g, const pump_plan_params* p, float radius,
 
 // Enqueue Explore; with `collect` read its control block back and fill `st`.
 int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* st, cudaStream_t s,
-                bool collect) {
+                bool collect, bool masks_pending) {
   ExploreArgs A;
   int rc = prepare_explore_args(g, p, radius, &A, s);
   if (rc) return rc;
   ExploreBufs& X = g->ex;
-  rc = run_explore_kernels(g, A, explore_mode(p->flags), s);
+  rc = run_explore_kernels(g, A, explore_mode(p->flags), s, masks_pending);
   if (rc) return rc;
   rc = run_goal_finalize(g, A, s);
   if (rc) return rc;
@@ -490,11 +490,19 @@ int pump_plan(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t p
   std::memset(&r, 0, sizeof(r));
   r.chosen_plan = -1;
   PUMP_CUDA_TRY(cudaEventRecord(g->ev[0], s));
-  rc = compute_edge_masks(g, s);
-  if (rc) return rc;
+  // box masks may run inside the Explore launch (then ms_masks covers only what precedes it);
+  // by default from the graph's second query, whose run also lays out the edge order once
+  const int fm = fused_masks_env();
+  const bool fuse = g->fuse_masks && !g->hsmc && explore_mode(p->flags) == 0 && fm != 0 &&
+                    (fm == 1 || g->plans_run > 0);
+  ++g->plans_run;
+  if (!fuse) {
+    rc = compute_edge_masks(g, s);
+    if (rc) return rc;
+  }
   PUMP_CUDA_TRY(cudaEventRecord(g->ev[1], s));
   const bool explore_only = (p->flags & PUMP_EXPLORE_ONLY) != 0;
-  rc = run_explore(g, p, g->radius, &r, s, explore_only);
+  rc = run_explore(g, p, g->radius, &r, s, explore_only, fuse);
   PUMP_CUDA_TRY(cudaEventRecord(g->ev[2], s));
   if (rc) return rc;
   if (!explore_only) {
@@ -510,6 +518,7 @@ int pump_plan(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t p
   cudaEventElapsedTime(&r.ms_masks, g->ev[0], g->ev[1]);
   cudaEventElapsedTime(&r.ms_explore, g->ev[1], g->ev[2]);
   cudaEventElapsedTime(&r.ms_select, g->ev[2], g->ev[3]);
+  r.fused = fuse && g->last_fused ? 1 : 0;
   *out = r;
   return r.status == PUMP_ERR_INFEASIBLE ? PUMP_ERR_INFEASIBLE : PUMP_OK;
 }
@@ -568,6 +577,7 @@ int pump_export(pump_graph* g, int32_t what, void* host_buf, size_t cap, size_t*
     case PUMP_EXPORT_GOAL_PLANS: if (!ex) return PUMP_ERR_INVALID_ARG; src = g->ex.goal_sorted; bytes = 4 * (size_t)g->last_goal; break;
     case PUMP_EXPORT_EDGE_BOX: if (!geo) return PUMP_ERR_INVALID_ARG; src = g->ibox; bytes = 24 * E; break;
     case PUMP_EXPORT_NOMINAL_VEL: if (!geo) return PUMP_ERR_INVALID_ARG; src = g->nvel; bytes = 12 * (size_t)g->W * E; break;
+    case PUMP_EXPORT_EDGE_ORDER: if (!g->eorder) return PUMP_ERR_INVALID_ARG; src = g->eorder; bytes = 8 * E; break;
     default: return PUMP_ERR_INVALID_ARG;
   }
   *needed = bytes;

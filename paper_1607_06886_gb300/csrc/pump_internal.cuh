@@ -98,6 +98,13 @@ struct ExploreArgs {
   int32_t* goal_all;
   ExploreCtl* ctl;
   long long spin_limit;
+  // fused form: finished edges per row, counted by the mask workers of the same launch (a
+  // member's row is read once its count reaches the row's degree); null when the masks are ready.
+  // Counts accumulate over runs: run e (from 1) starts at (e - 1) x degree (mod 2^32).
+  const uint32_t* rowcnt = nullptr;
+  uint32_t epoch_m1 = 0;            // e - 1
+  const uint32_t* done = nullptr;   // worker warps finished, accumulated over runs
+  uint32_t done_target = 0;         // its value once every worker warp of run e has finished
 };
 
 struct ExploreBufs {
@@ -171,6 +178,15 @@ struct pump_graph {
   bool hsmc = false;         // masks by Half-Space Monte Carlo
   int32_t* hs_off = nullptr; // E*W + 1: first half-space of waypoint (e, k) (HSMC)
   float4* hs_ab = nullptr;   // half-spaces (a xyz, b) that a particle of the edge can fire (HSMC)
+  // fused masks + Explore: edges in the order the mask workers take them (edge, source row),
+  // rows by increasing shortest-path cost from the start; finished edges per row
+  int2* eorder = nullptr;
+  uint32_t* rowcnt = nullptr;       // n + 1: finished edges per row, then worker warps finished
+  uint32_t fuse_epoch = 0;          // fused runs since the counts were last zeroed
+  bool rowcnt_dirty = true;         // counts must be zeroed before the next fused run
+  bool fuse_masks = true;    // pump_plan may run the masks inside the Explore launch
+  bool last_fused = false;   // the last Explore run computed the masks in its launch
+  int64_t plans_run = 0;     // pump_plan calls on this graph
   std::vector<pump::DevBuf> bufs;
   pump::ExploreBufs ex;
   // last explore
@@ -198,14 +214,19 @@ constexpr int kHsMax = 8;  // half-spaces per waypoint (HSMC)
 int compute_edge_masks(pump_graph* g, cudaStream_t s);
 int compute_edge_bounds(pump_graph* g, cudaStream_t s);
 int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* stats,
-                cudaStream_t s, bool collect);
+                cudaStream_t s, bool collect, bool masks_pending = false);
 void fill_explore_stats(pump_graph* g, const ExploreCtl& h, pump_plan_result* st);
 int run_select(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t path_cap,
                pump_plan_result* out, ExploreCtl* ctl_host, cudaStream_t s);
 int run_certify_path(pump_graph* g, const int32_t* path_host, int32_t path_len, int32_t n_mc,
                      int32_t substeps, uint64_t seed, int64_t* n_collide, cudaStream_t s);
 int ensure_explore_bufs(pump_graph* g, int64_t cap, int32_t kmax, cudaStream_t s);
-int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStream_t s);
+// masks_pending: the query's edge masks are not computed yet; the run computes them, inside the
+// Explore launch where the fused form applies (explore_cluster.cu), else before it.
+int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStream_t s, bool masks_pending = false);
+// Fused masks + Explore per the environment: PUMP_FUSED_MASKS=0 never, =1 from a graph's first
+// query, unset from its second (-1).
+int fused_masks_env();
 int ensure_edge_targets(pump_graph* g, cudaStream_t s);
 int prepare_explore_args(pump_graph* g, const pump_plan_params* p, float radius, ExploreArgs* out, cudaStream_t s);
 int check_plan_params(const pump_plan_params* p);

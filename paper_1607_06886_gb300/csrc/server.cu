@@ -113,6 +113,9 @@ struct pump_server {
     std::memset(&d->result, 0, sizeof(d->result));
     d->result.chosen_plan = -1;
     if (!rc) {
+      // requests overlap on the device: the masks keep their own launch, so a request's Explore
+      // holds one cluster's SMs, not the whole device
+      g->fuse_masks = false;
       d->path.assign(kPathCap, 0);
       rc = pump_plan(g, &j->pp, d->path.data(), kPathCap, &d->result, s);
       d->path.resize(std::min<int32_t>(d->result.path_len, kPathCap));

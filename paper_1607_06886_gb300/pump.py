@@ -25,6 +25,7 @@ EXPORT = {
     "counts": 0, "node_valid": 1, "row_ptr": 2, "col": 3, "ecost": 4, "tau": 5, "h": 6, "phi": 7, "L": 8,
     "nominal": 9, "linf": 10, "masks": 11, "plan_head": 12, "plan_parent": 13, "plan_cost": 14, "plan_mask": 15,
     "plan_popc": 16, "plan_created": 17, "plan_expanded": 18, "goal_plans": 19, "edge_box": 20, "nominal_vel": 21,
+    "edge_order": 22,
 }
 
 
@@ -60,7 +61,8 @@ class PlanResult(C.Structure):
                 ("n_candidates", C.c_int64), ("n_kept", C.c_int64), ("n_plans", C.c_int64),
                 ("n_iterations", C.c_int32), ("n_groups", C.c_int32), ("n_goal", C.c_int32),
                 ("n_certified", C.c_int32), ("path_len", C.c_int32), ("path_truncated", C.c_int32),
-                ("ms_masks", C.c_float), ("ms_explore", C.c_float), ("ms_select", C.c_float)]
+                ("ms_masks", C.c_float), ("ms_explore", C.c_float), ("ms_select", C.c_float),
+                ("fused", C.c_int32)]
 
     def as_dict(self) -> Dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -495,7 +497,8 @@ class Graph:
                   "plan_parent": (np.int32, (P,)), "plan_cost": (np.float32, (P,)), "plan_mask": (np.uint32, (P, w)),
                   "plan_popc": (np.int32, (P,)), "plan_created": (np.int32, (P,)),
                   "plan_expanded": (np.int32, (P,)), "goal_plans": (np.int32, (G,)),
-                  "edge_box": (np.float32, (E, 6)), "nominal_vel": (np.float32, (E, W, 3))}
+                  "edge_box": (np.float32, (E, 6)), "nominal_vel": (np.float32, (E, W, 3)),
+                  "edge_order": (np.int32, (E, 2))}
         dt, shp = shapes[what]
         return raw.view(dt).reshape(shp).copy()
 
