@@ -574,11 +574,17 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
     bool goal = false;
     float c = 0.f;
     if (p < a1) {
+      // the plan's row, goal flag and mask are loaded with its record, before the dominance
+      // test (distributed shared memory), so the two round trips overlap
+      const int32_t xp = ld32(A.head + p);
+      const int32_t r0p = A.row_ptr[xp], r1p = A.row_ptr[xp + 1];
+      const bool goalp = A.is_goal[xp] != 0;
+      const uint4 mp = (ofits && A.w <= 4) ? load_mask4(A.mask + (size_t)p * A.w, A.w) : make_uint4(0u, 0u, 0u, 0u);
       eff = old_eff_c<kDsm>(A, sm, cl, mbl, p, S.i, &x, &c, &pc);
       if (eff >= 0) {
-        r0 = A.row_ptr[x];
-        deg = A.row_ptr[x + 1] - r0;
-        goal = A.is_goal[x] != 0;
+        r0 = r0p;
+        deg = r1p - r0p;
+        goal = goalp;
         minb = min(minb, eff);
         min_open = min(min_open, (int32_t)p);
       }
@@ -591,7 +597,7 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
           sm->or0[o] = r0;
           sm->odg[o] = (uint32_t)deg | (goal ? kGoalBit : 0u);
           sm->opc[o] = (int16_t)pc;
-          if (A.w <= 4) sm->omask[o] = load_mask4(A.mask + (size_t)p * A.w, A.w);
+          if (A.w <= 4) sm->omask[o] = mp;
         }
       }
     }

@@ -270,6 +270,7 @@ static void destroy(pump_graph* g) {
   for (auto& b : g->bufs) dev_free(b.ptr, s);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
+  if (g->ctl_host) cudaFreeHost(g->ctl_host);
   cudaDeviceSynchronize();
   delete g;
 }
@@ -283,6 +284,7 @@ void destroy_on_stream(pump_graph* g, cudaStream_t s) {
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   cudaStreamSynchronize(s);
+  if (g->ctl_host) cudaFreeHost(g->ctl_host);
   delete g;
 }
 
@@ -298,6 +300,7 @@ int check_plan_params(const pump_plan_params* p) {
 int make_events(pump_graph* g) {
   for (auto& e : g->ev)
     if (!e) PUMP_CUDA_TRY(cudaEventCreate(&e));
+  if (!g->ctl_host) PUMP_CUDA_TRY(cudaHostAlloc((void**)&g->ctl_host, sizeof(ExploreCtl), cudaHostAllocDefault));
   return PUMP_OK;
 }
 
@@ -502,7 +505,7 @@ int pump_plan(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t p
   }
   PUMP_CUDA_TRY(cudaEventRecord(g->ev[1], s));
   const bool explore_only = (p->flags & PUMP_EXPLORE_ONLY) != 0;
-  rc = run_explore(g, p, g->radius, &r, s, explore_only, fuse);
+  rc = run_explore(g, p, g->radius, &r, s, false, fuse);
   PUMP_CUDA_TRY(cudaEventRecord(g->ev[2], s));
   if (rc) return rc;
   if (!explore_only) {
@@ -510,11 +513,18 @@ int pump_plan(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t p
     rc = run_select(g, p, path, path_cap, &r, &h, s);
     fill_explore_stats(g, h, &r);
     if (rc) return rc;
+    PUMP_CUDA_TRY(cudaEventRecord(g->ev[3], s));
+    PUMP_CUDA_TRY(cudaEventSynchronize(g->ev[3]));
   } else {
+    // one wait for the control block and the events (a pinned copy does not block the host)
+    PUMP_CUDA_TRY(cudaMemcpyAsync(g->ctl_host, g->ex.ctl, sizeof(ExploreCtl), cudaMemcpyDeviceToHost, s));
+    PUMP_CUDA_TRY(cudaEventRecord(g->ev[3], s));
+    PUMP_CUDA_TRY(cudaEventSynchronize(g->ev[3]));
+    const ExploreCtl h = *g->ctl_host;
+    fill_explore_stats(g, h, &r);
+    if (h.status) return h.status;
     r.status = PUMP_OK;
   }
-  PUMP_CUDA_TRY(cudaEventRecord(g->ev[3], s));
-  PUMP_CUDA_TRY(cudaEventSynchronize(g->ev[3]));
   cudaEventElapsedTime(&r.ms_masks, g->ev[0], g->ev[1]);
   cudaEventElapsedTime(&r.ms_explore, g->ev[1], g->ev[2]);
   cudaEventElapsedTime(&r.ms_select, g->ev[2], g->ev[3]);

@@ -194,6 +194,7 @@ struct pump_graph {
   int64_t last_plans = 0;
   int32_t last_goal = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  pump::ExploreCtl* ctl_host = nullptr;  // pinned copy of Explore's control block (pump_plan)
 };
 
 namespace pump {
