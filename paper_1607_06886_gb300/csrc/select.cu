@@ -129,58 +129,99 @@ __global__ void k_path_edges(const int32_t* __restrict__ nodes, int len, const i
   else atomicExch(err, 1);
 }
 
-// Per path edge: Phi(hs) (4), L(hs) (3), pad, then W*S*3 nominal positions.  Plan k's table
-// starts at k * kMaxPathEdges * stride.
-__global__ void k_mc_prep(const int32_t* __restrict__ n_cert_p, const int32_t* __restrict__ plen,
-                          const int32_t* __restrict__ pedges, const int32_t* __restrict__ pnodes,
-                          const float* __restrict__ states, const float* __restrict__ tau, int W, int S, float sigma,
-                          const float* __restrict__ boxes, int nb, float B, float* table) {
+// Per path edge: Phi(hs) (4), L(hs) (3), the bits of the boxes its particles can reach (1), then
+// W*S*3 nominal positions.  Plan k's table starts at k * kMaxPathEdges * stride.  A block per
+// path edge: its threads take the sample positions (double cubic, rounded to float) while the
+// last thread computes Phi and L; min/max of the positions by warp and block reduction.
+constexpr int kPrepThreads = 128;
+__global__ void __launch_bounds__(kPrepThreads) k_mc_prep(const int32_t* __restrict__ n_cert_p,
+                                                          const int32_t* __restrict__ plen,
+                                                          const int32_t* __restrict__ pedges,
+                                                          const int32_t* __restrict__ pnodes,
+                                                          const float* __restrict__ states,
+                                                          const float* __restrict__ tau, int W, int S, float sigma,
+                                                          const float* __restrict__ boxes, int nb, float B,
+                                                          float* table) {
   const int k = blockIdx.y;
   if (k >= *n_cert_p) return;
   const int L = plen[k];
   const int stride = 8 + W * S * 3;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < L; j += gridDim.x * blockDim.x) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  constexpr int kWarpsP = kPrepThreads / 32;
+  constexpr int kModel = kPrepThreads - 1;  // the thread computing Phi and L
+  __shared__ Cubic cq[3];
+  __shared__ float s_lo[kWarpsP][3], s_hi[kWarpsP][3];
+  for (int j = blockIdx.x; j < L; j += gridDim.x) {
     const int e = pedges[(size_t)k * kMaxPathEdges + j];
     const int v = pnodes[(size_t)k * (kMaxPathEdges + 1) + j], u = pnodes[(size_t)k * (kMaxPathEdges + 1) + j + 1];
     float* T = table + ((size_t)k * kMaxPathEdges + j) * stride;
     const float t32 = tau[e];
     const float h = __fdiv_rn(t32, (float)W);
     const float hs = __fdiv_rn(h, (float)S);
-    double Phi[4], Lm[3], Linf[3];
-    model_dev((double)sigma, (double)hs, Phi, Lm, Linf);
-    for (int q = 0; q < 4; ++q) T[q] = __double2float_rn(Phi[q]);
-    for (int q = 0; q < 3; ++q) T[4 + q] = __double2float_rn(Lm[q]);
-    T[7] = 0.f;
-    double xv[6], xu[6];
-    for (int q = 0; q < 6; ++q) {
-      xv[q] = (double)states[6 * v + q];
-      xu[q] = (double)states[6 * u + q];
+    if (t < 3) {
+      double xv[6], xu[6];
+      for (int q = 0; q < 6; ++q) {
+        xv[q] = (double)states[6 * v + q];
+        xu[q] = (double)states[6 * u + q];
+      }
+      cq[t] = cubic_dev(xv, xu, (double)t32, t);
     }
-    const double td = (double)t32;
+    __syncthreads();
     float lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
-      const Cubic c = cubic_dev(xv, xu, td, a);
       lo[a] = __int_as_float(0x7f800000);
       hi[a] = -lo[a];
-      for (int kk = 1; kk <= W; ++kk)
-        for (int s = 1; s <= S; ++s) {
-          const double t = (double)((kk - 1) * S + s) * (double)hs;
-          const float pv = __double2float_rn(cubic_at(c, t));
-          T[8 + (((kk - 1) * S + (s - 1)) * 3) + a] = pv;
+    }
+    if (t == kModel) {
+      double Phi[4], Lm[3], Linf[3];
+      model_dev((double)sigma, (double)hs, Phi, Lm, Linf);
+      for (int q = 0; q < 4; ++q) T[q] = __double2float_rn(Phi[q]);
+      for (int q = 0; q < 3; ++q) T[4 + q] = __double2float_rn(Lm[q]);
+    } else {
+      const int WS = W * S;
+      for (int q = t; q < WS; q += kPrepThreads - 1) {
+        const double tq = (double)(q + 1) * (double)hs;  // sample s of waypoint interval kk: (kk-1) S + s
+        for (int a = 0; a < 3; ++a) {
+          const float pv = __double2float_rn(cubic_at(cq[a], tq));
+          T[8 + q * 3 + a] = pv;
           lo[a] = fminf(lo[a], pv);
           hi[a] = fmaxf(hi[a], pv);
         }
-      lo[a] = __fsub_rn(lo[a], B);
-      hi[a] = __fadd_rn(hi[a], B);
+      }
     }
-    // boxes that can hold a position nominal + d0 with |d0| <= B on every axis
-    uint32_t bits = 0u;
-    for (int o = 0; o < nb && o < 32; ++o) {
-      const float* b = boxes + 6 * o;
-      if (b[0] <= hi[0] && lo[0] <= b[3] && b[1] <= hi[1] && lo[1] <= b[4] && b[2] <= hi[2] && lo[2] <= b[5])
-        bits |= 1u << o;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+        hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+      }
+    if (lane == 0)
+      for (int a = 0; a < 3; ++a) {
+        s_lo[warp][a] = lo[a];
+        s_hi[warp][a] = hi[a];
+      }
+    __syncthreads();
+    if (warp == 0) {
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = s_lo[0][a];
+        hi[a] = s_hi[0][a];
+        for (int r = 1; r < kWarpsP; ++r) {
+          lo[a] = fminf(lo[a], s_lo[r][a]);
+          hi[a] = fmaxf(hi[a], s_hi[r][a]);
+        }
+        lo[a] = __fsub_rn(lo[a], B);
+        hi[a] = __fadd_rn(hi[a], B);
+      }
+      // boxes that can hold a position nominal + d0 with |d0| <= B on every axis (lane o: box o)
+      bool ov = false;
+      if (lane < nb && lane < 32) {
+        const float* b = boxes + 6 * lane;
+        ov = b[0] <= hi[0] && lo[0] <= b[3] && b[1] <= hi[1] && lo[1] <= b[4] && b[2] <= hi[2] && lo[2] <= b[5];
+      }
+      const unsigned bits = __ballot_sync(0xffffffffu, ov);
+      if (lane == 0) T[7] = __uint_as_float(bits);
     }
-    T[7] = __uint_as_float(bits);
+    __syncthreads();  // cq and the reduction buffers are reused by the next path edge
   }
 }
 
@@ -584,11 +625,11 @@ int ensure_table(pump_graph* g, int S, cudaStream_t s) {
 int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert, int n_mc, int S, uint64_t seed,
              cudaStream_t s) {
   ExploreBufs& X = g->ex;
-  dim3 grid(kMaxPathEdges / 64, std::max(n_cert, 1));
+  dim3 grid(64, std::max(n_cert, 1));  // path edges j, j + 64, ... per block row
   // deviation bound for the box cull: 12 stationary position standard deviations (any B is exact)
   const double sq3 = 1.7320508075688772935;
   const float B = (float)(12.0 * (double)g->sigma * sqrt(1.0 / sq3 + 0.5 * sq3)) + 1e-6f;
-  k_mc_prep<<<grid, 64, 0, s>>>(n_cert_dev, X.mc_plen, X.mc_pedges, X.path_buf, g->states, g->tau, g->W, S,
+  k_mc_prep<<<grid, kPrepThreads, 0, s>>>(n_cert_dev, X.mc_plen, X.mc_pedges, X.path_buf, g->states, g->tau, g->W, S,
                                 g->sigma, g->boxes, g->n_boxes, B, X.mc_table);
   note_launch();
   PUMP_CUDA_TRY(cudaMemsetAsync(X.mc_count, 0, sizeof(int64_t) * std::max(n_cert, 1), s));
