@@ -85,7 +85,7 @@ typedef struct {
   float lambda;           /* group cost factor in (0, 1] (Algorithm 2, Algorithm 4)        */
   int32_t n_mc;           /* Monte Carlo rollouts per certification (Section III-A)       */
   int32_t mc_substeps;    /* rollout sub-steps per waypoint interval (>= 1)                */
-  uint64_t mc_seed;       /* Philox4x64-10 key of the rollout normals                      */
+  uint64_t mc_seed;       /* Philox4x32-10 key (lo, hi words) of the rollout normals       */
   int64_t max_plans;      /* plan arena capacity; more survivors -> PUMP_ERR_CAPACITY      */
   int32_t max_iterations; /* cap on Explore's group index; exceeded -> PUMP_ERR_TIMEOUT    */
   int32_t flags;          /* PUMP_NO_EARLY_STOP | PUMP_EXPLORE_ONLY | PUMP_STEPWISE |
@@ -306,9 +306,11 @@ void pump_server_destroy(pump_server* s);
  * rollouts of the closed loop: deviation drawn from the stationary
  * covariance at x_init and carried across connections; each waypoint
  * interval split into `substeps` steps of h/substeps; a rollout collides
- * iff a sub-step position lies in a box.  Rollout m, step s, axis j draws
- * its two normals by Box-Muller from Philox4x64-10 with counter (m, s, j, 0)
- * and key (seed, 0).  Writes the colliding count and count / n_mc.
+ * iff a sub-step position lies in a box.  Rollout m, step s takes two
+ * Philox4x32-10 calls, counters (m, s lo, q, s hi) for q = 0, 1 and key
+ * (seed lo, seed hi); axis j draws its two normals by Box-Muller from the top
+ * 24 bits of words 2j and 2j+1 of the eight.  Writes the colliding count and
+ * count / n_mc.
  * Errors: INVALID_ARG (imported graph, path not along edges), OOM, CUDA.
  * Synchronises.
  */

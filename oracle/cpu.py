@@ -73,6 +73,7 @@ def lib():
             L.orc_explore_free.argtypes = [P]
             L.orc_pair_costs.argtypes = [P, C.c_int, P]
             L.orc_philox4x64.argtypes = [P, P, P]
+            L.orc_philox4x32.argtypes = [P, P, P]
             L.orc_mc_normals.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, P]
             L.orc_mlp_draws.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int32, P, P]
             L.orc_mc_certify.argtypes = [P, P, C.c_int, P, C.c_int, C.c_float, P, C.c_int, C.c_int64,
@@ -235,6 +236,12 @@ def explore(n: int, row_ptr, col, ecost, emask, start: int, goal_idx, K_min: int
 def philox4x64(counter, key) -> np.ndarray:
     c = _c(counter, np.uint64); k = _c(key, np.uint64); o = np.zeros(4, np.uint64)
     lib().orc_philox4x64(_p(c), _p(k), _p(o))
+    return o
+
+
+def philox4x32(counter, key) -> np.ndarray:
+    c = _c(counter, np.uint32); k = _c(key, np.uint32); o = np.zeros(4, np.uint32)
+    lib().orc_philox4x32(_p(c), _p(k), _p(o))
     return o
 
 

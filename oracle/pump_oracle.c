@@ -893,6 +893,22 @@ void orc_philox4x64(const uint64_t* ctr_in, const uint64_t* key_in, uint64_t* ou
   for (int q = 0; q < 4; ++q) out[q] = c[q];
 }
 
+/* Philox4x32-10 (same paper): the 32-bit form, multipliers 0xD2511F53 and     */
+/* 0xCD9E8D57, Weyl constants 0x9E3779B9 and 0xBB67AE85, the same round.         */
+void orc_philox4x32(const uint32_t* ctr_in, const uint32_t* key_in, uint32_t* out) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += W0; k1 += W1; }
+    const uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+  for (int q = 0; q < 4; ++q) out[q] = c[q];
+}
+
 /* Standard normal pair from two 24-bit integers (Box and Muller, 1958):      */
 /* u = (bits + 1/2) 2^-24 in (0, 1), z0 = sqrt(-2 ln u1) cos(2 pi u2),          */
 /* z1 = sqrt(-2 ln u1) sin(2 pi u2), evaluated in double and rounded to float.  */
@@ -905,14 +921,18 @@ static void box_muller(uint64_t b1, uint64_t b2, float* z0, float* z1) {
   *z1 = (float)(rad * sin(ang));
 }
 
-/* Normals (xi0, xi1) of rollout m, step s, for the three axes: one Philox4x64-10 */
-/* call with counter (m, s, 0, 0) and key (seed, 0); axis j takes word j, whose  */
-/* bits 63..40 give u1 and bits 39..16 give u2.                                   */
+/* Normals (xi0, xi1) of rollout m, step s, for the three axes: two            */
+/* Philox4x32-10 calls, counters (m, s lo, q, s hi) for q = 0, 1, key (seed lo, */
+/* seed hi); words w0..w3 of the first call and w4, w5 of the second; axis j    */
+/* takes u1 from the top 24 bits of w(2j) and u2 from those of w(2j+1).          */
 void orc_mc_normals(uint64_t seed, uint64_t m, uint64_t s, float* xi /* 3 x 2 */) {
-  uint64_t key[2] = {seed, 0}, c[4] = {m, s, 0, 0}, o[4];
-  orc_philox4x64(c, key, o);
-  for (int j = 0; j < 3; ++j)
-    box_muller(o[j] >> 40, (o[j] >> 16) & 0xFFFFFFull, &xi[2 * j], &xi[2 * j + 1]);
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t w[8];
+  for (uint32_t q = 0; q < 2; ++q) {
+    const uint32_t c[4] = {(uint32_t)m, (uint32_t)s, q, (uint32_t)(s >> 32)};
+    orc_philox4x32(c, key, w + 4 * q);
+  }
+  for (int j = 0; j < 3; ++j) box_muller(w[2 * j] >> 8, w[2 * j + 1] >> 8, &xi[2 * j], &xi[2 * j + 1]);
 }
 
 /* ========================================================================== */

@@ -225,15 +225,18 @@ __global__ void __launch_bounds__(kPrepThreads) k_mc_prep(const int32_t* __restr
   }
 }
 
-// Normals of rollout m, step s for the three axes: one Philox4x64-10 call with counter
-// (m, s, 0, 0), key (seed, 0); axis j takes word j: bits 63..40 -> u1, bits 39..16 -> u2.
+// Normals of rollout m, step s for the three axes: two Philox4x32-10 calls, counters
+// (m, s lo, q, s hi) for q = 0, 1, key (seed lo, seed hi); words w0..w3, w4, w5; axis j takes u1
+// from the top 24 bits of w(2j) and u2 from those of w(2j+1).
 __device__ __forceinline__ void mc_normals(uint64_t seed, uint64_t m, uint64_t s, float* z) {
-  uint64_t o[4];
-  philox4x64(m, s, 0ull, 0ull, seed, 0ull, o);
+  uint32_t w[8];
+#pragma unroll
+  for (uint32_t q = 0; q < 2; ++q)
+    philox4x32((uint32_t)m, (uint32_t)s, q, (uint32_t)(s >> 32), (uint32_t)seed, (uint32_t)(seed >> 32), w + 4 * q);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const float u1 = ((float)(uint32_t)(o[j] >> 40) + 0.5f) * 5.9604644775390625e-08f;
-    const float u2 = ((float)(uint32_t)((o[j] >> 16) & 0xFFFFFFull) + 0.5f) * 5.9604644775390625e-08f;
+    const float u1 = ((float)(w[2 * j] >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    const float u2 = ((float)(w[2 * j + 1] >> 8) + 0.5f) * 5.9604644775390625e-08f;
     // hardware log2 and sine/cosine approximations (absolute error ~2^-21); the clamp keeps r
     // real where the approximate log of a u1 just below 1 comes out positive
     const float r = sqrtf(fmaxf(-2.0f * __logf(u1), 0.0f));
@@ -620,6 +623,20 @@ int ensure_table(pump_graph* g, int S, cudaStream_t s) {
   return PUMP_OK;
 }
 
+// MC form by the batch's plan count (measured): the warp scan up to kMcScanMax plans, two lanes
+// per rollout up to kMcTwoLaneMax, then one.  PUMP_MC_FORM (1, 2, 3) fixes one form (tuning).
+#ifndef PUMP_MC_FORM
+#define PUMP_MC_FORM 0
+#endif
+#ifndef PUMP_MC_SCAN_MAX
+#define PUMP_MC_SCAN_MAX 2
+#endif
+#ifndef PUMP_MC_TWO_LANE_MAX
+#define PUMP_MC_TWO_LANE_MAX 6
+#endif
+constexpr int kMcScanMax = PUMP_MC_SCAN_MAX;
+constexpr int kMcTwoLaneMax = PUMP_MC_TWO_LANE_MAX;
+
 // Certify the plans of the current batch (n_cert read on the device from the state).
 // n_cert: the batch's plan count, known on the host (the device copy n_cert_dev holds the same).
 int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert, int n_mc, int S, uint64_t seed,
@@ -638,14 +655,15 @@ int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert, int n_mc, int
   if (n_mc > 0 && n_cert > 0) {
     const size_t smem_boxes = sizeof(float) * 6 * (size_t)std::max(g->n_boxes, 1);
     unsigned long long* counts = reinterpret_cast<unsigned long long*>(X.mc_count);
-    if (n_cert <= 2) {
+    const int form = PUMP_MC_FORM ? PUMP_MC_FORM : (n_cert <= kMcScanMax ? 1 : (n_cert <= kMcTwoLaneMax ? 2 : 3));
+    if (form == 1) {
       PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_boxes));
       k_mc_scan<<<num_sms() * 4, kMcScanThreads, smem_boxes, s>>>(n_cert_dev, X.mc_plen, X.mc_table, g->W, S,
                                                                   g->linf_dev, g->boxes, g->n_boxes, n_mc, seed, B,
                                                                   counts);
     } else {
       const size_t smem = smem_boxes + sizeof(float) * kMcTableSmem;
-      if (n_cert <= 6) {
+      if (form == 2) {
         const int bpp = (n_mc + kMcThreads / 2 - 1) / (kMcThreads / 2);
         PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_rollout<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_mc_rollout<2><<<n_cert * bpp, kMcThreads, smem, s>>>(n_cert_dev, bpp, X.mc_plen, X.mc_table, g->W, S,

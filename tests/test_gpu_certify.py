@@ -1,6 +1,6 @@
 """MC(p) certification on the GPU vs the CPU oracle.
 
-Both sides draw the same Philox4x64-10 words for every rollout, step and axis and map them to the
+Both sides draw the same Philox4x32-10 words for every rollout, step and axis and map them to the
 same uniforms; Box-Muller differs (the GPU's hardware log and sine/cosine approximations, absolute
 error ~2^-21 per normal, against double rounded to float in the oracle), and the GPU's warp-scan
 form (one or two plans) composes the deviation recurrence across lanes (float rounding ~1e-7

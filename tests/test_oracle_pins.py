@@ -279,6 +279,29 @@ def test_philox4x64_matches_numpy(ctr, key):
     assert np.array_equal(cpu.philox4x64(c, key), ref.astype(np.uint64))
 
 
+@pytest.mark.parametrize("ctr,key,out", [
+    ([0, 0, 0, 0], [0, 0], [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]),
+    ([0xffffffff] * 4, [0xffffffff] * 2, [0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd]),
+    ([0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344], [0xa4093822, 0x299f31d0],
+     [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1])])
+def test_philox4x32_known_answers(ctr, key, out):
+    # known-answer vectors published with the generator (Salmon et al., SC'11, Random123)
+    assert cpu.philox4x32(ctr, key).tolist() == out
+
+
+def test_mc_normals_take_the_documented_philox_words():
+    # rollout m, step s: two Philox4x32-10 calls, counters (m, s lo, q, s hi), key (seed lo, seed hi);
+    # axis j: u1 from the top 24 bits of word 2j, u2 from word 2j + 1, Box-Muller in double
+    seed, m, s = 0x1234567890ABCDEF, 77, (5 << 32) + 9
+    w = np.concatenate([cpu.philox4x32([m, s & 0xffffffff, q, s >> 32], [seed & 0xffffffff, seed >> 32])
+                        for q in (0, 1)]).astype(np.int64)
+    u = ((w[:6] >> 8).astype(np.float64) + 0.5) / 2.0 ** 24
+    r = np.sqrt(-2.0 * np.log(u[0::2]))
+    ang = 2.0 * np.pi * u[1::2]
+    ref = np.stack([r * np.cos(ang), r * np.sin(ang)], axis=1).astype(np.float32)
+    np.testing.assert_array_equal(cpu.mc_normals(seed, m, s), ref)
+
+
 def test_mc_normals_are_standard_normal():
     z = np.concatenate([cpu.mc_normals(7, m, s).ravel() for m in range(300) for s in range(20)])
     assert abs(z.mean()) < 0.03 and abs(z.std() - 1) < 0.03
