@@ -31,7 +31,63 @@ using maskdev::kBoxStride;
 __host__ __device__ constexpr size_t edge_mask_fixed_smem(int nb) { return maskdev::fixed_smem(nb, kWarps); }
 
 // Graph-build pass (obstacle independent): per edge the largest |d0| over all particles,
-// waypoints and axes, as float bits (atomicMax over the edge's words).
+// waypoints and axes, as float bits.  A warp per edge: lane l runs particles 32 (w0 + j) + l of
+// NW words side by side (pairs of words in packed FP32x2 registers), the edge's Phi and L loaded
+// once; the warp's maximum is stored directly.
+#ifndef PUMP_BOUND_PACKED
+#define PUMP_BOUND_PACKED 1
+#endif
+template <int NW>
+__device__ __forceinline__ float bound_pass(const float2* __restrict__ xi, int N, int W, const float (&P)[4],
+                                            const float (&L)[3], const float (&linf)[3], int w0, int lane) {
+  const float2* xq = xi + w0 * 32 + lane;
+  float m = 0.f;
+  if constexpr (PUMP_BOUND_PACKED && NW % 2 == 0) {
+    const unsigned long long P2[4] = {maskdev::pk2(P[0], P[0]), maskdev::pk2(P[1], P[1]), maskdev::pk2(P[2], P[2]),
+                                      maskdev::pk2(P[3], P[3])};
+    const unsigned long long L2[3] = {maskdev::pk2(L[0], L[0]), maskdev::pk2(L[1], L[1]), maskdev::pk2(L[2], L[2])};
+    const unsigned long long I2[3] = {maskdev::pk2(linf[0], linf[0]), maskdev::pk2(linf[1], linf[1]),
+                                      maskdev::pk2(linf[2], linf[2])};
+    constexpr int NP = NW / 2 > 0 ? NW / 2 : 1;
+    unsigned long long d0[NP][3], d1[NP][3];
+#pragma unroll
+    for (int j = 0; j < NW / 2; ++j)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        maskdev::dev_init2(I2, xq[(size_t)a * N + 64 * j], xq[(size_t)a * N + 64 * j + 32], d0[j][a], d1[j][a]);
+    for (int k = 1; k <= W; ++k) {
+      const float2* xk = xq + (size_t)k * 3 * N;
+#pragma unroll
+      for (int j = 0; j < NW / 2; ++j)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          maskdev::dev_step2(P2, L2, xk[(size_t)a * N + 64 * j], xk[(size_t)a * N + 64 * j + 32], d0[j][a], d1[j][a]);
+          float u, v;
+          maskdev::upk2(d0[j][a], u, v);
+          m = fmaxf(m, fmaxf(fabsf(u), fabsf(v)));
+        }
+    }
+    return m;
+  } else {
+  float d0[NW][3], d1[NW][3];
+#pragma unroll
+  for (int j = 0; j < NW; ++j)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dev_init(linf, xq[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+  for (int k = 1; k <= W; ++k) {
+    const float2* xk = xq + (size_t)k * 3 * N;
+#pragma unroll
+    for (int j = 0; j < NW; ++j)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        dev_step(P, L, xk[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+        m = fmaxf(m, fabsf(d0[j][a]));
+      }
+  }
+  return m;
+  }
+}
+
 template <bool kSmemXi>
 __global__ void __launch_bounds__(kWarps * 32) k_edge_bound(const float2* __restrict__ xi_g, int N, int W,
                                                             const float* __restrict__ phi,
@@ -47,25 +103,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_edge_bound(const float2* __rest
   const float2* xi = kSmemXi ? xi_s : xi_g;
   const float linf[3] = {linf_g[0], linf_g[1], linf_g[2]};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long items = (long long)E * w;
-  for (long long it = (long long)blockIdx.x * kWarps + warp; it < items; it += (long long)gridDim.x * kWarps) {
-    const int e = (int)(it / w), word = (int)(it % w);
-    const int i = word * 32 + lane;
-    const float P[4] = {phi[4 * (size_t)e], phi[4 * (size_t)e + 1], phi[4 * (size_t)e + 2], phi[4 * (size_t)e + 3]};
-    const float L[3] = {Lg[3 * (size_t)e], Lg[3 * (size_t)e + 1], Lg[3 * (size_t)e + 2]};
+  for (long long e = (long long)blockIdx.x * kWarps + warp; e < E; e += (long long)gridDim.x * kWarps) {
+    const float P[4] = {phi[4 * e], phi[4 * e + 1], phi[4 * e + 2], phi[4 * e + 3]};
+    const float L[3] = {Lg[3 * e], Lg[3 * e + 1], Lg[3 * e + 2]};
     float m = 0.f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      float d0, d1;
-      dev_init(linf, xi[(size_t)a * N + i], d0, d1);
-      for (int k = 1; k <= W; ++k) {
-        dev_step(P, L, xi[((size_t)k * 3 + a) * N + i], d0, d1);
-        m = fmaxf(m, fabsf(d0));
-      }
+    int w0 = 0;
+    for (; w0 + 4 <= w; w0 += 4) m = fmaxf(m, bound_pass<4>(xi, N, W, P, L, linf, w0, lane));
+    if (w0 + 2 <= w) {
+      m = fmaxf(m, bound_pass<2>(xi, N, W, P, L, linf, w0, lane));
+      w0 += 2;
     }
+    if (w0 < w) m = fmaxf(m, bound_pass<1>(xi, N, W, P, L, linf, w0, lane));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) atomicMax(dbound + e, __float_as_uint(m));
+    if (lane == 0) dbound[e] = __float_as_uint(m);
   }
 }
 
@@ -351,10 +402,9 @@ int compute_edge_bounds(pump_graph* g, cudaStream_t s) {
   g->dmax = (unsigned int*)graph_alloc(g, sizeof(unsigned int) * (size_t)g->E, s);
   unsigned int* dbound = g->dmax;
   if (!dbound) return PUMP_ERR_OOM;
-  PUMP_CUDA_TRY(cudaMemsetAsync(dbound, 0, sizeof(unsigned int) * (size_t)g->E, s));
   const size_t smem_xi = sizeof(float2) * (size_t)(g->W + 1) * 3 * g->N;
   const bool use_smem = smem_xi <= 160 * 1024;
-  const long long items = (long long)g->E * g->n_words;
+  const long long items = (long long)g->E;  // a warp per edge
   int grid = 1;
   if (use_smem) {
     {

@@ -45,6 +45,46 @@ __device__ __forceinline__ void dev_step(const float* P, const float* L, float2 
   d1 = e1;
 }
 
+// Two floats in one 64-bit register and the packed FP32x2 operations of sm_100-class parts: each
+// half is rounded exactly as the scalar __fmul_rn / fmaf, so pairs of particles advance with
+// the same arithmetic in half the instructions.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// dev_init / dev_step for two particles at once (x, y: their normals' pairs).
+__device__ __forceinline__ void dev_init2(const unsigned long long* linf2, float2 x, float2 y, unsigned long long& d0,
+                                          unsigned long long& d1) {
+  const unsigned long long X0 = pk2(x.x, y.x), X1 = pk2(x.y, y.y);
+  d0 = mul2(linf2[0], X0);
+  d1 = fma2(linf2[1], X0, mul2(linf2[2], X1));
+}
+__device__ __forceinline__ void dev_step2(const unsigned long long* P2, const unsigned long long* L2, float2 x, float2 y,
+                                          unsigned long long& d0, unsigned long long& d1) {
+  const unsigned long long X0 = pk2(x.x, y.x), X1 = pk2(x.y, y.y);
+  const unsigned long long n0 = mul2(L2[0], X0);
+  const unsigned long long n1 = fma2(L2[1], X0, mul2(L2[2], X1));
+  const unsigned long long e0 = fma2(P2[0], d0, fma2(P2[1], d1, n0));
+  const unsigned long long e1 = fma2(P2[2], d0, fma2(P2[3], d1, n1));
+  d0 = e0;
+  d1 = e1;
+}
+
 // NW mask words of one edge: lane l advances particles 32 (w0 + j) + l, j < NW, side by side
 // through waypoints 1..k_last and tests the boxes left at each; the words are the warp ballots.
 // The warp stops early once every lane's particles have hit.
