@@ -390,7 +390,8 @@ def measured_traffic(kernel):
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        names = rec["sources"] if "sources" in rec else [rec["source"]]
+        src = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in names)
     except (OSError, KeyError, ValueError):
         return None
     if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
