@@ -208,11 +208,12 @@ int pump_explore(pump_graph* g, const pump_plan_params* params, float radius, pu
  * descending cost then ascending id; 1-based bisection with MC(P_m) > alpha
  * moving u = m - 1, else l = m; failure if the final MC(P_m) > alpha.
  * Smoothing is not applied.  `path` (host, capacity path_cap) receives the
- * node ids of the selected plan from x_init.  From a graph's second query on
- * (its edge order laid out once, then reused), the box masks run inside the
- * Explore launch where the device allows it (out->fused); the environment
- * variable PUMP_FUSED_MASKS=0 keeps them separate, =1 fuses from the first
- * query.  Results are the same either way.  `out` is written on PUMP_OK
+ * node ids of the selected plan from x_init.  The box masks run inside the
+ * Explore launch where the device allows it (out->fused); the graph's first
+ * such query also lays out its edge order (rows by shortest-path cost from
+ * the start), which later queries reuse.  The environment variable
+ * PUMP_FUSED_MASKS=0 keeps the masks in their own launch.  Results are the
+ * same either way.  `out` is written on PUMP_OK
  * and on PUMP_ERR_INFEASIBLE (out->status tells which).  Synchronises.
  * Errors: those of pump_explore, plus INFEASIBLE (no certified plan).
  */

@@ -1220,23 +1220,25 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t
 }
 
 // Row order of the fused form.  Shortest-path cost from the start over the graph's edges
-// (float sums; an ordering key only), by label-correcting rounds in one cooperative launch: a
-// warp per node whose cost fell in the previous round relaxes its out-edges (atomicMin on the
-// float bits, which order like the non-negative costs).  changed[r mod 3] says whether round r
-// has work; every thread reads it after the same grid barrier, so all leave together.
-__global__ void k_sssp(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                       const float* __restrict__ ecost, int32_t n, int32_t start, uint32_t* dist, uint8_t* fa,
-                       uint8_t* fb, int32_t* changed, int32_t max_rounds) {
-  cg::grid_group grid = cg::this_grid();
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nt = (long long)gridDim.x * blockDim.x;
+// (float sums; an ordering key only), by label-correcting rounds inside one thread-block cluster
+// (hardware cluster barriers between rounds): a warp per node whose cost fell in the previous
+// round relaxes its out-edges (atomicMin on the float bits, which order like the non-negative
+// costs).  changed[r mod 3] says whether round r has work; every thread reads it after the same
+// barrier, so all leave together.  At most max_rounds rounds (rows still unreached sort last).
+__global__ void __launch_bounds__(1024, 1) k_sssp(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                                  const float* __restrict__ ecost, int32_t n, int32_t start,
+                                                  uint32_t* dist, uint8_t* fa, uint8_t* fb, int32_t* changed,
+                                                  int32_t max_rounds) {
+  cg::cluster_group cl = cg::this_cluster();
+  const long long tid = (long long)cl.block_rank() * blockDim.x + threadIdx.x;
+  const long long nt = (long long)cl.num_blocks() * blockDim.x;
   for (long long x = tid; x < n; x += nt) {
     dist[x] = x == start ? 0u : 0x7f800000u;
     fa[x] = x == start ? 1 : 0;
     fb[x] = 0;
   }
   if (tid < 3) changed[tid] = tid == 0 ? 1 : 0;
-  grid.sync();
+  cl.sync();
   const int lane = threadIdx.x & 31;
   const long long gw = tid >> 5, nw = nt >> 5;
   for (int r = 0; r < max_rounds; ++r) {
@@ -1244,28 +1246,54 @@ __global__ void k_sssp(const int32_t* __restrict__ row_ptr, const int32_t* __res
     uint8_t* cur = (r & 1) ? fb : fa;
     uint8_t* nxt = (r & 1) ? fa : fb;
     bool any = false;
-    for (long long x = gw; x < n; x += nw) {
-      if (!__ldcg(cur + x)) continue;
-      const float dx = __uint_as_float(__ldcg(dist + x));
-      const int32_t e1 = row_ptr[x + 1];
-      for (int32_t e = row_ptr[x] + lane; e < e1; e += 32) {
-        const int32_t y = col[e];
-        const uint32_t nd = __float_as_uint(__fadd_rn(dx, ecost[e]));
-        if (nd < atomicMin(dist + y, nd)) {
-          nxt[y] = 1;
-          any = true;
+    // a warp takes 32 consecutive nodes at a time: their flags and row bounds in one load each
+    for (long long b = gw * 32; b < n; b += nw * 32) {
+      const long long xl = b + lane;
+      const bool on = xl < n && __ldcg(cur + xl) != 0;
+      const int32_t r0l = on ? row_ptr[xl] : 0, r1l = on ? row_ptr[xl + 1] : 0;
+      const float dl = on ? __uint_as_float(__ldcg(dist + xl)) : 0.f;
+      if (on) cur[xl] = 0;
+      // the flagged nodes' out-edges as one list (warp scan of their degrees); lanes take list
+      // positions k, k + 32, ... so the loads of all of them are in flight together
+      const int32_t degl = r1l - r0l;
+      int32_t incl = degl;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      for (int32_t k0 = 0; k0 < total; k0 += 32) {
+        const int32_t k = k0 + lane;
+        // source lane: the least lane whose inclusive prefix exceeds k
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+          if (v <= k) lo += step;
+        }
+        const int32_t before = __shfl_sync(0xffffffffu, incl - degl, lo);
+        const int32_t e0 = __shfl_sync(0xffffffffu, r0l, lo);
+        const float dx = __shfl_sync(0xffffffffu, dl, lo);
+        if (k < total) {
+          const int32_t e = e0 + (k - before);
+          const int32_t y = col[e];
+          const uint32_t nd = __float_as_uint(__fadd_rn(dx, ecost[e]));
+          if (nd < atomicMin(dist + y, nd)) {
+            nxt[y] = 1;
+            any = true;
+          }
         }
       }
-      __syncwarp();
-      if (lane == 0) cur[x] = 0;
     }
     if (__any_sync(0xffffffffu, any) && lane == 0) changed[(r + 1) % 3] = 1;
     if (tid == 0) changed[(r + 2) % 3] = 0;
-    grid.sync();
+    cl.sync();
   }
 }
 
 constexpr int kOrderBuckets = 4096;
+constexpr int kSsspRounds = 64;  // label-correcting rounds of the row order (converged in 11 on the indoor graph)
 constexpr int kOrderThreads = 1024;
 
 // Exclusive prefix of one value per thread over a kOrderThreads block; *tot gets the sum.
@@ -1571,67 +1599,131 @@ int run_explore_cluster_batch(const ExploreArgs* As_dev, const int32_t* starts_d
   return e == cudaSuccess ? PUMP_OK : PUMP_ERR_CUDA;
 }
 
-int fused_masks_env() {
+bool fused_masks_env() {
   const char* e = getenv("PUMP_FUSED_MASKS");
-  return e ? (atoi(e) != 0 ? 1 : 0) : -1;
+  return !(e && atoi(e) == 0);
+}
+
+// Side stream of the calling host thread (one per device, highest priority, so its blocks are
+// placed first when the graph build's own kernels become ready with them) and its two events.
+struct SideStream {
+  int dev = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static SideStream* side_stream() {
+  thread_local std::vector<SideStream> v;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  for (auto& x : v)
+    if (x.dev == dev) return &x;
+  SideStream x;
+  x.dev = dev;
+  int lo = 0, hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&x.s, cudaStreamNonBlocking, hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  v.push_back(x);
+  return &v.back();
 }
 
 // Row order of the fused form, once per graph (its arrays do not change afterwards): costs from
-// the start (k_sssp, cooperative), rows sorted by them, edges in that row order.  *ok = false
-// when the device cannot launch the cooperative pass (nothing is kept then).
-static int ensure_row_order(pump_graph* g, cudaStream_t s, bool* ok) {
-  *ok = g->eorder != nullptr;
-  if (*ok) return PUMP_OK;
-  int dev = 0, coop = 0;
-  PUMP_CUDA_TRY(cudaGetDevice(&dev));
-  PUMP_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  if (!coop) return PUMP_OK;
+// the start (k_sssp, one cluster), rows sorted by them, edges in that row order.  The kernels
+// run on stream `ks`; the memory comes from stream s.  row_order_begin starts them (on the
+// calling thread's side stream when `overlap`, after the work already on s), row_order_end
+// makes s wait for them and keeps the result.  Where the device cannot run the cluster pass,
+// nothing is kept and the fused form is not used.
+int row_order_begin(pump_graph* g, cudaStream_t s, bool overlap) {
+  if (g->eorder || g->order_scratch || g->E == 0 || g->hsmc) return PUMP_OK;
   const int32_t n = g->n;
-  const int threads = 1024;  // few blocks: the grid barrier of every round is cheaper
-  int per_sm = 0;
-  PUMP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sssp, threads, 0));
-  if (per_sm < 1) return PUMP_OK;
-  const int64_t want = ((int64_t)n + threads / 32 - 1) / (threads / 32);  // a warp per node
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per_sm * num_sms()));
-  uint32_t* dist = (uint32_t*)dev_alloc(sizeof(uint32_t) * (size_t)n, s);
-  uint8_t* fa = (uint8_t*)dev_alloc(2 * (size_t)n + 16, s);
-  int32_t* changed = (int32_t*)dev_alloc(sizeof(int32_t) * 4, s);
-  int32_t* order = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)n, s);
-  int32_t* epos = (int32_t*)dev_alloc(sizeof(int32_t) * ((size_t)n + 1), s);
-  int2* eo = (int2*)graph_alloc(g, sizeof(int2) * (size_t)g->E, s);
-  uint32_t* rowcnt = (uint32_t*)graph_alloc(g, sizeof(uint32_t) * ((size_t)n + 1), s);
-  int rc = (dist && fa && changed && order && epos && eo && rowcnt) ? PUMP_OK : PUMP_ERR_OOM;
-  if (!rc) {
-    const int32_t* row_ptr = g->row_ptr;
-    const int32_t* col = g->col;
-    const float* ecost = g->ecost;
-    int32_t nn = n, start = g->start, max_rounds = n + 1;
-    uint8_t* fb = fa + n;
-    void* args[] = {(void*)&row_ptr, (void*)&col, (void*)&ecost, &nn, &start, &dist, &fa, &fb, &changed, &max_rounds};
-    if (cudaLaunchCooperativeKernel((void*)k_sssp, dim3(blocks), dim3(threads), args, 0, s) != cudaSuccess) {
-      cudaGetLastError();
-      rc = -1;  // not available: the caller keeps the separate launches
-    } else {
-      note_launch();
-      k_row_order<<<1, kOrderThreads, 0, s>>>(dist, g->row_ptr, n, order, epos);
-      note_launch();
-      const int eb = (int)std::min<int64_t>(((int64_t)n * 32 + 255) / 256, 4096);
-      k_edge_order<<<eb, 256, 0, s>>>(order, epos, g->row_ptr, n, eo);
-      note_launch();
-      if (cudaGetLastError() != cudaSuccess) rc = PUMP_ERR_CUDA;
-    }
+  // one graph allocation (edge order, then the counts) and one scratch allocation: an allocator
+  // call can cost more than these kernels
+  const size_t eo_bytes = (sizeof(int2) * (size_t)g->E + 255) & ~size_t(255);
+  unsigned char* keep = (unsigned char*)graph_alloc(g, eo_bytes + sizeof(uint32_t) * ((size_t)n + 1), s);
+  const size_t n4 = ((size_t)n + 64) & ~size_t(63);  // 4-byte words per n-sized part, padded
+  uint32_t* scratch = (uint32_t*)dev_alloc(sizeof(uint32_t) * (3 * n4 + 64) + 2 * n4 + 64, s);
+  if (!keep || !scratch) {
+    if (scratch) dev_free(scratch, s);
+    return PUMP_ERR_OOM;
   }
-  dev_free(epos, s);
-  dev_free(order, s);
-  dev_free(changed, s);
-  dev_free(fa, s);
-  dev_free(dist, s);
-  if (rc == -1) return PUMP_OK;
-  if (rc) return rc;
-  g->eorder = eo;
-  g->rowcnt = rowcnt;
-  *ok = true;
+  int2* eo = reinterpret_cast<int2*>(keep);
+  uint32_t* dist = scratch;
+  int32_t* order = reinterpret_cast<int32_t*>(scratch + n4);
+  int32_t* epos = reinterpret_cast<int32_t*>(scratch + 2 * n4);
+  int32_t* changed = reinterpret_cast<int32_t*>(scratch + 3 * n4);
+  uint8_t* fa = reinterpret_cast<uint8_t*>(scratch + 3 * n4 + 64);
+  uint8_t* fb = fa + n;
+  SideStream* side = overlap ? side_stream() : nullptr;
+  cudaStream_t ks = s;
+  if (side && cudaEventRecord(side->fork, s) == cudaSuccess && cudaStreamWaitEvent(side->s, side->fork, 0) == cudaSuccess)
+    ks = side->s;
+  cudaGetLastError();
+  int32_t nn = n, start = g->start, max_rounds = kSsspRounds;
+  // one cluster: 16 CTAs where the device co-schedules them, else 8
+  cudaError_t e = cudaErrorUnknown;
+  for (int nr : {16, 8}) {
+    if (nr > 8 && cudaFuncSetAttribute(k_sssp, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(nr);
+    cfg.blockDim = dim3(1024);
+    cfg.stream = ks;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nr;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_sssp, g->row_ptr, g->col, g->ecost, nn, start, dist, fa, fb, changed, max_rounds);
+    if (e == cudaSuccess) break;
+    cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    note_launch();
+    k_row_order<<<1, kOrderThreads, 0, ks>>>(dist, g->row_ptr, n, order, epos);
+    note_launch();
+    const int eb = (int)std::min<int64_t>(((int64_t)n * 32 + 255) / 256, 4096);
+    k_edge_order<<<eb, 256, 0, ks>>>(order, epos, g->row_ptr, n, eo);
+    note_launch();
+  }
+  const bool launched = e == cudaSuccess && cudaGetLastError() == cudaSuccess;
+  if (ks != s) {  // s waits for the side stream at row_order_end (the scratch stays until then)
+    PUMP_CUDA_TRY(cudaEventRecord(side->join, ks));
+    g->order_join = side->join;
+  }
+  g->order_scratch = scratch;
+  g->order_keep = launched ? keep : nullptr;
   return PUMP_OK;
+}
+
+int row_order_end(pump_graph* g, cudaStream_t s) {
+  if (!g->order_scratch) return PUMP_OK;
+  if (g->order_join) PUMP_CUDA_TRY(cudaStreamWaitEvent(s, g->order_join, 0));
+  g->order_join = nullptr;
+  dev_free(g->order_scratch, s);
+  g->order_scratch = nullptr;
+  if (g->order_keep) {
+    const size_t eo_bytes = (sizeof(int2) * (size_t)g->E + 255) & ~size_t(255);
+    g->eorder = reinterpret_cast<int2*>(g->order_keep);
+    g->rowcnt = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(g->order_keep) + eo_bytes);
+    g->order_keep = nullptr;
+  }
+  return PUMP_OK;
+}
+
+// The order for a graph that has none yet (on s).
+static int ensure_row_order(pump_graph* g, cudaStream_t s, bool* ok) {
+  int rc = row_order_begin(g, s, false);
+  if (!rc) rc = row_order_end(g, s);
+  *ok = g->eorder != nullptr;
+  return rc;
 }
 
 // Fused form per device and shared-memory size: clusters the kernel can keep resident at once

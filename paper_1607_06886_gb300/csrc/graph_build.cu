@@ -819,6 +819,12 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
     k_scatter_edges<<<glist, kBlock, 0, s>>>(list, (long long)n_list, n, keep, wpre, res_tau, res_cost, src, g->col,
                                              etau, g->ecost);
     note_launch();
+    // the adjacency and costs are final: the fused form's edge order is laid out beside the
+    // per-edge fill and the deviation bounds (a side stream; joined before the build returns)
+    if (!g->hsmc && fused_masks_env()) {
+      const int rco = row_order_begin(g, s, true);
+      if (rco) return rco;
+    }
     k_fill_edges<<<(E + 127) / 128, 128, 0, s>>>(g->states, E, g->W, g->sigma, src, g->col, etau, g->tau, g->h,
                                                  g->phi, g->L, g->nom, g->nvel);
     note_launch();
@@ -832,6 +838,10 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   if (g->hsmc) {
     const int rch = build_halfspaces(g, s);
     if (rch) return rch;
+  }
+  {
+    const int rco = row_order_end(g, s);
+    if (rco) return rco;
   }
   // valid node count (for export)
   PUMP_CUDA_TRY(cudaMemsetAsync(deg, 0, sizeof(int32_t), s));

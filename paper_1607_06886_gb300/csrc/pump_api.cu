@@ -267,10 +267,10 @@ static void destroy(pump_graph* g) {
   if (!g) return;
   cudaStream_t s = 0;
   cudaDeviceSynchronize();
+  row_order_end(g, s);  // an edge order still being laid out (a build that failed): its scratch
   for (auto& b : g->bufs) dev_free(b.ptr, s);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
-  if (g->ctl_host) cudaFreeHost(g->ctl_host);
   cudaDeviceSynchronize();
   delete g;
 }
@@ -279,12 +279,12 @@ static void destroy(pump_graph* g) {
 // running (the server's workers).
 void destroy_on_stream(pump_graph* g, cudaStream_t s) {
   if (!g) return;
+  row_order_end(g, s);  // s waits for a side stream still laying out the edge order
   cudaStreamSynchronize(s);
   for (auto& b : g->bufs) dev_free(b.ptr, s);
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   cudaStreamSynchronize(s);
-  if (g->ctl_host) cudaFreeHost(g->ctl_host);
   delete g;
 }
 
@@ -297,10 +297,25 @@ int check_plan_params(const pump_plan_params* p) {
   return PUMP_OK;
 }
 
+// Pinned host copy of Explore's control block, one per host thread (a graph is used by one
+// thread at a time), allocated once: pinned allocations cost far more than a query's readback.
+static ExploreCtl* thread_ctl_host() {
+  struct Buf {
+    ExploreCtl* p = nullptr;
+    ~Buf() {
+      if (p) cudaFreeHost(p);
+    }
+  };
+  thread_local Buf b;
+  if (!b.p && cudaHostAlloc((void**)&b.p, sizeof(ExploreCtl), cudaHostAllocDefault) != cudaSuccess) b.p = nullptr;
+  return b.p;
+}
+
 int make_events(pump_graph* g) {
   for (auto& e : g->ev)
     if (!e) PUMP_CUDA_TRY(cudaEventCreate(&e));
-  if (!g->ctl_host) PUMP_CUDA_TRY(cudaHostAlloc((void**)&g->ctl_host, sizeof(ExploreCtl), cudaHostAllocDefault));
+  g->ctl_host = thread_ctl_host();
+  if (!g->ctl_host) return PUMP_ERR_CUDA;
   return PUMP_OK;
 }
 
@@ -493,12 +508,9 @@ int pump_plan(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t p
   std::memset(&r, 0, sizeof(r));
   r.chosen_plan = -1;
   PUMP_CUDA_TRY(cudaEventRecord(g->ev[0], s));
-  // box masks may run inside the Explore launch (then ms_masks covers only what precedes it);
-  // by default from the graph's second query, whose run also lays out the edge order once
-  const int fm = fused_masks_env();
-  const bool fuse = g->fuse_masks && !g->hsmc && explore_mode(p->flags) == 0 && fm != 0 &&
-                    (fm == 1 || g->plans_run > 0);
-  ++g->plans_run;
+  // box masks run inside the Explore launch where it applies (then ms_masks covers only what
+  // precedes it); the graph's first such run also lays out its edge order
+  const bool fuse = g->fuse_masks && !g->hsmc && explore_mode(p->flags) == 0 && fused_masks_env();
   if (!fuse) {
     rc = compute_edge_masks(g, s);
     if (rc) return rc;

@@ -183,10 +183,12 @@ struct pump_graph {
   int2* eorder = nullptr;
   uint32_t* rowcnt = nullptr;       // n + 1: finished edges per row, then worker warps finished
   uint32_t fuse_epoch = 0;          // fused runs since the counts were last zeroed
+  void* order_scratch = nullptr;    // edge order being laid out (graph build): its scratch,
+  void* order_keep = nullptr;       // the order's own allocation,
+  cudaEvent_t order_join = nullptr; // and the side stream's event to wait for
   bool rowcnt_dirty = true;         // counts must be zeroed before the next fused run
   bool fuse_masks = true;    // pump_plan may run the masks inside the Explore launch
   bool last_fused = false;   // the last Explore run computed the masks in its launch
-  int64_t plans_run = 0;     // pump_plan calls on this graph
   std::vector<pump::DevBuf> bufs;
   pump::ExploreBufs ex;
   // last explore
@@ -194,7 +196,8 @@ struct pump_graph {
   int64_t last_plans = 0;
   int32_t last_goal = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  pump::ExploreCtl* ctl_host = nullptr;  // pinned copy of Explore's control block (pump_plan)
+  pump::ExploreCtl* ctl_host = nullptr;  // pinned copy of Explore's control block (pump_plan; the
+                                         // calling thread's, not owned by the graph)
 };
 
 namespace pump {
@@ -210,6 +213,10 @@ void* graph_realloc(pump_graph* g, void* old, size_t bytes, cudaStream_t s);
   } while (0)
 
 int build_graph_device(pump_graph* g, cudaStream_t s);
+// Edge order of the fused form (explore_cluster.cu): begun during the graph build (on a side
+// stream when `overlap`), completed on s before the build returns.
+int row_order_begin(pump_graph* g, cudaStream_t s, bool overlap);
+int row_order_end(pump_graph* g, cudaStream_t s);
 int build_halfspaces(pump_graph* g, cudaStream_t s);
 constexpr int kHsMax = 8;  // half-spaces per waypoint (HSMC)
 int compute_edge_masks(pump_graph* g, cudaStream_t s);
@@ -225,9 +232,8 @@ int ensure_explore_bufs(pump_graph* g, int64_t cap, int32_t kmax, cudaStream_t s
 // masks_pending: the query's edge masks are not computed yet; the run computes them, inside the
 // Explore launch where the fused form applies (explore_cluster.cu), else before it.
 int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStream_t s, bool masks_pending = false);
-// Fused masks + Explore per the environment: PUMP_FUSED_MASKS=0 never, =1 from a graph's first
-// query, unset from its second (-1).
-int fused_masks_env();
+// Fused masks + Explore allowed by the environment (PUMP_FUSED_MASKS=0 turns it off).
+bool fused_masks_env();
 int ensure_edge_targets(pump_graph* g, cudaStream_t s);
 int prepare_explore_args(pump_graph* g, const pump_plan_params* p, float radius, ExploreArgs* out, cudaStream_t s);
 int check_plan_params(const pump_plan_params* p);

@@ -78,20 +78,17 @@ def test_fused_equals_separate_launches(name, seed, ns, N):
 
 
 def test_fused_form_is_taken():
-    """By default a graph's first query runs the separate launches and its second and later
-    queries the fused one (one launch fewer: no separate masks kernel)."""
+    """The graph build lays out the edge order (beside its own last kernels) and every query runs
+    the fused launch, one launch fewer than the separate form; PUMP_FUSED_MASKS=0 keeps them
+    separate, and a graph built under it gets its order from its first fused query."""
     wl = workload("indoor_4k", 1, 1500)
-    G = gpu_graph(wl)
     p = plan_params(wl, flags=pump.EXPLORE_ONLY)
     with env(PUMP_FUSED_MASKS=""):
         os.environ.pop("PUMP_FUSED_MASKS")
-        r = G.plan(p)
-        assert r["rc"] == pump.OK and r["fused"] == 0
-        with pytest.raises(pump.PumpError):
-            G.export("edge_order")
-        r = G.plan(p)  # lays out the edge order once
-        assert r["rc"] == pump.OK and r["fused"] == 1
+        G = gpu_graph(wl)
         G.export("edge_order")
+        r = G.plan(p)
+        assert r["rc"] == pump.OK and r["fused"] == 1
         n0 = pump.kernel_launches()
         r = G.plan(p)
         assert r["rc"] == pump.OK and r["fused"] == 1
@@ -99,8 +96,16 @@ def test_fused_form_is_taken():
     with env(PUMP_FUSED_MASKS=0):
         r = G.plan(p)
         assert r["rc"] == pump.OK and r["fused"] == 0
-    n2 = pump.kernel_launches()
+        n2 = pump.kernel_launches()
+        G2 = gpu_graph(wl)
     assert (n2 - n1) == (n1 - n0) + 1
+    with pytest.raises(pump.PumpError):
+        G2.export("edge_order")
+    with env(PUMP_FUSED_MASKS=1):
+        r2 = G2.plan(p)
+    assert r2["fused"] == 1 and r2["n_candidates"] == r["n_candidates"]
+    # the lazily laid out order is an order of the same edges (rows within a cost level may differ)
+    np.testing.assert_array_equal(np.sort(G2.export("edge_order")[:, 0]), np.sort(G.export("edge_order")[:, 0]))
 
 
 def shortest_costs(row_ptr, col, ecost, start):
