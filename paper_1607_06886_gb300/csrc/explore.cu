@@ -95,19 +95,6 @@ __device__ T block_sum(T v) {
   return tot;
 }
 
-__device__ int32_t block_min(int32_t v) {
-  __shared__ int32_t wm[kWarpsT];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if (lane == 0) wm[warp] = v;
-  __syncthreads();
-  int32_t r = wm[0];
-  for (int k = 1; k < kWarpsT; ++k) r = min(r, wm[k]);
-  __syncthreads();
-  return r;
-}
-
 // Sums of K int64 values over the block in one pass (one shared-memory round).
 template <int K>
 __device__ void block_sums(int64_t (&v)[K]) {

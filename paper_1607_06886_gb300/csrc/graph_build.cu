@@ -242,12 +242,10 @@ __global__ void k_steer_filter(const float* __restrict__ states, const int2* __r
   }
 }
 
-// Root of the increasing piece of f on [lo, hi]: Newton safeguarded by bisection, f evaluated in
-// double, the Newton quotient f / f' taken in float.  The quotient only sets the step; its
-// relative error (~1e-7) leaves the iteration converging to the same double root (each step
-// shrinks the error by that factor on top of the quadratic term), without a double division.
-// f and f' with fused multiply-adds (this unit is compiled without contraction; the root solver
-// only needs f's sign to locate the double root, not the as-written rounding).
+// f and f' of the steering polynomial with fused multiply-adds for the refinement's Newton steps
+// (this unit is compiled without contraction; the steps only need f's sign and an approximate
+// quotient f / f', taken in float: its relative error (~1e-7) leaves the iteration converging to
+// the same double root without a double division).
 struct SteerFma {
   double a4, b24, c36, a8;
 };
@@ -256,21 +254,6 @@ __device__ inline double st_f_fma(const SteerFma& k, double t) {
 }
 __device__ inline double st_fp_fma(const SteerFma& k, double t) {
   return __fma_rn(__fma_rn(4.0 * t, t, -k.a8), t, k.b24);
-}
-__device__ inline double st_root_fq(const SteerCoef& c, double lo, double hi) {
-  const SteerFma k{4.0 * c.a, 24.0 * c.b, 36.0 * c.c, 8.0 * c.a};
-  double x = 0.5 * (lo + hi);
-  for (int it = 0; it < 300; ++it) {
-    const double gx = st_f_fma(k, x);
-    if (gx == 0.0) return x;
-    if (gx < 0.0) lo = x; else hi = x;
-    double xn = x - (double)((float)gx / (float)st_fp_fma(k, x));
-    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-    const double step = fabs(xn - x);
-    x = xn;
-    if (step <= 4.0e-16 * fabs(x) || !(hi - lo > 2.5e-16 * fabs(hi))) break;
-  }
-  return x;
 }
 
 // J(t) as t + |dv|^2 / t + 12 |dp - vbar t|^2 / t^3 (the same function as st_J, written as a sum of
