@@ -1612,7 +1612,23 @@ struct SideStream {
   cudaEvent_t fork = nullptr, join = nullptr;
 };
 static SideStream* side_stream() {
-  thread_local std::vector<SideStream> v;
+  struct Holder {
+    std::vector<SideStream> v;
+    ~Holder() {  // the thread ends (a server worker): release its streams and events
+      for (auto& x : v) {
+        int cur = 0;
+        if (cudaGetDevice(&cur) != cudaSuccess) break;
+        cudaSetDevice(x.dev);
+        cudaEventDestroy(x.fork);
+        cudaEventDestroy(x.join);
+        cudaStreamDestroy(x.s);
+        cudaSetDevice(cur);
+      }
+      cudaGetLastError();
+    }
+  };
+  thread_local Holder h;
+  std::vector<SideStream>& v = h.v;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
   for (auto& x : v)
