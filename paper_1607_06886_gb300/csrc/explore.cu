@@ -693,6 +693,18 @@ int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStrea
     k_fill_u32<<<256, 256, 0, s>>>(A.mbest, mb, 0x7f800000u);
     note_launch();
   }
+  if (cl_nr > 0 && masks_pending) {
+    // the fused launch initialises the run and orders P_goal itself
+    bool launched = false;
+    int rc = run_explore_fused(g, A, cl_nr, cl_dsm, s, &launched);
+    if (rc) return rc;
+    if (launched) {
+      g->last_fused = true;
+      return PUMP_OK;
+    }
+    rc = compute_edge_masks(g, s);  // the device cannot run the fused form
+    if (rc) return rc;
+  }
   k_explore_init<<<1, 1, 0, s>>>(A, g->start);
   note_launch();
   PUMP_CUDA_TRY(cudaGetLastError());
@@ -702,17 +714,6 @@ int run_explore_kernels(pump_graph* g, const ExploreArgs& A, int mode, cudaStrea
   PUMP_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   const int sms = num_sms();
   if (cl_nr > 0) {
-    if (masks_pending) {
-      bool launched = false;
-      int rc = run_explore_fused(g, A, cl_nr, cl_dsm, s, &launched);
-      if (rc) return rc;
-      if (launched) {
-        g->last_fused = true;
-        return PUMP_OK;
-      }
-      rc = compute_edge_masks(g, s);  // the device cannot run the fused form
-      if (rc) return rc;
-    }
     const int rc = run_explore_cluster(g, A, cl_nr, cl_dsm, s);
     if (rc) return rc;
     PUMP_CUDA_TRY(cudaGetLastError());

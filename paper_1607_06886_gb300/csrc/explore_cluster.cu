@@ -1159,6 +1159,7 @@ struct FuseArgs {
   int32_t xi_smem;           // the normals fit in shared memory next to the boxes
   int32_t hold_row;          // test hook: this row is never counted (-1: none)
   int32_t head;              // positions [0, head) are computed by the Explore cluster first
+  int32_t* goal_sorted;      // P_goal in PlanSelection order (written after Explore, CTA 0)
 };
 
 // Shared memory a worker CTA uses (boxes, per-warp scratch, normals when they fit).
@@ -1207,12 +1208,16 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t
   const int nr = (int)cl.num_blocks();
   const long long warp = threadIdx.x >> 5;
   if ((int)blockIdx.x < nr) {
-    // shared memory serves as the mask scratch first; explore_one initialises what it uses
+    // the run's initial state (root plan, control block), read by every CTA after the barrier
+    // below; shared memory serves as the mask scratch first, explore_one initialises what it uses
+    if (blockIdx.x == 0 && threadIdx.x == 0) explore_init_thread(A, start);
     mask_positions(F, smem_raw, 0, F.head, (long long)blockIdx.x * kCW + warp, (long long)nr * kCW, false);
-    __syncthreads();
+    cl.sync();
     CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
     uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
     explore_one<kDsm>(A, start, sm, mbl, cl);
+    // P_goal in PlanSelection order (explore_one ends with a cluster barrier: every plan written)
+    if (blockIdx.x == 0) goal_finalize_block(A, A.group, F.goal_sorted);
     return;
   }
   const long long wb = (long long)blockIdx.x - nr, nwb = (long long)gridDim.x - nr;
@@ -1839,6 +1844,7 @@ int run_explore_fused(pump_graph* g, const ExploreArgs& A0, int nr, bool dsm, cu
   F.hold_row = hold ? atoi(hold) : -1;
   if (F.hold_row >= 0) g->rowcnt_dirty = true;  // that row's count stays short
   F.head = (int32_t)std::min<int64_t>(g->E, (int64_t)nr * kCW);
+  F.goal_sorted = g->ex.goal_sorted;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[2];
   cluster_config(&cfg, attr, nr, ncl, smem, s);

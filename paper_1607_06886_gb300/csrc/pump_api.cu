@@ -220,8 +220,10 @@ int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_pla
   ExploreBufs& X = g->ex;
   rc = run_explore_kernels(g, A, explore_mode(p->flags), s, masks_pending);
   if (rc) return rc;
-  rc = run_goal_finalize(g, A, s);
-  if (rc) return rc;
+  if (!g->last_fused) {  // the fused launch orders P_goal itself
+    rc = run_goal_finalize(g, A, s);
+    if (rc) return rc;
+  }
   g->explored = false;
   if (!collect) return PUMP_OK;
   ExploreCtl h;

@@ -79,8 +79,10 @@ def test_fused_equals_separate_launches(name, seed, ns, N):
 
 def test_fused_form_is_taken():
     """The graph build lays out the edge order (beside its own last kernels) and every query runs
-    the fused launch, one launch fewer than the separate form; PUMP_FUSED_MASKS=0 keeps them
-    separate, and a graph built under it gets its order from its first fused query."""
+    the fused launch: one kernel for an explore-only query (initialisation, masks, Explore and the
+    P_goal order), against four separately (masks, initialisation, Explore, P_goal order);
+    PUMP_FUSED_MASKS=0 keeps them separate, and a graph built under it gets its order from its
+    first fused query."""
     wl = workload("indoor_4k", 1, 1500)
     p = plan_params(wl, flags=pump.EXPLORE_ONLY)
     with env(PUMP_FUSED_MASKS=""):
@@ -98,7 +100,7 @@ def test_fused_form_is_taken():
         assert r["rc"] == pump.OK and r["fused"] == 0
         n2 = pump.kernel_launches()
         G2 = gpu_graph(wl)
-    assert (n2 - n1) == (n1 - n0) + 1
+    assert n1 - n0 == 1 and n2 - n1 == 4
     with pytest.raises(pump.PumpError):
         G2.export("edge_order")
     with env(PUMP_FUSED_MASKS=1):
