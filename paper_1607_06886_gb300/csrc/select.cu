@@ -681,6 +681,26 @@ int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert, int n_mc, int
   return PUMP_OK;
 }
 
+// Pinned read-back area of PlanSelection, one per host thread (allocated once): the control
+// block, the selection state, the error flag and the path arrive with one wait per round.
+struct SelHost {
+  ExploreCtl ctl;
+  SelState hs;
+  int32_t err;
+  int32_t path[kMaxPathEdges + 1];
+};
+static SelHost* sel_host() {
+  struct Buf {
+    SelHost* p = nullptr;
+    ~Buf() {
+      if (p) cudaFreeHost(p);
+    }
+  };
+  thread_local Buf b;
+  if (!b.p && cudaHostAlloc((void**)&b.p, sizeof(SelHost), cudaHostAllocDefault) != cudaSuccess) b.p = nullptr;
+  return b.p;
+}
+
 int run_select(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t path_cap, pump_plan_result* out,
                ExploreCtl* ctl_host, cudaStream_t s) {
   ExploreBufs& X = g->ex;
@@ -697,9 +717,12 @@ int run_select(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t 
   SelState* st = (SelState*)X.sel_state;
   const int32_t* n_cert_dev = &st->n_cert;
   PUMP_CUDA_TRY(cudaMemsetAsync(X.sel_err, 0, sizeof(int32_t) * 2, s));
+  SelHost* H = sel_host();
+  if (!H) return PUMP_ERR_CUDA;
   // Explore's outcome on the host: the first batch's plan count picks the certification form
-  PUMP_CUDA_TRY(cudaMemcpyAsync(ctl_host, X.ctl, sizeof(ExploreCtl), cudaMemcpyDeviceToHost, s));
+  PUMP_CUDA_TRY(cudaMemcpyAsync(&H->ctl, X.ctl, sizeof(ExploreCtl), cudaMemcpyDeviceToHost, s));
   PUMP_CUDA_TRY(cudaStreamSynchronize(s));
+  *ctl_host = H->ctl;
   const int G0 = ctl_host->status ? 0 : ctl_host->n_goal;
   SelState hs;
   out->n_certified = 0;
@@ -724,13 +747,15 @@ int run_select(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t 
                                  X.cost, X.popc, X.path_buf, kMaxPathEdges + 1);
     note_launch();
     PUMP_CUDA_TRY(cudaGetLastError());
-    PUMP_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    int32_t err = 0;
-    PUMP_CUDA_TRY(cudaMemcpyAsync(&err, X.sel_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PUMP_CUDA_TRY(cudaMemcpyAsync(&H->hs, st, sizeof(SelState), cudaMemcpyDeviceToHost, s));
+    PUMP_CUDA_TRY(cudaMemcpyAsync(&H->err, X.sel_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     const int ncopy = std::min(path_cap, kMaxPathEdges + 1);
     if (path && ncopy > 0)
-      PUMP_CUDA_TRY(cudaMemcpyAsync(path, X.path_buf, sizeof(int32_t) * ncopy, cudaMemcpyDeviceToHost, s));
+      PUMP_CUDA_TRY(cudaMemcpyAsync(H->path, X.path_buf, sizeof(int32_t) * ncopy, cudaMemcpyDeviceToHost, s));
     PUMP_CUDA_TRY(cudaStreamSynchronize(s));
+    hs = H->hs;
+    const int32_t err = H->err;
+    if (path && ncopy > 0) std::memcpy(path, H->path, sizeof(int32_t) * ncopy);
     if (err) return PUMP_ERR_INVALID_ARG;
     out->n_certified += hs.n_cert;
     if (hs.done) break;
