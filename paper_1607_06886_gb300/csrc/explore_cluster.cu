@@ -65,6 +65,8 @@
 // cleared between runs: run e expects (e - 1) x degree + degree.  Each worker
 // warp also counts itself when done; a CTA that sees every worker warp done
 // (phase B, an unordered read made an acquire by a fence) skips the waits.
+// The launch is the whole explore-only query: cluster 0 also initialises the
+// run before its first barrier and orders P_goal after its last one.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -1201,6 +1203,7 @@ __device__ __forceinline__ void mask_positions(const FuseArgs& F, unsigned char*
 // other clusters are mask workers.  The first positions of the order (the start row and its
 // neighbourhood, one edge per warp) are computed by the Explore cluster itself before it starts,
 // so the first groups do not wait for the workers' first edges; the workers take the rest.
+// Cluster 0 also writes the run's initial state first and P_goal's order last.
 template <bool kDsm>
 __global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t start, FuseArgs F) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1787,8 +1790,8 @@ static void fused_disable(int dev, size_t smem) {
 
 // Masks and Explore in one cooperative launch (k_explore_fused): cluster 0 explores, every other
 // co-resident cluster computes masks.  *launched = false, with nothing of the run enqueued,
-// where the form does not apply (box masks, mbest on chip, a second cluster resident, the
-// cooperative passes available); the caller then runs the separate launches.
+// where the form does not apply (box masks, mbest on chip, a second cluster resident, the edge
+// order available); the caller then runs the separate launches.
 int run_explore_fused(pump_graph* g, const ExploreArgs& A0, int nr, bool dsm, cudaStream_t s, bool* launched) {
   *launched = false;
   if (!dsm || g->hsmc || g->E == 0 || !g->has_geometry) return PUMP_OK;
