@@ -637,6 +637,52 @@ __global__ void k_scatter_edges(const int2* __restrict__ list, long long n_list,
 }
 
 // Per edge: float duration, waypoint step h = tau/W, Phi(h), L(h), nominal waypoints at t = k h.
+// Float-float (a pair of floats, ~48 significant bits; Dekker's and Knuth's exact sum and the
+// fused-multiply-add exact product) evaluation of the nominal cubic.  A value is rounded to float
+// from its float-float form only when that form lies farther than 2^-40 S from both float
+// rounding midpoints around it (S: the sum of the terms' magnitudes; the float-float error is
+// below 0.16 x 2^-40 S and the double evaluation's below 0.001 x 2^-40 S), so the float equals
+// the one the double evaluation rounds to; otherwise the double evaluation is taken.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF s = ff_two_sum(a.hi, b.hi);
+  const FF t = ff_two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = ff_fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return ff_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_fast_two_sum(p, e);
+}
+// The float nearest to v.hi + v.lo, or NaN where that value lies within M of a rounding midpoint.
+__device__ __forceinline__ float ff_round_checked(FF v, float M) {
+  const float f = __fadd_rn(v.hi, v.lo);
+  const float d = __fadd_rn(__fsub_rn(v.hi, f), v.lo);  // v - f (v.hi - f is exact)
+  const float up = __fsub_rn(nextafterf(f, __int_as_float(0x7f800000)), f);
+  const float dn = __fsub_rn(f, nextafterf(f, __int_as_float(0xff800000)));
+  if (f == 0.f || !(up < __int_as_float(0x7f800000)) || !(dn < __int_as_float(0x7f800000))) return __int_as_float(0x7fc00000);
+  return fabsf(d) + M < 0.4995f * fminf(up, dn) ? f : __int_as_float(0x7fc00000);
+}
+
 __global__ void k_fill_edges(const float* __restrict__ states, int E, int W, float sigma,
                              const int32_t* __restrict__ src, const int32_t* __restrict__ col,
                              const double* __restrict__ etau, float* tau_o, float* h_o, float* phi_o, float* L_o,
@@ -663,10 +709,27 @@ __global__ void k_fill_edges(const float* __restrict__ states, int E, int W, flo
   const double td = (double)t32;
   for (int j = 0; j < 3; ++j) {
     const Cubic c = cubic_dev(xv, xu, td, j);
+    // the cubic's terms in float-float (kk h has at most 30 significant bits: t is exact)
+    const FF p0 = ff_from_double(c.p0), v0 = ff_from_double(c.v0), c2 = ff_from_double(c.c2),
+             c3 = ff_from_double(c.c3), c2x2 = ff_from_double(2.0 * c.c2), c3x3 = ff_from_double(3.0 * c.c3);
+    const float a0 = fabsf(p0.hi), a1 = fabsf(v0.hi), a2 = fabsf(c2.hi), a3 = fabsf(c3.hi);
     for (int kk = 1; kk <= W; ++kk) {
       const double tk = (double)kk * (double)h;
-      nom_o[((size_t)e * W + (kk - 1)) * 3 + j] = __double2float_rn(cubic_at(c, tk));
-      nvel_o[((size_t)e * W + (kk - 1)) * 3 + j] = __double2float_rn(c.v0 + 2.0 * c.c2 * tk + 3.0 * c.c3 * tk * tk);
+      const FF t = ff_from_double(tk);
+      const float tf = fabsf(t.hi);
+      // nominal position p0 + v0 t + c2 t t + c3 t t t, in the double evaluation's association
+      const FF pos = ff_add(ff_add(ff_add(p0, ff_mul(v0, t)), ff_mul(ff_mul(c2, t), t)),
+                            ff_mul(ff_mul(ff_mul(c3, t), t), t));
+      const float Sp = 1.0001f * (a0 + tf * (a1 + tf * (a2 + tf * a3)));
+      float fp = ff_round_checked(pos, Sp * 0x1p-40f);
+      if (fp != fp) fp = __double2float_rn(cubic_at(c, tk));
+      nom_o[((size_t)e * W + (kk - 1)) * 3 + j] = fp;
+      // nominal velocity v0 + 2 c2 t + 3 c3 t t
+      const FF vel = ff_add(ff_add(v0, ff_mul(c2x2, t)), ff_mul(ff_mul(c3x3, t), t));
+      const float Sv = 1.0001f * (a1 + tf * (2.0f * a2 + 3.0f * tf * a3));
+      float fv = ff_round_checked(vel, Sv * 0x1p-40f);
+      if (fv != fv) fv = __double2float_rn(c.v0 + 2.0 * c.c2 * tk + 3.0 * c.c3 * tk * tk);
+      nvel_o[((size_t)e * W + (kk - 1)) * 3 + j] = fv;
     }
   }
 }
