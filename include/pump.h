@@ -64,7 +64,7 @@ typedef struct {
   int32_t n_particles; /* N, a multiple of 32 in [32, 1024]; masks have N/32 words       */
   int32_t n_waypoints; /* W >= 1 waypoints per connection                                */
   float sigma;         /* process-noise standard deviation, V_c = sigma^2 I (Eq. (1))    */
-  int32_t flags;       /* 0, or PUMP_GRAPH_HSMC                                          */
+  int32_t flags;       /* 0, or PUMP_GRAPH_HSMC | PUMP_GRAPH_SEPARATE_MASKS               */
 } pump_graph_params;
 
 /* Particle collision masks by Half-Space Monte Carlo (the paper's CP approximation, section
@@ -78,6 +78,11 @@ typedef struct {
  * OR over waypoints 1..W and half-spaces.  All of it in float, each operation rounded as
  * written, left to right (a waypoint on or inside a box ends its region). */
 #define PUMP_GRAPH_HSMC 1
+/* The graph's queries keep the edge masks in their own launch (pump_plan never fuses them into
+ * the Explore launch), so the build lays out no edge order for the fused form.  For callers that
+ * run many queries on the device at once (the request server), where a launch holding most of
+ * the device would stop the others from overlapping. */
+#define PUMP_GRAPH_SEPARATE_MASKS 2
 
 typedef struct {
   float alpha;            /* CP target (Eq. (3))                                          */

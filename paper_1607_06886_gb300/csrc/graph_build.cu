@@ -867,7 +867,7 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
     note_launch();
     // the adjacency and costs are final: the fused form's edge order is laid out beside the
     // per-edge fill and the deviation bounds (a side stream; joined before the build returns)
-    if (!g->hsmc && fused_masks_env()) {
+    if (!g->hsmc && g->fuse_masks && fused_masks_env()) {
       const int rco = row_order_begin(g, s, true);
       if (rco) return rco;
     }

@@ -377,6 +377,7 @@ int pump_graph_build(const float* states, int32_t n, int32_t start_idx, const in
   g->sigma = prm->sigma;
   g->has_geometry = true;
   g->hsmc = (prm->flags & PUMP_GRAPH_HSMC) != 0;
+  g->fuse_masks = (prm->flags & PUMP_GRAPH_SEPARATE_MASKS) == 0;
   g->states = (float*)graph_alloc(g, sizeof(float) * 6 * (size_t)n, s);
   g->boxes = (float*)graph_alloc(g, sizeof(float) * 6 * (size_t)std::max(n_boxes, 1), s);
   g->valid = (uint8_t*)graph_alloc(g, (size_t)n, s);

@@ -113,9 +113,6 @@ struct pump_server {
     std::memset(&d->result, 0, sizeof(d->result));
     d->result.chosen_plan = -1;
     if (!rc) {
-      // requests overlap on the device: the masks keep their own launch, so a request's Explore
-      // holds one cluster's SMs, not the whole device
-      g->fuse_masks = false;
       d->path.assign(kPathCap, 0);
       rc = pump_plan(g, &j->pp, d->path.data(), kPathCap, &d->result, s);
       d->path.resize(std::min<int32_t>(d->result.path_len, kPathCap));
@@ -197,6 +194,9 @@ int pump_server_submit(pump_server* s, const pump_request* r, int64_t* ticket) {
   j->n = r->n;
   j->start = r->start_idx;
   j->gp = r->graph;
+  // requests overlap on the device: their masks keep their own launch, and the build lays out no
+  // edge order for the fused form
+  j->gp.flags |= PUMP_GRAPH_SEPARATE_MASKS;
   j->pp = r->plan;
   j->bytes = estimate_bytes(r);
   j->t_submit = Clock::now();

@@ -19,7 +19,7 @@ from . import build as _build
 # status codes
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_INFEASIBLE = range(7)
 NO_EARLY_STOP, EXPLORE_ONLY, STEPWISE, EXPLORE_GRID = 1, 2, 4, 8
-GRAPH_HSMC = 1
+GRAPH_HSMC, GRAPH_SEPARATE_MASKS = 1, 2
 
 EXPORT = {
     "counts": 0, "node_valid": 1, "row_ptr": 2, "col": 3, "ecost": 4, "tau": 5, "h": 6, "phi": 7, "L": 8,
@@ -399,7 +399,8 @@ class Graph:
     @classmethod
     def build(cls, states, goal_idx, boxes, xi, radius: float, n_particles: int, n_waypoints: int,
               sigma: float, start_idx: int = 0, stream: Optional[int] = None, flags: int = 0) -> "Graph":
-        """pump_graph_build; flags = GRAPH_HSMC for Half-Space Monte Carlo masks."""
+        """pump_graph_build; flags: GRAPH_HSMC for Half-Space Monte Carlo masks, GRAPH_SEPARATE_MASKS
+        to keep the masks of every query in their own launch."""
         L = load()
         st = _np(states, np.float32)
         gi = _np(goal_idx, np.int32)

@@ -198,3 +198,23 @@ def test_repeated_fused_runs_are_identical():
             np.testing.assert_array_equal(a[k], a0[k])
         for k in ("rc", "chosen_plan", "mc_collisions", "n_candidates", "n_plans", "cost"):
             assert r[k] == r0[k], k
+
+
+def test_separate_masks_flag():
+    """PUMP_GRAPH_SEPARATE_MASKS (the request server's graphs): no edge order is laid out, every
+    query keeps the masks in their own launch, and the results equal a default graph's."""
+    wl = workload("indoor_4k", 9, 900)
+    Gs = pump.Graph.build(wl.states, wl.goal_idx, wl.boxes, wl.xi, wl.radius, wl.n_particles, wl.n_waypoints,
+                          wl.sigma, flags=pump.GRAPH_SEPARATE_MASKS)
+    with pytest.raises(pump.PumpError):
+        Gs.export("edge_order")
+    rs = Gs.plan(plan_params(wl))
+    assert rs["fused"] == 0
+    r1, m1, a1, _ = run(wl, True)
+    assert r1["fused"] == 1
+    np.testing.assert_array_equal(Gs.export("masks"), m1)
+    for k in ("rc", "chosen_plan", "mc_collisions", "n_candidates", "n_plans", "cost"):
+        assert rs[k] == r1[k], k
+    a = export_arena(Gs)
+    for k in a1:
+        np.testing.assert_array_equal(a[k], a1[k])
