@@ -215,7 +215,7 @@ def main():
                     help="queries of the HSMC leg (CP-hat vs Monte Carlo for box and half-space masks); 0 skips it")
     ap.add_argument("--serve-requests", type=int, default=150,
                     help="requests of the served leg (Poisson arrivals, continuous batching); 0 skips it")
-    ap.add_argument("--serve-rate", default="50,200",
+    ap.add_argument("--serve-rate", default="50,200,500",
                     help="arrival rates of the served leg (requests/s, comma-separated)")
     ap.add_argument("--learned-envs", type=int, default=10000,
                     help="training environments of the learned-proposal leg (plain PUMP solutions, then training "
