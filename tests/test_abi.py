@@ -64,3 +64,23 @@ def test_mlp_invalid_arguments_rejected_on_the_host():
     assert lib.pump_mlp_train(None, 16, 1, 1e-3, 0.1, 0, None, None) == pump.ERR_INVALID_ARG
     assert lib.pump_mlp_propose(None, None, 0, 1, 0, 0.1, None, None) == pump.ERR_INVALID_ARG
     lib.pump_mlp_destroy(None)
+
+
+def test_binding_constants_match_the_header():
+    """The binding's status codes, plan flags, graph flags and export kinds carry the header's
+    values (the binding restates them for ctypes)."""
+    text = open(os.path.join(ROOT, "include", "pump.h")).read()
+    defines = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define\s+(PUMP_\w+)\s+(0x[0-9a-fA-F]+|\d+)", text)}
+    enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(PUMP_\w+)\s*=\s*(\d+)", text)}
+    vals = {**defines, **enums}
+    pairs = {"OK": "PUMP_OK", "ERR_INVALID_ARG": "PUMP_ERR_INVALID_ARG", "ERR_OOM": "PUMP_ERR_OOM",
+             "ERR_CUDA": "PUMP_ERR_CUDA", "ERR_CAPACITY": "PUMP_ERR_CAPACITY", "ERR_TIMEOUT": "PUMP_ERR_TIMEOUT",
+             "ERR_INFEASIBLE": "PUMP_ERR_INFEASIBLE", "NO_EARLY_STOP": "PUMP_NO_EARLY_STOP",
+             "EXPLORE_ONLY": "PUMP_EXPLORE_ONLY", "STEPWISE": "PUMP_STEPWISE", "EXPLORE_GRID": "PUMP_EXPLORE_GRID",
+             "GRAPH_HSMC": "PUMP_GRAPH_HSMC", "GRAPH_SEPARATE_MASKS": "PUMP_GRAPH_SEPARATE_MASKS"}
+    for py, c in pairs.items():
+        assert c in vals, c
+        assert getattr(pump, py) == vals[c], (py, getattr(pump, py), vals[c])
+    for what, code in pump.EXPORT.items():
+        name = "PUMP_EXPORT_" + what.upper()
+        assert vals.get(name) == code, (name, vals.get(name), code)
