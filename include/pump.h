@@ -133,7 +133,7 @@ int pump_set_allocator(void* (*alloc)(size_t bytes, void* stream, void* ctx),
                        void (*free_)(void* ptr, void* stream, void* ctx), void* ctx);
 
 /* --------------------------------------------------------------------------
- * pump_graph_build: BuildGraph (Algorithm 3) plus the obstacle-dependent
+ * pump_build_graph: BuildGraph (Algorithm 3) plus the obstacle-dependent
  * edge geometry the exploration needs.
  *  states  : n x 6 float (p, v) row-major; x_init = states[start_idx].
  *  goal_idx: n_goal node ids forming X_goal (at least one; Algorithm 3 keeps
@@ -141,7 +141,12 @@ int pump_set_allocator(void* (*alloc)(size_t bytes, void* stream, void* ctx),
  *  boxes   : n_boxes closed AABBs (0 <= n_boxes <= 1024).
  *  xi      : N x (W+1) x 3 x 2 float standard normals (common random numbers
  *            of the particles: xi[i][0] draws the initial deviation from the
- *            stationary covariance, xi[i][k] drives step k).
+ *            stationary covariance, xi[i][k] drives step k).  The normals are
+ *            an input rather than a seed: they are the random numbers the
+ *            method draws (Section III-B), and taking them from the caller
+ *            lets any generator supply them and lets an independent
+ *            implementation consume exactly the same particles, so masks can
+ *            be compared bit for bit.
  * Computes: node validity (outside every box), directed edges v->u for
  * valid v != u with float(Cost(v,u)) < radius whose nominal connection,
  * sampled at 4W uniform times in (0, tau], stays outside the boxes; edges of
@@ -154,6 +159,10 @@ int pump_set_allocator(void* (*alloc)(size_t bytes, void* stream, void* ctx),
  * sigma < 0), OOM, CUDA.  On success *out owns device memory; release with
  * pump_graph_destroy.  Synchronises `stream`.
  */
+int pump_build_graph(const float* states, int32_t n, int32_t start_idx, const int32_t* goal_idx,
+                     int32_t n_goal, const pump_aabb* boxes, int32_t n_boxes, const float* xi,
+                     const pump_graph_params* params, void* stream, pump_graph** out);
+/* pump_graph_build: former name of pump_build_graph (same arguments, same behaviour). */
 int pump_graph_build(const float* states, int32_t n, int32_t start_idx, const int32_t* goal_idx,
                      int32_t n_goal, const pump_aabb* boxes, int32_t n_boxes, const float* xi,
                      const pump_graph_params* params, void* stream, pump_graph** out);
@@ -163,7 +172,7 @@ int pump_graph_build(const float* states, int32_t n, int32_t start_idx, const in
  * paper caches neighbours and edge controls offline, Section V-A).
  *  row_ptr : n+1 int32, col: E int32 targets (ascending within a row, no self
  *            loops), ecost: E float edge costs (>= 0), emask: E x (N/32) uint32.
- *  start_idx, goal_idx: as in pump_graph_build.
+ *  start_idx, goal_idx: as in pump_build_graph.
  * The graph has no geometry: pump_edge_masks and pump_certify return
  * INVALID_ARG on it.  Errors: INVALID_ARG, OOM, CUDA.  Synchronises.
  */
@@ -229,7 +238,7 @@ int pump_plan(pump_graph* g, const pump_plan_params* params, int32_t* path, int3
  * pump_plan_batch: pump_plan for n_queries independent queries, one per
  * built graph, with the Explore runs of all queries in one persistent launch
  * (no counterpart in the paper: a throughput form of Algorithm 2 for many
- * problems at once).  graphs[q] (distinct, built by pump_graph_build) is
+ * problems at once).  graphs[q] (distinct, built by pump_build_graph) is
  * planned with params[q]; results[q] receives what pump_plan would write for
  * it (the selected path is left in the graph: pump_export of the plan arrays
  * and goal plans), except that ms_masks / ms_explore / ms_select are the
@@ -261,14 +270,14 @@ int pump_plan_batch(pump_graph* const* graphs, int32_t n_queries, const pump_pla
  * and are admitted as soon as a slot is free and their estimated device memory
  * fits in `device_bytes` next to the admitted ones (a request larger than the
  * whole budget runs alone).  An admitted request builds its graph from its
- * arrays (pump_graph_build), plans (pump_plan) and frees the graph; requests in
+ * arrays (pump_build_graph), plans (pump_plan) and frees the graph; requests in
  * different slots run concurrently on the device.  Every result equals the
  * result of the same calls made alone.  Device memory comes from the installed
  * allocator (pump_set_allocator), called from the worker threads.
  */
 typedef struct pump_server pump_server;
 typedef struct {
-  const float* states;      /* n x 6, as pump_graph_build (host)            */
+  const float* states;      /* n x 6, as pump_build_graph (host)            */
   int32_t n;
   int32_t start_idx;
   const int32_t* goal_idx;  /* n_goal node ids (host)                       */
@@ -363,28 +372,34 @@ int pump_export(pump_graph* g, int32_t what, void* host_buf, size_t cap, size_t*
 
 /* --------------------------------------------------------------------------
  * pump_explore_noalloc: pump_explore for callers that cannot allocate device
- * memory (code inside a captured CUDA graph or another library's
- * stream-ordered region, runtimes whose device memory is fixed up front, or
- * processes whose allocator belongs to a host framework that must not be
- * re-entered).  No counterpart in the paper: it is the same Explore run as
- * pump_explore on an imported graph, with the same results, but it calls no
- * cudaMalloc, cudaFree or other allocating routine.
- *  Inputs (device pointers): row_ptr n+1, col E, ecost E, emask E x N/32
- *  (as for pump_graph_from_csr, which the caller must already satisfy: no
- *  checks are made on their contents), is_goal n bytes (nonzero = in X_goal).
- *  Outputs (device pointers, `capacity` entries each; plan_mask capacity x
- *  N/32 words): the plan arena as pump_export would return it, and goal_plans
- *  (P_goal in PlanSelection order, stats->n_goal entries).  stats receives
- *  the Explore counters.
+ * memory while they plan: a robot's real-time control loop that reserves its
+ * device memory at start-up (an allocation inside the loop can block for an
+ * unbounded time, or fail once memory is fragmented), an embedded runtime
+ * with a fixed memory budget, or a process whose device allocator belongs to
+ * a host framework that must not be re-entered from this library.  No
+ * counterpart in the paper: it is the same Explore run as pump_explore on an
+ * imported graph, with the same results, but it calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *  Inputs (device pointers on the current device, or managed memory):
+ *  row_ptr n+1, col E, ecost E, emask E x N/32 (as for pump_graph_from_csr,
+ *  which the caller must already satisfy: no checks are made on their
+ *  contents), is_goal n bytes (nonzero = in X_goal).
+ *  Outputs (same kind of pointers, `capacity` entries each; plan_mask
+ *  capacity x N/32 words): the plan arena as pump_export would return it,
+ *  and goal_plans (P_goal in PlanSelection order, stats->n_goal entries).
+ *  stats receives the Explore counters.  The arena used holds
+ *  C = min(capacity, params->max_plans) plans; more -> PUMP_ERR_CAPACITY.
  *  The kernels' scratch lives in a file-scope device array of 32 MiB that
  *  every GPU loading the library holds until the process exits.  A call
- *  needs 48 KiB + 4 n max(K_max, 1) + 36 capacity bytes (rounded up per
- *  buffer to 256 B); larger problems return PUMP_ERR_INVALID_ARG, as do host
- *  pointers.  The first call on a device looks up the array's device address
- *  (cudaGetSymbolAddress) with that device current; make that first call
- *  before any stream capture.  All calls on a device share the array: calls
- *  whose work overlaps on the GPU race and must be serialised by the caller.
- *  Synchronises `stream`.  Errors: INVALID_ARG, CUDA, CAPACITY, TIMEOUT.
+ *  needs 48 KiB + 4 n max(K_max, 1) + 36 C bytes (rounded up per buffer to
+ *  256 B); larger problems return PUMP_ERR_INVALID_ARG, as do host pointers
+ *  and pointers to another device's memory.  The first call on a device looks
+ *  up the array's device address (cudaGetSymbolAddress) with that device
+ *  current; make that first call before any stream capture.  All calls on a
+ *  device share the array and it keeps the last call's contents (each call
+ *  initialises what it reads): calls whose work overlaps on the GPU race and
+ *  must be serialised by the caller.  Synchronises `stream` before it returns,
+ *  on failure too.  Errors: INVALID_ARG, CUDA, CAPACITY, TIMEOUT.
  */
 int pump_explore_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col, const float* ecost,
                          const uint32_t* emask, int32_t n_particles, int32_t start_idx, const uint8_t* is_goal,

@@ -5,7 +5,7 @@ baseline use this module.  It builds pump_oracle.c with gcc (no fused
 multiply-add contraction) and exposes its functions on numpy arrays.  The
 Python here marshals arguments; three small pieces of the method are restated
 in it directly: the integer CP thresholds of Algorithm 2, plan backtracking by
-parent links, and the bisection of PlanSelection (Algorithm 5).
+parent links, and the ordering and bisection of PlanSelection (Algorithm 5).
 """
 from __future__ import annotations
 
@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
         return LIB_PATH
     tmp = LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-           "-Wall", "-o", tmp, SRC, "-lm"]
+           "-Wall", "-pthread", "-o", tmp, SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
@@ -60,6 +60,7 @@ def lib():
             L.orc_graph_export.argtypes = [P] * 11
             L.orc_graph_free.argtypes = [P]
             L.orc_edge_masks.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, C.c_int, P]
+            L.orc_edge_masks_mt.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, C.c_int, P, C.c_int]
             L.orc_graph_nvel.argtypes = [P, P]
             L.orc_halfspaces.argtypes = [P, P, P, C.c_int, C.c_int, P, P]
             L.orc_halfspaces.restype = C.c_int
@@ -68,6 +69,8 @@ def lib():
             L.orc_explore.argtypes = [C.c_int, P, P, P, P, C.c_int, C.c_int, P, C.c_int, C.c_int,
                                       C.c_float, C.c_float, C.c_int64, C.c_int, C.c_int]
             L.orc_explore.restype = P
+            L.orc_explore_mt.argtypes = L.orc_explore.argtypes + [C.c_int]
+            L.orc_explore_mt.restype = P
             L.orc_explore_summary.argtypes = [P, P]
             L.orc_explore_export.argtypes = [P] * 10
             L.orc_explore_free.argtypes = [P]
@@ -149,15 +152,20 @@ def pair_costs(states) -> np.ndarray:
     return out
 
 
-def edge_masks(graph: Dict, xi, boxes, n_particles: int) -> np.ndarray:
-    """Per-edge particle collision masks, (E, N/32) uint32."""
+def edge_masks(graph: Dict, xi, boxes, n_particles: int, n_threads: int = 1) -> np.ndarray:
+    """Per-edge particle collision masks, (E, N/32) uint32.  n_threads > 1 splits the edges over
+    host threads (timing only; the masks are the single-thread masks)."""
     E, W = graph["n_edges"], graph["W"]
     w = n_particles // 32
     out = np.zeros((E, w), np.uint32)
     x = _c(xi, np.float32)
     bx = _c(boxes, np.float32).reshape(-1, 6)
-    lib().orc_edge_masks(E, W, n_particles, _p(graph["phi"]), _p(graph["L"]), _p(graph["nom"]),
-                         _p(graph["linf"]), _p(x), _p(bx), bx.shape[0], _p(out))
+    args = (E, W, n_particles, _p(graph["phi"]), _p(graph["L"]), _p(graph["nom"]), _p(graph["linf"]), _p(x), _p(bx),
+            bx.shape[0], _p(out))
+    if n_threads > 1:
+        lib().orc_edge_masks_mt(*args, int(n_threads))
+    else:
+        lib().orc_edge_masks(*args)
     return out
 
 
@@ -202,16 +210,18 @@ def cp_thresholds(alpha: float, eta: float, n_particles: int):
 
 def explore(n: int, row_ptr, col, ecost, emask, start: int, goal_idx, K_min: int, K_max: int,
             lam: float, radius: float, max_plans: int = 1 << 24, flags: int = 0,
-            max_iterations: int = 1 << 20) -> Dict:
-    """Explore (Algorithm 4) on a CSR graph with edge costs and edge masks."""
+            max_iterations: int = 1 << 20, n_threads: int = 1) -> Dict:
+    """Explore (Algorithm 4) on a CSR graph with edge costs and edge masks.  n_threads > 1 splits
+    the expansion over group members and RemoveDominated over target nodes (timing only; the
+    result is the single-thread result)."""
     rp = _c(row_ptr, np.int32); cl = _c(col, np.int32); ec = _c(ecost, np.float32)
     em = _c(emask, np.uint32)
     w = em.shape[1] if em.ndim == 2 else 1
     is_goal = np.zeros(n, np.uint8)
     is_goal[np.asarray(goal_idx, dtype=np.int64)] = 1
-    R = lib().orc_explore(n, _p(rp), _p(cl), _p(ec), _p(em), w, int(start), _p(is_goal), int(K_min),
-                          int(K_max), C.c_float(lam), C.c_float(radius), int(max_plans), int(flags),
-                          int(max_iterations))
+    args = (n, _p(rp), _p(cl), _p(ec), _p(em), w, int(start), _p(is_goal), int(K_min), int(K_max), C.c_float(lam),
+            C.c_float(radius), int(max_plans), int(flags), int(max_iterations))
+    R = lib().orc_explore_mt(*args, int(n_threads)) if n_threads > 1 else lib().orc_explore(*args)
     if not R:
         raise MemoryError("oracle explore failed")
     try:
@@ -287,46 +297,64 @@ def mc_certify(states, path, edge_tau, W: int, sigma: float, boxes, n_mc: int, s
                                     bx.shape[0], int(n_mc), int(substeps), C.c_uint64(seed)))
 
 
-def plan_select(graph: Dict, ex: Dict, alpha: float, states, boxes, sigma: float, n_mc: int,
-                substeps: int, seed: int) -> Dict:
-    """PlanSelection (Algorithm 5) on an Explore result of the oracle.
+def selection_order(goal_plans, popc, cost):
+    """P_goal sorted for PlanSelection (Algorithm 5, "ascending CP-hat"): by popc ascending; ties
+    (the paper gives no rule) by cost descending, then plan id ascending, so that among plans of
+    equal CP-hat the cheaper one sits at the higher index, which the bisection prefers."""
+    return sorted((int(p) for p in goal_plans), key=lambda p: (int(popc[p]), -float(cost[p]), p))
 
-    P_goal is sorted by ascending CP-hat (popc), ties by descending cost then ascending id (our
-    reading: among equal CP-hat the cheaper plan sits at the higher index, which the bisection
-    prefers).  1-based bisection as printed: l = 1, u = |P|, m = ceil((l+u)/2); while l != u,
-    u = m - 1 if MC(P_m) > alpha else l = m.  MC(p) > alpha means n_collide / n_mc > alpha in
-    double.  Smoothing is not applied: it follows a cited method."""
-    st = _c(states, np.float32); bx = _c(boxes, np.float32).reshape(-1, 6)
-    G = ex["n_goal"]
-    if G == 0:
-        return {"status": ERR_INFEASIBLE, "chosen": -1, "collisions": -1, "sorted_goal": np.zeros(0, np.int32),
-                "n_probes": 0}
-    popc, cost = ex["popc"], ex["cost"]
-    order = sorted(ex["goal_plans"].tolist(), key=lambda p: (int(popc[p]), -float(cost[p]), p))
-    cache = {}
 
-    def mc(p):
-        if p not in cache:
-            path = backtrack(ex["parent"], ex["head"], p)
-            taus = [graph["tau"][edge_of(graph, int(path[k]), int(path[k + 1]))] for k in range(len(path) - 1)]
-            cache[p] = mc_certify(st, path, np.asarray(taus, np.float32), graph["W"], sigma, bx, n_mc,
-                                  substeps, seed)
-        return cache[p]
-
-    l, u = 1, G
+def bisect_select(order, mc_count, n_mc: int, alpha: float):
+    """The bisection of PlanSelection (Algorithm 5) over `order` with 1-based indices as printed:
+    l = 1, u = |P|, m = ceil((l + u) / 2); while l != u: u = m - 1 if MC(P_m) > alpha else l = m,
+    then m = ceil((l + u) / 2); finally failure iff MC(P_m) > alpha.  MC(p) > alpha is
+    mc_count(p) / n_mc > alpha in double, alpha taken as float32 (its type at the boundary).
+    Returns (status, chosen plan or -1 when P_goal is empty, its count, probed indices)."""
+    if len(order) == 0:
+        return ERR_INFEASIBLE, -1, -1, []
+    a = float(np.float32(alpha))
+    over = lambda c: c / n_mc > a
+    l, u = 1, len(order)
     m = (l + u + 1) // 2
-    probes = 0
+    probed = []
     while l != u:
-        c = mc(order[m - 1]); probes += 1
-        if c / n_mc > float(np.float32(alpha)):
+        probed.append(m)
+        if over(mc_count(order[m - 1])):
             u = m - 1
         else:
             l = m
         m = (l + u + 1) // 2
-    c = mc(order[m - 1])
-    status = ERR_INFEASIBLE if c / n_mc > float(np.float32(alpha)) else OK
-    return {"status": status, "chosen": order[m - 1], "collisions": c, "sorted_goal": np.asarray(order, np.int32),
-            "n_probes": probes}
+    c = mc_count(order[m - 1])
+    return (ERR_INFEASIBLE if over(c) else OK), order[m - 1], c, probed
+
+
+def plan_select(graph: Dict, ex: Dict, alpha: float, states, boxes, sigma: float, n_mc: int,
+                substeps: int, seed: int, mc_count=None) -> Dict:
+    """PlanSelection (Algorithm 5) on an Explore result of the oracle: selection_order, then
+    bisect_select with MC(p) from mc_certify on p's backtracked path (or `mc_count(p)` when given,
+    for tests that script the Monte Carlo outcomes).  Smoothing is not applied: it follows a cited
+    method."""
+    st = _c(states, np.float32); bx = _c(boxes, np.float32).reshape(-1, 6)
+    if ex["n_goal"] == 0:
+        return {"status": ERR_INFEASIBLE, "chosen": -1, "collisions": -1, "sorted_goal": np.zeros(0, np.int32),
+                "n_probes": 0}
+    order = selection_order(ex["goal_plans"].tolist(), ex["popc"], ex["cost"])
+    cache = {}
+
+    def mc(p):
+        if p not in cache:
+            if mc_count is not None:
+                cache[p] = int(mc_count(p))
+            else:
+                path = backtrack(ex["parent"], ex["head"], p)
+                taus = [graph["tau"][edge_of(graph, int(path[k]), int(path[k + 1]))] for k in range(len(path) - 1)]
+                cache[p] = mc_certify(st, path, np.asarray(taus, np.float32), graph["W"], sigma, bx, n_mc,
+                                      substeps, seed)
+        return cache[p]
+
+    status, chosen, c, probed = bisect_select(order, mc, n_mc, alpha)
+    return {"status": status, "chosen": chosen, "collisions": c, "sorted_goal": np.asarray(order, np.int32),
+            "n_probes": len(probed)}
 
 
 def plan(wl, exhaustive: bool = False, flags: int = 0, max_plans: int = 1 << 24) -> Dict:

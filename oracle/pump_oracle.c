@@ -4,7 +4,9 @@
  * on GPUs").
  *
  * TEST INFRASTRUCTURE.  This file is a plain, slow, single-threaded
- * restatement of what the planner computes.  Only the test-suite, the smoke
+ * restatement of what the planner computes (O4 and O5 also take a thread
+ * count, used only to time the oracle on all host cores: the threads split
+ * independent loops and the results are the single-thread results).  Only the test-suite, the smoke
  * check and the benchmark's CPU-baseline leg load it.  It shares no code with
  * the CUDA library: no headers, helpers or tables.  It must be compiled with
  * -ffp-contract=off so that the compiler does not fuse the float products and
@@ -27,6 +29,8 @@
  * tie rules, thresholds) are stated beside the code that takes them.
  */
 #include <math.h>
+#include <pthread.h>
+#include <stdatomic.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -449,10 +453,10 @@ void orc_graph_export(const orc_graph* g, uint8_t* valid, int32_t* row_ptr, int3
 /* xi is laid out [N][W+1][3][2].  Masks are w = N/32 words per edge, particle */
 /* i in word i/32, bit i%32.                                                     */
 /* ========================================================================== */
-void orc_edge_masks(int n_edges, int W, int N, const float* phi, const float* L, const float* nom,
-                    const float* linf, const float* xi, const float* boxes, int n_boxes, uint32_t* mask) {
+static void edge_masks_range(int e0, int e1, int W, int N, const float* phi, const float* L, const float* nom,
+                             const float* linf, const float* xi, const float* boxes, int n_boxes, uint32_t* mask) {
   int w = N / 32;
-  for (int e = 0; e < n_edges; ++e) {
+  for (int e = e0; e < e1; ++e) {
     for (int q = 0; q < w; ++q) mask[(size_t)e * w + q] = 0u;
     for (int i = 0; i < N; ++i) {
       int collisions = 0;
@@ -474,6 +478,49 @@ void orc_edge_masks(int n_edges, int W, int N, const float* phi, const float* L,
       if (collisions > 0) mask[(size_t)e * w + i / 32] |= 1u << (i % 32);
     }
   }
+}
+
+void orc_edge_masks(int n_edges, int W, int N, const float* phi, const float* L, const float* nom,
+                    const float* linf, const float* xi, const float* boxes, int n_boxes, uint32_t* mask) {
+  edge_masks_range(0, n_edges, W, N, phi, L, nom, linf, xi, boxes, n_boxes, mask);
+}
+
+/* All host cores: edges are independent, so threads take blocks of 64 edges from a shared     */
+/* counter; every mask word is the single-thread word.                                          */
+typedef struct {
+  atomic_int* next;
+  int n_edges, W, N, n_boxes;
+  const float *phi, *L, *nom, *linf, *xi, *boxes;
+  uint32_t* mask;
+} masks_job;
+
+static void* masks_worker(void* arg) {
+  masks_job* j = (masks_job*)arg;
+  for (;;) {
+    int e0 = atomic_fetch_add(j->next, 64);
+    if (e0 >= j->n_edges) break;
+    int e1 = e0 + 64 < j->n_edges ? e0 + 64 : j->n_edges;
+    edge_masks_range(e0, e1, j->W, j->N, j->phi, j->L, j->nom, j->linf, j->xi, j->boxes, j->n_boxes, j->mask);
+  }
+  return NULL;
+}
+
+void orc_edge_masks_mt(int n_edges, int W, int N, const float* phi, const float* L, const float* nom,
+                       const float* linf, const float* xi, const float* boxes, int n_boxes, uint32_t* mask,
+                       int n_threads) {
+  if (n_threads < 2) {
+    orc_edge_masks(n_edges, W, N, phi, L, nom, linf, xi, boxes, n_boxes, mask);
+    return;
+  }
+  atomic_int next = 0;
+  masks_job j = {&next, n_edges, W, N, n_boxes, phi, L, nom, linf, xi, boxes, mask};
+  pthread_t* t = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)n_threads);
+  int started = 0;
+  for (int k = 0; k < n_threads; ++k)
+    if (pthread_create(&t[started], NULL, masks_worker, &j) == 0) ++started;
+  if (started == 0) masks_worker(&j);
+  for (int k = 0; k < started; ++k) pthread_join(t[k], NULL);
+  free(t);
 }
 
 /* ========================================================================== */
@@ -644,17 +691,185 @@ static float group_threshold(int i, float lambda, float r) {
   return (float)((double)i * ((double)lambda * (double)r));
 }
 
-orc_explore_result* orc_explore(int n, const int32_t* row_ptr, const int32_t* col, const float* ecost,
-                                const uint32_t* emask, int n_words, int start, const uint8_t* is_goal,
-                                int K_min, int K_max, float lambda, float r, int64_t max_plans,
-                                int flags, int max_iterations) {
+/* Candidate buffer of one expansion: records in candidate order. */
+typedef struct {
+  int64_t n, cap;
+  int w;
+  int32_t* head;
+  int32_t* parent;
+  float* cost;
+  uint32_t* mask;
+  int32_t* popc;
+  uint8_t* dom;
+  int64_t evaluated; /* pairs evaluated (partial plans), kept or not */
+} cand_buf;
+
+static int cand_reserve(cand_buf* c, int64_t need) {
+  if (need <= c->cap) return 0;
+  int64_t cap = c->cap ? c->cap : 1024;
+  while (cap < need) cap *= 2;
+  c->head = (int32_t*)realloc(c->head, sizeof(int32_t) * cap);
+  c->parent = (int32_t*)realloc(c->parent, sizeof(int32_t) * cap);
+  c->cost = (float*)realloc(c->cost, sizeof(float) * cap);
+  c->mask = (uint32_t*)realloc(c->mask, sizeof(uint32_t) * cap * c->w);
+  c->popc = (int32_t*)realloc(c->popc, sizeof(int32_t) * cap);
+  c->dom = (uint8_t*)realloc(c->dom, cap);
+  if (!c->head || !c->parent || !c->cost || !c->mask || !c->popc || !c->dom) return -1;
+  c->cap = cap;
+  return 0;
+}
+
+static void cand_free(cand_buf* c) {
+  free(c->head); free(c->parent); free(c->cost); free(c->mask); free(c->popc); free(c->dom);
+}
+
+/* Expansion of group members group[g0 .. g1): for p in the group (in order), for x in          */
+/* N(p.head) (in CSR order): q = (x, cost + Cost(head, x), mask OR edge mask); q is kept iff its */
+/* CP-hat passes the alpha_max cutoff (popc < K_max).                                          */
+typedef struct {
+  const orc_explore_result* R;
+  const int32_t* group;
+  int g0, g1;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const float* ecost;
+  const uint32_t* emask;
+  int K_max;
+  cand_buf* out;
+} expand_job;
+
+static void* expand_members(void* arg) {
+  expand_job* j = (expand_job*)arg;
+  const orc_explore_result* R = j->R;
+  cand_buf* c = j->out;
+  int w = c->w;
+  for (int gi = j->g0; gi < j->g1; ++gi) {
+    int p = j->group[gi];
+    int v = R->head[p];
+    for (int e = j->row_ptr[v]; e < j->row_ptr[v + 1]; ++e) {
+      c->evaluated++;
+      uint32_t m[64];
+      int pc = 0;
+      for (int q = 0; q < w; ++q) {
+        m[q] = R->mask[(size_t)p * w + q] | j->emask[(size_t)e * w + q];
+        pc += popcount32(m[q]);
+      }
+      if (!(pc < j->K_max)) continue; /* CP cutoff */
+      if (cand_reserve(c, c->n + 1)) return (void*)1;
+      int64_t k = c->n++;
+      c->head[k] = j->col[e];
+      c->parent[k] = p;
+      float pc_cost = R->cost[p];
+      float ec = j->ecost[e];
+      c->cost[k] = pc_cost + ec;
+      for (int q = 0; q < w; ++q) c->mask[(size_t)k * w + q] = m[q];
+      c->popc[k] = pc;
+      c->dom[k] = 0;
+    }
+  }
+  return NULL;
+}
+
+/* RemoveDominated at nodes touched[t0 .. t1).  S_x = P(x) plus the new candidates at x;        */
+/* dominance is decided against the whole of S_x before anything is removed.  Removes the        */
+/* dominated open plans of P(x) (from P(x), P_open and the arena's live set) and flags the        */
+/* dominated candidates.  Each node's plans and candidates belong to that node alone.            */
+typedef struct {
+  orc_explore_result* R;
+  uint8_t* open_;
+  ivec* P;
+  ivec* NEWAT;
+  const int32_t* touched;
+  int t0, t1;
+  cand_buf* c;
+  int64_t removed_open; /* open plans removed */
+} dominate_job;
+
+static void* dominate_nodes(void* arg) {
+  dominate_job* j = (dominate_job*)arg;
+  orc_explore_result* R = j->R;
+  cand_buf* c = j->c;
+  for (int ti = j->t0; ti < j->t1; ++ti) {
+    int x = j->touched[ti];
+    ivec* old = &j->P[x];
+    ivec* nw = &j->NEWAT[x];
+    uint8_t* old_dom = (uint8_t*)calloc((size_t)(old->n ? old->n : 1), 1);
+    /* existing open plans */
+    for (int a = 0; a < old->n; ++a) {
+      int p = old->v[a];
+      if (!j->open_[p]) continue;
+      int dom = 0;
+      for (int b2 = 0; b2 < old->n && !dom; ++b2) {
+        int d = old->v[b2];
+        if (R->cost[d] < R->cost[p] && R->popc[d] <= R->popc[p]) dom = 1;
+      }
+      for (int b2 = 0; b2 < nw->n && !dom; ++b2) {
+        int d = nw->v[b2];
+        if (c->cost[d] < R->cost[p] && c->popc[d] <= R->popc[p]) dom = 1;
+      }
+      old_dom[a] = (uint8_t)dom;
+    }
+    /* new candidates (all open) */
+    for (int a = 0; a < nw->n; ++a) {
+      int q = nw->v[a];
+      int dom = 0;
+      for (int b2 = 0; b2 < old->n && !dom; ++b2) {
+        int d = old->v[b2];
+        if (R->cost[d] < c->cost[q] && R->popc[d] <= c->popc[q]) dom = 1;
+      }
+      for (int b2 = 0; b2 < nw->n && !dom; ++b2) {
+        int d = nw->v[b2];
+        if (c->cost[d] < c->cost[q] && c->popc[d] <= c->popc[q]) dom = 1;
+      }
+      c->dom[q] = (uint8_t)dom;
+    }
+    /* apply removals of existing plans */
+    int keep = 0;
+    for (int a = 0; a < old->n; ++a) {
+      int p = old->v[a];
+      if (old_dom[a]) { R->removed[p] = 1; j->open_[p] = 0; j->removed_open++; }
+      else old->v[keep++] = p;
+    }
+    old->n = keep;
+    free(old_dom);
+  }
+  return NULL;
+}
+
+/* Runs fn over jobs[0 .. n): on the calling thread when n == 1, else one thread per job.       */
+static int run_jobs(void* (*fn)(void*), void* jobs, size_t job_size, int n) {
+  int rc = 0;
+  if (n == 1) return fn(jobs) != NULL;
+  pthread_t* t = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)n);
+  int* live = (int*)calloc((size_t)n, sizeof(int));
+  for (int k = 0; k < n; ++k) {
+    void* jk = (char*)jobs + job_size * (size_t)k;
+    if (pthread_create(&t[k], NULL, fn, jk) == 0) live[k] = 1;
+    else if (fn(jk) != NULL) rc = 1;
+  }
+  for (int k = 0; k < n; ++k) {
+    void* r = NULL;
+    if (live[k]) {
+      pthread_join(t[k], &r);
+      if (r != NULL) rc = 1;
+    }
+  }
+  free(t); free(live);
+  return rc;
+}
+
+static orc_explore_result* explore_impl(int n, const int32_t* row_ptr, const int32_t* col, const float* ecost,
+                                        const uint32_t* emask, int n_words, int start, const uint8_t* is_goal,
+                                        int K_min, int K_max, float lambda, float r, int64_t max_plans,
+                                        int flags, int max_iterations, int n_threads) {
   orc_explore_result* R = (orc_explore_result*)calloc(1, sizeof(orc_explore_result));
   if (!R) return NULL;
   R->n_words = n_words;
-  if (n <= 0 || start < 0 || start >= n || n_words <= 0 || max_plans < 1) {
+  if (n <= 0 || start < 0 || start >= n || n_words <= 0 || n_words > 64 || max_plans < 1) {
     R->status = ORC_ERR_INVALID_ARG;
     return R;
   }
+  if (n_threads < 1) n_threads = 1;
   int w = n_words;
   int64_t cap = 1024;
 #define GROW_PLANS(NEED)                                                                       \
@@ -683,14 +898,12 @@ orc_explore_result* orc_explore(int n, const int32_t* row_ptr, const int32_t* co
   ivec* P = (ivec*)calloc((size_t)n, sizeof(ivec));      /* P(x): live plans with head x */
   ivec* NEWAT = (ivec*)calloc((size_t)n, sizeof(ivec));  /* new candidates per node, one iteration */
   ivec group = {0}, touched = {0}, next_group = {0};
-  /* candidate buffer */
-  int64_t ccap = 1024, nc = 0;
-  int32_t* c_head = (int32_t*)malloc(sizeof(int32_t) * ccap);
-  int32_t* c_parent = (int32_t*)malloc(sizeof(int32_t) * ccap);
-  float* c_cost = (float*)malloc(sizeof(float) * ccap);
-  uint32_t* c_mask = (uint32_t*)malloc(sizeof(uint32_t) * ccap * w);
-  int32_t* c_popc = (int32_t*)malloc(sizeof(int32_t) * ccap);
-  uint8_t* c_dom = (uint8_t*)malloc(ccap);
+  cand_buf cb = {0};                                     /* candidates of one iteration */
+  cb.w = w;
+  cand_buf* part = (cand_buf*)calloc((size_t)n_threads, sizeof(cand_buf)); /* per-thread parts */
+  expand_job* ej = (expand_job*)calloc((size_t)n_threads, sizeof(expand_job));
+  dominate_job* dj = (dominate_job*)calloc((size_t)n_threads, sizeof(dominate_job));
+  for (int k = 0; k < n_threads; ++k) part[k].w = w;
 
   /* root plan (x_init, {}, 0, 0) */
   R->head[0] = start; R->parent[0] = -1; R->cost[0] = 0.0f;
@@ -713,101 +926,64 @@ orc_explore_result* orc_explore(int n, const int32_t* row_ptr, const int32_t* co
       if (stop) break;
     }
     if (i >= max_iterations) { R->status = ORC_ERR_TIMEOUT; break; }
-    /* expansion: candidates q = (x, path + head, cost + Cost(head, x), CP-hat) */
-    nc = 0;
-    for (int gi = 0; gi < group.n; ++gi) {
-      int p = group.v[gi];
-      int v = R->head[p];
-      for (int e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
-        R->n_candidates++;
-        uint32_t m[64];
-        int pc = 0;
-        for (int q = 0; q < w; ++q) {
-          m[q] = R->mask[(size_t)p * w + q] | emask[(size_t)e * w + q];
-          pc += popcount32(m[q]);
-        }
-        if (!(pc < K_max)) continue;  /* CP cutoff */
-        if (nc == ccap) {
-          ccap *= 2;
-          c_head = (int32_t*)realloc(c_head, sizeof(int32_t) * ccap);
-          c_parent = (int32_t*)realloc(c_parent, sizeof(int32_t) * ccap);
-          c_cost = (float*)realloc(c_cost, sizeof(float) * ccap);
-          c_mask = (uint32_t*)realloc(c_mask, sizeof(uint32_t) * ccap * w);
-          c_popc = (int32_t*)realloc(c_popc, sizeof(int32_t) * ccap);
-          c_dom = (uint8_t*)realloc(c_dom, ccap);
-        }
-        c_head[nc] = col[e];
-        c_parent[nc] = p;
-        float pc_cost = R->cost[p];
-        float ec = ecost[e];
-        c_cost[nc] = pc_cost + ec;
-        for (int q = 0; q < w; ++q) c_mask[(size_t)nc * w + q] = m[q];
-        c_popc[nc] = pc;
-        c_dom[nc] = 0;
-        if (NEWAT[col[e]].n == 0) ivec_push(&touched, col[e]);
-        ivec_push(&NEWAT[col[e]], (int32_t)nc);
-        ++nc;
+    /* expansion: candidates q = (x, path + head, cost + Cost(head, x), CP-hat), group members */
+    /* in order, each member's out-edges in CSR order (members split into contiguous chunks   */
+    /* across threads, the chunks' candidates concatenated in order)                          */
+    int T = n_threads < group.n ? n_threads : (group.n > 0 ? group.n : 1);
+    cb.n = 0;
+    cb.evaluated = 0;
+    for (int k = 0; k < T; ++k) {
+      cand_buf* out = T == 1 ? &cb : &part[k];
+      out->n = 0;
+      out->evaluated = 0;
+      expand_job J = {R, group.v, (int)((int64_t)group.n * k / T), (int)((int64_t)group.n * (k + 1) / T),
+                      row_ptr, col, ecost, emask, K_max, out};
+      ej[k] = J;
+    }
+    if (run_jobs(expand_members, ej, sizeof(expand_job), T)) { R->status = ORC_ERR_OOM; break; }
+    if (T > 1) {
+      for (int k = 0; k < T; ++k) {
+        if (cand_reserve(&cb, cb.n + part[k].n)) { R->status = ORC_ERR_OOM; break; }
+        int64_t m = part[k].n;
+        memcpy(cb.head + cb.n, part[k].head, sizeof(int32_t) * m);
+        memcpy(cb.parent + cb.n, part[k].parent, sizeof(int32_t) * m);
+        memcpy(cb.cost + cb.n, part[k].cost, sizeof(float) * m);
+        memcpy(cb.mask + cb.n * w, part[k].mask, sizeof(uint32_t) * m * w);
+        memcpy(cb.popc + cb.n, part[k].popc, sizeof(int32_t) * m);
+        memcpy(cb.dom + cb.n, part[k].dom, m);
+        cb.n += m;
+        cb.evaluated += part[k].evaluated;
       }
+      if (R->status != ORC_OK) break;
+    }
+    R->n_candidates += cb.evaluated;
+    int64_t nc = cb.n;
+    for (int64_t q = 0; q < nc; ++q) {
+      int x = cb.head[q];
+      if (NEWAT[x].n == 0) ivec_push(&touched, x);
+      ivec_push(&NEWAT[x], (int32_t)q);
     }
     R->n_kept += nc;
-    /* RemoveDominated on every node that received candidates.  S_x = P(x) plus */
-    /* the new candidates at x; dominance is decided against the whole of S_x   */
-    /* before anything is removed.                                               */
-    for (int ti = 0; ti < touched.n; ++ti) {
-      int x = touched.v[ti];
-      ivec* old = &P[x];
-      ivec* nw = &NEWAT[x];
-      uint8_t* old_dom = (uint8_t*)calloc((size_t)(old->n ? old->n : 1), 1);
-      /* existing open plans */
-      for (int a = 0; a < old->n; ++a) {
-        int p = old->v[a];
-        if (!open_[p]) continue;
-        int dom = 0;
-        for (int b2 = 0; b2 < old->n && !dom; ++b2) {
-          int d = old->v[b2];
-          if (R->cost[d] < R->cost[p] && R->popc[d] <= R->popc[p]) dom = 1;
-        }
-        for (int b2 = 0; b2 < nw->n && !dom; ++b2) {
-          int d = nw->v[b2];
-          if (c_cost[d] < R->cost[p] && c_popc[d] <= R->popc[p]) dom = 1;
-        }
-        old_dom[a] = (uint8_t)dom;
-      }
-      /* new candidates (all open) */
-      for (int a = 0; a < nw->n; ++a) {
-        int q = nw->v[a];
-        int dom = 0;
-        for (int b2 = 0; b2 < old->n && !dom; ++b2) {
-          int d = old->v[b2];
-          if (R->cost[d] < c_cost[q] && R->popc[d] <= c_popc[q]) dom = 1;
-        }
-        for (int b2 = 0; b2 < nw->n && !dom; ++b2) {
-          int d = nw->v[b2];
-          if (c_cost[d] < c_cost[q] && c_popc[d] <= c_popc[q]) dom = 1;
-        }
-        c_dom[q] = (uint8_t)dom;
-      }
-      /* apply removals of existing plans */
-      int keep = 0;
-      for (int a = 0; a < old->n; ++a) {
-        int p = old->v[a];
-        if (old_dom[a]) { R->removed[p] = 1; open_[p] = 0; --n_open; }
-        else old->v[keep++] = p;
-      }
-      old->n = keep;
-      free(old_dom);
+    /* RemoveDominated on every node that received candidates (nodes split across threads) */
+    int TD = n_threads < touched.n ? n_threads : (touched.n > 0 ? touched.n : 1);
+    for (int k = 0; k < TD; ++k) {
+      dominate_job J = {R, open_, P, NEWAT, touched.v, (int)((int64_t)touched.n * k / TD),
+                        (int)((int64_t)touched.n * (k + 1) / TD), &cb, 0};
+      dj[k] = J;
     }
+    run_jobs(dominate_nodes, dj, sizeof(dominate_job), TD);
+    for (int k = 0; k < TD; ++k) n_open -= dj[k].removed_open;
     /* survivors get ids in candidate order */
     for (int64_t q = 0; q < nc; ++q) {
-      if (c_dom[q]) continue;
+      if (cb.dom[q]) continue;
       if ((int64_t)R->n_plans + 1 > max_plans) { R->status = ORC_ERR_CAPACITY; break; }
       int64_t id = R->n_plans;
       GROW_PLANS(id + 1);
-      R->head[id] = c_head[q]; R->parent[id] = c_parent[q]; R->cost[id] = c_cost[q];
-      for (int k = 0; k < w; ++k) R->mask[(size_t)id * w + k] = c_mask[(size_t)q * w + k];
-      R->popc[id] = c_popc[q]; R->t_created[id] = i; R->e_expanded[id] = -1; R->removed[id] = 0;
+      R->head[id] = cb.head[q]; R->parent[id] = cb.parent[q]; R->cost[id] = cb.cost[q];
+      for (int k = 0; k < w; ++k) R->mask[(size_t)id * w + k] = cb.mask[(size_t)q * w + k];
+      R->popc[id] = cb.popc[q]; R->t_created[id] = i; R->e_expanded[id] = -1; R->removed[id] = 0;
       open_[id] = 1; ++n_open;
-      ivec_push(&P[c_head[q]], (int32_t)id);
+      ivec_push(&P[cb.head[q]], (int32_t)id);
       R->n_plans++;
     }
     for (int ti = 0; ti < touched.n; ++ti) NEWAT[touched.v[ti]].n = 0;
@@ -839,9 +1015,29 @@ orc_explore_result* orc_explore(int n, const int32_t* row_ptr, const int32_t* co
     if (is_goal[R->head[p]] && !R->removed[p]) R->goal_plans[R->n_goal++] = p;
   for (int v = 0; v < n; ++v) { free(P[v].v); free(NEWAT[v].v); }
   free(P); free(NEWAT); free(group.v); free(next_group.v); free(touched.v); free(open_);
-  free(c_head); free(c_parent); free(c_cost); free(c_mask); free(c_popc); free(c_dom);
+  cand_free(&cb);
+  for (int k = 0; k < n_threads; ++k) cand_free(&part[k]);
+  free(part); free(ej); free(dj);
 #undef GROW_PLANS
   return R;
+}
+
+orc_explore_result* orc_explore(int n, const int32_t* row_ptr, const int32_t* col, const float* ecost,
+                                const uint32_t* emask, int n_words, int start, const uint8_t* is_goal,
+                                int K_min, int K_max, float lambda, float r, int64_t max_plans,
+                                int flags, int max_iterations) {
+  return explore_impl(n, row_ptr, col, ecost, emask, n_words, start, is_goal, K_min, K_max, lambda, r, max_plans,
+                      flags, max_iterations, 1);
+}
+
+/* Explore on all host cores (timing): the same run with the expansion split over group members */
+/* and RemoveDominated over target nodes; every result equals orc_explore's.                    */
+orc_explore_result* orc_explore_mt(int n, const int32_t* row_ptr, const int32_t* col, const float* ecost,
+                                   const uint32_t* emask, int n_words, int start, const uint8_t* is_goal,
+                                   int K_min, int K_max, float lambda, float r, int64_t max_plans,
+                                   int flags, int max_iterations, int n_threads) {
+  return explore_impl(n, row_ptr, col, ecost, emask, n_words, start, is_goal, K_min, K_max, lambda, r, max_plans,
+                      flags, max_iterations, n_threads);
 }
 
 void orc_explore_summary(const orc_explore_result* R, int64_t* out /* status, n_plans, n_cand, n_kept, n_iter, n_groups, n_goal */) {

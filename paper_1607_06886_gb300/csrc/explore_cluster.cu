@@ -104,6 +104,25 @@ __device__ __forceinline__ int64_t ld64(const int64_t* p) { return __ldcg(reinte
 __device__ __forceinline__ float ldf(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ uint32_t ldu(const uint32_t* p) { return __ldcg(p); }
 
+// Launch shape a cluster kernel was sized for on the host: CTAs per cluster (the on-chip
+// dominance table is partitioned over exactly that many CTAs) and dynamic shared memory bytes.
+struct LaunchShape {
+  int32_t nr;
+  uint32_t smem;
+};
+
+// True iff the kernel runs with the launch shape the host sized it for.  A launch of the same
+// kernel with another cluster size or less shared memory would index the partitioned table and
+// the staging arrays out of range; the kernels check this on entry and refuse such a launch
+// (PUMP_ERR_CUDA in the control block) before touching shared memory.
+__device__ __forceinline__ bool launch_shape_ok(const LaunchShape& ls) {
+  uint32_t nct, dsz;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(nct));
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
+  return nct == (uint32_t)ls.nr && dsz >= ls.smem && blockDim.x == (unsigned)kCT && blockDim.y == 1 &&
+         blockDim.z == 1 && gridDim.x % (unsigned)ls.nr == 0;
+}
+
 // Counts one CTA publishes after phase B (every CTA reads them in phase C).
 struct Pub {
   int32_t surv;      // survivors of the CTA's chunk
@@ -1105,8 +1124,12 @@ __device__ void explore_one(const ExploreArgs& A, int32_t start, CSmem* sm, uint
 }
 
 template <bool kDsm>
-__global__ void __launch_bounds__(kCT, 1) k_explore_cluster(ExploreArgs A, int32_t start) {
+__global__ void __launch_bounds__(kCT, 1) k_explore_cluster(ExploreArgs A, int32_t start, LaunchShape ls) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (!launch_shape_ok(ls)) {  // every CTA sees the same shape: all leave here
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->status = PUMP_ERR_CUDA;
+    return;
+  }
   CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
   uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
   cg::cluster_group cl = cg::this_cluster();
@@ -1118,8 +1141,13 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_cluster(ExploreArgs A, int32
 template <bool kDsm>
 __global__ void __launch_bounds__(kCT, 1) k_explore_cluster_batch(const ExploreArgs* __restrict__ As,
                                                                   const int32_t* __restrict__ starts, int32_t nq,
-                                                                  int32_t* next) {
+                                                                  int32_t* next, LaunchShape ls) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (!launch_shape_ok(ls)) {
+    if (blockIdx.x == 0)
+      for (int q = threadIdx.x; q < nq; q += kCT) As[q].ctl->status = PUMP_ERR_CUDA;
+    return;
+  }
   CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
   uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
   cg::cluster_group cl = cg::this_cluster();
@@ -1205,8 +1233,15 @@ __device__ __forceinline__ void mask_positions(const FuseArgs& F, unsigned char*
 // so the first groups do not wait for the workers' first edges; the workers take the rest.
 // Cluster 0 also writes the run's initial state first and P_goal's order last.
 template <bool kDsm>
-__global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t start, FuseArgs F) {
+__global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t start, FuseArgs F, LaunchShape ls) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (!launch_shape_ok(ls)) {  // refused before any shared memory or count is touched
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      explore_init_thread(A, start);
+      A.ctl->status = PUMP_ERR_CUDA;
+    }
+    return;
+  }
   cg::cluster_group cl = cg::this_cluster();
   const int nr = (int)cl.num_blocks();
   const long long warp = threadIdx.x >> 5;
@@ -1575,10 +1610,11 @@ int run_explore_cluster(pump_graph* g, const ExploreArgs& A, int nr, bool dsm, c
   cluster_config(&cfg, attr, nr, 1, smem, s);
   const int32_t start = g->start;
   cudaError_t e;
+  const LaunchShape ls{nr, (uint32_t)smem};
   if (dsm)
-    e = cudaLaunchKernelEx(&cfg, k_explore_cluster<true>, A, start);
+    e = cudaLaunchKernelEx(&cfg, k_explore_cluster<true>, A, start, ls);
   else
-    e = cudaLaunchKernelEx(&cfg, k_explore_cluster<false>, A, start);
+    e = cudaLaunchKernelEx(&cfg, k_explore_cluster<false>, A, start, ls);
   note_launch();
   return e == cudaSuccess ? PUMP_OK : PUMP_ERR_CUDA;
 }
@@ -1599,10 +1635,11 @@ int run_explore_cluster_batch(const ExploreArgs* As_dev, const int32_t* starts_d
   cudaLaunchAttribute attr[1];
   cluster_config(&cfg, attr, nr, n_clusters, smem, s);
   cudaError_t e;
+  const LaunchShape ls{nr, (uint32_t)smem};
   if (dsm)
-    e = cudaLaunchKernelEx(&cfg, k_explore_cluster_batch<true>, As_dev, starts_dev, nq, next_dev);
+    e = cudaLaunchKernelEx(&cfg, k_explore_cluster_batch<true>, As_dev, starts_dev, nq, next_dev, ls);
   else
-    e = cudaLaunchKernelEx(&cfg, k_explore_cluster_batch<false>, As_dev, starts_dev, nq, next_dev);
+    e = cudaLaunchKernelEx(&cfg, k_explore_cluster_batch<false>, As_dev, starts_dev, nq, next_dev, ls);
   note_launch();
   return e == cudaSuccess ? PUMP_OK : PUMP_ERR_CUDA;
 }
@@ -1855,7 +1892,8 @@ int run_explore_fused(pump_graph* g, const ExploreArgs& A0, int nr, bool dsm, cu
   attr[1].val.cooperative = 1;
   cfg.numAttrs = 2;
   const int32_t start = g->start;
-  if (cudaLaunchKernelEx(&cfg, k_explore_fused<true>, A, start, F) != cudaSuccess) {
+  const LaunchShape ls{nr, (uint32_t)smem};
+  if (cudaLaunchKernelEx(&cfg, k_explore_fused<true>, A, start, F, ls) != cudaSuccess) {
     cudaGetLastError();
     fused_disable(dev, smem);
     g->rowcnt_dirty = true;

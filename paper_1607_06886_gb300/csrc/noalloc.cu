@@ -1,9 +1,11 @@
 // Explore for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a captured
-// CUDA graph or another library's stream-ordered region, an embedded runtime
-// whose memory is pinned down up front, or a process whose allocator belongs
-// to a host framework that may not be re-entered from here.  For them
+// Some callers of a motion planner cannot call cudaMalloc while they plan: a
+// robot's real-time control loop that reserves all of its device memory at
+// start-up (an allocation mid-loop can block for an unbounded time or fail
+// when memory is fragmented), an embedded runtime whose memory budget is
+// fixed up front, or a process whose device allocator belongs to a host
+// framework that must not be re-entered from inside this library.  For them
 // pump_explore_noalloc runs the same Explore kernels as pump_explore, but the
 // kernels' scratch (per-node dominance table, group list and offsets, block
 // counters, control block, goal list) lives in one file-scope device array of
@@ -15,7 +17,8 @@
 // device shares it.  Its contents persist from the previous call; everything
 // the kernels read is written by the call's own initialisation first.  Two
 // calls whose work overlaps on the GPU (different streams, or another thread)
-// race on the array.
+// race on the array.  A call waits for its own work before it returns, also
+// when it fails after its first launch, so serialised calls never overlap.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -53,13 +56,15 @@ int scratch_address(unsigned char** out) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-bool on_device(const void* p) {
+// Device memory of device `dev` (the scratch array used is that device's copy), or managed memory.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 int32_t popc_bound(double a, int N) {
@@ -68,7 +73,8 @@ int32_t popc_bound(double a, int N) {
   return (int32_t)(k < (double)N + 1.0 ? k : (double)N + 1.0);
 }
 
-// Bytes of the scratch array one call needs.
+// Bytes of the scratch array one call needs; `capacity` is the arena size the kernels use
+// (min of the caller's buffers and max_plans).
 int scratch_bytes(int32_t n, int32_t n_particles, const pump_plan_params* p, int64_t capacity, size_t* bytes) {
   if (!p || !bytes || n < 1 || n_particles < 32 || capacity < 1) return PUMP_ERR_INVALID_ARG;
   const int32_t kmax = popc_bound(((double)p->eta * (double)p->alpha) * (double)n_particles, n_particles);
@@ -96,12 +102,15 @@ extern "C" int pump_explore_noalloc(int32_t n, const int32_t* row_ptr, const int
   if (!(radius > 0.f) || !(p->lambda > 0.f) || !(p->lambda <= 1.f) || !(p->alpha >= 0.f) || !(p->eta > 0.f) ||
       p->max_iterations < 1 || p->max_plans < 1)
     return PUMP_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PUMP_ERR_CUDA;
   const void* dev_ptrs[] = {row_ptr, col, ecost, emask, is_goal, plan_head, plan_parent, plan_cost,
                             plan_mask, plan_popc, plan_created, plan_expanded, goal_plans};
   for (const void* q : dev_ptrs)
-    if (!q || !on_device(q)) return PUMP_ERR_INVALID_ARG;
+    if (!q || !on_device(q, dev)) return PUMP_ERR_INVALID_ARG;
+  const int64_t cap = capacity < p->max_plans ? capacity : p->max_plans;  // arena the kernels use
   size_t need = 0;
-  int rc = scratch_bytes(n, n_particles, p, capacity, &need);
+  int rc = scratch_bytes(n, n_particles, p, cap, &need);
   if (rc) return rc;
   if (need > kStaticScratchBytes) return PUMP_ERR_INVALID_ARG;
   unsigned char* base = nullptr;
@@ -125,12 +134,12 @@ extern "C" int pump_explore_noalloc(int32_t n, const int32_t* row_ptr, const int
   A.bcnt = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * kBlockSlots));
   A.bdeg = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * kBlockSlots));
   A.mbest = reinterpret_cast<uint32_t*>(carve(sizeof(uint32_t) * (size_t)n * kstride));
-  A.group = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)capacity));
-  A.ginfo = reinterpret_cast<int4*>(carve(sizeof(int4) * (size_t)capacity));
-  A.pedge = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)capacity));
-  A.goal_all = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)capacity));
+  A.group = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)cap));
+  A.ginfo = reinterpret_cast<int4*>(carve(sizeof(int4) * (size_t)cap));
+  A.pedge = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)cap));
+  A.goal_all = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)cap));
   A.etgt = nullptr;  // edge targets are read from the graph arrays
-  A.goff = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * ((size_t)capacity + 1)));
+  A.goff = reinterpret_cast<int64_t*>(carve(sizeof(int64_t) * ((size_t)cap + 1)));
   A.row_ptr = row_ptr;
   A.col = col;
   A.ecost = ecost;
@@ -151,7 +160,7 @@ extern "C" int pump_explore_noalloc(int32_t n, const int32_t* row_ptr, const int
   A.cost = plan_cost;
   A.popc = plan_popc;
   A.mask = plan_mask;
-  A.cap = capacity < p->max_plans ? capacity : p->max_plans;
+  A.cap = cap;
   A.spin_limit = 20000000ll;
 
   // a stack graph record carries the node count, start and goal output; it owns no memory
@@ -161,9 +170,19 @@ extern "C" int pump_explore_noalloc(int32_t n, const int32_t* row_ptr, const int
   shell.ex.goal_sorted = goal_plans;
   rc = run_explore_kernels(&shell, A, explore_mode(p->flags), s);
   if (!rc) rc = run_goal_finalize(&shell, A, s);
-  if (rc) return rc;
+  if (rc) {
+    // kernels enqueued before the failure may still use the shared array: the next call must
+    // not start before they end
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    return rc;
+  }
   ExploreCtl h;
-  if (cudaMemcpyAsync(&h, A.ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PUMP_ERR_CUDA;
+  if (cudaMemcpyAsync(&h, A.ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    return PUMP_ERR_CUDA;
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) return PUMP_ERR_CUDA;
   pump_plan_result r{};
   r.status = h.status;

@@ -154,6 +154,8 @@ static int32_t popc_bound(double a, int N) {
 
 void fill_explore_stats(pump_graph* g, const ExploreCtl& h, pump_plan_result* st) {
   g->explored = true;
+  // a fused launch that refused its launch shape counted no row: zero the counts before the next
+  if (g->last_fused && h.status == PUMP_ERR_CUDA) g->rowcnt_dirty = true;
   g->last_plans = h.n_plans;
   g->last_goal = h.status ? 0 : h.n_goal;
   st->n_candidates = h.n_candidates;
@@ -347,7 +349,7 @@ const char* pump_status_str(int st) {
   }
 }
 
-int pump_graph_build(const float* states, int32_t n, int32_t start_idx, const int32_t* goal_idx, int32_t n_goal,
+int pump_build_graph(const float* states, int32_t n, int32_t start_idx, const int32_t* goal_idx, int32_t n_goal,
                      const pump_aabb* boxes, int32_t n_boxes, const float* xi, const pump_graph_params* prm,
                      void* stream, pump_graph** out) {
   if (!out || !states || !goal_idx || !xi || !prm) return PUMP_ERR_INVALID_ARG;
@@ -412,6 +414,13 @@ int pump_graph_build(const float* states, int32_t n, int32_t start_idx, const in
   }
   *out = g;
   return PUMP_OK;
+}
+
+// Former name of pump_build_graph, kept for existing callers.
+int pump_graph_build(const float* states, int32_t n, int32_t start_idx, const int32_t* goal_idx, int32_t n_goal,
+                     const pump_aabb* boxes, int32_t n_boxes, const float* xi, const pump_graph_params* prm,
+                     void* stream, pump_graph** out) {
+  return pump_build_graph(states, n, start_idx, goal_idx, n_goal, boxes, n_boxes, xi, prm, stream, out);
 }
 
 int pump_graph_from_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, const float* ecost,

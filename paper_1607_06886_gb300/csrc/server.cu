@@ -107,7 +107,7 @@ struct pump_server {
 
   void run(Job* j, cudaStream_t s, Done* d) {
     pump_graph* g = nullptr;
-    int rc = pump_graph_build(j->states.data(), j->n, j->start, j->goal.data(), (int32_t)j->goal.size(),
+    int rc = pump_build_graph(j->states.data(), j->n, j->start, j->goal.data(), (int32_t)j->goal.size(),
                               j->boxes.empty() ? nullptr : j->boxes.data(), (int32_t)j->boxes.size(), j->xi.data(),
                               &j->gp, s, &g);
     std::memset(&d->result, 0, sizeof(d->result));

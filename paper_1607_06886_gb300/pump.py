@@ -97,7 +97,7 @@ def load(build_if_missing: bool = False):
     L = C.CDLL(path)
     P, i32, i64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
     L.pump_set_allocator.argtypes = [_ALLOC_T, _FREE_T, P]
-    L.pump_graph_build.argtypes = [P, i32, i32, P, i32, P, i32, P, C.POINTER(GraphParams), P, C.POINTER(P)]
+    L.pump_build_graph.argtypes = [P, i32, i32, P, i32, P, i32, P, C.POINTER(GraphParams), P, C.POINTER(P)]
     L.pump_graph_from_csr.argtypes = [i32, P, P, P, P, i32, i32, P, i32, P, C.POINTER(P)]
     L.pump_edge_masks.argtypes = [P, P]
     L.pump_explore.argtypes = [P, C.POINTER(PlanParams), f32, C.POINTER(PlanResult), P]
@@ -399,7 +399,7 @@ class Graph:
     @classmethod
     def build(cls, states, goal_idx, boxes, xi, radius: float, n_particles: int, n_waypoints: int,
               sigma: float, start_idx: int = 0, stream: Optional[int] = None, flags: int = 0) -> "Graph":
-        """pump_graph_build; flags: GRAPH_HSMC for Half-Space Monte Carlo masks, GRAPH_SEPARATE_MASKS
+        """pump_build_graph; flags: GRAPH_HSMC for Half-Space Monte Carlo masks, GRAPH_SEPARATE_MASKS
         to keep the masks of every query in their own launch."""
         L = load()
         st = _np(states, np.float32)
@@ -411,10 +411,10 @@ class Graph:
         prm = GraphParams(float(radius), int(n_particles), int(n_waypoints), float(sigma), int(flags))
         out = C.c_void_p()
         s = current_stream() if stream is None else stream
-        rc = L.pump_graph_build(_ptr(st), n, int(start_idx), _ptr(gi), int(len(gi)), _ptr(bx) if nb else None, nb,
+        rc = L.pump_build_graph(_ptr(st), n, int(start_idx), _ptr(gi), int(len(gi)), _ptr(bx) if nb else None, nb,
                                 _ptr(x), C.byref(prm), s, C.byref(out))
         if rc:
-            raise PumpError(rc, "pump_graph_build")
+            raise PumpError(rc, "pump_build_graph")
         return cls(out.value)
 
     @classmethod

@@ -19,7 +19,7 @@ def declared_symbols():
 
 def test_header_declares_the_boundary():
     syms = declared_symbols()
-    for s in ("pump_graph_build", "pump_plan", "pump_certify", "pump_explore", "pump_edge_masks",
+    for s in ("pump_build_graph", "pump_graph_build", "pump_plan", "pump_certify", "pump_explore", "pump_edge_masks",
               "pump_graph_from_csr", "pump_export", "pump_graph_destroy", "pump_status_str", "pump_set_allocator"):
         assert s in syms
 
@@ -42,6 +42,7 @@ def test_invalid_arguments_rejected_before_any_device_work():
     lib = pump.load()
     out = ctypes.c_void_p()
     # NULL pointers and bad sizes are refused on the host
+    assert lib.pump_build_graph(None, 0, 0, None, 0, None, 0, None, None, None, ctypes.byref(out)) == pump.ERR_INVALID_ARG
     assert lib.pump_graph_build(None, 0, 0, None, 0, None, 0, None, None, None, ctypes.byref(out)) == pump.ERR_INVALID_ARG
     assert lib.pump_graph_from_csr(0, None, None, None, None, 32, 0, None, 0, None, ctypes.byref(out)) == pump.ERR_INVALID_ARG
     assert lib.pump_plan(None, None, None, 0, None, None) == pump.ERR_INVALID_ARG

@@ -352,6 +352,55 @@ def test_mc_matches_independent_simulation():
     assert abs(c / M1 - p) <= 5 * math.sqrt(p * (1 - p) * (1 / M1 + 1 / M2))
 
 
+def _sim_crossing(taus, W, S_, sigma, delta, M, joint, seed):
+    """Fraction of closed-loop deviation paths whose x component reaches delta at some sub-step of
+    a path of connections with durations `taus` (independent numpy simulation: exact transition
+    e^{A h} and Van Loan noise per step, h = float(float(tau / W) / substeps)).  joint: 'carry'
+    keeps the deviation through each joint, 'redraw' draws it afresh from the stationary law,
+    'zero' resets it to 0."""
+    S = scipy.linalg.solve_continuous_lyapunov(A_CL, -sigma ** 2 * np.eye(2))
+    rng = np.random.default_rng(seed)
+    d = rng.multivariate_normal(np.zeros(2), S, size=M)
+    hit = np.zeros(M, bool)
+    for ei, tau in enumerate(taus):
+        if ei > 0 and joint == "redraw":
+            d = rng.multivariate_normal(np.zeros(2), S, size=M)
+        elif ei > 0 and joint == "zero":
+            d = np.zeros((M, 2))
+        hs = float(np.float32(np.float32(np.float32(tau) / np.float32(W)) / np.float32(S_)))
+        Phi = scipy.linalg.expm(A_CL * hs)
+        F = scipy.linalg.expm(np.block([[-A_CL, sigma ** 2 * np.eye(2)], [np.zeros((2, 2)), A_CL.T]]) * hs)
+        Q = F[2:, 2:].T @ F[:2, 2:]
+        for _ in range(W * S_):
+            d = d @ Phi.T + rng.multivariate_normal(np.zeros(2), Q, size=M)
+            hit |= d[:, 0] >= delta
+    return float(hit.mean())
+
+
+def test_mc_carries_deviation_across_connections():
+    """MC(p) (Section III-A) is the collision probability of the whole plan: the tracking
+    deviation runs on through the joint between two connections.  Two straight constant-velocity
+    connections of different durations (so different sub-step sizes) beside a face: the oracle's
+    count matches an independent simulation that carries the deviation through the joint, and is
+    far from what re-drawing it at the joint or resetting it to zero would give (about 27 and 14
+    standard errors apart), so either mistake in the oracle fails here."""
+    sigma, W, S_, v = 0.02, 10, 4, 0.6
+    taus = [np.float32(0.15), np.float32(0.35)]
+    ys = [0.2, 0.2 + 0.6 * 0.15, 0.2 + 0.6 * 0.5]
+    st = np.array([[0.5, y, 0.5, 0.0, v, 0.0] for y in ys], np.float32)
+    S = scipy.linalg.solve_continuous_lyapunov(A_CL, -sigma ** 2 * np.eye(2))
+    delta = 1.5 * math.sqrt(S[0, 0])
+    box = np.array([[0.5 + delta, -1, -1, 3, 3, 3]], np.float32)
+    M1, M2 = 20000, 200000
+    c = cpu.mc_certify(st, [0, 1, 2], taus, W, sigma, box, M1, S_, 17)
+    p_carry = _sim_crossing(taus, W, S_, sigma, delta, M2, "carry", 5)
+    sd = math.sqrt(p_carry * (1 - p_carry) * (1 / M1 + 1 / M2))
+    assert abs(c / M1 - p_carry) <= 5 * sd, (c / M1, p_carry, sd)
+    for joint in ("redraw", "zero"):
+        p_alt = _sim_crossing(taus, W, S_, sigma, delta, M2, joint, 6)
+        assert abs(c / M1 - p_alt) > 8 * sd, (joint, c / M1, p_alt, sd)
+
+
 # --------------------------------------------------------------------------- thresholds
 def test_cp_thresholds_golden():
     rows = [l.split() for l in open(os.path.join(GOLDEN, "cp_thresholds.txt")) if l.strip() and not l.startswith("#")]
@@ -563,3 +612,26 @@ def test_explore_capacity_error():
     ex = cpu.explore(g.n, g.row_ptr, g.col, g.ecost, g.emask, 0, [1], 1, 3, 0.5, g.radius, max_plans=50,
                      flags=cpu.NO_EARLY_STOP)
     assert ex["status"] == cpu.ERR_CAPACITY
+
+
+# --------------------------------------------------------------------------- all-cores oracle
+@pytest.mark.parametrize("threads", [2, 5])
+def test_all_cores_oracle_equals_single_thread(threads):
+    """The threaded oracle (used only to time the oracle on every host core) gives the
+    single-thread masks and Explore result exactly."""
+    wl = inputs.make_workload("indoor_4k", seed=1, n_samples=500)
+    g = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
+    m1 = cpu.edge_masks(g, wl.xi, wl.boxes, wl.n_particles)
+    mt = cpu.edge_masks(g, wl.xi, wl.boxes, wl.n_particles, n_threads=threads)
+    assert np.array_equal(m1, mt) and m1.any()
+    kmin, kmax = cpu.cp_thresholds(wl.alpha, wl.eta, wl.n_particles)
+    for flags in (0, cpu.NO_EARLY_STOP):
+        a = cpu.explore(g["n"], g["row_ptr"], g["col"], g["ecost"], m1, 0, wl.goal_idx, kmin, kmax, wl.lam,
+                        wl.radius, flags=flags)
+        b = cpu.explore(g["n"], g["row_ptr"], g["col"], g["ecost"], m1, 0, wl.goal_idx, kmin, kmax, wl.lam,
+                        wl.radius, flags=flags, n_threads=threads)
+        for k in ("status", "n_plans", "n_candidates", "n_kept", "n_iterations", "n_groups_expanded", "n_goal"):
+            assert a[k] == b[k], k
+        for k in ("head", "parent", "mask", "popc", "t_created", "e_expanded", "removed", "goal_plans"):
+            assert np.array_equal(a[k], b[k]), k
+        assert np.array_equal(a["cost"].view(np.uint32), b["cost"].view(np.uint32))
