@@ -266,38 +266,56 @@ def main():
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    # warm-up
+    # warm-up (synchronous: gives the step's partial-plan count)
     for _ in range(max(args.warmup, 3)):
         res = G.plan(prm_step)
         assert res["rc"] == pump.OK, res
     torch.cuda.synchronize()
+    step_cands = res["n_candidates"]
 
-    # timed region: K plan steps, device time by CUDA events; L2 flushed between steps
+    # timed region: K steps enqueued back to back (PUMP_NO_WAIT: no host round trip per query),
+    # device time of each by CUDA events on the launching stream; L2 flushed between steps
+    prm_async = plan_params(pump, wl)
+    prm_async.flags = pump.EXPLORE_ONLY | pump.NO_WAIT
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = pump.kernel_launches()
-    cands = 0
-    parts = {"ms_masks": 0.0, "ms_explore": 0.0, "ms_select": 0.0}
     fused_steps = 0
     with ClockSampler(torch.cuda.current_device()) as clk:
         barrier(ws)
         torch.cuda.synchronize()
+        for _ in range(4):  # device work ahead of the first step, so its launch is not waited for
+            flush.zero_()
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
-            res = G.plan(prm_step)
+            r = G.plan(prm_async)
             ev[k][1].record(stream)
-            cands += res["n_candidates"]
-            fused_steps += res["fused"]
-            for key in ("ms_masks", "ms_explore"):
-                parts[key] += res[key]
+            assert r["rc"] == pump.OK, r
+            fused_steps += r["fused"]
         torch.cuda.synchronize()
         barrier(ws)
     launches = pump.kernel_launches() - launches0
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    chk = G.collect()  # the last step's counters: the same query every step
+    assert chk["rc"] == pump.OK and chk["n_candidates"] == step_cands, (chk, step_cands)
+    cands = args.steps * step_cands
+    step_times = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_times)
     ms_max = max_over_ranks(ms, ws)
     cands_all = sum_over_ranks(cands, ws)
     value = cands_all / (ms_max / 1000.0)
     ms_per_step = ms_max / args.steps
+
+    # the same step as a synchronous call (host launch path, read-back and wait included)
+    sync_t = []
+    for _ in range(max(10, min(args.steps, 40))):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rs = G.plan(prm_step)
+        b.record(stream)
+        sync_t.append((a, b))
+    torch.cuda.synchronize()
+    sync_ms = [a.elapsed_time(b) for a, b in sync_t]
 
     # the whole query on the resident graph (with PlanSelection and Monte Carlo certification)
     fq = []
@@ -314,8 +332,9 @@ def main():
     full = fq[-1][2]
     assert full["rc"] in (pump.OK, pump.ERR_INFEASIBLE), full
 
-    # dominant kernels timed alone with CUDA events on the launching stream
-    fused_ms = parts["ms_explore"] / args.steps if fused_steps == args.steps else None
+    # dominant kernels timed alone with CUDA events on the launching stream; in the fused form a
+    # step is the one Explore launch, so its mean device time is the launch's
+    fused_ms = ms / args.steps if fused_steps == args.steps else None
     roof, kernel_detail = roofline_measure(pump, G, prm, wl, dev, flush, args.steps, fused_ms)
 
     # end to end through the public API from pinned host buffers
@@ -354,11 +373,16 @@ def main():
                    "waypoints": wl.n_waypoints, "boxes": int(wl.boxes.shape[0]), "cp_target": wl.alpha,
                    "edges": int(G.counts()[1]), "partial_plans_per_step": res["n_candidates"],
                    "plans_per_step": res["n_plans"], "groups": res["n_groups"], "seed_per_rank": "rank",
-                   "l2": "flushed between steps (2x L2 buffer write)", "parallelism": f"replicas{ws}"},
+                   "l2": "flushed between steps (2x L2 buffer write)", "parallelism": f"replicas{ws}",
+                   "steps_enqueued": "back to back without a host wait (PUMP_NO_WAIT); counts read once after"},
         "step": "edge masks + Explore (Algorithm 4), graph resident",
         "step_form": ("fused: masks computed by worker clusters inside the Explore launch"
                       if fused_steps == args.steps else "separate launches: masks kernel, then Explore"),
-        "step_ms": {k: v / args.steps for k, v in parts.items() if k != "ms_select"},
+        "step_ms": {"enqueued_mean": ms / args.steps, "enqueued_min": min(step_times),
+                    "enqueued_max": max(step_times), "synchronous_p50": float(np.percentile(sync_ms, 50)),
+                    "synchronous_p99": float(np.percentile(sync_ms, 99)),
+                    "synchronous": "one pump_plan call per step that waits for its counters (host launch path "
+                                   "and read-back included)"},
         "full_query": {"ms": fq_ms, "value": full["n_candidates"] / (fq_ms / 1000.0), "unit": "partial_plans/s",
                        "ms_masks": full["ms_masks"], "ms_explore": full["ms_explore"], "ms_select": full["ms_select"],
                        "includes": "edge masks + Explore + PlanSelection with Monte Carlo certification"},

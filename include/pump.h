@@ -50,6 +50,8 @@ typedef enum {
 #define PUMP_STEPWISE 4      /* run Explore's phases as separate launches           */
 #define PUMP_EXPLORE_GRID 8  /* run Explore as one grid-wide cooperative kernel
                                 instead of one thread-block cluster                 */
+#define PUMP_NO_WAIT 16      /* with PUMP_EXPLORE_ONLY: pump_plan enqueues the query
+                                and returns at once (see pump_plan_collect)         */
 
 typedef struct pump_graph pump_graph;
 
@@ -94,7 +96,7 @@ typedef struct {
   int64_t max_plans;      /* plan arena capacity; more survivors -> PUMP_ERR_CAPACITY      */
   int32_t max_iterations; /* cap on Explore's group index; exceeded -> PUMP_ERR_TIMEOUT    */
   int32_t flags;          /* PUMP_NO_EARLY_STOP | PUMP_EXPLORE_ONLY | PUMP_STEPWISE |
-                             PUMP_EXPLORE_GRID                                        */
+                             PUMP_EXPLORE_GRID | PUMP_NO_WAIT                         */
 } pump_plan_params;
 
 typedef struct {
@@ -228,11 +230,27 @@ int pump_explore(pump_graph* g, const pump_plan_params* params, float radius, pu
  * the start), which later queries reuse.  The environment variable
  * PUMP_FUSED_MASKS=0 keeps the masks in their own launch.  Results are the
  * same either way.  `out` is written on PUMP_OK
- * and on PUMP_ERR_INFEASIBLE (out->status tells which).  Synchronises.
- * Errors: those of pump_explore, plus INFEASIBLE (no certified plan).
+ * and on PUMP_ERR_INFEASIBLE (out->status tells which).  Synchronises,
+ * except with PUMP_EXPLORE_ONLY | PUMP_NO_WAIT: the query (masks and
+ * Explore) is only enqueued on `stream` and out->status, out->fused are
+ * written, no counters or times; read the counters with pump_plan_collect.
+ * Queries enqueued back to back on one graph run in stream order; a device
+ * error (a timed-out wait) in one may make the next ones fail as well.
+ * Errors: those of pump_explore, plus INFEASIBLE (no certified plan);
+ * INVALID_ARG for PUMP_NO_WAIT without PUMP_EXPLORE_ONLY.
  */
 int pump_plan(pump_graph* g, const pump_plan_params* params, int32_t* path, int32_t path_cap,
               pump_plan_result* out, void* stream);
+
+/* --------------------------------------------------------------------------
+ * pump_plan_collect: waits for `stream` and writes the Explore counters of
+ * the graph's last query to `out` (as pump_explore does); afterwards
+ * pump_export reads that query's arena.  For queries enqueued with
+ * PUMP_NO_WAIT.  No counterpart in the paper (runtime plumbing).  Returns the
+ * query's status.  Errors: INVALID_ARG (NULL, or no query ran), CUDA, and
+ * the query's own CAPACITY / TIMEOUT.
+ */
+int pump_plan_collect(pump_graph* g, pump_plan_result* out, void* stream);
 
 /* --------------------------------------------------------------------------
  * pump_plan_batch: pump_plan for n_queries independent queries, one per

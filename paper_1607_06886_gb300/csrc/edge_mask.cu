@@ -1,8 +1,8 @@
 // Edge particle collision masks (Section III-B, with a direct particle-in-box
 // test in place of the half-space test): the graph-build bound pass, the query
 // pass over every edge (a warp per edge, the per-edge routine in mask_dev.cuh)
-// and the Half-Space Monte Carlo forms.  The normals xi_t[k][axis][i] and the
-// boxes sit in shared memory; the grids are persistent over the edges.
+// and the Half-Space Monte Carlo forms.  The normals (xi_t[k][axis][i], or pair-major for the box
+// masks) and the boxes sit in shared memory; the grids are persistent over the edges.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -139,33 +139,44 @@ __global__ void k_edge_ibox(const float* __restrict__ nom, const unsigned int* _
   }
 }
 
-// Query pass: a warp per edge (maskdev::edge_mask_one), grid persistent over the edges.
+// Query pass: a warp per edge (maskdev::edge_mask_one), grid persistent over the edges; each warp
+// takes the next kMaskChunk edges from a counter (edges differ widely in work: one whose position
+// box meets no obstacle is a few instructions), so no SM idles while others hold long edges.
 #ifndef PUMP_MASK_MIN_BLOCKS
-#define PUMP_MASK_MIN_BLOCKS 4  // 64 registers: four 256-thread blocks per SM (measured best)
+#define PUMP_MASK_MIN_BLOCKS 3  // 85 registers: three 256-thread blocks per SM (packed pairs of words)
 #endif
+constexpr int kMaskChunk = 4;
 template <bool kSmemXi>
-__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask(const float2* __restrict__ xi_g, int N, int W,
+__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask(const float4* __restrict__ xp_g, int N, int W,
                                                            const float* __restrict__ phi, const float* __restrict__ Lg,
                                                            const float* __restrict__ nom, const float* __restrict__ linf_g,
                                                            const float* __restrict__ ibox_g,
                                                            const unsigned int* __restrict__ dmax,
                                                            const float* __restrict__ boxes_g, int nb, int E, int w,
+                                                           unsigned long long* __restrict__ ctr,
                                                            uint32_t* __restrict__ mask) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* boxes = reinterpret_cast<float*>(smem);  // kBoxStride floats per box (16-byte aligned rows)
   int* cand = reinterpret_cast<int*>(boxes + kBoxStride * nb);
   uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kWarps * maskdev::kCandCap);
-  float2* xi_s = reinterpret_cast<float2*>(smem + edge_mask_fixed_smem(nb));
-  const int xi_n = (W + 1) * 3 * N;
-  maskdev::stage(boxes_g, nb, boxes, xi_g, kSmemXi ? xi_s : nullptr, xi_n);
+  float4* xp_s = reinterpret_cast<float4*>(smem + edge_mask_fixed_smem(nb));
+  const int xp_n = (W + 1) * 3 * maskdev::pair_count(w) * 32;
+  maskdev::stage(boxes_g, nb, boxes, xp_g, kSmemXi ? xp_s : nullptr, xp_n);
   __syncthreads();
-  const float2* xi = kSmemXi ? xi_s : xi_g;
+  const float4* xp = kSmemXi ? xp_s : xp_g;
   const float linf[3] = {linf_g[0], linf_g[1], linf_g[2]};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int* my_cand = cand + warp * maskdev::kCandCap;
   uint32_t* wm = wmask_all + warp * kMaxWaypoints;
-  for (long long e = (long long)blockIdx.x * kWarps + warp; e < E; e += (long long)gridDim.x * kWarps)
-    maskdev::edge_mask_one(e, xi, N, W, phi, Lg, nom, linf, ibox_g, dmax, boxes, nb, w, my_cand, wm, lane, mask);
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(ctr, (unsigned long long)kMaskChunk);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= (unsigned long long)E) break;
+    const long long e1 = min((long long)E, (long long)t + kMaskChunk);
+    for (long long e = (long long)t; e < e1; ++e)
+      maskdev::edge_mask_one(e, xp, N, W, phi, Lg, nom, linf, ibox_g, dmax, boxes, nb, w, my_cand, wm, lane, mask);
+  }
 }
 
 // ---------------------------------------------------------------- Half-Space Monte Carlo
@@ -298,7 +309,7 @@ __device__ __forceinline__ void word_pass_hs(const float2* __restrict__ xi, int 
 }
 
 template <bool kSmemXi>
-__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask_hs(
+__global__ void __launch_bounds__(kWarps * 32, 4) k_edge_mask_hs(
     const float2* __restrict__ xi_g, int N, int W, const float* __restrict__ phi, const float* __restrict__ Lg,
     const float* __restrict__ linf_g, const int32_t* __restrict__ hs_off, const float4* __restrict__ hs_ab, int E,
     int w, uint32_t* __restrict__ mask) {
@@ -354,7 +365,7 @@ __global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask
 
 size_t edge_mask_smem(int N, int W, int nb, bool xi_in_smem) {
   size_t b = edge_mask_fixed_smem(nb);
-  if (xi_in_smem) b += sizeof(float2) * (size_t)(W + 1) * 3 * N;
+  if (xi_in_smem) b += sizeof(float4) * (size_t)(W + 1) * 3 * maskdev::pair_count(N / 32) * 32;
   return b;
 }
 
@@ -495,21 +506,24 @@ int compute_edge_masks(pump_graph* g, cudaStream_t s) {
   const bool use_smem = smem_xi <= 160 * 1024;
   const size_t smem = use_smem ? smem_xi : edge_mask_smem(g->N, g->W, g->n_boxes, false);
   int grid = 1;
+  PUMP_CUDA_TRY(cudaMemsetAsync(g->wctr, 0, sizeof(unsigned long long), s));
   if (use_smem) {
     {
-      const int rco = occupancy_grid(k_edge_mask<true>, smem, kWarps, g->E, &grid);
+      const int rco = occupancy_grid(k_edge_mask<true>, smem, kWarps * kMaskChunk, g->E, &grid);
       if (rco) return rco;
     }
-    k_edge_mask<true><<<grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
-                                                      g->ibox, g->dmax, g->boxes, g->n_boxes, g->E, g->n_words, g->emask);
+    k_edge_mask<true><<<grid, kWarps * 32, smem, s>>>(g->xi_p, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
+                                                      g->ibox, g->dmax, g->boxes, g->n_boxes, g->E, g->n_words,
+                                                      g->wctr, g->emask);
     note_launch();
   } else {
     {
-      const int rco = occupancy_grid(k_edge_mask<false>, smem, kWarps, g->E, &grid);
+      const int rco = occupancy_grid(k_edge_mask<false>, smem, kWarps * kMaskChunk, g->E, &grid);
       if (rco) return rco;
     }
-    k_edge_mask<false><<<grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
-                                                       g->ibox, g->dmax, g->boxes, g->n_boxes, g->E, g->n_words, g->emask);
+    k_edge_mask<false><<<grid, kWarps * 32, smem, s>>>(g->xi_p, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
+                                                       g->ibox, g->dmax, g->boxes, g->n_boxes, g->E, g->n_words,
+                                                       g->wctr, g->emask);
     note_launch();
   }
   PUMP_CUDA_TRY(cudaGetLastError());

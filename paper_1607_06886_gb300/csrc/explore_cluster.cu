@@ -123,16 +123,19 @@ __device__ __forceinline__ bool launch_shape_ok(const LaunchShape& ls) {
          blockDim.z == 1 && gridDim.x % (unsigned)ls.nr == 0;
 }
 
-// Counts one CTA publishes after phase B (every CTA reads them in phase C).
-struct Pub {
+// Counts one CTA publishes after phase B (every CTA reads them in phase C).  16-byte aligned:
+// the end of phase B copies the whole record into every CTA's shared memory with vector stores.
+struct alignas(16) Pub {
+  unsigned long long odeg[kWin], ndeg[kWin];
+  int32_t ocnt[kWin], ncnt[kWin];
   int32_t surv;      // survivors of the CTA's chunk
   int32_t minb;      // least group index of an open undominated plan seen by the CTA
   int32_t min_open;  // least id of an older open undominated plan (INT_MAX if none)
   uint32_t stop;     // bit q: a member of group i+1+q is a goal plan with popc < K_min
   int32_t err;       // a wait for a row's masks ran out (fused form)
-  int32_t ocnt[kWin], ncnt[kWin];
-  unsigned long long odeg[kWin], ndeg[kWin];
 };
+constexpr int kPubVec = (int)(sizeof(Pub) / 16);
+static_assert(sizeof(Pub) % 16 == 0, "Pub copies as 16-byte words");
 // Counts for one group index beyond the window (extra round).
 struct PubS {
   int32_t ocnt, ncnt;
@@ -178,8 +181,9 @@ struct CSmem {
   uint32_t odg[kOCap];
   float ocost[kOCap];
   int16_t opc[kOCap];
-  Pub pub;     // this CTA's counts (accumulated in phase B, read by every CTA in phase C)
-  PubS pubs_s; // the same for a group index beyond the window
+  Pub pub;     // this CTA's counts (accumulated in phase B)
+  Pub pub_all[kMaxCluster];  // every CTA's counts (copied here by their owners at the end of phase B)
+  PubS pubs_s; // the same for a group index beyond the window (read remotely in phase C)
   // cluster-wide values of phase C, derived by warp 0 and read by the whole CTA
   int32_t b_nbk, b_min_open, b_before_s, b_total_s, b_before_o, b_total_o, b_before_n, b_total_n, b_stop, b_fast, b_err;
   int32_t werr;        // this CTA: a wait for a row's masks ran out (fused form)
@@ -635,6 +639,15 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
     sm->pub.minb = minb;
     sm->pub.min_open = min_open;
   }
+  __syncthreads();
+  // the record into slot r of every CTA (the cluster barrier that closes this phase orders the
+  // stores before phase C reads them; slot r is rewritten only after two more barriers)
+  const uint4* src = reinterpret_cast<const uint4*>(&sm->pub);
+  for (int t = threadIdx.x; t < kPubVec * nr; t += kCT) {
+    const int dr = t / kPubVec, wv = t - dr * kPubVec;
+    uint4* dst = reinterpret_cast<uint4*>(cl.map_shared_rank(&sm->pub_all[r], (unsigned)dr));
+    dst[wv] = src[wv];
+  }
 }
 
 // Warp 0: exclusive prefix over CTAs (lanes) of v for this CTA, and the total.
@@ -762,7 +775,7 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
   // Warp 0 reads every CTA's counts (lane l from CTA l) and derives the cluster-wide values.
   if (warp == 0) {
     const bool on = lane < nr;
-    const Pub* rp = cl.map_shared_rank(&sm->pub, (unsigned)(on ? lane : 0));
+    const Pub* rp = &sm->pub_all[on ? lane : 0];
     int32_t minb = on ? rp->minb : kNoBucket;
     int32_t mo = on ? rp->min_open : INT_MAX;
     const int32_t sv = on ? rp->surv : 0;
@@ -1173,7 +1186,7 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_cluster_batch(const ExploreA
 // ---------------------------------------------------------------- fused form
 // Mask workers' arguments: the query pass's inputs and the order they take the edges in.
 struct FuseArgs {
-  const float2* xi;          // [(W+1)][3][N] normals
+  const float4* xp;          // pair-major normals (maskdev::pair_count)
   const float* phi;          // E x 4
   const float* L;            // E x 3
   const float* nom;          // E x W x 3
@@ -1185,52 +1198,79 @@ struct FuseArgs {
   uint32_t* emask;           // E x w (written)
   uint32_t* rowcnt;          // n + 1: finished edges per row, then worker warps finished (both
                              // accumulated over runs)
+  unsigned long long* wctr;  // positions taken by the workers, accumulated over runs
   int32_t N, W, nb, E, w, n;
   int32_t xi_smem;           // the normals fit in shared memory next to the boxes
   int32_t hold_row;          // test hook: this row is never counted (-1: none)
-  int32_t head;              // positions [0, head) are computed by the Explore cluster first
   int32_t* goal_sorted;      // P_goal in PlanSelection order (written after Explore, CTA 0)
 };
 
 // Shared memory a worker CTA uses (boxes, per-warp scratch, normals when they fit).
 __host__ __device__ constexpr size_t worker_smem(int nb, int N, int W, bool xi_smem) {
-  return maskdev::fixed_smem(nb, kCW) + (xi_smem ? sizeof(float2) * (size_t)(W + 1) * 3 * N : 0);
+  return maskdev::fixed_smem(nb, kCW) +
+         (xi_smem ? sizeof(float4) * (size_t)(W + 1) * 3 * maskdev::pair_count(N / 32) * 32 : 0);
 }
 
-#ifndef PUMP_FUSED_MASK_NW
-#define PUMP_FUSED_MASK_NW 2  // mask words side by side per pass in the fused kernel (2: no spills beside Explore)
+#ifndef PUMP_FUSED_MASK_NP
+#define PUMP_FUSED_MASK_NP 1  // word pairs side by side per pass in the fused kernel (1: no spills beside Explore)
 #endif
-// Positions q0 + v, q0 + v + V, ... below q1 of the edge order, warp v of V: the edge's mask
-// words, then its count toward its row by a release add after the warp barrier.  The caller's
-// block stages the boxes (and the normals) first.
+constexpr int kWorkChunk = 2;  // positions a worker warp takes at a time
+
+// Mask of the edge at position q of the order, then its count toward its row by a release add
+// after the warp barrier.
+__device__ __forceinline__ void mask_position(const FuseArgs& F, const float4* xp, const float (&linf)[3],
+                                              const float* boxes, int* my_cand, uint32_t* wm, int lane, long long q) {
+  const int2 ex = __ldg(F.eorder + q);
+  maskdev::edge_mask_one<PUMP_FUSED_MASK_NP>(ex.x, xp, F.N, F.W, F.phi, F.L, F.nom, linf, F.ibox, F.dmax, boxes,
+                                             F.nb, F.w, my_cand, wm, lane, F.emask);
+  __syncwarp();
+  if (lane == 0 && ex.y != F.hold_row) red_release_add(F.rowcnt + ex.y, 1u);
+}
+
+// The block stages the boxes (and the normals, when they fit) in shared memory.  Then either
+// positions q0 + v, q0 + v + V, ... below q1 (warp v of V; `dynamic` false), or, with `dynamic`,
+// chunks of kWorkChunk positions from [q0, q1) in increasing order from the run's counter: run e
+// of a graph takes increments (e - 1) x per_run onward, per_run being the increments every run
+// makes (each worker warp takes chunks until one starts at or past q1).  A worker warp counts
+// itself done at the end.
 __device__ __forceinline__ void mask_positions(const FuseArgs& F, unsigned char* smem, long long q0, long long q1,
-                                               long long v, long long V, bool count_done) {
+                                               long long v, long long V, bool dynamic, uint32_t epoch_m1,
+                                               long long n_workers) {
   float* boxes = reinterpret_cast<float*>(smem);
   int* cand = reinterpret_cast<int*>(boxes + maskdev::kBoxStride * F.nb);
   uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kCW * maskdev::kCandCap);
-  float2* xi_s = reinterpret_cast<float2*>(smem + maskdev::fixed_smem(F.nb, kCW));
-  const int xi_n = (F.W + 1) * 3 * F.N;
-  maskdev::stage(F.boxes, F.nb, boxes, F.xi, F.xi_smem ? xi_s : nullptr, xi_n);
+  float4* xp_s = reinterpret_cast<float4*>(smem + maskdev::fixed_smem(F.nb, kCW));
+  const int xp_n = (F.W + 1) * 3 * maskdev::pair_count(F.w) * 32;
+  maskdev::stage(F.boxes, F.nb, boxes, F.xp, F.xi_smem ? xp_s : nullptr, xp_n);
   __syncthreads();
-  const float2* xi = F.xi_smem ? xi_s : F.xi;
+  const float4* xp = F.xi_smem ? xp_s : F.xp;
   const float linf[3] = {F.linf[0], F.linf[1], F.linf[2]};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int* my_cand = cand + warp * maskdev::kCandCap;
   uint32_t* wm = wmask_all + warp * kMaxWaypoints;
-  for (long long q = q0 + v; q < q1; q += V) {
-    const int2 ex = __ldg(F.eorder + q);
-    maskdev::edge_mask_one<PUMP_FUSED_MASK_NW>(ex.x, xi, F.N, F.W, F.phi, F.L, F.nom, linf, F.ibox, F.dmax, boxes, F.nb, F.w, my_cand, wm,
-                           lane, F.emask);
-    __syncwarp();
-    if (lane == 0 && ex.y != F.hold_row) red_release_add(F.rowcnt + ex.y, 1u);
+  if (!dynamic) {
+    for (long long q = q0 + v; q < q1; q += V) mask_position(F, xp, linf, boxes, my_cand, wm, lane, q);
+    return;
   }
-  if (count_done && lane == 0) red_release_add(F.rowcnt + F.n, 1u);  // this warp's edges are counted
+  const unsigned long long chunks = (unsigned long long)((max(q1 - q0, 0ll) + kWorkChunk - 1) / kWorkChunk);
+  const unsigned long long per_run = (chunks + (unsigned long long)n_workers) * kWorkChunk;
+  const unsigned long long base = (unsigned long long)epoch_m1 * per_run;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(F.wctr, (unsigned long long)kWorkChunk);
+    t = __shfl_sync(0xffffffffu, t, 0) - base;
+    const long long qa = q0 + (long long)t;
+    if (t >= (unsigned long long)(q1 - q0) || qa >= q1) break;
+    const long long qb = min(q1, qa + kWorkChunk);
+    for (long long q = qa; q < qb; ++q) mask_position(F, xp, linf, boxes, my_cand, wm, lane, q);
+  }
+  if (lane == 0) red_release_add(F.rowcnt + F.n, 1u);  // this warp's edges are counted
 }
 
 // Masks and Explore in one cooperative launch: cluster 0 runs Explore (A.rowcnt set), the
-// other clusters are mask workers.  The first positions of the order (the start row and its
-// neighbourhood, one edge per warp) are computed by the Explore cluster itself before it starts,
-// so the first groups do not wait for the workers' first edges; the workers take the rest.
+// other clusters are mask workers.  The first positions of the order (the start row, one edge per
+// warp on different SMs) are computed by the Explore cluster itself before it starts, so group 0
+// does not wait for the workers' first edges; the workers take the rest.
 // Cluster 0 also writes the run's initial state first and P_goal's order last.
 template <bool kDsm>
 __global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t start, FuseArgs F, LaunchShape ls) {
@@ -1245,11 +1285,15 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t
   cg::cluster_group cl = cg::this_cluster();
   const int nr = (int)cl.num_blocks();
   const long long warp = threadIdx.x >> 5;
+  // positions [0, head) (the start row's out-degree: the start's row comes first in the order)
+  // are computed by the Explore cluster before group 0, the rest by the workers
+  const long long head = min((long long)F.E, (long long)(__ldg(A.row_ptr + start + 1) - __ldg(A.row_ptr + start)));
   if ((int)blockIdx.x < nr) {
     // the run's initial state (root plan, control block), read by every CTA after the barrier
     // below; shared memory serves as the mask scratch first, explore_one initialises what it uses
     if (blockIdx.x == 0 && threadIdx.x == 0) explore_init_thread(A, start);
-    mask_positions(F, smem_raw, 0, F.head, (long long)blockIdx.x * kCW + warp, (long long)nr * kCW, false);
+    // position q to CTA q mod nr: the few prologue edges run on different SMs
+    mask_positions(F, smem_raw, 0, head, warp * nr + blockIdx.x, (long long)nr * kCW, false, 0, 0);
     cl.sync();
     CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
     uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
@@ -1258,8 +1302,8 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t
     if (blockIdx.x == 0) goal_finalize_block(A, A.group, F.goal_sorted);
     return;
   }
-  const long long wb = (long long)blockIdx.x - nr, nwb = (long long)gridDim.x - nr;
-  mask_positions(F, smem_raw, F.head, F.E, wb * kCW + warp, nwb * kCW, true);
+  const long long nwb = (long long)gridDim.x - nr;
+  mask_positions(F, smem_raw, head, F.E, 0, 0, true, A.epoch_m1, nwb * kCW);
 }
 
 // Row order of the fused form.  Shortest-path cost from the start over the graph's edges
@@ -1847,6 +1891,7 @@ int run_explore_fused(pump_graph* g, const ExploreArgs& A0, int nr, bool dsm, cu
   // them short
   if (g->rowcnt_dirty) {
     PUMP_CUDA_TRY(cudaMemsetAsync(g->rowcnt, 0, sizeof(uint32_t) * ((size_t)g->n + 1), s));
+    PUMP_CUDA_TRY(cudaMemsetAsync(g->wctr + 1, 0, sizeof(unsigned long long), s));
     g->fuse_epoch = 0;
     g->rowcnt_dirty = false;
   }
@@ -1863,7 +1908,8 @@ int run_explore_fused(pump_graph* g, const ExploreArgs& A0, int nr, bool dsm, cu
   const char* lim = getenv("PUMP_TEST_SPIN_LIMIT");
   if (lim && atoll(lim) > 0) A.spin_limit = atoll(lim);
   FuseArgs F;
-  F.xi = g->xi_t;
+  F.xp = g->xi_p;
+  F.wctr = g->wctr + 1;
   F.phi = g->phi;
   F.L = g->L;
   F.nom = g->nom;
@@ -1883,7 +1929,6 @@ int run_explore_fused(pump_graph* g, const ExploreArgs& A0, int nr, bool dsm, cu
   F.xi_smem = xi_smem ? 1 : 0;
   F.hold_row = hold ? atoi(hold) : -1;
   if (F.hold_row >= 0) g->rowcnt_dirty = true;  // that row's count stays short
-  F.head = (int32_t)std::min<int64_t>(g->E, (int64_t)nr * kCW);
   F.goal_sorted = g->ex.goal_sorted;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[2];

@@ -745,6 +745,22 @@ __global__ void k_transpose_xi(const float* __restrict__ xi, int N, int W, float
   xi_t[((size_t)k * 3 + a) * N + i] = make_float2(xi[2 * (size_t)q], xi[2 * (size_t)q + 1]);
 }
 
+// xi_t -> pair-major xi_p[((k * 3 + a) * npair + jp) * 32 + l] = (xi0 of particles 64 jp + l and
+// 64 jp + 32 + l, then their xi1; zeros past N).
+__global__ void k_pair_xi(const float2* __restrict__ xi_t, int N, int W, int npair, float4* xi_p) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)(W + 1) * 3 * npair * 32;
+  if (q >= total) return;
+  const int l = (int)(q & 31);
+  const long long r = q >> 5;
+  const int jp = (int)(r % npair);
+  const long long ka = r / npair;  // k * 3 + a
+  const int i0 = 64 * jp + l, i1 = i0 + 32;
+  const float2 x0 = i0 < N ? xi_t[ka * N + i0] : make_float2(0.f, 0.f);
+  const float2 x1 = i1 < N ? xi_t[ka * N + i1] : make_float2(0.f, 0.f);
+  xi_p[q] = make_float4(x0.x, x1.x, x0.y, x1.y);
+}
+
 __global__ void k_linf(float sigma, float* out) {
   double Phi[4], L[3], Linf[3];
   model_dev((double)sigma, 1.0, Phi, L, Linf);
@@ -930,6 +946,10 @@ int launch_node_flags(pump_graph* g, const int32_t* goal_dev, cudaStream_t s) {
 int launch_transpose_xi(pump_graph* g, const float* xi_dev, cudaStream_t s) {
   int total = g->N * (g->W + 1) * 3;
   k_transpose_xi<<<(total + kBlock - 1) / kBlock, kBlock, 0, s>>>(xi_dev, g->N, g->W, g->xi_t);
+  note_launch();
+  const int npair = (g->N / 32 + 1) / 2;
+  const long long ptot = (long long)(g->W + 1) * 3 * npair * 32;
+  k_pair_xi<<<(unsigned)((ptot + kBlock - 1) / kBlock), kBlock, 0, s>>>(g->xi_t, g->N, g->W, npair, g->xi_p);
   note_launch();
   PUMP_CUDA_TRY(cudaGetLastError());
   return PUMP_OK;

@@ -67,6 +67,12 @@ __device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigne
   return d;
 }
 
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // dev_init / dev_step for two particles at once (x, y: their normals' pairs).
 __device__ __forceinline__ void dev_init2(const unsigned long long* linf2, float2 x, float2 y, unsigned long long& d0,
                                           unsigned long long& d1) {
@@ -147,9 +153,98 @@ __device__ __forceinline__ void word_pass(const float2* __restrict__ xi, int N, 
   }
 }
 
+// Pair-major normals.  xi_p[((k * 3 + a) * npair + jp) * 32 + l] = (xi0 of particle 64 jp + l,
+// xi0 of particle 64 jp + 32 + l, xi1 of the first, xi1 of the second) for waypoint step k, axis
+// a: one 16-byte load gives a lane both halves of its particle pair (zeros past N).
+__host__ __device__ constexpr int pair_count(int w) { return (w + 1) / 2; }
+
+// NP pairs of mask words (pairs p0 .. p0 + NP - 1, i.e. words 2 p0 .. 2 (p0 + NP) - 1 below w):
+// lane l advances particles 64 jp + l and 64 jp + 32 + l in the two halves of packed FP32x2
+// registers (each half rounds exactly as the scalar dev_init / dev_step and the position add),
+// through waypoints 1..k_last, and tests the boxes left at each.  The words are the warp ballots
+// of each half.  The warp stops early once every lane's particles have hit.
+template <int NP>
+__device__ __forceinline__ void pair_pass(const float4* __restrict__ xp, int npair, const unsigned long long (&P2)[4],
+                                          const unsigned long long (&L2)[3], const unsigned long long (&I2)[3],
+                                          const float* __restrict__ nm, int k_last, bool narrow, const uint32_t* wm,
+                                          const int* my_cand, bool all, int nc, const float* boxes, int p0, int w,
+                                          int lane, uint32_t* out) {
+  unsigned long long d0[NP][3], d1[NP][3];
+  bool hit[NP][2];
+  const float4* xq = xp + (size_t)p0 * 32 + lane;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    hit[j][0] = hit[j][1] = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float4 x = xq[((size_t)a * npair + j) * 32];
+      const unsigned long long X0 = pk2(x.x, x.y), X1 = pk2(x.z, x.w);
+      d0[j][a] = mul2(I2[0], X0);
+      d1[j][a] = fma2(I2[1], X0, mul2(I2[2], X1));
+    }
+  }
+  for (int k = 1; k <= k_last; ++k) {
+    const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
+    const unsigned long long N2[3] = {pk2(n0, n0), pk2(n1, n1), pk2(n2, n2)};
+    const float4* xk = xq + (size_t)k * 3 * npair * 32;
+    float p[NP][2][3];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float4 x = xk[((size_t)a * npair + j) * 32];
+        const unsigned long long X0 = pk2(x.x, x.y), X1 = pk2(x.z, x.w);
+        const unsigned long long m0 = mul2(L2[0], X0);
+        const unsigned long long m1 = fma2(L2[1], X0, mul2(L2[2], X1));
+        const unsigned long long e0 = fma2(P2[0], d0[j][a], fma2(P2[1], d1[j][a], m0));
+        const unsigned long long e1 = fma2(P2[2], d0[j][a], fma2(P2[3], d1[j][a], m1));
+        d0[j][a] = e0;
+        d1[j][a] = e1;
+        upk2(add2(N2[a], e0), p[j][0][a], p[j][1][a]);
+      }
+    }
+    unsigned bits = narrow ? wm[k - 1] : 0u;
+    int c = 0;
+    for (;;) {
+      int o;
+      if (narrow) {
+        if (!bits) break;
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        o = my_cand[b];
+      } else {
+        if (c >= nc) break;
+        o = all ? c : my_cand[c];
+        ++c;
+      }
+      const float4 b0 = *reinterpret_cast<const float4*>(boxes + kBoxStride * o);      // lo x, y, z, hi x
+      const float2 b1 = *reinterpret_cast<const float2*>(boxes + kBoxStride * o + 4);  // hi y, z
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          hit[j][h] = hit[j][h] || (b0.x <= p[j][h][0] && p[j][h][0] <= b0.w && b0.y <= p[j][h][1] &&
+                                    p[j][h][1] <= b1.x && b0.z <= p[j][h][2] && p[j][h][2] <= b1.y);
+    }
+    bool done = true;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) done = done && hit[j][0] && hit[j][1];
+    if (__all_sync(0xffffffffu, done)) break;
+  }
+#pragma unroll
+  for (int j = 0; j < NP; ++j)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int word = 2 * (p0 + j) + h;
+      const unsigned bits = __ballot_sync(0xffffffffu, hit[j][h]);
+      if (lane == 0 && word < w) out[word] = bits;
+    }
+}
+
 // Stages the boxes in shared memory (kBoxStride floats per box) and, when given, the normals.
+template <typename T>
 __device__ __forceinline__ void stage(const float* __restrict__ boxes_g, int nb, float* boxes,
-                                      const float2* __restrict__ xi_g, float2* xi_s, int xi_n) {
+                                      const T* __restrict__ xi_g, T* xi_s, int xi_n) {
   for (int k = threadIdx.x; k < kBoxStride * nb; k += blockDim.x) {
     const int o = k / kBoxStride, c = k - o * kBoxStride;
     boxes[k] = c < 6 ? boxes_g[6 * o + c] : 0.f;
@@ -167,8 +262,8 @@ __device__ __forceinline__ void stage(const float* __restrict__ boxes_g, int nb,
 // then runs the recurrence once and its lanes stop testing when all of them have hit (up to
 // kMaxNW words side by side per pass: fewer live registers with 2).  my_cand (kCandCap ints) and
 // wm (kMaxWaypoints words) are the warp's shared-memory scratch.
-template <int kMaxNW = 4>
-__device__ __forceinline__ void edge_mask_one(long long e, const float2* __restrict__ xi, int N, int W,
+template <int kMaxNP = 2>
+__device__ __forceinline__ void edge_mask_one(long long e, const float4* __restrict__ xp, int N, int W,
                                               const float* __restrict__ phi, const float* __restrict__ Lg,
                                               const float* __restrict__ nom, const float (&linf)[3],
                                               const float* __restrict__ ibox_g, const unsigned int* __restrict__ dmax,
@@ -216,16 +311,18 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float2* __restr
   }
   const bool all = n_cand > kCandCap;
   const int nc = all ? nb : n_cand;
-  const float P[4] = {phi[4 * e], phi[4 * e + 1], phi[4 * e + 2], phi[4 * e + 3]};
-  const float L[3] = {Lg[3 * e], Lg[3 * e + 1], Lg[3 * e + 2]};
+  const float4 ph = *reinterpret_cast<const float4*>(phi + 4 * e);
+  const float l0 = Lg[3 * e], l1 = Lg[3 * e + 1], l2 = Lg[3 * e + 2];
+  const unsigned long long P2[4] = {pk2(ph.x, ph.x), pk2(ph.y, ph.y), pk2(ph.z, ph.z), pk2(ph.w, ph.w)};
+  const unsigned long long L2[3] = {pk2(l0, l0), pk2(l1, l1), pk2(l2, l2)};
+  const unsigned long long I2[3] = {pk2(linf[0], linf[0]), pk2(linf[1], linf[1]), pk2(linf[2], linf[2])};
+  const int npair = pair_count(w);
   uint32_t* out = mask + (size_t)e * w;
-  int w0 = 0;
-  if (kMaxNW >= 4)
-    for (; w0 + 4 <= w; w0 += 4)
-      word_pass<4>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
-  for (; w0 + 2 <= w; w0 += 2)
-    word_pass<2>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
-  if (w0 < w) word_pass<1>(xi, N, W, P, L, linf, nm, k_last, narrow, wm, my_cand, all, nc, boxes, w0, lane, out);
+  int p = 0;
+  if (kMaxNP >= 2)
+    for (; p + 2 <= npair; p += 2)
+      pair_pass<2>(xp, npair, P2, L2, I2, nm, k_last, narrow, wm, my_cand, all, nc, boxes, p, w, lane, out);
+  for (; p < npair; ++p) pair_pass<1>(xp, npair, P2, L2, I2, nm, k_last, narrow, wm, my_cand, all, nc, boxes, p, w, lane, out);
   __syncwarp();
 }
 

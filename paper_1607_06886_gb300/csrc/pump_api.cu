@@ -385,11 +385,14 @@ int pump_build_graph(const float* states, int32_t n, int32_t start_idx, const in
   g->valid = (uint8_t*)graph_alloc(g, (size_t)n, s);
   g->is_goal = (uint8_t*)graph_alloc(g, (size_t)n, s);
   g->xi_t = (float2*)graph_alloc(g, sizeof(float2) * (size_t)(W + 1) * 3 * N, s);
+  g->xi_p = (float4*)graph_alloc(g, sizeof(float4) * (size_t)(W + 1) * 3 * ((N / 32 + 1) / 2) * 32, s);
+  g->wctr = (unsigned long long*)graph_alloc(g, 2 * sizeof(unsigned long long), s);
   g->linf_dev = (float*)graph_alloc(g, sizeof(float) * 4, s);
   int32_t* goal_dev = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)n_goal, s);
   float* xi_raw = (float*)dev_alloc(sizeof(float) * (size_t)N * (W + 1) * 6, s);
   rc = PUMP_OK;
-  if (!g->states || !g->boxes || !g->valid || !g->is_goal || !g->xi_t || !g->linf_dev || !goal_dev || !xi_raw)
+  if (!g->states || !g->boxes || !g->valid || !g->is_goal || !g->xi_t || !g->xi_p || !g->wctr || !g->linf_dev ||
+      !goal_dev || !xi_raw)
     rc = PUMP_ERR_OOM;
   if (!rc) rc = stage(g->states, states, sizeof(float) * 6 * (size_t)n, s);
   if (!rc && n_boxes) rc = stage(g->boxes, boxes, sizeof(float) * 6 * (size_t)n_boxes, s);
@@ -513,6 +516,8 @@ int pump_plan(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t p
               void* stream) {
   if (!g || !out || check_plan_params(p) || !g->has_geometry) return PUMP_ERR_INVALID_ARG;
   if (path_cap < 0 || (path_cap > 0 && !path)) return PUMP_ERR_INVALID_ARG;
+  const bool no_wait = (p->flags & PUMP_NO_WAIT) != 0;
+  if (no_wait && !(p->flags & PUMP_EXPLORE_ONLY)) return PUMP_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int rc = make_events(g);
   if (rc) return rc;
@@ -539,6 +544,12 @@ int pump_plan(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t p
     if (rc) return rc;
     PUMP_CUDA_TRY(cudaEventRecord(g->ev[3], s));
     PUMP_CUDA_TRY(cudaEventSynchronize(g->ev[3]));
+  } else if (no_wait) {
+    // enqueued only: the counters are read by pump_plan_collect
+    r.status = PUMP_OK;
+    r.fused = fuse && g->last_fused ? 1 : 0;
+    *out = r;
+    return PUMP_OK;
   } else {
     // one wait for the control block and the events (a pinned copy does not block the host)
     PUMP_CUDA_TRY(cudaMemcpyAsync(g->ctl_host, g->ex.ctl, sizeof(ExploreCtl), cudaMemcpyDeviceToHost, s));
@@ -555,6 +566,24 @@ int pump_plan(pump_graph* g, const pump_plan_params* p, int32_t* path, int32_t p
   r.fused = fuse && g->last_fused ? 1 : 0;
   *out = r;
   return r.status == PUMP_ERR_INFEASIBLE ? PUMP_ERR_INFEASIBLE : PUMP_OK;
+}
+
+int pump_plan_collect(pump_graph* g, pump_plan_result* out, void* stream) {
+  if (!g || !out || !g->ex.ctl) return PUMP_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = make_events(g);
+  if (rc) return rc;
+  PUMP_CUDA_TRY(cudaMemcpyAsync(g->ctl_host, g->ex.ctl, sizeof(ExploreCtl), cudaMemcpyDeviceToHost, s));
+  PUMP_CUDA_TRY(cudaStreamSynchronize(s));
+  const ExploreCtl h = *g->ctl_host;
+  pump_plan_result r;
+  std::memset(&r, 0, sizeof(r));
+  r.chosen_plan = -1;
+  fill_explore_stats(g, h, &r);
+  r.status = h.status;
+  r.fused = g->last_fused ? 1 : 0;
+  *out = r;
+  return h.status;
 }
 
 int pump_certify(pump_graph* g, const int32_t* path, int32_t path_len, int32_t n_mc, int32_t substeps, uint64_t seed,

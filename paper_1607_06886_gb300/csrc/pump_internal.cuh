@@ -160,6 +160,9 @@ struct pump_graph {
   float* states = nullptr;   // n x 6
   float* boxes = nullptr;    // n_boxes x 6 (lo, hi)
   float2* xi_t = nullptr;    // [(W+1)][3][N] (xi0, xi1) pairs
+  float4* xi_p = nullptr;    // pair-major normals of the box masks (maskdev::pair_count)
+  unsigned long long* wctr = nullptr;  // edge counters of the mask passes: [0] stand-alone kernel
+                                       // (zeroed per launch), [1] fused workers (over runs)
   uint8_t* valid = nullptr;
   uint8_t* is_goal = nullptr;
   int32_t* row_ptr = nullptr;

@@ -18,7 +18,7 @@ from . import build as _build
 
 # status codes
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_INFEASIBLE = range(7)
-NO_EARLY_STOP, EXPLORE_ONLY, STEPWISE, EXPLORE_GRID = 1, 2, 4, 8
+NO_EARLY_STOP, EXPLORE_ONLY, STEPWISE, EXPLORE_GRID, NO_WAIT = 1, 2, 4, 8, 16
 GRAPH_HSMC, GRAPH_SEPARATE_MASKS = 1, 2
 
 EXPORT = {
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = False):
     L.pump_edge_masks.argtypes = [P, P]
     L.pump_explore.argtypes = [P, C.POINTER(PlanParams), f32, C.POINTER(PlanResult), P]
     L.pump_plan.argtypes = [P, C.POINTER(PlanParams), P, i32, C.POINTER(PlanResult), P]
+    L.pump_plan_collect.argtypes = [P, C.POINTER(PlanResult), P]
     L.pump_certify.argtypes = [P, P, i32, i32, i32, C.c_uint64, C.POINTER(i64), C.POINTER(C.c_double), P]
     L.pump_export.argtypes = [P, i32, P, C.c_size_t, C.POINTER(C.c_size_t)]
     L.pump_graph_destroy.argtypes = [P]
@@ -463,6 +464,15 @@ class Graph:
         d = res.as_dict()
         d["rc"] = rc
         d["path"] = path[:res.path_len].copy()
+        return d
+
+    def collect(self, stream: Optional[int] = None) -> Dict:
+        """pump_plan_collect: wait for the stream and read the last query's Explore counters (for
+        queries enqueued with NO_WAIT)."""
+        res = PlanResult()
+        rc = load().pump_plan_collect(self._h, C.byref(res), current_stream() if stream is None else stream)
+        d = res.as_dict()
+        d["rc"] = rc
         return d
 
     def certify(self, path, n_mc: int, substeps: int, seed: int, stream: Optional[int] = None):

@@ -46,6 +46,7 @@ def test_invalid_arguments_rejected_before_any_device_work():
     assert lib.pump_graph_build(None, 0, 0, None, 0, None, 0, None, None, None, ctypes.byref(out)) == pump.ERR_INVALID_ARG
     assert lib.pump_graph_from_csr(0, None, None, None, None, 32, 0, None, 0, None, ctypes.byref(out)) == pump.ERR_INVALID_ARG
     assert lib.pump_plan(None, None, None, 0, None, None) == pump.ERR_INVALID_ARG
+    assert lib.pump_plan_collect(None, None, None) == pump.ERR_INVALID_ARG
     assert lib.pump_explore(None, None, 1.0, None, None) == pump.ERR_INVALID_ARG
     assert lib.pump_edge_masks(None, None) == pump.ERR_INVALID_ARG
     n = ctypes.c_size_t()
@@ -78,7 +79,7 @@ def test_binding_constants_match_the_header():
              "ERR_CUDA": "PUMP_ERR_CUDA", "ERR_CAPACITY": "PUMP_ERR_CAPACITY", "ERR_TIMEOUT": "PUMP_ERR_TIMEOUT",
              "ERR_INFEASIBLE": "PUMP_ERR_INFEASIBLE", "NO_EARLY_STOP": "PUMP_NO_EARLY_STOP",
              "EXPLORE_ONLY": "PUMP_EXPLORE_ONLY", "STEPWISE": "PUMP_STEPWISE", "EXPLORE_GRID": "PUMP_EXPLORE_GRID",
-             "GRAPH_HSMC": "PUMP_GRAPH_HSMC", "GRAPH_SEPARATE_MASKS": "PUMP_GRAPH_SEPARATE_MASKS"}
+             "NO_WAIT": "PUMP_NO_WAIT", "GRAPH_HSMC": "PUMP_GRAPH_HSMC", "GRAPH_SEPARATE_MASKS": "PUMP_GRAPH_SEPARATE_MASKS"}
     for py, c in pairs.items():
         assert c in vals, c
         assert getattr(pump, py) == vals[c], (py, getattr(pump, py), vals[c])

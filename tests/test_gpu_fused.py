@@ -218,3 +218,31 @@ def test_separate_masks_flag():
     a = export_arena(Gs)
     for k in a1:
         np.testing.assert_array_equal(a[k], a1[k])
+
+
+def test_queries_enqueued_without_waiting_equal_a_synchronous_query():
+    """PUMP_NO_WAIT: explore-only queries enqueued back to back on one graph (fused and separate,
+    with an L2-sized buffer write between them on the same stream) leave the arena and counters of
+    a synchronous query; pump_plan_collect reads them."""
+    import torch
+    wl = workload("indoor_4k", 4, 2000)
+    G = gpu_graph(wl)
+    ref = G.plan(plan_params(wl, flags=pump.EXPLORE_ONLY))
+    a_ref = export_arena(G)
+    junk = torch.empty(1 << 26, dtype=torch.float32, device="cuda")
+    for fused in (1, 0):
+        with env(PUMP_FUSED_MASKS=fused):
+            for _ in range(5):
+                r = G.plan(plan_params(wl, flags=pump.EXPLORE_ONLY | pump.NO_WAIT))
+                assert r["rc"] == pump.OK and r["n_candidates"] == 0 and r["fused"] == fused
+                junk.zero_()
+        c = G.collect()
+        assert c["rc"] == pump.OK
+        for k in ("n_candidates", "n_plans", "n_kept", "n_iterations", "n_groups", "n_goal"):
+            assert c[k] == ref[k], k
+        a = export_arena(G)
+        for k in a_ref:
+            np.testing.assert_array_equal(a[k], a_ref[k])
+    bad = G.plan(plan_params(wl, flags=pump.NO_WAIT))  # no-wait needs explore-only
+    assert bad["rc"] == pump.ERR_INVALID_ARG
+    G.close()
