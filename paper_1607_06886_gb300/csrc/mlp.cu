@@ -12,19 +12,16 @@
 // Parameters live in one flat FP32 vector (per layer W (out x in, row-major) then b), with Adam's
 // moments and a BF16 copy beside it, so one launch updates every layer.
 //
-// GEMM.  C[M x N] = A[M x K] B[K x N] with BF16 operands given either K-major (a row of the
-// operand holds consecutive k) or M/N-major (consecutive m or n):
+// Products, all on the 5th-generation tensor cores (k_gemm_tc, tcgen05.mma with TMEM accumulators,
+// operands brought in by TMA tensor copies):
 //   forward   pre_l  = h_l W_l^T     A = h_l (K-major), B = W_l (K-major)
-//   backward  dh_l   = g_l W_l       A = g_l (K-major), B = W_l (N-major)
-//             dW_l   = g_l^T h_l     A = g_l (M-major), B = h_l (N-major), split over K (the batch)
-// so no operand is ever transposed in memory.  A 64 x 64 block tile, four warps of 32 x 32, K
-// steps of 32 staged by cp.async four buffers deep; fragments come from ldmatrix (.trans for the
-// M/N-major tiles) and feed mma.sync m16n8k16 (BF16 in, FP32 accumulate).  Tile rows are padded
-// (K-major 40 elements, M/N-major 72) so that every ldmatrix phase hits 32 distinct banks.  The
-// epilogue is fused: bias + ReLU to BF16, bias to FP32, ReLU-mask of the layer below to BF16, or
-// plain FP32 partial sums (split K; the blocks of the first N tile also sum the gradient's columns,
-// the bias gradient).  The weight-gradient partials of the S splits stay separate
-// and the Adam launch adds them in a fixed order, so a training step is deterministic.
+//   backward  dh_l   = g_l W_l       A = g_l (K-major), B = W_l^T (K-major copy kept by Adam)
+//             dW_l   = g_l^T h_l     A = g_l, B = h_l, both MN-major (consecutive m or n in memory),
+//                                    split over K (the batch); db_l from the same products
+// so no activation or gradient is ever transposed in memory.  The epilogues are fused: bias + ReLU
+// to BF16, bias to FP32, ReLU mask of the layer below to BF16, or plain FP32 partial sums (split K).
+// The weight-gradient partials of the S splits stay separate and the Adam launch adds them in a
+// fixed order, so a training step is deterministic.
 //
 // Device-side step counter.  ctl[0] counts the Adam steps taken; the batch assembly of step t
 // draws with t, the loss kernel advances the counter, and Adam corrects its moments with the new
@@ -48,19 +45,11 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int kBM = 64, kBN = 64, kBK = 32;
-constexpr int kKPad = kBK + 8;  // row length of a K-major tile (elements)
-constexpr int kMPad = kBM + 8;  // row length of an M- or N-major tile (elements)
-constexpr int kTileElems = kBM * kKPad;  // >= kBK * kMPad
-constexpr int kGemmThreads = 128;
-constexpr int kStages = 4;  // K steps of 32 in flight per block (cp.async groups)
 constexpr int kLatent = 8;
 constexpr int kOutUsed = 6;
-constexpr int kMaxSplit = 8;
+constexpr int kMaxSplit = 32;
 constexpr int kLossThreads = 256;
-constexpr int kLossBlocksMax = 64;
-
-static_assert(kBK * kMPad <= kTileElems, "tile buffer too small");
+constexpr int kLossBlocksMax = 1024;
 
 enum Epi : int {
   kEpiBiasRelu = 0,  // out_bf16 = bf16(relu(acc + bias))
@@ -86,168 +75,6 @@ struct GemmArgs {
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src),
-               "r"(pred ? 16 : 0));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int kN>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(kN));
-}
-
-__device__ __forceinline__ void ldsm4(uint32_t* r, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_addr(p)));
-}
-__device__ __forceinline__ void ldsm4t(uint32_t* r, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_addr(p)));
-}
-
-// Stage one K step of an operand into `t`: rows r0 .. r0+63 of R (M or N), k in [k0, k0+32)
-// clipped to [.., ke).  Out-of-range vectors are zero-filled (cp.async with source size 0 reads
-// nothing; the source address is then the operand's base).
-template <bool kKMajor>
-__device__ __forceinline__ void stage_tile(bf16* t, const bf16* X, int ld, int R, int r0, int k0, int ke, int tid) {
-#pragma unroll
-  for (int q = tid; q < kBM * kBK / 8; q += kGemmThreads) {
-    if (kKMajor) {
-      const int r = q >> 2, c = (q & 3) * 8;
-      const bool ok = r0 + r < R && k0 + c < ke;
-      cp_async16(t + r * kKPad + c, ok ? X + (size_t)(r0 + r) * ld + k0 + c : X, ok);
-    } else {
-      const int kr = q >> 3, c = (q & 7) * 8;
-      const bool ok = k0 + kr < ke && r0 + c < R;
-      cp_async16(t + kr * kMPad + c, ok ? X + (size_t)(k0 + kr) * ld + r0 + c : X, ok);
-    }
-  }
-}
-
-template <int kEpi, bool kAK, bool kBK_>
-__global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
-  __shared__ __align__(128) bf16 sA[kStages][kTileElems];
-  __shared__ __align__(128) bf16 sB[kStages][kTileElems];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-  const int kb = blockIdx.z * g.kchunk, ke = min(g.K, kb + g.kchunk);
-  const int nk = ke > kb ? (ke - kb + kBK - 1) / kBK : 0;
-  float acc[2][4][4];
-  float csum = 0.f;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
-
-  // prologue: the first kStages - 1 K steps in flight (one commit group each, empty past nk)
-#pragma unroll
-  for (int st = 0; st < kStages - 1; ++st) {
-    if (st < nk) {
-      stage_tile<kAK>(sA[st], g.A, g.lda, g.M, m0, kb + st * kBK, ke, tid);
-      stage_tile<kBK_>(sB[st], g.B, g.ldb, g.N, n0, kb + st * kBK, ke, tid);
-    }
-    cp_async_commit();
-  }
-  const int mi = lane >> 3, i8 = lane & 7;
-  for (int it = 0; it < nk; ++it) {
-    cp_async_wait<kStages - 2>();  // step it has landed
-    __syncthreads();               // ... for every thread; and step it - 1's buffer is free
-    {
-      const int nx = it + kStages - 1;
-      if (nx < nk) {
-        stage_tile<kAK>(sA[nx % kStages], g.A, g.lda, g.M, m0, kb + nx * kBK, ke, tid);
-        stage_tile<kBK_>(sB[nx % kStages], g.B, g.ldb, g.N, n0, kb + nx * kBK, ke, tid);
-      }
-      cp_async_commit();
-    }
-    const bf16* tA = sA[it % kStages];
-    const bf16* tB = sB[it % kStages];
-    if (kEpi == kEpiPartial && !kAK && g.colsum && blockIdx.x == 0) {
-      // column sums of the M-major A tile: thread t takes column t % 64, rows (t / 64) * 16 .. + 16
-      const int cm = tid & 63, k0r = (tid >> 6) * 16;
-#pragma unroll
-      for (int kr = 0; kr < 16; ++kr) csum += __bfloat162float(tA[(k0r + kr) * kMPad + cm]);
-    }
-#pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int mb = wm * 32 + i * 16;
-        if (kAK)
-          ldsm4(a[i], tA + (mb + (mi & 1) * 8 + i8) * kKPad + kk + (mi >> 1) * 8);
-        else
-          ldsm4t(a[i], tA + (kk + (mi >> 1) * 8 + i8) * kMPad + mb + (mi & 1) * 8);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; j += 2) {
-        const int nb = wn * 32 + j * 8;
-        uint32_t r[4];
-        if (kBK_)
-          ldsm4(r, tB + (nb + (mi >> 1) * 8 + i8) * kKPad + kk + (mi & 1) * 8);
-        else
-          ldsm4t(r, tB + (kk + (mi & 1) * 8 + i8) * kMPad + nb + (mi >> 1) * 8);
-        b[j][0] = r[0];
-        b[j][1] = r[1];
-        b[j + 1][0] = r[2];
-        b[j + 1][1] = r[3];
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};\n"
-              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
-    }
-  }
-
-  if (kEpi == kEpiPartial && !kAK && g.colsum && blockIdx.x == 0) {
-    __shared__ float cs[kGemmThreads];
-    cs[tid] = csum;
-    __syncthreads();
-    if (tid < 64 && m0 + tid < g.M) g.colsum[blockIdx.z * g.split_stride + m0 + tid] = cs[tid] + cs[tid + 64];
-  }
-  // accumulator (i, j): [0..1] row g, columns 2t, 2t+1; [2..3] row g + 8
-  const int gq = lane >> 2, tq = lane & 3;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = m0 + wm * 32 + i * 16 + gq + 8 * h;
-        const int c = n0 + wn * 32 + j * 8 + 2 * tq;
-        if (r >= g.M || c >= g.N) continue;
-        float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
-        const size_t o = (size_t)r * g.ldo + c;
-        if (kEpi == kEpiBiasRelu) {
-          v0 = fmaxf(v0 + g.bias[c], 0.f);
-          v1 = fmaxf(v1 + g.bias[c + 1], 0.f);
-          *reinterpret_cast<__nv_bfloat162*>(g.out_bf16 + o) = __floats2bfloat162_rn(v0, v1);
-        } else if (kEpi == kEpiBias) {
-          g.out_f32[o] = v0 + g.bias[c];
-          g.out_f32[o + 1] = v1 + g.bias[c + 1];
-        } else if (kEpi == kEpiMask) {
-          const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(g.mask + o);
-          v0 = __low2float(mk) > 0.f ? v0 : 0.f;
-          v1 = __high2float(mk) > 0.f ? v1 : 0.f;
-          *reinterpret_cast<__nv_bfloat162*>(g.out_bf16 + o) = __floats2bfloat162_rn(v0, v1);
-        } else {
-          float* out = g.out_f32 + blockIdx.z * g.split_stride;
-          out[o] = v0;
-          out[o + 1] = v1;
-        }
-      }
-}
-
 // ---------------------------------------------------------------------------------------------
 // GEMM on the 5th-generation tensor cores: C[M x N] = A[M x K] B[N x K]^T, both operands K-major
 // BF16, accumulator FP32 in tensor memory.  A block owns 128 rows (the accumulator's 128 TMEM
@@ -261,8 +88,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(const GemmArgs g) {
 // and refills the buffer once that one has fired; the last commit tells the epilogue that the
 // accumulator is complete.  Every mbarrier wait is bounded: on expiry the block records an error,
 // skips its epilogue and still frees its tensor memory.  The epilogue reads the accumulator with
-// tcgen05.ld (warp w: lanes 32w .. 32w + 31, 16 columns at a time) and applies the same fused
-// operations as the mma.sync kernel.
+// tcgen05.ld (warp w: lanes 32w .. 32w + 31, 16 columns at a time) and applies the fused
+// operations listed at the top of this file.
 constexpr int kTcM = 128, kTcNMax = 256, kTcK = 64, kTcStages = 4, kTcThreads = 128;
 constexpr int kTcStageBytes = (kTcM + kTcNMax) * kTcK * 2;  // 48 KB
 constexpr int kTcSmem = kTcStages * kTcStageBytes + 1024;   // + alignment
@@ -276,7 +103,17 @@ struct TcArgs {
   float* out_f32;
   int ldo;
   int* err;
+  // weight-gradient form (MN-major operands, kEpiPartial): split z covers k in [z kchunk,
+  // (z + 1) kchunk) (kchunk a multiple of kTcK) and writes out_f32 + z split_stride; blocks of the
+  // first N tile also write the split's column sums of A to colsum + z split_stride
+  int kchunk;
+  int64_t split_stride;
+  float* colsum;
 };
+
+constexpr int kTcMnBox = 64;          // M/N elements of one MN-major box (128 B rows)
+constexpr int kTcMnBoxBytes = kTcK * kTcMnBox * 2;  // 8 KB: 64 K rows of 128 B
+constexpr int kTcOnes = 16;           // extra accumulator columns of the column sums (N step)
 
 // Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzled layout: start
 // address, leading offset 16 B (not used by this layout), 8-row groups 1024 B apart, version 1,
@@ -284,6 +121,15 @@ struct TcArgs {
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Descriptor of an MN-major operand in the 128-byte swizzled layout: each box holds 64 K rows of
+// 64 M (or N) elements (128 B), so 8-row K groups are 1024 B apart (stride offset) and successive
+// 64-wide M/N blocks kTcMnBoxBytes apart (leading offset); a K = 16 step starts 16 rows (2048 B)
+// further on.
+__device__ __forceinline__ uint64_t tc_desc_mn(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(kTcMnBoxBytes >> 4) << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
@@ -316,22 +162,64 @@ __device__ __forceinline__ void tc_load(const CUtensorMap* tmA, const CUtensorMa
       : "memory");
 }
 
-template <int kEpi>
+// One K step of MN-major operands: A (M 128) as two 64-wide boxes, B as tileN / 64 boxes, each box
+// 64 K rows from k; the full mbarrier expects every box's bytes.
+__device__ __forceinline__ void tc_load_mn(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t sa, uint32_t sb,
+                                           uint32_t full, int m0, int n0, int k, int nbox_b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full), "r"(bytes) : "memory");
+#pragma unroll
+  for (int h = 0; h < kTcM / kTcMnBox; ++h)
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            sa + h * kTcMnBoxBytes),
+        "l"((uint64_t)tmA), "r"(m0 + h * kTcMnBox), "r"(k), "r"(full)
+        : "memory");
+  for (int j = 0; j < nbox_b; ++j)
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            sb + j * kTcMnBoxBytes),
+        "l"((uint64_t)tmB), "r"(n0 + j * kTcMnBox), "r"(k), "r"(full)
+        : "memory");
+}
+
+// kMN: the weight-gradient form, C = A^T B over the batch with A (K x M) and B (K x N) stored
+// MN-major (row k holds consecutive m or n): the TMA boxes are 64 K rows x 64 M/N elements, the
+// descriptors MN-major (tc_desc_mn) and the instruction descriptor transposes both operands.
+// Blocks of the first N tile append a 64-wide block of BF16 ones to their B tile and run the
+// products kTcOnes columns wider: accumulator column tileN then holds sum_k A[k][m] (the bias
+// gradient), summed by the same tensor-core products.
+template <int kEpi, bool kMN = false, int kSt = kTcStages>
 __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB, const TcArgs g) {
   extern __shared__ uint8_t tc_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], done;
+  __shared__ __align__(8) uint64_t full[kSt], empty[kSt], done;
   __shared__ int ok_all;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * g.tileN;
   const int nt = min(g.tileN, g.N - n0);
-  const int nk = (g.K + kTcK - 1) / kTcK;
-  const uint32_t bytes = (uint32_t)(kTcM + g.tileN) * kTcK * 2;
-  const uint32_t stage = (bytes + 1023) & ~1023u;  // buffer stride
+  // K range: the whole of K, or split blockIdx.z of the weight-gradient form
+  const int kb = kMN ? blockIdx.z * g.kchunk : 0;
+  const int ke = kMN ? min(g.K, kb + g.kchunk) : g.K;
+  const int nk = ke > kb ? (ke - kb + kTcK - 1) / kTcK : 0;
+  const bool sums = kMN && g.colsum != nullptr && blockIdx.x == 0;  // this block adds the ones block
+  const int nbox_b = g.tileN / kTcMnBox;
+  const uint32_t bytes = (uint32_t)(kTcM + g.tileN) * kTcK * 2;  // TMA bytes per K step
+  const uint32_t b_bytes = (uint32_t)(g.tileN + (kMN ? kTcMnBox : 0)) * kTcK * 2;
+  const uint32_t stage = ((uint32_t)kTcM * kTcK * 2 + b_bytes + 1023) & ~1023u;  // buffer stride
+  const int nmma = sums ? g.tileN + kTcOnes : g.tileN;  // N of the products (weight-gradient form)
+  if (kMN && sums) {
+    // the ones block after each buffer's B boxes (never written by the copies)
+    const uint32_t one2 = 0x3F803F80u;
+    for (int b = 0; b < kSt; ++b) {
+      uint32_t* o = reinterpret_cast<uint32_t*>(smem + b * stage + kTcM * kTcK * 2 + nbox_b * kTcMnBoxBytes);
+      for (int q = tid; q < kTcMnBoxBytes / 4; q += kTcThreads) o[q] = one2;
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // visible to the tensor cores
+  }
   if (tid == 0) {
-    for (int b = 0; b < kTcStages; ++b) {
+    for (int b = 0; b < kSt; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&full[b])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&empty[b])));
     }
@@ -349,18 +237,22 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(const __grid_constant__ 
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = tmem_base;
   if (tid == 0) {
-    // kind::f16: D F32, A and B BF16, both K-major, N = nt, M = 128
-    const uint32_t idesc =
-        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+    // kind::f16: D F32, A and B BF16, both K-major (or both MN-major: transpose bits 15, 16),
+    // N = nmma, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (kMN ? (1u << 15) | (1u << 16) : 0u) |
+                           ((uint32_t)((kMN ? nmma : nt) >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
     const uint32_t base = smem_addr(smem);
     bool ok = true;
-    for (int c = 0; c < kTcStages && c < nk; ++c) {
+    for (int c = 0; c < kSt && c < nk; ++c) {
       const uint32_t sa = base + c * stage;
-      tc_load(&tmA, &tmB, sa, sa + kTcM * kTcK * 2, smem_addr(&full[c]), m0, n0, c, bytes);
+      if (kMN)
+        tc_load_mn(&tmA, &tmB, sa, sa + kTcM * kTcK * 2, smem_addr(&full[c]), m0, n0, kb + c * kTcK, nbox_b, bytes);
+      else
+        tc_load(&tmA, &tmB, sa, sa + kTcM * kTcK * 2, smem_addr(&full[c]), m0, n0, c, bytes);
     }
     for (int c = 0; c < nk && ok; ++c) {
-      const int st = c % kTcStages;
-      const uint32_t ph = (uint32_t)((c / kTcStages) & 1);
+      const int st = c % kSt;
+      const uint32_t ph = (uint32_t)((c / kSt) & 1);
       if (!mbar_wait(smem_addr(&full[st]), ph)) {
         ok = false;
         break;
@@ -370,19 +262,24 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(const __grid_constant__ 
 #pragma unroll
       for (int kk = 0; kk < kTcK / 16; ++kk) {
         const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t da = kMN ? tc_desc_mn(a0 + kk * 2048) : tc_desc(a0 + kk * 32);
+        const uint64_t db = kMN ? tc_desc_mn(b0 + kk * 2048) : tc_desc(b0 + kk * 32);
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                 tmem),
-            "l"(tc_desc(a0 + kk * 32)), "l"(tc_desc(b0 + kk * 32)), "r"(idesc), "r"(acc));
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
           smem_addr(&empty[st])));
-      if (c + kTcStages < nk) {
+      if (c + kSt < nk) {
         if (!mbar_wait(smem_addr(&empty[st]), ph)) {
           ok = false;
           break;
         }
-        tc_load(&tmA, &tmB, a0, b0, smem_addr(&full[st]), m0, n0, c + kTcStages, bytes);
+        if (kMN)
+          tc_load_mn(&tmA, &tmB, a0, b0, smem_addr(&full[st]), m0, n0, kb + (c + kSt) * kTcK, nbox_b, bytes);
+        else
+          tc_load(&tmA, &tmB, a0, b0, smem_addr(&full[st]), m0, n0, c + kSt, bytes);
       }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_addr(&done)));
@@ -393,7 +290,49 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(const __grid_constant__ 
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-  if (ok_all) {
+  if (ok_all && kMN && nk == 0) {
+    // an empty split (K past the end): zero partials
+    const int r = m0 + warp * 32 + lane;
+    if (r < g.M) {
+      float* out = g.out_f32 + blockIdx.z * g.split_stride + (size_t)r * g.ldo + n0;
+      for (int c = 0; c < nt; ++c) out[c] = 0.f;
+      if (sums) g.colsum[blockIdx.z * g.split_stride + r] = 0.f;
+    }
+  } else if (ok_all && kMN) {
+    const int r = m0 + warp * 32 + lane;
+    float* out = g.out_f32 + blockIdx.z * g.split_stride + (size_t)r * g.ldo + n0;
+    for (int c00 = 0; c00 < nt; c00 += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+            "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c00));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+      if (r < g.M) {
+        if (c00 + 16 <= nt && (g.ldo & 3) == 0 && (n0 & 3) == 0) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4*>(out + c00 + j) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                                    __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c00 + j < nt) out[c00 + j] = __uint_as_float(v[j]);
+        }
+      }
+    }
+    if (sums) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+            "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)g.tileN));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+      if (r < g.M) g.colsum[blockIdx.z * g.split_stride + r] = __uint_as_float(v[0]);
+    }
+  } else if (ok_all) {
     const int r = m0 + warp * 32 + lane;
     for (int c00 = 0; c00 < nt; c00 += 32) {
       uint32_t vv[2][16];
@@ -522,14 +461,21 @@ __global__ void k_assemble(const float* __restrict__ feat, int F, int n_env, int
     if (r >= B) break;
     const float* f = feat + (size_t)e[rr] * F;
     bf16* xr = x + (size_t)r * d0;
-#pragma unroll 4
-    for (int c = lane; c < d0; c += 32) {
-      float v = 0.f;
-      if (c < F)
-        v = f[c];
-      else if (c < F + kLatent)
-        v = z[rr][c - F];
-      xr[c] = __float2bfloat16_rn(v);
+    // eight columns per lane, one 16-byte store (d0 is a multiple of 16)
+    for (int c0 = lane * 8; c0 < d0; c0 += 256) {
+      uint32_t pk[4];
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        float v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = c0 + j + h;
+          v[h] = c < F ? f[c] : (c < F + kLatent ? z[rr][c - F] : 0.f);
+        }
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
+        pk[j / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+      *reinterpret_cast<uint4*>(xr + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
   }
 }
@@ -556,8 +502,8 @@ struct LossArgs {
 // the point at fraction u = Phi(z_0) of the targets' polyline: a = u (n - 1),
 // i = min(floor(a), n - 2), y = y_i + (a - i)(y_{i+1} - y_i).  Writes g = bf16(d mean loss / d o)
 // (B x ld, zero past column 6) and, after a fixed-order reduction,
-// trace[ctl[0] - ctl[1]] = mean loss (the blocks' sums added in block order by the last block to
-// finish); then advances ctl[0].
+// trace[ctl[0] - ctl[1]] = mean loss (the blocks' sums added by the last block to finish in a fixed
+// order: thread t adds blocks t, t + 256, ..., then a tree over the threads); then advances ctl[0].
 __global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__ o, int B, int ld, float vmax,
                                                        const float* __restrict__ tg, const int32_t* __restrict__ ntg,
                                                        int T, const int32_t* __restrict__ env, const LossArgs la,
@@ -609,15 +555,28 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__
       }
     }
     local += loss;
-    for (int j = 0; j < ld; ++j) {
-      float gj = 0.f;
-      if (has && j < kOutUsed) {
-        const float th = tanhf(o[(size_t)r * ld + j]);
-        const float ds = (j < 3 ? 0.5f : vmax) * (1.f - th * th);
-        gj = 2.f * (s[j] - y[j]) * ds / (float)B;
+    // the row's gradient: the used columns, then zeros, eight BF16 per 16-byte store (ld is a
+    // multiple of 16)
+    uint32_t pk[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      float gv[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = j + h;
+        gv[h] = 0.f;
+        if (has && c < kOutUsed) {
+          const float th = tanhf(o[(size_t)r * ld + c]);
+          const float ds = (c < 3 ? 0.5f : vmax) * (1.f - th * th);
+          gv[h] = 2.f * (s[c] - y[c]) * ds / (float)B;
+        }
       }
-      gout[(size_t)r * ld + j] = __float2bfloat16_rn(gj);
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(gv[0], gv[1]);
+      pk[j / 2] = *reinterpret_cast<const uint32_t*>(&b2);
     }
+    uint4* gr = reinterpret_cast<uint4*>(gout + (size_t)r * ld);
+    gr[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    for (int q = 1; q < ld / 8; ++q) gr[q] = make_uint4(0u, 0u, 0u, 0u);
   }
   red[threadIdx.x] = local;
   __syncthreads();
@@ -632,14 +591,24 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last) {
+    // thread t adds blocks t, t + 256, ... in that order, then a fixed tree over the threads
     __threadfence();
-    float sum = 0.f;
-    for (int b = 0; b < (int)gridDim.x; ++b) sum += ((volatile float*)part)[b];
-    const int64_t idx = ctl[0] - ctl[1];
-    if (trace && idx >= 0 && idx < trace_cap) trace[idx] = sum / (float)B;
-    ctl[0] += 1;
-    *ticket = 0u;
+    float v = 0.f;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kLossThreads) v += ((volatile float*)part)[b];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kLossThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const float sum = red[0];
+      const int64_t idx = ctl[0] - ctl[1];
+      if (trace && idx >= 0 && idx < trace_cap) trace[idx] = sum / (float)B;
+      ctl[0] += 1;
+      *ticket = 0u;
+    }
   }
 }
 
@@ -830,16 +799,10 @@ int ensure_trace(pump_mlp* m, int n) {
   return PUMP_OK;
 }
 
-// Splits of the weight-gradient products over the batch.
-int n_splits(int B) { return std::max(1, std::min(kMaxSplit, B / 512)); }
-int split_chunk(int B, int S) { return ((B + S - 1) / S + kBK - 1) / kBK * kBK; }
-
-template <int kEpi, bool kAK, bool kBK_>
-void gemm(const GemmArgs& a, int splits, cudaStream_t s, int* launches) {
-  dim3 grid((a.N + kBN - 1) / kBN, (a.M + kBM - 1) / kBM, splits);
-  k_gemm<kEpi, kAK, kBK_><<<grid, kGemmThreads, 0, s>>>(a);
-  ++*launches;
-}
+// Splits of the weight-gradient products over the batch (256 rows or more each, at most
+// kMaxSplit), each a multiple of the tensor-core K step: small batches still spread over the SMs.
+int n_splits(int B) { return std::max(1, std::min(kMaxSplit, B / 256)); }
+int split_chunk(int B, int S) { return ((B + S - 1) / S + kTcK - 1) / kTcK * kTcK; }
 
 void note_err(pump_mlp* m, int rc) {
   if (rc && !m->host_err) m->host_err = rc;
@@ -868,6 +831,55 @@ int tensor_map(CUtensorMap* map, const bf16* X, int rows, int K, int box_rows) {
   return r == CUDA_SUCCESS ? PUMP_OK : PUMP_ERR_CUDA;
 }
 
+// Tensor map of an MN-major BF16 operand (K rows x MN, row stride MN): boxes of 64 MN elements
+// (128 B) x 64 K rows in the 128-byte swizzled layout.
+int tensor_map_mn(CUtensorMap* map, const bf16* X, int MN, int K) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !encode) {
+      encode = nullptr;
+      return PUMP_ERR_CUDA;
+    }
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)MN, (cuuint64_t)K};
+  const cuuint64_t strides[1] = {(cuuint64_t)MN * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcMnBox, (cuuint32_t)kTcK};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)X, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? PUMP_OK : PUMP_ERR_CUDA;
+}
+
+// Weight gradient on the tensor cores: C[M x N] = A^T B summed over K (the batch) in S splits of
+// `chunk` rows, A = g (K x M) and B = h (K x N) MN-major; partial z to of + z split_stride (row
+// stride ldo) and the column sums of A (the bias gradient) to colsum + z split_stride.  N tile 128.
+int gemm_tc_wgrad(pump_mlp* m, const bf16* A, const bf16* B, int M, int N, int K, int S, int chunk, float* of,
+                  int ldo, int64_t split_stride, float* colsum, cudaStream_t s, int* launches) {
+  constexpr int tileN = 128;
+  constexpr int stage = ((kTcM * kTcK * 2 + (tileN + kTcMnBox) * kTcK * 2) + 1023) & ~1023;
+  constexpr int smem = kTcStages * stage + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc<kEpiPartial, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  CUtensorMap ta, tb;
+  int rc = tensor_map_mn(&ta, A, M, K);
+  if (!rc) rc = tensor_map_mn(&tb, B, N, K);
+  if (rc) return rc;
+  int cols = 32;
+  while (cols < tileN + kTcOnes) cols <<= 1;
+  TcArgs a{M, N, K, tileN, cols, nullptr, nullptr, nullptr, of, ldo, m->tc_err, chunk, split_stride, colsum};
+  k_gemm_tc<kEpiPartial, true><<<dim3((N + tileN - 1) / tileN, (M + kTcM - 1) / kTcM, S), kTcThreads, smem, s>>>(
+      ta, tb, a);
+  ++*launches;
+  return PUMP_OK;
+}
+
 // Tensor-core GEMM (K-major A and B): N tile 256, 128 or 64, the widest that still gives about one
 // block per SM.
 template <int kEpi>
@@ -875,7 +887,8 @@ int gemm_tc(pump_mlp* m, const bf16* A, const bf16* B, int M, int N, int K, cons
             bf16* ob, float* of, int ldo, cudaStream_t s, int* launches) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc<kEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(k_gemm_tc<kEpi, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaFuncSetAttribute(k_gemm_tc<kEpi, false, kTcStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     attr = true;
   }
   const int mt = (M + kTcM - 1) / kTcM, sms = num_sms();
@@ -889,8 +902,14 @@ int gemm_tc(pump_mlp* m, const bf16* A, const bf16* B, int M, int N, int K, cons
   int cols = 32;
   while (cols < tileN) cols <<= 1;
   const int stage = ((kTcM + tileN) * kTcK * 2 + 1023) & ~1023;
-  TcArgs a{M, N, K, tileN, cols, bias, mask, ob, of, ldo, m->tc_err};
-  k_gemm_tc<kEpi><<<dim3((N + tileN - 1) / tileN, mt), kTcThreads, kTcStages * stage + 1024, s>>>(ta, tb, a);
+  TcArgs a{M, N, K, tileN, cols, bias, mask, ob, of, ldo, m->tc_err, 0, 0, nullptr};
+  // a short K (at most 8 steps) needs two buffers: then two blocks share an SM, one's epilogue
+  // beside the other's copies and products
+  if (K <= 8 * kTcK)
+    k_gemm_tc<kEpi, false, 2><<<dim3((N + tileN - 1) / tileN, mt), kTcThreads, 2 * stage + 1024, s>>>(ta, tb, a);
+  else
+    k_gemm_tc<kEpi, false, kTcStages><<<dim3((N + tileN - 1) / tileN, mt), kTcThreads, kTcStages * stage + 1024, s>>>(
+        ta, tb, a);
   ++*launches;
   return PUMP_OK;
 }
@@ -924,20 +943,9 @@ void backward(pump_mlp* m, int B, cudaStream_t s, int* launches) {
   bf16* gn = m->gB;
   for (int l = m->L - 1; l >= 0; --l) {
     const int in = m->dims[l], out = m->dims[l + 1];
-    GemmArgs w{};  // dW_l = g^T h_l, and db_l = column sums of g
-    w.A = g;
-    w.lda = out;
-    w.B = m->act[l];
-    w.ldb = in;
-    w.M = out;
-    w.N = in;
-    w.K = B;
-    w.kchunk = chunk;
-    w.out_f32 = m->part + m->offW[l];
-    w.ldo = in;
-    w.split_stride = m->P;
-    w.colsum = m->part + m->offb[l];
-    gemm<kEpiPartial, false, false>(w, S, s, launches);
+    // dW_l = g^T h_l and db_l = column sums of g, on the tensor cores (MN-major operands)
+    note_err(m, gemm_tc_wgrad(m, g, m->act[l], out, in, B, S, chunk, m->part + m->offW[l], in, m->P,
+                              m->part + m->offb[l], s, launches));
     if (l > 0) {
       // g_{l-1} = (g W_l) * [h_l > 0]: B operand W_l^T (in x out, K-major)
       note_err(m, gemm_tc<kEpiMask>(m, g, m->wbt + m->offW[l], B, in, out, nullptr, m->act[l], gn, nullptr, in, s,
