@@ -230,9 +230,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hsmc-seeds", type=int, default=8,
                     help="queries of the HSMC leg (CP-hat vs Monte Carlo for box and half-space masks); 0 skips it")
-    ap.add_argument("--serve-requests", type=int, default=150,
-                    help="requests of the served leg (Poisson arrivals, continuous batching); 0 skips it")
-    ap.add_argument("--serve-rate", default="50,200,500",
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the served leg per arrival rate (Poisson arrivals, continuous batching); 0 "
+                         "skips it")
+    ap.add_argument("--serve-rate", default="50,100,200,500",
                     help="arrival rates of the served leg (requests/s, comma-separated)")
     ap.add_argument("--learned-envs", type=int, default=10000,
                     help="training environments of the learned-proposal leg (plain PUMP solutions, then training "
@@ -450,28 +451,33 @@ def learned_measure(pump, args):
     (indoor scenes, U{10..32} boxes, 4000 uniform samples, N = 128, W = 10, CP 1 %) through the
     request server; the BF16 network trained on the certified plans' states with the device loop
     (batch 2048, Adam 1e-3, args.learned_steps steps) under both losses; then the paired held-out
-    evaluation (seeds 1,000,000 on): 4000 uniform samples against the same first 2000 + 2000
-    proposals.  Also the training step's time and tensor throughput."""
-    from paper_1607_06886_gb300 import proposal
+    evaluation (seeds 1,000,000 on): 4000 uniform samples against the same first uniform samples
+    plus proposals kept clear of the boxes, at the fraction chosen on validation environments (seeds
+    2,000,000 on) and at the configuration's 50 %.  Also the training step's time and tensor
+    throughput."""
+    from paper_1607_06886_gb300 import inputs, proposal
     peak = float(load_peaks()["bf16_tflops"])
     data = proposal.collect(list(range(args.learned_envs)))
-    held = list(range(1_000_000, 1_000_000 + args.learned_eval))
-    out = {"workload": f"proposal_indoor_4k_{args.learned_envs}env", "collect": data.stats}
+    held = list(range(proposal.HELDOUT_SEED0, proposal.HELDOUT_SEED0 + args.learned_eval))
+    val = list(range(proposal.VALIDATION_SEED0, proposal.VALIDATION_SEED0 + args.learned_eval))
+    ru = proposal.run_queries([inputs.proposal_workload(int(s), 4000) for s in held])
+    ru_val = proposal.run_queries([inputs.proposal_workload(int(s), 4000) for s in val])
+    out = {"workload": f"proposal_indoor_4k_{args.learned_envs}env", "collect": data.stats,
+           "clearance": proposal.CLEARANCE, "learned": proposal.LEARNED,
+           "selection": "clearance and learned fraction chosen on validation environments (seeds 2,000,000 on): "
+                        "success at least uniform, then the lowest median cost ratio"}
+    sig0 = [(r["rc"], r["cost"], r["n_candidates"]) for r in ru]
     for name, kind in (("path_indexed", proposal.PATH_INDEXED), ("wta", proposal.WTA)):
         m = proposal.make_model(0, kind)
         tr = proposal.train(m, data, args.learned_steps)
         tr.pop("trace")
         out[f"train_{name}"] = tr
-        ev = proposal.evaluate(m, held, raw=True)
-        ru = ev.pop("raw_uniform")
-        ev.pop("raw_mixed")
-        sig = [(r["rc"], r["cost"], r["n_candidates"]) for r in ru]
-        if "uniform_results" in out and out["uniform_results"] != sig:
-            bad = [i for i, (a, b) in enumerate(zip(out["uniform_results"], sig)) if a != b]
-            ev["uniform_arm_differs"] = {"queries": bad[:10], "first": [out["uniform_results"][bad[0]], sig[bad[0]]]}
-        out["uniform_results"] = sig
-        out[f"eval_{name}"] = ev
+        out[f"eval_{name}"] = proposal.evaluate(m, held, uniform=ru)
+        out[f"validation_{name}"] = proposal.evaluate(m, val, uniform=ru_val)
         if kind == proposal.PATH_INDEXED:
+            out["eval_path_indexed_half_learned"] = proposal.evaluate(m, held, n_learned=2000, uniform=ru)
+            out["eval_path_indexed_no_clearance"] = proposal.evaluate(m, held, n_learned=2000, uniform=ru,
+                                                                      clearance=0.0)
             perf = {}
             for B, steps in ((2048, 500), (32768, 50)):
                 m.train(B, 3, 1e-3, 0.1, 1)
@@ -484,7 +490,13 @@ def learned_measure(pump, args):
                                      note="one training step = draws + forward + loss + backward + Adam, replayed as "
                                           "a CUDA graph; host-timed over the replays (one sync)")
         m.close()
-    out.pop("uniform_results")
+    # the uniform arm planned again: the same results (each query is deterministic)
+    ru2 = proposal.run_queries([inputs.proposal_workload(int(s), 4000) for s in held])
+    sig1 = [(r["rc"], r["cost"], r["n_candidates"]) for r in ru2]
+    out["uniform_arm_repeat_equal"] = sig0 == sig1
+    if sig0 != sig1:
+        bad = [i for i, (a, b) in enumerate(zip(sig0, sig1)) if a != b]
+        out["uniform_arm_differs"] = {"queries": bad[:10], "first": [sig0[bad[0]], sig1[bad[0]]]}
     return out
 
 
@@ -587,9 +599,15 @@ def served_measure(pump, args, rank, ws, rate):
     keys = ("status", "chosen_plan", "cost", "mc_collisions", "n_candidates", "n_plans")
     same = all(all(a[k] == b[k] for k in keys) for a, b in zip(rc_, rs_))
     cands = sum(r["n_candidates"] for r in rc_)
+    errs = {}
+    for form, rs in (("continuous", rc_), ("sequential", rs_)):
+        for r in rs:
+            if r["rc"] not in (pump.OK, pump.ERR_INFEASIBLE):
+                errs[f"{form}: {pump.status_str(r['rc'])}"] = errs.get(f"{form}: {pump.status_str(r['rc'])}", 0) + 1
     return {"workload": f"served_{R}_at_{rate:g}rps", "requests": R, "arrival_rate_rps": rate,
             "continuous_batching": dict(cont, slots=8), "sequential_fifo": dict(seq, slots=1),
-            "p99_speedup": seq["p99_ms"] / cont["p99_ms"], "results_equal": bool(same), "partial_plans": cands,
+            "p99_speedup": seq["p99_ms"] / cont["p99_ms"], "results_equal": bool(same), "errors": errs,
+            "partial_plans": cands,
             "includes": "graph build from host arrays + masks + Explore + PlanSelection with MC + readback",
             "inputs": "seeded synthetic: samples U{1000..16000}, boxes U{5..50}, N in {64,128,256}, W=10, CP 1%"}
 

@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "pump_internal.cuh"
@@ -637,6 +638,28 @@ int ensure_table(pump_graph* g, int S, cudaStream_t s) {
 constexpr int kMcScanMax = PUMP_MC_SCAN_MAX;
 constexpr int kMcTwoLaneMax = PUMP_MC_TWO_LANE_MAX;
 
+// Dynamic shared memory ceiling of the Monte Carlo kernels, set once per device to the most any
+// query can ask for (every box and a full staged table).  The attribute belongs to the kernel,
+// not to a launch: a per-query value set by one host thread could lower the limit under another
+// thread's launch between its own set and launch (the request server plans queries on several
+// threads), and that launch would fail.
+constexpr size_t kMcSmemMax = sizeof(float) * 6 * (size_t)kMaxBoxes + sizeof(float) * kMcTableSmem;
+std::mutex g_mc_attr_mu;
+std::vector<int> g_mc_attr_dev;
+
+int mc_attributes() {
+  int dev = 0;
+  PUMP_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mc_attr_mu);
+  for (int d : g_mc_attr_dev)
+    if (d == dev) return PUMP_OK;
+  PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMcSmemMax));
+  PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_rollout<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMcSmemMax));
+  PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_rollout<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMcSmemMax));
+  g_mc_attr_dev.push_back(dev);
+  return PUMP_OK;
+}
+
 // Certify the plans of the current batch (n_cert read on the device from the state).
 // n_cert: the batch's plan count, known on the host (the device copy n_cert_dev holds the same).
 int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert, int n_mc, int S, uint64_t seed,
@@ -653,11 +676,12 @@ int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert, int n_mc, int
   // the form that measured fastest for this many plans: the warp scan while few rollouts are in
   // flight (one or two plans), then two and one lanes per rollout
   if (n_mc > 0 && n_cert > 0) {
+    const int rca = mc_attributes();
+    if (rca) return rca;
     const size_t smem_boxes = sizeof(float) * 6 * (size_t)std::max(g->n_boxes, 1);
     unsigned long long* counts = reinterpret_cast<unsigned long long*>(X.mc_count);
     const int form = PUMP_MC_FORM ? PUMP_MC_FORM : (n_cert <= kMcScanMax ? 1 : (n_cert <= kMcTwoLaneMax ? 2 : 3));
     if (form == 1) {
-      PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_boxes));
       k_mc_scan<<<num_sms() * 4, kMcScanThreads, smem_boxes, s>>>(n_cert_dev, X.mc_plen, X.mc_table, g->W, S,
                                                                   g->linf_dev, g->boxes, g->n_boxes, n_mc, seed, B,
                                                                   counts);
@@ -665,12 +689,10 @@ int mc_batch(pump_graph* g, const int32_t* n_cert_dev, int n_cert, int n_mc, int
       const size_t smem = smem_boxes + sizeof(float) * kMcTableSmem;
       if (form == 2) {
         const int bpp = (n_mc + kMcThreads / 2 - 1) / (kMcThreads / 2);
-        PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_rollout<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_mc_rollout<2><<<n_cert * bpp, kMcThreads, smem, s>>>(n_cert_dev, bpp, X.mc_plen, X.mc_table, g->W, S,
                                                                g->linf_dev, g->boxes, g->n_boxes, n_mc, seed, B, counts);
       } else {
         const int bpp = (n_mc + kMcThreads - 1) / kMcThreads;
-        PUMP_CUDA_TRY(cudaFuncSetAttribute(k_mc_rollout<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_mc_rollout<1><<<n_cert * bpp, kMcThreads, smem, s>>>(n_cert_dev, bpp, X.mc_plen, X.mc_table, g->W, S,
                                                                g->linf_dev, g->boxes, g->n_boxes, n_mc, seed, B, counts);
       }
