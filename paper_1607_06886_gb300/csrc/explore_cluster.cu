@@ -202,6 +202,24 @@ __device__ __forceinline__ void chunk(int64_t total, int r, int nr, int64_t* lo,
   *hi = min(total, *lo + per);
 }
 
+// Whether iteration k runs on state S (the loop's exit tests; every CTA decides alike).
+__device__ __forceinline__ bool iter_runs(const St& S, const ExploreArgs& A, int k) {
+  return !(S.status || S.stop || S.g == 0) && !(S.i >= A.max_iter || k >= A.max_iter);
+}
+
+// Thread 0: this CTA's share of iteration k (set where the previous state is final, so the cluster
+// barrier that follows publishes it and the loop needs no CTA barrier of its own).
+__device__ __forceinline__ void iter_setup(St& S, int k, int r, int nr) {
+  S.k = k;
+  S.ncand += S.C;
+  ++S.n_groups;
+  chunk(S.C, r, nr, &S.c0, &S.c1);
+  chunk(S.base - S.lo, r, nr, &S.a0, &S.a1);
+  S.a0 += S.lo;
+  S.a1 += S.lo;
+  S.big = (S.C + nr - 1) / nr > kCCap ? 1 : 0;
+}
+
 // Exclusive block scan over kCT threads; returns the prefix and writes the total.
 template <typename T>
 __device__ T cscan(T v, T* total) {
@@ -552,6 +570,67 @@ __device__ __forceinline__ int32_t old_eff_c(const ExploreArgs& A, const CSmem* 
 }
 
 // ---------------------------------------------------------------- phase B
+// Candidate jl of the CTA's chunk: dominance test, group index; keeps its counts.
+template <bool kDsm>
+__device__ __forceinline__ void filter_cand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl,
+                                            const St& S, int jl, bool fits, int32_t& surv, int32_t& minb, bool& keep,
+                                            int32_t& eff, int32_t& deg, bool& gstop) {
+  CCand q;
+  if (fits) {
+    q.x = sm->cx[jl];
+    q.pc = sm->cpc[jl];
+    q.cost = sm->ccost[jl];
+    q.dg = sm->cdg[jl];
+  } else {
+    q = cand_at_c(A, S.c0 + jl, S.g, &sm->werr);
+  }
+  keep = q.pc < A.kmax && !dominated_c<kDsm>(A, cl, mbl, q.x, q.pc, q.cost);
+  if (keep) {
+    eff = eff_new(sm, A, S.i, q.cost);
+    deg = (int32_t)(q.dg & ~kGoalBit);
+    ++surv;
+    minb = min(minb, eff);
+    gstop = (q.dg & kGoalBit) && q.pc < A.kmin;
+  }
+  if (fits) sm->ceff[jl] = eff;
+}
+
+// Older plan p (ids [a0, a1) of the CTA): open and undominated, and its group index; keeps its
+// counts and, when the range fits, its record for phase C.
+template <bool kDsm>
+__device__ __forceinline__ void filter_old(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl,
+                                           const St& S, int64_t p, int64_t a0, bool ofits, int32_t& minb,
+                                           int32_t& min_open, int32_t& eff, int32_t& pc, int32_t& deg, bool& goal) {
+  int32_t x = 0, r0 = 0;
+  float c = 0.f;
+  // the plan's row, goal flag and mask are loaded with its record, before the dominance test
+  // (distributed shared memory), so the two round trips overlap
+  const int32_t xp = ld32(A.head + p);
+  const int32_t r0p = A.row_ptr[xp], r1p = A.row_ptr[xp + 1];
+  const bool goalp = A.is_goal[xp] != 0;
+  const uint4 mp = (ofits && A.w <= 4) ? load_mask4(A.mask + (size_t)p * A.w, A.w) : make_uint4(0u, 0u, 0u, 0u);
+  eff = old_eff_c<kDsm>(A, sm, cl, mbl, p, S.i, &x, &c, &pc);
+  if (eff >= 0) {
+    r0 = r0p;
+    deg = r1p - r0p;
+    goal = goalp;
+    minb = min(minb, eff);
+    min_open = min(min_open, (int32_t)p);
+  }
+  if (ofits) {
+    const int o = (int)(p - a0);
+    sm->oeff[o] = eff;
+    if (eff >= 0) {
+      sm->ox[o] = x;
+      sm->ocost[o] = c;
+      sm->or0[o] = r0;
+      sm->odg[o] = (uint32_t)deg | (goal ? kGoalBit : 0u);
+      sm->opc[o] = (int16_t)pc;
+      if (A.w <= 4) sm->omask[o] = mp;
+    }
+  }
+}
+
 template <bool kDsm>
 __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl, const St& S) {
   const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
@@ -564,68 +643,83 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
   uint32_t done_seen = 0;
   const bool poll_done = A.done && threadIdx.x == 0 && !sm->rows_ready;
   if (poll_done) done_seen = *reinterpret_cast<const volatile uint32_t*>(A.done);
-  for (int t0 = 0; t0 < n; t0 += kCT) {
-    const int jl = t0 + threadIdx.x;
-    bool keep = false;
-    int32_t eff = -1, deg = 0;
-    bool gstop = false;
-    if (jl < n) {
-      CCand q;
-      if (fits) {
-        q.x = sm->cx[jl];
-        q.pc = sm->cpc[jl];
-        q.cost = sm->ccost[jl];
-        q.dg = sm->cdg[jl];
-      } else {
-        q = cand_at_c(A, c0 + jl, S.g, &sm->werr);
-      }
-      keep = q.pc < A.kmax && !dominated_c<kDsm>(A, cl, mbl, q.x, q.pc, q.cost);
-      if (keep) {
-        eff = eff_new(sm, A, S.i, q.cost);
-        deg = (int32_t)(q.dg & ~kGoalBit);
-        ++surv;
-        minb = min(minb, eff);
-        gstop = (q.dg & kGoalBit) && q.pc < A.kmin;
-      }
-      if (fits) sm->ceff[jl] = eff;
-    }
-    bucket_add(keep, eff - S.i - 1, deg, gstop, sm->pub.ncnt, sm->pub.ndeg, &sm->pub.stop);
-  }
+  // A cached chunk of two passes (kCT < n <= kCCap) loads both passes' dominance rows before
+  // testing either (one distributed-shared-memory round trip instead of two); the tests and the
+  // counts are the same as pass by pass.
+  const bool two = fits && n > kCT && A.kmax <= 4;
   const int64_t a0 = S.a0, a1 = S.a1;
   const bool ofits = a1 - a0 <= kOCap;
-  for (int64_t t0 = a0; t0 < a1; t0 += kCT) {
-    const int64_t p = t0 + threadIdx.x;
-    int32_t eff = -1, x = 0, pc = 0, deg = 0, r0 = 0;
-    bool goal = false;
-    float c = 0.f;
-    if (p < a1) {
-      // the plan's row, goal flag and mask are loaded with its record, before the dominance
-      // test (distributed shared memory), so the two round trips overlap
-      const int32_t xp = ld32(A.head + p);
-      const int32_t r0p = A.row_ptr[xp], r1p = A.row_ptr[xp + 1];
-      const bool goalp = A.is_goal[xp] != 0;
-      const uint4 mp = (ofits && A.w <= 4) ? load_mask4(A.mask + (size_t)p * A.w, A.w) : make_uint4(0u, 0u, 0u, 0u);
-      eff = old_eff_c<kDsm>(A, sm, cl, mbl, p, S.i, &x, &c, &pc);
-      if (eff >= 0) {
-        r0 = r0p;
-        deg = r1p - r0p;
-        goal = goalp;
+  // candidates and older plans in one pass when both fit it: disjoint threads, so their dependent
+  // load chains overlap (the counts are sums, independent of the order)
+  const bool merged = fits && !two && (int64_t)n + (a1 - a0) <= kCT;
+  if (merged) {
+    const int t = threadIdx.x;
+    bool keep = false, gstop = false, goal = false;
+    int32_t eff = -1, deg = 0, oeff = -1, opc = 0, odeg = 0;
+    if (t < n)
+      filter_cand<kDsm>(A, sm, mbl, cl, S, t, true, surv, minb, keep, eff, deg, gstop);
+    else if (t < n + (int)(a1 - a0))
+      filter_old<kDsm>(A, sm, mbl, cl, S, a0 + (t - n), a0, ofits, minb, min_open, oeff, opc, odeg, goal);
+    bucket_add(keep, eff - S.i - 1, deg, gstop, sm->pub.ncnt, sm->pub.ndeg, &sm->pub.stop);
+    bucket_add(oeff >= 0, oeff - S.i - 1, odeg, goal && opc < A.kmin, sm->pub.ocnt, sm->pub.odeg, &sm->pub.stop);
+  }
+  for (int t0 = 0; t0 < n && !merged; t0 += two ? 2 * kCT : kCT) {
+    const int jl = t0 + threadIdx.x, jl2 = jl + kCT;
+    bool keep = false, keep2 = false;
+    int32_t eff = -1, deg = 0, eff2 = -1, deg2 = 0;
+    bool gstop = false, gstop2 = false;
+    if (two) {
+      // rows of both candidates (popc < kmax <= 4: entries 0 .. popc of one 4-entry row)
+      const bool on1 = jl < n, on2 = jl2 < n;
+      const int32_t x1 = on1 ? sm->cx[jl] : 0, pc1 = on1 ? sm->cpc[jl] : A.kmax;
+      const int32_t x2 = on2 ? sm->cx[jl2] : 0, pc2 = on2 ? sm->cpc[jl2] : A.kmax;
+      const float cc1 = on1 ? sm->ccost[jl] : 0.f, cc2 = on2 ? sm->ccost[jl2] : 0.f;
+      const bool t1 = pc1 < A.kmax, t2 = pc2 < A.kmax;
+      uint32_t v1[4], v2[4];
+      const uint32_t* row1 = mb_row<kDsm>(A, cl, mbl, t1 ? x1 : 0);
+      const uint32_t* row2 = mb_row<kDsm>(A, cl, mbl, t2 ? x2 : 0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v1[j] = t1 && j <= pc1 ? mb_ld<kDsm>(row1 + j) : 0x7f800000u;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v2[j] = t2 && j <= pc2 ? mb_ld<kDsm>(row2 + j) : 0x7f800000u;
+      bool d1 = false, d2 = false;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        d1 = d1 || __uint_as_float(v1[j]) < cc1;
+        d2 = d2 || __uint_as_float(v2[j]) < cc2;
+      }
+      keep = t1 && !d1;
+      keep2 = t2 && !d2;
+      if (keep) {
+        const uint32_t dg = sm->cdg[jl];
+        eff = eff_new(sm, A, S.i, cc1);
+        deg = (int32_t)(dg & ~kGoalBit);
+        ++surv;
         minb = min(minb, eff);
-        min_open = min(min_open, (int32_t)p);
+        gstop = (dg & kGoalBit) && pc1 < A.kmin;
       }
-      if (ofits) {
-        const int o = (int)(p - a0);
-        sm->oeff[o] = eff;
-        if (eff >= 0) {
-          sm->ox[o] = x;
-          sm->ocost[o] = c;
-          sm->or0[o] = r0;
-          sm->odg[o] = (uint32_t)deg | (goal ? kGoalBit : 0u);
-          sm->opc[o] = (int16_t)pc;
-          if (A.w <= 4) sm->omask[o] = mp;
-        }
+      if (keep2) {
+        const uint32_t dg = sm->cdg[jl2];
+        eff2 = eff_new(sm, A, S.i, cc2);
+        deg2 = (int32_t)(dg & ~kGoalBit);
+        ++surv;
+        minb = min(minb, eff2);
+        gstop2 = (dg & kGoalBit) && pc2 < A.kmin;
       }
+      if (on1) sm->ceff[jl] = eff;
+      if (on2) sm->ceff[jl2] = eff2;
+      bucket_add(keep, eff - S.i - 1, deg, gstop, sm->pub.ncnt, sm->pub.ndeg, &sm->pub.stop);
+      bucket_add(keep2, eff2 - S.i - 1, deg2, gstop2, sm->pub.ncnt, sm->pub.ndeg, &sm->pub.stop);
+      continue;
     }
+    if (jl < n) filter_cand<kDsm>(A, sm, mbl, cl, S, jl, fits, surv, minb, keep, eff, deg, gstop);
+    bucket_add(keep, eff - S.i - 1, deg, gstop, sm->pub.ncnt, sm->pub.ndeg, &sm->pub.stop);
+  }
+  for (int64_t t0 = a0; t0 < a1 && !merged; t0 += kCT) {
+    const int64_t p = t0 + threadIdx.x;
+    int32_t eff = -1, pc = 0, deg = 0;
+    bool goal = false;
+    if (p < a1) filter_old<kDsm>(A, sm, mbl, cl, S, p, a0, ofits, minb, min_open, eff, pc, deg, goal);
     bucket_add(eff >= 0, eff - S.i - 1, deg, goal && pc < A.kmin, sm->pub.ocnt, sm->pub.odeg, &sm->pub.stop);
   }
   if (poll_done && done_seen == A.done_target) {
@@ -1042,7 +1136,8 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
   }
   const int32_t gn = has_next ? total_o + total_n : 0;
   if (r == 0 && threadIdx.x == 0) A.goff[gn] = Cn;
-  // next state (the same in every CTA of the cluster)
+  // next state (the same in every CTA of the cluster) and, if it runs, the next iteration's share;
+  // the cluster barrier after this phase publishes both
   __syncthreads();
   if (threadIdx.x == 0) {
     S.lo = min((int64_t)min_open, S.base);
@@ -1052,8 +1147,8 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
     S.i = has_next ? nbk : S.i + 1;
     S.stop = A.early_stop && stop_any ? 1 : 0;
     if (sm->b_err) S.status = PUMP_ERR_TIMEOUT;
+    if (iter_runs(S, A, S.k + 1)) iter_setup(S, S.k + 1, r, nr);
   }
-  __syncthreads();
 }
 
 // One Explore run by the whole cluster.  Starts and ends with a cluster barrier, so a cluster
@@ -1091,6 +1186,7 @@ __device__ void explore_one(const ExploreArgs& A, int32_t start, CSmem* sm, uint
     S.status = 0;
     S.n_groups = 0;
     S.k = 0;
+    if (iter_runs(S, A, 0)) iter_setup(S, 0, r, nr);
   }
   cl.sync();
   int k = 0;
@@ -1104,18 +1200,6 @@ __device__ void explore_one(const ExploreArgs& A, int32_t start, CSmem* sm, uint
       __syncthreads();
       break;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      S.k = k;
-      S.ncand += S.C;
-      ++S.n_groups;
-      chunk(S.C, r, nr, &S.c0, &S.c1);
-      chunk(S.base - S.lo, r, nr, &S.a0, &S.a1);
-      S.a0 += S.lo;
-      S.a1 += S.lo;
-      S.big = (S.C + nr - 1) / nr > kCCap ? 1 : 0;
-    }
-    __syncthreads();
     c_expand<kDsm>(A, sm, mbl, cl, S);
     cl.sync();
     c_filter<kDsm>(A, sm, mbl, cl, S);
@@ -1227,6 +1311,39 @@ __device__ __forceinline__ void mask_position(const FuseArgs& F, const float4* x
   if (lane == 0 && ex.y != F.hold_row) red_release_add(F.rowcnt + ex.y, 1u);
 }
 
+// Prologue of the fused launch (Explore cluster, before group 0): positions [0, head) of the order,
+// position q on CTA q mod nr, each of its word pairs on its own warp (half a warp's chain per
+// task for N = 128), every position counted toward its row after the CTA's tasks are done.
+__device__ __forceinline__ void mask_prologue(const FuseArgs& F, unsigned char* smem, long long head, int r, int nr) {
+  float* boxes = reinterpret_cast<float*>(smem);
+  int* cand = reinterpret_cast<int*>(boxes + maskdev::kBoxStride * F.nb);
+  uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kCW * maskdev::kCandCap);
+  float4* xp_s = reinterpret_cast<float4*>(smem + maskdev::fixed_smem(F.nb, kCW));
+  const int xp_n = (F.W + 1) * 3 * maskdev::pair_count(F.w) * 32;
+  maskdev::stage(F.boxes, F.nb, boxes, F.xp, F.xi_smem ? xp_s : nullptr, xp_n);
+  __syncthreads();
+  const float4* xp = F.xi_smem ? xp_s : F.xp;
+  const float linf[3] = {F.linf[0], F.linf[1], F.linf[2]};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* my_cand = cand + warp * maskdev::kCandCap;
+  uint32_t* wm = wmask_all + warp * kMaxWaypoints;
+  const int npair = maskdev::pair_count(F.w);
+  const long long mine = head > r ? (head - r + nr - 1) / nr : 0;  // positions r, r + nr, ... below head
+  for (long long t = warp; t < mine * npair; t += kCW) {
+    const long long q = r + (t / npair) * nr;
+    const int pr = (int)(t % npair);
+    const int2 ex = __ldg(F.eorder + q);
+    maskdev::edge_mask_one<PUMP_FUSED_MASK_NP>(ex.x, xp, F.N, F.W, F.phi, F.L, F.nom, linf, F.ibox, F.dmax, boxes,
+                                               F.nb, F.w, my_cand, wm, lane, F.emask, pr, pr + 1);
+  }
+  __syncthreads();
+  for (long long j = threadIdx.x; j < mine; j += kCT) {
+    const int2 ex = __ldg(F.eorder + r + j * nr);
+    __threadfence();
+    if (ex.y != F.hold_row) red_release_add(F.rowcnt + ex.y, 1u);
+  }
+}
+
 // The block stages the boxes (and the normals, when they fit) in shared memory.  Then either
 // positions q0 + v, q0 + v + V, ... below q1 (warp v of V; `dynamic` false), or, with `dynamic`,
 // chunks of kWorkChunk positions from [q0, q1) in increasing order from the run's counter: run e
@@ -1284,7 +1401,6 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t
   }
   cg::cluster_group cl = cg::this_cluster();
   const int nr = (int)cl.num_blocks();
-  const long long warp = threadIdx.x >> 5;
   // positions [0, head) (the start row's out-degree: the start's row comes first in the order)
   // are computed by the Explore cluster before group 0, the rest by the workers
   const long long head = min((long long)F.E, (long long)(__ldg(A.row_ptr + start + 1) - __ldg(A.row_ptr + start)));
@@ -1292,8 +1408,7 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t
     // the run's initial state (root plan, control block), read by every CTA after the barrier
     // below; shared memory serves as the mask scratch first, explore_one initialises what it uses
     if (blockIdx.x == 0 && threadIdx.x == 0) explore_init_thread(A, start);
-    // position q to CTA q mod nr: the few prologue edges run on different SMs
-    mask_positions(F, smem_raw, 0, head, warp * nr + blockIdx.x, (long long)nr * kCW, false, 0, 0);
+    mask_prologue(F, smem_raw, head, (int)blockIdx.x, nr);
     cl.sync();
     CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
     uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));

@@ -260,15 +260,16 @@ __device__ __forceinline__ void stage(const float* __restrict__ boxes_g, int nb,
 // largest |d0|, rounded the way the positions are), so only boxes meeting that box are tested
 // there, and the particles run only up to the last waypoint that has one.  Each 32-particle word
 // then runs the recurrence once and its lanes stop testing when all of them have hit (up to
-// kMaxNW words side by side per pass: fewer live registers with 2).  my_cand (kCandCap ints) and
-// wm (kMaxWaypoints words) are the warp's shared-memory scratch.
+// kMaxNP word pairs side by side per pass: fewer live registers with 1).  With [p_first, p_last)
+// only those word pairs are computed (an edge with no box left still gets all its words zeroed).
+// my_cand (kCandCap ints) and wm (kMaxWaypoints words) are the warp's shared-memory scratch.
 template <int kMaxNP = 2>
 __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restrict__ xp, int N, int W,
                                               const float* __restrict__ phi, const float* __restrict__ Lg,
                                               const float* __restrict__ nom, const float (&linf)[3],
                                               const float* __restrict__ ibox_g, const unsigned int* __restrict__ dmax,
                                               const float* boxes, int nb, int w, int* my_cand, uint32_t* wm, int lane,
-                                              uint32_t* __restrict__ mask) {
+                                              uint32_t* __restrict__ mask, int p_first = 0, int p_last = -1) {
   const float* ib = ibox_g + 6 * e;
   const float lo0 = ib[0], lo1 = ib[1], lo2 = ib[2], hi0 = ib[3], hi1 = ib[4], hi2 = ib[5];
   int n_cand = 0;
@@ -317,12 +318,13 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
   const unsigned long long L2[3] = {pk2(l0, l0), pk2(l1, l1), pk2(l2, l2)};
   const unsigned long long I2[3] = {pk2(linf[0], linf[0]), pk2(linf[1], linf[1]), pk2(linf[2], linf[2])};
   const int npair = pair_count(w);
+  const int pe = p_last < 0 ? npair : min(p_last, npair);
   uint32_t* out = mask + (size_t)e * w;
-  int p = 0;
+  int p = p_first;
   if (kMaxNP >= 2)
-    for (; p + 2 <= npair; p += 2)
+    for (; p + 2 <= pe; p += 2)
       pair_pass<2>(xp, npair, P2, L2, I2, nm, k_last, narrow, wm, my_cand, all, nc, boxes, p, w, lane, out);
-  for (; p < npair; ++p) pair_pass<1>(xp, npair, P2, L2, I2, nm, k_last, narrow, wm, my_cand, all, nc, boxes, p, w, lane, out);
+  for (; p < pe; ++p) pair_pass<1>(xp, npair, P2, L2, I2, nm, k_last, narrow, wm, my_cand, all, nc, boxes, p, w, lane, out);
   __syncwarp();
 }
 
