@@ -59,7 +59,7 @@ def assert_arena_equal(ga, ex, n_words):
 
 def compare_graphs(gg, og, radius):
     """Graph tier: identical node flags; identical edge sets except pairs whose oracle cost lies within
-    2 float ulps of r; edge values within a few float ulps.  Returns the number of edges whose values
+    2 float ulps of r; every edge value within 1 float ulp.  Returns the number of edges whose values
     are not bit-identical."""
     np.testing.assert_array_equal(gg["node_valid"], og["valid"])
     n = len(og["row_ptr"]) - 1
@@ -81,9 +81,13 @@ def compare_graphs(gg, og, radius):
     assert ulp_diff(gg["ecost"], og["ecost"]).max(initial=0) <= 1
     assert ulp_diff(gg["tau"], og["tau"]).max(initial=0) <= 1
     assert ulp_diff(gg["h"], og["h"]).max(initial=0) <= 1
-    assert ulp_diff(gg["phi"], og["phi"]).max(initial=0) <= 4
-    assert ulp_diff(gg["L"], og["L"]).max(initial=0) <= 8
-    assert ulp_diff(gg["nominal"], og["nom"]).max(initial=0) <= 2
+    # 1 ulp for every per-edge value (measured on one GB300 over 236,641 edges of four workloads:
+    # everything bit-identical except one L value, one ulp apart; the double arithmetic of the two
+    # sides differs in order and math library, so a value next to a float rounding midpoint can
+    # round the other way)
+    assert ulp_diff(gg["phi"], og["phi"]).max(initial=0) <= 1
+    assert ulp_diff(gg["L"], og["L"]).max(initial=0) <= 1
+    assert ulp_diff(gg["nominal"], og["nom"]).max(initial=0) <= 1
     assert ulp_diff(gg["linf"], og["linf"]).max(initial=0) <= 1
     E = len(og["col"])
     diff = np.zeros(E, bool)
