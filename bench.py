@@ -659,17 +659,51 @@ def batched_measure(pump, args, dev, flush, rank, ws):
     nbytes = sum(r["n_candidates"] * (12 + 4 * (G.counts()[4] // 32)) + r["n_plans"] * (28 + 4 * (G.counts()[4] // 32))
                  for r, G in zip(res, Gs))
     hbm = float(load_peaks()["hbm_gbs"])
+    # the mask pass against the ALU peak: lane-ops counted exactly on every 16th query, scaled to the
+    # batch by edges
+    import torch
+    edges = [int(G.counts()[1]) for G in Gs]
+    samp = list(range(0, nq, 16))
+    ops_s = sum(mask_lane_ops(Gs[k], wls[k].boxes)[0] for k in samp)
+    ops_mask = ops_s * sum(edges) / max(sum(edges[k] for k in samp), 1)
+    props = torch.cuda.get_device_properties(dev)
+    alu_peak = props.multi_processor_count * 128 * float(load_peaks().get("sm_max_mhz", 2070.0)) * 1e6
     out = {"workload": f"batch_{nq}", "queries": nq, "value": sum_over_ranks(cands, ws) / (ms / 1e3),
            "unit": "partial_plans/s", "ms_per_batch": ms, "ms_masks": ms_mask, "ms_explore": ms_expl,
            "partial_plans": cands, "plans": plans, "edges": int(sum(int(G.counts()[1]) for G in Gs)),
            "single_queries_ms": seq_ms, "speedup_vs_single_queries": seq_ms / ms, "results_equal_single": bool(same),
-           "launch": {"cluster_size": cfg.cluster_size, "mbest_global": cfg.mbest_global, "tuned_ms": rec.get("explore_ms")},
+           "launch": {"cluster_size": cfg.cluster_size, "mbest_global": cfg.mbest_global, "tuned_ms": rec.get("explore_ms"),
+                      "mask_pairs": cfg.mask_pairs, "mask_chunk": cfg.mask_chunk, "mask_tuned_ms": rec.get("mask_ms")},
            "explore_roofline": {"bound": "hbm", "achieved": nbytes / (ms_expl / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                                 "frac": nbytes / (ms_expl / 1e3) / 1e9 / hbm},
+           "mask_roofline": {"bound": "alu", "achieved": ops_mask / (ms_mask / 1e3) / 1e12, "peak": alu_peak / 1e12,
+                             "unit": "Tops/s", "frac": ops_mask / (ms_mask / 1e3) / alu_peak,
+                             "work": f"lane-ops counted on {len(samp)} of {nq} queries, scaled by edges",
+                             "peak_source": "SMs x 128 lanes x sm_max_mhz (derived)"},
            "inputs": "seeded synthetic: samples U{1000..8000}, boxes U{5..50}, N in {64,128,256}, W=10, CP 1%"}
     for G in Gs:
         G.close()
     return out
+
+
+def mask_lane_ops(G, boxes):
+    """Algorithmic lane-op work of one edge-mask pass over graph G: every edge tests its position
+    box against the O obstacles (6 comparisons each); an edge whose box meets k obstacles runs the
+    deviation recurrence and position of every particle and waypoint (3 axes x 8 float ops) and
+    tests those k obstacles (6 comparisons each, counted in full although a hit ends the scan).
+    Returns (lane-ops, live-edge flags)."""
+    cnt = G.counts()
+    E, N, W = int(cnt[1]), int(cnt[4]), int(cnt[5])
+    boxes = np.asarray(boxes, np.float32).reshape(-1, 6)
+    O = int(boxes.shape[0])
+    ib = G.export("edge_box")
+    ov = np.zeros(E, np.int64)
+    for o in range(O):
+        b = boxes[o]
+        ov += ((b[0] <= ib[:, 3]) & (ib[:, 0] <= b[3]) & (b[1] <= ib[:, 4]) & (ib[:, 1] <= b[4]) &
+               (b[2] <= ib[:, 5]) & (ib[:, 2] <= b[5])).astype(np.int64)
+    live = ov > 0
+    return float(E) * 6 * O + float(N) * W * float(np.sum(24 + 6 * ov[live])), live
 
 
 def roofline_measure(pump, G, prm, wl, dev, flush, steps, fused_ms=None):
@@ -709,16 +743,7 @@ def roofline_measure(pump, G, prm, wl, dev, flush, steps, fused_ms=None):
     # the O obstacles (6 comparisons each); an edge whose box meets k obstacles runs the deviation
     # recurrence and position for every particle and waypoint (3 axes x 8 float ops = 24) and tests
     # those k obstacles (6 comparisons each, counted in full although a hit ends the scan).
-    boxes = np.asarray(wl.boxes, np.float32).reshape(-1, 6)
-    O = int(boxes.shape[0])
-    ib = G.export("edge_box")
-    ov = np.zeros(E, np.int64)
-    for o in range(O):
-        b = boxes[o]
-        ov += ((b[0] <= ib[:, 3]) & (ib[:, 0] <= b[3]) & (b[1] <= ib[:, 4]) & (ib[:, 1] <= b[4]) &
-               (b[2] <= ib[:, 5]) & (ib[:, 2] <= b[5])).astype(np.int64)
-    live = ov > 0
-    ops_mask = float(E) * 6 * O + float(N) * W * float(np.sum(24 + 6 * ov[live]))
+    ops_mask, live = mask_lane_ops(G, wl.boxes)
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
     alu_peak = props.multi_processor_count * 128 * sm_mhz * 1e6  # lane-ops/s

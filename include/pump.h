@@ -262,13 +262,16 @@ int pump_plan_collect(pump_graph* g, pump_plan_result* out, void* stream);
  * and goal plans), except that ms_masks / ms_explore / ms_select are the
  * whole batch's phase times.  Each result equals the single-query result:
  * every query runs exactly the single-query algorithm, only concurrently.
- * `config` (may be NULL) chooses the form of the Explore launch:
+ * `config` (may be NULL) chooses the form of the Explore launch and of the
+ * edge-mask launches (results are the same in every form):
  */
 typedef struct {
   int32_t cluster_size; /* CTAs per query: 16, 8 or 4; 0 = the largest the device co-schedules */
   int32_t mbest_global; /* 1: dominance tables in global memory instead of on chip             */
   int32_t max_clusters; /* queries in flight at once; 0 = as many as fit on the device          */
-  int32_t reserved;     /* 0                                                                    */
+  int32_t mask_pairs;   /* particle block of the mask pass: mask-word pairs a warp advances side
+                           by side (1 or 2; 0 = 2)                                             */
+  int32_t mask_chunk;   /* edges a warp of the mask pass takes at a time (1 .. 64; 0 = 4)       */
 } pump_batch_config;
 /* Queries whose params set PUMP_EXPLORE_ONLY stop after Explore; the others
  * run PlanSelection one after another.  Synchronises.

@@ -1,10 +1,12 @@
 """Launch-form autotuner for the batched form (pump_plan_batch).
 
-For a batch it times the candidate forms of the Explore launch (CTAs per query, dominance table on
-chip or in global memory) on the batch itself, keeps the fastest, and remembers the choice in a
-JSON file keyed by the batch's shape: query count, particle counts, and sample-count and box-count
-buckets.  Later batches of the same shape reuse it without timing.  Every form gives the same
-results; only the time differs.
+For a batch it times, on the batch itself, the candidate forms of the Explore launch (the tile of
+a query: CTAs per query, dominance table on chip or in global memory) and then those of the
+edge-mask launches (the particle block: mask-word pairs a warp advances side by side, and the
+edges a warp takes at a time), keeps the fastest of each, and remembers the choice in a JSON file
+keyed by the batch's shape: query count, particle counts and sample-count bucket.  Later batches of
+the same shape reuse it without timing.  Every form gives the same results; only the time
+differs.
 
 The cache lives at $PUMP_TUNE_CACHE, else ~/.cache/pump_gb300/tune.json.
 """
@@ -18,6 +20,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 from . import pump
 
 CANDIDATES: Tuple[Tuple[int, int], ...] = ((16, 0), (16, 1), (8, 0), (8, 1), (4, 0))
+MASK_CANDIDATES: Tuple[Tuple[int, int], ...] = ((2, 4), (2, 1), (2, 16), (1, 4))  # (word pairs, edges per take)
 
 
 def cache_path() -> str:
@@ -59,41 +62,56 @@ def _store(d: Dict) -> None:
         pass
 
 
+def _timed(graphs, prm, cfg, reps: int, field: str) -> Optional[float]:
+    ms = []
+    for _ in range(reps + 1):
+        rc, res = pump.plan_batch(graphs, prm, cfg)
+        if rc not in (pump.OK, pump.ERR_INFEASIBLE):
+            return None
+        ms.append(res[0][field])
+    return min(ms[1:])
+
+
 def tune_batch(graphs: Sequence["pump.Graph"], params, reps: int = 2, force: bool = False,
-               candidates: Sequence[Tuple[int, int]] = CANDIDATES) -> Tuple["pump.BatchConfig", Dict]:
+               candidates: Sequence[Tuple[int, int]] = CANDIDATES,
+               mask_candidates: Sequence[Tuple[int, int]] = MASK_CANDIDATES) -> Tuple["pump.BatchConfig", Dict]:
     """Best BatchConfig for this batch shape (timed now unless cached).  Returns (config, record)
-    where the record holds the per-form Explore times in ms."""
+    where the record holds the per-form Explore and mask times in ms."""
     key = batch_key(graphs)
     cache = _load()
     if not force and key in cache:
         rec = cache[key]
-        return pump.BatchConfig(int(rec["cluster_size"]), int(rec["mbest_global"]), 0, 0), rec
+        return pump.BatchConfig(int(rec["cluster_size"]), int(rec["mbest_global"]), 0, int(rec.get("mask_pairs", 0)),
+                                int(rec.get("mask_chunk", 0))), rec
     if isinstance(params, pump.PlanParams):
         params = [params] * len(graphs)
     prm = []
-    for p in params:   # time Explore only
+    for p in params:   # time Explore and the masks only
         q = pump.PlanParams.from_buffer_copy(p)
         q.flags |= pump.EXPLORE_ONLY
         prm.append(q)
     times: Dict[str, float] = {}
     best, best_ms = None, math.inf
     for cs, mg in candidates:
-        cfg = pump.BatchConfig(cs, mg, 0, 0)
-        ms = []
-        for _ in range(reps + 1):
-            rc, res = pump.plan_batch(graphs, prm, cfg)
-            if rc not in (pump.OK, pump.ERR_INFEASIBLE):
-                break
-            ms.append(res[0]["ms_explore"])
-        if len(ms) < reps + 1:
+        t = _timed(graphs, prm, pump.BatchConfig(cs, mg, 0, 0, 0), reps, "ms_explore")
+        if t is None:
             continue
-        t = min(ms[1:])
         times[f"{cs}/{mg}"] = t
         if t < best_ms:
             best, best_ms = (cs, mg), t
     if best is None:
         best = (0, 0)
-    rec = {"cluster_size": best[0], "mbest_global": best[1], "explore_ms": times}
+    mtimes: Dict[str, float] = {}
+    mbest, mbest_ms = (0, 0), math.inf
+    for pairs, chunk in mask_candidates:
+        t = _timed(graphs, prm, pump.BatchConfig(best[0], best[1], 0, pairs, chunk), reps, "ms_masks")
+        if t is None:
+            continue
+        mtimes[f"{pairs}/{chunk}"] = t
+        if t < mbest_ms:
+            mbest, mbest_ms = (pairs, chunk), t
+    rec = {"cluster_size": best[0], "mbest_global": best[1], "explore_ms": times, "mask_pairs": mbest[0],
+           "mask_chunk": mbest[1], "mask_ms": mtimes}
     cache[key] = rec
     _store(cache)
-    return pump.BatchConfig(best[0], best[1], 0, 0), rec
+    return pump.BatchConfig(best[0], best[1], 0, mbest[0], mbest[1]), rec

@@ -145,15 +145,15 @@ __global__ void k_edge_ibox(const float* __restrict__ nom, const unsigned int* _
 #ifndef PUMP_MASK_MIN_BLOCKS
 #define PUMP_MASK_MIN_BLOCKS 3  // 85 registers: three 256-thread blocks per SM (packed pairs of words)
 #endif
-constexpr int kMaskChunk = 4;
-template <bool kSmemXi>
+constexpr int kMaskChunk = 4;  // default edges per take
+template <bool kSmemXi, int kNP = 2>
 __global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask(const float4* __restrict__ xp_g, int N, int W,
                                                            const float* __restrict__ phi, const float* __restrict__ Lg,
                                                            const float* __restrict__ nom, const float* __restrict__ linf_g,
                                                            const float* __restrict__ ibox_g,
                                                            const unsigned int* __restrict__ dmax,
                                                            const float* __restrict__ boxes_g, int nb, int E, int w,
-                                                           unsigned long long* __restrict__ ctr,
+                                                           unsigned long long* __restrict__ ctr, int chunk,
                                                            uint32_t* __restrict__ mask) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* boxes = reinterpret_cast<float*>(smem);  // kBoxStride floats per box (16-byte aligned rows)
@@ -170,12 +170,13 @@ __global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask
   uint32_t* wm = wmask_all + warp * kMaxWaypoints;
   for (;;) {
     unsigned long long t = 0;
-    if (lane == 0) t = atomicAdd(ctr, (unsigned long long)kMaskChunk);
+    if (lane == 0) t = atomicAdd(ctr, (unsigned long long)chunk);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= (unsigned long long)E) break;
-    const long long e1 = min((long long)E, (long long)t + kMaskChunk);
+    const long long e1 = min((long long)E, (long long)t + chunk);
     for (long long e = (long long)t; e < e1; ++e)
-      maskdev::edge_mask_one(e, xp, N, W, phi, Lg, nom, linf, ibox_g, dmax, boxes, nb, w, my_cand, wm, lane, mask);
+      maskdev::edge_mask_one<kNP>(e, xp, N, W, phi, Lg, nom, linf, ibox_g, dmax, boxes, nb, w, my_cand, wm, lane,
+                                  mask);
   }
 }
 
@@ -496,7 +497,21 @@ static int compute_edge_masks_hs(pump_graph* g, cudaStream_t s) {
   return PUMP_OK;
 }
 
-int compute_edge_masks(pump_graph* g, cudaStream_t s) {
+// Launch of the query pass with kNP word pairs per warp pass.
+template <bool kSmemXi, int kNP>
+static int launch_edge_mask(pump_graph* g, size_t smem, int chunk, cudaStream_t s) {
+  int grid = 1;
+  const int rco = occupancy_grid(k_edge_mask<kSmemXi, kNP>, smem, kWarps * (long long)chunk, g->E, &grid);
+  if (rco) return rco;
+  k_edge_mask<kSmemXi, kNP><<<grid, kWarps * 32, smem, s>>>(g->xi_p, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
+                                                            g->ibox, g->dmax, g->boxes, g->n_boxes, g->E,
+                                                            g->n_words, g->wctr, chunk, g->emask);
+  note_launch();
+  return PUMP_OK;
+}
+
+// pairs: word pairs per warp pass (1 or 2; 0 = 2); chunk: edges a warp takes at a time (0 = 4).
+int compute_edge_masks(pump_graph* g, cudaStream_t s, int pairs, int chunk) {
   if (g->E == 0) {
     g->masks_ready = true;
     return PUMP_OK;
@@ -505,27 +520,14 @@ int compute_edge_masks(pump_graph* g, cudaStream_t s) {
   const size_t smem_xi = edge_mask_smem(g->N, g->W, g->n_boxes, true);
   const bool use_smem = smem_xi <= 160 * 1024;
   const size_t smem = use_smem ? smem_xi : edge_mask_smem(g->N, g->W, g->n_boxes, false);
-  int grid = 1;
+  if (chunk <= 0) chunk = kMaskChunk;
   PUMP_CUDA_TRY(cudaMemsetAsync(g->wctr, 0, sizeof(unsigned long long), s));
-  if (use_smem) {
-    {
-      const int rco = occupancy_grid(k_edge_mask<true>, smem, kWarps * kMaskChunk, g->E, &grid);
-      if (rco) return rco;
-    }
-    k_edge_mask<true><<<grid, kWarps * 32, smem, s>>>(g->xi_p, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
-                                                      g->ibox, g->dmax, g->boxes, g->n_boxes, g->E, g->n_words,
-                                                      g->wctr, g->emask);
-    note_launch();
-  } else {
-    {
-      const int rco = occupancy_grid(k_edge_mask<false>, smem, kWarps * kMaskChunk, g->E, &grid);
-      if (rco) return rco;
-    }
-    k_edge_mask<false><<<grid, kWarps * 32, smem, s>>>(g->xi_p, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
-                                                       g->ibox, g->dmax, g->boxes, g->n_boxes, g->E, g->n_words,
-                                                       g->wctr, g->emask);
-    note_launch();
-  }
+  int rc;
+  if (pairs == 1)
+    rc = use_smem ? launch_edge_mask<true, 1>(g, smem, chunk, s) : launch_edge_mask<false, 1>(g, smem, chunk, s);
+  else
+    rc = use_smem ? launch_edge_mask<true, 2>(g, smem, chunk, s) : launch_edge_mask<false, 2>(g, smem, chunk, s);
+  if (rc) return rc;
   PUMP_CUDA_TRY(cudaGetLastError());
   g->masks_ready = true;
   return PUMP_OK;

@@ -222,7 +222,7 @@ int row_order_begin(pump_graph* g, cudaStream_t s, bool overlap);
 int row_order_end(pump_graph* g, cudaStream_t s);
 int build_halfspaces(pump_graph* g, cudaStream_t s);
 constexpr int kHsMax = 8;  // half-spaces per waypoint (HSMC)
-int compute_edge_masks(pump_graph* g, cudaStream_t s);
+int compute_edge_masks(pump_graph* g, cudaStream_t s, int pairs = 0, int chunk = 0);
 int compute_edge_bounds(pump_graph* g, cudaStream_t s);
 int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* stats,
                 cudaStream_t s, bool collect, bool masks_pending = false);
@@ -242,7 +242,6 @@ int prepare_explore_args(pump_graph* g, const pump_plan_params* p, float radius,
 int check_plan_params(const pump_plan_params* p);
 int make_events(pump_graph* g);
 void destroy_on_stream(pump_graph* g, cudaStream_t s);
-int compute_edge_masks(pump_graph* g, cudaStream_t s);
 // Explore kernel form from pump_plan_params.flags (see run_explore_kernels).
 inline int explore_mode(int32_t flags) {
   return (flags & PUMP_STEPWISE) ? 2 : ((flags & PUMP_EXPLORE_GRID) ? 1 : 0);

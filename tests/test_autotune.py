@@ -26,22 +26,27 @@ def test_tune_picks_fastest_and_caches(tmp_path, monkeypatch):
     timing = {(16, 0): 5.0, (16, 1): 4.0, (8, 0): 3.0, (8, 1): 3.5, (4, 0): 6.0}
     calls = []
 
+    mask_timing = {(2, 4): 7.0, (2, 1): 8.0, (2, 16): 6.5, (1, 4): 9.0}
+
     def fake_batch(graphs, params, cfg=None, stream=None):
         calls.append((cfg.cluster_size, cfg.mbest_global))
         assert all(p.flags & pump.EXPLORE_ONLY for p in params)
-        return pump.OK, [{"ms_explore": timing[(cfg.cluster_size, cfg.mbest_global)]} for _ in graphs]
+        mk = mask_timing.get((cfg.mask_pairs, cfg.mask_chunk), 10.0)
+        return pump.OK, [{"ms_explore": timing[(cfg.cluster_size, cfg.mbest_global)], "ms_masks": mk} for _ in graphs]
 
     monkeypatch.setattr(pump, "plan_batch", fake_batch)
     gs = [FakeGraph(2000, 128), FakeGraph(4000, 128)]
     prm = pump.default_plan_params(alpha=0.01)
     cfg, rec = autotune.tune_batch(gs, prm, reps=1)
     assert (cfg.cluster_size, cfg.mbest_global) == (8, 0)
+    assert (cfg.mask_pairs, cfg.mask_chunk) == (2, 16)  # the mask form, timed with the chosen Explore form
+    assert rec["mask_ms"]["1/4"] == 9.0
     assert prm.flags & pump.EXPLORE_ONLY == 0          # caller's params untouched
     stored = json.loads((tmp_path / "tune.json").read_text())
     assert stored[autotune.batch_key(gs)]["cluster_size"] == 8
     n_calls = len(calls)
     cfg2, _ = autotune.tune_batch(gs, prm, reps=1)     # cached: no timing
-    assert len(calls) == n_calls and cfg2.cluster_size == 8
+    assert len(calls) == n_calls and cfg2.cluster_size == 8 and (cfg2.mask_pairs, cfg2.mask_chunk) == (2, 16)
 
 
 def test_tune_skips_failing_forms(tmp_path, monkeypatch):
@@ -50,7 +55,7 @@ def test_tune_skips_failing_forms(tmp_path, monkeypatch):
     def fake_batch(graphs, params, cfg=None, stream=None):
         if cfg.cluster_size == 16:
             return pump.ERR_CUDA, []
-        return pump.OK, [{"ms_explore": float(cfg.cluster_size + cfg.mbest_global)} for _ in graphs]
+        return pump.OK, [{"ms_explore": float(cfg.cluster_size + cfg.mbest_global), "ms_masks": 1.0} for _ in graphs]
 
     monkeypatch.setattr(pump, "plan_batch", fake_batch)
     cfg, rec = autotune.tune_batch([FakeGraph(1000, 32)], pump.default_plan_params(alpha=0.05), reps=1)

@@ -2,8 +2,8 @@
 the single-query result (pump_plan on the same graph) bit for bit: counters, the whole plan arena,
 P_goal, the selected plan and its Monte Carlo count.  One batch is also checked against the CPU
 oracle directly.  Covers the launch forms (cluster sizes 16, 8, 4; dominance table on chip and in
-global memory; fewer clusters than queries), explore-only queries mixed with full ones, and the
-argument checks."""
+global memory; fewer clusters than queries; mask passes of one or two word pairs and 1 to 64
+edges per take), explore-only queries mixed with full ones, and the argument checks."""
 import numpy as np
 import pytest
 
@@ -52,9 +52,12 @@ def check_same(ref, ref_arena, res, G):
         np.testing.assert_array_equal(arena[k], v, err_msg=k)
 
 
-@pytest.mark.parametrize("cfg", [None, (16, 0, 0), (8, 0, 0), (4, 0, 2), (16, 1, 0), (8, 1, 3)])
+@pytest.mark.parametrize("cfg", [None, (16, 0, 0, 0, 0), (8, 0, 0, 1, 1), (4, 0, 2, 2, 16), (16, 1, 0, 1, 64),
+                                 (8, 1, 3, 2, 3)])
 def test_batch_equals_single_queries(queries, cfg):
-    config = None if cfg is None else pump.BatchConfig(cfg[0], cfg[1], cfg[2], 0)
+    """Every launch form (Explore: CTAs per query, table placement, clusters in flight; masks: word
+    pairs per warp pass, edges per take) gives the single-query results."""
+    config = None if cfg is None else pump.BatchConfig(*cfg)
     rc, res = pump.plan_batch([q[1] for q in queries], [q[2] for q in queries], config)
     assert rc in (pump.OK, pump.ERR_INFEASIBLE)
     for (wl, G, prm, ref, ref_arena), r in zip(queries, res):
@@ -98,7 +101,7 @@ def test_batch_matches_oracle():
 
 def test_batch_single_query_and_many_clusters(queries):
     wl, G, prm, ref, ref_arena = queries[1]
-    rc, res = pump.plan_batch([G], [prm], pump.BatchConfig(0, 0, 64, 0))
+    rc, res = pump.plan_batch([G], [prm], pump.BatchConfig(0, 0, 64, 0, 0))
     check_same(ref, ref_arena, res[0], G)
 
 
@@ -107,7 +110,8 @@ def test_batch_rejects_bad_arguments(queries):
     p0 = queries[0][2]
     rc, _ = pump.plan_batch([G0, G0], [p0, p0])
     assert rc == pump.ERR_INVALID_ARG
-    for bad in [(3, 0, 0, 0), (32, 0, 0, 0), (0, 2, 0, 0), (0, 0, -1, 0), (0, 0, 0, 1)]:
+    for bad in [(3, 0, 0, 0, 0), (32, 0, 0, 0, 0), (0, 2, 0, 0, 0), (0, 0, -1, 0, 0), (0, 0, 0, 3, 0),
+                (0, 0, 0, -1, 0), (0, 0, 0, 0, 65), (0, 0, 0, 0, -2)]:
         rc, _ = pump.plan_batch([G0, G1], [p0, queries[1][2]], pump.BatchConfig(*bad))
         assert rc == pump.ERR_INVALID_ARG, bad
     g = inputs.random_explore_graph(20, 3, 32, 0)
