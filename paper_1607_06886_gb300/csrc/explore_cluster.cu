@@ -309,6 +309,24 @@ __device__ __forceinline__ uint32_t* mb_row(const ExploreArgs& A, cg::cluster_gr
   return A.mbest + (size_t)x * A.kstride;
 }
 
+// mbest[x][k] = min(mbest[x][k], v) without waiting for the old value: a cluster-scope reduction
+// into the owning CTA's shared memory (or a global one).  The cluster barrier closing phase A
+// orders every reduction before phase B reads the table.
+template <bool kDsm>
+__device__ __forceinline__ void mb_min(const ExploreArgs& A, cg::cluster_group& cl, uint32_t* mbl, int32_t x, int k,
+                                       uint32_t v) {
+  if (kDsm) {
+    const unsigned nr = cl.num_blocks();
+    const uint32_t local = (uint32_t)__cvta_generic_to_shared(mbl + (size_t)(x / (int)nr) * A.kstride + k);
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"((unsigned)(x % (int)nr)));
+    asm volatile("red.relaxed.cluster.shared::cluster.min.u32 [%0], %1;" ::"r"(remote), "r"(v) : "memory");
+  } else {
+    asm volatile("red.relaxed.gpu.global.min.u32 [%0], %1;" ::"l"(A.mbest + (size_t)x * A.kstride + k), "r"(v)
+                 : "memory");
+  }
+}
+
 template <bool kDsm>
 __device__ __forceinline__ uint32_t mb_ld(const uint32_t* p) {
   if (kDsm) return *reinterpret_cast<const volatile uint32_t*>(p);
@@ -498,6 +516,45 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
         pmv.z = __shfl_sync(0xffffffffu, pmw, 2);
         pmv.w = __shfl_sync(0xffffffffu, pmw, 3);
       }
+      // w <= 4: two candidates per lane per round, both edges' targets and masks loaded before
+      // either is used (their L2 round trips overlap)
+      if (w <= 4) {
+        auto em_load = [&](int32_t e) -> uint4 {
+          if (w == 4) return __ldcg(reinterpret_cast<const uint4*>(A.emask) + e);
+          const uint32_t* ep = A.emask + (size_t)e * w;
+          return make_uint4(ldu(ep), w > 1 ? ldu(ep + 1) : 0u, w > 2 ? ldu(ep + 2) : 0u, 0u);
+        };
+        auto put = [&](int64_t c, int32_t e, const int4& t, const uint4& em) {
+          const float cost = __fadd_rn(pcost, __int_as_float(t.y));
+          const int jl = (int)(c - c0);
+          const uint4 m = make_uint4(pmv.x | em.x, pmv.y | em.y, pmv.z | em.z, pmv.w | em.w);
+          const int pc = __popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w);
+          sm->cmask[jl] = m;
+          sm->cx[jl] = t.x;
+          sm->cpar[jl] = p;
+          sm->cedge[jl] = e;
+          sm->ccost[jl] = cost;
+          sm->cpc[jl] = (int16_t)pc;
+          sm->cr0[jl] = t.z;
+          sm->cdg[jl] = (uint32_t)t.w;
+          if (pc < A.kmax) {
+            mb_min<kDsm>(A, cl, mbl, t.x, pc, __float_as_uint(cost));
+            ++kept;
+          }
+        };
+        for (int64_t c = lo + lane; c < hi; c += 64) {
+          const int64_t c2 = c + 32;
+          const bool two = c2 < hi;
+          const int32_t e = r0 + (int32_t)(c - lo_s), e2 = r0 + (int32_t)(c2 - lo_s);
+          const int4 t = edge_target(A, e);
+          const int4 t2 = two ? edge_target(A, e2) : make_int4(0, 0, 0, 0);
+          const uint4 em = em_load(e);
+          const uint4 em2 = two ? em_load(e2) : make_uint4(0u, 0u, 0u, 0u);
+          put(c, e, t, em);
+          if (two) put(c2, e2, t2, em2);
+        }
+        continue;
+      }
       for (int64_t c = lo + lane; c < hi; c += 32) {
         const int32_t e = r0 + (int32_t)(c - lo_s);
         const int4 t = edge_target(A, e);
@@ -530,7 +587,7 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
         sm->cr0[jl] = t.z;
         sm->cdg[jl] = (uint32_t)t.w;
         if (pc < A.kmax) {
-          atomicMin(mb_row<kDsm>(A, cl, mbl, t.x) + pc, __float_as_uint(cost));
+          mb_min<kDsm>(A, cl, mbl, t.x, pc, __float_as_uint(cost));
           ++kept;
         }
       }
@@ -539,7 +596,7 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
     for (int64_t c = c0 + threadIdx.x; c < c1; c += kCT) {
       const CCand q = cand_at_c(A, c, S.g, &sm->werr);
       if (q.pc < A.kmax) {
-        atomicMin(mb_row<kDsm>(A, cl, mbl, q.x) + q.pc, __float_as_uint(q.cost));
+        mb_min<kDsm>(A, cl, mbl, q.x, q.pc, __float_as_uint(q.cost));
         ++kept;
       }
     }
