@@ -249,6 +249,46 @@ __device__ T cscan(T v, T* total) {
   return pre;
 }
 
+// Two exclusive block scans in one shared-memory round: warp 0 scans the warp totals of the
+// first values, warp 1 those of the second.  Returns the first prefix; *pb is the second.
+static_assert(kCW >= 2, "two warps scan the warp totals");
+template <typename T>
+__device__ T cscan2(T a, T b, T* ta, T* tb, T* pb) {
+  __shared__ T ws2[2][kCW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x = a, y = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T u = __shfl_up_sync(0xffffffffu, x, o);
+    const T w = __shfl_up_sync(0xffffffffu, y, o);
+    if (lane >= o) {
+      x += u;
+      y += w;
+    }
+  }
+  if (lane == 31) {
+    ws2[0][warp] = x;
+    ws2[1][warp] = y;
+  }
+  __syncthreads();
+  if (warp < 2) {
+    T s = lane < kCW ? ws2[warp][lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T u = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += u;
+    }
+    if (lane < kCW) ws2[warp][lane] = s;
+  }
+  __syncthreads();
+  const T pa = (warp > 0 ? ws2[0][warp - 1] : T(0)) + x - a;
+  *pb = (warp > 0 ? ws2[1][warp - 1] : T(0)) + y - b;
+  *ta = ws2[0][kCW - 1];
+  *tb = ws2[1][kCW - 1];
+  __syncthreads();
+  return pa;
+}
+
 // Block sum and two minima in one shared-memory round.
 __device__ void creduce(int32_t& sum, int32_t& mn, int32_t& mn2) {
   __shared__ int32_t s_sum[kCW], s_mn[kCW], s_mn2[kCW];
@@ -918,6 +958,51 @@ __device__ __forceinline__ void send_member(CSmem* sm, cg::cluster_group& cl, in
   }
 }
 
+// Arena record of survivor q at id; its mask from the candidate cache (slot jl) when the chunk is
+// cached and w <= 4, else the parent's mask OR the edge's.  Returns the mask words (w <= 4).
+__device__ __forceinline__ uint4 put_survivor(const ExploreArgs& A, CSmem* sm, int64_t id, const CCand& q, int jl,
+                                              bool cached, int32_t i) {
+  A.head[id] = q.x;
+  A.parent[id] = q.parent;
+  A.pedge[id] = q.edge;
+  A.cost[id] = q.cost;
+  A.popc[id] = q.pc;
+  A.tcre[id] = i;
+  A.eexp[id] = -1;
+  uint32_t* om = A.mask + (size_t)id * A.w;
+  uint4 m = make_uint4(0u, 0u, 0u, 0u);
+  if (cached && A.w <= 4) {
+    m = sm->cmask[jl];
+    if (A.w == 4) {
+      *reinterpret_cast<uint4*>(om) = m;
+    } else {
+      om[0] = m.x;
+      if (A.w > 1) om[1] = m.y;
+      if (A.w > 2) om[2] = m.z;
+    }
+  } else {
+    const uint32_t* pm = A.mask + (size_t)q.parent * A.w;
+    const uint32_t* em = A.emask + (size_t)q.edge * A.w;
+    for (int j = 0; j < A.w; ++j) om[j] = ldu(pm + j) | ldu(em + j);
+  }
+  if (q.dg & kGoalBit) {
+    const int slot = atomicAdd(&A.ctl->n_goal_all, 1);
+    A.goal_all[slot] = (int32_t)id;
+  }
+  return m;
+}
+
+// Member at position pos of the next group: its record in the group list, and its copy to the
+// CTAs whose candidate chunks it feeds.
+__device__ __forceinline__ void put_member(const ExploreArgs& A, CSmem* sm, cg::cluster_group& cl, int64_t Cn,
+                                           int64_t per, int32_t gen, int64_t pos, int64_t off, int32_t id, int32_t x,
+                                           int32_t r0, float c, int32_t deg, uint4 m) {
+  const int4 info = make_int4(id, x, r0, __float_as_int(c));
+  A.ginfo[pos] = info;
+  A.goff[pos] = off;
+  send_member(sm, cl, Cn, per, gen, (int32_t)pos, info, off, deg, m);
+}
+
 // ---------------------------------------------------------------- phase C
 template <bool kDsm>
 __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl, St& S) {
@@ -1034,161 +1119,174 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
   // phase overwrites with the next group: then survivors are written first, and after a barrier
   // (taken by every CTA: `big` is the same everywhere) the members are read back from the arena.
   const bool big = S.big != 0;
+  const int64_t a0 = S.a0, a1 = S.a1;
+  const int no = (int)min(a1 - a0, (int64_t)kCT + 1);
   int64_t run = S.base + before_s;
   int64_t mrun = total_o + before_n;
   int64_t drun = dtotal_o + dbefore_n;
-  for (int t0 = 0; t0 < n; t0 += kCT) {
-    const int jl = t0 + threadIdx.x;
-    bool keep = false;
-    int32_t eff = -1;
+  if (!big && has_next && n + no <= kCT) {
+    // cached survivors (threads below n) and cached older plans (threads n .. n + no - 1) in one
+    // pass, both lists' positions from one scan round
+    const int t = threadIdx.x;
+    bool keep = false, sel = false;
+    int32_t eff = -1, x = 0, r0 = 0, odeg = 0;
+    float c = 0.f;
+    uint4 m = make_uint4(0u, 0u, 0u, 0u);
     CCand q;
     q.x = q.parent = q.edge = q.pc = q.r0 = 0;
     q.dg = 0u;
     q.cost = 0.f;
-    if (jl < n) {
-      if (fits) {
-        eff = sm->ceff[jl];
-        keep = eff >= 0;
-        if (keep) {
-          q.x = sm->cx[jl];
-          q.parent = sm->cpar[jl];
-          q.edge = sm->cedge[jl];
-          q.cost = sm->ccost[jl];
-          q.pc = sm->cpc[jl];
-          q.r0 = sm->cr0[jl];
-          q.dg = sm->cdg[jl];
-        }
-      } else {
-        q = cand_at_c(A, c0 + jl, S.g, &sm->werr);
-        keep = q.pc < A.kmax && !dominated_c<kDsm>(A, cl, mbl, q.x, q.pc, q.cost);
-        if (keep) eff = eff_new(sm, A, S.i, q.cost);
+    if (t < n) {
+      eff = sm->ceff[t];
+      keep = eff >= 0;
+      if (keep) {
+        q.x = sm->cx[t];
+        q.parent = sm->cpar[t];
+        q.edge = sm->cedge[t];
+        q.cost = sm->ccost[t];
+        q.pc = sm->cpc[t];
+        q.r0 = sm->cr0[t];
+        q.dg = sm->cdg[t];
+      }
+    } else if (t < n + no) {
+      const int o = t - n;
+      sel = sm->oeff[o] == nbk;
+      if (sel) {
+        x = sm->ox[o];
+        c = sm->ocost[o];
+        r0 = sm->or0[o];
+        odeg = (int32_t)(sm->odg[o] & ~kGoalBit);
+        if (small_w) m = sm->omask[o];
       }
     }
     const int32_t deg = (int32_t)(q.dg & ~kGoalBit);
-    const bool member = !big && keep && eff == nbk;
-    int64_t tk;
-    const int64_t rk = cscan<int64_t>((keep ? (int64_t(1) << 52) : 0) | (member ? pack_cd(1, deg) : 0), &tk);
+    const bool member = keep && eff == nbk;
+    int64_t tk, tpk, rpk;
+    const int64_t rk = cscan2<int64_t>((keep ? (int64_t(1) << 52) : 0) | (member ? pack_cd(1, deg) : 0),
+                                       sel ? pack_cd(1, odeg) : 0, &tk, &tpk, &rpk);
     if (keep) {
       const int64_t id = run + pack_k(rk);
-      A.head[id] = q.x;
-      A.parent[id] = q.parent;
-      A.pedge[id] = q.edge;
-      A.cost[id] = q.cost;
-      A.popc[id] = q.pc;
-      A.tcre[id] = S.i;
-      A.eexp[id] = -1;
-      uint32_t* om = A.mask + (size_t)id * A.w;
-      uint4 m = make_uint4(0u, 0u, 0u, 0u);
-      if (fits && small_w) {
-        m = sm->cmask[jl];
-        if (A.w == 4) {
-          *reinterpret_cast<uint4*>(om) = m;
-        } else {
-          om[0] = m.x;
-          if (A.w > 1) om[1] = m.y;
-          if (A.w > 2) om[2] = m.z;
-        }
-      } else {
-        const uint32_t* pm = A.mask + (size_t)q.parent * A.w;
-        const uint32_t* em = A.emask + (size_t)q.edge * A.w;
-        for (int j = 0; j < A.w; ++j) om[j] = ldu(pm + j) | ldu(em + j);
-      }
-      if (q.dg & kGoalBit) {
-        const int slot = atomicAdd(&A.ctl->n_goal_all, 1);
-        A.goal_all[slot] = (int32_t)id;
-      }
-      if (member) {
-        const int64_t pos = mrun + pack_c(rk);
-        const int64_t off = drun + pack_d(rk);
-        const int4 info = make_int4((int32_t)id, q.x, q.r0, __float_as_int(q.cost));
-        A.ginfo[pos] = info;
-        A.goff[pos] = off;
-        send_member(sm, cl, Cn, per_n, S.k + 1, (int32_t)pos, info, off, deg, m);
-      }
+      const uint4 sm4 = put_survivor(A, sm, id, q, t, true, S.i);
+      if (member)
+        put_member(A, sm, cl, Cn, per_n, S.k + 1, mrun + pack_c(rk), drun + pack_d(rk), (int32_t)id, q.x, q.r0, q.cost,
+                   deg, sm4);
     }
-    run += pack_k(tk);
-    mrun += pack_c(tk);
-    drun += pack_d(tk);
-  }
-  if (big) {
-    cl.sync();
-    const int32_t mine = sm->pub.surv;
-    const int64_t id0 = S.base + before_s;
-    for (int t0 = 0; t0 < mine; t0 += kCT) {
-      const int k = t0 + threadIdx.x;
-      bool sel = false;
-      int32_t x = 0, r0 = 0, deg = 0;
-      float c = 0.f;
-      if (k < mine) {
-        c = ldf(A.cost + id0 + k);
-        sel = has_next && eff_new(sm, A, S.i, c) == nbk;
-        if (sel) {
-          x = ld32(A.head + id0 + k);
-          r0 = A.row_ptr[x];
-          deg = A.row_ptr[x + 1] - r0;
-        }
-      }
-      int64_t tm;
-      const int64_t mr = cscan<int64_t>(sel ? pack_cd(1, deg) : 0, &tm);
-      if (sel) {
-        const int64_t pos = mrun + pack_c(mr);
-        const int64_t off = drun + pack_d(mr);
-        const int4 info = make_int4((int32_t)(id0 + k), x, r0, __float_as_int(c));
-        A.ginfo[pos] = info;
-        A.goff[pos] = off;
-        const uint4 m = small_w ? load_mask4(A.mask + (size_t)(id0 + k) * A.w, A.w) : make_uint4(0u, 0u, 0u, 0u);
-        send_member(sm, cl, Cn, per_n, S.k + 1, (int32_t)pos, info, off, deg, m);
-      }
-      mrun += pack_c(tm);
-      drun += pack_d(tm);
-    }
-  }
-  // older members (ids below every survivor's) come first in the next group
-  if (has_next) {
-    const int64_t a0 = S.a0, a1 = S.a1;
-    const bool ofits = a1 - a0 <= kOCap;
-    int64_t orun = before_o, odrun = dbefore_o;
-    for (int64_t t0 = a0; t0 < a1; t0 += kCT) {
-      const int64_t p = t0 + threadIdx.x;
-      bool sel = false;
-      int32_t x = 0, r0 = 0, deg = 0;
-      float c = 0.f;
-      uint4 m = make_uint4(0u, 0u, 0u, 0u);
-      if (p < a1) {
-        int32_t eff;
-        if (ofits) {
-          const int o = (int)(p - a0);
-          eff = sm->oeff[o];
-          if (eff == nbk) {
-            x = sm->ox[o];
-            c = sm->ocost[o];
-            r0 = sm->or0[o];
-            deg = (int32_t)(sm->odg[o] & ~kGoalBit);
-            if (small_w) m = sm->omask[o];
+    if (sel)
+      put_member(A, sm, cl, Cn, per_n, S.k + 1, before_o + pack_c(rpk), dbefore_o + pack_d(rpk),
+                 (int32_t)(a0 + (t - n)), x, r0, c, odeg, m);
+  } else {
+    for (int t0 = 0; t0 < n; t0 += kCT) {
+      const int jl = t0 + threadIdx.x;
+      bool keep = false;
+      int32_t eff = -1;
+      CCand q;
+      q.x = q.parent = q.edge = q.pc = q.r0 = 0;
+      q.dg = 0u;
+      q.cost = 0.f;
+      if (jl < n) {
+        if (fits) {
+          eff = sm->ceff[jl];
+          keep = eff >= 0;
+          if (keep) {
+            q.x = sm->cx[jl];
+            q.parent = sm->cpar[jl];
+            q.edge = sm->cedge[jl];
+            q.cost = sm->ccost[jl];
+            q.pc = sm->cpc[jl];
+            q.r0 = sm->cr0[jl];
+            q.dg = sm->cdg[jl];
           }
         } else {
-          int32_t pc;
-          eff = old_eff_c<kDsm>(A, sm, cl, mbl, p, S.i, &x, &c, &pc);
-          if (eff == nbk) {
+          q = cand_at_c(A, c0 + jl, S.g, &sm->werr);
+          keep = q.pc < A.kmax && !dominated_c<kDsm>(A, cl, mbl, q.x, q.pc, q.cost);
+          if (keep) eff = eff_new(sm, A, S.i, q.cost);
+        }
+      }
+      const int32_t deg = (int32_t)(q.dg & ~kGoalBit);
+      const bool member = !big && keep && eff == nbk;
+      int64_t tk;
+      const int64_t rk = cscan<int64_t>((keep ? (int64_t(1) << 52) : 0) | (member ? pack_cd(1, deg) : 0), &tk);
+      if (keep) {
+        const int64_t id = run + pack_k(rk);
+        const uint4 m = put_survivor(A, sm, id, q, jl, fits, S.i);
+        if (member)
+          put_member(A, sm, cl, Cn, per_n, S.k + 1, mrun + pack_c(rk), drun + pack_d(rk), (int32_t)id, q.x, q.r0,
+                     q.cost, deg, m);
+      }
+      run += pack_k(tk);
+      mrun += pack_c(tk);
+      drun += pack_d(tk);
+    }
+    if (big) {
+      cl.sync();
+      const int32_t mine = sm->pub.surv;
+      const int64_t id0 = S.base + before_s;
+      for (int t0 = 0; t0 < mine; t0 += kCT) {
+        const int k = t0 + threadIdx.x;
+        bool sel = false;
+        int32_t x = 0, r0 = 0, deg = 0;
+        float c = 0.f;
+        if (k < mine) {
+          c = ldf(A.cost + id0 + k);
+          sel = has_next && eff_new(sm, A, S.i, c) == nbk;
+          if (sel) {
+            x = ld32(A.head + id0 + k);
             r0 = A.row_ptr[x];
             deg = A.row_ptr[x + 1] - r0;
-            if (small_w) m = load_mask4(A.mask + (size_t)p * A.w, A.w);
           }
         }
-        sel = eff == nbk;
+        int64_t tm;
+        const int64_t mr = cscan<int64_t>(sel ? pack_cd(1, deg) : 0, &tm);
+        if (sel) {
+          const uint4 m = small_w ? load_mask4(A.mask + (size_t)(id0 + k) * A.w, A.w) : make_uint4(0u, 0u, 0u, 0u);
+          put_member(A, sm, cl, Cn, per_n, S.k + 1, mrun + pack_c(mr), drun + pack_d(mr), (int32_t)(id0 + k), x, r0, c,
+                     deg, m);
+        }
+        mrun += pack_c(tm);
+        drun += pack_d(tm);
       }
-      int64_t tpk;
-      const int64_t rpk = cscan<int64_t>(sel ? pack_cd(1, deg) : 0, &tpk);
-      if (sel) {
-        const int64_t pos = orun + pack_c(rpk);
-        const int64_t off = odrun + pack_d(rpk);
-        const int4 info = make_int4((int32_t)p, x, r0, __float_as_int(c));
-        A.ginfo[pos] = info;
-        A.goff[pos] = off;
-        send_member(sm, cl, Cn, per_n, S.k + 1, (int32_t)pos, info, off, deg, m);
+    }
+    // older members (ids below every survivor's) come first in the next group
+    if (has_next) {
+      const bool ofits = a1 - a0 <= kOCap;
+      int64_t orun = before_o, odrun = dbefore_o;
+      for (int64_t t0 = a0; t0 < a1; t0 += kCT) {
+        const int64_t p = t0 + threadIdx.x;
+        bool sel = false;
+        int32_t x = 0, r0 = 0, deg = 0;
+        float c = 0.f;
+        uint4 m = make_uint4(0u, 0u, 0u, 0u);
+        if (p < a1) {
+          int32_t eff;
+          if (ofits) {
+            const int o = (int)(p - a0);
+            eff = sm->oeff[o];
+            if (eff == nbk) {
+              x = sm->ox[o];
+              c = sm->ocost[o];
+              r0 = sm->or0[o];
+              deg = (int32_t)(sm->odg[o] & ~kGoalBit);
+              if (small_w) m = sm->omask[o];
+            }
+          } else {
+            int32_t pc;
+            eff = old_eff_c<kDsm>(A, sm, cl, mbl, p, S.i, &x, &c, &pc);
+            if (eff == nbk) {
+              r0 = A.row_ptr[x];
+              deg = A.row_ptr[x + 1] - r0;
+              if (small_w) m = load_mask4(A.mask + (size_t)p * A.w, A.w);
+            }
+          }
+          sel = eff == nbk;
+        }
+        int64_t tpk;
+        const int64_t rpk = cscan<int64_t>(sel ? pack_cd(1, deg) : 0, &tpk);
+        if (sel)
+          put_member(A, sm, cl, Cn, per_n, S.k + 1, orun + pack_c(rpk), odrun + pack_d(rpk), (int32_t)p, x, r0, c, deg,
+                     m);
+        orun += pack_c(tpk);
+        odrun += pack_d(tpk);
       }
-      orun += pack_c(tpk);
-      odrun += pack_d(tpk);
     }
   }
   const int32_t gn = has_next ? total_o + total_n : 0;
