@@ -119,9 +119,14 @@ __device__ __forceinline__ bool launch_shape_ok(const LaunchShape& ls) {
   uint32_t nct, dsz;
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(nct));
   asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
-  return nct == (uint32_t)ls.nr && dsz >= ls.smem && blockDim.x == (unsigned)kCT && blockDim.y == 1 &&
-         blockDim.z == 1 && gridDim.x % (unsigned)ls.nr == 0;
+  return nct == (uint32_t)ls.nr && (ls.nr & (ls.nr - 1)) == 0 && dsz >= ls.smem && blockDim.x == (unsigned)kCT &&
+         blockDim.y == 1 && blockDim.z == 1 && gridDim.x % (unsigned)ls.nr == 0;
 }
+
+// Cluster sizes are powers of two (the host picks 16, 8 or 4 and the launch-shape check refuses
+// others), so per-CTA shares and the node -> (CTA, row) split of the dominance table are shifts
+// and masks instead of integer divisions on the phases' dependent chains.
+__device__ __forceinline__ int log2_nr(int nr) { return __ffs(nr) - 1; }
 
 // Counts one CTA publishes after phase B (every CTA reads them in phase C).  16-byte aligned:
 // the end of phase B copies the whole record into every CTA's shared memory with vector stores.
@@ -197,7 +202,7 @@ struct CSmem {
 };
 
 __device__ __forceinline__ void chunk(int64_t total, int r, int nr, int64_t* lo, int64_t* hi) {
-  const int64_t per = (total + nr - 1) / nr;
+  const int64_t per = (total + nr - 1) >> log2_nr(nr);
   *lo = min(total, (int64_t)r * per);
   *hi = min(total, *lo + per);
 }
@@ -217,7 +222,7 @@ __device__ __forceinline__ void iter_setup(St& S, int k, int r, int nr) {
   chunk(S.base - S.lo, r, nr, &S.a0, &S.a1);
   S.a0 += S.lo;
   S.a1 += S.lo;
-  S.big = (S.C + nr - 1) / nr > kCCap ? 1 : 0;
+  S.big = ((S.C + nr - 1) >> log2_nr(nr)) > kCCap ? 1 : 0;
 }
 
 // Exclusive block scan over kCT threads; returns the prefix and writes the total.
@@ -343,8 +348,8 @@ __device__ __forceinline__ int64_t pack_d(int64_t x) { return x & ((int64_t(1) <
 template <bool kDsm>
 __device__ __forceinline__ uint32_t* mb_row(const ExploreArgs& A, cg::cluster_group& cl, uint32_t* mbl, int32_t x) {
   if (kDsm) {
-    const unsigned nr = cl.num_blocks();
-    return cl.map_shared_rank(mbl + (size_t)(x / (int)nr) * A.kstride, (unsigned)(x % (int)nr));
+    const int nr = (int)cl.num_blocks();
+    return cl.map_shared_rank(mbl + (size_t)(x >> log2_nr(nr)) * A.kstride, (unsigned)(x & (nr - 1)));
   }
   return A.mbest + (size_t)x * A.kstride;
 }
@@ -356,10 +361,10 @@ template <bool kDsm>
 __device__ __forceinline__ void mb_min(const ExploreArgs& A, cg::cluster_group& cl, uint32_t* mbl, int32_t x, int k,
                                        uint32_t v) {
   if (kDsm) {
-    const unsigned nr = cl.num_blocks();
-    const uint32_t local = (uint32_t)__cvta_generic_to_shared(mbl + (size_t)(x / (int)nr) * A.kstride + k);
+    const int nr = (int)cl.num_blocks();
+    const uint32_t local = (uint32_t)__cvta_generic_to_shared(mbl + (size_t)(x >> log2_nr(nr)) * A.kstride + k);
     uint32_t remote;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"((unsigned)(x % (int)nr)));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"((unsigned)(x & (nr - 1))));
     asm volatile("red.relaxed.cluster.shared::cluster.min.u32 [%0], %1;" ::"r"(remote), "r"(v) : "memory");
   } else {
     asm volatile("red.relaxed.gpu.global.min.u32 [%0], %1;" ::"l"(A.mbest + (size_t)x * A.kstride + k), "r"(v)
@@ -1091,7 +1096,7 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
   }
   if (threadIdx.x == 0) {
     const long long Cn = nbk != kNoBucket ? sm->b_dtotal_o + sm->b_dtotal_n : 0;
-    sm->b_per_n = (Cn + nr - 1) / nr;
+    sm->b_per_n = (Cn + nr - 1) >> log2_nr(nr);
   }
   __syncthreads();
   const int32_t total_s = sm->b_total_s, before_s = sm->b_before_s;
@@ -1328,7 +1333,7 @@ __device__ void explore_one(const ExploreArgs& A, int32_t start, CSmem* sm, uint
     sm->rows_ready = A.rowcnt ? 0 : 1;
   }
   __syncthreads();
-  if (kDsm && start % nr == r && threadIdx.x == 0) mbl[(size_t)(start / nr) * A.kstride] = 0u;  // root: cost 0
+  if (kDsm && (start & (nr - 1)) == r && threadIdx.x == 0) mbl[(size_t)(start >> log2_nr(nr)) * A.kstride] = 0u;  // root: cost 0
   St& S = sm->st;
   if (threadIdx.x == 0) {
     S.C = ld64(&ctl->st[0].group_cands);
@@ -1875,7 +1880,7 @@ int plan_cluster_form(int32_t n, int32_t kstride, int want_nr, bool want_global,
   int n_sizes = 3;
   const int want = env > 0 ? env : want_nr;
   if (want > 0) {
-    if (want > kMaxCluster) return PUMP_OK;
+    if (want > kMaxCluster || (want & (want - 1))) return PUMP_OK;  // the kernels need a power of two
     sizes[0] = want;
     n_sizes = 1;
   }
