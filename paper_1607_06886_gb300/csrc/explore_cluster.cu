@@ -1472,9 +1472,11 @@ __device__ __forceinline__ void mask_position(const FuseArgs& F, const float4* x
 }
 
 // Prologue of the fused launch (Explore cluster, before group 0): positions [0, head) of the order,
-// position q on CTA q mod nr, each of its word pairs on its own warp (half a warp's chain per
-// task for N = 128), every position counted toward its row after the CTA's tasks are done.
-__device__ __forceinline__ void mask_prologue(const FuseArgs& F, unsigned char* smem, long long head, int r, int nr) {
+// which are the start row's edges r0s, r0s + 1, ... (its row comes first), position q on CTA
+// q mod nr, each of its word pairs on its own warp (half a warp's chain per task for N = 128),
+// the CTA's positions counted toward the start row after its tasks are done.
+__device__ __forceinline__ void mask_prologue(const FuseArgs& F, unsigned char* smem, long long head, int32_t start,
+                                              int32_t r0s, int r, int nr) {
   float* boxes = reinterpret_cast<float*>(smem);
   int* cand = reinterpret_cast<int*>(boxes + maskdev::kBoxStride * F.nb);
   uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kCW * maskdev::kCandCap);
@@ -1492,15 +1494,13 @@ __device__ __forceinline__ void mask_prologue(const FuseArgs& F, unsigned char* 
   for (long long t = warp; t < mine * npair; t += kCW) {
     const long long q = r + (t / npair) * nr;
     const int pr = (int)(t % npair);
-    const int2 ex = __ldg(F.eorder + q);
-    maskdev::edge_mask_one<PUMP_FUSED_MASK_NP>(ex.x, xp, F.N, F.W, F.phi, F.L, F.nom, linf, F.ibox, F.dmax, boxes,
+    maskdev::edge_mask_one<PUMP_FUSED_MASK_NP>(r0s + q, xp, F.N, F.W, F.phi, F.L, F.nom, linf, F.ibox, F.dmax, boxes,
                                                F.nb, F.w, my_cand, wm, lane, F.emask, pr, pr + 1);
   }
   __syncthreads();
-  for (long long j = threadIdx.x; j < mine; j += kCT) {
-    const int2 ex = __ldg(F.eorder + r + j * nr);
+  if (threadIdx.x == 0 && mine > 0 && start != F.hold_row) {
     __threadfence();
-    if (ex.y != F.hold_row) red_release_add(F.rowcnt + ex.y, 1u);
+    red_release_add(F.rowcnt + start, (uint32_t)mine);
   }
 }
 
@@ -1563,12 +1563,13 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t
   const int nr = (int)cl.num_blocks();
   // positions [0, head) (the start row's out-degree: the start's row comes first in the order)
   // are computed by the Explore cluster before group 0, the rest by the workers
-  const long long head = min((long long)F.E, (long long)(__ldg(A.row_ptr + start + 1) - __ldg(A.row_ptr + start)));
+  const int32_t r0s = __ldg(A.row_ptr + start);
+  const long long head = min((long long)F.E, (long long)(__ldg(A.row_ptr + start + 1) - r0s));
   if ((int)blockIdx.x < nr) {
     // the run's initial state (root plan, control block), read by every CTA after the barrier
     // below; shared memory serves as the mask scratch first, explore_one initialises what it uses
     if (blockIdx.x == 0 && threadIdx.x == 0) explore_init_thread(A, start);
-    mask_prologue(F, smem_raw, head, (int)blockIdx.x, nr);
+    mask_prologue(F, smem_raw, head, start, r0s, (int)blockIdx.x, nr);
     cl.sync();
     CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
     uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
@@ -1685,12 +1686,14 @@ __device__ int32_t order_scan(int32_t v, int32_t* wsum, int32_t* tot) {
   return pre;
 }
 
-// Rows by increasing cost (counting sort on the cost quantised to kOrderBuckets - 1 levels over
-// [0, largest finite cost]; unreachable rows last; order inside a level unspecified), and the
-// exclusive prefix of their out-degrees (n + 1 entries).  One block of kOrderThreads threads.
+// Rows by increasing cost (the start's row alone first, then a counting sort on the cost quantised
+// to kOrderBuckets - 2 levels over [0, largest finite cost]; unreachable rows last; order inside a
+// level unspecified), and the exclusive prefix of their out-degrees (n + 1 entries).  One block of
+// kOrderThreads threads.
 __global__ void __launch_bounds__(kOrderThreads) k_row_order(const uint32_t* __restrict__ dist,
                                                              const int32_t* __restrict__ row_ptr, int32_t n,
-                                                             int32_t* __restrict__ order, int32_t* __restrict__ epos) {
+                                                             int32_t start, int32_t* __restrict__ order,
+                                                             int32_t* __restrict__ epos) {
   __shared__ int32_t hist[kOrderBuckets];
   __shared__ float s_max[32];
   __shared__ int32_t wsum[32];
@@ -1708,11 +1711,12 @@ __global__ void __launch_bounds__(kOrderThreads) k_row_order(const uint32_t* __r
   __syncthreads();
   m = 0.f;
   for (int k = 0; k < 32; ++k) m = fmaxf(m, s_max[k]);
-  const float scale = m > 0.f ? (float)(kOrderBuckets - 2) / m : 0.f;
+  const float scale = m > 0.f ? (float)(kOrderBuckets - 3) / m : 0.f;
   auto level = [&](int32_t x) {
+    if (x == start) return 0;
     const float d = __uint_as_float(dist[x]);
     if (!(d < __int_as_float(0x7f800000))) return kOrderBuckets - 1;
-    return min(kOrderBuckets - 2, (int)(d * scale));
+    return 1 + min(kOrderBuckets - 3, (int)(d * scale));
   };
   for (int32_t x = t; x < n; x += kOrderThreads) atomicAdd(&hist[level(x)], 1);
   __syncthreads();
@@ -2067,7 +2071,7 @@ int row_order_begin(pump_graph* g, cudaStream_t s, bool overlap) {
   }
   if (e == cudaSuccess) {
     note_launch();
-    k_row_order<<<1, kOrderThreads, 0, ks>>>(dist, g->row_ptr, n, order, epos);
+    k_row_order<<<1, kOrderThreads, 0, ks>>>(dist, g->row_ptr, n, g->start, order, epos);
     note_launch();
     const int eb = (int)std::min<int64_t>(((int64_t)n * 32 + 255) / 256, 4096);
     k_edge_order<<<eb, 256, 0, ks>>>(order, epos, g->row_ptr, n, eo);

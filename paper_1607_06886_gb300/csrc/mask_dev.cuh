@@ -272,6 +272,14 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
                                               uint32_t* __restrict__ mask, int p_first = 0, int p_last = -1) {
   const float* ib = ibox_g + 6 * e;
   const float lo0 = ib[0], lo1 = ib[1], lo2 = ib[2], hi0 = ib[3], hi1 = ib[4], hi2 = ib[5];
+  // every per-edge read issued here, together: the box culling, the narrowing and the passes
+  // would otherwise wait for them one after another
+  const float M = __uint_as_float(dmax[e]);
+  const float4 ph = *reinterpret_cast<const float4*>(phi + 4 * e);
+  const float l0 = Lg[3 * e], l1 = Lg[3 * e + 1], l2 = Lg[3 * e + 2];
+  const float* nm = nom + (size_t)e * W * 3;
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(nm));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(nm + (W * 3 - 1)));
   int n_cand = 0;
   for (int base = 0; base < nb; base += 32) {
     const int o = base + lane;
@@ -286,12 +294,10 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
     n_cand += __popc(bal);
   }
   __syncwarp();
-  const float* nm = nom + (size_t)e * W * 3;
   int k_last = W;
   const bool narrow = n_cand > 0 && n_cand <= 32;
   if (narrow) {
     // boxes per waypoint: lane c tests candidate c against waypoint k's position box
-    const float M = __uint_as_float(dmax[e]);
     const float* bc = boxes + kBoxStride * my_cand[lane < n_cand ? lane : 0];
     k_last = 0;
     for (int k = 1; k <= W; ++k) {
@@ -312,8 +318,6 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
   }
   const bool all = n_cand > kCandCap;
   const int nc = all ? nb : n_cand;
-  const float4 ph = *reinterpret_cast<const float4*>(phi + 4 * e);
-  const float l0 = Lg[3 * e], l1 = Lg[3 * e + 1], l2 = Lg[3 * e + 2];
   const unsigned long long P2[4] = {pk2(ph.x, ph.x), pk2(ph.y, ph.y), pk2(ph.z, ph.z), pk2(ph.w, ph.w)};
   const unsigned long long L2[3] = {pk2(l0, l0), pk2(l1, l1), pk2(l2, l2)};
   const unsigned long long I2[3] = {pk2(linf[0], linf[0]), pk2(linf[1], linf[1]), pk2(linf[2], linf[2])};

@@ -147,7 +147,9 @@ def test_edge_order_is_a_row_order_by_cost(name, seed, ns):
     for a, b in zip(starts, np.r_[starts[1:], E]):
         x = eo[a, 1]
         np.testing.assert_array_equal(eo[a:b, 0], np.arange(rp[x], rp[x + 1]))
-    # rows by cost from the start: nondecreasing up to the quantisation (4094 levels over the
+    # the start's row first (the fused launch's prologue computes exactly its edges)
+    assert rows[0] == wl.start_idx
+    # rows by cost from the start: nondecreasing up to the quantisation (4093 levels over the
     # largest finite cost) and the float sums the device adds in another order; unreachable last
     d = shortest_costs(rp, col, ec, wl.start_idx)
     dr = d[rows]
