@@ -193,6 +193,7 @@ struct CSmem {
   int32_t b_nbk, b_min_open, b_before_s, b_total_s, b_before_o, b_total_o, b_before_n, b_total_n, b_stop, b_fast, b_err;
   int32_t werr;        // this CTA: a wait for a row's masks ran out (fused form)
   int32_t rows_ready;  // this CTA saw every worker warp finished: no more waits (fused form)
+  int32_t ready_row;   // a row whose masks are complete from the first group on, or -1 (fused form)
   long long b_dbefore_o, b_dtotal_o, b_dbefore_n, b_dtotal_n, b_per_n;
   ExploreArgs args;  // the query's arguments (batched form)
   int32_t qnext;     // query index taken by the cluster (batched form; written by CTA 0)
@@ -550,7 +551,7 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
       const int64_t lo = max(lo_s, c0), hi = min(hi_s, c1);
       if (lo >= hi) continue;
       const int32_t p = gi.x, r0 = gi.z;
-      if (A.rowcnt && !sm->rows_ready)
+      if (A.rowcnt && !sm->rows_ready && gi.y != sm->ready_row)
         row_wait(A.rowcnt, gi.y, (uint32_t)(hi_s - lo_s), A.epoch_m1, A.spin_limit, &sm->werr);
       const float pcost = __int_as_float(gi.w);
       const uint32_t* pm = A.mask + (size_t)p * w;
@@ -1311,36 +1312,57 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
   }
 }
 
-// One Explore run by the whole cluster.  Starts and ends with a cluster barrier, so a cluster
-// can run several in a row (batched form).
+// Dominance table of this CTA's nodes: +inf, and the root's entry (start, 0) = 0.
 template <bool kDsm>
-__device__ void explore_one(const ExploreArgs& A, int32_t start, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl) {
-  const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
-  ExploreCtl* ctl = A.ctl;
-  if (kDsm) {
-    const int rows = (A.n + nr - 1) / nr;
-    for (int k = threadIdx.x; k < rows * A.kstride; k += kCT) mbl[k] = 0x7f800000u;  // +inf
-  }
+__device__ void explore_table_init(const ExploreArgs& A, int32_t start, uint32_t* mbl, int r, int nr) {
+  if (!kDsm) return;
+  const int rows = (A.n + nr - 1) / nr;
+  for (int k = threadIdx.x; k < rows * A.kstride; k += kCT) mbl[k] = 0x7f800000u;  // +inf
+  __syncthreads();
+  if ((start & (nr - 1)) == r && threadIdx.x == 0) mbl[(size_t)(start >> log2_nr(nr)) * A.kstride] = 0u;
+}
+
+// The CTA's search state before group 0.  fresh: the run starts from the root alone (the state
+// explore_init_thread writes), derived here instead of read back, and the root is this CTA's
+// local member; otherwise the state comes from the control block.
+template <bool kDsm>
+__device__ void explore_state_init(const ExploreArgs& A, int32_t start, CSmem* sm, int r, int nr, bool fresh,
+                                   int32_t ready_row) {
   for (int k = threadIdx.x; k < kMemCap; k += kCT) {
     sm->mt_tag[k] = -1;
     sm->mt_gen[k] = -1;
   }
+  __syncthreads();
+  St& S = sm->st;
   if (threadIdx.x == 0) {
     sm->slot0 = 0;  // group 0 is the root alone
     sm->slot_end = 0;
     sm->kept = 0;
     sm->werr = 0;
     sm->rows_ready = A.rowcnt ? 0 : 1;
-  }
-  __syncthreads();
-  if (kDsm && (start & (nr - 1)) == r && threadIdx.x == 0) mbl[(size_t)(start >> log2_nr(nr)) * A.kstride] = 0u;  // root: cost 0
-  St& S = sm->st;
-  if (threadIdx.x == 0) {
-    S.C = ld64(&ctl->st[0].group_cands);
-    S.g = ld32(&ctl->st[0].group_size);
-    S.i = ld32(&ctl->st[0].iter);
-    S.stop = ld32(&ctl->st[0].stop);
-    S.base = ld64(&ctl->n_plans);
+    sm->ready_row = ready_row;
+    if (fresh) {
+      const int32_t r0 = A.row_ptr[start];
+      const int64_t d0 = A.row_ptr[start + 1] - r0;
+      S.C = d0;
+      S.g = 1;
+      S.i = 0;
+      S.stop = (A.early_stop && A.is_goal[start] && 0 < A.kmin) ? 1 : 0;
+      S.base = 1;
+      sm->mt_info[0] = make_int4(0, start, r0, __float_as_int(0.f));
+      sm->mt_off[0] = 0;
+      sm->mt_deg[0] = (int32_t)d0;
+      sm->mt_mask[0] = make_uint4(0u, 0u, 0u, 0u);
+      sm->mt_tag[0] = 0;
+      sm->mt_gen[0] = 0;
+    } else {
+      ExploreCtl* ctl = A.ctl;
+      S.C = ld64(&ctl->st[0].group_cands);
+      S.g = ld32(&ctl->st[0].group_size);
+      S.i = ld32(&ctl->st[0].iter);
+      S.stop = ld32(&ctl->st[0].stop);
+      S.base = ld64(&ctl->n_plans);
+    }
     S.lo = 0;
     S.ncand = 0;
     S.status = 0;
@@ -1348,7 +1370,15 @@ __device__ void explore_one(const ExploreArgs& A, int32_t start, CSmem* sm, uint
     S.k = 0;
     if (iter_runs(S, A, 0)) iter_setup(S, 0, r, nr);
   }
-  cl.sync();
+}
+
+// The group loop and the run's results; starts after a cluster barrier that follows the table
+// and state initialisation, ends with one.
+template <bool kDsm>
+__device__ void explore_loop(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl) {
+  const int r = (int)cl.block_rank();
+  ExploreCtl* ctl = A.ctl;
+  St& S = sm->st;
   int k = 0;
   for (;; ++k) {
     if (S.status || S.stop || S.g == 0) break;
@@ -1378,6 +1408,17 @@ __device__ void explore_one(const ExploreArgs& A, int32_t start, CSmem* sm, uint
     ctl->k_exit = k;
   }
   cl.sync();  // no CTA leaves (or starts another run) while another may still touch its shared memory
+}
+
+// One Explore run by the whole cluster.  Starts and ends with a cluster barrier, so a cluster
+// can run several in a row (batched form).
+template <bool kDsm>
+__device__ void explore_one(const ExploreArgs& A, int32_t start, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl) {
+  const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
+  explore_table_init<kDsm>(A, start, mbl, r, nr);
+  explore_state_init<kDsm>(A, start, sm, r, nr, false, -1);
+  cl.sync();
+  explore_loop<kDsm>(A, sm, mbl, cl);
 }
 
 template <bool kDsm>
@@ -1566,15 +1607,32 @@ __global__ void __launch_bounds__(kCT, 1) k_explore_fused(ExploreArgs A, int32_t
   const int32_t r0s = __ldg(A.row_ptr + start);
   const long long head = min((long long)F.E, (long long)(__ldg(A.row_ptr + start + 1) - r0s));
   if ((int)blockIdx.x < nr) {
-    // the run's initial state (root plan, control block), read by every CTA after the barrier
-    // below; shared memory serves as the mask scratch first, explore_one initialises what it uses
-    if (blockIdx.x == 0 && threadIdx.x == 0) explore_init_thread(A, start);
-    mask_prologue(F, smem_raw, head, start, r0s, (int)blockIdx.x, nr);
-    cl.sync();
+    const int r = (int)cl.block_rank();
     CSmem* sm = reinterpret_cast<CSmem*>(smem_raw);
-    uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + ((sizeof(CSmem) + 15) & ~size_t(15)));
-    explore_one<kDsm>(A, start, sm, mbl, cl);
-    // P_goal in PlanSelection order (explore_one ends with a cluster barrier: every plan written)
+    const size_t mbl_off = (sizeof(CSmem) + 15) & ~size_t(15);
+    uint32_t* mbl = reinterpret_cast<uint32_t*>(smem_raw + mbl_off);
+    // shared memory serves as the prologue's mask scratch first (from offset 0); when that ends
+    // below the dominance table, the table is set up before the prologue and one cluster barrier
+    // closes both, every CTA deriving the root state itself (the start row's masks are complete
+    // at that barrier, so group 0 does not wait for them)
+    const size_t pro_end = maskdev::fixed_smem(F.nb, kCW) +
+                           (F.xi_smem ? sizeof(float4) * (size_t)(F.W + 1) * 3 * maskdev::pair_count(F.w) * 32 : 0);
+    const bool early = pro_end <= mbl_off;
+    if (early) explore_table_init<kDsm>(A, start, mbl, r, nr);
+    // the run's initial state in global memory (root plan, control block), read after a barrier
+    if (blockIdx.x == 0 && threadIdx.x == 0) explore_init_thread(A, start);
+    mask_prologue(F, smem_raw, head, start, r0s, r, nr);
+    if (early) {
+      __syncthreads();
+    } else {
+      cl.sync();
+      explore_table_init<kDsm>(A, start, mbl, r, nr);
+    }
+    // (the test hook that withholds a row's count keeps that row's waits)
+    explore_state_init<kDsm>(A, start, sm, r, nr, early, early && start != F.hold_row ? start : -1);
+    cl.sync();
+    explore_loop<kDsm>(A, sm, mbl, cl);
+    // P_goal in PlanSelection order (the loop ends with a cluster barrier: every plan written)
     if (blockIdx.x == 0) goal_finalize_block(A, A.group, F.goal_sorted);
     return;
   }
