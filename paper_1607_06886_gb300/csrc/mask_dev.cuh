@@ -272,14 +272,6 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
                                               uint32_t* __restrict__ mask, int p_first = 0, int p_last = -1) {
   const float* ib = ibox_g + 6 * e;
   const float lo0 = ib[0], lo1 = ib[1], lo2 = ib[2], hi0 = ib[3], hi1 = ib[4], hi2 = ib[5];
-  // every per-edge read issued here, together: the box culling, the narrowing and the passes
-  // would otherwise wait for them one after another
-  const float M = __uint_as_float(dmax[e]);
-  const float4 ph = *reinterpret_cast<const float4*>(phi + 4 * e);
-  const float l0 = Lg[3 * e], l1 = Lg[3 * e + 1], l2 = Lg[3 * e + 2];
-  const float* nm = nom + (size_t)e * W * 3;
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(nm));
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(nm + (W * 3 - 1)));
   int n_cand = 0;
   for (int base = 0; base < nb; base += 32) {
     const int o = base + lane;
@@ -294,8 +286,21 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
     n_cand += __popc(bal);
   }
   __syncwarp();
+  if (n_cand == 0) {
+    for (int word = lane; word < w; word += 32) mask[(size_t)e * w + word] = 0u;
+    __syncwarp();
+    return;
+  }
+  // the live edge's other reads issued together: the narrowing and the passes would otherwise
+  // wait for them one after another
+  const float M = __uint_as_float(dmax[e]);
+  const float4 ph = *reinterpret_cast<const float4*>(phi + 4 * e);
+  const float l0 = Lg[3 * e], l1 = Lg[3 * e + 1], l2 = Lg[3 * e + 2];
+  const float* nm = nom + (size_t)e * W * 3;
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(nm));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(nm + (W * 3 - 1)));
   int k_last = W;
-  const bool narrow = n_cand > 0 && n_cand <= 32;
+  const bool narrow = n_cand <= 32;
   if (narrow) {
     // boxes per waypoint: lane c tests candidate c against waypoint k's position box
     const float* bc = boxes + kBoxStride * my_cand[lane < n_cand ? lane : 0];
@@ -311,7 +316,7 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
     }
     __syncwarp();
   }
-  if (n_cand == 0 || k_last == 0) {
+  if (k_last == 0) {
     for (int word = lane; word < w; word += 32) mask[(size_t)e * w + word] = 0u;
     __syncwarp();
     return;
