@@ -615,9 +615,9 @@ def served_measure(pump, args, rank, ws, rate):
 def batched_measure(pump, args, dev, flush, rank, ws):
     """The batched form: args.batch_queries independent queries of uneven size (samples
     U{1000..8000}, boxes U{5..50}, N in {64, 128, 256}, W = 10, CP target 1 %), graphs resident,
-    each step = edge masks of every query + all Explore runs in one persistent launch
-    (pump_plan_batch, Explore only).  The launch form comes from the autotuner.  Also times the
-    same queries one after another through the single-query call."""
+    each step = the edge masks of every query in one persistent launch + all Explore runs in
+    another (pump_plan_batch, Explore only).  The launch forms come from the autotuner.  Also times
+    the same queries one after another through the single-query call."""
     import torch
     from paper_1607_06886_gb300 import autotune, inputs
     nq = args.batch_queries
@@ -673,7 +673,8 @@ def batched_measure(pump, args, dev, flush, rank, ws):
            "partial_plans": cands, "plans": plans, "edges": int(sum(int(G.counts()[1]) for G in Gs)),
            "single_queries_ms": seq_ms, "speedup_vs_single_queries": seq_ms / ms, "results_equal_single": bool(same),
            "launch": {"cluster_size": cfg.cluster_size, "mbest_global": cfg.mbest_global, "tuned_ms": rec.get("explore_ms"),
-                      "mask_pairs": cfg.mask_pairs, "mask_chunk": cfg.mask_chunk, "mask_tuned_ms": rec.get("mask_ms")},
+                      "mask_pairs": cfg.mask_pairs, "mask_chunk": cfg.mask_chunk, "mask_span": cfg.mask_span,
+                      "mask_tuned_ms": rec.get("mask_ms")},
            "explore_roofline": {"bound": "hbm", "achieved": nbytes / (ms_expl / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                                 "frac": nbytes / (ms_expl / 1e3) / 1e9 / hbm},
            "mask_roofline": {"bound": "alu", "achieved": ops_mask / (ms_mask / 1e3) / 1e12, "peak": alu_peak / 1e12,

@@ -254,9 +254,9 @@ int pump_plan_collect(pump_graph* g, pump_plan_result* out, void* stream);
 
 /* --------------------------------------------------------------------------
  * pump_plan_batch: pump_plan for n_queries independent queries, one per
- * built graph, with the Explore runs of all queries in one persistent launch
- * (no counterpart in the paper: a throughput form of Algorithm 2 for many
- * problems at once).  graphs[q] (distinct, built by pump_build_graph) is
+ * built graph, with the box masks of all queries in one persistent launch and
+ * the Explore runs of all queries in another (no counterpart in the paper: a
+ * throughput form of Algorithm 2 for many problems at once).  graphs[q] (distinct, built by pump_build_graph) is
  * planned with params[q]; results[q] receives what pump_plan would write for
  * it (the selected path is left in the graph: pump_export of the plan arrays
  * and goal plans), except that ms_masks / ms_explore / ms_select are the
@@ -272,6 +272,8 @@ typedef struct {
   int32_t mask_pairs;   /* particle block of the mask pass: mask-word pairs a warp advances side
                            by side (1 or 2; 0 = 2)                                             */
   int32_t mask_chunk;   /* edges a warp of the mask pass takes at a time (1 .. 64; 0 = 4)       */
+  int32_t mask_span;    /* edges of one graph a block of the mask pass takes at a time (a
+                           multiple of 32, 32 .. 65536; 0 = 1024)                              */
 } pump_batch_config;
 /* Queries whose params set PUMP_EXPLORE_ONLY stop after Explore; the others
  * run PlanSelection one after another.  Synchronises.

@@ -2,8 +2,8 @@
 
 For a batch it times, on the batch itself, the candidate forms of the Explore launch (the tile of
 a query: CTAs per query, dominance table on chip or in global memory) and then those of the
-edge-mask launches (the particle block: mask-word pairs a warp advances side by side, and the
-edges a warp takes at a time), keeps the fastest of each, and remembers the choice in a JSON file
+edge-mask launch (the particle block: mask-word pairs a warp advances side by side; the edges a
+warp takes at a time; the edges of one graph a block takes at a time), keeps the fastest of each, and remembers the choice in a JSON file
 keyed by the batch's shape: query count, particle counts and sample-count bucket.  Later batches of
 the same shape reuse it without timing.  Every form gives the same results; only the time
 differs.
@@ -20,7 +20,9 @@ from typing import Dict, List, Optional, Sequence, Tuple
 from . import pump
 
 CANDIDATES: Tuple[Tuple[int, int], ...] = ((16, 0), (16, 1), (8, 0), (8, 1), (4, 0))
-MASK_CANDIDATES: Tuple[Tuple[int, int], ...] = ((2, 4), (2, 1), (2, 16), (1, 4))  # (word pairs, edges per take)
+# (word pairs, edges per warp take, edges per block item)
+MASK_CANDIDATES: Tuple[Tuple[int, int, int], ...] = ((2, 4, 1024), (2, 1, 1024), (2, 4, 512), (2, 4, 2048),
+                                                     (2, 16, 1024), (1, 4, 1024))
 
 
 def cache_path() -> str:
@@ -74,7 +76,7 @@ def _timed(graphs, prm, cfg, reps: int, field: str) -> Optional[float]:
 
 def tune_batch(graphs: Sequence["pump.Graph"], params, reps: int = 2, force: bool = False,
                candidates: Sequence[Tuple[int, int]] = CANDIDATES,
-               mask_candidates: Sequence[Tuple[int, int]] = MASK_CANDIDATES) -> Tuple["pump.BatchConfig", Dict]:
+               mask_candidates: Sequence[Tuple[int, int, int]] = MASK_CANDIDATES) -> Tuple["pump.BatchConfig", Dict]:
     """Best BatchConfig for this batch shape (timed now unless cached).  Returns (config, record)
     where the record holds the per-form Explore and mask times in ms."""
     key = batch_key(graphs)
@@ -82,7 +84,7 @@ def tune_batch(graphs: Sequence["pump.Graph"], params, reps: int = 2, force: boo
     if not force and key in cache:
         rec = cache[key]
         return pump.BatchConfig(int(rec["cluster_size"]), int(rec["mbest_global"]), 0, int(rec.get("mask_pairs", 0)),
-                                int(rec.get("mask_chunk", 0))), rec
+                                int(rec.get("mask_chunk", 0)), int(rec.get("mask_span", 0))), rec
     if isinstance(params, pump.PlanParams):
         params = [params] * len(graphs)
     prm = []
@@ -102,16 +104,16 @@ def tune_batch(graphs: Sequence["pump.Graph"], params, reps: int = 2, force: boo
     if best is None:
         best = (0, 0)
     mtimes: Dict[str, float] = {}
-    mbest, mbest_ms = (0, 0), math.inf
-    for pairs, chunk in mask_candidates:
-        t = _timed(graphs, prm, pump.BatchConfig(best[0], best[1], 0, pairs, chunk), reps, "ms_masks")
+    mbest, mbest_ms = (0, 0, 0), math.inf
+    for pairs, chunk, span in mask_candidates:
+        t = _timed(graphs, prm, pump.BatchConfig(best[0], best[1], 0, pairs, chunk, span), reps, "ms_masks")
         if t is None:
             continue
-        mtimes[f"{pairs}/{chunk}"] = t
+        mtimes[f"{pairs}/{chunk}/{span}"] = t
         if t < mbest_ms:
-            mbest, mbest_ms = (pairs, chunk), t
+            mbest, mbest_ms = (pairs, chunk, span), t
     rec = {"cluster_size": best[0], "mbest_global": best[1], "explore_ms": times, "mask_pairs": mbest[0],
-           "mask_chunk": mbest[1], "mask_ms": mtimes}
+           "mask_chunk": mbest[1], "mask_span": mbest[2], "mask_ms": mtimes}
     cache[key] = rec
     _store(cache)
-    return pump.BatchConfig(best[0], best[1], 0, mbest[0], mbest[1]), rec
+    return pump.BatchConfig(best[0], best[1], 0, mbest[0], mbest[1], mbest[2]), rec

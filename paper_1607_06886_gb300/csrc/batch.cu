@@ -60,11 +60,12 @@ extern "C" int pump_plan_batch(pump_graph* const* graphs, int32_t nq, const pump
                                const pump_batch_config* config, pump_plan_result* results, void* stream) {
   using namespace pump;
   if (!graphs || !params || !results || nq < 1 || nq > (1 << 20)) return PUMP_ERR_INVALID_ARG;
-  pump_batch_config cfg = {0, 0, 0, 0, 0};
+  pump_batch_config cfg = {0, 0, 0, 0, 0, 0};
   if (config) cfg = *config;
   if ((cfg.cluster_size != 0 && cfg.cluster_size != 4 && cfg.cluster_size != 8 && cfg.cluster_size != 16) ||
       (cfg.mbest_global != 0 && cfg.mbest_global != 1) || cfg.max_clusters < 0 || cfg.mask_pairs < 0 ||
-      cfg.mask_pairs > 2 || cfg.mask_chunk < 0 || cfg.mask_chunk > 64)
+      cfg.mask_pairs > 2 || cfg.mask_chunk < 0 || cfg.mask_chunk > 64 || cfg.mask_span < 0 ||
+      cfg.mask_span > 65536 || cfg.mask_span % 32)
     return PUMP_ERR_INVALID_ARG;
   std::vector<pump_graph*> gs(graphs, graphs + nq);
   for (int q = 0; q < nq; ++q)
@@ -87,9 +88,9 @@ extern "C" int pump_plan_batch(pump_graph* const* graphs, int32_t nq, const pump
     return rc;
   };
   if (cudaEventRecord(ev[0], s) != cudaSuccess) return finish(PUMP_ERR_CUDA);
-  // edge masks, query by query (each launch spans the whole device)
-  for (int q = 0; q < nq; ++q) {
-    const int rc = compute_edge_masks(gs[q], s, cfg.mask_pairs, cfg.mask_chunk);
+  // edge masks of every query in one launch
+  {
+    const int rc = compute_edge_masks_batch(gs.data(), nq, s, cfg.mask_pairs, cfg.mask_chunk, cfg.mask_span);
     if (rc) return finish(rc);
   }
   if (cudaEventRecord(ev[1], s) != cudaSuccess) return finish(PUMP_ERR_CUDA);

@@ -180,6 +180,83 @@ __global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask
   }
 }
 
+// Batched query pass: the box masks of many graphs in one persistent launch.  Their edges form one
+// list of items (graph j's edges [i * span, (i + 1) * span) for i < ceil(E_j / span); graph j's
+// items from item0[j] on).  A block takes the next item from one counter, stages the graph's boxes
+// (and normals, when xi_smem) when the item belongs to another graph than its last one, and its
+// warps take the item's edges, chunk at a time, from a shared counter.  Thread 0 keeps the graph
+// index and moves it forward (items come in increasing order).
+struct MaskJob {
+  const float4* xp;
+  const float* phi;
+  const float* L;
+  const float* nom;
+  const float* linf;
+  const float* ibox;
+  const unsigned int* dmax;
+  const float* boxes;
+  uint32_t* emask;
+  long long E;
+  int32_t N, W, nb, w, xi_smem;
+};
+
+template <int kNP>
+__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS)
+    k_edge_mask_batch(const MaskJob* __restrict__ jobs, const long long* __restrict__ item0, int nq, int span,
+                      int chunk, unsigned long long* __restrict__ ctr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long s_item;
+  __shared__ int s_job;
+  __shared__ unsigned int s_next;
+  const long long n_items = __ldg(item0 + nq);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int cur = -1, jq = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(ctr, 1ull);
+      if (it < n_items)
+        while (jq + 1 < nq && __ldg(item0 + jq + 1) <= it) ++jq;
+      s_item = it;
+      s_job = jq;
+      s_next = 0u;
+    }
+    __syncthreads();
+    const long long it = s_item;
+    if (it >= n_items) break;
+    const int j = s_job;
+    const MaskJob& J = jobs[j];
+    const int nb = J.nb, W = J.W, w = J.w, N = J.N;
+    float* boxes = reinterpret_cast<float*>(smem);
+    int* cand = reinterpret_cast<int*>(boxes + kBoxStride * nb);
+    uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kWarps * maskdev::kCandCap);
+    float4* xp_s = reinterpret_cast<float4*>(smem + edge_mask_fixed_smem(nb));
+    if (j != cur) {
+      const int xp_n = (W + 1) * 3 * maskdev::pair_count(w) * 32;
+      maskdev::stage(J.boxes, nb, boxes, J.xp, J.xi_smem ? xp_s : nullptr, xp_n);
+      __syncthreads();
+      cur = j;
+    }
+    const float4* xp = J.xi_smem ? xp_s : J.xp;
+    const float linf[3] = {J.linf[0], J.linf[1], J.linf[2]};
+    int* my_cand = cand + warp * maskdev::kCandCap;
+    uint32_t* wm = wmask_all + warp * kMaxWaypoints;
+    const long long e_begin = (it - __ldg(item0 + j)) * (long long)span;
+    const long long e_end = min(J.E, e_begin + span);
+    for (;;) {
+      unsigned int t = 0u;
+      if (lane == 0) t = atomicAdd(&s_next, (unsigned int)chunk);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      const long long e0 = e_begin + (long long)t;
+      if (e0 >= e_end) break;
+      const long long e1 = min(e_end, e0 + chunk);
+      for (long long e = e0; e < e1; ++e)
+        maskdev::edge_mask_one<kNP>(e, xp, N, W, J.phi, J.L, J.nom, linf, J.ibox, J.dmax, boxes, nb, w, my_cand, wm,
+                                    lane, J.emask);
+    }
+    __syncthreads();  // the item's edges are done: the staging and the shared counter are reused
+  }
+}
+
 // ---------------------------------------------------------------- Half-Space Monte Carlo
 //
 // Local convex region of waypoint y (nominal position) with nominal velocity v, in the arithmetic
@@ -530,6 +607,83 @@ int compute_edge_masks(pump_graph* g, cudaStream_t s, int pairs, int chunk) {
   if (rc) return rc;
   PUMP_CUDA_TRY(cudaGetLastError());
   g->masks_ready = true;
+  return PUMP_OK;
+}
+
+// Box masks of several graphs in one launch of k_edge_mask_batch (HSMC graphs and graphs without
+// edges take their own path).  span: edges per item (0 = 1024); pairs and chunk as above.
+int compute_edge_masks_batch(pump_graph* const* gs, int nq, cudaStream_t s, int pairs, int chunk, int span) {
+  if (chunk <= 0) chunk = kMaskChunk;
+  if (span <= 0) span = 1024;
+  std::vector<MaskJob> jobs;
+  std::vector<long long> item0(1, 0);
+  std::vector<pump_graph*> done;
+  size_t smem_fixed = 0, smem_xi = 0;
+  for (int q = 0; q < nq; ++q) {
+    pump_graph* g = gs[q];
+    if (g->E == 0 || g->hsmc) {
+      const int rc = compute_edge_masks(g, s, pairs, chunk);
+      if (rc) return rc;
+      continue;
+    }
+    smem_fixed = std::max(smem_fixed, edge_mask_smem(g->N, g->W, g->n_boxes, false));
+    smem_xi = std::max(smem_xi, edge_mask_smem(g->N, g->W, g->n_boxes, true));
+  }
+  // one allocation for every job: the normals of a job stay in shared memory when its staging
+  // fits the launch's (the largest that fits 160 KiB)
+  const size_t smem = smem_xi <= 160 * 1024 ? smem_xi : std::max(smem_fixed, (size_t)160 * 1024);
+  for (int q = 0; q < nq; ++q) {
+    pump_graph* g = gs[q];
+    if (g->E == 0 || g->hsmc) continue;
+    MaskJob J;
+    J.xp = g->xi_p;
+    J.phi = g->phi;
+    J.L = g->L;
+    J.nom = g->nom;
+    J.linf = g->linf_dev;
+    J.ibox = g->ibox;
+    J.dmax = g->dmax;
+    J.boxes = g->boxes;
+    J.emask = g->emask;
+    J.E = g->E;
+    J.N = g->N;
+    J.W = g->W;
+    J.nb = g->n_boxes;
+    J.w = g->n_words;
+    J.xi_smem = edge_mask_smem(g->N, g->W, g->n_boxes, true) <= smem ? 1 : 0;
+    jobs.push_back(J);
+    item0.push_back(item0.back() + (g->E + span - 1) / span);
+    done.push_back(g);
+  }
+  const int nj = (int)jobs.size();
+  if (nj == 0) return PUMP_OK;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_jobs = al(sizeof(MaskJob) * (size_t)nj), b_item = al(sizeof(long long) * (size_t)(nj + 1));
+  unsigned char* buf = (unsigned char*)dev_alloc(b_jobs + b_item + 256, s);
+  if (!buf) return PUMP_ERR_OOM;
+  MaskJob* jobs_dev = reinterpret_cast<MaskJob*>(buf);
+  long long* item0_dev = reinterpret_cast<long long*>(buf + b_jobs);
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(buf + b_jobs + b_item);
+  int rc = PUMP_OK;
+  if (cudaMemcpyAsync(jobs_dev, jobs.data(), sizeof(MaskJob) * nj, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(item0_dev, item0.data(), sizeof(long long) * (nj + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    rc = PUMP_ERR_CUDA;
+  int grid = 1;
+  if (!rc)
+    rc = pairs == 1 ? occupancy_grid(k_edge_mask_batch<1>, smem, 1, item0.back(), &grid)
+                    : occupancy_grid(k_edge_mask_batch<2>, smem, 1, item0.back(), &grid);
+  if (!rc) {
+    if (pairs == 1)
+      k_edge_mask_batch<1><<<grid, kWarps * 32, smem, s>>>(jobs_dev, item0_dev, nj, span, chunk, ctr);
+    else
+      k_edge_mask_batch<2><<<grid, kWarps * 32, smem, s>>>(jobs_dev, item0_dev, nj, span, chunk, ctr);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = PUMP_ERR_CUDA;
+  }
+  dev_free(buf, s);
+  if (rc) return rc;
+  for (pump_graph* g : done) g->masks_ready = true;
   return PUMP_OK;
 }
 

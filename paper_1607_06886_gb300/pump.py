@@ -52,7 +52,7 @@ class Request(C.Structure):
 
 class BatchConfig(C.Structure):
     _fields_ = [("cluster_size", C.c_int32), ("mbest_global", C.c_int32), ("max_clusters", C.c_int32),
-                ("mask_pairs", C.c_int32), ("mask_chunk", C.c_int32)]
+                ("mask_pairs", C.c_int32), ("mask_chunk", C.c_int32), ("mask_span", C.c_int32)]
 
 
 class PlanResult(C.Structure):

@@ -26,12 +26,13 @@ def test_tune_picks_fastest_and_caches(tmp_path, monkeypatch):
     timing = {(16, 0): 5.0, (16, 1): 4.0, (8, 0): 3.0, (8, 1): 3.5, (4, 0): 6.0}
     calls = []
 
-    mask_timing = {(2, 4): 7.0, (2, 1): 8.0, (2, 16): 6.5, (1, 4): 9.0}
+    mask_timing = {(2, 4, 1024): 7.0, (2, 1, 1024): 8.0, (2, 4, 512): 7.5, (2, 4, 2048): 6.0, (2, 16, 1024): 6.5,
+                   (1, 4, 1024): 9.0}
 
     def fake_batch(graphs, params, cfg=None, stream=None):
         calls.append((cfg.cluster_size, cfg.mbest_global))
         assert all(p.flags & pump.EXPLORE_ONLY for p in params)
-        mk = mask_timing.get((cfg.mask_pairs, cfg.mask_chunk), 10.0)
+        mk = mask_timing.get((cfg.mask_pairs, cfg.mask_chunk, cfg.mask_span), 10.0)
         return pump.OK, [{"ms_explore": timing[(cfg.cluster_size, cfg.mbest_global)], "ms_masks": mk} for _ in graphs]
 
     monkeypatch.setattr(pump, "plan_batch", fake_batch)
@@ -39,14 +40,16 @@ def test_tune_picks_fastest_and_caches(tmp_path, monkeypatch):
     prm = pump.default_plan_params(alpha=0.01)
     cfg, rec = autotune.tune_batch(gs, prm, reps=1)
     assert (cfg.cluster_size, cfg.mbest_global) == (8, 0)
-    assert (cfg.mask_pairs, cfg.mask_chunk) == (2, 16)  # the mask form, timed with the chosen Explore form
-    assert rec["mask_ms"]["1/4"] == 9.0
+    # the mask form, timed with the chosen Explore form
+    assert (cfg.mask_pairs, cfg.mask_chunk, cfg.mask_span) == (2, 4, 2048)
+    assert rec["mask_ms"]["1/4/1024"] == 9.0
     assert prm.flags & pump.EXPLORE_ONLY == 0          # caller's params untouched
     stored = json.loads((tmp_path / "tune.json").read_text())
     assert stored[autotune.batch_key(gs)]["cluster_size"] == 8
     n_calls = len(calls)
     cfg2, _ = autotune.tune_batch(gs, prm, reps=1)     # cached: no timing
-    assert len(calls) == n_calls and cfg2.cluster_size == 8 and (cfg2.mask_pairs, cfg2.mask_chunk) == (2, 16)
+    assert len(calls) == n_calls and cfg2.cluster_size == 8
+    assert (cfg2.mask_pairs, cfg2.mask_chunk, cfg2.mask_span) == (2, 4, 2048)
 
 
 def test_tune_skips_failing_forms(tmp_path, monkeypatch):

@@ -1,9 +1,11 @@
-"""pump_plan_batch: many queries in one persistent Explore launch.  Each query's result must equal
-the single-query result (pump_plan on the same graph) bit for bit: counters, the whole plan arena,
-P_goal, the selected plan and its Monte Carlo count.  One batch is also checked against the CPU
-oracle directly.  Covers the launch forms (cluster sizes 16, 8, 4; dominance table on chip and in
-global memory; fewer clusters than queries; mask passes of one or two word pairs and 1 to 64
-edges per take), explore-only queries mixed with full ones, and the argument checks."""
+"""pump_plan_batch: the box masks of many queries in one persistent launch, their Explore runs in
+another.  Each query's result must equal the single-query result (pump_plan on the same graph) bit
+for bit: counters, the whole plan arena, P_goal, the selected plan and its Monte Carlo count.  One
+batch is also checked against the CPU oracle directly.  Covers the launch forms (cluster sizes 16,
+8, 4; dominance table on chip and in global memory; fewer clusters than queries; mask passes of
+one or two word pairs, 1 to 64 edges per warp take and 32 to 4096 edges per block item; graphs of
+different particle and box counts in one mask launch; an HSMC graph beside box graphs),
+explore-only queries mixed with full ones, and the argument checks."""
 import numpy as np
 import pytest
 
@@ -52,11 +54,12 @@ def check_same(ref, ref_arena, res, G):
         np.testing.assert_array_equal(arena[k], v, err_msg=k)
 
 
-@pytest.mark.parametrize("cfg", [None, (16, 0, 0, 0, 0), (8, 0, 0, 1, 1), (4, 0, 2, 2, 16), (16, 1, 0, 1, 64),
-                                 (8, 1, 3, 2, 3)])
+@pytest.mark.parametrize("cfg", [None, (16, 0, 0, 0, 0), (8, 0, 0, 1, 1, 32), (4, 0, 2, 2, 16, 4096),
+                                 (16, 1, 0, 1, 64, 96), (8, 1, 3, 2, 3, 256)])
 def test_batch_equals_single_queries(queries, cfg):
     """Every launch form (Explore: CTAs per query, table placement, clusters in flight; masks: word
-    pairs per warp pass, edges per take) gives the single-query results."""
+    pairs per warp pass, edges per warp take, edges per block item) gives the single-query
+    results."""
     config = None if cfg is None else pump.BatchConfig(*cfg)
     rc, res = pump.plan_batch([q[1] for q in queries], [q[2] for q in queries], config)
     assert rc in (pump.OK, pump.ERR_INFEASIBLE)
@@ -111,7 +114,8 @@ def test_batch_rejects_bad_arguments(queries):
     rc, _ = pump.plan_batch([G0, G0], [p0, p0])
     assert rc == pump.ERR_INVALID_ARG
     for bad in [(3, 0, 0, 0, 0), (32, 0, 0, 0, 0), (0, 2, 0, 0, 0), (0, 0, -1, 0, 0), (0, 0, 0, 3, 0),
-                (0, 0, 0, -1, 0), (0, 0, 0, 0, 65), (0, 0, 0, 0, -2)]:
+                (0, 0, 0, -1, 0), (0, 0, 0, 0, 65), (0, 0, 0, 0, -2), (0, 0, 0, 0, 0, -32), (0, 0, 0, 0, 0, 48),
+                (0, 0, 0, 0, 0, 65568)]:
         rc, _ = pump.plan_batch([G0, G1], [p0, queries[1][2]], pump.BatchConfig(*bad))
         assert rc == pump.ERR_INVALID_ARG, bad
     g = inputs.random_explore_graph(20, 3, 32, 0)
@@ -121,3 +125,20 @@ def test_batch_rejects_bad_arguments(queries):
     bad_p = pump.default_plan_params(alpha=0.01, lam=2.0)
     rc, _ = pump.plan_batch([G0], [bad_p])
     assert rc == pump.ERR_INVALID_ARG
+
+
+def test_batch_with_an_hsmc_graph(queries):
+    """An HSMC graph takes its own mask pass beside the box graphs' shared launch; every result
+    equals its single query."""
+    wl = inputs.make_workload("indoor_4k", 21, 300)
+    Gh = pump.Graph.build(wl.states, wl.goal_idx, wl.boxes, wl.xi, wl.radius, wl.n_particles, wl.n_waypoints,
+                          wl.sigma, flags=pump.GRAPH_HSMC)
+    ph = plan_params(wl, n_mc=2000)
+    refh = Gh.plan(ph)
+    arh = export_arena(Gh)
+    sel = [queries[0], queries[1], queries[3]]
+    rc, res = pump.plan_batch([sel[0][1], Gh, sel[1][1], sel[2][1]], [sel[0][2], ph, sel[1][2], sel[2][2]])
+    assert rc in (pump.OK, pump.ERR_INFEASIBLE)
+    check_same(refh, arh, res[1], Gh)
+    for (wl_, G, prm, ref, ref_arena), r in zip(sel, [res[0], res[2], res[3]]):
+        check_same(ref, ref_arena, r, G)
