@@ -755,6 +755,28 @@ def roofline_measure(pump, G, prm, wl, dev, flush, steps, fused_ms=None):
     bytes_expl = float(st["n_candidates"]) * (4 + 4 + 4 * w + 4) + float(st["n_plans"]) * (28 + 4 * w)
     hbm = float(peaks["hbm_gbs"])
     expl_gbs = bytes_expl / (ms_expl / 1e3) / 1e9
+    # ablation: the masks recomputed per (plan, edge) pair, as an expansion that evaluates the
+    # collision probability per candidate does (the library computes each edge's mask once per
+    # query); the pairs are this run's candidates, every out-edge of every expanded plan
+    heads, expd, rp = G.export("plan_head"), G.export("plan_expanded"), G.export("row_ptr")
+    pairs = np.concatenate([np.arange(rp[h], rp[h + 1], dtype=np.int32) for h in heads[expd >= 0]])
+    assert len(pairs) == int(st["n_candidates"]), (len(pairs), st["n_candidates"])
+    ed = torch.from_numpy(pairs).to(dev)
+    out_rows = torch.empty((len(pairs), w), dtype=torch.int32, device=dev)
+    bad = torch.zeros(1, dtype=torch.int32, device=dev)
+    t = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rc = G.edge_masks_list(ed.data_ptr(), len(pairs), out_rows.data_ptr(), bad.data_ptr())
+        b.record(stream)
+        assert rc == pump.OK, rc
+        t.append((a, b))
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 0
+    ms_pairs = float(np.mean([a.elapsed_time(b) for a, b in t]))
+    del ed, out_rows, bad
     detail = {
         "edge_mask": {"ms": ms_mask, "bound": "alu", "ops": ops_mask, "live_edges": int(live.sum()), "edges": E,
                       "achieved_tops": ops_mask / (ms_mask / 1e3) / 1e12, "peak_tops": alu_peak / 1e12,
@@ -762,6 +784,10 @@ def roofline_measure(pump, G, prm, wl, dev, flush, steps, fused_ms=None):
         "explore": {"ms": ms_expl, "bound": "hbm", "bytes": bytes_expl, "achieved_gbs": expl_gbs, "peak_gbs": hbm,
                     "frac": expl_gbs / hbm, "iterations": st["n_iterations"],
                     "traffic": measured_traffic("k_explore_cluster")},
+        "per_pair_masks": {"pairs": int(len(pairs)), "edges": E, "ms": ms_pairs, "ms_per_edge_memo": ms_mask,
+                           "ratio": ms_pairs / ms_mask,
+                           "what": "ablation: every candidate (plan, edge) pair's mask recomputed "
+                                   "(pump_edge_masks_list over the run's candidates) against one mask per edge"},
     }
     if fused_ms:
         # one launch does both: the mask workers' lane operations are its throughput work, and

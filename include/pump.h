@@ -198,6 +198,22 @@ int pump_graph_from_csr(int32_t n, const int32_t* row_ptr, const int32_t* col, c
  */
 int pump_edge_masks(pump_graph* g, void* stream);
 
+/* pump_edge_masks_list: the same masks for a list of edges, repeats allowed:
+ * row j of out_masks (device, n x N/32 words, caller-owned) is the mask of
+ * edge edges[j] (device int32 ids in [0, E)).  This is the per-(plan, edge)
+ * recomputation that an expansion performs when it evaluates the collision
+ * probability per candidate, as Algorithm 4's expansion is written; the
+ * library's own path computes each edge's mask once per query instead (a
+ * mask does not depend on the plan).  The call exists for that comparison
+ * and for callers that want candidate masks directly.  Box graphs only.
+ * An id outside [0, E) leaves its row untouched and is counted in *bad_ids
+ * (device uint32, caller-owned, zeroed by the call; may be NULL).  Enqueued on
+ * `stream`, no synchronisation.  Errors: INVALID_ARG (NULL, imported or HSMC
+ * graph, n < 0), OOM, CUDA.
+ */
+int pump_edge_masks_list(pump_graph* g, const int32_t* edges, int64_t n, uint32_t* out_masks, uint32_t* bad_ids,
+                         void* stream);
+
 /* --------------------------------------------------------------------------
  * pump_explore: Explore (Algorithm 4) on the graph's current edge masks.
  * Starts from the root plan (x_init, {}, 0, 0); groups G_i = open plans with

@@ -257,6 +257,49 @@ __global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS)
   }
 }
 
+// Masks of a list of edges (repeats allowed): row j of out = the mask of edge elist[j], the
+// per-(plan, edge) recomputation an expansion performs without the per-edge memo.  Warps take list
+// positions from a counter like k_edge_mask; an id outside [0, E) leaves its row untouched and
+// counts in *bad.
+template <bool kSmemXi>
+__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS)
+    k_edge_mask_list(const float4* __restrict__ xp_g, int N, int W, const float* __restrict__ phi,
+                     const float* __restrict__ Lg, const float* __restrict__ nom, const float* __restrict__ linf_g,
+                     const float* __restrict__ ibox_g, const unsigned int* __restrict__ dmax,
+                     const float* __restrict__ boxes_g, int nb, int E, int w, const int32_t* __restrict__ elist,
+                     long long n, unsigned long long* __restrict__ ctr, int chunk, uint32_t* __restrict__ out,
+                     unsigned int* __restrict__ bad) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* boxes = reinterpret_cast<float*>(smem);
+  int* cand = reinterpret_cast<int*>(boxes + kBoxStride * nb);
+  uint32_t* wmask_all = reinterpret_cast<uint32_t*>(cand + kWarps * maskdev::kCandCap);
+  float4* xp_s = reinterpret_cast<float4*>(smem + edge_mask_fixed_smem(nb));
+  const int xp_n = (W + 1) * 3 * maskdev::pair_count(w) * 32;
+  maskdev::stage(boxes_g, nb, boxes, xp_g, kSmemXi ? xp_s : nullptr, xp_n);
+  __syncthreads();
+  const float4* xp = kSmemXi ? xp_s : xp_g;
+  const float linf[3] = {linf_g[0], linf_g[1], linf_g[2]};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* my_cand = cand + warp * maskdev::kCandCap;
+  uint32_t* wm = wmask_all + warp * kMaxWaypoints;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(ctr, (unsigned long long)chunk);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= (unsigned long long)n) break;
+    const long long j1 = min(n, (long long)t + chunk);
+    for (long long j = (long long)t; j < j1; ++j) {
+      const int32_t e = __ldg(elist + j);
+      if (e < 0 || e >= E) {
+        if (lane == 0) atomicAdd(bad, 1u);
+        continue;
+      }
+      maskdev::edge_mask_one<2>(e, xp, N, W, phi, Lg, nom, linf, ibox_g, dmax, boxes, nb, w, my_cand, wm, lane, out,
+                                0, -1, j);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- Half-Space Monte Carlo
 //
 // Local convex region of waypoint y (nominal position) with nominal velocity v, in the arithmetic
@@ -608,6 +651,41 @@ int compute_edge_masks(pump_graph* g, cudaStream_t s, int pairs, int chunk) {
   PUMP_CUDA_TRY(cudaGetLastError());
   g->masks_ready = true;
   return PUMP_OK;
+}
+
+// Masks of n listed edges into out (n x w words); *bad (device, may be null) counts ids outside
+// [0, E).  Enqueued only.
+int compute_edge_masks_list(pump_graph* g, const int32_t* elist, long long n, uint32_t* out, uint32_t* bad,
+                            cudaStream_t s) {
+  const size_t smem_xi = edge_mask_smem(g->N, g->W, g->n_boxes, true);
+  const bool use_smem = smem_xi <= 160 * 1024;
+  const size_t smem = use_smem ? smem_xi : edge_mask_smem(g->N, g->W, g->n_boxes, false);
+  // the list's take counter, and a count of bad ids when the caller keeps none
+  unsigned long long* scratch = (unsigned long long*)dev_alloc(2 * sizeof(unsigned long long), s);
+  if (!scratch) return PUMP_ERR_OOM;
+  unsigned int* badc = bad ? bad : reinterpret_cast<unsigned int*>(scratch + 1);
+  int rc = PUMP_OK;
+  if (cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess ||
+      (bad && cudaMemsetAsync(bad, 0, sizeof(unsigned int), s) != cudaSuccess))
+    rc = PUMP_ERR_CUDA;
+  int grid = 1;
+  if (!rc && n > 0)
+    rc = use_smem ? occupancy_grid(k_edge_mask_list<true>, smem, kWarps * (long long)kMaskChunk, n, &grid)
+                  : occupancy_grid(k_edge_mask_list<false>, smem, kWarps * (long long)kMaskChunk, n, &grid);
+  if (!rc && n > 0) {
+    if (use_smem)
+      k_edge_mask_list<true><<<grid, kWarps * 32, smem, s>>>(g->xi_p, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
+                                                             g->ibox, g->dmax, g->boxes, g->n_boxes, (int)g->E,
+                                                             g->n_words, elist, n, scratch, kMaskChunk, out, badc);
+    else
+      k_edge_mask_list<false><<<grid, kWarps * 32, smem, s>>>(g->xi_p, g->N, g->W, g->phi, g->L, g->nom, g->linf_dev,
+                                                              g->ibox, g->dmax, g->boxes, g->n_boxes, (int)g->E,
+                                                              g->n_words, elist, n, scratch, kMaskChunk, out, badc);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = PUMP_ERR_CUDA;
+  }
+  dev_free(scratch, s);
+  return rc;
 }
 
 // Box masks of several graphs in one launch of k_edge_mask_batch (HSMC graphs and graphs without

@@ -263,13 +263,15 @@ __device__ __forceinline__ void stage(const float* __restrict__ boxes_g, int nb,
 // kMaxNP word pairs side by side per pass: fewer live registers with 1).  With [p_first, p_last)
 // only those word pairs are computed (an edge with no box left still gets all its words zeroed).
 // my_cand (kCandCap ints) and wm (kMaxWaypoints words) are the warp's shared-memory scratch.
+// The words go to row `row` of mask (row < 0: row e).
 template <int kMaxNP = 2>
 __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restrict__ xp, int N, int W,
                                               const float* __restrict__ phi, const float* __restrict__ Lg,
                                               const float* __restrict__ nom, const float (&linf)[3],
                                               const float* __restrict__ ibox_g, const unsigned int* __restrict__ dmax,
                                               const float* boxes, int nb, int w, int* my_cand, uint32_t* wm, int lane,
-                                              uint32_t* __restrict__ mask, int p_first = 0, int p_last = -1) {
+                                              uint32_t* __restrict__ mask, int p_first = 0, int p_last = -1,
+                                              long long row = -1) {
   const float* ib = ibox_g + 6 * e;
   const float lo0 = ib[0], lo1 = ib[1], lo2 = ib[2], hi0 = ib[3], hi1 = ib[4], hi2 = ib[5];
   int n_cand = 0;
@@ -287,7 +289,7 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
   }
   __syncwarp();
   if (n_cand == 0) {
-    for (int word = lane; word < w; word += 32) mask[(size_t)e * w + word] = 0u;
+    for (int word = lane; word < w; word += 32) mask[(size_t)(row < 0 ? e : row) * w + word] = 0u;
     __syncwarp();
     return;
   }
@@ -317,7 +319,7 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
     __syncwarp();
   }
   if (k_last == 0) {
-    for (int word = lane; word < w; word += 32) mask[(size_t)e * w + word] = 0u;
+    for (int word = lane; word < w; word += 32) mask[(size_t)(row < 0 ? e : row) * w + word] = 0u;
     __syncwarp();
     return;
   }
@@ -328,7 +330,7 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
   const unsigned long long I2[3] = {pk2(linf[0], linf[0]), pk2(linf[1], linf[1]), pk2(linf[2], linf[2])};
   const int npair = pair_count(w);
   const int pe = p_last < 0 ? npair : min(p_last, npair);
-  uint32_t* out = mask + (size_t)e * w;
+  uint32_t* out = mask + (size_t)(row < 0 ? e : row) * w;
   int p = p_first;
   if (kMaxNP >= 2)
     for (; p + 2 <= pe; p += 2)

@@ -500,6 +500,13 @@ int pump_edge_masks(pump_graph* g, void* stream) {
   return compute_edge_masks(g, (cudaStream_t)stream);
 }
 
+int pump_edge_masks_list(pump_graph* g, const int32_t* edges, int64_t n, uint32_t* out_masks, uint32_t* bad_ids,
+                         void* stream) {
+  if (!g || !g->has_geometry || g->hsmc || n < 0 || (n > 0 && (!edges || !out_masks))) return PUMP_ERR_INVALID_ARG;
+  if (g->E > INT32_MAX) return PUMP_ERR_INVALID_ARG;
+  return compute_edge_masks_list(g, edges, (long long)n, out_masks, bad_ids, (cudaStream_t)stream);
+}
+
 int pump_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* stats, void* stream) {
   if (!g || !stats || check_plan_params(p)) return PUMP_ERR_INVALID_ARG;
   if (!g->masks_ready) return PUMP_ERR_INVALID_ARG;

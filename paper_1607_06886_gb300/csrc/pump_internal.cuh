@@ -223,6 +223,8 @@ int row_order_end(pump_graph* g, cudaStream_t s);
 int build_halfspaces(pump_graph* g, cudaStream_t s);
 constexpr int kHsMax = 8;  // half-spaces per waypoint (HSMC)
 int compute_edge_masks(pump_graph* g, cudaStream_t s, int pairs = 0, int chunk = 0);
+int compute_edge_masks_list(pump_graph* g, const int32_t* elist, long long n, uint32_t* out, uint32_t* bad,
+                            cudaStream_t s);
 int compute_edge_masks_batch(pump_graph* const* gs, int nq, cudaStream_t s, int pairs = 0, int chunk = 0, int span = 0);
 int compute_edge_bounds(pump_graph* g, cudaStream_t s);
 int run_explore(pump_graph* g, const pump_plan_params* p, float radius, pump_plan_result* stats,

@@ -100,6 +100,7 @@ def load(build_if_missing: bool = False):
     L.pump_build_graph.argtypes = [P, i32, i32, P, i32, P, i32, P, C.POINTER(GraphParams), P, C.POINTER(P)]
     L.pump_graph_from_csr.argtypes = [i32, P, P, P, P, i32, i32, P, i32, P, C.POINTER(P)]
     L.pump_edge_masks.argtypes = [P, P]
+    L.pump_edge_masks_list.argtypes = [P, P, C.c_int64, P, P, P]
     L.pump_explore.argtypes = [P, C.POINTER(PlanParams), f32, C.POINTER(PlanResult), P]
     L.pump_plan.argtypes = [P, C.POINTER(PlanParams), P, i32, C.POINTER(PlanResult), P]
     L.pump_plan_collect.argtypes = [P, C.POINTER(PlanResult), P]
@@ -447,6 +448,13 @@ class Graph:
         rc = load().pump_edge_masks(self._h, current_stream() if stream is None else stream)
         if rc:
             raise PumpError(rc, "pump_edge_masks")
+
+    def edge_masks_list(self, edges_ptr: int, n: int, out_ptr: int, bad_ptr: int = 0,
+                        stream: Optional[int] = None) -> int:
+        """pump_edge_masks_list on device buffers (int32 edge ids, n x N/32 uint32 rows, optional uint32
+        count of bad ids); returns the status."""
+        return load().pump_edge_masks_list(self._h, C.c_void_p(edges_ptr), int(n), C.c_void_p(out_ptr),
+                                           C.c_void_p(bad_ptr or None), current_stream() if stream is None else stream)
 
     def explore(self, params: PlanParams, radius: float = 0.0, stream: Optional[int] = None) -> Dict:
         res = PlanResult()

@@ -49,6 +49,7 @@ def test_invalid_arguments_rejected_before_any_device_work():
     assert lib.pump_plan_collect(None, None, None) == pump.ERR_INVALID_ARG
     assert lib.pump_explore(None, None, 1.0, None, None) == pump.ERR_INVALID_ARG
     assert lib.pump_edge_masks(None, None) == pump.ERR_INVALID_ARG
+    assert lib.pump_edge_masks_list(None, None, 0, None, None, None) == pump.ERR_INVALID_ARG
     n = ctypes.c_size_t()
     assert lib.pump_export(None, 0, None, 0, ctypes.byref(n)) == pump.ERR_INVALID_ARG
     lib.pump_graph_destroy(None)
