@@ -91,68 +91,6 @@ __device__ __forceinline__ void dev_step2(const unsigned long long* P2, const un
   d1 = e1;
 }
 
-// NW mask words of one edge: lane l advances particles 32 (w0 + j) + l, j < NW, side by side
-// through waypoints 1..k_last and tests the boxes left at each; the words are the warp ballots.
-// The warp stops early once every lane's particles have hit.
-template <int NW>
-__device__ __forceinline__ void word_pass(const float2* __restrict__ xi, int N, int W, const float (&P)[4],
-                                          const float (&L)[3], const float (&linf)[3], const float* __restrict__ nm,
-                                          int k_last, bool narrow, const uint32_t* wm, const int* my_cand, bool all,
-                                          int nc, const float* boxes, int w0, int lane, uint32_t* out) {
-  float d0[NW][3], d1[NW][3];
-  bool hit[NW];
-  const float2* xq = xi + w0 * 32 + lane;
-#pragma unroll
-  for (int j = 0; j < NW; ++j) {
-    hit[j] = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dev_init(linf, xq[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
-  }
-  for (int k = 1; k <= k_last; ++k) {
-    const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
-    const float2* xk = xq + (size_t)k * 3 * N;
-    float p[NW][3];
-#pragma unroll
-    for (int j = 0; j < NW; ++j) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) dev_step(P, L, xk[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
-      p[j][0] = __fadd_rn(n0, d0[j][0]);
-      p[j][1] = __fadd_rn(n1, d0[j][1]);
-      p[j][2] = __fadd_rn(n2, d0[j][2]);
-    }
-    unsigned bits = narrow ? wm[k - 1] : 0u;
-    int c = 0;
-    for (;;) {
-      int o;
-      if (narrow) {
-        if (!bits) break;
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        o = my_cand[b];
-      } else {
-        if (c >= nc) break;
-        o = all ? c : my_cand[c];
-        ++c;
-      }
-      const float4 b0 = *reinterpret_cast<const float4*>(boxes + kBoxStride * o);      // lo x, y, z, hi x
-      const float2 b1 = *reinterpret_cast<const float2*>(boxes + kBoxStride * o + 4);  // hi y, z
-#pragma unroll
-      for (int j = 0; j < NW; ++j)
-        hit[j] = hit[j] || (b0.x <= p[j][0] && p[j][0] <= b0.w && b0.y <= p[j][1] && p[j][1] <= b1.x &&
-                            b0.z <= p[j][2] && p[j][2] <= b1.y);
-    }
-    bool done = true;
-#pragma unroll
-    for (int j = 0; j < NW; ++j) done = done && hit[j];
-    if (__all_sync(0xffffffffu, done)) break;
-  }
-#pragma unroll
-  for (int j = 0; j < NW; ++j) {
-    const unsigned bits = __ballot_sync(0xffffffffu, hit[j]);
-    if (lane == 0) out[w0 + j] = bits;
-  }
-}
-
 // Pair-major normals.  xi_p[((k * 3 + a) * npair + jp) * 32 + l] = (xi0 of particle 64 jp + l,
 // xi0 of particle 64 jp + 32 + l, xi1 of the first, xi1 of the second) for waypoint step k, axis
 // a: one 16-byte load gives a lane both halves of its particle pair (zeros past N).
