@@ -104,6 +104,19 @@ __device__ __forceinline__ int64_t ld64(const int64_t* p) { return __ldcg(reinte
 __device__ __forceinline__ float ldf(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ uint32_t ldu(const uint32_t* p) { return __ldcg(p); }
 
+// Asynchronous global -> shared copies (no register staging; the issuing thread waits for its own
+// copies with cp_async_wait, and a barrier after that makes them visible to the CTA).
+template <int kBytes>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  if constexpr (kBytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src), "n"(kBytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Launch shape a cluster kernel was sized for on the host: CTAs per cluster (the on-chip
 // dominance table is partitioned over exactly that many CTAs) and dynamic shared memory bytes.
 struct LaunchShape {
@@ -186,6 +199,9 @@ struct CSmem {
   uint32_t odg[kOCap];
   float ocost[kOCap];
   int16_t opc[kOCap];
+  // an older plan's record, copied in during phase A (cp.async) when the arena keeps plan rows
+  int32_t opf[kOCap], otc[kOCap];  // popcount, creation index
+  int2 orw[kOCap];                  // row start, degree | goal bit
   Pub pub;     // this CTA's counts (accumulated in phase B)
   Pub pub_all[kMaxCluster];  // every CTA's counts (copied here by their owners at the end of phase B)
   PubS pubs_s; // the same for a group index beyond the window (read remotely in phase C)
@@ -523,6 +539,32 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
   }
   if (threadIdx.x == 0) sm->pub.stop = 0;
   if (threadIdx.x < kThr) sm->thr[threadIdx.x] = group_thr(S.i + (int32_t)threadIdx.x, A.lr);
+  // the older plans phase B re-tests: their records copied into shared memory now, behind the
+  // expansion, so that phase B only looks up their dominance (the same decision as phase B's)
+  const bool pf = A.prow != nullptr && S.a1 - S.a0 <= kOCap;
+  if (pf) {
+    const int no = (int)(S.a1 - S.a0);
+    for (int o = threadIdx.x; o < no; o += kCT) {
+      const int64_t p = S.a0 + o;
+      cp_async<4>(&sm->ox[o], A.head + p);
+      cp_async<4>(&sm->ocost[o], A.cost + p);
+      cp_async<4>(&sm->opf[o], A.popc + p);
+      cp_async<4>(&sm->otc[o], A.tcre + p);
+      cp_async<8>(&sm->orw[o], A.prow + p);
+      if (A.w == 4) {
+        cp_async<16>(&sm->omask[o], A.mask + (size_t)p * 4);
+      } else if (A.w < 4) {
+        uint32_t* om = reinterpret_cast<uint32_t*>(&sm->omask[o]);
+        for (int j = 0; j < 4; ++j) {
+          if (j < A.w)
+            cp_async<4>(om + j, A.mask + (size_t)p * A.w + j);
+          else
+            om[j] = 0u;
+        }
+      }
+    }
+    cp_async_commit();
+  }
   for (int64_t s = (int64_t)r * kCT + threadIdx.x; s < S.g; s += (int64_t)nr * kCT)
     A.eexp[ld32(&A.ginfo[s].x)] = S.i;
   const int64_t c0 = S.c0, c1 = S.c1;
@@ -647,11 +689,26 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
       }
     }
   }
+  if (pf) cp_async_wait();  // the barriers that close the phase publish the copies to the CTA
   kept = csum_ll(kept);
   if (threadIdx.x == 0) sm->kept += kept;
 }
 
-// Older plan p: its group index if open and undominated, else -1 (see the header on older plans).
+// Group index of an older plan (head x, cost c, popcount pc, created in group t) if it is open and
+// undominated, else -1 (see the header on older plans).
+template <bool kDsm>
+__device__ __forceinline__ int32_t old_eff_vals(const ExploreArgs& A, const CSmem* sm, cg::cluster_group& cl,
+                                                uint32_t* mbl, int32_t x, float c, int32_t pc, int32_t t, int32_t i) {
+  // bucket(c) <= i iff c <= thr_i; above it the table gives the bucket
+  const int32_t b = c <= sm->thr[0] ? (t + 1 <= i ? -1 : bucket_far(c, A.lr)) : bucket_gt(sm, A, i, c, 0);
+  if (b < 0) return -1;
+  const int32_t eff = max(b, t + 1);
+  if (eff <= i) return -1;
+  if (dominated_c<kDsm>(A, cl, mbl, x, pc, c)) return -1;
+  return eff;
+}
+
+// Older plan p: its group index if open and undominated, else -1.
 template <bool kDsm>
 __device__ __forceinline__ int32_t old_eff_c(const ExploreArgs& A, const CSmem* sm, cg::cluster_group& cl,
                                              uint32_t* mbl, int64_t p, int32_t i, int32_t* x_out, float* c_out,
@@ -663,13 +720,7 @@ __device__ __forceinline__ int32_t old_eff_c(const ExploreArgs& A, const CSmem* 
   *x_out = x;
   *c_out = c;
   *pc_out = pc;
-  // bucket(c) <= i iff c <= thr_i; above it the table gives the bucket
-  const int32_t b = c <= sm->thr[0] ? (t + 1 <= i ? -1 : bucket_far(c, A.lr)) : bucket_gt(sm, A, i, c, 0);
-  if (b < 0) return -1;
-  const int32_t eff = max(b, t + 1);
-  if (eff <= i) return -1;
-  if (dominated_c<kDsm>(A, cl, mbl, x, pc, c)) return -1;
-  return eff;
+  return old_eff_vals<kDsm>(A, sm, cl, mbl, x, c, pc, t, i);
 }
 
 // ---------------------------------------------------------------- phase B
@@ -704,6 +755,25 @@ template <bool kDsm>
 __device__ __forceinline__ void filter_old(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl,
                                            const St& S, int64_t p, int64_t a0, bool ofits, int32_t& minb,
                                            int32_t& min_open, int32_t& eff, int32_t& pc, int32_t& deg, bool& goal) {
+  if (A.prow != nullptr && ofits) {
+    // the record was copied into shared memory during phase A
+    const int o = (int)(p - a0);
+    const int32_t x = sm->ox[o], pcp = sm->opf[o];
+    const int2 rw = sm->orw[o];
+    eff = old_eff_vals<kDsm>(A, sm, cl, mbl, x, sm->ocost[o], pcp, sm->otc[o], S.i);
+    pc = pcp;
+    sm->oeff[o] = eff;
+    if (eff >= 0) {
+      deg = (int32_t)((uint32_t)rw.y & ~kGoalBit);
+      goal = ((uint32_t)rw.y & kGoalBit) != 0;
+      minb = min(minb, eff);
+      min_open = min(min_open, (int32_t)p);
+      sm->or0[o] = rw.x;
+      sm->odg[o] = (uint32_t)rw.y;
+      sm->opc[o] = (int16_t)pcp;
+    }
+    return;
+  }
   int32_t x = 0, r0 = 0;
   float c = 0.f;
   // the plan's row, goal flag and mask are loaded with its record, before the dominance test
@@ -975,6 +1045,7 @@ __device__ __forceinline__ uint4 put_survivor(const ExploreArgs& A, CSmem* sm, i
   A.popc[id] = q.pc;
   A.tcre[id] = i;
   A.eexp[id] = -1;
+  if (A.prow) A.prow[id] = make_int2(q.r0, (int32_t)q.dg);
   uint32_t* om = A.mask + (size_t)id * A.w;
   uint4 m = make_uint4(0u, 0u, 0u, 0u);
   if (cached && A.w <= 4) {

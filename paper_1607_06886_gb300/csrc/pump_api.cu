@@ -120,8 +120,9 @@ int ensure_explore_bufs(pump_graph* g, int64_t cap, int32_t kmax, cudaStream_t s
     X.goff = (int64_t*)graph_realloc(g, X.goff, sizeof(int64_t) * (cap + 1), s);
     X.goal_all = (int32_t*)graph_realloc(g, X.goal_all, sizeof(int32_t) * cap, s);
     X.goal_sorted = (int32_t*)graph_realloc(g, X.goal_sorted, sizeof(int32_t) * cap, s);
+    X.prow = (int2*)graph_realloc(g, X.prow, sizeof(int2) * cap, s);
     if (!X.head || !X.parent || !X.pedge || !X.tcre || !X.eexp || !X.cost || !X.popc || !X.mask || !X.group ||
-        !X.ginfo || !X.goff || !X.goal_all || !X.goal_sorted) {
+        !X.ginfo || !X.goff || !X.goal_all || !X.goal_sorted || !X.prow) {
       X.cap = 0;
       return PUMP_ERR_OOM;
     }
@@ -202,6 +203,7 @@ int prepare_explore_args(pump_graph* g, const pump_plan_params* p, float radius,
   A.bcnt = X.bcnt;
   A.bdeg = X.bdeg;
   A.goal_all = X.goal_all;
+  A.prow = X.prow;
   A.ctl = X.ctl;
   A.spin_limit = 20000000ll;
   A.kstride = std::max(kmax, 1);

@@ -93,6 +93,7 @@ struct ExploreArgs {
   int4* ginfo;      // per group slot: plan id, head node, row start, cost bits
   int64_t* goff;    // group_size + 1 candidate offsets
   const int4* etgt; // per edge: target node, cost bits, target row start, degree | goal bit (or null)
+  int2* prow = nullptr;  // per plan: its head's row start, degree | goal bit (cluster forms; or null)
   int32_t* bcnt;    // per-block survivor / selection counts
   int64_t* bdeg;    // per-block degree sums
   int32_t* goal_all;
@@ -127,6 +128,7 @@ struct ExploreBufs {
   int64_t* bdeg = nullptr;
   int32_t* goal_all = nullptr;
   int32_t* goal_sorted = nullptr;
+  int2* prow = nullptr;
   ExploreCtl* ctl = nullptr;
   // selection / certification scratch
   void* sel_state = nullptr;      // bisection state
@@ -420,6 +422,7 @@ __device__ __forceinline__ void explore_init_thread(const ExploreArgs& A, int32_
   const int64_t d0 = A.row_ptr[start + 1] - A.row_ptr[start];
   A.goff[0] = 0;
   A.goff[1] = d0;
+  if (A.prow) A.prow[0] = make_int2(A.row_ptr[start], (int32_t)((uint32_t)d0 | (A.is_goal[start] ? 0x80000000u : 0u)));
   c->n_plans = 1;
   c->n_candidates = 0;
   c->n_kept = 0;
