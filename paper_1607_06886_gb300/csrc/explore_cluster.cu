@@ -153,6 +153,7 @@ struct alignas(16) Pub {
   int32_t err;       // a wait for a row's masks ran out (fused form)
 };
 constexpr int kPubVec = (int)(sizeof(Pub) / 16);
+constexpr int kPubErrWord = (int)(offsetof(Pub, err) / 4);  // 32-bit word of the error flag
 static_assert(sizeof(Pub) % 16 == 0, "Pub copies as 16-byte words");
 // Counts for one group index beyond the window (extra round).
 struct PubS {
@@ -210,7 +211,7 @@ struct CSmem {
   int32_t werr;        // this CTA: a wait for a row's masks ran out (fused form)
   int32_t rows_ready;  // this CTA saw every worker warp finished: no more waits (fused form)
   int32_t ready_row;   // a row whose masks are complete from the first group on, or -1 (fused form)
-  long long b_dbefore_o, b_dtotal_o, b_dbefore_n, b_dtotal_n, b_per_n;
+  long long b_dbefore_o, b_dtotal_o, b_dbefore_n, b_dtotal_n;
   ExploreArgs args;  // the query's arguments (batched form)
   int32_t qnext;     // query index taken by the cluster (batched form; written by CTA 0)
   int32_t slot0;     // member holding the first candidate of this CTA's chunk (set by its writer)
@@ -309,34 +310,6 @@ __device__ T cscan2(T a, T b, T* ta, T* tb, T* pb) {
   *tb = ws2[1][kCW - 1];
   __syncthreads();
   return pa;
-}
-
-// Block sum and two minima in one shared-memory round.
-__device__ void creduce(int32_t& sum, int32_t& mn, int32_t& mn2) {
-  __shared__ int32_t s_sum[kCW], s_mn[kCW], s_mn2[kCW];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    mn2 = min(mn2, __shfl_xor_sync(0xffffffffu, mn2, o));
-  }
-  if (lane == 0) {
-    s_sum[warp] = sum;
-    s_mn[warp] = mn;
-    s_mn2[warp] = mn2;
-  }
-  __syncthreads();
-  sum = lane < kCW ? s_sum[lane] : 0;
-  mn = lane < kCW ? s_mn[lane] : INT_MAX;
-  mn2 = lane < kCW ? s_mn2[lane] : INT_MAX;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    mn2 = min(mn2, __shfl_xor_sync(0xffffffffu, mn2, o));
-  }
-  __syncthreads();
 }
 
 __device__ __forceinline__ long long csum_ll(long long v) {
@@ -537,7 +510,12 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
     sm->pub.odeg[threadIdx.x] = 0;
     sm->pub.ndeg[threadIdx.x] = 0;
   }
-  if (threadIdx.x == 0) sm->pub.stop = 0;
+  if (threadIdx.x == 0) {
+    sm->pub.stop = 0;
+    sm->pub.surv = 0;
+    sm->pub.minb = kNoBucket;
+    sm->pub.min_open = INT_MAX;
+  }
   if (threadIdx.x < kThr) sm->thr[threadIdx.x] = group_thr(S.i + (int32_t)threadIdx.x, A.lr);
   // the older plans phase B re-tests: their records copied into shared memory now, behind the
   // expansion, so that phase B only looks up their dominance (the same decision as phase B's)
@@ -899,21 +877,31 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
     sm->rows_ready = 1;  // read by phase A after this phase's barriers
   }
-  creduce(surv, minb, min_open);
-  if (threadIdx.x == 0) {
-    sm->pub.err = sm->werr;
-    sm->pub.surv = surv;
-    sm->pub.minb = minb;
-    sm->pub.min_open = min_open;
+  // the CTA's survivor count and minima: warp reductions, then one shared-memory atomic per warp
+  // into the record (reset in phase A)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    surv += __shfl_xor_sync(0xffffffffu, surv, o);
+    minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
+    min_open = min(min_open, __shfl_xor_sync(0xffffffffu, min_open, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (surv) atomicAdd(&sm->pub.surv, surv);
+    if (minb != kNoBucket) atomicMin(&sm->pub.minb, minb);
+    if (min_open != INT_MAX) atomicMin(&sm->pub.min_open, min_open);
   }
   __syncthreads();
   // the record into slot r of every CTA (the cluster barrier that closes this phase orders the
-  // stores before phase C reads them; slot r is rewritten only after two more barriers)
+  // stores before phase C reads them; slot r is rewritten only after two more barriers), with the
+  // error flag as it stands after the barrier above (every wait of this phase has ended)
   const uint4* src = reinterpret_cast<const uint4*>(&sm->pub);
+  const uint32_t werr = (uint32_t)sm->werr;
   for (int t = threadIdx.x; t < kPubVec * nr; t += kCT) {
     const int dr = t / kPubVec, wv = t - dr * kPubVec;
     uint4* dst = reinterpret_cast<uint4*>(cl.map_shared_rank(&sm->pub_all[r], (unsigned)dr));
-    dst[wv] = src[wv];
+    uint4 v = src[wv];
+    if (wv == kPubErrWord / 4) reinterpret_cast<uint32_t*>(&v)[kPubErrWord % 4] = werr;
+    dst[wv] = v;
   }
 }
 
@@ -1166,11 +1154,6 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const long long Cn = nbk != kNoBucket ? sm->b_dtotal_o + sm->b_dtotal_n : 0;
-    sm->b_per_n = (Cn + nr - 1) >> log2_nr(nr);
-  }
-  __syncthreads();
   const int32_t total_s = sm->b_total_s, before_s = sm->b_before_s;
   const int32_t total_o = sm->b_total_o, before_o = sm->b_before_o;
   const int32_t total_n = sm->b_total_n, before_n = sm->b_before_n;
@@ -1186,7 +1169,7 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
   }
   const bool has_next = nbk != kNoBucket;
   const int64_t Cn = has_next ? dtotal_o + dtotal_n : 0;
-  const int64_t per_n = sm->b_per_n;
+  const int64_t per_n = (Cn + nr - 1) >> log2_nr(nr);  // the next group's candidates per CTA
   const bool small_w = A.w <= 4;
   // survivors to the arena, members among them to the group list
   const int64_t c0 = S.c0, c1 = S.c1;
