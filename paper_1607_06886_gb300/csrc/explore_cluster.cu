@@ -273,7 +273,9 @@ __device__ T cscan(T v, T* total) {
 }
 
 // Two exclusive block scans in one shared-memory round: warp 0 scans the warp totals of the
-// first values, warp 1 those of the second.  Returns the first prefix; *pb is the second.
+// first values, warp 1 those of the second.  Returns the first prefix; *pb is the second.  Its
+// shared words are rewritten only by the next call, so the caller needs a CTA barrier between
+// two calls.
 static_assert(kCW >= 2, "two warps scan the warp totals");
 template <typename T>
 __device__ T cscan2(T a, T b, T* ta, T* tb, T* pb) {
@@ -308,8 +310,7 @@ __device__ T cscan2(T a, T b, T* ta, T* tb, T* pb) {
   *pb = (warp > 0 ? ws2[1][warp - 1] : T(0)) + y - b;
   *ta = ws2[0][kCW - 1];
   *tb = ws2[1][kCW - 1];
-  __syncthreads();
-  return pa;
+  return pa;  // no trailing barrier: one call per phase, and a barrier follows before the next
 }
 
 __device__ __forceinline__ long long csum_ll(long long v) {
@@ -667,9 +668,12 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
       }
     }
   }
-  if (pf) cp_async_wait();  // the barriers that close the phase publish the copies to the CTA
-  kept = csum_ll(kept);
-  if (threadIdx.x == 0) sm->kept += kept;
+  if (pf) cp_async_wait();  // the cluster barrier that closes the phase publishes the copies
+  // the run's count of kept candidates (a statistic read after the loop): warp sums, one
+  // shared-memory atomic per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+  if (lane == 0 && kept) atomicAdd(reinterpret_cast<unsigned long long*>(&sm->kept), (unsigned long long)kept);
 }
 
 // Group index of an older plan (head x, cost c, popcount pc, created in group t) if it is open and
@@ -1184,10 +1188,13 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
   int64_t run = S.base + before_s;
   int64_t mrun = total_o + before_n;
   int64_t drun = dtotal_o + dbefore_n;
-  if (!big && has_next && n + no <= kCT) {
+  const bool one_pass = !big && has_next && n + no <= kCT;
+  if (one_pass) {
     // cached survivors (threads below n) and cached older plans (threads n .. n + no - 1) in one
-    // pass, both lists' positions from one scan round
+    // pass, both lists' positions from one scan round; the state fields used after the scan are
+    // read before it, so thread 0 may rewrite the state without a barrier of its own at the end
     const int t = threadIdx.x;
+    const int32_t Si = S.i, k1 = S.k + 1;
     bool keep = false, sel = false;
     int32_t eff = -1, x = 0, r0 = 0, odeg = 0;
     float c = 0.f;
@@ -1226,13 +1233,13 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
                                        sel ? pack_cd(1, odeg) : 0, &tk, &tpk, &rpk);
     if (keep) {
       const int64_t id = run + pack_k(rk);
-      const uint4 sm4 = put_survivor(A, sm, id, q, t, true, S.i);
+      const uint4 sm4 = put_survivor(A, sm, id, q, t, true, Si);
       if (member)
-        put_member(A, sm, cl, Cn, per_n, S.k + 1, mrun + pack_c(rk), drun + pack_d(rk), (int32_t)id, q.x, q.r0, q.cost,
-                   deg, sm4);
+        put_member(A, sm, cl, Cn, per_n, k1, mrun + pack_c(rk), drun + pack_d(rk), (int32_t)id, q.x, q.r0, q.cost, deg,
+                   sm4);
     }
     if (sel)
-      put_member(A, sm, cl, Cn, per_n, S.k + 1, before_o + pack_c(rpk), dbefore_o + pack_d(rpk),
+      put_member(A, sm, cl, Cn, per_n, k1, before_o + pack_c(rpk), dbefore_o + pack_d(rpk),
                  (int32_t)(a0 + (t - n)), x, r0, c, odeg, m);
   } else {
     for (int t0 = 0; t0 < n; t0 += kCT) {
@@ -1353,7 +1360,7 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
   if (r == 0 && threadIdx.x == 0) A.goff[gn] = Cn;
   // next state (the same in every CTA of the cluster) and, if it runs, the next iteration's share;
   // the cluster barrier after this phase publishes both
-  __syncthreads();
+  if (!one_pass) __syncthreads();
   if (threadIdx.x == 0) {
     S.lo = min((int64_t)min_open, S.base);
     S.base += total_s;
