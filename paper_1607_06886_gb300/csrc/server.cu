@@ -58,7 +58,9 @@ int64_t estimate_bytes(const pump_request* r) {
   const double E = n * deg;
   const double per_edge = 4 + 4 + 4 + 4 + 16 + 12 + 12 * W + 4 * w + 24 + 4 + 16 + 32;
   const double build = 2.0 * n * n / 8.0 + 64.0 * n;
-  const double arena = (double)r->plan.max_plans * (44.0 + 4.0 * w);
+  // per plan: head, parent, edge, creation and expansion stamps, cost, popcount (7 x 4 B), mask
+  // words, group slot (4), group record (16) and offset (8), goal lists (2 x 4), row record (8)
+  const double arena = (double)r->plan.max_plans * (72.0 + 4.0 * w);
   return (int64_t)(E * per_edge + build + arena) + (16ll << 20);
 }
 
