@@ -141,18 +141,26 @@ __device__ __forceinline__ bool launch_shape_ok(const LaunchShape& ls) {
 // and masks instead of integer divisions on the phases' dependent chains.
 __device__ __forceinline__ int log2_nr(int nr) { return __ffs(nr) - 1; }
 
-// Counts one CTA publishes after phase B (every CTA reads them in phase C).  16-byte aligned:
-// the end of phase B copies the whole record into every CTA's shared memory with vector stores.
+// Counts toward one group index: older and new plans, and their out-degree sums.
+struct PubQ {
+  unsigned long long odeg, ndeg;
+  int32_t ocnt, ncnt;
+};
+// Counts one CTA publishes after phase B (every CTA reads them in phase C).  16-byte aligned: the
+// end of phase B copies the record's prefix up to entry qn into every CTA's shared memory with
+// vector stores; entries from qn on are zero in the owner's record and not read by anyone.
 struct alignas(16) Pub {
-  unsigned long long odeg[kWin], ndeg[kWin];
-  int32_t ocnt[kWin], ncnt[kWin];
   int32_t surv;      // survivors of the CTA's chunk
   int32_t minb;      // least group index of an open undominated plan seen by the CTA
   int32_t min_open;  // least id of an older open undominated plan (INT_MAX if none)
   uint32_t stop;     // bit q: a member of group i+1+q is a goal plan with popc < K_min
   int32_t err;       // a wait for a row's masks ran out (fused form)
+  int32_t qn;        // entries q[0 .. qn) may be nonzero (the last counted group index + 1)
+  int32_t pad[2];
+  PubQ q[kWin];
 };
 constexpr int kPubVec = (int)(sizeof(Pub) / 16);
+constexpr int kPubHead = (int)(offsetof(Pub, q));  // bytes before the entries
 constexpr int kPubErrWord = (int)(offsetof(Pub, err) / 4);  // 32-bit word of the error flag
 static_assert(sizeof(Pub) % 16 == 0, "Pub copies as 16-byte words");
 // Counts for one group index beyond the window (extra round).
@@ -462,9 +470,9 @@ __device__ __forceinline__ uint4 load_mask4(const uint32_t* p, int w) {
   return make_uint4(ldu(p), w > 1 ? ldu(p + 1) : 0u, w > 2 ? ldu(p + 2) : 0u, w > 3 ? ldu(p + 3) : 0u);
 }
 
-// Warp-aggregated count of a plan toward group index i+1+q (q in [0, kWin)).
-__device__ __forceinline__ void bucket_add(bool on, int q, int deg, bool goal_stop, int32_t* cnt,
-                                           unsigned long long* dsum, uint32_t* stop_bits) {
+// Warp-aggregated count of a plan (an older one or a new one) toward group index i+1+q (q in
+// [0, kWin)).
+__device__ __forceinline__ void bucket_add(bool on, int q, int deg, bool goal_stop, bool older, Pub* pub) {
   const bool in = on && q >= 0 && q < kWin;
   const unsigned act = __ballot_sync(0xffffffffu, in);
   if (!in) return;
@@ -472,9 +480,11 @@ __device__ __forceinline__ void bucket_add(bool on, int q, int deg, bool goal_st
   const unsigned ds = __reduce_add_sync(peers, (unsigned)deg);
   const bool st = __any_sync(peers, goal_stop);
   if ((threadIdx.x & 31) == __ffs(peers) - 1) {
-    atomicAdd(cnt + q, __popc(peers));
-    atomicAdd(dsum + q, (unsigned long long)ds);
-    if (st) atomicOr(stop_bits, 1u << q);
+    PubQ& e = pub->q[q];
+    atomicAdd(older ? &e.ocnt : &e.ncnt, __popc(peers));
+    atomicAdd(older ? &e.odeg : &e.ndeg, (unsigned long long)ds);
+    if (st) atomicOr(&pub->stop, 1u << q);
+    atomicMax(&pub->qn, q + 1);
   }
 }
 
@@ -506,13 +516,14 @@ __device__ void c_expand(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // this CTA's counts for phase B (the copies other CTAs hold are separate)
   if (threadIdx.x < kWin) {
-    sm->pub.ocnt[threadIdx.x] = 0;
-    sm->pub.ncnt[threadIdx.x] = 0;
-    sm->pub.odeg[threadIdx.x] = 0;
-    sm->pub.ndeg[threadIdx.x] = 0;
+    sm->pub.q[threadIdx.x].ocnt = 0;
+    sm->pub.q[threadIdx.x].ncnt = 0;
+    sm->pub.q[threadIdx.x].odeg = 0;
+    sm->pub.q[threadIdx.x].ndeg = 0;
   }
   if (threadIdx.x == 0) {
     sm->pub.stop = 0;
+    sm->pub.qn = 0;
     sm->pub.surv = 0;
     sm->pub.minb = kNoBucket;
     sm->pub.min_open = INT_MAX;
@@ -815,8 +826,8 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
       filter_cand<kDsm>(A, sm, mbl, cl, S, t, true, surv, minb, keep, eff, deg, gstop);
     else if (t < n + (int)(a1 - a0))
       filter_old<kDsm>(A, sm, mbl, cl, S, a0 + (t - n), a0, ofits, minb, min_open, oeff, opc, odeg, goal);
-    bucket_add(keep, eff - S.i - 1, deg, gstop, sm->pub.ncnt, sm->pub.ndeg, &sm->pub.stop);
-    bucket_add(oeff >= 0, oeff - S.i - 1, odeg, goal && opc < A.kmin, sm->pub.ocnt, sm->pub.odeg, &sm->pub.stop);
+    bucket_add(keep, eff - S.i - 1, deg, gstop, false, &sm->pub);
+    bucket_add(oeff >= 0, oeff - S.i - 1, odeg, goal && opc < A.kmin, true, &sm->pub);
   }
   for (int t0 = 0; t0 < n && !merged; t0 += two ? 2 * kCT : kCT) {
     const int jl = t0 + threadIdx.x, jl2 = jl + kCT;
@@ -863,19 +874,19 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
       }
       if (on1) sm->ceff[jl] = eff;
       if (on2) sm->ceff[jl2] = eff2;
-      bucket_add(keep, eff - S.i - 1, deg, gstop, sm->pub.ncnt, sm->pub.ndeg, &sm->pub.stop);
-      bucket_add(keep2, eff2 - S.i - 1, deg2, gstop2, sm->pub.ncnt, sm->pub.ndeg, &sm->pub.stop);
+      bucket_add(keep, eff - S.i - 1, deg, gstop, false, &sm->pub);
+      bucket_add(keep2, eff2 - S.i - 1, deg2, gstop2, false, &sm->pub);
       continue;
     }
     if (jl < n) filter_cand<kDsm>(A, sm, mbl, cl, S, jl, fits, surv, minb, keep, eff, deg, gstop);
-    bucket_add(keep, eff - S.i - 1, deg, gstop, sm->pub.ncnt, sm->pub.ndeg, &sm->pub.stop);
+    bucket_add(keep, eff - S.i - 1, deg, gstop, false, &sm->pub);
   }
   for (int64_t t0 = a0; t0 < a1 && !merged; t0 += kCT) {
     const int64_t p = t0 + threadIdx.x;
     int32_t eff = -1, pc = 0, deg = 0;
     bool goal = false;
     if (p < a1) filter_old<kDsm>(A, sm, mbl, cl, S, p, a0, ofits, minb, min_open, eff, pc, deg, goal);
-    bucket_add(eff >= 0, eff - S.i - 1, deg, goal && pc < A.kmin, sm->pub.ocnt, sm->pub.odeg, &sm->pub.stop);
+    bucket_add(eff >= 0, eff - S.i - 1, deg, goal && pc < A.kmin, true, &sm->pub);
   }
   if (poll_done && done_seen == A.done_target) {
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
@@ -900,8 +911,9 @@ __device__ void c_filter(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clu
   // error flag as it stands after the barrier above (every wait of this phase has ended)
   const uint4* src = reinterpret_cast<const uint4*>(&sm->pub);
   const uint32_t werr = (uint32_t)sm->werr;
-  for (int t = threadIdx.x; t < kPubVec * nr; t += kCT) {
-    const int dr = t / kPubVec, wv = t - dr * kPubVec;
+  const int len = (kPubHead + (int)sizeof(PubQ) * sm->pub.qn + 15) / 16;  // 16-byte words pushed
+  for (int t = threadIdx.x; t < len * nr; t += kCT) {
+    const int dr = t / len, wv = t - dr * len;
     uint4* dst = reinterpret_cast<uint4*>(cl.map_shared_rank(&sm->pub_all[r], (unsigned)dr));
     uint4 v = src[wv];
     if (wv == kPubErrWord / 4) reinterpret_cast<uint32_t*>(&v)[kPubErrWord % 4] = werr;
@@ -1098,8 +1110,9 @@ __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::clus
     long long dbo = 0, dto = 0, dbn = 0, dtn = 0;
     bool stp = false;
     if (minb != kNoBucket && fast) {
-      const int32_t oc = on ? rp->ocnt[q] : 0, nc = on ? rp->ncnt[q] : 0;
-      const long long od = on ? (long long)rp->odeg[q] : 0, nd = on ? (long long)rp->ndeg[q] : 0;
+      const bool has = on && q < rp->qn;  // entries from qn on were not pushed: zero
+      const int32_t oc = has ? rp->q[q].ocnt : 0, nc = has ? rp->q[q].ncnt : 0;
+      const long long od = has ? (long long)rp->q[q].odeg : 0, nd = has ? (long long)rp->q[q].ndeg : 0;
       const bool sb = on && ((rp->stop >> q) & 1u);
       lane_prefix<int32_t>(oc, r, &bo, &to);
       lane_prefix<int32_t>(nc, r, &bn, &tn);
