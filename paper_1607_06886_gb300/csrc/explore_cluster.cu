@@ -1089,53 +1089,59 @@ template <bool kDsm>
 __device__ void c_write(const ExploreArgs& A, CSmem* sm, uint32_t* mbl, cg::cluster_group& cl, St& S) {
   const int r = (int)cl.block_rank(), nr = (int)cl.num_blocks();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // Warp 0 reads every CTA's counts (lane l from CTA l) and derives the cluster-wide values.
-  if (warp == 0) {
+  // Warps 0-3 read every CTA's counts (lane l from CTA l) and derive the cluster-wide values:
+  // each the least group index, then warp 0 the survivors' and older plans' prefixes, warp 1 the
+  // new plans', warps 2 and 3 the degree sums of the older and the new ones.
+  if (warp < 4) {
     const bool on = lane < nr;
     const Pub* rp = &sm->pub_all[on ? lane : 0];
     int32_t minb = on ? rp->minb : kNoBucket;
-    int32_t mo = on ? rp->min_open : INT_MAX;
-    const int32_t sv = on ? rp->surv : 0;
-    const bool werr = __any_sync(0xffffffffu, on && rp->err != 0);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
-      mo = min(mo, __shfl_xor_sync(0xffffffffu, mo, o));
-    }
-    int32_t bs, ts;
-    lane_prefix<int32_t>(sv, r, &bs, &ts);
+    for (int o = 16; o > 0; o >>= 1) minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
     const int32_t q = minb == kNoBucket ? -1 : minb - S.i - 1;
     const bool fast = minb == kNoBucket || (q >= 0 && q < kWin);
-    int32_t bo = 0, to = 0, bn = 0, tn = 0;
-    long long dbo = 0, dto = 0, dbn = 0, dtn = 0;
-    bool stp = false;
-    if (minb != kNoBucket && fast) {
-      const bool has = on && q < rp->qn;  // entries from qn on were not pushed: zero
-      const int32_t oc = has ? rp->q[q].ocnt : 0, nc = has ? rp->q[q].ncnt : 0;
-      const long long od = has ? (long long)rp->q[q].odeg : 0, nd = has ? (long long)rp->q[q].ndeg : 0;
-      const bool sb = on && ((rp->stop >> q) & 1u);
-      lane_prefix<int32_t>(oc, r, &bo, &to);
-      lane_prefix<int32_t>(nc, r, &bn, &tn);
-      lane_prefix<long long>(od, r, &dbo, &dto);
-      lane_prefix<long long>(nd, r, &dbn, &dtn);
-      stp = __any_sync(0xffffffffu, sb);
-    }
-    if (lane == 0) {
-      sm->b_nbk = minb;
-      sm->b_min_open = mo;
-      sm->b_before_s = bs;
-      sm->b_total_s = ts;
-      sm->b_fast = fast ? 1 : 0;
-      sm->b_before_o = bo;
-      sm->b_total_o = to;
-      sm->b_before_n = bn;
-      sm->b_total_n = tn;
-      sm->b_dbefore_o = dbo;
-      sm->b_dtotal_o = dto;
-      sm->b_dbefore_n = dbn;
-      sm->b_dtotal_n = dtn;
-      sm->b_stop = stp ? 1 : 0;
-      sm->b_err = werr ? 1 : 0;
+    const bool has = minb != kNoBucket && fast && on && q < rp->qn;  // entries from qn on were not pushed
+    if (warp == 0) {
+      int32_t mo = on ? rp->min_open : INT_MAX;
+      const int32_t sv = on ? rp->surv : 0;
+      const bool werr = __any_sync(0xffffffffu, on && rp->err != 0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mo = min(mo, __shfl_xor_sync(0xffffffffu, mo, o));
+      int32_t bs, ts, bo, to;
+      lane_prefix<int32_t>(sv, r, &bs, &ts);
+      lane_prefix<int32_t>(has ? rp->q[q].ocnt : 0, r, &bo, &to);
+      const bool stp = minb != kNoBucket && fast && __any_sync(0xffffffffu, on && ((rp->stop >> q) & 1u));
+      if (lane == 0) {
+        sm->b_nbk = minb;
+        sm->b_min_open = mo;
+        sm->b_before_s = bs;
+        sm->b_total_s = ts;
+        sm->b_fast = fast ? 1 : 0;
+        sm->b_before_o = bo;
+        sm->b_total_o = to;
+        sm->b_stop = stp ? 1 : 0;
+        sm->b_err = werr ? 1 : 0;
+      }
+    } else if (warp == 1) {
+      int32_t bn, tn;
+      lane_prefix<int32_t>(has ? rp->q[q].ncnt : 0, r, &bn, &tn);
+      if (lane == 0) {
+        sm->b_before_n = bn;
+        sm->b_total_n = tn;
+      }
+    } else {
+      long long db, dt;
+      const bool older = warp == 2;
+      lane_prefix<long long>(has ? (long long)(older ? rp->q[q].odeg : rp->q[q].ndeg) : 0, r, &db, &dt);
+      if (lane == 0) {
+        if (older) {
+          sm->b_dbefore_o = db;
+          sm->b_dtotal_o = dt;
+        } else {
+          sm->b_dbefore_n = db;
+          sm->b_dtotal_n = dt;
+        }
+      }
     }
   }
   __syncthreads();
