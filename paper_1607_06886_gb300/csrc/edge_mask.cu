@@ -389,96 +389,131 @@ __global__ void k_hs_build(const float* __restrict__ nom, const float* __restric
   }
 }
 
-// Query pass (HSMC): a warp per edge, NW mask words per lane pass as in word_pass; at waypoint k
-// the particles test the edge's kept half-spaces hs[off_k .. off_{k+1}).
-template <int NW>
-__device__ __forceinline__ void word_pass_hs(const float2* __restrict__ xi, int N, const float (&P)[4],
-                                             const float (&L)[3], const float (&linf)[3], const int32_t* woff,
-                                             const float4* hs, int k_last, int w0, int lane, uint32_t* out) {
-  float d0[NW][3], d1[NW][3];
-  bool hit[NW];
-  const float2* xq = xi + w0 * 32 + lane;
+// Query pass (HSMC): a warp per edge; lane l advances the particles of NP pairs of mask words in
+// packed FP32x2 registers (pair-major normals, as the box pass), and at waypoint k each particle
+// tests the edge's kept half-spaces hs[off_k .. off_{k+1}): a . dy, the sums and products rounded
+// as written, above b.  Packed FP32x2 arithmetic rounds each half as the scalar operation does, so
+// the words equal the scalar evaluation's.
+template <int NP>
+__device__ __forceinline__ void pair_pass_hs(const float4* __restrict__ xp, int npair,
+                                             const unsigned long long (&P2)[4], const unsigned long long (&L2)[3],
+                                             const unsigned long long (&I2)[3], const int32_t* woff,
+                                             const float4* hs, int k_last, int p0, int w, int lane, uint32_t* out) {
+  using namespace maskdev;
+  unsigned long long d0[NP][3], d1[NP][3];
+  bool hit[NP][2];
+  const float4* xq = xp + (size_t)p0 * 32 + lane;
 #pragma unroll
-  for (int j = 0; j < NW; ++j) {
-    hit[j] = false;
+  for (int j = 0; j < NP; ++j) {
+    hit[j][0] = hit[j][1] = false;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) dev_init(linf, xq[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+    for (int a = 0; a < 3; ++a) {
+      const float4 x = xq[((size_t)a * npair + j) * 32];
+      const unsigned long long X0 = pk2(x.x, x.y), X1 = pk2(x.z, x.w);
+      d0[j][a] = mul2(I2[0], X0);
+      d1[j][a] = fma2(I2[1], X0, mul2(I2[2], X1));
+    }
   }
   for (int k = 1; k <= k_last; ++k) {
-    const float2* xk = xq + (size_t)k * 3 * N;
+    const float4* xk = xq + (size_t)k * 3 * npair * 32;
 #pragma unroll
-    for (int j = 0; j < NW; ++j) {
+    for (int j = 0; j < NP; ++j) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) dev_step(P, L, xk[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+      for (int a = 0; a < 3; ++a) {
+        const float4 x = xk[((size_t)a * npair + j) * 32];
+        const unsigned long long X0 = pk2(x.x, x.y), X1 = pk2(x.z, x.w);
+        const unsigned long long m0 = mul2(L2[0], X0);
+        const unsigned long long m1 = fma2(L2[1], X0, mul2(L2[2], X1));
+        const unsigned long long e0 = fma2(P2[0], d0[j][a], fma2(P2[1], d1[j][a], m0));
+        const unsigned long long e1 = fma2(P2[2], d0[j][a], fma2(P2[3], d1[j][a], m1));
+        d0[j][a] = e0;
+        d1[j][a] = e1;
+      }
     }
     for (int h = woff[k - 1]; h < woff[k]; ++h) {
       const float4 q = hs[h];
+      const unsigned long long A0 = pk2(q.x, q.x), A1 = pk2(q.y, q.y), A2 = pk2(q.z, q.z);
 #pragma unroll
-      for (int j = 0; j < NW; ++j)
-        hit[j] = hit[j] || fmaf(q.z, d0[j][2], fmaf(q.y, d0[j][1], __fmul_rn(q.x, d0[j][0]))) > q.w;
+      for (int j = 0; j < NP; ++j) {
+        float s0, s1;
+        upk2(fma2(A2, d0[j][2], fma2(A1, d0[j][1], mul2(A0, d0[j][0]))), s0, s1);
+        hit[j][0] = hit[j][0] || s0 > q.w;
+        hit[j][1] = hit[j][1] || s1 > q.w;
+      }
     }
     bool done = true;
 #pragma unroll
-    for (int j = 0; j < NW; ++j) done = done && hit[j];
+    for (int j = 0; j < NP; ++j) done = done && hit[j][0] && hit[j][1];
     if (__all_sync(0xffffffffu, done)) break;
   }
 #pragma unroll
-  for (int j = 0; j < NW; ++j) {
-    const unsigned bits = __ballot_sync(0xffffffffu, hit[j]);
-    if (lane == 0) out[w0 + j] = bits;
-  }
+  for (int j = 0; j < NP; ++j)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int word = 2 * (p0 + j) + h;
+      const unsigned bits = __ballot_sync(0xffffffffu, hit[j][h]);
+      if (lane == 0 && word < w) out[word] = bits;
+    }
 }
 
+// Warps take edges, kMaskChunk at a time, from a counter (edges differ widely in work).
 template <bool kSmemXi>
-__global__ void __launch_bounds__(kWarps * 32, 4) k_edge_mask_hs(
-    const float2* __restrict__ xi_g, int N, int W, const float* __restrict__ phi, const float* __restrict__ Lg,
+__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask_hs(
+    const float4* __restrict__ xp_g, int N, int W, const float* __restrict__ phi, const float* __restrict__ Lg,
     const float* __restrict__ linf_g, const int32_t* __restrict__ hs_off, const float4* __restrict__ hs_ab, int E,
-    int w, uint32_t* __restrict__ mask) {
+    int w, unsigned long long* __restrict__ ctr, uint32_t* __restrict__ mask) {
+  using namespace maskdev;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* stage_all = reinterpret_cast<float4*>(smem);
   int32_t* woff_all = reinterpret_cast<int32_t*>(stage_all + kWarps * kHsStage);
-  float2* xi_s = reinterpret_cast<float2*>(smem + edge_mask_hs_fixed_smem());
-  const int xi_n = (W + 1) * 3 * N;
+  float4* xp_s = reinterpret_cast<float4*>(smem + edge_mask_hs_fixed_smem());
+  const int npair = pair_count(w);
+  const int xp_n = (W + 1) * 3 * npair * 32;
   if (kSmemXi)
-    for (int k = threadIdx.x; k < xi_n; k += blockDim.x) xi_s[k] = xi_g[k];
+    for (int k = threadIdx.x; k < xp_n; k += blockDim.x) xp_s[k] = xp_g[k];
   __syncthreads();
-  const float2* xi = kSmemXi ? xi_s : xi_g;
-  const float linf[3] = {linf_g[0], linf_g[1], linf_g[2]};
+  const float4* xp = kSmemXi ? xp_s : xp_g;
+  const unsigned long long I2[3] = {pk2(linf_g[0], linf_g[0]), pk2(linf_g[1], linf_g[1]), pk2(linf_g[2], linf_g[2])};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4* stage = stage_all + warp * kHsStage;
   int32_t* woff = woff_all + warp * (kMaxWaypoints + 1);
-  for (long long e = (long long)blockIdx.x * kWarps + warp; e < E; e += (long long)gridDim.x * kWarps) {
-    const int32_t* off = hs_off + (size_t)e * W;
-    const int32_t o0 = off[0], o1 = off[W];
-    uint32_t* out = mask + (size_t)e * w;
-    if (o0 == o1) {
-      for (int word = lane; word < w; word += 32) out[word] = 0u;
-      continue;
-    }
-    // waypoint offsets relative to the edge's first half-space, and the last waypoint with one
-    int k_last = 0;
-    for (int k = lane; k <= W; k += 32) {
-      woff[k] = off[k] - o0;
-      if (k > 0 && off[k] > off[k - 1]) k_last = max(k_last, k);
-    }
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(ctr, (unsigned long long)kMaskChunk);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= (unsigned long long)E) break;
+    const long long e1 = min((long long)E, (long long)t + kMaskChunk);
+    for (long long e = (long long)t; e < e1; ++e) {
+      const int32_t* off = hs_off + (size_t)e * W;
+      const int32_t o0 = off[0], o1 = off[W];
+      uint32_t* out = mask + (size_t)e * w;
+      if (o0 == o1) {
+        for (int word = lane; word < w; word += 32) out[word] = 0u;
+        continue;
+      }
+      const float4 ph = *reinterpret_cast<const float4*>(phi + 4 * e);
+      const float l0 = Lg[3 * e], l1 = Lg[3 * e + 1], l2 = Lg[3 * e + 2];
+      // waypoint offsets relative to the edge's first half-space, and the last waypoint with one
+      int k_last = 0;
+      for (int k = lane; k <= W; k += 32) {
+        woff[k] = off[k] - o0;
+        if (k > 0 && off[k] > off[k - 1]) k_last = max(k_last, k);
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) k_last = max(k_last, __shfl_xor_sync(0xffffffffu, k_last, o));
-    const int nh = o1 - o0;
-    const bool staged = nh <= kHsStage;
-    if (staged)
-      for (int h = lane; h < nh; h += 32) stage[h] = hs_ab[o0 + h];
-    __syncwarp();
-    const float4* hs = staged ? stage : hs_ab + o0;
-    const float P[4] = {phi[4 * e], phi[4 * e + 1], phi[4 * e + 2], phi[4 * e + 3]};
-    const float L[3] = {Lg[3 * e], Lg[3 * e + 1], Lg[3 * e + 2]};
-    int w0 = 0;
-    for (; w0 + 4 <= w; w0 += 4) word_pass_hs<4>(xi, N, P, L, linf, woff, hs, k_last, w0, lane, out);
-    if (w0 + 2 <= w) {
-      word_pass_hs<2>(xi, N, P, L, linf, woff, hs, k_last, w0, lane, out);
-      w0 += 2;
+      for (int o = 16; o > 0; o >>= 1) k_last = max(k_last, __shfl_xor_sync(0xffffffffu, k_last, o));
+      const int nh = o1 - o0;
+      const bool staged = nh <= kHsStage;
+      if (staged)
+        for (int h = lane; h < nh; h += 32) stage[h] = hs_ab[o0 + h];
+      __syncwarp();
+      const float4* hs = staged ? stage : hs_ab + o0;
+      const unsigned long long P2[4] = {pk2(ph.x, ph.x), pk2(ph.y, ph.y), pk2(ph.z, ph.z), pk2(ph.w, ph.w)};
+      const unsigned long long L2[3] = {pk2(l0, l0), pk2(l1, l1), pk2(l2, l2)};
+      int p = 0;
+      for (; p + 2 <= npair; p += 2) pair_pass_hs<2>(xp, npair, P2, L2, I2, woff, hs, k_last, p, w, lane, out);
+      for (; p < npair; ++p) pair_pass_hs<1>(xp, npair, P2, L2, I2, woff, hs, k_last, p, w, lane, out);
+      __syncwarp();
     }
-    if (w0 < w) word_pass_hs<1>(xi, N, P, L, linf, woff, hs, k_last, w0, lane, out);
-    __syncwarp();
   }
 }
 
@@ -596,20 +631,22 @@ int build_halfspaces(pump_graph* g, cudaStream_t s) {
 }
 
 static int compute_edge_masks_hs(pump_graph* g, cudaStream_t s) {
-  const size_t smem_xi = edge_mask_hs_fixed_smem() + sizeof(float2) * (size_t)(g->W + 1) * 3 * g->N;
+  const size_t smem_xi = edge_mask_hs_fixed_smem() +
+                         sizeof(float4) * (size_t)(g->W + 1) * 3 * maskdev::pair_count(g->n_words) * 32;
   const bool use_smem = smem_xi <= 160 * 1024;
   const size_t smem = use_smem ? smem_xi : edge_mask_hs_fixed_smem();
+  PUMP_CUDA_TRY(cudaMemsetAsync(g->wctr, 0, sizeof(unsigned long long), s));
   int grid = 1;
   if (use_smem) {
-    const int rco = occupancy_grid(k_edge_mask_hs<true>, smem, kWarps, g->E, &grid);
+    const int rco = occupancy_grid(k_edge_mask_hs<true>, smem, kWarps * (long long)kMaskChunk, g->E, &grid);
     if (rco) return rco;
-    k_edge_mask_hs<true><<<grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->linf_dev, g->hs_off,
-                                                         g->hs_ab, g->E, g->n_words, g->emask);
+    k_edge_mask_hs<true><<<grid, kWarps * 32, smem, s>>>(g->xi_p, g->N, g->W, g->phi, g->L, g->linf_dev, g->hs_off,
+                                                         g->hs_ab, g->E, g->n_words, g->wctr, g->emask);
   } else {
-    const int rco = occupancy_grid(k_edge_mask_hs<false>, smem, kWarps, g->E, &grid);
+    const int rco = occupancy_grid(k_edge_mask_hs<false>, smem, kWarps * (long long)kMaskChunk, g->E, &grid);
     if (rco) return rco;
-    k_edge_mask_hs<false><<<grid, kWarps * 32, smem, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->linf_dev, g->hs_off,
-                                                          g->hs_ab, g->E, g->n_words, g->emask);
+    k_edge_mask_hs<false><<<grid, kWarps * 32, smem, s>>>(g->xi_p, g->N, g->W, g->phi, g->L, g->linf_dev, g->hs_off,
+                                                          g->hs_ab, g->E, g->n_words, g->wctr, g->emask);
   }
   note_launch();
   PUMP_CUDA_TRY(cudaGetLastError());
