@@ -50,13 +50,128 @@ __device__ inline bool prefilter(const float* sv, const float* su, float r) {
   return true;
 }
 
+// A uniform grid over the valid nodes' positions, so that a source scans only the cells its
+// prefilter bound can reach.  Cell index per axis: min(G - 1, floor((p - lo) * inv)), monotone in
+// p, so every target within the bound of a source lies in the cells between the indices of the
+// bound's two ends.
+constexpr int kGridMax = 32;  // cells per axis at most
+struct Grid {
+  float lo[3], inv[3];
+  int G[3];
+  float vmax;  // largest |velocity| of a valid node
+};
+__device__ __forceinline__ int grid_cell(const Grid& gr, int a, float p) {
+  const float t = floorf(__fmul_rn(__fsub_rn(p, gr.lo[a]), gr.inv[a]));
+  return t < 0.f ? 0 : (t >= (float)(gr.G[a] - 1) ? gr.G[a] - 1 : (int)t);
+}
+// Half-width of the position window a pair with source speed |v_v| = vv can pass: the prefilter's
+// position threshold with |vbar| <= (vmax + vv) / 2, widened by 1e-4 relative and 1e-6 absolute
+// (the float rounding of the prefilter's sums and square roots is below 1e-6 relative).
+__device__ __forceinline__ float grid_bound(const Grid& gr, float vv, float r) {
+  return ((0.5f * (gr.vmax + vv) * r + 0.09375f * r * r) * 1.0001f + 1e-6f) * 1.0001f + 1e-6f;
+}
+
+// One block: bounding box and largest speed of the valid nodes, then the grid (cells about a
+// quarter of the widest bound per side, at most kGridMax per axis).
+__global__ void k_grid_setup(const float* __restrict__ states, const uint8_t* __restrict__ valid, int n, float r,
+                             Grid* out) {
+  __shared__ float s_lo[3][32], s_hi[3][32], s_v[32];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, vm = 0.f;
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    if (!valid[v]) continue;
+    const float* x = states + 6 * v;
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fminf(lo[a], x[a]);
+      hi[a] = fmaxf(hi[a], x[a]);
+    }
+    vm = fmaxf(vm, sqrtf(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+    }
+    vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+  }
+  if (lane == 0) {
+    for (int a = 0; a < 3; ++a) {
+      s_lo[a][warp] = lo[a];
+      s_hi[a][warp] = hi[a];
+    }
+    s_v[warp] = vm;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nwarp = (int)(blockDim.x >> 5);
+    Grid gr;
+    gr.vmax = 0.f;
+    for (int w = 0; w < nwarp; ++w) gr.vmax = fmaxf(gr.vmax, s_v[w]);
+    gr.vmax *= 1.0001f;
+    const float cell = fmaxf(0.25f * ((gr.vmax * r + 0.09375f * r * r) * 1.0001f + 1e-6f), 1e-30f);
+    for (int a = 0; a < 3; ++a) {
+      float l = INFINITY, h = -INFINITY;
+      for (int w = 0; w < nwarp; ++w) {
+        l = fminf(l, s_lo[a][w]);
+        h = fmaxf(h, s_hi[a][w]);
+      }
+      if (!(h >= l)) {  // no valid node
+        l = 0.f;
+        h = 0.f;
+      }
+      const float ext = h - l;
+      int G = (int)fminf((float)kGridMax, fmaxf(1.f, ceilf(ext / cell)));
+      gr.lo[a] = l;
+      gr.G[a] = G;
+      gr.inv[a] = ext > 0.f ? (float)G / ext : 0.f;
+    }
+    *out = gr;
+  }
+}
+
+__global__ void k_grid_count(const float* __restrict__ states, const uint8_t* __restrict__ valid, int n,
+                             const Grid* __restrict__ grid, int32_t* __restrict__ cnt) {
+  const Grid gr = *grid;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    if (!valid[v]) continue;
+    const float* x = states + 6 * v;
+    const int c = (grid_cell(gr, 2, x[2]) * gr.G[1] + grid_cell(gr, 1, x[1])) * gr.G[0] + grid_cell(gr, 0, x[0]);
+    atomicAdd(cnt + c, 1);
+  }
+}
+
+// Nodes by cell (cells in z, y, x order; the order inside a cell is not fixed, and nothing
+// downstream depends on it: kept pairs are placed by their rank in the keep bitmap).
+__global__ void k_grid_scatter(const float* __restrict__ states, const uint8_t* __restrict__ valid, int n,
+                               const Grid* __restrict__ grid, const long long* __restrict__ off,
+                               int32_t* __restrict__ cursor, int32_t* __restrict__ sorted,
+                               float* __restrict__ sorted_states) {
+  const Grid gr = *grid;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    if (!valid[v]) continue;
+    const float* x = states + 6 * v;
+    const int c = (grid_cell(gr, 2, x[2]) * gr.G[1] + grid_cell(gr, 1, x[1])) * gr.G[0] + grid_cell(gr, 0, x[0]);
+    const long long i = off[c] + atomicAdd(cursor + c, 1);
+    sorted[i] = v;
+    for (int j = 0; j < 6; ++j) sorted_states[6 * i + j] = x[j];  // the states in cell order too
+  }
+}
+
+// Exclusive scan of the grid's cell counts into 64-bit offsets (the cell count read from the grid).
+__global__ void k_grid_scan(const int32_t* __restrict__ in, const Grid* __restrict__ grid, long long* __restrict__ out);
+
 // The pairs (v, u), v != u, both valid, that pass the prefilter, row by row: a warp per source v
-// takes the targets u 32 at a time.  Pass 1 counts each row's pairs, an exclusive scan gives the
-// row offsets, and pass 2 writes each row's pairs in ascending u from its offset: no atomics, and
-// the list order is fixed.
+// scans the grid rows (y, z) its bound reaches, each row's cells [x0, x1] one contiguous slice of
+// the sorted nodes, 32 targets at a time.  Pass 1 counts each row's pairs, an exclusive scan gives
+// the row offsets, and pass 2 writes each row's pairs from its offset (the same targets in the
+// same order as pass 1 counted them): no atomics.
 template <bool kWrite>
 __global__ void k_prefilter(const float* __restrict__ states, const uint8_t* __restrict__ valid, int n, float r,
+                            const Grid* __restrict__ grid, const long long* __restrict__ coff,
+                            const int32_t* __restrict__ sorted, const float* __restrict__ sorted_states,
                             int32_t* __restrict__ cnt, const long long* __restrict__ off, int2* __restrict__ list) {
+  const Grid gr = *grid;
   const int lane = threadIdx.x & 31;
   const int warps = (int)(((long long)gridDim.x * blockDim.x) >> 5);
   for (int v = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); v < n; v += warps) {
@@ -65,13 +180,39 @@ __global__ void k_prefilter(const float* __restrict__ states, const uint8_t* __r
       float sv[6];
 #pragma unroll
       for (int j = 0; j < 6; ++j) sv[j] = states[6 * v + j];
+      const float R = grid_bound(gr, sqrtf(sv[3] * sv[3] + sv[4] * sv[4] + sv[5] * sv[5]), r);
+      int c0[3], c1[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        // the window's ends, widened by their own rounding (relative to the coordinate's size)
+        const float w = R + (fabsf(sv[a]) + R) * 1e-6f;
+        c0[a] = grid_cell(gr, a, __fsub_rn(sv[a], w));
+        c1[a] = grid_cell(gr, a, __fadd_rn(sv[a], w));
+      }
       long long base = kWrite ? off[v] : 0;
-      for (int u0 = 0; u0 < n; u0 += 32) {
-        const int u = u0 + lane;
-        const bool ok = u < n && u != v && valid[u] && prefilter(sv, states + 6 * u, r);
-        const unsigned b = __ballot_sync(0xffffffffu, ok);
-        if (kWrite && ok) list[base + c + __popc(b & ((1u << lane) - 1u))] = make_int2(v, u);
-        c += __popc(b);
+      const int ny = c1[1] - c0[1] + 1, nrows = ny * (c1[2] - c0[2] + 1);
+      for (int rb = 0; rb < nrows; rb += 32) {
+        // the slices of up to 32 grid rows (y, z), one per lane, loaded together
+        long long sa = 0, se = 0;
+        if (rb + lane < nrows) {
+          const int q = rb + lane, cz = c0[2] + q / ny, cy = c0[1] + q % ny;
+          const int row = (cz * gr.G[1] + cy) * gr.G[0];
+          sa = coff[row + c0[0]];
+          se = coff[row + c1[0] + 1];
+        }
+        const int nb = min(32, nrows - rb);
+        for (int t = 0; t < nb; ++t) {
+          const long long ia = __shfl_sync(0xffffffffu, sa, t), ie = __shfl_sync(0xffffffffu, se, t);
+          for (long long i0 = ia; i0 < ie; i0 += 32) {
+            const long long i = i0 + lane;
+            const bool in = i < ie;
+            const int u = in ? sorted[i] : v;
+            const bool ok = in && u != v && prefilter(sv, sorted_states + 6 * (in ? i : ia), r);
+            const unsigned bl = __ballot_sync(0xffffffffu, ok);
+            if (kWrite && ok) list[base + c + __popc(bl & ((1u << lane) - 1u))] = make_int2(v, u);
+            c += __popc(bl);
+          }
+        }
       }
     }
     if (!kWrite && lane == 0) cnt[v] = c;
@@ -95,6 +236,30 @@ __global__ void k_scan_ll(const int32_t* __restrict__ in, int n, long long* __re
     __syncthreads();
   }
   long long run = part[t] - sum;  // exclusive prefix of this thread's chunk
+  for (int i = b0; i < b1; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  if (t == T - 1) out[n] = part[T - 1];
+}
+
+__global__ void k_grid_scan(const int32_t* __restrict__ in, const Grid* __restrict__ grid, long long* __restrict__ out) {
+  __shared__ long long part[1024];
+  const int n = grid->G[0] * grid->G[1] * grid->G[2];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int per = (n + T - 1) / T;
+  const int b0 = min(n, t * per), b1 = min(n, b0 + per);
+  long long sum = 0;
+  for (int i = b0; i < b1; ++i) sum += in[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int d = 1; d < T; d <<= 1) {
+    const long long add = t >= d ? part[t - d] : 0;
+    __syncthreads();
+    part[t] += add;
+    __syncthreads();
+  }
+  long long run = part[t] - sum;
   for (int i = b0; i < b1; ++i) {
     out[i] = run;
     run += in[i];
@@ -791,8 +956,28 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   long long* roff = (long long*)dev_alloc(sizeof(long long) * (size_t)(n + 1), s);
   if (!d_count || !rcnt || !roff) return PUMP_ERR_OOM;
   PUMP_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long) * 5, s));
+  // the valid nodes on a position grid: cell counts, offsets, the nodes in cell order
+  constexpr int kCells = kGridMax * kGridMax * kGridMax;
+  Grid* d_grid = (Grid*)dev_alloc(sizeof(Grid), s);
+  int32_t* ccnt = (int32_t*)dev_alloc(sizeof(int32_t) * 2 * (size_t)kCells, s);  // counts, then cursors
+  long long* coff = (long long*)dev_alloc(sizeof(long long) * ((size_t)kCells + 1), s);
+  int32_t* sorted = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)std::max(n, 1), s);
+  float* sorted_states = (float*)dev_alloc(sizeof(float) * 6 * (size_t)std::max(n, 1), s);
+  if (!d_grid || !ccnt || !coff || !sorted || !sorted_states) return PUMP_ERR_OOM;
+  PUMP_CUDA_TRY(cudaMemsetAsync(ccnt, 0, sizeof(int32_t) * 2 * (size_t)kCells, s));
+  const int gnodes = std::max(1, std::min((n + kBlock - 1) / kBlock, sms * 8));
+  k_grid_setup<<<1, 1024, 0, s>>>(g->states, g->valid, n, g->radius, d_grid);
+  note_launch();
+  k_grid_count<<<gnodes, kBlock, 0, s>>>(g->states, g->valid, n, d_grid, ccnt);
+  note_launch();
+  k_grid_scan<<<1, 1024, 0, s>>>(ccnt, d_grid, coff);
+  note_launch();
+  k_grid_scatter<<<gnodes, kBlock, 0, s>>>(g->states, g->valid, n, d_grid, coff, ccnt + kCells, sorted,
+                                           sorted_states);
+  note_launch();
   const int grid = (int)std::min<long long>(((long long)n * 32 + kBlock - 1) / kBlock, (long long)sms * 16);
-  k_prefilter<false><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, rcnt, nullptr, nullptr);
+  k_prefilter<false><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, d_grid, coff, sorted, sorted_states,
+                                             rcnt, nullptr, nullptr);
   note_launch();
   k_scan_ll<<<1, 1024, 0, s>>>(rcnt, n, roff);
   note_launch();
@@ -804,9 +989,15 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   if (n_list) {
     list = (int2*)dev_alloc(sizeof(int2) * n_list, s);
     if (!list) { dev_free(d_count, s); return PUMP_ERR_OOM; }
-    k_prefilter<true><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, nullptr, roff, list);
+    k_prefilter<true><<<grid, kBlock, 0, s>>>(g->states, g->valid, n, g->radius, d_grid, coff, sorted, sorted_states,
+                                              nullptr, roff, list);
     note_launch();
   }
+  dev_free(sorted_states, s);
+  dev_free(sorted, s);
+  dev_free(coff, s);
+  dev_free(ccnt, s);
+  dev_free(d_grid, s);
   uint32_t* keep = (uint32_t*)dev_alloc(sizeof(uint32_t) * (size_t)n * nw, s);
   int32_t* deg = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)(n + 1), s);
   int32_t* wpre = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)n * nw, s);
