@@ -219,3 +219,27 @@ def test_edge_boxes_hold_every_particle_position():
         # control: a slab from the first nominal waypoint's x upward catches particles
         s = np.array([nom[e, 0, 0], -big, -big, big, big, big], np.float32)
         assert cpu.edge_masks(one, wl.xi, s[None], wl.n_particles).any(), e
+
+
+@pytest.mark.parametrize("shift,flat", [((1000.0, -250.0, 0.0), False), ((0.0, 0.0, 0.0), True)])
+def test_graph_on_moved_and_flat_scenes(shift, flat):
+    """The graph stage's position grid (the prefilter scans only the cells a source's bound
+    reaches) on coordinates far from the origin, where the bound's ends round by more than its
+    relative margin, and on a scene flattened onto one plane (an axis of zero extent): the graph
+    equals the oracle's."""
+    wl = inputs.make_workload("three_box_1k", 3, 400)
+    st = wl.states.copy()
+    bx = wl.boxes.copy()
+    if flat:
+        st[:, 2] = 0.5
+        st[:, 5] = 0.0
+        bx[:, 2], bx[:, 5] = 0.0, 1.0  # boxes spanning the plane
+    st[:, 0:3] += np.asarray(shift, np.float32)
+    bx[:, 0:3] += np.asarray(shift, np.float32)
+    bx[:, 3:6] += np.asarray(shift, np.float32)
+    wl2 = inputs.Workload(**{**wl.__dict__, "states": st, "boxes": bx})
+    G = gpu_graph(wl2)
+    og = cpu.graph_build(wl2.states, wl2.boxes, wl2.radius, wl2.n_waypoints, wl2.sigma)
+    assert og["n_edges"] > 0
+    ndiff, _ = compare_graphs(export_graph(G), og, wl2.radius)
+    assert ndiff <= max(2, int(1e-4 * og["n_edges"])), ndiff
