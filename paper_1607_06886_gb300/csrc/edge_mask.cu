@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask
     if (t >= (unsigned long long)E) break;
     const long long e1 = min((long long)E, (long long)t + chunk);
     for (long long e = (long long)t; e < e1; ++e)
-      maskdev::edge_mask_one<kNP>(e, xp, N, W, phi, Lg, nom, linf, ibox_g, dmax, boxes, nb, w, my_cand, wm, lane,
+      maskdev::edge_mask_one<kNP, false>(e, xp, N, W, phi, Lg, nom, linf, ibox_g, dmax, boxes, nb, w, my_cand, wm, lane,
                                   mask);
   }
 }
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS)
         if (lane == 0) atomicAdd(bad, 1u);
         continue;
       }
-      maskdev::edge_mask_one<2>(e, xp, N, W, phi, Lg, nom, linf, ibox_g, dmax, boxes, nb, w, my_cand, wm, lane, out,
+      maskdev::edge_mask_one<2, false>(e, xp, N, W, phi, Lg, nom, linf, ibox_g, dmax, boxes, nb, w, my_cand, wm, lane, out,
                                 0, -1, j);
     }
   }

@@ -22,7 +22,9 @@ namespace pump {
 namespace maskdev {
 
 constexpr int kCandCap = 64;
-constexpr int kBoxStride = 8;  // floats per box in shared memory: lo xyz, hi xyz, 2 pad
+// floats per box in shared memory, each coordinate twice (one packed FP32x2 operand):
+// lo x x y y | lo z z, hi x x | hi y y z z, with -0 stored as +0
+constexpr int kBoxStride = 12;
 
 // Shared memory of one block of the query pass before the normals: boxes, per-warp candidate
 // lists and per-warp waypoint box masks (16-byte aligned end).
@@ -67,6 +69,11 @@ __device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigne
   return d;
 }
 
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 __device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
   unsigned long long d;
   asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
@@ -101,18 +108,26 @@ __host__ __device__ constexpr int pair_count(int w) { return (w + 1) / 2; }
 // registers (each half rounds exactly as the scalar dev_init / dev_step and the position add),
 // through waypoints 1..k_last, and tests the boxes left at each.  The words are the warp ballots
 // of each half.  The warp stops early once every lane's particles have hit.
-template <int NP>
+//
+// Box test on packed positions: lo <= p iff p - lo has its sign bit clear, and p <= hi iff hi - p
+// has, for finite values with no -0 on either side (a difference of equal values is +0; only
+// -0 - +0 gives -0).  Boxes are staged with -0 as +0, and the nominal waypoint is taken the same
+// way, so no position is -0 (p = nominal + deviation is -0 only when both are).  Six packed
+// subtractions and the OR of their sign bits test two particles against one box.  kStaged loads
+// the box's three 16-byte rows one at a time beside their tests (fewer live registers); otherwise
+// all three first.
+template <int NP, bool kStaged>
 __device__ __forceinline__ void pair_pass(const float4* __restrict__ xp, int npair, const unsigned long long (&P2)[4],
                                           const unsigned long long (&L2)[3], const unsigned long long (&I2)[3],
                                           const float* __restrict__ nm, int k_last, bool narrow, const uint32_t* wm,
                                           const int* my_cand, bool all, int nc, const float* boxes, int p0, int w,
                                           int lane, uint32_t* out) {
   unsigned long long d0[NP][3], d1[NP][3];
-  bool hit[NP][2];
+  unsigned long long acc[NP];  // the sign bit of each half: that particle has hit a box
   const float4* xq = xp + (size_t)p0 * 32 + lane;
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
-    hit[j][0] = hit[j][1] = false;
+    acc[j] = 0ull;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const float4 x = xq[((size_t)a * npair + j) * 32];
@@ -122,10 +137,11 @@ __device__ __forceinline__ void pair_pass(const float4* __restrict__ xp, int npa
     }
   }
   for (int k = 1; k <= k_last; ++k) {
-    const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
+    const float n0 = __fadd_rn(nm[(k - 1) * 3], 0.f), n1 = __fadd_rn(nm[(k - 1) * 3 + 1], 0.f),
+                n2 = __fadd_rn(nm[(k - 1) * 3 + 2], 0.f);  // -0 as +0
     const unsigned long long N2[3] = {pk2(n0, n0), pk2(n1, n1), pk2(n2, n2)};
     const float4* xk = xq + (size_t)k * 3 * npair * 32;
-    float p[NP][2][3];
+    unsigned long long p[NP][3];  // positions, both halves
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
 #pragma unroll
@@ -138,7 +154,7 @@ __device__ __forceinline__ void pair_pass(const float4* __restrict__ xp, int npa
         const unsigned long long e1 = fma2(P2[2], d0[j][a], fma2(P2[3], d1[j][a], m1));
         d0[j][a] = e0;
         d1[j][a] = e1;
-        upk2(add2(N2[a], e0), p[j][0][a], p[j][1][a]);
+        p[j][a] = add2(N2[a], e0);
       }
     }
     unsigned bits = narrow ? wm[k - 1] : 0u;
@@ -155,18 +171,30 @@ __device__ __forceinline__ void pair_pass(const float4* __restrict__ xp, int npa
         o = all ? c : my_cand[c];
         ++c;
       }
-      const float4 b0 = *reinterpret_cast<const float4*>(boxes + kBoxStride * o);      // lo x, y, z, hi x
-      const float2 b1 = *reinterpret_cast<const float2*>(boxes + kBoxStride * o + 4);  // hi y, z
+      const ulonglong2* bq = reinterpret_cast<const ulonglong2*>(boxes + kBoxStride * o);
+      if (kStaged) {
+        unsigned long long ob[NP];
+        const ulonglong2 q0 = bq[0];  // lo x, lo y
 #pragma unroll
-      for (int j = 0; j < NP; ++j)
+        for (int j = 0; j < NP; ++j) ob[j] = sub2(p[j][0], q0.x) | sub2(p[j][1], q0.y);
+        const ulonglong2 q1 = bq[1];  // lo z, hi x
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-          hit[j][h] = hit[j][h] || (b0.x <= p[j][h][0] && p[j][h][0] <= b0.w && b0.y <= p[j][h][1] &&
-                                    p[j][h][1] <= b1.x && b0.z <= p[j][h][2] && p[j][h][2] <= b1.y);
+        for (int j = 0; j < NP; ++j) ob[j] |= sub2(p[j][2], q1.x) | sub2(q1.y, p[j][0]);
+        const ulonglong2 q2 = bq[2];  // hi y, hi z
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[j] |= ~(ob[j] | sub2(q2.x, p[j][1]) | sub2(q2.y, p[j][2]));
+      } else {
+        const ulonglong2 q0 = bq[0], q1 = bq[1], q2 = bq[2];
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+          acc[j] |= ~(sub2(p[j][0], q0.x) | sub2(q1.y, p[j][0]) | sub2(p[j][1], q0.y) | sub2(q2.x, p[j][1]) |
+                      sub2(p[j][2], q1.x) | sub2(q2.y, p[j][2]));
+      }
     }
-    bool done = true;
+    unsigned long long all_hit = ~0ull;
 #pragma unroll
-    for (int j = 0; j < NP; ++j) done = done && hit[j][0] && hit[j][1];
+    for (int j = 0; j < NP; ++j) all_hit &= acc[j];
+    const bool done = (all_hit & 0x8000000080000000ull) == 0x8000000080000000ull;
     if (__all_sync(0xffffffffu, done)) break;
   }
 #pragma unroll
@@ -174,7 +202,7 @@ __device__ __forceinline__ void pair_pass(const float4* __restrict__ xp, int npa
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int word = 2 * (p0 + j) + h;
-      const unsigned bits = __ballot_sync(0xffffffffu, hit[j][h]);
+      const unsigned bits = __ballot_sync(0xffffffffu, ((acc[j] >> (32 * h + 31)) & 1ull) != 0);
       if (lane == 0 && word < w) out[word] = bits;
     }
 }
@@ -185,7 +213,7 @@ __device__ __forceinline__ void stage(const float* __restrict__ boxes_g, int nb,
                                       const T* __restrict__ xi_g, T* xi_s, int xi_n) {
   for (int k = threadIdx.x; k < kBoxStride * nb; k += blockDim.x) {
     const int o = k / kBoxStride, c = k - o * kBoxStride;
-    boxes[k] = c < 6 ? boxes_g[6 * o + c] : 0.f;
+    boxes[k] = __fadd_rn(boxes_g[6 * o + (c >> 1)], 0.f);  // -0 becomes +0, every other value stays
   }
   if (xi_s)
     for (int k = threadIdx.x; k < xi_n; k += blockDim.x) xi_s[k] = xi_g[k];
@@ -202,7 +230,7 @@ __device__ __forceinline__ void stage(const float* __restrict__ boxes_g, int nb,
 // only those word pairs are computed (an edge with no box left still gets all its words zeroed).
 // my_cand (kCandCap ints) and wm (kMaxWaypoints words) are the warp's shared-memory scratch.
 // The words go to row `row` of mask (row < 0: row e).
-template <int kMaxNP = 2>
+template <int kMaxNP = 2, bool kStaged = true>
 __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restrict__ xp, int N, int W,
                                               const float* __restrict__ phi, const float* __restrict__ Lg,
                                               const float* __restrict__ nom, const float (&linf)[3],
@@ -218,7 +246,7 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
     bool ov = false;
     if (o < nb) {
       const float* b = boxes + kBoxStride * o;
-      ov = b[0] <= hi0 && lo0 <= b[3] && b[1] <= hi1 && lo1 <= b[4] && b[2] <= hi2 && lo2 <= b[5];
+      ov = b[0] <= hi0 && lo0 <= b[6] && b[2] <= hi1 && lo1 <= b[8] && b[4] <= hi2 && lo2 <= b[10];
     }
     const unsigned bal = __ballot_sync(0xffffffffu, ov);
     const int pos = n_cand + __popc(bal & ((1u << lane) - 1u));
@@ -247,9 +275,9 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
     k_last = 0;
     for (int k = 1; k <= W; ++k) {
       const float n0 = nm[(k - 1) * 3], n1 = nm[(k - 1) * 3 + 1], n2 = nm[(k - 1) * 3 + 2];
-      const bool ov = lane < n_cand && bc[0] <= __fadd_rn(n0, M) && __fsub_rn(n0, M) <= bc[3] &&
-                      bc[1] <= __fadd_rn(n1, M) && __fsub_rn(n1, M) <= bc[4] &&
-                      bc[2] <= __fadd_rn(n2, M) && __fsub_rn(n2, M) <= bc[5];
+      const bool ov = lane < n_cand && bc[0] <= __fadd_rn(n0, M) && __fsub_rn(n0, M) <= bc[6] &&
+                      bc[2] <= __fadd_rn(n1, M) && __fsub_rn(n1, M) <= bc[8] &&
+                      bc[4] <= __fadd_rn(n2, M) && __fsub_rn(n2, M) <= bc[10];
       const unsigned m = __ballot_sync(0xffffffffu, ov);
       if (lane == 0) wm[k - 1] = m;
       if (m) k_last = k;
@@ -272,8 +300,8 @@ __device__ __forceinline__ void edge_mask_one(long long e, const float4* __restr
   int p = p_first;
   if (kMaxNP >= 2)
     for (; p + 2 <= pe; p += 2)
-      pair_pass<2>(xp, npair, P2, L2, I2, nm, k_last, narrow, wm, my_cand, all, nc, boxes, p, w, lane, out);
-  for (; p < pe; ++p) pair_pass<1>(xp, npair, P2, L2, I2, nm, k_last, narrow, wm, my_cand, all, nc, boxes, p, w, lane, out);
+      pair_pass<2, kStaged>(xp, npair, P2, L2, I2, nm, k_last, narrow, wm, my_cand, all, nc, boxes, p, w, lane, out);
+  for (; p < pe; ++p) pair_pass<1, kStaged>(xp, npair, P2, L2, I2, nm, k_last, narrow, wm, my_cand, all, nc, boxes, p, w, lane, out);
   __syncwarp();
 }
 
