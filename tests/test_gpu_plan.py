@@ -243,3 +243,35 @@ def test_graph_on_moved_and_flat_scenes(shift, flat):
     assert og["n_edges"] > 0
     ndiff, _ = compare_graphs(export_graph(G), og, wl2.radius)
     assert ndiff <= max(2, int(1e-4 * og["n_edges"])), ndiff
+
+
+def test_masks_with_particles_on_signed_zero_faces():
+    """Every particle exactly on a box face at z = 0: a scene on the plane z = 0 (start states at
+    +0 and -0), normals with zero z components (so every deviation along z is a zero), and boxes
+    whose faces along z are +0 (below the plane), -0 (above it) or both (a slab of zero thickness).
+    A zero compares equal to either sign, so each particle's mask bit is decided by x and y alone.
+    The masks equal the oracle's, and each box catches some particles."""
+    wl = inputs.make_workload("three_box_1k", 5, 400)
+    st = wl.states.copy()
+    st[:, 2] = 0.0
+    st[1::2, 2] = -0.0
+    st[:, 5] = 0.0
+    xi = wl.xi.copy()
+    xi[:, :, 2, :] = 0.0
+    bx = wl.boxes.copy()
+    bx[0, 2], bx[0, 5] = 0.0, 1.0
+    bx[1, 2], bx[1, 5] = -1.0, -0.0
+    bx[2, 2], bx[2, 5] = -0.0, 0.0
+    assert np.signbit(bx[1, 5]) and np.signbit(bx[2, 2])
+    wl2 = inputs.Workload(**{**wl.__dict__, "states": st, "boxes": bx, "xi": xi})
+    G = gpu_graph(wl2)
+    og = cpu.graph_build(wl2.states, wl2.boxes, wl2.radius, wl2.n_waypoints, wl2.sigma)
+    ndiff, diff = compare_graphs(export_graph(G), og, wl2.radius)
+    assert ndiff <= max(2, int(1e-4 * og["n_edges"])), ndiff
+    G.edge_masks()
+    gm = G.export("masks")
+    om = cpu.edge_masks(og, xi, bx, wl2.n_particles)
+    same = ~diff
+    np.testing.assert_array_equal(gm[same], om[same])
+    for b in range(3):
+        assert cpu.edge_masks(og, xi, bx[b:b + 1], wl2.n_particles).any(), b
