@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "pump_internal.cuh"
 
@@ -934,18 +935,25 @@ __global__ void k_linf(float sigma, float* out) {
   out[2] = __double2float_rn(Linf[2]);
 }
 
-__global__ void k_count_valid(const uint8_t* __restrict__ valid, int n, int32_t* out) {
+// What the build reads back at its end, in one copy: out[0] the valid node count (atomics onto a
+// zeroed word), out[1] the start's validity, out[2..4] the bits of L_inf.
+__global__ void k_build_summary(const uint8_t* __restrict__ valid, int n, int32_t start,
+                                const float* __restrict__ linf, int32_t* out) {
   int c = 0;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) c += valid[v];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    out[1] = valid[start];
+    for (int a = 0; a < 3; ++a) out[2 + a] = __float_as_int(linf[a]);
+  }
 }
 
 }  // namespace
 
 // Expects g->states, g->boxes, g->valid, g->is_goal, xi (raw, device) staged.
-int build_graph_device(pump_graph* g, cudaStream_t s) {
+int build_graph_device(pump_graph* g, int32_t start_idx, bool* start_valid, cudaStream_t s) {
   const int n = g->n;
   const int nw = (n + 31) / 32;
   const int sms = num_sms();
@@ -999,7 +1007,7 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
   dev_free(ccnt, s);
   dev_free(d_grid, s);
   uint32_t* keep = (uint32_t*)dev_alloc(sizeof(uint32_t) * (size_t)n * nw, s);
-  int32_t* deg = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)(n + 1), s);
+  int32_t* deg = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)std::max(n + 1, 8), s);
   int32_t* wpre = (int32_t*)dev_alloc(sizeof(int32_t) * (size_t)n * nw, s);
   double* res_tau = (double*)dev_alloc(sizeof(double) * (n_list ? n_list : 1), s);
   float* res_cost = (float*)dev_alloc(sizeof(float) * (n_list ? n_list : 1), s);
@@ -1096,13 +1104,17 @@ int build_graph_device(pump_graph* g, cudaStream_t s) {
     const int rco = row_order_end(g, s);
     if (rco) return rco;
   }
-  // valid node count (for export)
+  // valid node count (for export), the start's validity and L_inf: one read-back
   PUMP_CUDA_TRY(cudaMemsetAsync(deg, 0, sizeof(int32_t), s));
-  k_count_valid<<<32, kBlock, 0, s>>>(g->valid, n, deg);
+  k_build_summary<<<32, kBlock, 0, s>>>(g->valid, n, start_idx, g->linf_dev, deg);
   note_launch();
-  PUMP_CUDA_TRY(cudaMemcpyAsync(&g->n_valid, deg, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  int32_t summary[5] = {0, 0, 0, 0, 0};
+  PUMP_CUDA_TRY(cudaMemcpyAsync(summary, deg, sizeof(summary), cudaMemcpyDeviceToHost, s));
   PUMP_CUDA_TRY(cudaGetLastError());
   PUMP_CUDA_TRY(cudaStreamSynchronize(s));
+  g->n_valid = summary[0];
+  *start_valid = summary[1] != 0;
+  std::memcpy(g->linf, summary + 2, sizeof(float) * 3);
   dev_free(d_count, s);
   if (list) dev_free(list, s);
   if (surv) dev_free(surv, s);

@@ -217,7 +217,7 @@ void* graph_realloc(pump_graph* g, void* old, size_t bytes, cudaStream_t s);
     if (_e != cudaSuccess) return PUMP_ERR_CUDA;   \
   } while (0)
 
-int build_graph_device(pump_graph* g, cudaStream_t s);
+int build_graph_device(pump_graph* g, int32_t start_idx, bool* start_valid, cudaStream_t s);
 // Edge order of the fused form (explore_cluster.cu): begun during the graph build (on a side
 // stream when `overlap`), completed on s before the build returns.
 int row_order_begin(pump_graph* g, cudaStream_t s, bool overlap);

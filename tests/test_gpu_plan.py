@@ -275,3 +275,22 @@ def test_masks_with_particles_on_signed_zero_faces():
     np.testing.assert_array_equal(gm[same], om[same])
     for b in range(3):
         assert cpu.edge_masks(og, xi, bx[b:b + 1], wl2.n_particles).any(), b
+
+
+def test_build_rejects_a_start_inside_a_box_and_stays_usable():
+    """A start state inside an obstacle box is refused (INVALID_ARG), whichever start index it has,
+    and a valid build on the same stream right after it still equals the oracle's graph."""
+    wl = inputs.make_workload("three_box_1k", 0, 300)
+    b = wl.boxes[0]
+    inside = (0.5 * (b[0:3] + b[3:6])).astype(np.float32)
+    for start in (0, 7):
+        st = wl.states.copy()
+        st[start, 0:3] = inside
+        with pytest.raises(pump.PumpError) as e:
+            pump.Graph.build(st, wl.goal_idx, wl.boxes, wl.xi, wl.radius, wl.n_particles, wl.n_waypoints, wl.sigma,
+                             start_idx=start)
+        assert e.value.status == pump.ERR_INVALID_ARG
+    G = gpu_graph(wl)
+    og = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
+    ndiff, _ = compare_graphs(export_graph(G), og, wl.radius)
+    assert ndiff <= max(2, int(1e-4 * og["n_edges"])), ndiff
