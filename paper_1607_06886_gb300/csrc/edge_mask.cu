@@ -24,96 +24,79 @@ __host__ __device__ constexpr size_t edge_mask_hs_fixed_smem() {
   return (sizeof(float4) * kWarps * kHsStage + sizeof(int32_t) * kWarps * (kMaxWaypoints + 1) + 15) & ~(size_t)15;
 }
 
-using maskdev::dev_init;
-using maskdev::dev_step;
 using maskdev::kBoxStride;
 
 __host__ __device__ constexpr size_t edge_mask_fixed_smem(int nb) { return maskdev::fixed_smem(nb, kWarps); }
 
 // Graph-build pass (obstacle independent): per edge the largest |d0| over all particles,
-// waypoints and axes, as float bits.  A warp per edge: lane l runs particles 32 (w0 + j) + l of
-// NW words side by side (pairs of words in packed FP32x2 registers), the edge's Phi and L loaded
-// once; the warp's maximum is stored directly.
-#ifndef PUMP_BOUND_PACKED
-#define PUMP_BOUND_PACKED 1
-#endif
-template <int NW>
-__device__ __forceinline__ float bound_pass(const float2* __restrict__ xi, int N, int W, const float (&P)[4],
-                                            const float (&L)[3], const float (&linf)[3], int w0, int lane) {
-  const float2* xq = xi + w0 * 32 + lane;
-  float m = 0.f;
-  if constexpr (PUMP_BOUND_PACKED && NW % 2 == 0) {
-    const unsigned long long P2[4] = {maskdev::pk2(P[0], P[0]), maskdev::pk2(P[1], P[1]), maskdev::pk2(P[2], P[2]),
-                                      maskdev::pk2(P[3], P[3])};
-    const unsigned long long L2[3] = {maskdev::pk2(L[0], L[0]), maskdev::pk2(L[1], L[1]), maskdev::pk2(L[2], L[2])};
-    const unsigned long long I2[3] = {maskdev::pk2(linf[0], linf[0]), maskdev::pk2(linf[1], linf[1]),
-                                      maskdev::pk2(linf[2], linf[2])};
-    constexpr int NP = NW / 2 > 0 ? NW / 2 : 1;
-    unsigned long long d0[NP][3], d1[NP][3];
+// waypoints and axes, as float bits.  A warp per edge, the edge's Phi and L loaded once: lane l
+// runs the particles of NP word pairs (pair-major normals, one 16-byte load per pair and axis)
+// in the halves of packed FP32x2 registers, with the arithmetic of the query pass; the warp's
+// maximum is stored directly.  Particles past N have zero normals and add nothing.
+template <int NP>
+__device__ __forceinline__ float bound_pass(const float4* __restrict__ xp, int npair, int W,
+                                            const unsigned long long (&P2)[4], const unsigned long long (&L2)[3],
+                                            const unsigned long long (&I2)[3], int p0, int lane) {
+  const float4* xq = xp + (size_t)p0 * 32 + lane;
+  unsigned long long d0[NP][3], d1[NP][3];
 #pragma unroll
-    for (int j = 0; j < NW / 2; ++j)
+  for (int j = 0; j < NP; ++j)
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
-        maskdev::dev_init2(I2, xq[(size_t)a * N + 64 * j], xq[(size_t)a * N + 64 * j + 32], d0[j][a], d1[j][a]);
-    for (int k = 1; k <= W; ++k) {
-      const float2* xk = xq + (size_t)k * 3 * N;
-#pragma unroll
-      for (int j = 0; j < NW / 2; ++j)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          maskdev::dev_step2(P2, L2, xk[(size_t)a * N + 64 * j], xk[(size_t)a * N + 64 * j + 32], d0[j][a], d1[j][a]);
-          float u, v;
-          maskdev::upk2(d0[j][a], u, v);
-          m = fmaxf(m, fmaxf(fabsf(u), fabsf(v)));
-        }
+    for (int a = 0; a < 3; ++a) {
+      const float4 x = xq[((size_t)a * npair + j) * 32];
+      const unsigned long long X0 = maskdev::pk2(x.x, x.y), X1 = maskdev::pk2(x.z, x.w);
+      d0[j][a] = maskdev::mul2(I2[0], X0);
+      d1[j][a] = maskdev::fma2(I2[1], X0, maskdev::mul2(I2[2], X1));
     }
-    return m;
-  } else {
-  float d0[NW][3], d1[NW][3];
-#pragma unroll
-  for (int j = 0; j < NW; ++j)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dev_init(linf, xq[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
+  float m = 0.f;
   for (int k = 1; k <= W; ++k) {
-    const float2* xk = xq + (size_t)k * 3 * N;
+    const float4* xk = xq + (size_t)k * 3 * npair * 32;
 #pragma unroll
-    for (int j = 0; j < NW; ++j)
+    for (int j = 0; j < NP; ++j)
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        dev_step(P, L, xk[(size_t)a * N + 32 * j], d0[j][a], d1[j][a]);
-        m = fmaxf(m, fabsf(d0[j][a]));
+        const float4 x = xk[((size_t)a * npair + j) * 32];
+        const unsigned long long X0 = maskdev::pk2(x.x, x.y), X1 = maskdev::pk2(x.z, x.w);
+        const unsigned long long m0 = maskdev::mul2(L2[0], X0);
+        const unsigned long long m1 = maskdev::fma2(L2[1], X0, maskdev::mul2(L2[2], X1));
+        const unsigned long long e0 = maskdev::fma2(P2[0], d0[j][a], maskdev::fma2(P2[1], d1[j][a], m0));
+        const unsigned long long e1 = maskdev::fma2(P2[2], d0[j][a], maskdev::fma2(P2[3], d1[j][a], m1));
+        d0[j][a] = e0;
+        d1[j][a] = e1;
+        float u, v;
+        maskdev::upk2(e0, u, v);
+        m = fmaxf(m, fmaxf(fabsf(u), fabsf(v)));
       }
   }
   return m;
-  }
 }
 
 template <bool kSmemXi>
-__global__ void __launch_bounds__(kWarps * 32) k_edge_bound(const float2* __restrict__ xi_g, int N, int W,
+__global__ void __launch_bounds__(kWarps * 32) k_edge_bound(const float4* __restrict__ xp_g, int npair, int W,
                                                             const float* __restrict__ phi,
                                                             const float* __restrict__ Lg,
-                                                            const float* __restrict__ linf_g, int E, int w,
+                                                            const float* __restrict__ linf_g, int E,
                                                             unsigned int* __restrict__ dbound) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* xi_s = reinterpret_cast<float2*>(smem);
-  const int xi_n = (W + 1) * 3 * N;
+  float4* xp_s = reinterpret_cast<float4*>(smem);
+  const int xp_n = (W + 1) * 3 * npair * 32;
   if (kSmemXi)
-    for (int k = threadIdx.x; k < xi_n; k += blockDim.x) xi_s[k] = xi_g[k];
+    for (int k = threadIdx.x; k < xp_n; k += blockDim.x) xp_s[k] = xp_g[k];
   __syncthreads();
-  const float2* xi = kSmemXi ? xi_s : xi_g;
-  const float linf[3] = {linf_g[0], linf_g[1], linf_g[2]};
+  const float4* xp = kSmemXi ? xp_s : xp_g;
+  const unsigned long long I2[3] = {maskdev::pk2(linf_g[0], linf_g[0]), maskdev::pk2(linf_g[1], linf_g[1]),
+                                    maskdev::pk2(linf_g[2], linf_g[2])};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (long long e = (long long)blockIdx.x * kWarps + warp; e < E; e += (long long)gridDim.x * kWarps) {
-    const float P[4] = {phi[4 * e], phi[4 * e + 1], phi[4 * e + 2], phi[4 * e + 3]};
-    const float L[3] = {Lg[3 * e], Lg[3 * e + 1], Lg[3 * e + 2]};
+    const float4 ph = *reinterpret_cast<const float4*>(phi + 4 * e);
+    const float l0 = Lg[3 * e], l1 = Lg[3 * e + 1], l2 = Lg[3 * e + 2];
+    const unsigned long long P2[4] = {maskdev::pk2(ph.x, ph.x), maskdev::pk2(ph.y, ph.y), maskdev::pk2(ph.z, ph.z),
+                                      maskdev::pk2(ph.w, ph.w)};
+    const unsigned long long L2[3] = {maskdev::pk2(l0, l0), maskdev::pk2(l1, l1), maskdev::pk2(l2, l2)};
     float m = 0.f;
-    int w0 = 0;
-    for (; w0 + 4 <= w; w0 += 4) m = fmaxf(m, bound_pass<4>(xi, N, W, P, L, linf, w0, lane));
-    if (w0 + 2 <= w) {
-      m = fmaxf(m, bound_pass<2>(xi, N, W, P, L, linf, w0, lane));
-      w0 += 2;
-    }
-    if (w0 < w) m = fmaxf(m, bound_pass<1>(xi, N, W, P, L, linf, w0, lane));
+    int p = 0;
+    for (; p + 2 <= npair; p += 2) m = fmaxf(m, bound_pass<2>(xp, npair, W, P2, L2, I2, p, lane));
+    if (p < npair) m = fmaxf(m, bound_pass<1>(xp, npair, W, P2, L2, I2, p, lane));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) dbound[e] = __float_as_uint(m);
@@ -569,7 +552,8 @@ int compute_edge_bounds(pump_graph* g, cudaStream_t s) {
   g->dmax = (unsigned int*)graph_alloc(g, sizeof(unsigned int) * (size_t)g->E, s);
   unsigned int* dbound = g->dmax;
   if (!dbound) return PUMP_ERR_OOM;
-  const size_t smem_xi = sizeof(float2) * (size_t)(g->W + 1) * 3 * g->N;
+  const int npair = maskdev::pair_count(g->n_words);
+  const size_t smem_xi = sizeof(float4) * (size_t)(g->W + 1) * 3 * npair * 32;
   const bool use_smem = smem_xi <= 160 * 1024;
   const long long items = (long long)g->E;  // a warp per edge
   int grid = 1;
@@ -578,16 +562,16 @@ int compute_edge_bounds(pump_graph* g, cudaStream_t s) {
       const int rco = occupancy_grid(k_edge_bound<true>, smem_xi, kWarps, items, &grid);
       if (rco) return rco;
     }
-    k_edge_bound<true><<<grid, kWarps * 32, smem_xi, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->linf_dev, g->E,
-                                                          g->n_words, dbound);
+    k_edge_bound<true><<<grid, kWarps * 32, smem_xi, s>>>(g->xi_p, npair, g->W, g->phi, g->L, g->linf_dev, g->E,
+                                                          dbound);
     note_launch();
   } else {
     {
       const int rco = occupancy_grid(k_edge_bound<false>, 16, kWarps, items, &grid);
       if (rco) return rco;
     }
-    k_edge_bound<false><<<grid, kWarps * 32, 16, s>>>(g->xi_t, g->N, g->W, g->phi, g->L, g->linf_dev, g->E,
-                                                      g->n_words, dbound);
+    k_edge_bound<false><<<grid, kWarps * 32, 16, s>>>(g->xi_p, npair, g->W, g->phi, g->L, g->linf_dev, g->E,
+                                                      dbound);
     note_launch();
   }
   k_edge_ibox<<<(g->E + 255) / 256, 256, 0, s>>>(g->nom, dbound, g->E, g->W, g->ibox);

@@ -33,19 +33,12 @@ __host__ __device__ constexpr size_t fixed_smem(int nb, int warps) {
           sizeof(uint32_t) * warps * kMaxWaypoints + 15) & ~(size_t)15;
 }
 
-__device__ __forceinline__ void dev_init(const float* linf, float2 x, float& d0, float& d1) {
-  d0 = __fmul_rn(linf[0], x.x);
-  d1 = fmaf(linf[1], x.x, __fmul_rn(linf[2], x.y));
-}
-
-__device__ __forceinline__ void dev_step(const float* P, const float* L, float2 x, float& d0, float& d1) {
-  float n0 = __fmul_rn(L[0], x.x);
-  float n1 = fmaf(L[1], x.x, __fmul_rn(L[2], x.y));
-  float e0 = fmaf(P[0], d0, fmaf(P[1], d1, n0));
-  float e1 = fmaf(P[2], d0, fmaf(P[3], d1, n1));
-  d0 = e0;
-  d1 = e1;
-}
+// The particle deviation recurrence (Section III-B), per axis with normals (x0, x1): at step 0
+// d0 = Linf0 x0, d1 = fma(Linf1, x0, Linf2 x1); at each step k, with the edge's Phi and L,
+// n0 = L0 x0, n1 = fma(L1, x0, L2 x1), d0' = fma(P0, d0, fma(P1, d1, n0)),
+// d1' = fma(P2, d0, fma(P3, d1, n1)), every product and fused multiply-add rounded to nearest in
+// this order; the position offset at waypoint k is the new d0.  The passes below run it on two
+// particles per packed register.
 
 // Two floats in one 64-bit register and the packed FP32x2 operations of sm_100-class parts: each
 // half is rounded exactly as the scalar __fmul_rn / fmaf, so pairs of particles advance with
@@ -80,24 +73,6 @@ __device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigne
   return d;
 }
 
-// dev_init / dev_step for two particles at once (x, y: their normals' pairs).
-__device__ __forceinline__ void dev_init2(const unsigned long long* linf2, float2 x, float2 y, unsigned long long& d0,
-                                          unsigned long long& d1) {
-  const unsigned long long X0 = pk2(x.x, y.x), X1 = pk2(x.y, y.y);
-  d0 = mul2(linf2[0], X0);
-  d1 = fma2(linf2[1], X0, mul2(linf2[2], X1));
-}
-__device__ __forceinline__ void dev_step2(const unsigned long long* P2, const unsigned long long* L2, float2 x, float2 y,
-                                          unsigned long long& d0, unsigned long long& d1) {
-  const unsigned long long X0 = pk2(x.x, y.x), X1 = pk2(x.y, y.y);
-  const unsigned long long n0 = mul2(L2[0], X0);
-  const unsigned long long n1 = fma2(L2[1], X0, mul2(L2[2], X1));
-  const unsigned long long e0 = fma2(P2[0], d0, fma2(P2[1], d1, n0));
-  const unsigned long long e1 = fma2(P2[2], d0, fma2(P2[3], d1, n1));
-  d0 = e0;
-  d1 = e1;
-}
-
 // Pair-major normals.  xi_p[((k * 3 + a) * npair + jp) * 32 + l] = (xi0 of particle 64 jp + l,
 // xi0 of particle 64 jp + 32 + l, xi1 of the first, xi1 of the second) for waypoint step k, axis
 // a: one 16-byte load gives a lane both halves of its particle pair (zeros past N).
@@ -105,7 +80,7 @@ __host__ __device__ constexpr int pair_count(int w) { return (w + 1) / 2; }
 
 // NP pairs of mask words (pairs p0 .. p0 + NP - 1, i.e. words 2 p0 .. 2 (p0 + NP) - 1 below w):
 // lane l advances particles 64 jp + l and 64 jp + 32 + l in the two halves of packed FP32x2
-// registers (each half rounds exactly as the scalar dev_init / dev_step and the position add),
+// registers (each half rounds exactly as the scalar recurrence above and the position add),
 // through waypoints 1..k_last, and tests the boxes left at each.  The words are the warp ballots
 // of each half.  The warp stops early once every lane's particles have hit.
 //
