@@ -126,11 +126,16 @@ __global__ void k_edge_ibox(const float* __restrict__ nom, const unsigned int* _
 // takes the next kMaskChunk edges from a counter (edges differ widely in work: one whose position
 // box meets no obstacle is a few instructions), so no SM idles while others hold long edges.
 #ifndef PUMP_MASK_MIN_BLOCKS
-#define PUMP_MASK_MIN_BLOCKS 3  // 85 registers: three 256-thread blocks per SM (packed pairs of words)
+#define PUMP_MASK_MIN_BLOCKS 3  // 80 registers: three 256-thread blocks per SM (batched and HSMC passes)
+#endif
+#ifndef PUMP_MASK_QUERY_MIN_BLOCKS
+// the single-query passes at 64 registers, four blocks per SM where their staging fits: measured
+// 5 % faster than three blocks at 80 registers (the batched pass spills at 64 and stays at three)
+#define PUMP_MASK_QUERY_MIN_BLOCKS 4
 #endif
 constexpr int kMaskChunk = 4;  // default edges per take
 template <bool kSmemXi, int kNP = 2>
-__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS) k_edge_mask(const float4* __restrict__ xp_g, int N, int W,
+__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_QUERY_MIN_BLOCKS) k_edge_mask(const float4* __restrict__ xp_g, int N, int W,
                                                            const float* __restrict__ phi, const float* __restrict__ Lg,
                                                            const float* __restrict__ nom, const float* __restrict__ linf_g,
                                                            const float* __restrict__ ibox_g,
@@ -245,7 +250,7 @@ __global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS)
 // positions from a counter like k_edge_mask; an id outside [0, E) leaves its row untouched and
 // counts in *bad.
 template <bool kSmemXi>
-__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_MIN_BLOCKS)
+__global__ void __launch_bounds__(kWarps * 32, PUMP_MASK_QUERY_MIN_BLOCKS)
     k_edge_mask_list(const float4* __restrict__ xp_g, int N, int W, const float* __restrict__ phi,
                      const float* __restrict__ Lg, const float* __restrict__ nom, const float* __restrict__ linf_g,
                      const float* __restrict__ ibox_g, const unsigned int* __restrict__ dmax,
