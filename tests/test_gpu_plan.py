@@ -294,3 +294,40 @@ def test_build_rejects_a_start_inside_a_box_and_stays_usable():
     og = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
     ndiff, _ = compare_graphs(export_graph(G), og, wl.radius)
     assert ndiff <= max(2, int(1e-4 * og["n_edges"])), ndiff
+
+
+@pytest.mark.parametrize("N,W", [(1024, 8), (128, 64)])
+def test_masks_and_explore_at_maximum_sizes(N, W):
+    """The largest particle count (32 mask words; the normals no longer fit in shared memory, so the
+    mask, bound and fused kernels read them from global memory) and the largest waypoint count:
+    masks equal the oracle's on every edge with identical descriptors, and the explore-only query
+    (fused form) equals the oracle's explore on the GPU's masks."""
+    wl = inputs.make_workload("three_box_1k", 4, 120)
+    wl.n_particles, wl.n_waypoints = N, W
+    wl.xi = inputs.particle_normals(N, W, 4)
+    G = gpu_graph(wl)
+    og = cpu.graph_build(wl.states, wl.boxes, wl.radius, wl.n_waypoints, wl.sigma)
+    assert og["n_edges"] > 0
+    gg = export_graph(G)
+    ndiff, diff = compare_graphs(gg, og, wl.radius)  # every value within 1 ulp
+    # which values differ where an edge is not bit-identical.  The per-edge model is double on both
+    # sides with different math libraries, rounded to float; at 64 waypoints (h = tau / 64) one GB300
+    # gave 3 of 2403 edges with one L value one ulp apart, every nominal value bit-identical, and none
+    # at 8 or 10 waypoints on the same scene
+    E = og["n_edges"]
+    fields = {k: int((gg[a].reshape(E, -1).view(np.uint32) != og[b].reshape(E, -1).view(np.uint32)).any(axis=1).sum())
+              for k, a, b in (("ecost", "ecost", "ecost"), ("tau", "tau", "tau"), ("phi", "phi", "phi"),
+                              ("L", "L", "L"), ("nominal", "nominal", "nom"))}
+    assert ndiff <= max(4, int(2e-3 * E)), fields
+    G.edge_masks()
+    gm = G.export("masks")
+    om = cpu.edge_masks(og, wl.xi, wl.boxes, N)
+    same = ~diff
+    np.testing.assert_array_equal(gm[same], om[same])
+    assert (om[same] != 0).any()
+    r = G.plan(plan_params(wl, flags=pump.EXPLORE_ONLY))
+    assert r["rc"] == pump.OK
+    kmin, kmax = cpu.cp_thresholds(wl.alpha, wl.eta, N)
+    ex = cpu.explore(og["n"], G.export("row_ptr"), G.export("col"), G.export("ecost"), gm, wl.start_idx, wl.goal_idx,
+                     kmin, kmax, wl.lam, wl.radius)
+    assert_arena_equal(export_arena(G), ex, N // 32)
