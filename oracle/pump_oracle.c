@@ -1105,30 +1105,33 @@ void orc_philox4x32(const uint32_t* ctr_in, const uint32_t* key_in, uint32_t* ou
   for (int q = 0; q < 4; ++q) out[q] = c[q];
 }
 
-/* Standard normal pair from two 24-bit integers (Box and Muller, 1958):      */
-/* u = (bits + 1/2) 2^-24 in (0, 1), z0 = sqrt(-2 ln u1) cos(2 pi u2),          */
+/* Standard normal pair from two nbits-bit integers (Box and Muller, 1958):    */
+/* u = (bits + 1/2) 2^-nbits in (0, 1), z0 = sqrt(-2 ln u1) cos(2 pi u2),       */
 /* z1 = sqrt(-2 ln u1) sin(2 pi u2), evaluated in double and rounded to float.  */
-static void box_muller(uint64_t b1, uint64_t b2, float* z0, float* z1) {
-  double u1 = ((double)b1 + 0.5) * (1.0 / 16777216.0);
-  double u2 = ((double)b2 + 0.5) * (1.0 / 16777216.0);
+static void box_muller(uint64_t b1, uint64_t b2, int nbits, float* z0, float* z1) {
+  const double scale = ldexp(1.0, -nbits);
+  double u1 = ((double)b1 + 0.5) * scale;
+  double u2 = ((double)b2 + 0.5) * scale;
   double rad = sqrt(-2.0 * log(u1));
   double ang = 6.283185307179586476925286766559 * u2;
   *z0 = (float)(rad * cos(ang));
   *z1 = (float)(rad * sin(ang));
 }
 
-/* Normals (xi0, xi1) of rollout m, step s, for the three axes: two            */
-/* Philox4x32-10 calls, counters (m, s lo, q, s hi) for q = 0, 1, key (seed lo, */
-/* seed hi); words w0..w3 of the first call and w4, w5 of the second; axis j    */
-/* takes u1 from the top 24 bits of w(2j) and u2 from those of w(2j+1).          */
+/* Normals (xi0, xi1) of rollout m, step s, for the three axes: one            */
+/* Philox4x32-10 call, counter (m, s lo, 0, s hi), key (seed lo, seed hi),      */
+/* words w0..w3 cut into six 21-bit fields: b_j = top 21 bits of w_j (j < 4),   */
+/* b4 = low 11 bits of w0 then bits 10..1 of w1, b5 the same from w2 and w3;    */
+/* axis j takes u1 from b(2j) and u2 from b(2j+1), u = (b + 1/2) 2^-21.          */
 void orc_mc_normals(uint64_t seed, uint64_t m, uint64_t s, float* xi /* 3 x 2 */) {
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-  uint32_t w[8];
-  for (uint32_t q = 0; q < 2; ++q) {
-    const uint32_t c[4] = {(uint32_t)m, (uint32_t)s, q, (uint32_t)(s >> 32)};
-    orc_philox4x32(c, key, w + 4 * q);
-  }
-  for (int j = 0; j < 3; ++j) box_muller(w[2 * j] >> 8, w[2 * j + 1] >> 8, &xi[2 * j], &xi[2 * j + 1]);
+  const uint32_t c[4] = {(uint32_t)m, (uint32_t)s, 0u, (uint32_t)(s >> 32)};
+  uint32_t w[4];
+  orc_philox4x32(c, key, w);
+  const uint32_t b[6] = {w[0] >> 11, w[1] >> 11, w[2] >> 11, w[3] >> 11,
+                         ((w[0] & 0x7FFu) << 10) | ((w[1] & 0x7FFu) >> 1),
+                         ((w[2] & 0x7FFu) << 10) | ((w[3] & 0x7FFu) >> 1)};
+  for (int j = 0; j < 3; ++j) box_muller(b[2 * j], b[2 * j + 1], 21, &xi[2 * j], &xi[2 * j + 1]);
 }
 
 /* ========================================================================== */
@@ -1218,7 +1221,8 @@ void orc_mlp_draws(uint64_t seed, uint64_t t, uint64_t stream, int64_t rows, int
   for (int64_t r = 0; r < rows; ++r) {
     uint64_t c[4] = {t, (uint64_t)r, stream, 0}, o[4];
     orc_philox4x64(c, key, o);
-    for (int j = 0; j < 4; ++j) box_muller(o[j] >> 40, (o[j] >> 16) & 0xFFFFFFull, &z[8 * r + 2 * j], &z[8 * r + 2 * j + 1]);
+    for (int j = 0; j < 4; ++j)
+      box_muller(o[j] >> 40, (o[j] >> 16) & 0xFFFFFFull, 24, &z[8 * r + 2 * j], &z[8 * r + 2 * j + 1]);
     if (n_env > 0 && env) {
       uint64_t c2[4] = {t, (uint64_t)r, stream + 1, 0};
       orc_philox4x64(c2, key, o);

@@ -13,9 +13,9 @@
 // The first min(|P_goal|, 32) plans are certified in one batch up front, which
 // settles any P_goal of up to 32 plans with a single host synchronisation.
 //
-// MC(p).  One thread per rollout.  Rollout m, step s draws one Philox4x64-10
-// block with counter (m, s, 0, 0) and key (seed, 0); axis j takes word j, whose
-// bits 63..40 and 39..16 give u1, u2 in (0,1), and Box-Muller gives
+// MC(p).  Rollout m, step s draws one Philox4x32-10 block with counter
+// (m, s lo, 0, s hi) and key (seed lo, seed hi); its 128 bits give six 21-bit
+// uniforms u in (0,1) (mc_normals), and Box-Muller gives
 // sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2) in float for (xi0, xi1).  The
 // deviation starts at Linf xi (step 0) and is carried over the plan's
 // connections; each waypoint interval takes `substeps` steps of
@@ -226,18 +226,21 @@ __global__ void __launch_bounds__(kPrepThreads) k_mc_prep(const int32_t* __restr
   }
 }
 
-// Normals of rollout m, step s for the three axes: two Philox4x32-10 calls, counters
-// (m, s lo, q, s hi) for q = 0, 1, key (seed lo, seed hi); words w0..w3, w4, w5; axis j takes u1
-// from the top 24 bits of w(2j) and u2 from those of w(2j+1).
+// Normals of rollout m, step s for the three axes: one Philox4x32-10 call, counter
+// (m, s lo, 0, s hi), key (seed lo, seed hi), its words w0..w3 cut into six 21-bit fields: the
+// top 21 bits of each word, then the low 11 bits of w0 followed by bits 10..1 of w1, and the same
+// from w2 and w3; axis j takes u1 from field 2j and u2 from field 2j + 1, u = (b + 1/2) 2^-21
+// (exact in float).
 __device__ __forceinline__ void mc_normals(uint64_t seed, uint64_t m, uint64_t s, float* z) {
-  uint32_t w[8];
-#pragma unroll
-  for (uint32_t q = 0; q < 2; ++q)
-    philox4x32((uint32_t)m, (uint32_t)s, q, (uint32_t)(s >> 32), (uint32_t)seed, (uint32_t)(seed >> 32), w + 4 * q);
+  uint32_t w[4];
+  philox4x32((uint32_t)m, (uint32_t)s, 0u, (uint32_t)(s >> 32), (uint32_t)seed, (uint32_t)(seed >> 32), w);
+  const uint32_t b[6] = {w[0] >> 11, w[1] >> 11, w[2] >> 11, w[3] >> 11,
+                         ((w[0] & 0x7FFu) << 10) | ((w[1] & 0x7FFu) >> 1),
+                         ((w[2] & 0x7FFu) << 10) | ((w[3] & 0x7FFu) >> 1)};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const float u1 = ((float)(w[2 * j] >> 8) + 0.5f) * 5.9604644775390625e-08f;
-    const float u2 = ((float)(w[2 * j + 1] >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    const float u1 = ((float)b[2 * j] + 0.5f) * 4.76837158203125e-07f;
+    const float u2 = ((float)b[2 * j + 1] + 0.5f) * 4.76837158203125e-07f;
     // hardware log2 and sine/cosine approximations (absolute error ~2^-21); the clamp keeps r
     // real where the approximate log of a u1 just below 1 comes out positive
     const float r = sqrtf(fmaxf(-2.0f * __logf(u1), 0.0f));

@@ -290,12 +290,16 @@ def test_philox4x32_known_answers(ctr, key, out):
 
 
 def test_mc_normals_take_the_documented_philox_words():
-    # rollout m, step s: two Philox4x32-10 calls, counters (m, s lo, q, s hi), key (seed lo, seed hi);
-    # axis j: u1 from the top 24 bits of word 2j, u2 from word 2j + 1, Box-Muller in double
+    # rollout m, step s: one Philox4x32-10 call, counter (m, s lo, 0, s hi), key (seed lo, seed hi);
+    # six 21-bit fields: the top 21 bits of each word, then the low 11 bits of word 0 followed by
+    # bits 10..1 of word 1, and the same from words 2 and 3; axis j: u1 from field 2j, u2 from
+    # field 2j + 1, u = (b + 1/2) / 2^21, Box-Muller in double
     seed, m, s = 0x1234567890ABCDEF, 77, (5 << 32) + 9
-    w = np.concatenate([cpu.philox4x32([m, s & 0xffffffff, q, s >> 32], [seed & 0xffffffff, seed >> 32])
-                        for q in (0, 1)]).astype(np.int64)
-    u = ((w[:6] >> 8).astype(np.float64) + 0.5) / 2.0 ** 24
+    w = np.asarray(cpu.philox4x32([m, s & 0xffffffff, 0, s >> 32], [seed & 0xffffffff, seed >> 32]), np.int64)
+    b = [int(w[0]) >> 11, int(w[1]) >> 11, int(w[2]) >> 11, int(w[3]) >> 11,
+         ((int(w[0]) & 0x7FF) << 10) | ((int(w[1]) & 0x7FF) >> 1), ((int(w[2]) & 0x7FF) << 10) | ((int(w[3]) & 0x7FF) >> 1)]
+    assert all(0 <= x < 2 ** 21 for x in b)
+    u = (np.asarray(b, np.float64) + 0.5) / 2.0 ** 21
     r = np.sqrt(-2.0 * np.log(u[0::2]))
     ang = 2.0 * np.pi * u[1::2]
     ref = np.stack([r * np.cos(ang), r * np.sin(ang)], axis=1).astype(np.float32)
