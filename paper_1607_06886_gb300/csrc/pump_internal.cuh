@@ -386,9 +386,6 @@ __device__ inline Cubic cubic_dev(const double* x0, const double* x1, double tau
   return q;
 }
 __device__ inline double cubic_at(const Cubic& q, double t) { return q.p0 + q.v0 * t + q.c2 * t * t + q.c3 * t * t * t; }
-__device__ inline double nominal_dev(const double* x0, const double* x1, double tau, int j, double t) {
-  return cubic_at(cubic_dev(x0, x1, tau, j), t);
-}
 
 __device__ inline bool in_box_dev(float x, float y, float z, const float* b) {
   return b[0] <= x && x <= b[3] && b[1] <= y && y <= b[4] && b[2] <= z && z <= b[5];
