@@ -102,7 +102,8 @@ def test_gradients_match_oracle(B):
             scale = np.abs(b).max()
             assert np.abs(a - b).max() <= 2e-2 * scale, (l, np.abs(a - b).max(), scale)
             assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b), (l, np.linalg.norm(a - b), np.linalg.norm(b))
-    # parameters untouched
+    # parameters untouched, and the library's vector length is the oracle's count
+    assert m.n_params == orc.param_count(DIMS) == len(p)
     assert np.array_equal(m.get_params()[0], p)
     m.close()
 
