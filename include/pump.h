@@ -360,10 +360,12 @@ void pump_server_destroy(pump_server* s);
  * rollouts of the closed loop: deviation drawn from the stationary
  * covariance at x_init and carried across connections; each waypoint
  * interval split into `substeps` steps of h/substeps; a rollout collides
- * iff a sub-step position lies in a box.  Rollout m, step s takes two
- * Philox4x32-10 calls, counters (m, s lo, q, s hi) for q = 0, 1 and key
- * (seed lo, seed hi); axis j draws its two normals by Box-Muller from the top
- * 24 bits of words 2j and 2j+1 of the eight.  Writes the colliding count and
+ * iff a sub-step position lies in a box.  Rollout m, step s takes one
+ * Philox4x32-10 call, counter (m, s lo, 0, s hi) and key (seed lo, seed hi);
+ * its words w0..w3 give six 21-bit fields (the top 21 bits of each word,
+ * then the low 11 bits of w0 followed by bits 10..1 of w1, and the same from
+ * w2 and w3), and axis j draws its two normals by Box-Muller from fields 2j
+ * and 2j+1, u = (b + 1/2) 2^-21.  Writes the colliding count and
  * count / n_mc.
  * Errors: INVALID_ARG (imported graph, path not along edges), OOM, CUDA.
  * Synchronises.
