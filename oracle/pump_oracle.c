@@ -21,7 +21,8 @@
  *   O4 edge particle collision masks       Section III-B (OR over time, count / N)
  *   O5 Explore                             Algorithm 4 and RemoveDominated, Section IV
  *   O6 PlanSelection and MC(p)             Algorithm 5, Section III-A
- *   Philox4x64-10 counter-based generator  Salmon et al., SC'11
+ *   Philox4x64-10 and Philox4x32-10        Salmon et al., SC'11 (MC normals:
+ *      Philox4x32-10; proposal draws: Philox4x64-10)
  *   O7 draws of the learned sampling proposal (latents, batch rows); the
  *      proposal network itself is restated in oracle/mlp.py
  *
